@@ -1,0 +1,259 @@
+"""Pins for the CPU oracle: each test checks it against something other than
+itself (closed forms, a library routine, brute force on tiny sizes, the
+paper's convergence theory, the invariants of Cahn-Hilliard)."""
+import numpy as np
+import pytest
+import scipy.sparse as sps
+import scipy.sparse.linalg as spla
+
+from oracle import pint_oracle as O
+from paper_2304_14021_gb300 import synth
+
+
+def P(**kw):
+    return O.Problem(**kw)
+
+
+# --- spatial spectra (Sec. 2.2.2 spectral discussion, Remark 2.5) -------------
+
+@pytest.mark.parametrize("bc", ["ss", "neumann"])
+@pytest.mark.parametrize("n", [5, 8, 13])
+def test_laplacian_1d_spectrum_closed_form(bc, n):
+    L = O.laplacian_1d(n, bc).toarray()
+    h = 1.0 / (n + 1) if bc == "ss" else 1.0 / n
+    if bc == "ss":
+        lam = [-(4 / h**2) * np.sin(p * np.pi / (2 * (n + 1))) ** 2 for p in range(1, n + 1)]
+    else:
+        lam = [-(4 / h**2) * np.sin(p * np.pi / (2 * n)) ** 2 for p in range(n)]
+    assert np.allclose(np.sort(np.linalg.eigvalsh(L)), np.sort(lam), rtol=1e-12, atol=1e-9)
+    assert np.allclose(L, L.T)
+
+
+@pytest.mark.parametrize("bc", ["ss", "neumann"])
+def test_laplacian_2d_spectrum_and_modes(bc):
+    p = P(dim=2, nx=6, ny=4, bc=bc)
+    L = O.laplacian(p).toarray()
+    # Eigenvectors are products of the 1-D sine / cosine modes.
+    x, y = synth.grid_points_1d(6, bc), synth.grid_points_1d(4, bc)
+    for (a, b) in [(1, 1), (2, 3), (4, 2)]:
+        if bc == "ss":
+            phi = np.outer(np.sin(b * np.pi * y), np.sin(a * np.pi * x)).ravel()
+            lam = -(4 * 49) * np.sin(a * np.pi / 14) ** 2 - (4 * 25) * np.sin(b * np.pi / 10) ** 2
+        else:
+            a, b = a - 1, b - 1
+            phi = np.outer(np.cos(b * np.pi * y), np.cos(a * np.pi * x)).ravel()
+            lam = -(4 * 36) * np.sin(a * np.pi / 12) ** 2 - (4 * 16) * np.sin(b * np.pi / 8) ** 2
+        assert np.allclose(L @ phi, lam * phi, atol=1e-9 * abs(lam) + 1e-10)
+
+
+def test_neumann_laplacian_conserves_mass():
+    # Column sums vanish: sum(Delta_h u) = 0 for any u (cell-centred Neumann).
+    for p in [P(nx=9, bc="neumann"), P(dim=2, nx=5, ny=7, bc="neumann")]:
+        L = O.laplacian(p)
+        assert np.abs(np.asarray(L.sum(axis=0))).max() < 1e-9
+
+
+# --- exact per-mode decay of the sequential scheme (Eq. 2.5, theta = 1) -------
+
+@pytest.mark.parametrize("eq", [O.BIHARMONIC, O.LINEAR_CH])
+@pytest.mark.parametrize("bc", ["ss", "neumann"])
+def test_sequential_eigenmode_decay(eq, bc):
+    n, nt, T, mode = 24, 12, 3e-4, 3
+    p = P(equation=eq, nx=n, bc=bc, eps=0.05, beta=0.5, T=T, nt=nt)
+    x = synth.grid_points_1d(n, bc)
+    h = 1.0 / (n + 1) if bc == "ss" else 1.0 / n
+    if bc == "ss":
+        phi = np.sin(mode * np.pi * x)
+        lam = -(4 / h**2) * np.sin(mode * np.pi / (2 * (n + 1))) ** 2
+    else:
+        phi = np.cos(mode * np.pi * x)
+        lam = -(4 / h**2) * np.sin(mode * np.pi / (2 * n)) ** 2
+    mu = lam**2 if eq == O.BIHARMONIC else 0.25 * lam + 0.0025 * lam**2
+    U = O.sequential(p, phi)
+    expect = np.array([(1 + p.dt * mu) ** (-(k + 1)) * phi for k in range(nt)])
+    assert O.rel_err(U, expect) < 1e-12
+
+
+def test_config1_closed_form():
+    # 1-D biharmonic, simply supported, 64 vertices, u0 = sin(pi x) + 0.5 sin(3 pi x):
+    # two exact sine modes, so U_n = sum_k a_k (1 + dt lambda_k^2)^{-n} sin(k pi x).
+    n, nt, T = 64, 32, 0.01
+    p = P(equation=O.BIHARMONIC, nx=n, bc="ss", T=T, nt=nt)
+    u0 = synth.u0_sine_modes(n)
+    U = O.sequential(p, u0)
+    x = synth.grid_points_1d(n, "ss")
+    h = 1.0 / 65
+    ex = np.zeros_like(U)
+    for k, a in [(1, 1.0), (3, 0.5)]:
+        lam = -(4 / h**2) * np.sin(k * np.pi / 130) ** 2
+        for m in range(nt):
+            ex[m] += a * (1 + p.dt * lam**2) ** (-(m + 1)) * np.sin(k * np.pi * x)
+    # cond(I + dt A) ~ 1e5 here, so each banded solve carries ~1e-11 roundoff.
+    assert O.rel_err(U, ex) < 2e-11
+
+
+def test_sequential_step_matches_library_sparse_solve():
+    p = P(equation=O.LINEAR_CH, dim=2, nx=8, ny=8, bc="neumann", eps=0.05, beta=0.5, T=1e-3, nt=4)
+    u0 = synth.u0_uniform(64, -0.05, 0.05, 3)
+    U = O.sequential(p, u0)
+    A = O.operator_A(p)
+    M = (np.eye(64) / p.dt + A.toarray())
+    u = u0.copy()
+    for k in range(4):
+        u = spla.spsolve(sps.csr_matrix(M), u / p.dt)
+        assert np.allclose(U[k], u, rtol=1e-12, atol=1e-14)
+
+
+# --- all-at-once system (Eq. 2.6-2.7) vs sequential --------------------------
+
+@pytest.mark.parametrize("theta", [1.0, 0.5])
+@pytest.mark.parametrize("eq,bc,dim", [(O.BIHARMONIC, "ss", 1), (O.LINEAR_CH, "neumann", 1),
+                                       (O.LINEAR_CH, "neumann", 2)])
+def test_all_at_once_dense_equals_sequential(theta, eq, bc, dim):
+    p = P(equation=eq, dim=dim, nx=6, ny=5, bc=bc, eps=0.1, beta=0.4, T=2e-3, nt=6, theta=theta)
+    u0 = synth.u0_uniform(p.nspace, -1, 1, 7)
+    assert O.rel_err(O.all_at_once_dense_linear(p, u0), O.sequential(p, u0)) < 1e-11
+
+
+def test_ch_all_at_once_newton_equals_sequential():
+    p = P(equation=O.CAHN_HILLIARD, nx=12, bc="neumann", eps=0.1, T=4e-3, nt=5)
+    u0 = 0.6 * np.cos(np.pi * synth.grid_points_1d(12, "neumann")) + 0.1
+    assert O.rel_err(O.all_at_once_newton_ch(p, u0), O.sequential(p, u0)) < 1e-11
+
+
+@pytest.mark.parametrize("eq", [O.BIHARMONIC, O.LINEAR_CH, O.CAHN_HILLIARD])
+def test_residual_vanishes_at_sequential_and_equals_b_at_zero(eq):
+    bc = "ss" if eq == O.BIHARMONIC else "neumann"
+    p = P(equation=eq, dim=2, nx=6, ny=6, bc=bc, eps=0.1, beta=0.5, T=2e-3, nt=4)
+    u0 = synth.u0_ch(36, 1, amp=0.5)
+    U = O.sequential(p, u0)
+    r = O.residual(p, u0, U)
+    scale = np.abs(U).max() / p.dt
+    assert np.abs(r).max() < 1e-11 * scale
+    r0 = O.residual(p, u0, np.zeros_like(U))
+    assert np.allclose(r0[0], u0 / p.dt) and np.all(r0[1:] == 0)
+    assert np.isclose(O.rhs_norm(p, u0), np.linalg.norm(u0) / p.dt)
+
+
+# --- the iteration: paper form (Eq. 2.6) vs residual form ---------------------
+
+@pytest.mark.parametrize("theta", [1.0, 0.5])
+def test_paper_form_iterates_equal_residual_form(theta):
+    p = P(equation=O.LINEAR_CH, nx=7, bc="neumann", eps=0.08, beta=0.5, T=5e-3, nt=6,
+          theta=theta, alpha=0.05)
+    u0 = synth.u0_uniform(7, -1, 1, 2)
+    U0 = synth.random_iterate(6, 7, 4)
+    a = O.pint_iteration_paper_form(p, u0, U0, 5)
+    b = O.pint_iteration_residual_form(p, u0, U0, 5)
+    for x, y in zip(a, b):
+        assert O.rel_err(x, y) < 1e-12
+
+
+@pytest.mark.parametrize("eq,dim,theta", [(O.BIHARMONIC, 1, 1.0), (O.LINEAR_CH, 2, 1.0),
+                                          (O.LINEAR_CH, 1, 0.5), (O.CAHN_HILLIARD, 2, 1.0)])
+def test_diagonalized_steps_equal_dense_preconditioner(eq, dim, theta):
+    # Steps 1-3 of Eq. 2.8 (Eq. 4.14) with the Lemma 2.1 eigenvalues == dense P_alpha^{-1}.
+    bc = "ss" if eq == O.BIHARMONIC else "neumann"
+    p = P(equation=eq, dim=dim, nx=6, ny=4, bc=bc, eps=0.1, beta=0.5, T=3e-3, nt=8,
+          theta=theta, alpha=0.02)
+    r = synth.random_iterate(8, p.nspace, 11)
+    jb = 0.7 if eq == O.CAHN_HILLIARD else None
+    d1 = O.diagonalized_apply(p, p.alpha, r, jb)
+    d2 = O.precond_dense(p, p.alpha, r, jb)
+    assert O.rel_err(d1, d2) < 1e-11
+
+
+def test_preconditioner_is_exact_solver_at_alpha_zero_limit():
+    # P_alpha -> K as alpha -> 0: one iteration from U = 0 with tiny alpha lands
+    # on the sequential solution up to O(alpha).
+    p = P(equation=O.BIHARMONIC, nx=10, bc="ss", T=1e-3, nt=8, alpha=1e-9)
+    u0 = synth.u0_sine_modes(10)
+    U1 = O.pint_iteration_residual_form(p, u0, np.zeros((8, 10)), 1)[0]
+    assert O.rel_err(U1, O.sequential(p, u0)) < 1e-7
+
+
+# --- convergence theory (Eq. 2.17-2.18, Thm 2.4, Thm 3.3) ----------------------
+
+def _signed_mode_factors(p):
+    """-alpha R^N / (1 - alpha R^N) per eigenmode of A (Eq. 2.18), R = 1/(1 + dt mu)."""
+    mu, Q = np.linalg.eigh(O.operator_A(p).toarray())
+    RN = (1.0 / (1.0 + p.dt * mu)) ** p.nt
+    return -p.alpha * RN / (1.0 - p.alpha * RN), Q
+
+
+@pytest.mark.parametrize("eq,bc,alpha", [(O.BIHARMONIC, "ss", 0.05), (O.BIHARMONIC, "neumann", 0.05),
+                                         (O.LINEAR_CH, "neumann", 0.05), (O.LINEAR_CH, "neumann", 0.2)])
+def test_per_mode_error_recurrence_and_bounds(eq, bc, alpha):
+    # From the second iterate on, each spatial eigenmode of the last-level error
+    # is multiplied by exactly -alpha R^N/(1 - alpha R^N) per iteration (Eq. 2.17-2.18).
+    p = P(equation=eq, nx=8, bc=bc, eps=0.08, beta=0.5, T=0.02, nt=8, alpha=alpha)
+    u0 = synth.u0_uniform(8, -1, 1, 9)
+    Useq = O.sequential(p, u0)
+    its = O.pint_iteration_paper_form(p, u0, synth.random_iterate(8, 8, 5), 5)
+    fac, Q = _signed_mode_factors(p)
+    E = [Q.T @ (U[-1] - Useq[-1]) for U in its]
+    checked = 0
+    for k in range(1, 4):
+        # roundoff in U (~1e-15) bounds how well a small mode's ratio is resolved
+        floor = 1e-12 * np.abs(E[0]).max()
+        assert np.all(np.abs(E[k] - fac * E[k - 1]) <= 1e-6 * np.abs(E[k - 1]) + floor)
+        checked += int((np.abs(E[k]) > 1e3 * floor).sum())
+    assert checked >= 3
+    exact = O.mode_contraction(p)
+    assert np.isclose(exact, np.abs(fac).max(), rtol=1e-12)
+    if eq == O.BIHARMONIC:
+        assert exact <= O.thm_bound_biharmonic(alpha) * (1 + 1e-12)
+        if bc == "neumann":     # constant mode: mu = 0, R = 1, factor alpha/(1-alpha)
+            assert np.isclose(exact, alpha / (1 - alpha), rtol=1e-12)
+    else:
+        assert exact <= O.thm_bound_linear_ch(p) * (1 + 1e-9)
+
+
+def test_config2_contraction_close_to_thm33_bound():
+    # 2-D linearized CH, 256^2 cell-centred Neumann, beta=0.5, eps=0.05, N_t=128, T=0.1.
+    for alpha in (1e-2, 1e-3):
+        p = P(equation=O.LINEAR_CH, dim=2, nx=256, ny=256, bc="neumann", eps=0.05, beta=0.5,
+              T=0.1, nt=128, alpha=alpha)
+        exact, bound = O.mode_contraction(p), O.thm_bound_linear_ch(p)
+        assert exact <= bound
+        assert exact > 0.999 * bound      # the discrete spectrum nearly hits z*
+        assert 0.9 * alpha < exact < 2.5 * alpha
+
+
+# --- Cahn-Hilliard invariants (Eq. 1.5) ---------------------------------------
+
+def test_ch_mass_conserved_energy_decreasing_2d():
+    p = P(equation=O.CAHN_HILLIARD, dim=2, nx=16, ny=16, bc="neumann", eps=0.05, T=2.4e-3, nt=24)
+    u0 = synth.u0_ch(256, 0)
+    U = O.sequential(p, u0)
+    m0 = O.discrete_mass(p, u0)
+    assert max(abs(O.discrete_mass(p, u) - m0) for u in U) < 1e-12
+    E = [O.discrete_energy(p, u0)] + [O.discrete_energy(p, u) for u in U]
+    assert all(E[i + 1] <= E[i] + 1e-14 for i in range(len(E) - 1))
+    assert E[-1] < E[0]
+
+
+def test_ch_constant_state_is_stationary():
+    p = P(equation=O.CAHN_HILLIARD, dim=2, nx=8, ny=8, bc="neumann", eps=0.02, T=1e-3, nt=5)
+    u0 = np.full(64, 0.3)
+    assert np.abs(O.sequential(p, u0) - 0.3).max() < 1e-14
+
+
+def test_ch_newton_step_solves_the_be_equation():
+    p = P(equation=O.CAHN_HILLIARD, nx=32, bc="neumann", eps=0.05, T=1e-4, nt=1)
+    u0 = synth.u0_ch(32, 4, amp=0.8)
+    u1, its = O.ch_step_newton(p, u0)
+    L = O.laplacian(p).toarray()
+    F = (u1 - u0) / p.dt - L @ (u1**3 - u1) + p.eps**2 * L @ L @ u1
+    assert np.abs(F).max() < 1e-9 * np.abs(u0).max() / p.dt
+    assert its <= 10
+
+
+def test_ch_iteration_converges_to_sequential():
+    # PinT-I (one quasi-Newton step per WR step, scalar averaged Jacobian)
+    # reaches the sequential BE solution (the fixed point is unchanged).
+    p = P(equation=O.CAHN_HILLIARD, nx=16, bc="neumann", eps=0.1, T=4e-3, nt=8, alpha=0.01)
+    u0 = 0.5 * np.cos(np.pi * synth.grid_points_1d(16, "neumann"))
+    Useq = O.sequential(p, u0)
+    its = O.pint_iteration_residual_form(p, u0, np.tile(u0, (8, 1)), 40, dense=False)
+    assert O.rel_err(its[-1], Useq) < 1e-11
