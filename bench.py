@@ -1,0 +1,380 @@
+#!/usr/bin/env python
+"""Throughput of the parallel-in-time solve: space-time DOF/s at relative
+residual 1e-8 on one GB300 (N GPUs: independent replicas, weak scaling).
+
+One step = one pint_solve of the workload from U^0 = u0 (every time level) to
+||b - K(U)|| / ||b|| <= tol: residual, alpha-scaled time FFT, spatial shifted
+solves, inverse FFT + update, repeated until the tolerance is met.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+                  [--alpha A] [--workload NAME] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle
+(sequential backward Euler with banded LU) on a bounded sample of the same
+workload, single-threaded.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# Workloads (synthetic inputs shaped like the paper's experiments).
+WORKLOADS = {
+    # 2-D linearized Cahn-Hilliard, homogeneous Neumann, cell-centred 256x256,
+    # beta = 0.5, eps = 0.05, N_t = 128, T = 0.1, u0 iid uniform[-0.05, 0.05].
+    "linear_ch_2d_256x256_nt128": dict(equation="linear_ch", dim=2, nx=256, ny=256, bc="neumann", eps=0.05,
+                                       beta=0.5, T=0.1, nt=128, n_windows=1, u0="uniform0.05"),
+    # 1-D biharmonic, simply supported, 64 vertices, N_t = 32, T = 0.01, u0 = sin(pi x) + 0.5 sin(3 pi x)
+    "biharmonic_1d_64_nt32": dict(equation="biharmonic", dim=1, nx=64, ny=1, bc="ss", eps=1.0, beta=0.0,
+                                  T=0.01, nt=32, n_windows=1, u0="sines"),
+}
+DEFAULT_WORKLOAD = "linear_ch_2d_256x256_nt128"
+L2_FLUSH_BYTES = 512 * 2**20   # > 129 MB L2
+
+
+def make_u0(wl: dict, seed: int):
+    from paper_2304_14021_gb300 import synth
+    ns = wl["nx"] * (wl["ny"] if wl["dim"] == 2 else 1)
+    if wl["u0"] == "uniform0.05":
+        return synth.u0_uniform(ns, -0.05, 0.05, seed)
+    if wl["u0"] == "sines":
+        return synth.u0_sine_modes(wl["nx"])
+    return synth.u0_ch(ns, seed)
+
+
+def solver_kw(wl: dict, args) -> dict:
+    kw = {k: v for k, v in wl.items() if k != "u0"}
+    kw.update(alpha=args.alpha, tol=args.tol, max_iter=200, precision=args.precision)
+    return kw
+
+
+def phase_bytes_per_dof(precision: str, nt: int) -> dict:
+    """Algorithmic HBM bytes per space-time DOF of each phase (one launch)."""
+    t = 4 if precision == "mixed" else 8                 # real transform word
+    spec = 2 * t * (nt // 2 + 1) / nt                    # half spectrum, complex, per DOF
+    return {
+        "residual": 8 + t,            # read U (f64), write s = gamma r
+        "check": 0.0,
+        "time_fwd": t + spec,         # read s, write S
+        "spatial0": 2 * spec, "spatial1": 2 * spec, "spatial2": 2 * spec,   # read + write S
+        "time_inv": spec + 16,        # read S, read + write U (f64)
+        "setup": 8.0,
+    }
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={CLOCK_Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.idx), "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline): run single-threaded in a child
+# ----------------------------------------------------------------------------
+def cpu_worker(workload: str, alpha: float, budget_s: float, seed: int) -> dict:
+    """Time the oracle's sequential solve on a bounded sample of the workload:
+    the banded LU factorization plus as many time steps as fit in budget_s,
+    extrapolated to the full N_t-step solve (DOF/s)."""
+    import numpy as np
+    import scipy.sparse as sp
+
+    from oracle import pint_oracle as O
+    wl = WORKLOADS[workload]
+    p = O.Problem(**{k: wl[k] for k in ("equation", "dim", "nx", "ny", "bc", "eps", "beta", "T", "nt",
+                                         "n_windows")}, alpha=alpha)
+    u0 = make_u0(wl, seed)
+    if p.equation == O.CAHN_HILLIARD:
+        t0 = time.perf_counter()
+        n = 0
+        u = u0.copy()
+        while n < p.nt and (n == 0 or time.perf_counter() - t0 < budget_s):
+            u, _ = O.ch_step_newton(p, u)
+            n += 1
+        t = time.perf_counter() - t0
+        total = t / n * p.nt
+        sample = f"{n} of {p.nt} Newton BE steps"
+    else:
+        A = O.operator_A(p)
+        I = sp.identity(A.shape[0], format="csr")
+        bw = 2 if p.dim == 1 else 2 * p.nx
+        t0 = time.perf_counter()
+        lu = O.BandedLU(I / p.dt + A, bw, bw)
+        tf = time.perf_counter() - t0
+        rhs = (I / p.dt).tocsr()
+        u = u0.copy()
+        n = 0
+        t1 = time.perf_counter()
+        while n < p.nt and (n == 0 or time.perf_counter() - t1 < budget_s):
+            u = lu.solve(rhs @ u)
+            n += 1
+        ts = (time.perf_counter() - t1) / n
+        total = tf + ts * p.nt
+        sample = (f"banded LU factorization ({tf:.2f} s) + {n} of {p.nt} backward-Euler steps "
+                  f"({ts * 1e3:.1f} ms each), extrapolated to the full {p.nt}-step solve")
+    dof = p.nspace * p.nt
+    _ = np
+    return {"value": dof / total, "seconds_full_solve": total, "sample": sample, "cores": 1}
+
+
+def run_cpu_worker(workload: str, alpha: float, budget_s: float, seed: int = 0) -> dict:
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", "--workload", workload,
+           "--alpha", str(alpha), "--cpu-budget", str(budget_s), "--seed", str(seed)]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError(f"cpu worker failed: {r.stderr[-2000:]}")
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def main_gpu(args) -> None:
+    import numpy as np
+    import torch
+
+    from paper_2304_14021_gb300 import build_lib, pint
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0:
+        build_lib.build()
+    if dist:
+        dist.barrier()
+
+    wl = WORKLOADS[args.workload]
+    kw = solver_kw(wl, args)
+    u0_np = make_u0(wl, args.seed + rank)          # each replica solves its own instance
+    stream = torch.cuda.current_stream()
+    s = pint.Solver(stream=stream, **kw)
+    nt, ns = s.nt, s.nspace
+    dof = nt * ns
+    u0 = torch.from_numpy(u0_np).cuda()
+    U = torch.zeros(nt, ns, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    stats = None
+    for _ in range(args.warmup):
+        stats = s.solve(u0, U)
+    s.profile_enable(True)
+    s.profile_read(reset=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    times = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.zero_()                                # L2 flush outside the timed events
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats = s.solve(u0, U)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    prof = s.profile_read(reset=True)
+    s.profile_enable(False)
+    ms = statistics.mean(times)
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # End to end through the host-buffer entry point: H2D of u0 and D2H of U inside.
+    U_host = torch.zeros(nt, ns, dtype=torch.float64).pin_memory().numpy()
+    u0_host = torch.from_numpy(u0_np.copy()).pin_memory().numpy()
+    s.solve_host(u0_host, U_host)
+    e2e_times = []
+    for _ in range(max(1, args.steps)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.solve_host(u0_host, U_host)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = statistics.mean(e2e_times)
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # Roofline of the dominant phase (largest device time in the timed region).
+    bpd = phase_bytes_per_dof(args.precision, nt)
+    dom = max((k for k in prof if prof[k]["launches"] > 0 and k != "check"), key=lambda k: prof[k]["ms"])
+    per_launch_ms = prof[dom]["ms"] / max(1, prof[dom]["launches"])
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    active_launches = None
+    achieved = bpd[dom] * dof / (per_launch_ms * 1e-3) / 1e9
+    launches_total = sum(v["launches"] for v in prof.values())
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            try:
+                cpu = run_cpu_worker(args.workload, args.alpha, args.cpu_budget, args.seed)
+                cpu = {"value": cpu["value"], "unit": "space-time DOF/s", "cores": cpu["cores"], "kind": "oracle",
+                       "sample": cpu["sample"]}
+            except Exception as ex:  # report, do not hide
+                cpu = {"value": None, "unit": "space-time DOF/s", "cores": 1, "kind": "oracle",
+                       "sample": f"failed: {ex}"}
+        out = {
+            "metric": "space-time DOF/s at rel. residual 1e-8",
+            "value": world * dof / (ms * 1e-3),
+            "unit": "space-time DOF/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "precision": args.precision, "alpha": args.alpha,
+                       "tol": args.tol, "dof_per_gpu": dof, "iterations": stats["iters"],
+                       "final_rel_residual": stats["rel_residual"], "l2": "flushed between steps",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": world * dof / e2e_s, "unit": "space-time DOF/s", "h2d_bytes_per_step": ns * 8,
+                    "d2h_bytes_per_step": dof * 8},
+            "gpu_launches": launches_total,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "bytes_per_dof": bpd[dom], "per_launch_us": per_launch_ms * 1e3},
+            "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
+            "phases_launches_per_step": {k: v["launches"] / args.steps for k, v in prof.items()},
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        _ = active_launches
+        print(json.dumps(out), flush=True)
+    s.close()
+    if dist:
+        dist.destroy_process_group()
+    _ = np
+
+
+def main_reference(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    times, res = [], None
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        res = run_cpu_worker(args.workload, args.alpha, args.cpu_budget, args.seed)
+        if i >= args.warmup:
+            times.append(res["seconds_full_solve"])
+    wl = WORKLOADS[args.workload]
+    dof = wl["nx"] * (wl["ny"] if wl["dim"] == 2 else 1) * wl["nt"]
+    secs = statistics.mean(times)
+    v = dof / secs
+    out = {"impl": "reference", "metric": "space-time DOF/s at rel. residual 1e-8", "value": v,
+           "unit": "space-time DOF/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": secs * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "precision": "fp64 (oracle)", "alpha": args.alpha},
+           "cpu_baseline": {"value": v, "unit": "space-time DOF/s", "cores": 1, "kind": "oracle",
+                            "sample": res["sample"]},
+           "e2e": {"value": v, "unit": "space-time DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--alpha", type=float, default=1e-2)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--cpu-budget", type=float, default=8.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-worker", action="store_true")
+    args = ap.parse_args()
+    if args.cpu_worker:
+        print(json.dumps(cpu_worker(args.workload, args.alpha, args.cpu_budget, args.seed)))
+        return
+    if args.impl == "reference":
+        main_reference(args)
+        return
+    main_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,165 @@
+/*
+ * pint.h - C ABI of libpint: the all-at-once preconditioned iteration of the
+ * diagonalization-based parallel-in-time (PinT) method of Garai & Mandal,
+ * "Diagonalization Based Parallel-in-Time Method for a Class of Fourth Order
+ * Time Dependent PDEs" (arXiv 2304.14021), on one NVIDIA GB300 (sm_103a).
+ *
+ * Equations (paper numbering):
+ *   biharmonic heat         u_t = -Lap^2 u                        (Eq. 1.1, 2.1)
+ *   linearized Cahn-Hilliard u_t = -beta^2 Lap u - eps^2 Lap^2 u  (Eq. 1.2, 3.1)
+ *   Cahn-Hilliard           u_t = Lap(u^3 - u) - eps^2 Lap^2 u    (Eq. 1.3, 4.1)
+ * on [0,1] or [0,1]^2, discretized by centred differences (Eq. 2.4) and
+ * backward Euler (the theta-method of Eq. 2.5 with theta = 1; Eq. 4.5).
+ *
+ * One outer iteration (Sec. 2.1 Eq. 2.6-2.8; Sec. 4.1 Eq. 4.11-4.14, PinT-I)
+ * is computed in residual-correction form,
+ *     U <- U + P_alpha^{-1} (b - K(U)),
+ * with K the alpha = 0 all-at-once operator and P_alpha its alpha-circulant
+ * approximation; P_alpha^{-1} is applied by the three steps of Eq. 2.8:
+ * alpha-scaled FFT along time, one shifted spatial solve per frequency, inverse
+ * FFT and unscaling.  For Cahn-Hilliard the averaged Jacobian of Eq. 4.12 is
+ * the scalar mean of 3u^2 over all space-time points.
+ *
+ * Memory: every pointer named *_dev is a CUDA device pointer in the current
+ * device's primary context; *_host pointers are host memory.  Arrays are FP64,
+ * C-contiguous, time-major [n][y][x] with x fastest (1-D: ny = 1).  The caller
+ * owns all arrays it passes; a handle owns its workspace and tables, allocated
+ * in pint_create and freed in pint_destroy.  All device work is issued on the
+ * stream given to pint_create.  No function throws; each returns a pint code.
+ */
+#ifndef PINT_H
+#define PINT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define PINT_OK          0
+#define PINT_EINVAL     -1   /* invalid or unsupported problem parameter / argument */
+#define PINT_ENOMEM     -2   /* device or host allocation failed */
+#define PINT_ECUDA      -3   /* a CUDA runtime call failed */
+#define PINT_ENOCONV    -4   /* max_iter reached; U holds the last iterate, stats are filled */
+#define PINT_EDIVERGED  -5   /* residual non-finite or grew by 1e6 over its first value */
+
+typedef enum { PINT_BIHARMONIC = 0, PINT_LINEAR_CH = 1, PINT_CAHN_HILLIARD = 2 } pint_equation;
+
+/* Boundary conditions (Sec. 5.1 lists the variants):
+ *  SIMPLY_SUPPORTED: u = Lap u = 0, vertex grid of n interior points, h = 1/(n+1);
+ *                    spatial solves by sine transforms (DST-I).
+ *  NEUMANN:          d_nu u = d_nu Lap u = 0, cell-centred grid of n cells, h = 1/n;
+ *                    spatial solves by cosine transforms (DCT-II), n a power of two. */
+typedef enum { PINT_BC_SIMPLY_SUPPORTED = 0, PINT_BC_NEUMANN = 1 } pint_bc;
+
+/* PINT_FP64:  every step in FP64 (the plain form).
+ * PINT_MIXED: residual, alpha-scaling, unscaling and the update in FP64; the
+ *             time FFTs and the spatial shifted solves in FP32 / complex64, so
+ *             the outer iteration is an iterative refinement. */
+typedef enum { PINT_FP64 = 0, PINT_MIXED = 1 } pint_precision;
+
+/* Problem statement (Eq. 2.1-2.2, 3.1-3.2, 4.1-4.2, the tolerance of Sec. 5). */
+typedef struct {
+    int    equation;     /* pint_equation */
+    int    dim;          /* 1 or 2 */
+    int    nx, ny;       /* grid points per axis; ny ignored (treated as 1) when dim == 1 */
+    int    bc;           /* pint_bc */
+    double eps;          /* interface width epsilon (linear and nonlinear CH) */
+    double beta;         /* beta of the linearized CH equation */
+    double T;            /* final time; dt = T / (nt * n_windows) */
+    int    nt;           /* time steps per window, a power of two in [2, 1024] */
+    int    n_windows;    /* consecutive windows; window w starts from the last step of window w-1 */
+    double theta;        /* theta-method parameter; only 1 (backward Euler) is accepted */
+    double alpha;        /* PinT parameter alpha in (0, 1) (Eq. 2.2) */
+    double tol;          /* stop when ||b - K(U)||_2 / ||b||_2 <= tol */
+    int    max_iter;     /* outer iterations per window, 1..PINT_HIST_MAX */
+    int    precision;    /* pint_precision */
+    int    init_guess;   /* 0: each window starts from U^0 = u0 at every time level;
+                            1: the first window starts from the iterate passed in U */
+} pint_problem;
+
+#define PINT_HIST_MAX 256
+
+typedef struct {
+    int    status;            /* PINT_OK, PINT_ENOCONV or PINT_EDIVERGED of the last window run */
+    int    iters;             /* preconditioner applications, summed over windows */
+    int    windows;           /* windows completed */
+    int    iters_last;        /* iterations of the last window */
+    double rel_residual;      /* final ||r||/||b|| of the last window */
+    double contraction;       /* geometric mean of rho_k / rho_{k-1} over the last window */
+    double jbar;              /* last averaged Jacobian mean(3u^2) (Cahn-Hilliard), else 0 */
+    double hist[PINT_HIST_MAX];  /* rho_0 .. rho_{iters_last} of the last window */
+} pint_stats;
+
+typedef struct pint_handle pint_handle;
+
+/* Validate p, build the eigenvalue / twiddle tables (FP64 on the host) and
+ * allocate the workspace on the current device.  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream).  On success *out owns it all.
+ * Errors: PINT_EINVAL (bad parameter: dim, sizes, nt not a power of two,
+ * NEUMANN with n not a power of two, alpha not in (0,1), theta != 1, ...),
+ * PINT_ENOMEM, PINT_ECUDA. */
+int pint_create(const pint_problem* p, void* cuda_stream, pint_handle** out);
+
+/* Device bytes pint_create would allocate for p (workspace + tables), or a
+ * negative code if p is invalid.  Used for admission by memory footprint. */
+long long pint_footprint(const pint_problem* p);
+
+/* Run the PinT iteration over all windows.
+ *  u0_dev: initial condition, nx*ny doubles (read only).
+ *  U_dev:  nt*nx*ny doubles; on return the iterate of the last window
+ *          (time levels 1..nt of that window).  With init_guess = 1 it also
+ *          supplies the first window's initial iterate.
+ *  st:     may be NULL.
+ * Returns PINT_OK when every window reached tol, else PINT_ENOCONV /
+ * PINT_EDIVERGED (iteration stopped at that window; U holds its last
+ * iterate), or PINT_EINVAL / PINT_ECUDA.  Blocks the host until the stream
+ * has finished the solve. */
+int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* st);
+
+/* pint_solve with host buffers: copies u0_host (and U_host if init_guess = 1)
+ * to handle-owned device buffers, solves, copies the result to U_host. */
+int pint_solve_host(pint_handle* h, const double* u0_host, double* U_host, pint_stats* st);
+
+/* All-at-once residual of one window (Eq. 2.6 / Eq. 4.8 with alpha = 0):
+ * r = b - K(U), b = (u0/dt, 0, ..., 0).  r_dev (nt*nx*ny doubles) may be NULL;
+ * *rel_res (may be NULL) receives ||r||_2 / ||b||_2.  Computed in FP64 in
+ * both precisions. */
+int pint_residual(pint_handle* h, const double* u0_dev, const double* U_dev,
+                  double* r_dev, double* rel_res);
+
+/* One application of the diagonalized preconditioner (Eq. 2.8; Eq. 4.14 for
+ * Cahn-Hilliard with averaged Jacobian jbar): delta = P_alpha^{-1} r, in the
+ * handle's precision.  r_dev, delta_dev: nt*nx*ny doubles (may not alias). */
+int pint_precond_apply(pint_handle* h, double jbar, const double* r_dev, double* delta_dev);
+
+/* Per-phase accounting of the kernels a handle launches.  Phases:
+ *  0 residual (+ alpha-scaling)      1 convergence check (reduction, status)
+ *  2 time FFT (Step 1)               3,4,5 spatial solve stages (Step 2; 1-D uses 3 only)
+ *  6 inverse time FFT + unscale + update (Step 3)     7 window set-up
+ * launches[] is always counted; ms[] (device time between CUDA events
+ * recorded on the handle's stream around each phase) only while enabled. */
+#define PINT_NPHASE 8
+typedef struct {
+    double    ms[PINT_NPHASE];
+    long long launches[PINT_NPHASE];
+} pint_profile;
+
+/* Enable (on = 1) or disable event timing of the phases.  Errors: PINT_EINVAL, PINT_ECUDA. */
+int pint_profile_enable(pint_handle* h, int on);
+
+/* Copy the accumulated profile into *out; reset = 1 zeroes it afterwards. */
+int pint_profile_read(pint_handle* h, pint_profile* out, int reset);
+
+/* Free everything the handle owns (NULL is allowed). */
+void pint_destroy(pint_handle* h);
+
+/* Static description of a return code. */
+const char* pint_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PINT_H */

@@ -1,0 +1,305 @@
+// k_residual.cu - FP64 all-at-once residual, its norm, and the per-iteration
+// control reduction.
+//
+// Residual (Eq. 2.6 / Eq. 4.8 with alpha = 0, theta = 1):
+//   r_n = (u_{n-1} - u_n)/dt - A(u_n),   u_{-1} := u0 (the initial condition),
+//   A(u) = c2 Lap^2 u + c1 Lap u + cN Lap(u^3).
+// Lap is the centred 3-point (1-D) / 5-point (2-D) difference of Eq. 2.4.  The
+// boundary conditions enter as reflections of the grid function: even about
+// the cell face for cell-centred Neumann (u_{-1} = u_0), odd about the
+// boundary vertex for simply supported (u_{-1} = 0, u_{-2} = -u_0).  With
+// those ghost values Lap u is then correct on the ghost layer as well
+// (Neumann: Lap u mirrors; simply supported: Lap u = 0 on the boundary), so
+// Lap^2 u = Lap(Lap u) needs no further boundary logic.
+#include "pint_common.cuh"
+#include "pint_kernels.h"
+
+namespace pint {
+
+// Reflected read of one time level (n fixed) at integer grid index (gx, gy).
+__device__ __forceinline__ double ext_read(const double* __restrict__ u, int gx, int gy, int nx, int ny,
+                                           int dim, int bc) {
+    double sgn = 1.0;
+    if (bc == 1) {  // Neumann, cell-centred: even about the faces at -1/2 and n-1/2
+        if (gx < 0) gx = -1 - gx;
+        else if (gx >= nx) gx = 2 * nx - 1 - gx;
+        if (dim == 2) {
+            if (gy < 0) gy = -1 - gy;
+            else if (gy >= ny) gy = 2 * ny - 1 - gy;
+        }
+    } else {  // simply supported, vertex grid: odd about the boundary vertices -1 and n
+        if (gx == -1 || gx == nx) return 0.0;
+        if (gx < -1) { gx = -2 - gx; sgn = -sgn; }
+        else if (gx > nx) { gx = 2 * nx - gx; sgn = -sgn; }
+        if (dim == 2) {
+            if (gy == -1 || gy == ny) return 0.0;
+            if (gy < -1) { gy = -2 - gy; sgn = -sgn; }
+            else if (gy > ny) { gy = 2 * ny - gy; sgn = -sgn; }
+        }
+    }
+    if (gx < 0 || gx >= nx || (dim == 2 && (gy < 0 || gy >= ny))) return 0.0;  // tiles wider than the grid
+    return sgn * u[(dim == 2 ? gy * nx : 0) + gx];
+}
+
+template <int DIM> struct ResTile;
+template <> struct ResTile<1> { static constexpr int TX = 256, TY = 1; };
+template <> struct ResTile<2> { static constexpr int TX = 32, TY = 8; };
+
+// One CTA: spatial tile TX x TY, time levels [n0, n0 + chunk).
+// Outputs (each optional): r (FP64), s = gamma_n r_n cast to TS.
+// partials[cta] = (sum r^2, sum u^2) over its points.
+template <int DIM, class TS>
+__global__ void __launch_bounds__(256) k_residual(Geo g, const double* __restrict__ U,
+                                                  const double* __restrict__ u0,
+                                                  const double* __restrict__ gam, double* __restrict__ r_out,
+                                                  TS* __restrict__ s_out, double* __restrict__ partials,
+                                                  const Ctl* __restrict__ ctl, int chunk) {
+    if (ctl && ctl->status != ST_RUNNING) return;
+    constexpr int TX = ResTile<DIM>::TX, TY = ResTile<DIM>::TY;
+    constexpr int HY = DIM == 2 ? 2 : 0;
+    constexpr int SX = TX + 4, SY = TY + 2 * HY;
+    constexpr int LX = TX + 2, LY = TY + (DIM == 2 ? 2 : 0);
+    __shared__ double su[SY * SX];
+    __shared__ double sL[LY * LX];
+    __shared__ double red[2][8];
+
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int gx = x0 + tx, gy = y0 + ty;
+    const bool inside = gx < g.nx && (DIM == 1 || gy < g.ny);
+    const int pidx = (DIM == 2 ? gy * g.nx : 0) + gx;
+    const int n0 = blockIdx.z * chunk;
+    const int n1 = min(g.nt, n0 + chunk);
+
+    double uprev = 0.0;
+    if (inside) uprev = n0 == 0 ? u0[pidx] : U[(size_t)(n0 - 1) * g.nspace + pidx];
+    double acc_r2 = 0.0, acc_u2 = 0.0;
+
+    for (int n = n0; n < n1; ++n) {
+        const double* un = U + (size_t)n * g.nspace;
+        for (int e = threadIdx.x; e < SX * SY; e += TX * TY) {
+            int ix = e % SX, iy = e / SX;
+            su[e] = ext_read(un, x0 - 2 + ix, y0 - HY + iy, g.nx, g.ny, DIM, g.bc);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < LX * LY; e += TX * TY) {
+            int ix = e % LX, iy = e / LX;
+            const int c = (DIM == 2 ? (iy + 1) * SX : 0) + ix + 1;  // su index of this L point
+            double v = (su[c - 1] + su[c + 1] - 2.0 * su[c]) * g.ihx2;
+            if (DIM == 2) v += (su[c - SX] + su[c + SX] - 2.0 * su[c]) * g.ihy2;
+            sL[e] = v;
+        }
+        __syncthreads();
+        if (inside) {
+            const int cl = (DIM == 2 ? (ty + 1) * LX : 0) + tx + 1;
+            const int cu = (ty + HY) * SX + tx + 2;
+            const double L = sL[cl];
+            double L2 = (sL[cl - 1] + sL[cl + 1] - 2.0 * L) * g.ihx2;
+            if (DIM == 2) L2 += (sL[cl - LX] + sL[cl + LX] - 2.0 * L) * g.ihy2;
+            const double u = su[cu];
+            double A = g.c2 * L2 + g.c1 * L;
+            if (g.cN != 0.0) {
+                double w0 = u * u * u;
+                double we = su[cu + 1] * su[cu + 1] * su[cu + 1];
+                double ww = su[cu - 1] * su[cu - 1] * su[cu - 1];
+                double lw = (we + ww - 2.0 * w0) * g.ihx2;
+                if (DIM == 2) {
+                    double wn = su[cu - SX] * su[cu - SX] * su[cu - SX];
+                    double ws = su[cu + SX] * su[cu + SX] * su[cu + SX];
+                    lw += (wn + ws - 2.0 * w0) * g.ihy2;
+                }
+                A = fma(g.cN, lw, A);
+            }
+            const double r = (uprev - u) * g.inv_dt - A;
+            const size_t o = (size_t)n * g.nspace + pidx;
+            if (r_out) r_out[o] = r;
+            if (s_out) s_out[o] = (TS)(gam[n] * r);
+            acc_r2 = fma(r, r, acc_r2);
+            acc_u2 = fma(u, u, acc_u2);
+            uprev = u;
+        }
+        __syncthreads();
+    }
+    // deterministic block reduction
+    acc_r2 = warp_sum(acc_r2);
+    acc_u2 = warp_sum(acc_u2);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (lane == 0) { red[0][warp] = acc_r2; red[1][warp] = acc_u2; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (TX * TY) / 32; ++w) { a += red[0][w]; b += red[1][w]; }
+        size_t cta = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        partials[2 * cta] = a;
+        partials[2 * cta + 1] = b;
+    }
+}
+
+// partials[cta] = (sum u0^2, 0) over a 1-D chunking of u0.
+__global__ void __launch_bounds__(256) k_norm2(const double* __restrict__ v, int n, double* __restrict__ partials) {
+    __shared__ double red[8];
+    double a = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a = fma(v[i], v[i], a);
+    a = warp_sum(a);
+    if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += red[w];
+        partials[2 * blockIdx.x] = s;
+        partials[2 * blockIdx.x + 1] = 0.0;
+    }
+}
+
+// Sum the (a, b) partial pairs in a fixed order; one CTA of 256 threads.
+__device__ void reduce_pairs(const double* __restrict__ partials, int np, double& A, double& B) {
+    __shared__ double ra[8], rb[8];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < np; i += 256) { a += partials[2 * i]; b += partials[2 * i + 1]; }
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (threadIdx.x % 32 == 0) { ra[threadIdx.x / 32] = a; rb[threadIdx.x / 32] = b; }
+    __syncthreads();
+    A = 0.0;
+    B = 0.0;
+    for (int w = 0; w < 8; ++w) { A += ra[w]; B += rb[w]; }
+}
+
+// Start of a window: ||b|| = ||u0|| / dt (theta = 1), reset the iteration state.
+__global__ void __launch_bounds__(256) k_begin_window(const double* __restrict__ partials, int np, double inv_dt,
+                                                      int max_iter, double tol, Ctl* ctl) {
+    double A, B;
+    reduce_pairs(partials, np, A, B);
+    if (threadIdx.x == 0) {
+        ctl->bnorm = sqrt(A) * inv_dt;
+        ctl->status = ST_RUNNING;
+        ctl->iter = 0;
+        ctl->max_iter = max_iter;
+        ctl->tol = tol;
+        ctl->rho0 = 0.0;
+        ctl->rho = 0.0;
+    }
+}
+
+// After the residual of iterate k: rho_k, jbar, stopping decision.
+__global__ void __launch_bounds__(256) k_after_residual(const double* __restrict__ partials, int np,
+                                                        double inv_dof, Ctl* ctl) {
+    if (ctl->status != ST_RUNNING) return;
+    double A, B;
+    reduce_pairs(partials, np, A, B);
+    if (threadIdx.x == 0) {
+        const int k = ctl->iter;
+        const double bn = ctl->bnorm;
+        const double rho = bn > 0.0 ? sqrt(A) / bn : sqrt(A);
+        ctl->sum_r2 = A;
+        ctl->sum_u2 = B;
+        ctl->rho = rho;
+        ctl->jbar = 3.0 * B * inv_dof;
+        if (k < 256) ctl->hist[k] = rho;
+        if (k == 0) ctl->rho0 = rho;
+        if (!(rho == rho) || rho > 1e300 || (k > 0 && rho > 1e6 * ctl->rho0)) ctl->status = -5;  // PINT_EDIVERGED
+        else if (rho <= ctl->tol) ctl->status = 0;                                              // PINT_OK
+        else if (k >= ctl->max_iter) ctl->status = -4;                                          // PINT_ENOCONV
+        else ctl->iter = k + 1;
+    }
+}
+
+// Plain reduction for pint_residual: ctl->rho = sqrt(sum r^2)/bnorm, status untouched.
+__global__ void __launch_bounds__(256) k_residual_norm(const double* __restrict__ partials, int np, Ctl* ctl) {
+    double A, B;
+    reduce_pairs(partials, np, A, B);
+    if (threadIdx.x == 0) {
+        const double bn = ctl->bnorm;
+        ctl->sum_r2 = A;
+        ctl->rho = bn > 0.0 ? sqrt(A) / bn : sqrt(A);
+    }
+}
+
+__global__ void k_set_running(Ctl* ctl, double jbar) {
+    ctl->status = ST_RUNNING;
+    ctl->jbar = jbar;
+}
+
+// U[n][p] = u0[p] for all n.
+__global__ void k_broadcast(double* __restrict__ U, const double* __restrict__ u0, int nspace, int nt) {
+    size_t total = (size_t)nspace * nt;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x)
+        U[i] = u0[i % nspace];
+}
+
+// s[n][p] = (TS)(gamma_n r[n][p])  (the alpha-scaling of Step 1 for pint_precond_apply)
+template <class TS>
+__global__ void k_scale_cast(const double* __restrict__ r, const double* __restrict__ gam, TS* __restrict__ s,
+                             int nspace, int nt) {
+    size_t total = (size_t)nspace * nt;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x)
+        s[i] = (TS)(gam[i / nspace] * r[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+int residual_grid(const Geo& g, int& gx, int& gy, int& gz, int& chunk) {
+    const int TX = g.dim == 2 ? 32 : 256, TY = g.dim == 2 ? 8 : 1;
+    gx = (g.nx + TX - 1) / TX;
+    gy = g.dim == 2 ? (g.ny + TY - 1) / TY : 1;
+    const long tiles = (long)gx * gy;
+    // enough CTAs for ~4 waves of 152 SMs, at least 4 time levels per CTA
+    long want = (608 + tiles - 1) / tiles;
+    chunk = (int)((g.nt + want - 1) / want);
+    if (chunk < 4) chunk = 4;
+    if (chunk > g.nt) chunk = g.nt;
+    gz = (g.nt + chunk - 1) / chunk;
+    return gx * gy * gz;
+}
+
+template <class TS>
+void launch_residual(const Geo& g, const double* U, const double* u0, const double* gam, double* r_out, TS* s_out,
+                     double* partials, const Ctl* ctl, cudaStream_t st) {
+    int gx, gy, gz, chunk;
+    residual_grid(g, gx, gy, gz, chunk);
+    dim3 grid(gx, gy, gz);
+    if (g.dim == 2)
+        k_residual<2, TS><<<grid, 256, 0, st>>>(g, U, u0, gam, r_out, s_out, partials, ctl, chunk);
+    else
+        k_residual<1, TS><<<grid, 256, 0, st>>>(g, U, u0, gam, r_out, s_out, partials, ctl, chunk);
+}
+template void launch_residual<float>(const Geo&, const double*, const double*, const double*, double*, float*,
+                                     double*, const Ctl*, cudaStream_t);
+template void launch_residual<double>(const Geo&, const double*, const double*, const double*, double*, double*,
+                                      double*, const Ctl*, cudaStream_t);
+
+int norm2_blocks(int n) {
+    int b = (n + 255) / 256;
+    return b > 1024 ? 1024 : (b < 1 ? 1 : b);
+}
+void launch_begin_window(const double* u0, int nspace, double inv_dt, int max_iter, double tol, double* partials,
+                         Ctl* ctl, cudaStream_t st) {
+    int nb = norm2_blocks(nspace);
+    k_norm2<<<nb, 256, 0, st>>>(u0, nspace, partials);
+    k_begin_window<<<1, 256, 0, st>>>(partials, nb, inv_dt, max_iter, tol, ctl);
+}
+void launch_after_residual(const double* partials, int np, double inv_dof, Ctl* ctl, cudaStream_t st) {
+    k_after_residual<<<1, 256, 0, st>>>(partials, np, inv_dof, ctl);
+}
+void launch_residual_norm(const double* partials, int np, Ctl* ctl, cudaStream_t st) {
+    k_residual_norm<<<1, 256, 0, st>>>(partials, np, ctl);
+}
+void launch_set_running(Ctl* ctl, double jbar, cudaStream_t st) { k_set_running<<<1, 1, 0, st>>>(ctl, jbar); }
+void launch_broadcast(double* U, const double* u0, int nspace, int nt, cudaStream_t st) {
+    size_t total = (size_t)nspace * nt;
+    int nb = (int)((total + 255) / 256);
+    if (nb > 4 * 152 * 8) nb = 4 * 152 * 8;
+    k_broadcast<<<nb, 256, 0, st>>>(U, u0, nspace, nt);
+}
+template <class TS>
+void launch_scale_cast(const double* r, const double* gam, TS* s, int nspace, int nt, cudaStream_t st) {
+    size_t total = (size_t)nspace * nt;
+    int nb = (int)((total + 255) / 256);
+    if (nb > 4 * 152 * 8) nb = 4 * 152 * 8;
+    k_scale_cast<TS><<<nb, 256, 0, st>>>(r, gam, s, nspace, nt);
+}
+template void launch_scale_cast<float>(const double*, const double*, float*, int, int, cudaStream_t);
+template void launch_scale_cast<double>(const double*, const double*, double*, int, int, cudaStream_t);
+
+}  // namespace pint

@@ -1,0 +1,172 @@
+// k_timefft.cu - Steps 1 and 3 of the diagonalized solve (Eq. 2.8): the FFT
+// along the time axis of the (already alpha-scaled) space-time block and its
+// inverse followed by the Gamma_alpha^{-1} unscaling.
+//
+// The time signal at each spatial point is real, so two spatial points share
+// one complex FFT (point a in the real part, point b in the imaginary part):
+//   forward:  Z = FFT(s_a + i s_b),  S_a[k] = (Z_k + conj Z_{N-k})/2,
+//             S_b[k] = (Z_k - conj Z_{N-k})/(2i),   k = 0..N/2;
+//   inverse:  Z_k = S_a[k] + i S_b[k] over the full Hermitian spectrum,
+//             z = IFFT(Z),  x_a = Re z, x_b = Im z.
+// A CTA holds CW complex columns (2*CW consecutive spatial points) times all
+// N_t time levels in shared memory: loads and stores are rows of CW
+// consecutive values per time level / frequency, i.e. coalesced.
+#include "pint_common.cuh"
+#include "pint_kernels.h"
+
+namespace pint {
+
+template <class T, int NT> struct TimeCfg {
+    static constexpr int CW = sizeof(T) == 4 ? (NT <= 512 ? 32 : 16) : (NT <= 256 ? 32 : (NT == 512 ? 16 : 8));
+    static constexpr int NTH = NT <= 256 ? 256 : 512;
+    static constexpr size_t SMEM = sizeof(c_t<T>) * ((size_t)NT * CW + NT);
+};
+
+template <class T, int NT>
+__global__ void __launch_bounds__(TimeCfg<T, NT>::NTH)
+    k_time_fwd(int nspace, const T* __restrict__ s, c_t<T>* __restrict__ S, const c_t<T>* __restrict__ twt,
+               const Ctl* __restrict__ ctl) {
+    using C = c_t<T>;
+    constexpr int CW = TimeCfg<T, NT>::CW, NTH = TimeCfg<T, NT>::NTH;
+    if (ctl && ctl->status != ST_RUNNING) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* z = reinterpret_cast<C*>(smem_raw);
+    C* tw = z + NT * CW;
+    const int tid = threadIdx.x;
+    const long p0 = (long)blockIdx.x * 2 * CW;
+    for (int i = tid; i < NT; i += NTH) tw[i] = twt[i];
+    for (int e = tid; e < NT * CW; e += NTH) {
+        const int c = e % CW, n = e / CW;
+        const long pa = p0 + c, pb = p0 + CW + c;
+        const T* row = s + (size_t)n * nspace;
+        T a = pa < nspace ? row[pa] : T(0);
+        T b = pb < nspace ? row[pb] : T(0);
+        z[e] = mkc(a, b);
+    }
+    __syncthreads();
+    smem_fft<C, NT, -1, NTH, CW, CW, 1>(z, tw);
+    const T half = T(0.5);
+    for (int e = tid; e < (NT / 2 + 1) * CW; e += NTH) {
+        const int c = e % CW, k = e / CW;
+        const C zk = z[k * CW + c];
+        const C zr = z[((NT - k) % NT) * CW + c];
+        const long pa = p0 + c, pb = p0 + CW + c;
+        C* row = S + (size_t)k * nspace;
+        if (pa < nspace) row[pa] = mkc(half * (zk.x + zr.x), half * (zk.y - zr.y));
+        if (pb < nspace) row[pb] = mkc(half * (zk.y + zr.y), half * (zr.x - zk.x));
+    }
+}
+
+template <class T, int NT>
+__global__ void __launch_bounds__(TimeCfg<T, NT>::NTH)
+    k_time_inv(int nspace, const c_t<T>* __restrict__ S, const c_t<T>* __restrict__ twt,
+               const double* __restrict__ ginv, double* __restrict__ out, int accumulate,
+               const Ctl* __restrict__ ctl) {
+    using C = c_t<T>;
+    constexpr int CW = TimeCfg<T, NT>::CW, NTH = TimeCfg<T, NT>::NTH;
+    if (ctl && ctl->status != ST_RUNNING) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* z = reinterpret_cast<C*>(smem_raw);
+    C* tw = z + NT * CW;
+    const int tid = threadIdx.x;
+    const long p0 = (long)blockIdx.x * 2 * CW;
+    for (int i = tid; i < NT; i += NTH) tw[i] = twt[i];
+    for (int e = tid; e < (NT / 2 + 1) * CW; e += NTH) {
+        const int c = e % CW, k = e / CW;
+        const long pa = p0 + c, pb = p0 + CW + c;
+        const C* row = S + (size_t)k * nspace;
+        C a = pa < nspace ? row[pa] : mkc(T(0), T(0));
+        C b = pb < nspace ? row[pb] : mkc(T(0), T(0));
+        if (k == 0 || k == NT / 2) { a.y = T(0); b.y = T(0); }  // real in exact arithmetic
+        z[k * CW + c] = mkc(a.x - b.y, a.y + b.x);
+        if (k > 0 && k < NT / 2) z[(NT - k) * CW + c] = mkc(a.x + b.y, b.x - a.y);
+    }
+    __syncthreads();
+    smem_fft<C, NT, +1, NTH, CW, CW, 1>(z, tw);
+    for (int e = tid; e < NT * CW; e += NTH) {
+        const int c = e % CW, n = e / CW;
+        const C v = z[e];
+        const double gi = ginv[n];
+        const long pa = p0 + c, pb = p0 + CW + c;
+        double* row = out + (size_t)n * nspace;
+        const double da = (double)v.x * gi, db = (double)v.y * gi;   // FP64 unscaling
+        if (accumulate) {
+            if (pa < nspace) row[pa] += da;
+            if (pb < nspace) row[pb] += db;
+        } else {
+            if (pa < nspace) row[pa] = da;
+            if (pb < nspace) row[pb] = db;
+        }
+    }
+}
+
+template <class T, int NT>
+static cudaError_t configure_time() {
+    cudaError_t e = cudaFuncSetAttribute(k_time_fwd<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)TimeCfg<T, NT>::SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_time_inv<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)TimeCfg<T, NT>::SMEM);
+}
+
+template <class T>
+cudaError_t configure_time_all() {
+    cudaError_t e;
+#define PINT_CFG(NT) if ((e = configure_time<T, NT>()) != cudaSuccess) return e;
+    PINT_CFG(2) PINT_CFG(4) PINT_CFG(8) PINT_CFG(16) PINT_CFG(32) PINT_CFG(64) PINT_CFG(128) PINT_CFG(256)
+    PINT_CFG(512) PINT_CFG(1024)
+#undef PINT_CFG
+    return cudaSuccess;
+}
+template cudaError_t configure_time_all<float>();
+template cudaError_t configure_time_all<double>();
+
+template <class T, int NT>
+static void time_fwd_nt(int nspace, const T* s, c_t<T>* S, const c_t<T>* twt, const Ctl* ctl, cudaStream_t st) {
+    constexpr int CW = TimeCfg<T, NT>::CW;
+    int grid = (nspace + 2 * CW - 1) / (2 * CW);
+    k_time_fwd<T, NT><<<grid, TimeCfg<T, NT>::NTH, TimeCfg<T, NT>::SMEM, st>>>(nspace, s, S, twt, ctl);
+}
+template <class T, int NT>
+static void time_inv_nt(int nspace, const c_t<T>* S, const c_t<T>* twt, const double* ginv, double* out, int acc,
+                        const Ctl* ctl, cudaStream_t st) {
+    constexpr int CW = TimeCfg<T, NT>::CW;
+    int grid = (nspace + 2 * CW - 1) / (2 * CW);
+    k_time_inv<T, NT><<<grid, TimeCfg<T, NT>::NTH, TimeCfg<T, NT>::SMEM, st>>>(nspace, S, twt, ginv, out, acc, ctl);
+}
+
+#define PINT_NT_SWITCH(CALL)                                                                            \
+    switch (nt) {                                                                                       \
+        case 2: CALL(2); break;     case 4: CALL(4); break;     case 8: CALL(8); break;                 \
+        case 16: CALL(16); break;   case 32: CALL(32); break;   case 64: CALL(64); break;               \
+        case 128: CALL(128); break; case 256: CALL(256); break; case 512: CALL(512); break;             \
+        case 1024: CALL(1024); break;                                                                   \
+        default: return cudaErrorInvalidValue;                                                          \
+    }
+
+template <class T>
+cudaError_t launch_time_fwd(int nt, int nspace, const T* s, c_t<T>* S, const c_t<T>* twt, const Ctl* ctl,
+                            cudaStream_t st) {
+#define CALL(N) time_fwd_nt<T, N>(nspace, s, S, twt, ctl, st)
+    PINT_NT_SWITCH(CALL)
+#undef CALL
+    return cudaGetLastError();
+}
+template <class T>
+cudaError_t launch_time_inv(int nt, int nspace, const c_t<T>* S, const c_t<T>* twt, const double* ginv, double* out,
+                            int accumulate, const Ctl* ctl, cudaStream_t st) {
+#define CALL(N) time_inv_nt<T, N>(nspace, S, twt, ginv, out, accumulate, ctl, st)
+    PINT_NT_SWITCH(CALL)
+#undef CALL
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_time_fwd<float>(int, int, const float*, float2*, const float2*, const Ctl*, cudaStream_t);
+template cudaError_t launch_time_fwd<double>(int, int, const double*, double2*, const double2*, const Ctl*,
+                                             cudaStream_t);
+template cudaError_t launch_time_inv<float>(int, int, const float2*, const float2*, const double*, double*, int,
+                                            const Ctl*, cudaStream_t);
+template cudaError_t launch_time_inv<double>(int, int, const double2*, const double2*, const double*, double*, int,
+                                             const Ctl*, cudaStream_t);
+
+}  // namespace pint

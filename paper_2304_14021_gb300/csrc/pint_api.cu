@@ -1,0 +1,588 @@
+// pint_api.cu - the C ABI of libpint (declared in include/pint.h): handle
+// lifetime, host-built FP64 tables, and the outer iteration
+//     U <- U + P_alpha^{-1} (b - K(U))
+// (residual-correction form of the PinT iteration, Eq. 2.6-2.8; PinT-I of
+// Eq. 4.11-4.14 for Cahn-Hilliard) driven from the host in chunks of
+// iterations with a device-side status word, so the host reads back one small
+// control block per chunk instead of synchronizing every iteration.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <complex>
+#include <new>
+#include <vector>
+
+#include "../../include/pint.h"
+#include "pint_common.cuh"
+#include "pint_kernels.h"
+
+namespace pint {
+
+template <class T> cudaError_t configure_time_all();
+template <class T> cudaError_t configure_spatial_all();
+
+cudaError_t configure_kernels() {
+    static int done = -1;  // per process: the attributes are per device function
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorUnknown;
+    if (done == dev) return cudaSuccess;
+    cudaError_t e;
+    if ((e = configure_time_all<float>()) != cudaSuccess) return e;
+    if ((e = configure_time_all<double>()) != cudaSuccess) return e;
+    if ((e = configure_spatial_all<float>()) != cudaSuccess) return e;
+    if ((e = configure_spatial_all<double>()) != cudaSuccess) return e;
+    done = dev;
+    return cudaSuccess;
+}
+
+static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// Per-axis transform path: 1 = FFT-based cosine transform, 0 = dense basis.
+static int axis_fft(int n, int bc, int nmax_fft) { return bc == PINT_BC_NEUMANN && is_pow2(n) && n >= 2 && n <= nmax_fft; }
+
+static int validate(const pint_problem* p) {
+    if (!p) return PINT_EINVAL;
+    if (p->equation < 0 || p->equation > 2) return PINT_EINVAL;
+    if (p->dim != 1 && p->dim != 2) return PINT_EINVAL;
+    if (p->bc != PINT_BC_SIMPLY_SUPPORTED && p->bc != PINT_BC_NEUMANN) return PINT_EINVAL;
+    if (p->nx < 2 || (p->dim == 2 && p->ny < 2)) return PINT_EINVAL;
+    if (!is_pow2(p->nt) || p->nt < 2 || p->nt > 1024) return PINT_EINVAL;
+    if (p->n_windows < 1) return PINT_EINVAL;
+    if (p->theta != 1.0) return PINT_EINVAL;
+    if (!(p->alpha > 0.0 && p->alpha < 1.0)) return PINT_EINVAL;
+    if (!(p->tol > 0.0) || !isfinite(p->tol)) return PINT_EINVAL;
+    if (p->max_iter < 1 || p->max_iter >= PINT_HIST_MAX) return PINT_EINVAL;
+    if (p->precision != PINT_FP64 && p->precision != PINT_MIXED) return PINT_EINVAL;
+    if (!(p->T > 0.0) || !isfinite(p->T)) return PINT_EINVAL;
+    if (p->equation != PINT_BIHARMONIC && !(p->eps > 0.0)) return PINT_EINVAL;
+    if (!isfinite(p->beta) || !isfinite(p->eps)) return PINT_EINVAL;
+    if (p->init_guess != 0 && p->init_guess != 1) return PINT_EINVAL;
+    const int ny = p->dim == 2 ? p->ny : 1;
+    if (!axis_fft(p->nx, p->bc, 4096) && p->nx > 1024) return PINT_EINVAL;
+    if (p->dim == 2 && !axis_fft(ny, p->bc, 1024) && ny > 1024) return PINT_EINVAL;
+    if ((long long)p->nx * ny > (1LL << 30)) return PINT_EINVAL;
+    return PINT_OK;
+}
+
+static double grid_h(int n, int bc) { return bc == PINT_BC_SIMPLY_SUPPORTED ? 1.0 / (n + 1) : 1.0 / n; }
+
+// Eigenvalue of the 1-D Delta_h for transform index p (Sec. 2.2 spectrum).
+static double lap_eig(int p, int n, int bc) {
+    const double h = grid_h(n, bc);
+    const double s = bc == PINT_BC_SIMPLY_SUPPORTED ? sin(M_PI * (p + 1) / (2.0 * (n + 1))) : sin(M_PI * p / (2.0 * n));
+    return -4.0 / (h * h) * s * s;
+}
+
+struct Sizes {
+    size_t nspace, dof, nk, partials, tables_T, tables_bytes;
+};
+
+template <class T> struct Impl;
+
+}  // namespace pint
+
+struct pint_handle {
+    pint_problem p;
+    cudaStream_t st;
+    int fft_x, fft_y;
+    pint::Geo geo;
+    pint::SolveCoef coef;
+    pint::Ctl* ctl = nullptr;       // device
+    pint::Ctl* hctl = nullptr;      // pinned host mirror
+    double* partials = nullptr;
+    int npart = 0;
+    double* gam = nullptr;          // alpha^{n/nt}
+    double* ginv = nullptr;         // alpha^{-n/nt} / nt
+    double* u0buf = nullptr;        // window initial condition
+    double* hU = nullptr;           // pint_solve_host buffers (lazy)
+    double* hu0 = nullptr;
+    void* s = nullptr;              // alpha-scaled residual, transform precision
+    void* S = nullptr;              // half spectrum, complex transform precision
+    void* tab = nullptr;            // tables block
+    long long bytes = 0;
+    void* tabs_ptrs = nullptr;      // Tabs<T>* (host struct of device pointers)
+    // profiling: launch counters always, event pairs around phases when enabled
+    long long launches[PINT_NPHASE] = {0};
+    double ms[PINT_NPHASE] = {0};
+    int prof_on = 0;
+    static const int NEV = 64;      // event pairs in the pool
+    cudaEvent_t ev[2 * NEV] = {};
+    int ev_phase[NEV] = {0};
+    int nev = 0;
+};
+
+namespace pint {
+
+template <class T> static Tabs<T>& tabs_of(pint_handle* h) { return *reinterpret_cast<Tabs<T>*>(h->tabs_ptrs); }
+
+// Layout of the tables block (elements of T; complex = 2 T).
+struct TabLayout {
+    size_t twt, twx, twy, wx, wy, fx, ix, fy, iy, lamx, lamy, lam1, lam2, total;
+};
+static TabLayout tab_layout(const pint_problem* p, int fft_x, int fft_y) {
+    TabLayout L{};
+    const size_t nx = p->nx, ny = p->dim == 2 ? p->ny : 1, nt = p->nt;
+    size_t o = 0;
+    auto take = [&](size_t n) { size_t a = o; o += (n + 7) / 8 * 8; return a; };
+    L.twt = take(2 * nt);
+    L.twx = take(2 * nx);
+    L.twy = take(2 * ny);
+    L.wx = take(2 * nx);
+    L.wy = take(2 * ny);
+    L.fx = take(fft_x ? 0 : nx * nx);
+    L.ix = take(fft_x ? 0 : nx * nx);
+    const bool dy = p->dim == 2 && !fft_y;
+    L.fy = take(dy ? ny * ny : 0);
+    L.iy = take(dy ? ny * ny : 0);
+    L.lamx = take(nx);
+    L.lamy = take(ny);
+    L.lam1 = take(2 * (nt / 2 + 1));
+    L.lam2 = take(2 * (nt / 2 + 1));
+    L.total = o;
+    return L;
+}
+
+// Dense basis of one axis: F[p][j] (forward) and Fi[j][p] (inverse).
+static void dense_basis(int n, int bc, std::vector<double>& F, std::vector<double>& Fi) {
+    F.assign((size_t)n * n, 0.0);
+    Fi.assign((size_t)n * n, 0.0);
+    for (int p = 0; p < n; ++p)
+        for (int j = 0; j < n; ++j) {
+            double f, fi;
+            if (bc == PINT_BC_SIMPLY_SUPPORTED) {  // DST-I: sin(pi (p+1)(j+1)/(n+1)), inverse 2/(n+1) F^T
+                f = sin(M_PI * (double)((long)(p + 1) * (j + 1) % (2 * (n + 1))) / (n + 1));
+                fi = 2.0 / (n + 1) * f;
+            } else {  // DCT-II: cos(pi p (j+1/2)/n), inverse (1 or 2)/n F^T
+                f = cos(M_PI * (double)(((long)p * (2 * j + 1)) % (4 * n)) / (2.0 * n));
+                fi = (p == 0 ? 1.0 : 2.0) / n * f;
+            }
+            F[(size_t)p * n + j] = f;
+            Fi[(size_t)j * n + p] = fi;
+        }
+}
+
+template <class T>
+static int build_tables(pint_handle* h) {
+    const pint_problem* p = &h->p;
+    const int nx = p->nx, ny = p->dim == 2 ? p->ny : 1, nt = p->nt;
+    TabLayout L = tab_layout(p, h->fft_x, h->fft_y);
+    std::vector<T> host(L.total, T(0));
+    auto cset = [&](size_t off, int i, std::complex<double> z) {
+        host[off + 2 * i] = (T)z.real();
+        host[off + 2 * i + 1] = (T)z.imag();
+    };
+    auto expi = [](double turns) {  // exp(2 pi i * turns), turns a dyadic rational
+        return std::complex<double>(cos(2.0 * M_PI * turns), sin(2.0 * M_PI * turns));
+    };
+    for (int j = 0; j < nt; ++j) cset(L.twt, j, expi(-(double)j / nt));
+    for (int j = 0; j < nx; ++j) cset(L.twx, j, expi(-(double)j / nx));
+    for (int j = 0; j < ny; ++j) cset(L.twy, j, expi(-(double)j / ny));
+    for (int j = 0; j < nx; ++j) cset(L.wx, j, expi(-(double)j / (4.0 * nx)));
+    for (int j = 0; j < ny; ++j) cset(L.wy, j, expi(-(double)j / (4.0 * ny)));
+    std::vector<double> F, Fi;
+    if (!h->fft_x) {
+        dense_basis(nx, p->bc, F, Fi);
+        for (size_t i = 0; i < F.size(); ++i) { host[L.fx + i] = (T)F[i]; host[L.ix + i] = (T)Fi[i]; }
+    }
+    if (p->dim == 2 && !h->fft_y) {
+        dense_basis(ny, p->bc, F, Fi);
+        for (size_t i = 0; i < F.size(); ++i) { host[L.fy + i] = (T)F[i]; host[L.iy + i] = (T)Fi[i]; }
+    }
+    for (int i = 0; i < nx; ++i) host[L.lamx + i] = (T)lap_eig(i, nx, p->bc);
+    for (int i = 0; i < ny; ++i) host[L.lamy + i] = p->dim == 2 ? (T)lap_eig(i, ny, p->bc) : T(0);
+    // Lemma 2.1 with the forward transform exp(-2 pi i nk/nt):
+    //   lambda_1k = (1 - alpha^{1/nt} e^{-2 pi i k/nt}) / dt,  lambda_2k = theta + (1-theta) alpha^{1/nt} e^{...}
+    const double dt = h->geo.dt, a1 = pow(p->alpha, 1.0 / nt);
+    for (int k = 0; k <= nt / 2; ++k) {
+        std::complex<double> z = a1 * expi(-(double)k / nt);
+        cset(L.lam1, k, (1.0 - z) / dt);
+        cset(L.lam2, k, p->theta + (1.0 - p->theta) * z);
+    }
+    if (cudaMemcpy(h->tab, host.data(), L.total * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+        return PINT_ECUDA;
+    Tabs<T>* tb = new (std::nothrow) Tabs<T>;
+    if (!tb) return PINT_ENOMEM;
+    const T* base = reinterpret_cast<const T*>(h->tab);
+    tb->twt = reinterpret_cast<const c_t<T>*>(base + L.twt);
+    tb->twx = reinterpret_cast<const c_t<T>*>(base + L.twx);
+    tb->twy = reinterpret_cast<const c_t<T>*>(base + L.twy);
+    tb->wx = reinterpret_cast<const c_t<T>*>(base + L.wx);
+    tb->wy = reinterpret_cast<const c_t<T>*>(base + L.wy);
+    tb->fx = base + L.fx;
+    tb->ix = base + L.ix;
+    tb->fy = base + L.fy;
+    tb->iy = base + L.iy;
+    tb->lamx = base + L.lamx;
+    tb->lamy = base + L.lamy;
+    tb->lam1 = reinterpret_cast<const c_t<T>*>(base + L.lam1);
+    tb->lam2 = reinterpret_cast<const c_t<T>*>(base + L.lam2);
+    h->tabs_ptrs = tb;
+    // gamma tables (always FP64: the scaling and unscaling are FP64 steps)
+    std::vector<double> g(nt), gi(nt);
+    for (int n = 0; n < nt; ++n) {
+        g[n] = pow(p->alpha, (double)n / nt);
+        gi[n] = pow(p->alpha, -(double)n / nt) / nt;
+    }
+    if (cudaMemcpy(h->gam, g.data(), nt * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) return PINT_ECUDA;
+    if (cudaMemcpy(h->ginv, gi.data(), nt * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) return PINT_ECUDA;
+    return PINT_OK;
+}
+
+static void derive(const pint_problem* p, pint_handle* h) {
+    Geo& g = h->geo;
+    g.nx = p->nx;
+    g.ny = p->dim == 2 ? p->ny : 1;
+    g.dim = p->dim;
+    g.bc = p->bc;
+    g.nt = p->nt;
+    g.nspace = g.nx * g.ny;
+    g.dt = p->T / ((double)p->nt * p->n_windows);
+    g.inv_dt = 1.0 / g.dt;
+    const double hx = grid_h(p->nx, p->bc), hy = grid_h(g.ny, p->bc);
+    g.ihx2 = 1.0 / (hx * hx);
+    g.ihy2 = p->dim == 2 ? 1.0 / (hy * hy) : 0.0;
+    h->coef.ch = 0;
+    switch (p->equation) {
+        case PINT_BIHARMONIC: g.c2 = 1.0; g.c1 = 0.0; g.cN = 0.0; break;
+        case PINT_LINEAR_CH: g.c2 = p->eps * p->eps; g.c1 = p->beta * p->beta; g.cN = 0.0; break;
+        default: g.c2 = p->eps * p->eps; g.c1 = 1.0; g.cN = -1.0; h->coef.ch = 1; break;
+    }
+    h->coef.c2 = g.c2;
+    h->coef.c1 = g.c1;
+    h->fft_x = axis_fft(p->nx, p->bc, 4096);
+    h->fft_y = p->dim == 2 ? axis_fft(g.ny, p->bc, 1024) : 1;
+}
+
+static Sizes sizes_of(const pint_problem* p, pint_handle* tmp) {
+    derive(p, tmp);
+    Sizes z{};
+    z.nspace = (size_t)tmp->geo.nspace;
+    z.dof = z.nspace * p->nt;
+    z.nk = p->nt / 2 + 1;
+    int gx, gy, gz, chunk;
+    const int nres = residual_grid(tmp->geo, gx, gy, gz, chunk);
+    const int nn = norm2_blocks((int)z.nspace);
+    z.partials = (size_t)(nres > nn ? nres : nn);
+    TabLayout L = tab_layout(p, tmp->fft_x, tmp->fft_y);
+    z.tables_T = L.total;
+    const size_t ts = p->precision == PINT_MIXED ? 4 : 8;
+    z.tables_bytes = L.total * ts;
+    return z;
+}
+
+static long long footprint_of(const pint_problem* p) {
+    pint_handle tmp;
+    memset(&tmp.p, 0, sizeof(tmp.p));
+    Sizes z = sizes_of(p, &tmp);
+    const size_t ts = p->precision == PINT_MIXED ? 4 : 8;
+    long long b = 0;
+    b += sizeof(Ctl);
+    b += z.partials * 2 * sizeof(double);
+    b += 2 * (size_t)p->nt * sizeof(double);
+    b += z.nspace * sizeof(double);
+    b += z.dof * ts;                 // s
+    b += z.nk * z.nspace * 2 * ts;   // S
+    b += z.tables_bytes;
+    return b;
+}
+
+// ---------------------------------------------------------------------------
+// Phase accounting
+// ---------------------------------------------------------------------------
+enum { PH_RES = 0, PH_CHECK = 1, PH_TFWD = 2, PH_SP0 = 3, PH_SP1 = 4, PH_SP2 = 5, PH_TINV = 6, PH_SETUP = 7 };
+
+static void prof_flush(pint_handle* h) {  // stream must be idle past the recorded events
+    for (int i = 0; i < h->nev; ++i) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, h->ev[2 * i], h->ev[2 * i + 1]) == cudaSuccess) h->ms[h->ev_phase[i]] += t;
+        else cudaGetLastError();
+    }
+    h->nev = 0;
+}
+static void prof_begin(pint_handle* h, int ph) {
+    if (!h->prof_on) return;
+    if (h->nev == pint_handle::NEV) {
+        cudaStreamSynchronize(h->st);
+        prof_flush(h);
+    }
+    h->ev_phase[h->nev] = ph;
+    cudaEventRecord(h->ev[2 * h->nev], h->st);
+}
+static void prof_end(pint_handle* h, int ph, int nlaunch) {
+    h->launches[ph] += nlaunch;
+    if (!h->prof_on) return;
+    cudaEventRecord(h->ev[2 * h->nev + 1], h->st);
+    h->nev++;
+}
+
+// ---------------------------------------------------------------------------
+// The iteration
+// ---------------------------------------------------------------------------
+template <class T> struct Impl {
+    static cudaError_t spatial(pint_handle* h, c_t<T>* S, const Tabs<T>& tb) {
+        const int nst = h->geo.dim == 2 ? 3 : 1;
+        for (int stg = 0; stg < nst; ++stg) {
+            prof_begin(h, PH_SP0 + stg);
+            cudaError_t e = launch_spatial_stage<T>(stg, h->geo, S, tb, h->coef, h->fft_x, h->fft_y, h->ctl, h->st);
+            prof_end(h, PH_SP0 + stg, 1);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    static cudaError_t iteration(pint_handle* h, double* U, const double* u0w) {
+        const Geo& g = h->geo;
+        T* s = reinterpret_cast<T*>(h->s);
+        c_t<T>* S = reinterpret_cast<c_t<T>*>(h->S);
+        const Tabs<T>& tb = tabs_of<T>(h);
+        prof_begin(h, PH_RES);
+        launch_residual<T>(g, U, u0w, h->gam, nullptr, s, h->partials, h->ctl, h->st);
+        prof_end(h, PH_RES, 1);
+        int gx, gy, gz, chunk;
+        const int np = residual_grid(g, gx, gy, gz, chunk);
+        prof_begin(h, PH_CHECK);
+        launch_after_residual(h->partials, np, 1.0 / ((double)g.nt * g.nspace), h->ctl, h->st);
+        prof_end(h, PH_CHECK, 1);
+        prof_begin(h, PH_TFWD);
+        cudaError_t e = launch_time_fwd<T>(g.nt, g.nspace, s, S, tb.twt, h->ctl, h->st);
+        prof_end(h, PH_TFWD, 1);
+        if (e != cudaSuccess) return e;
+        if ((e = spatial(h, S, tb)) != cudaSuccess) return e;
+        prof_begin(h, PH_TINV);
+        e = launch_time_inv<T>(g.nt, g.nspace, S, tb.twt, h->ginv, U, 1, h->ctl, h->st);
+        prof_end(h, PH_TINV, 1);
+        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
+    }
+    static cudaError_t precond(pint_handle* h, double jbar, const double* r, double* delta) {
+        const Geo& g = h->geo;
+        T* s = reinterpret_cast<T*>(h->s);
+        c_t<T>* S = reinterpret_cast<c_t<T>*>(h->S);
+        const Tabs<T>& tb = tabs_of<T>(h);
+        launch_set_running(h->ctl, jbar, h->st);
+        launch_scale_cast<T>(r, h->gam, s, g.nspace, g.nt, h->st);
+        cudaError_t e = launch_time_fwd<T>(g.nt, g.nspace, s, S, tb.twt, h->ctl, h->st);
+        if (e != cudaSuccess) return e;
+        if ((e = spatial(h, S, tb)) != cudaSuccess) return e;
+        e = launch_time_inv<T>(g.nt, g.nspace, S, tb.twt, h->ginv, delta, 0, h->ctl, h->st);
+        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
+    }
+};
+
+static cudaError_t iteration(pint_handle* h, double* U, const double* u0w) {
+    return h->p.precision == PINT_MIXED ? Impl<float>::iteration(h, U, u0w) : Impl<double>::iteration(h, U, u0w);
+}
+
+}  // namespace pint
+
+using namespace pint;
+
+#define PINT_CK(call)                                  \
+    do {                                               \
+        if ((call) != cudaSuccess) return PINT_ECUDA;  \
+    } while (0)
+
+extern "C" {
+
+const char* pint_strerror(int code) {
+    switch (code) {
+        case PINT_OK: return "ok";
+        case PINT_EINVAL: return "invalid or unsupported parameter";
+        case PINT_ENOMEM: return "out of memory";
+        case PINT_ECUDA: return "CUDA runtime error";
+        case PINT_ENOCONV: return "iteration did not reach the tolerance within max_iter";
+        case PINT_EDIVERGED: return "iteration diverged (residual non-finite or grew by 1e6)";
+        default: return "unknown pint error code";
+    }
+}
+
+long long pint_footprint(const pint_problem* p) {
+    int rc = validate(p);
+    if (rc != PINT_OK) return rc;
+    return footprint_of(p);
+}
+
+void pint_destroy(pint_handle* h) {
+    if (!h) return;
+    cudaFree(h->ctl);
+    cudaFreeHost(h->hctl);
+    cudaFree(h->partials);
+    cudaFree(h->gam);
+    cudaFree(h->ginv);
+    cudaFree(h->u0buf);
+    cudaFree(h->hU);
+    cudaFree(h->hu0);
+    cudaFree(h->s);
+    cudaFree(h->S);
+    cudaFree(h->tab);
+    for (int i = 0; i < 2 * pint_handle::NEV; ++i)
+        if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+    if (h->tabs_ptrs) {
+        if (h->p.precision == PINT_MIXED) delete reinterpret_cast<Tabs<float>*>(h->tabs_ptrs);
+        else delete reinterpret_cast<Tabs<double>*>(h->tabs_ptrs);
+    }
+    delete h;
+}
+
+int pint_create(const pint_problem* p, void* cuda_stream, pint_handle** out) {
+    if (!out) return PINT_EINVAL;
+    *out = nullptr;
+    int rc = validate(p);
+    if (rc != PINT_OK) return rc;
+    if (configure_kernels() != cudaSuccess) return PINT_ECUDA;
+    pint_handle* h = new (std::nothrow) pint_handle;
+    if (!h) return PINT_ENOMEM;
+    h->p = *p;
+    h->st = (cudaStream_t)cuda_stream;
+    Sizes z = sizes_of(p, h);
+    const size_t ts = p->precision == PINT_MIXED ? 4 : 8;
+    auto dalloc = [&](void** ptr, size_t bytes) -> int {
+        if (cudaMalloc(ptr, bytes < 16 ? 16 : bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return PINT_ENOMEM;
+        }
+        h->bytes += (long long)bytes;
+        return PINT_OK;
+    };
+    rc = PINT_OK;
+    if (!rc) rc = dalloc((void**)&h->ctl, sizeof(Ctl));
+    if (!rc) rc = dalloc((void**)&h->partials, z.partials * 2 * sizeof(double));
+    if (!rc) rc = dalloc((void**)&h->gam, p->nt * sizeof(double));
+    if (!rc) rc = dalloc((void**)&h->ginv, p->nt * sizeof(double));
+    if (!rc) rc = dalloc((void**)&h->u0buf, z.nspace * sizeof(double));
+    if (!rc) rc = dalloc(&h->s, z.dof * ts);
+    if (!rc) rc = dalloc(&h->S, z.nk * z.nspace * 2 * ts);
+    if (!rc) rc = dalloc(&h->tab, z.tables_bytes);
+    if (!rc && cudaMallocHost((void**)&h->hctl, sizeof(Ctl)) != cudaSuccess) rc = PINT_ENOMEM;
+    if (!rc) rc = p->precision == PINT_MIXED ? build_tables<float>(h) : build_tables<double>(h);
+    if (!rc && cudaMemset(h->ctl, 0, sizeof(Ctl)) != cudaSuccess) rc = PINT_ECUDA;
+    if (rc) {
+        pint_destroy(h);
+        return rc;
+    }
+    h->npart = (int)z.partials;
+    *out = h;
+    return PINT_OK;
+}
+
+static int read_ctl(pint_handle* h) {
+    PINT_CK(cudaMemcpyAsync(h->hctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->st));
+    PINT_CK(cudaStreamSynchronize(h->st));
+    prof_flush(h);
+    return PINT_OK;
+}
+
+int pint_profile_enable(pint_handle* h, int on) {
+    if (!h || (on != 0 && on != 1)) return PINT_EINVAL;
+    if (on && !h->ev[0]) {
+        for (int i = 0; i < 2 * pint_handle::NEV; ++i)
+            if (cudaEventCreate(&h->ev[i]) != cudaSuccess) return PINT_ECUDA;
+    }
+    PINT_CK(cudaStreamSynchronize(h->st));
+    prof_flush(h);
+    h->prof_on = on;
+    return PINT_OK;
+}
+
+int pint_profile_read(pint_handle* h, pint_profile* out, int reset) {
+    if (!h || !out) return PINT_EINVAL;
+    PINT_CK(cudaStreamSynchronize(h->st));
+    prof_flush(h);
+    for (int i = 0; i < PINT_NPHASE; ++i) {
+        out->ms[i] = h->ms[i];
+        out->launches[i] = h->launches[i];
+        if (reset) { h->ms[i] = 0.0; h->launches[i] = 0; }
+    }
+    return PINT_OK;
+}
+
+int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* st) {
+    if (!h || !u0_dev || !U_dev) return PINT_EINVAL;
+    const pint_problem& p = h->p;
+    const Geo& g = h->geo;
+    pint_stats S;
+    memset(&S, 0, sizeof(S));
+    int rc = PINT_OK;
+    for (int w = 0; w < p.n_windows; ++w) {
+        const double* u0w = w == 0 ? u0_dev : h->u0buf;
+        prof_begin(h, PH_SETUP);
+        const bool bc = w > 0 || !p.init_guess;
+        if (bc) launch_broadcast(U_dev, u0w, g.nspace, g.nt, h->st);
+        launch_begin_window(u0w, g.nspace, g.inv_dt, p.max_iter, p.tol, h->partials, h->ctl, h->st);
+        prof_end(h, PH_SETUP, bc ? 3 : 2);
+        int enqueued = 0;
+        for (;;) {
+            int chunk = enqueued == 0 ? 3 : 2;
+            for (int c = 0; c < chunk; ++c)
+                if (iteration(h, U_dev, u0w) != cudaSuccess) return PINT_ECUDA;
+            enqueued += chunk;
+            if ((rc = read_ctl(h)) != PINT_OK) return rc;
+            if (h->hctl->status != ST_RUNNING) break;
+            if (enqueued > p.max_iter + 8) return PINT_ECUDA;  // the device loop must have stopped by now
+        }
+        const Ctl& c = *h->hctl;
+        const int k = c.iter;
+        S.status = c.status;
+        S.iters += k;
+        S.iters_last = k;
+        S.rel_residual = c.rho;
+        S.jbar = h->coef.ch ? c.jbar : 0.0;
+        for (int i = 0; i <= k && i < PINT_HIST_MAX; ++i) S.hist[i] = c.hist[i];
+        S.contraction = k >= 2 ? pow(c.hist[k] / c.hist[1], 1.0 / (k - 1)) : (k == 1 ? c.hist[1] / c.hist[0] : 0.0);
+        if (c.status != PINT_OK) {
+            rc = c.status;
+            break;
+        }
+        S.windows = w + 1;
+        if (w + 1 < p.n_windows)
+            PINT_CK(cudaMemcpyAsync(h->u0buf, U_dev + (size_t)(g.nt - 1) * g.nspace, g.nspace * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, h->st));
+    }
+    if (st) *st = S;
+    return rc;
+}
+
+int pint_solve_host(pint_handle* h, const double* u0_host, double* U_host, pint_stats* st) {
+    if (!h || !u0_host || !U_host) return PINT_EINVAL;
+    const size_t ns = (size_t)h->geo.nspace, dof = ns * h->geo.nt;
+    if (!h->hU) {
+        if (cudaMalloc((void**)&h->hU, dof * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return PINT_ENOMEM; }
+        if (cudaMalloc((void**)&h->hu0, ns * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return PINT_ENOMEM; }
+    }
+    PINT_CK(cudaMemcpyAsync(h->hu0, u0_host, ns * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    if (h->p.init_guess)
+        PINT_CK(cudaMemcpyAsync(h->hU, U_host, dof * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    int rc = pint_solve(h, h->hu0, h->hU, st);
+    if (rc != PINT_OK && rc != PINT_ENOCONV && rc != PINT_EDIVERGED) return rc;
+    PINT_CK(cudaMemcpyAsync(U_host, h->hU, dof * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    PINT_CK(cudaStreamSynchronize(h->st));
+    return rc;
+}
+
+int pint_residual(pint_handle* h, const double* u0_dev, const double* U_dev, double* r_dev, double* rel_res) {
+    if (!h || !u0_dev || !U_dev) return PINT_EINVAL;
+    const Geo& g = h->geo;
+    launch_begin_window(u0_dev, g.nspace, g.inv_dt, h->p.max_iter, h->p.tol, h->partials, h->ctl, h->st);
+    launch_residual<double>(g, U_dev, u0_dev, h->gam, r_dev, nullptr, h->partials, nullptr, h->st);
+    int gx, gy, gz, chunk;
+    const int np = residual_grid(g, gx, gy, gz, chunk);
+    launch_residual_norm(h->partials, np, h->ctl, h->st);
+    PINT_CK(cudaGetLastError());
+    int rc = read_ctl(h);
+    if (rc != PINT_OK) return rc;
+    if (rel_res) *rel_res = h->hctl->rho;
+    return PINT_OK;
+}
+
+int pint_precond_apply(pint_handle* h, double jbar, const double* r_dev, double* delta_dev) {
+    if (!h || !r_dev || !delta_dev || r_dev == delta_dev) return PINT_EINVAL;
+    cudaError_t e = h->p.precision == PINT_MIXED ? Impl<float>::precond(h, jbar, r_dev, delta_dev)
+                                                  : Impl<double>::precond(h, jbar, r_dev, delta_dev);
+    if (e != cudaSuccess) return PINT_ECUDA;
+    PINT_CK(cudaStreamSynchronize(h->st));
+    return PINT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,204 @@
+// pint_common.cuh - types and device building blocks shared by the libpint kernels.
+//
+// Layout conventions (all kernels):
+//   U, r, s        [n][y][x] real, x fastest, n = 0..nt-1 (time levels 1..N_t)
+//   S (spectrum)   [k][y][x] complex, k = 0..nt/2 (half spectrum of the real
+//                  time signal; the other half is its complex conjugate)
+// Forward transforms use exp(-2 pi i jk/N) and are unnormalized; every
+// normalization sits in the inverse path.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+namespace pint {
+
+template <class T> struct cplx_of;
+template <> struct cplx_of<float> { using type = float2; };
+template <> struct cplx_of<double> { using type = double2; };
+template <class T> using c_t = typename cplx_of<T>::type;
+
+template <class C> struct real_of;
+template <> struct real_of<float2> { using type = float; };
+template <> struct real_of<double2> { using type = double; };
+
+__host__ __device__ __forceinline__ float2 mkc(float a, float b) { return make_float2(a, b); }
+__host__ __device__ __forceinline__ double2 mkc(double a, double b) { return make_double2(a, b); }
+
+template <class C> __device__ __forceinline__ C operator+(C a, C b) { return mkc(a.x + b.x, a.y + b.y); }
+template <class C> __device__ __forceinline__ C operator-(C a, C b) { return mkc(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+template <class C> __device__ __forceinline__ C conjc(C a) { return mkc(a.x, -a.y); }
+template <class C, class R> __device__ __forceinline__ C scalec(C a, R s) { return mkc(a.x * s, a.y * s); }
+// a / b for complex b != 0
+template <class C> __device__ __forceinline__ C cdiv(C a, C b) {
+    using R = typename real_of<C>::type;
+    R inv = R(1) / (b.x * b.x + b.y * b.y);
+    return mkc((a.x * b.x + a.y * b.y) * inv, (a.y * b.x - a.x * b.y) * inv);
+}
+// multiply by exp(DIR * i pi/2): DIR=-1 -> -i, DIR=+1 -> +i
+template <int DIR, class C> __device__ __forceinline__ C rot90(C a) {
+    return DIR < 0 ? mkc(a.y, -a.x) : mkc(-a.y, a.x);
+}
+
+// ---------------------------------------------------------------------------
+// Small DFTs in registers: X_k = sum_j v_j exp(DIR 2 pi i jk / R)
+// ---------------------------------------------------------------------------
+template <int DIR, class C> __device__ __forceinline__ void dft2(C* v) {
+    C a = v[0];
+    v[0] = a + v[1];
+    v[1] = a - v[1];
+}
+template <int DIR, class C> __device__ __forceinline__ void dft4(C& v0, C& v1, C& v2, C& v3) {
+    C a = v0 + v2, b = v0 - v2, c = v1 + v3, d = rot90<DIR>(v1 - v3);
+    v0 = a + c;
+    v2 = a - c;
+    v1 = b + d;
+    v3 = b - d;
+}
+template <int DIR, class C> __device__ __forceinline__ void dft4(C* v) { dft4<DIR>(v[0], v[1], v[2], v[3]); }
+template <int DIR, class C> __device__ __forceinline__ void dft8(C* v) {
+    using R = typename real_of<C>::type;
+    const R s = R(0.70710678118654752440);
+    C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    C o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4<DIR>(e0, e1, e2, e3);
+    dft4<DIR>(o0, o1, o2, o3);
+    // twiddles exp(DIR 2 pi i k/8), k = 1, 2, 3
+    C t1 = DIR < 0 ? mkc(s * (o1.x + o1.y), s * (o1.y - o1.x)) : mkc(s * (o1.x - o1.y), s * (o1.x + o1.y));
+    C t2 = rot90<DIR>(o2);
+    C t3 = DIR < 0 ? mkc(s * (o3.y - o3.x), -s * (o3.x + o3.y)) : mkc(-s * (o3.x + o3.y), s * (o3.x - o3.y));
+    v[0] = e0 + o0;
+    v[4] = e0 - o0;
+    v[1] = e1 + t1;
+    v[5] = e1 - t1;
+    v[2] = e2 + t2;
+    v[6] = e2 - t2;
+    v[3] = e3 + t3;
+    v[7] = e3 - t3;
+}
+template <int R, int DIR, class C> __device__ __forceinline__ void dftR(C* v) {
+    if constexpr (R == 2) dft2<DIR>(v);
+    else if constexpr (R == 4) dft4<DIR>(v);
+    else dft8<DIR>(v);
+}
+
+constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
+// Radix of the next Stockham pass when M = log2(remaining length): 8 while
+// possible, 4x4 for 16, then 4 or 2.
+constexpr int next_radix(int M) { return (M >= 3 && M != 4) ? 8 : (M == 4 || M == 2) ? 4 : 2; }
+
+// ---------------------------------------------------------------------------
+// Stockham autosort FFT on sequences held in shared memory, executed by the
+// whole CTA.  Element i of sequence b lives at buf[b*SSTR + i*ESTR].  Each
+// pass reads all inputs of the thread's butterflies into registers, barriers,
+// then writes the outputs, so it works in place.  tw[j] = exp(-2 pi i j/N).
+// Task mapping keeps neighbouring threads on neighbouring addresses: for
+// column layouts (ESTR > 1) the batch index is fastest, for rows the
+// butterfly index.
+// ---------------------------------------------------------------------------
+template <class C, int N, int R, int NS, int DIR, int NTH, int B, int ESTR, int SSTR>
+__device__ __forceinline__ void stockham_pass(C* buf, const C* __restrict__ tw) {
+    constexpr int NB = N / R;              // butterflies per sequence
+    constexpr int NTASK = NB * B;
+    constexpr int TPT = (NTASK + NTH - 1) / NTH;
+    constexpr bool COL = ESTR > 1;
+    C v[TPT][R];
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) {
+        int t = tid + q * NTH;
+        if (TPT * NTH == NTASK || t < NTASK) {
+            int b = COL ? t % B : t / NB;
+            int j = COL ? t / B : t % NB;
+            const C* src = buf + b * SSTR;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[q][r] = src[(j + r * NB) * ESTR];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) {
+        int t = tid + q * NTH;
+        if (TPT * NTH == NTASK || t < NTASK) {
+            int b = COL ? t % B : t / NB;
+            int j = COL ? t / B : t % NB;
+            if constexpr (NS > 1) {
+                int jm = j % NS;
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    C w = tw[jm * r * (N / (NS * R))];
+                    if (DIR > 0) w = conjc(w);
+                    v[q][r] = cmul(v[q][r], w);
+                }
+            }
+            dftR<R, DIR>(v[q]);
+            C* dst = buf + b * SSTR;
+            int base = (j / NS) * NS * R + (j % NS);
+#pragma unroll
+            for (int r = 0; r < R; ++r) dst[(base + r * NS) * ESTR] = v[q][r];
+        }
+    }
+    __syncthreads();
+}
+
+template <class C, int N, int NS, int M, int DIR, int NTH, int B, int ESTR, int SSTR>
+__device__ __forceinline__ void fft_passes(C* buf, const C* __restrict__ tw) {
+    if constexpr (M > 0) {
+        constexpr int R = next_radix(M);
+        stockham_pass<C, N, R, NS, DIR, NTH, B, ESTR, SSTR>(buf, tw);
+        fft_passes<C, N, NS * R, M - ilog2(R), DIR, NTH, B, ESTR, SSTR>(buf, tw);
+    }
+}
+
+// In-place length-N FFT (N a power of two) of B sequences in shared memory.
+// The caller must __syncthreads() before (data ready); the last pass ends
+// with a barrier.
+template <class C, int N, int DIR, int NTH, int B, int ESTR, int SSTR>
+__device__ __forceinline__ void smem_fft(C* buf, const C* __restrict__ tw) {
+    fft_passes<C, N, 1, ilog2(N), DIR, NTH, B, ESTR, SSTR>(buf, tw);
+}
+
+// ---------------------------------------------------------------------------
+// Device control block of one solve (one per handle).
+// ---------------------------------------------------------------------------
+enum : int { ST_RUNNING = 1 };
+
+struct Ctl {
+    int status;       // ST_RUNNING while iterating; then PINT_OK / PINT_ENOCONV / PINT_EDIVERGED
+    int iter;         // index k of the residual being evaluated
+    int max_iter;
+    int pad;
+    double tol;
+    double bnorm;     // ||b||_2
+    double rho0;      // rho of the first residual of the window
+    double rho;       // last rho
+    double jbar;      // mean(3u^2) of the current iterate (Cahn-Hilliard)
+    double sum_r2;
+    double sum_u2;
+    double hist[256];
+};
+
+// Geometry and coefficients of one problem (by value into kernels).
+// A(u) = c2 Lap^2 u + c1 Lap u + cN Lap(u^3)    (u_t + A(u) = 0)
+struct Geo {
+    int nx, ny, dim, bc, nt, nspace;
+    double dt, inv_dt, ihx2, ihy2;   // 1/h^2 per axis
+    double c2, c1, cN;
+};
+
+// Reduction helpers (deterministic: fixed shuffle tree, fixed warp order).
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace pint

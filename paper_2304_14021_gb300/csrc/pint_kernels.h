@@ -1,0 +1,67 @@
+// pint_kernels.h - host-side launchers of the libpint kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "pint_common.cuh"
+
+namespace pint {
+
+// Device tables of one problem in the transform precision T.
+template <class T> struct Tabs {
+    const c_t<T>* twt;   // nt:  exp(-2 pi i j / nt)
+    const c_t<T>* twx;   // nx:  exp(-2 pi i j / nx)          (FFT cosine path)
+    const c_t<T>* twy;   // ny
+    const c_t<T>* wx;    // nx:  exp(-i pi p / (2 nx))        (DCT-II post-twiddle)
+    const c_t<T>* wy;    // ny
+    const T* fx;         // nx*nx dense forward basis [p][j]  (dense path)
+    const T* ix;         // nx*nx dense inverse basis [j][p]
+    const T* fy;         // ny*ny
+    const T* iy;         // ny*ny
+    const T* lamx;       // nx:  eigenvalues of the 1-D Laplacian along x
+    const T* lamy;       // ny
+    const c_t<T>* lam1;  // nt/2+1: lambda_1k of Lemma 2.1
+    const c_t<T>* lam2;  // nt/2+1: lambda_2k
+};
+
+// Coefficients of the shifted spatial solve: mu(Lam) = c2 Lam^2 + c1 Lam,
+// c1 = 1 - jbar (read from ctl) when ch != 0.
+struct SolveCoef {
+    double c2, c1;
+    int ch;
+};
+
+int residual_grid(const Geo& g, int& gx, int& gy, int& gz, int& chunk);
+template <class TS>
+void launch_residual(const Geo& g, const double* U, const double* u0, const double* gam, double* r_out, TS* s_out,
+                     double* partials, const Ctl* ctl, cudaStream_t st);
+int norm2_blocks(int n);
+void launch_begin_window(const double* u0, int nspace, double inv_dt, int max_iter, double tol, double* partials,
+                         Ctl* ctl, cudaStream_t st);
+void launch_after_residual(const double* partials, int np, double inv_dof, Ctl* ctl, cudaStream_t st);
+void launch_residual_norm(const double* partials, int np, Ctl* ctl, cudaStream_t st);
+void launch_set_running(Ctl* ctl, double jbar, cudaStream_t st);
+void launch_broadcast(double* U, const double* u0, int nspace, int nt, cudaStream_t st);
+template <class TS>
+void launch_scale_cast(const double* r, const double* gam, TS* s, int nspace, int nt, cudaStream_t st);
+
+// Step 1: S[k] = sum_n s[n] exp(-2 pi i nk/nt), k = 0..nt/2 (s already alpha-scaled).
+template <class T>
+cudaError_t launch_time_fwd(int nt, int nspace, const T* s, c_t<T>* S, const c_t<T>* twt, const Ctl* ctl,
+                            cudaStream_t st);
+// Step 3: delta_n = ginv[n] * Re( sum_k S[k] exp(+2 pi i nk/nt) ) over the full
+// Hermitian spectrum; U += delta (accumulate) or out = delta.
+template <class T>
+cudaError_t launch_time_inv(int nt, int nspace, const c_t<T>* S, const c_t<T>* twt, const double* ginv, double* out,
+                            int accumulate, const Ctl* ctl, cudaStream_t st);
+// Step 2: per frequency k, S[k] <- (lambda_1k I + lambda_2k A)^{-1} S[k], in
+// stages: 1-D: stage 0 = fused transform/divide/inverse along x.  2-D: stage 0
+// = forward along x, 1 = fused along y (with the division), 2 = inverse along x.
+template <class T>
+cudaError_t launch_spatial_stage(int stage, const Geo& g, c_t<T>* S, const Tabs<T>& tb, SolveCoef co, int fft_x,
+                                 int fft_y, const Ctl* ctl, cudaStream_t st);
+
+// Opt-in shared memory sizes for the kernels that need more than 48 KB.
+cudaError_t configure_kernels();
+
+}  // namespace pint

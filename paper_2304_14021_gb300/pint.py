@@ -1,0 +1,210 @@
+"""Thin ctypes binding of libpint (include/pint.h): argument marshalling only.
+
+Every step of the solve runs in the CUDA kernels of libpint.  Tensors are
+torch CUDA tensors (FP64, contiguous, layout [n][y][x]); PyTorch only provides
+device memory and the stream.  There is no CPU fallback: if the shared library
+is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "_lib", "libpint.so")
+
+PINT_OK, PINT_EINVAL, PINT_ENOMEM, PINT_ECUDA, PINT_ENOCONV, PINT_EDIVERGED = 0, -1, -2, -3, -4, -5
+BIHARMONIC, LINEAR_CH, CAHN_HILLIARD = 0, 1, 2
+BC_SIMPLY_SUPPORTED, BC_NEUMANN = 0, 1
+FP64, MIXED = 0, 1
+HIST_MAX = 256
+
+EQUATIONS = {"biharmonic": BIHARMONIC, "linear_ch": LINEAR_CH, "cahn_hilliard": CAHN_HILLIARD}
+BCS = {"ss": BC_SIMPLY_SUPPORTED, "neumann": BC_NEUMANN}
+PRECISIONS = {"fp64": FP64, "mixed": MIXED}
+
+
+class Problem(C.Structure):
+    _fields_ = [("equation", C.c_int), ("dim", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("bc", C.c_int),
+                ("eps", C.c_double), ("beta", C.c_double), ("T", C.c_double), ("nt", C.c_int),
+                ("n_windows", C.c_int), ("theta", C.c_double), ("alpha", C.c_double), ("tol", C.c_double),
+                ("max_iter", C.c_int), ("precision", C.c_int), ("init_guess", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("status", C.c_int), ("iters", C.c_int), ("windows", C.c_int), ("iters_last", C.c_int),
+                ("rel_residual", C.c_double), ("contraction", C.c_double), ("jbar", C.c_double),
+                ("hist", C.c_double * HIST_MAX)]
+
+    def as_dict(self) -> dict:
+        return {"status": self.status, "iters": self.iters, "windows": self.windows,
+                "iters_last": self.iters_last, "rel_residual": self.rel_residual,
+                "contraction": self.contraction, "jbar": self.jbar,
+                "hist": [self.hist[i] for i in range(min(self.iters_last + 1, HIST_MAX))]}
+
+
+NPHASE = 8
+PHASES = ["residual", "check", "time_fwd", "spatial0", "spatial1", "spatial2", "time_inv", "setup"]
+
+
+class Profile(C.Structure):
+    _fields_ = [("ms", C.c_double * NPHASE), ("launches", C.c_longlong * NPHASE)]
+
+
+class PintError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+        self.code = code
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libpint.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError(f"libpint.so not built at {LIB_PATH}; run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, dp = C.c_void_p, C.POINTER(C.c_double)
+        L.pint_create.argtypes = [C.POINTER(Problem), vp, C.POINTER(vp)]
+        L.pint_create.restype = C.c_int
+        L.pint_footprint.argtypes = [C.POINTER(Problem)]
+        L.pint_footprint.restype = C.c_longlong
+        L.pint_solve.argtypes = [vp, vp, vp, C.POINTER(Stats)]
+        L.pint_solve.restype = C.c_int
+        L.pint_solve_host.argtypes = [vp, vp, vp, C.POINTER(Stats)]
+        L.pint_solve_host.restype = C.c_int
+        L.pint_residual.argtypes = [vp, vp, vp, vp, dp]
+        L.pint_residual.restype = C.c_int
+        L.pint_precond_apply.argtypes = [vp, C.c_double, vp, vp]
+        L.pint_precond_apply.restype = C.c_int
+        L.pint_profile_enable.argtypes = [vp, C.c_int]
+        L.pint_profile_enable.restype = C.c_int
+        L.pint_profile_read.argtypes = [vp, C.POINTER(Profile), C.c_int]
+        L.pint_profile_read.restype = C.c_int
+        L.pint_destroy.argtypes = [vp]
+        L.pint_destroy.restype = None
+        L.pint_strerror.argtypes = [C.c_int]
+        L.pint_strerror.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return lib().pint_strerror(code).decode()
+    except OSError:
+        return f"pint error {code}"
+
+
+def make_problem(equation="biharmonic", dim=1, nx=64, ny=1, bc="ss", eps=1.0, beta=0.0, T=0.01, nt=32,
+                 n_windows=1, theta=1.0, alpha=1e-2, tol=1e-10, max_iter=100, precision="fp64",
+                 init_guess=0) -> Problem:
+    eq = EQUATIONS.get(equation, equation)
+    b = BCS.get(bc, bc)
+    pr = PRECISIONS.get(precision, precision)
+    return Problem(int(eq), int(dim), int(nx), int(ny if dim == 2 else 1), int(b), float(eps), float(beta),
+                   float(T), int(nt), int(n_windows), float(theta), float(alpha), float(tol), int(max_iter),
+                   int(pr), int(init_guess))
+
+
+def footprint(**kw) -> int:
+    p = make_problem(**kw)
+    return int(lib().pint_footprint(C.byref(p)))
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return None
+    if not t.is_cuda or str(t.dtype) != "torch.float64" or not t.is_contiguous():
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return t.data_ptr()
+
+
+class Solver:
+    """One pint handle: pint_create / pint_solve / pint_residual /
+    pint_precond_apply / pint_destroy."""
+
+    def __init__(self, stream=None, **problem):
+        import torch
+        self.problem = make_problem(**problem)
+        self.kw = dict(problem)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = C.c_void_p()
+        rc = lib().pint_create(C.byref(self.problem), C.c_void_p(stream.cuda_stream), C.byref(h))
+        if rc != PINT_OK:
+            raise PintError(rc, "pint_create")
+        self._h = h
+
+    @property
+    def nt(self) -> int:
+        return self.problem.nt
+
+    @property
+    def nspace(self) -> int:
+        return self.problem.nx * (self.problem.ny if self.problem.dim == 2 else 1)
+
+    def solve(self, u0, U, check: bool = True) -> dict:
+        st = Stats()
+        rc = lib().pint_solve(self._h, C.c_void_p(_ptr(u0)), C.c_void_p(_ptr(U)), C.byref(st))
+        if check and rc not in (PINT_OK,):
+            raise PintError(rc, "pint_solve")
+        d = st.as_dict()
+        d["rc"] = rc
+        return d
+
+    def solve_host(self, u0, U, check: bool = True) -> dict:
+        """u0, U: numpy float64 arrays (C-contiguous) in host memory."""
+        st = Stats()
+        rc = lib().pint_solve_host(self._h, C.c_void_p(u0.ctypes.data), C.c_void_p(U.ctypes.data), C.byref(st))
+        if check and rc != PINT_OK:
+            raise PintError(rc, "pint_solve_host")
+        d = st.as_dict()
+        d["rc"] = rc
+        return d
+
+    def residual(self, u0, U, r=None) -> float:
+        rel = C.c_double(0.0)
+        rc = lib().pint_residual(self._h, C.c_void_p(_ptr(u0)), C.c_void_p(_ptr(U)),
+                                 C.c_void_p(_ptr(r)) if r is not None else None, C.byref(rel))
+        if rc != PINT_OK:
+            raise PintError(rc, "pint_residual")
+        return rel.value
+
+    def precond_apply(self, r, delta, jbar: float = 0.0) -> None:
+        rc = lib().pint_precond_apply(self._h, C.c_double(jbar), C.c_void_p(_ptr(r)), C.c_void_p(_ptr(delta)))
+        if rc != PINT_OK:
+            raise PintError(rc, "pint_precond_apply")
+
+    def profile_enable(self, on: bool = True) -> None:
+        rc = lib().pint_profile_enable(self._h, 1 if on else 0)
+        if rc != PINT_OK:
+            raise PintError(rc, "pint_profile_enable")
+
+    def profile_read(self, reset: bool = False) -> dict:
+        pr = Profile()
+        rc = lib().pint_profile_read(self._h, C.byref(pr), 1 if reset else 0)
+        if rc != PINT_OK:
+            raise PintError(rc, "pint_profile_read")
+        return {name: {"ms": pr.ms[i], "launches": int(pr.launches[i])} for i, name in enumerate(PHASES)}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().pint_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

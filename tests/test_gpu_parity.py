@@ -1,0 +1,231 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances: FP64 path <= 1e-10 max relative error against the oracle's
+sequential solution; mixed path (complex64 transforms, FP64 residual and
+update) <= 1e-8.  For a single preconditioner application the mixed path is
+compared within c * 1e-7 / alpha: the complex64 transforms carry ~1e-7
+relative error and the unscaling by alpha^{-n/N_t} amplifies it by up to 1/alpha.
+"""
+import numpy as np
+import pytest
+
+from oracle import pint_oracle as O
+from paper_2304_14021_gb300 import build_lib, pint, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build_lib.build()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def oprob(kw):
+    keys = ("equation", "dim", "nx", "ny", "bc", "eps", "beta", "T", "nt", "n_windows", "theta", "alpha")
+    return O.Problem(**{k: kw[k] for k in keys if k in kw})
+
+
+def full(kw):
+    d = dict(equation="biharmonic", dim=1, nx=64, ny=1, bc="ss", eps=1.0, beta=0.0, T=0.01, nt=32, n_windows=1,
+             theta=1.0, alpha=1e-2, tol=1e-12, max_iter=100, precision="fp64", init_guess=0)
+    d.update(kw)
+    if d["dim"] == 1:
+        d["ny"] = 1
+    return d
+
+
+# --- single preconditioner application (Eq. 2.8 / 4.14) vs dense P_alpha^{-1} ----
+
+PRECOND_CASES = [
+    dict(equation="biharmonic", dim=1, nx=64, bc="ss", nt=32, T=0.01),                       # dense DST-I
+    dict(equation="linear_ch", dim=1, nx=64, bc="neumann", nt=16, T=0.01, eps=0.05, beta=0.5),  # FFT DCT
+    dict(equation="linear_ch", dim=2, nx=32, ny=16, bc="neumann", nt=8, T=0.005, eps=0.05, beta=0.5),
+    dict(equation="biharmonic", dim=2, nx=12, ny=10, bc="ss", nt=4, T=1e-3),                 # dense 2-D
+    dict(equation="cahn_hilliard", dim=2, nx=16, ny=16, bc="neumann", nt=8, T=8e-4, eps=0.05),
+    dict(equation="linear_ch", dim=2, nx=20, ny=16, bc="neumann", nt=16, T=0.01, eps=0.05, beta=0.5),  # x dense
+    dict(equation="linear_ch", dim=1, nx=37, bc="neumann", nt=2, T=1e-3, eps=0.1, beta=0.3),  # nt = 2, ragged
+]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", range(len(PRECOND_CASES)))
+def test_precond_apply_matches_dense_solve(case, precision):
+    kw = full(dict(PRECOND_CASES[case], precision=precision))
+    p = oprob(kw)
+    r = synth.random_iterate(p.nt, p.nspace, 100 + case)
+    jbar = 0.4 if kw["equation"] == "cahn_hilliard" else None
+    ref = O.precond_dense(p, p.alpha, r, jbar) if p.nt * p.nspace <= 4096 else O.diagonalized_apply(p, p.alpha, r, jbar)
+    with pint.Solver(**kw) as s:
+        out = torch.zeros(p.nt, p.nspace, dtype=torch.float64, device="cuda")
+        s.precond_apply(dev(r), out, jbar=jbar or 0.0)
+        err = O.rel_err(host(out), ref)
+    tol = 1e-11 if precision == "fp64" else 3e-6 / p.alpha
+    assert err < tol, err
+
+
+# --- residual (Eq. 2.6 / 4.8, alpha = 0) --------------------------------------
+
+@pytest.mark.parametrize("kw", [
+    dict(equation="biharmonic", dim=1, nx=64, bc="ss", nt=32, T=0.01),
+    dict(equation="linear_ch", dim=2, nx=40, ny=24, bc="neumann", nt=8, T=0.01, eps=0.05, beta=0.5),
+    dict(equation="cahn_hilliard", dim=2, nx=33, ny=17, bc="neumann", nt=8, T=8e-4, eps=0.05),
+    dict(equation="biharmonic", dim=2, nx=9, ny=70, bc="ss", nt=4, T=1e-3),
+])
+def test_residual_matches_oracle(kw):
+    kw = full(kw)
+    p = oprob(kw)
+    u0 = synth.u0_uniform(p.nspace, -1, 1, 1)
+    U = synth.random_iterate(p.nt, p.nspace, 2)
+    ref = O.residual(p, u0, U)
+    with pint.Solver(**kw) as s:
+        r = torch.empty(p.nt, p.nspace, dtype=torch.float64, device="cuda")
+        rel = s.residual(dev(u0), dev(U), r)
+    assert O.rel_err(host(r), ref) < 1e-13
+    assert abs(rel - np.linalg.norm(ref) / O.rhs_norm(p, u0)) < 1e-12 * rel
+
+
+# --- full solves vs the sequential oracle --------------------------------------
+
+def run_solve(kw, u0, U0=None):
+    p = oprob(kw)
+    with pint.Solver(**kw) as s:
+        U = dev(U0) if U0 is not None else torch.zeros(p.nt, p.nspace, dtype=torch.float64, device="cuda")
+        st = s.solve(dev(u0), U, check=False)
+        return host(U), st
+
+
+def test_config1_biharmonic_1d_fp64():
+    # 1-D biharmonic, simply supported, 64 vertices, N_t = 32, T = 0.01, alpha = 1e-2, FP64, tol 1e-10
+    kw = full(dict(tol=1e-10))
+    p = oprob(kw)
+    u0 = synth.u0_sine_modes(64)
+    U, st = run_solve(kw, u0)
+    assert st["rc"] == 0, st
+    assert O.rel_err(U, O.sequential(p, u0)) < 1e-10
+    assert 3 <= st["iters"] <= 8
+    h = st["hist"]
+    assert all(h[i + 1] < h[i] for i in range(len(h) - 1))
+    # Error contraction per iteration is bounded by the slowest mode's factor
+    # (Eq. 2.18): residual ratios are at most a small multiple of it.
+    assert st["contraction"] < 3 * O.mode_contraction(p)
+
+
+@pytest.mark.parametrize("precision,alpha", [("fp64", 1e-2), ("mixed", 1e-2), ("mixed", 1e-3), ("fp64", 1e-3)])
+def test_linear_ch_2d_solve(precision, alpha):
+    # 2-D linearized CH, cell-centred Neumann 64^2, beta = 0.5, eps = 0.05, dt = 0.1/128
+    kw = full(dict(equation="linear_ch", dim=2, nx=64, ny=64, bc="neumann", eps=0.05, beta=0.5, nt=32,
+                   T=32 * 0.1 / 128, alpha=alpha, precision=precision, tol=1e-11))
+    p = oprob(kw)
+    u0 = synth.u0_uniform(p.nspace, -0.05, 0.05, 0)
+    U, st = run_solve(kw, u0)
+    assert st["rc"] == 0, st
+    err = O.rel_err(U, O.sequential(p, u0))
+    assert err < (1e-10 if precision == "fp64" else 1e-8), err
+
+
+def test_biharmonic_1d_fft_long_rows_mixed():
+    kw = full(dict(equation="biharmonic", dim=1, nx=4096, bc="neumann", nt=16, T=1e-9, precision="mixed",
+                   tol=1e-11))
+    p = oprob(kw)
+    u0 = synth.u0_uniform(p.nspace, -1, 1, 3)
+    U, st = run_solve(kw, u0)
+    assert st["rc"] == 0, st
+    assert O.rel_err(U, O.sequential(p, u0)) < 1e-8
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cahn_hilliard_2d_windows(precision):
+    # 2-D CH, cell-centred Neumann 32^2, eps = 0.05, dt = 1e-4, 3 windows of 16 steps,
+    # u0 = 0.1 uniform[-1,1] minus its mean.
+    nt, W = 16, 3
+    kw = full(dict(equation="cahn_hilliard", dim=2, nx=32, ny=32, bc="neumann", eps=0.05, nt=nt, n_windows=W,
+                   T=nt * W * 1e-4, alpha=1e-2, precision=precision, tol=1e-11))
+    p = oprob(kw)
+    u0 = synth.u0_ch(p.nspace, 0)
+    U, st = run_solve(kw, u0)
+    assert st["rc"] == 0 and st["windows"] == W, st
+    Useq = O.sequential(p, u0)
+    err = O.rel_err(U, Useq[-nt:])
+    assert err < (1e-10 if precision == "fp64" else 1e-8), err
+    m0 = O.discrete_mass(p, u0)
+    assert max(abs(O.discrete_mass(p, u) - m0) for u in U) < 1e-12
+    E = [O.discrete_energy(p, u) for u in U]
+    assert all(E[i + 1] <= E[i] + 1e-13 for i in range(len(E) - 1))
+    assert 0.0 < st["jbar"] < 3.0
+
+
+def test_max_iter_reports_enoconv():
+    kw = full(dict(max_iter=1, tol=1e-15))
+    u0 = synth.u0_sine_modes(64)
+    U, st = run_solve(kw, u0)
+    assert st["rc"] == pint.PINT_ENOCONV and st["status"] == pint.PINT_ENOCONV
+    assert st["iters_last"] == 1 and len(st["hist"]) == 2 and st["hist"][1] < st["hist"][0]
+
+
+def test_resonant_alpha_reports_ediverged():
+    # Linearized CH with a growing mode: alpha R^{N_t} near 1 makes the
+    # per-mode factor |alpha R^N / (1 - alpha R^N)| > 1 (Eq. 2.18), so the
+    # iteration diverges; the status word reports it and the solve returns.
+    kw = full(dict(equation="linear_ch", dim=1, nx=32, bc="neumann", eps=0.05, beta=0.5, nt=64, T=0.7,
+                   alpha=0.01, tol=1e-12, max_iter=200))
+    p = oprob(kw)
+    assert O.mode_contraction(p) > 2.0
+    u0 = synth.u0_uniform(32, -1, 1, 5)
+    U, st = run_solve(kw, u0)
+    assert st["rc"] == pint.PINT_EDIVERGED, st
+
+
+def test_init_guess_at_solution_needs_no_iteration():
+    kw = full(dict(init_guess=1, tol=1e-9))
+    p = oprob(kw)
+    u0 = synth.u0_sine_modes(64)
+    Useq = O.sequential(p, u0)
+    U, st = run_solve(kw, u0, Useq)
+    assert st["rc"] == 0 and st["iters"] == 0
+    assert np.array_equal(U, Useq)
+
+
+def test_random_initial_iterate_converges_to_same_solution():
+    kw = full(dict(equation="linear_ch", dim=2, nx=16, ny=16, bc="neumann", eps=0.05, beta=0.5, nt=8, T=0.00625,
+                   init_guess=1))
+    p = oprob(kw)
+    u0 = synth.u0_uniform(p.nspace, -0.05, 0.05, 8)
+    U, st = run_solve(kw, u0, synth.random_iterate(8, p.nspace, 9))
+    assert st["rc"] == 0
+    assert O.rel_err(U, O.sequential(p, u0)) < 1e-10
+
+
+def test_host_entry_equals_device_entry_and_is_deterministic():
+    kw = full(dict(equation="linear_ch", dim=2, nx=32, ny=32, bc="neumann", eps=0.05, beta=0.5, nt=16,
+                   T=0.0125, precision="mixed", tol=1e-10))
+    p = oprob(kw)
+    u0 = synth.u0_uniform(p.nspace, -0.05, 0.05, 4)
+    with pint.Solver(**kw) as s:
+        U1 = torch.zeros(p.nt, p.nspace, dtype=torch.float64, device="cuda")
+        U2 = torch.zeros_like(U1)
+        s.solve(dev(u0), U1)
+        s.solve(dev(u0), U2)
+        Uh = np.zeros((p.nt, p.nspace))
+        st = s.solve_host(np.ascontiguousarray(u0), Uh)
+    assert torch.equal(U1, U2)
+    assert np.array_equal(host(U1), Uh) and st["rc"] == 0
+
+
+@pytest.mark.parametrize("nt", [2, 4, 1024])
+def test_time_axis_extremes(nt):
+    kw = full(dict(equation="linear_ch", dim=1, nx=16, bc="neumann", eps=0.05, beta=0.5, nt=nt, T=nt * 1e-4,
+                   precision="fp64"))
+    p = oprob(kw)
+    u0 = synth.u0_uniform(16, -1, 1, nt)
+    U, st = run_solve(kw, u0)
+    assert st["rc"] == 0
+    assert O.rel_err(U, O.sequential(p, u0)) < 1e-10
