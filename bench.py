@@ -2,12 +2,12 @@
 """Throughput of the parallel-in-time solve: space-time DOF/s at relative
 residual 1e-8 on one GB300 (N GPUs: independent replicas, weak scaling).
 
-One step = one pint_solve of the workload from U^0 = u0 (every time level) to
+One step = one pint_solve of the workload from the initial iterate (zero by default) to
 ||b - K(U)|| / ||b|| <= tol: residual, alpha-scaled time FFT, spatial shifted
 solves, inverse FFT + update, repeated until the tolerance is met.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
-                  [--alpha A] [--workload NAME] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed_ff|mixed|fp64]
+                  [--alpha A] [--init 0|2] [--workload NAME] [--impl ours|reference]
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle
 (sequential backward Euler with banded LU) on a bounded sample of the same
@@ -33,6 +33,9 @@ WORKLOADS = {
     # beta = 0.5, eps = 0.05, N_t = 128, T = 0.1, u0 iid uniform[-0.05, 0.05].
     "linear_ch_2d_256x256_nt128": dict(equation="linear_ch", dim=2, nx=256, ny=256, bc="neumann", eps=0.05,
                                        beta=0.5, T=0.1, nt=128, n_windows=1, u0="uniform0.05"),
+    # The same equation on a 512x512 grid (inputs larger than L2; used for kernel profiles).
+    "linear_ch_2d_512x512_nt128": dict(equation="linear_ch", dim=2, nx=512, ny=512, bc="neumann", eps=0.05,
+                                       beta=0.5, T=0.1, nt=128, n_windows=1, u0="uniform0.05"),
     # 1-D biharmonic, simply supported, 64 vertices, N_t = 32, T = 0.01, u0 = sin(pi x) + 0.5 sin(3 pi x)
     "biharmonic_1d_64_nt32": dict(equation="biharmonic", dim=1, nx=64, ny=1, bc="ss", eps=1.0, beta=0.0,
                                   T=0.01, nt=32, n_windows=1, u0="sines"),
@@ -51,15 +54,34 @@ def make_u0(wl: dict, seed: int):
     return synth.u0_ch(ns, seed)
 
 
-def solver_kw(wl: dict, args) -> dict:
+def solver_kw(wl: dict, args, precision=None) -> dict:
     kw = {k: v for k, v in wl.items() if k != "u0"}
-    kw.update(alpha=args.alpha, tol=args.tol, max_iter=200, precision=args.precision)
+    kw.update(alpha=args.alpha, tol=args.tol, max_iter=200, precision=precision or args.precision,
+              init_guess=args.init)
     return kw
+
+
+def ff_residual_flops_per_dof(equation: str, dim: int) -> float:
+    """FP32 flops per space-time DOF of the float-float residual kernel, counted
+    from its operations (FMA = 2): accurate double-word add 20, double-word
+    multiply 10, (a + b) - 2c 42, one Laplacian point 62 (1-D) / 124 (2-D); the
+    first Laplacian is evaluated on the tile plus a one-point halo."""
+    lap = 62.0 if dim == 1 else 124.0
+    halo = 258.0 / 256.0 if dim == 1 else (34.0 * 10.0) / (32.0 * 8.0)
+    f = lap * halo + lap            # Lap u on tile + halo, Lap(Lap u) on the tile
+    f += 10.0                       # c2 * Lap^2 u
+    if equation in ("linear_ch", "cahn_hilliard"):
+        f += 30.0                   # + c1 * Lap u
+    if equation == "cahn_hilliard":
+        cube = 20.0
+        f += (3 if dim == 1 else 5) * cube + lap + 20.0   # Lap(u^3), subtract
+    f += 30.0 + 20.0 + 7.0          # time difference * (1/dt), r = T - A, scaling and sums
+    return f
 
 
 def phase_bytes_per_dof(precision: str, nt: int) -> dict:
     """Algorithmic HBM bytes per space-time DOF of each phase (one launch)."""
-    t = 4 if precision == "mixed" else 8                 # real transform word
+    t = 4 if precision in ("mixed", "mixed_ff") else 8   # real transform word (the iterate is 8 B in all modes)
     spec = 2 * t * (nt // 2 + 1) / nt                    # half spectrum, complex, per DOF
     return {
         "residual": 8 + t,            # read U (f64), write s = gamma r
@@ -251,34 +273,86 @@ def main_gpu(args) -> None:
         ms = float(t.item())
 
     # End to end through the host-buffer entry point: H2D of u0 and D2H of U inside.
-    U_host = torch.zeros(nt, ns, dtype=torch.float64).pin_memory().numpy()
-    u0_host = torch.from_numpy(u0_np.copy()).pin_memory().numpy()
-    s.solve_host(u0_host, U_host)
-    e2e_times = []
-    for _ in range(max(1, args.steps)):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
+    e2e_s = None
+    if not args.no_e2e:
+        U_host = torch.zeros(nt, ns, dtype=torch.float64).pin_memory().numpy()
+        u0_host = torch.from_numpy(u0_np.copy()).pin_memory().numpy()
         s.solve_host(u0_host, U_host)
-        e2e_times.append(time.perf_counter() - t0)
-    e2e_s = statistics.mean(e2e_times)
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        e2e_times = []
+        for _ in range(max(1, args.steps)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.solve_host(u0_host, U_host)
+            e2e_times.append(time.perf_counter() - t0)
+        e2e_s = statistics.mean(e2e_times)
+        if dist:
+            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+
+    # The other precision forms on the same input (fewer steps): plain FP64 and
+    # FP64-residual mixed.
+    variants = {}
+    if not args.no_variants:
+        for prec in ("fp64", "mixed", "mixed_ff"):
+            if prec == args.precision:
+                continue
+            with pint.Solver(stream=stream, **solver_kw(wl, args, prec)) as sv:
+                for _ in range(2):
+                    st_v = sv.solve(u0, U)
+                tv = []
+                for _ in range(3):
+                    flush.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    st_v = sv.solve(u0, U)
+                    e1.record(stream)
+                    e1.synchronize()
+                    tv.append(e0.elapsed_time(e1))
+            mv = statistics.mean(tv)
+            variants[prec] = {"ms_per_step": mv, "value": dof / (mv * 1e-3), "iterations": st_v["iters"],
+                              "final_rel_residual": st_v["rel_residual"]}
 
     # Roofline of the dominant phase (largest device time in the timed region).
+    # Per-launch time = phase time / launches, where launches that found the
+    # solve already converged (early exits at the end of a chunk) are excluded.
     bpd = phase_bytes_per_dof(args.precision, nt)
     dom = max((k for k in prof if prof[k]["launches"] > 0 and k != "check"), key=lambda k: prof[k]["ms"])
-    per_launch_ms = prof[dom]["ms"] / max(1, prof[dom]["launches"])
+    iters_per_step = stats["iters"]
+    active = {k: (args.steps * ((iters_per_step + 1) if k == "residual" else iters_per_step)
+                  if k not in ("setup", "check") else prof[k]["launches"]) for k in prof}
+    per_launch_ms = prof[dom]["ms"] / max(1, active[dom])
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    peak = float(peaks.get("hbm_gbs", 6800.0))
-    active_launches = None
-    achieved = bpd[dom] * dof / (per_launch_ms * 1e-3) / 1e9
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    # FP32 peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2070 MHz
+    fp32_peak = 152 * 128 * 2 * 2.070e9 / 1e12
+    if dom == "residual" and args.precision == "mixed_ff":
+        flops = ff_residual_flops_per_dof(wl["equation"], wl["dim"]) * dof
+        ach = flops / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_residual_ff", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": ach / fp32_peak, "traffic": None,
+                "flops_per_dof": flops / dof, "per_launch_us": per_launch_ms * 1e3,
+                "hbm_frac": bpd[dom] * dof / (per_launch_ms * 1e-3) / 1e9 / hbm_peak,
+                "peak_note": "FP32 nominal (152 SMs x 128 lanes x 2 x 2.07 GHz)"}
+    else:
+        ach = bpd[dom] * dof / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "traffic": None, "bytes_per_dof": bpd[dom],
+                "per_launch_us": per_launch_ms * 1e3, "peak_note": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+    phases = {}
+    for k, v in prof.items():
+        if v["launches"] == 0:
+            continue
+        t_l = v["ms"] / max(1, active[k])
+        phases[k] = {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
+                     "us_per_active_launch": t_l * 1e3,
+                     "hbm_frac": (bpd[k] * dof / (t_l * 1e-3) / 1e9 / hbm_peak) if bpd.get(k) else None}
     launches_total = sum(v["launches"] for v in prof.values())
 
     if rank == 0:
@@ -302,24 +376,23 @@ def main_gpu(args) -> None:
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+            "dtype": {"mixed_ff": "f32 (float-float iterate)", "mixed": "f32+f64", "fp64": "f64"}[args.precision],
             "data": "synthetic",
             "config": {"workload": args.workload, "precision": args.precision, "alpha": args.alpha,
-                       "tol": args.tol, "dof_per_gpu": dof, "iterations": stats["iters"],
+                       "tol": args.tol, "init": "zero" if args.init == 2 else "u0", "dof_per_gpu": dof,
+                       "iterations": stats["iters"],
                        "final_rel_residual": stats["rel_residual"], "l2": "flushed between steps",
                        "parallelism": f"replicas x{world}"},
-            "e2e": {"value": world * dof / e2e_s, "unit": "space-time DOF/s", "h2d_bytes_per_step": ns * 8,
-                    "d2h_bytes_per_step": dof * 8},
+            "e2e": ({"value": world * dof / e2e_s, "unit": "space-time DOF/s", "h2d_bytes_per_step": ns * 8,
+                     "d2h_bytes_per_step": dof * 8} if e2e_s else None),
             "gpu_launches": launches_total,
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "bytes_per_dof": bpd[dom], "per_launch_us": per_launch_ms * 1e3},
-            "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
-            "phases_launches_per_step": {k: v["launches"] / args.steps for k, v in prof.items()},
+            "roofline": roof,
+            "phases": phases,
+            "variants": variants,
+            "speedup_vs_fp64": (variants["fp64"]["ms_per_step"] / ms) if "fp64" in variants else None,
             "clocks": clk,
             "cpu_baseline": cpu,
         }
-        _ = active_launches
         print(json.dumps(out), flush=True)
     s.close()
     if dist:
@@ -358,7 +431,11 @@ def main() -> None:
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed_ff", choices=["mixed_ff", "mixed", "fp64"])
+    ap.add_argument("--init", type=int, default=2, choices=[0, 2],
+                    help="initial iterate: 0 = u0 at every level, 2 = zero")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--alpha", type=float, default=1e-2)
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))

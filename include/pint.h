@@ -41,23 +41,31 @@ extern "C" {
 #define PINT_EINVAL     -1   /* invalid or unsupported problem parameter / argument */
 #define PINT_ENOMEM     -2   /* device or host allocation failed */
 #define PINT_ECUDA      -3   /* a CUDA runtime call failed */
-#define PINT_ENOCONV    -4   /* max_iter reached; U holds the last iterate, stats are filled */
-#define PINT_EDIVERGED  -5   /* residual non-finite or grew by 1e6 over its first value */
+#define PINT_ENOCONV    -4   /* max_iter reached, or no decrease over three iterations (rounding
+                                floor); U holds the last iterate, stats are filled */
+#define PINT_EDIVERGED  -5   /* residual non-finite, grew by 1e6 over its first value, or
+                                by 10x over three iterations */
 
 typedef enum { PINT_BIHARMONIC = 0, PINT_LINEAR_CH = 1, PINT_CAHN_HILLIARD = 2 } pint_equation;
 
 /* Boundary conditions (Sec. 5.1 lists the variants):
  *  SIMPLY_SUPPORTED: u = Lap u = 0, vertex grid of n interior points, h = 1/(n+1);
- *                    spatial solves by sine transforms (DST-I).
+ *                    spatial solves in the sine basis (DST-I, dense, n <= 1024).
  *  NEUMANN:          d_nu u = d_nu Lap u = 0, cell-centred grid of n cells, h = 1/n;
- *                    spatial solves by cosine transforms (DCT-II), n a power of two. */
+ *                    spatial solves in the cosine basis (DCT-II): by FFT when n is a
+ *                    power of two (x: n <= 4096, y: n <= 1024), else dense (n <= 1024). */
 typedef enum { PINT_BC_SIMPLY_SUPPORTED = 0, PINT_BC_NEUMANN = 1 } pint_bc;
 
-/* PINT_FP64:  every step in FP64 (the plain form).
- * PINT_MIXED: residual, alpha-scaling, unscaling and the update in FP64; the
- *             time FFTs and the spatial shifted solves in FP32 / complex64, so
- *             the outer iteration is an iterative refinement. */
-typedef enum { PINT_FP64 = 0, PINT_MIXED = 1 } pint_precision;
+/* PINT_FP64:     every step in FP64 (the plain form).
+ * PINT_MIXED:    residual, alpha-scaling, unscaling and the update in FP64; the
+ *                time FFTs and the spatial shifted solves in FP32 / complex64, so
+ *                the outer iteration is an iterative refinement.
+ * PINT_MIXED_FF: as PINT_MIXED, but the iterate and the residual are kept in
+ *                float-float (two FP32 words, about 48 significant bits, error-free
+ *                stencil sums) on the FP32 pipes, and the alpha-scaling/unscaling is
+ *                an FP32 product.  No FP64 arithmetic in the iteration; the FP64
+ *                result is assembled once per solve. */
+typedef enum { PINT_FP64 = 0, PINT_MIXED = 1, PINT_MIXED_FF = 2 } pint_precision;
 
 /* Problem statement (Eq. 2.1-2.2, 3.1-3.2, 4.1-4.2, the tolerance of Sec. 5). */
 typedef struct {
@@ -76,7 +84,9 @@ typedef struct {
     int    max_iter;     /* outer iterations per window, 1..PINT_HIST_MAX */
     int    precision;    /* pint_precision */
     int    init_guess;   /* 0: each window starts from U^0 = u0 at every time level;
-                            1: the first window starts from the iterate passed in U */
+                            1: the first window starts from the iterate passed in U,
+                               later windows as 0;
+                            2: each window starts from U^0 = 0 */
 } pint_problem;
 
 #define PINT_HIST_MAX 256

@@ -18,7 +18,7 @@ BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libpint.so")
 
-SOURCES = ["pint_api.cu", "k_residual.cu", "k_timefft.cu", "k_spatial.cu"]
+SOURCES = ["pint_api.cu", "k_residual.cu", "k_residual_ff.cu", "k_timefft.cu", "k_spatial.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(os.path.dirname(PKG), "include")]
@@ -61,7 +61,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
     tmp = LIB + ".tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "--cudart=static", "-o", tmp, *objs]
+    cmd = [nvcc(), *ARCH, "-shared", "--cudart=static", "-Xlinker", "--no-undefined", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -197,9 +197,14 @@ __global__ void __launch_bounds__(256) k_after_residual(const double* __restrict
         ctl->jbar = 3.0 * B * inv_dof;
         if (k < 256) ctl->hist[k] = rho;
         if (k == 0) ctl->rho0 = rho;
-        if (!(rho == rho) || rho > 1e300 || (k > 0 && rho > 1e6 * ctl->rho0)) ctl->status = -5;  // PINT_EDIVERGED
+        // stagnation: no decrease over the last three corrections (the residual
+        // sits at the rounding floor of the iterate's precision)
+        // (growth by 10x over three corrections counts as divergence)
+        const bool stalled = k >= 4 && k < 256 && rho >= 0.99 * ctl->hist[k - 3];
+        const bool growing = stalled && rho > 10.0 * ctl->hist[k - 3];
+        if (!(rho == rho) || rho > 1e300 || (k > 0 && rho > 1e6 * ctl->rho0) || growing) ctl->status = -5;  // PINT_EDIVERGED
         else if (rho <= ctl->tol) ctl->status = 0;                                              // PINT_OK
-        else if (k >= ctl->max_iter) ctl->status = -4;                                          // PINT_ENOCONV
+        else if (k >= ctl->max_iter || stalled) ctl->status = -4;                               // PINT_ENOCONV
         else ctl->iter = k + 1;
     }
 }

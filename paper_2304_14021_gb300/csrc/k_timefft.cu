@@ -11,6 +11,7 @@
 // A CTA holds CW complex columns (2*CW consecutive spatial points) times all
 // N_t time levels in shared memory: loads and stores are rows of CW
 // consecutive values per time level / frequency, i.e. coalesced.
+#include "ff.cuh"
 #include "pint_common.cuh"
 #include "pint_kernels.h"
 
@@ -57,11 +58,13 @@ __global__ void __launch_bounds__(TimeCfg<T, NT>::NTH)
     }
 }
 
-template <class T, int NT>
+// OUTK = 0: FP64 output (out = delta, or out += delta when accumulate);
+// OUTK = 1: float-float iterate, outff += delta with delta = x * ginvf[n] in FP32.
+template <class T, int NT, int OUTK>
 __global__ void __launch_bounds__(TimeCfg<T, NT>::NTH)
     k_time_inv(int nspace, const c_t<T>* __restrict__ S, const c_t<T>* __restrict__ twt,
-               const double* __restrict__ ginv, double* __restrict__ out, int accumulate,
-               const Ctl* __restrict__ ctl) {
+               const double* __restrict__ ginv, const float* __restrict__ ginvf, double* __restrict__ out,
+               float2* __restrict__ outff, int accumulate, const Ctl* __restrict__ ctl) {
     using C = c_t<T>;
     constexpr int CW = TimeCfg<T, NT>::CW, NTH = TimeCfg<T, NT>::NTH;
     if (ctl && ctl->status != ST_RUNNING) return;
@@ -86,8 +89,15 @@ __global__ void __launch_bounds__(TimeCfg<T, NT>::NTH)
     for (int e = tid; e < NT * CW; e += NTH) {
         const int c = e % CW, n = e / CW;
         const C v = z[e];
-        const double gi = ginv[n];
         const long pa = p0 + c, pb = p0 + CW + c;
+        if constexpr (OUTK == 1) {
+            const float gi = ginvf[n];
+            float2* row = outff + (size_t)n * nspace;
+            if (pa < nspace) row[pa] = ff_add_f(row[pa], (float)v.x * gi);
+            if (pb < nspace) row[pb] = ff_add_f(row[pb], (float)v.y * gi);
+            continue;
+        }
+        const double gi = ginv[n];
         double* row = out + (size_t)n * nspace;
         const double da = (double)v.x * gi, db = (double)v.y * gi;   // FP64 unscaling
         if (accumulate) {
@@ -102,11 +112,14 @@ __global__ void __launch_bounds__(TimeCfg<T, NT>::NTH)
 
 template <class T, int NT>
 static cudaError_t configure_time() {
-    cudaError_t e = cudaFuncSetAttribute(k_time_fwd<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)TimeCfg<T, NT>::SMEM);
+    const int sm = (int)TimeCfg<T, NT>::SMEM;
+    cudaError_t e = cudaFuncSetAttribute(k_time_fwd<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_time_inv<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)TimeCfg<T, NT>::SMEM);
+    e = cudaFuncSetAttribute(k_time_inv<T, NT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e != cudaSuccess) return e;
+    if constexpr (sizeof(T) == 4)
+        e = cudaFuncSetAttribute(k_time_inv<T, NT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    return e;
 }
 
 template <class T>
@@ -132,7 +145,16 @@ static void time_inv_nt(int nspace, const c_t<T>* S, const c_t<T>* twt, const do
                         const Ctl* ctl, cudaStream_t st) {
     constexpr int CW = TimeCfg<T, NT>::CW;
     int grid = (nspace + 2 * CW - 1) / (2 * CW);
-    k_time_inv<T, NT><<<grid, TimeCfg<T, NT>::NTH, TimeCfg<T, NT>::SMEM, st>>>(nspace, S, twt, ginv, out, acc, ctl);
+    k_time_inv<T, NT, 0><<<grid, TimeCfg<T, NT>::NTH, TimeCfg<T, NT>::SMEM, st>>>(nspace, S, twt, ginv, nullptr, out,
+                                                                                  nullptr, acc, ctl);
+}
+template <int NT>
+static void time_inv_ff_nt(int nspace, const float2* S, const float2* twt, const float* ginvf, float2* Uff,
+                           const Ctl* ctl, cudaStream_t st) {
+    constexpr int CW = TimeCfg<float, NT>::CW;
+    int grid = (nspace + 2 * CW - 1) / (2 * CW);
+    k_time_inv<float, NT, 1><<<grid, TimeCfg<float, NT>::NTH, TimeCfg<float, NT>::SMEM, st>>>(
+        nspace, S, twt, nullptr, ginvf, nullptr, Uff, 1, ctl);
 }
 
 #define PINT_NT_SWITCH(CALL)                                                                            \
@@ -156,6 +178,14 @@ template <class T>
 cudaError_t launch_time_inv(int nt, int nspace, const c_t<T>* S, const c_t<T>* twt, const double* ginv, double* out,
                             int accumulate, const Ctl* ctl, cudaStream_t st) {
 #define CALL(N) time_inv_nt<T, N>(nspace, S, twt, ginv, out, accumulate, ctl, st)
+    PINT_NT_SWITCH(CALL)
+#undef CALL
+    return cudaGetLastError();
+}
+
+cudaError_t launch_time_inv_ff(int nt, int nspace, const float2* S, const float2* twt, const float* ginvf,
+                               float2* Uff, const Ctl* ctl, cudaStream_t st) {
+#define CALL(N) time_inv_ff_nt<N>(nspace, S, twt, ginvf, Uff, ctl, st)
     PINT_NT_SWITCH(CALL)
 #undef CALL
     return cudaGetLastError();

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "../../include/pint.h"
+#include "ff.cuh"
 #include "pint_common.cuh"
 #include "pint_kernels.h"
 
@@ -54,11 +55,11 @@ static int validate(const pint_problem* p) {
     if (!(p->alpha > 0.0 && p->alpha < 1.0)) return PINT_EINVAL;
     if (!(p->tol > 0.0) || !isfinite(p->tol)) return PINT_EINVAL;
     if (p->max_iter < 1 || p->max_iter >= PINT_HIST_MAX) return PINT_EINVAL;
-    if (p->precision != PINT_FP64 && p->precision != PINT_MIXED) return PINT_EINVAL;
+    if (p->precision != PINT_FP64 && p->precision != PINT_MIXED && p->precision != PINT_MIXED_FF) return PINT_EINVAL;
     if (!(p->T > 0.0) || !isfinite(p->T)) return PINT_EINVAL;
     if (p->equation != PINT_BIHARMONIC && !(p->eps > 0.0)) return PINT_EINVAL;
     if (!isfinite(p->beta) || !isfinite(p->eps)) return PINT_EINVAL;
-    if (p->init_guess != 0 && p->init_guess != 1) return PINT_EINVAL;
+    if (p->init_guess < 0 || p->init_guess > 2) return PINT_EINVAL;
     const int ny = p->dim == 2 ? p->ny : 1;
     if (!axis_fft(p->nx, p->bc, 4096) && p->nx > 1024) return PINT_EINVAL;
     if (p->dim == 2 && !axis_fft(ny, p->bc, 1024) && ny > 1024) return PINT_EINVAL;
@@ -74,6 +75,8 @@ static double lap_eig(int p, int n, int bc) {
     const double s = bc == PINT_BC_SIMPLY_SUPPORTED ? sin(M_PI * (p + 1) / (2.0 * (n + 1))) : sin(M_PI * p / (2.0 * n));
     return -4.0 / (h * h) * s * s;
 }
+
+static bool f32_transforms(const pint_problem* p) { return p->precision != PINT_FP64; }
 
 struct Sizes {
     size_t nspace, dof, nk, partials, tables_T, tables_bytes;
@@ -101,6 +104,12 @@ struct pint_handle {
     void* s = nullptr;              // alpha-scaled residual, transform precision
     void* S = nullptr;              // half spectrum, complex transform precision
     void* tab = nullptr;            // tables block
+    // PINT_MIXED_FF: float-float iterate and its tables
+    float2* Uff = nullptr;          // nt*nspace
+    float2* u0ff = nullptr;         // nspace
+    float* gamf = nullptr;          // alpha^{n/nt} (FP32)
+    float* ginvf = nullptr;         // alpha^{-n/nt}/nt (FP32)
+    pint::GeoFF gff;
     long long bytes = 0;
     void* tabs_ptrs = nullptr;      // Tabs<T>* (host struct of device pointers)
     // profiling: launch counters always, event pairs around phases when enabled
@@ -227,6 +236,13 @@ static int build_tables(pint_handle* h) {
     }
     if (cudaMemcpy(h->gam, g.data(), nt * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) return PINT_ECUDA;
     if (cudaMemcpy(h->ginv, gi.data(), nt * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) return PINT_ECUDA;
+    if (h->gamf) {
+        std::vector<float> gf(nt), gif(nt);
+        for (int n = 0; n < nt; ++n) { gf[n] = (float)g[n]; gif[n] = (float)gi[n]; }
+        if (cudaMemcpy(h->gamf, gf.data(), nt * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) return PINT_ECUDA;
+        if (cudaMemcpy(h->ginvf, gif.data(), nt * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+            return PINT_ECUDA;
+    }
     return PINT_OK;
 }
 
@@ -253,6 +269,19 @@ static void derive(const pint_problem* p, pint_handle* h) {
     h->coef.c1 = g.c1;
     h->fft_x = axis_fft(p->nx, p->bc, 4096);
     h->fft_y = p->dim == 2 ? axis_fft(g.ny, p->bc, 1024) : 1;
+    GeoFF& f = h->gff;
+    f.nx = g.nx;
+    f.ny = g.ny;
+    f.dim = g.dim;
+    f.bc = g.bc;
+    f.nt = g.nt;
+    f.nspace = g.nspace;
+    f.ihx2 = ff_from_double(g.ihx2);
+    f.ihy2 = ff_from_double(g.ihy2);
+    f.inv_dt = ff_from_double(g.inv_dt);
+    f.c2 = ff_from_double(g.c2);
+    f.c1 = ff_from_double(g.c1);
+    f.cN = (float)g.cN;
 }
 
 static Sizes sizes_of(const pint_problem* p, pint_handle* tmp) {
@@ -267,7 +296,7 @@ static Sizes sizes_of(const pint_problem* p, pint_handle* tmp) {
     z.partials = (size_t)(nres > nn ? nres : nn);
     TabLayout L = tab_layout(p, tmp->fft_x, tmp->fft_y);
     z.tables_T = L.total;
-    const size_t ts = p->precision == PINT_MIXED ? 4 : 8;
+    const size_t ts = f32_transforms(p) ? 4 : 8;
     z.tables_bytes = L.total * ts;
     return z;
 }
@@ -276,7 +305,7 @@ static long long footprint_of(const pint_problem* p) {
     pint_handle tmp;
     memset(&tmp.p, 0, sizeof(tmp.p));
     Sizes z = sizes_of(p, &tmp);
-    const size_t ts = p->precision == PINT_MIXED ? 4 : 8;
+    const size_t ts = f32_transforms(p) ? 4 : 8;
     long long b = 0;
     b += sizeof(Ctl);
     b += z.partials * 2 * sizeof(double);
@@ -285,6 +314,7 @@ static long long footprint_of(const pint_problem* p) {
     b += z.dof * ts;                 // s
     b += z.nk * z.nspace * 2 * ts;   // S
     b += z.tables_bytes;
+    if (p->precision == PINT_MIXED_FF) b += z.dof * 8 + z.nspace * 8 + 2 * (size_t)p->nt * 4;
     return b;
 }
 
@@ -331,7 +361,33 @@ template <class T> struct Impl {
         }
         return cudaSuccess;
     }
-    static cudaError_t iteration(pint_handle* h, double* U, const double* u0w) {
+    // PINT_MIXED_FF: float-float residual and update, FP32 transforms.
+static cudaError_t iteration_ff(pint_handle* h) {
+    const Geo& g = h->geo;
+    float* s = reinterpret_cast<float*>(h->s);
+    float2* S = reinterpret_cast<float2*>(h->S);
+    const Tabs<float>& tb = tabs_of<float>(h);
+    prof_begin(h, PH_RES);
+    launch_residual_ff(h->gff, g, h->Uff, h->u0ff, h->gamf, s, h->partials, h->ctl, h->st);
+    prof_end(h, PH_RES, 1);
+    int gx, gy, gz, chunk;
+    const int np = residual_grid(g, gx, gy, gz, chunk);
+    prof_begin(h, PH_CHECK);
+    launch_after_residual(h->partials, np, 1.0 / ((double)g.nt * g.nspace), h->ctl, h->st);
+    prof_end(h, PH_CHECK, 1);
+    prof_begin(h, PH_TFWD);
+    cudaError_t e = launch_time_fwd<float>(g.nt, g.nspace, s, S, tb.twt, h->ctl, h->st);
+    prof_end(h, PH_TFWD, 1);
+    if (e != cudaSuccess) return e;
+    if ((e = Impl<float>::spatial(h, S, tb)) != cudaSuccess) return e;
+    prof_begin(h, PH_TINV);
+    e = launch_time_inv_ff(g.nt, g.nspace, S, tb.twt, h->ginvf, h->Uff, h->ctl, h->st);
+    prof_end(h, PH_TINV, 1);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+static cudaError_t iteration(pint_handle* h, double* U, const double* u0w) {
         const Geo& g = h->geo;
         T* s = reinterpret_cast<T*>(h->s);
         c_t<T>* S = reinterpret_cast<c_t<T>*>(h->S);
@@ -371,8 +427,34 @@ template <class T> struct Impl {
     }
 };
 
+// PINT_MIXED_FF: float-float residual and update, FP32 transforms.
+static cudaError_t iteration_ff(pint_handle* h) {
+    const Geo& g = h->geo;
+    float* s = reinterpret_cast<float*>(h->s);
+    float2* S = reinterpret_cast<float2*>(h->S);
+    const Tabs<float>& tb = tabs_of<float>(h);
+    prof_begin(h, PH_RES);
+    launch_residual_ff(h->gff, g, h->Uff, h->u0ff, h->gamf, s, h->partials, h->ctl, h->st);
+    prof_end(h, PH_RES, 1);
+    int gx, gy, gz, chunk;
+    const int np = residual_grid(g, gx, gy, gz, chunk);
+    prof_begin(h, PH_CHECK);
+    launch_after_residual(h->partials, np, 1.0 / ((double)g.nt * g.nspace), h->ctl, h->st);
+    prof_end(h, PH_CHECK, 1);
+    prof_begin(h, PH_TFWD);
+    cudaError_t e = launch_time_fwd<float>(g.nt, g.nspace, s, S, tb.twt, h->ctl, h->st);
+    prof_end(h, PH_TFWD, 1);
+    if (e != cudaSuccess) return e;
+    if ((e = Impl<float>::spatial(h, S, tb)) != cudaSuccess) return e;
+    prof_begin(h, PH_TINV);
+    e = launch_time_inv_ff(g.nt, g.nspace, S, tb.twt, h->ginvf, h->Uff, h->ctl, h->st);
+    prof_end(h, PH_TINV, 1);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
 static cudaError_t iteration(pint_handle* h, double* U, const double* u0w) {
-    return h->p.precision == PINT_MIXED ? Impl<float>::iteration(h, U, u0w) : Impl<double>::iteration(h, U, u0w);
+    return f32_transforms(&h->p) ? Impl<float>::iteration(h, U, u0w) : Impl<double>::iteration(h, U, u0w);
 }
 
 }  // namespace pint
@@ -417,10 +499,14 @@ void pint_destroy(pint_handle* h) {
     cudaFree(h->s);
     cudaFree(h->S);
     cudaFree(h->tab);
+    cudaFree(h->Uff);
+    cudaFree(h->u0ff);
+    cudaFree(h->gamf);
+    cudaFree(h->ginvf);
     for (int i = 0; i < 2 * pint_handle::NEV; ++i)
         if (h->ev[i]) cudaEventDestroy(h->ev[i]);
     if (h->tabs_ptrs) {
-        if (h->p.precision == PINT_MIXED) delete reinterpret_cast<Tabs<float>*>(h->tabs_ptrs);
+        if (f32_transforms(&h->p)) delete reinterpret_cast<Tabs<float>*>(h->tabs_ptrs);
         else delete reinterpret_cast<Tabs<double>*>(h->tabs_ptrs);
     }
     delete h;
@@ -437,7 +523,7 @@ int pint_create(const pint_problem* p, void* cuda_stream, pint_handle** out) {
     h->p = *p;
     h->st = (cudaStream_t)cuda_stream;
     Sizes z = sizes_of(p, h);
-    const size_t ts = p->precision == PINT_MIXED ? 4 : 8;
+    const size_t ts = f32_transforms(p) ? 4 : 8;
     auto dalloc = [&](void** ptr, size_t bytes) -> int {
         if (cudaMalloc(ptr, bytes < 16 ? 16 : bytes) != cudaSuccess) {
             cudaGetLastError();
@@ -455,8 +541,14 @@ int pint_create(const pint_problem* p, void* cuda_stream, pint_handle** out) {
     if (!rc) rc = dalloc(&h->s, z.dof * ts);
     if (!rc) rc = dalloc(&h->S, z.nk * z.nspace * 2 * ts);
     if (!rc) rc = dalloc(&h->tab, z.tables_bytes);
+    if (!rc && p->precision == PINT_MIXED_FF) {
+        rc = dalloc((void**)&h->Uff, z.dof * sizeof(float2));
+        if (!rc) rc = dalloc((void**)&h->u0ff, z.nspace * sizeof(float2));
+        if (!rc) rc = dalloc((void**)&h->gamf, p->nt * sizeof(float));
+        if (!rc) rc = dalloc((void**)&h->ginvf, p->nt * sizeof(float));
+    }
     if (!rc && cudaMallocHost((void**)&h->hctl, sizeof(Ctl)) != cudaSuccess) rc = PINT_ENOMEM;
-    if (!rc) rc = p->precision == PINT_MIXED ? build_tables<float>(h) : build_tables<double>(h);
+    if (!rc) rc = f32_transforms(p) ? build_tables<float>(h) : build_tables<double>(h);
     if (!rc && cudaMemset(h->ctl, 0, sizeof(Ctl)) != cudaSuccess) rc = PINT_ECUDA;
     if (rc) {
         pint_destroy(h);
@@ -502,21 +594,34 @@ int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* 
     if (!h || !u0_dev || !U_dev) return PINT_EINVAL;
     const pint_problem& p = h->p;
     const Geo& g = h->geo;
+    const bool ffm = p.precision == PINT_MIXED_FF;
+    const size_t dof = (size_t)g.nt * g.nspace;
     pint_stats S;
     memset(&S, 0, sizeof(S));
     int rc = PINT_OK;
+    if (ffm && p.init_guess == 1) launch_f64_to_ff(U_dev, h->Uff, dof, h->st);
     for (int w = 0; w < p.n_windows; ++w) {
         const double* u0w = w == 0 ? u0_dev : h->u0buf;
         prof_begin(h, PH_SETUP);
-        const bool bc = w > 0 || !p.init_guess;
-        if (bc) launch_broadcast(U_dev, u0w, g.nspace, g.nt, h->st);
+        int nl = 2;
+        if (ffm && w == 0) { launch_f64_to_ff(u0_dev, h->u0ff, g.nspace, h->st); nl++; }
+        if (p.init_guess == 2) {
+            PINT_CK(ffm ? cudaMemsetAsync(h->Uff, 0, dof * sizeof(float2), h->st)
+                        : cudaMemsetAsync(U_dev, 0, dof * sizeof(double), h->st));
+        } else if (w > 0 || p.init_guess == 0) {
+            if (ffm) launch_broadcast_ff(h->Uff, h->u0ff, g.nspace, g.nt, h->st);
+            else launch_broadcast(U_dev, u0w, g.nspace, g.nt, h->st);
+            nl++;
+        }
         launch_begin_window(u0w, g.nspace, g.inv_dt, p.max_iter, p.tol, h->partials, h->ctl, h->st);
-        prof_end(h, PH_SETUP, bc ? 3 : 2);
+        prof_end(h, PH_SETUP, nl);
         int enqueued = 0;
         for (;;) {
             int chunk = enqueued == 0 ? 3 : 2;
-            for (int c = 0; c < chunk; ++c)
-                if (iteration(h, U_dev, u0w) != cudaSuccess) return PINT_ECUDA;
+            for (int c = 0; c < chunk; ++c) {
+                cudaError_t e = ffm ? iteration_ff(h) : iteration(h, U_dev, u0w);
+                if (e != cudaSuccess) return PINT_ECUDA;
+            }
             enqueued += chunk;
             if ((rc = read_ctl(h)) != PINT_OK) return rc;
             if (h->hctl->status != ST_RUNNING) break;
@@ -536,9 +641,21 @@ int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* 
             break;
         }
         S.windows = w + 1;
-        if (w + 1 < p.n_windows)
-            PINT_CK(cudaMemcpyAsync(h->u0buf, U_dev + (size_t)(g.nt - 1) * g.nspace, g.nspace * sizeof(double),
-                                    cudaMemcpyDeviceToDevice, h->st));
+        if (w + 1 < p.n_windows) {
+            if (ffm) {
+                PINT_CK(cudaMemcpyAsync(h->u0ff, h->Uff + (size_t)(g.nt - 1) * g.nspace, g.nspace * sizeof(float2),
+                                        cudaMemcpyDeviceToDevice, h->st));
+                launch_ff_to_f64(h->u0ff, h->u0buf, g.nspace, h->st);
+            } else {
+                PINT_CK(cudaMemcpyAsync(h->u0buf, U_dev + (size_t)(g.nt - 1) * g.nspace, g.nspace * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, h->st));
+            }
+        }
+    }
+    if (ffm) {
+        launch_ff_to_f64(h->Uff, U_dev, dof, h->st);
+        h->launches[PH_SETUP] += 1;
+        PINT_CK(cudaStreamSynchronize(h->st));
     }
     if (st) *st = S;
     return rc;
@@ -578,7 +695,7 @@ int pint_residual(pint_handle* h, const double* u0_dev, const double* U_dev, dou
 
 int pint_precond_apply(pint_handle* h, double jbar, const double* r_dev, double* delta_dev) {
     if (!h || !r_dev || !delta_dev || r_dev == delta_dev) return PINT_EINVAL;
-    cudaError_t e = h->p.precision == PINT_MIXED ? Impl<float>::precond(h, jbar, r_dev, delta_dev)
+    cudaError_t e = f32_transforms(&h->p) ? Impl<float>::precond(h, jbar, r_dev, delta_dev)
                                                   : Impl<double>::precond(h, jbar, r_dev, delta_dev);
     if (e != cudaSuccess) return PINT_ECUDA;
     PINT_CK(cudaStreamSynchronize(h->st));

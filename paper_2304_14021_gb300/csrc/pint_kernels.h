@@ -31,7 +31,21 @@ struct SolveCoef {
     int ch;
 };
 
+// Float-float form of Geo for the PINT_MIXED_FF residual (constants as hi + lo pairs).
+struct GeoFF {
+    int nx, ny, dim, bc, nt, nspace;
+    float2 ihx2, ihy2, inv_dt, c2, c1;
+    float cN;
+};
+
 int residual_grid(const Geo& g, int& gx, int& gy, int& gz, int& chunk);
+void launch_residual_ff(const GeoFF& g, const Geo& g64, const float2* U, const float2* u0, const float* gamf,
+                        float* s, double* partials, const Ctl* ctl, cudaStream_t st);
+void launch_f64_to_ff(const double* in, float2* out, size_t n, cudaStream_t st);
+void launch_ff_to_f64(const float2* in, double* out, size_t n, cudaStream_t st);
+void launch_broadcast_ff(float2* U, const float2* u0, int nspace, int nt, cudaStream_t st);
+cudaError_t launch_time_inv_ff(int nt, int nspace, const float2* S, const float2* twt, const float* ginvf,
+                               float2* Uff, const Ctl* ctl, cudaStream_t st);
 template <class TS>
 void launch_residual(const Geo& g, const double* U, const double* u0, const double* gam, double* r_out, TS* s_out,
                      double* partials, const Ctl* ctl, cudaStream_t st);

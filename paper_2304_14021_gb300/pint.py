@@ -16,12 +16,12 @@ LIB_PATH = os.path.join(PKG, "_lib", "libpint.so")
 PINT_OK, PINT_EINVAL, PINT_ENOMEM, PINT_ECUDA, PINT_ENOCONV, PINT_EDIVERGED = 0, -1, -2, -3, -4, -5
 BIHARMONIC, LINEAR_CH, CAHN_HILLIARD = 0, 1, 2
 BC_SIMPLY_SUPPORTED, BC_NEUMANN = 0, 1
-FP64, MIXED = 0, 1
+FP64, MIXED, MIXED_FF = 0, 1, 2
 HIST_MAX = 256
 
 EQUATIONS = {"biharmonic": BIHARMONIC, "linear_ch": LINEAR_CH, "cahn_hilliard": CAHN_HILLIARD}
 BCS = {"ss": BC_SIMPLY_SUPPORTED, "neumann": BC_NEUMANN}
-PRECISIONS = {"fp64": FP64, "mixed": MIXED}
+PRECISIONS = {"fp64": FP64, "mixed": MIXED, "mixed_ff": MIXED_FF}
 
 
 class Problem(C.Structure):

@@ -51,7 +51,7 @@ def test_strerror(lib):
 BAD = [dict(dim=3), dict(nx=1), dict(nt=48), dict(nt=2048), dict(nt=1), dict(alpha=0.0), dict(alpha=1.0),
        dict(theta=0.5), dict(tol=0.0), dict(max_iter=0), dict(max_iter=256), dict(precision=7),
        dict(T=-1.0), dict(equation=5), dict(bc=3), dict(n_windows=0), dict(nx=2000, bc="ss"),
-       dict(equation="linear_ch", eps=0.0), dict(init_guess=2), dict(dim=2, ny=1)]
+       dict(equation="linear_ch", eps=0.0), dict(init_guess=3), dict(dim=2, ny=1)]
 
 
 @pytest.mark.parametrize("bad", BAD)
