@@ -162,6 +162,16 @@ int pint_profile_enable(pint_handle* h, int on);
 /* Copy the accumulated profile into *out; reset = 1 zeroes it afterwards. */
 int pint_profile_read(pint_handle* h, pint_profile* out, int reset);
 
+/* Execution options.
+ *  PINT_OPT_GRAPHS (default 1): run each window's iteration loop as one CUDA
+ *    graph with a device-controlled while-node (no host round trip per
+ *    iteration; the graph is built on the first solve and cached).  0 = launch
+ *    kernels from the host in chunks of iterations.  While phase timing is
+ *    enabled (pint_profile_enable) the host-launched path is used.
+ * Errors: PINT_EINVAL for an unknown option or value. */
+#define PINT_OPT_GRAPHS 1
+int pint_set_option(pint_handle* h, int option, long long value);
+
 /* Free everything the handle owns (NULL is allowed). */
 void pint_destroy(pint_handle* h);
 

@@ -181,10 +181,17 @@ __global__ void __launch_bounds__(256) k_begin_window(const double* __restrict__
     }
 }
 
-// After the residual of iterate k: rho_k, jbar, stopping decision.
+// After the residual of iterate k: rho_k, jbar, stopping decision.  When the
+// iteration runs as a CUDA-graph while-loop, this kernel also sets the loop
+// condition (1 = run another iteration); it does so on every path, so a loop
+// whose status is already final stops after this iteration.
 __global__ void __launch_bounds__(256) k_after_residual(const double* __restrict__ partials, int np,
-                                                        double inv_dof, Ctl* ctl) {
-    if (ctl->status != ST_RUNNING) return;
+                                                        double inv_dof, Ctl* ctl, cudaGraphConditionalHandle cond,
+                                                        int use_cond) {
+    if (ctl->status != ST_RUNNING) {
+        if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+        return;
+    }
     double A, B;
     reduce_pairs(partials, np, A, B);
     if (threadIdx.x == 0) {
@@ -206,6 +213,7 @@ __global__ void __launch_bounds__(256) k_after_residual(const double* __restrict
         else if (rho <= ctl->tol) ctl->status = 0;                                              // PINT_OK
         else if (k >= ctl->max_iter || stalled) ctl->status = -4;                               // PINT_ENOCONV
         else ctl->iter = k + 1;
+        if (use_cond) cudaGraphSetConditional(cond, ctl->status == ST_RUNNING ? 1u : 0u);
     }
 }
 
@@ -217,6 +225,26 @@ __global__ void __launch_bounds__(256) k_residual_norm(const double* __restrict_
         const double bn = ctl->bnorm;
         ctl->sum_r2 = A;
         ctl->rho = bn > 0.0 ? sqrt(A) / bn : sqrt(A);
+    }
+}
+
+// First iteration from U = 0: S[k][p] = u0[p]/dt for every k (the transform of
+// b = (u0/dt, 0, ..., 0) with gamma_0 = 1); rho_0 = ||b||/||b|| = 1.
+template <class T>
+__global__ void k_zero_start(c_t<T>* __restrict__ S, const double* __restrict__ u0, double inv_dt, int nspace,
+                             int nk, Ctl* __restrict__ ctl) {
+    if (ctl->status != ST_RUNNING) return;
+    const size_t total = (size_t)nspace * nk;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x)
+        S[i] = mkc((T)(u0[i % nspace] * inv_dt), T(0));
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const double rho = ctl->bnorm > 0.0 ? 1.0 : 0.0;
+        ctl->hist[0] = rho;
+        ctl->rho0 = rho;
+        ctl->rho = rho;
+        ctl->jbar = 0.0;
+        if (rho <= ctl->tol) ctl->status = 0;
+        else ctl->iter = 1;
     }
 }
 
@@ -284,8 +312,9 @@ void launch_begin_window(const double* u0, int nspace, double inv_dt, int max_it
     k_norm2<<<nb, 256, 0, st>>>(u0, nspace, partials);
     k_begin_window<<<1, 256, 0, st>>>(partials, nb, inv_dt, max_iter, tol, ctl);
 }
-void launch_after_residual(const double* partials, int np, double inv_dof, Ctl* ctl, cudaStream_t st) {
-    k_after_residual<<<1, 256, 0, st>>>(partials, np, inv_dof, ctl);
+void launch_after_residual(const double* partials, int np, double inv_dof, Ctl* ctl, cudaStream_t st,
+                           unsigned long long cond, int use_cond) {
+    k_after_residual<<<1, 256, 0, st>>>(partials, np, inv_dof, ctl, (cudaGraphConditionalHandle)cond, use_cond);
 }
 void launch_residual_norm(const double* partials, int np, Ctl* ctl, cudaStream_t st) {
     k_residual_norm<<<1, 256, 0, st>>>(partials, np, ctl);
@@ -297,6 +326,16 @@ void launch_broadcast(double* U, const double* u0, int nspace, int nt, cudaStrea
     if (nb > 4 * 152 * 8) nb = 4 * 152 * 8;
     k_broadcast<<<nb, 256, 0, st>>>(U, u0, nspace, nt);
 }
+template <class T>
+void launch_zero_start(c_t<T>* S, const double* u0, double inv_dt, int nspace, int nk, Ctl* ctl, cudaStream_t st) {
+    size_t total = (size_t)nspace * nk;
+    int nb = (int)((total + 255) / 256);
+    if (nb > 4 * 152 * 8) nb = 4 * 152 * 8;
+    k_zero_start<T><<<nb, 256, 0, st>>>(S, u0, inv_dt, nspace, nk, ctl);
+}
+template void launch_zero_start<float>(float2*, const double*, double, int, int, Ctl*, cudaStream_t);
+template void launch_zero_start<double>(double2*, const double*, double, int, int, Ctl*, cudaStream_t);
+
 template <class TS>
 void launch_scale_cast(const double* r, const double* gam, TS* s, int nspace, int nt, cudaStream_t st) {
     size_t total = (size_t)nspace * nt;

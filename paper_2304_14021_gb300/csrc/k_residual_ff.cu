@@ -44,74 +44,108 @@ __device__ __forceinline__ ff ext_read_ff(const ff* __restrict__ u, int gx, int 
 __device__ __forceinline__ ff ff_d2(ff a, ff b, ff c) { return ff_add(ff_add(a, b), ff_scale2(c, -2.f)); }
 __device__ __forceinline__ ff ff_cube(ff x) { return ff_mul(ff_mul(x, x), x); }
 
+// CTA tile: TX x TY points, each thread owns PPT points (rows ty, ty + TY/PPT, ...).
 template <int DIM> struct ResTileFF;
-template <> struct ResTileFF<1> { static constexpr int TX = 256, TY = 1; };
-template <> struct ResTileFF<2> { static constexpr int TX = 32, TY = 8; };
+template <> struct ResTileFF<1> { static constexpr int TX = 512, TY = 1, PPT = 2; };
+template <> struct ResTileFF<2> { static constexpr int TX = 32, TY = 16, PPT = 2; };
 
-template <int DIM>
+// SQ (square cells, hx == hy, and every 1-D grid): the stencil sums are taken
+// unscaled (integer coefficients only) and the 1/h^2, 1/h^4 factors are folded
+// into the coefficients c1/h^2, c2/h^4, cN/h^2.  Otherwise each axis is scaled
+// by its own 1/h^2 before the sum.
+template <int DIM, bool SQ>
+__device__ __forceinline__ ff lap_ff(const ff* __restrict__ a, int c, int sx, const GeoFF& g) {
+    if constexpr (SQ) {
+        ff v = ff_add(a[c - 1], a[c + 1]);
+        if constexpr (DIM == 2) {
+            v = ff_add(v, a[c - sx]);
+            v = ff_add(v, a[c + sx]);
+        }
+        return ff_add(v, ff_scale2(a[c], DIM == 2 ? -4.f : -2.f));
+    } else {
+        ff v = ff_mul(ff_d2(a[c - 1], a[c + 1], a[c]), g.ihx2);
+        if constexpr (DIM == 2) v = ff_add(v, ff_mul(ff_d2(a[c - sx], a[c + sx], a[c]), g.ihy2));
+        return v;
+    }
+}
+
+template <int DIM, bool SQ>
 __global__ void __launch_bounds__(256) k_residual_ff(GeoFF g, const ff* __restrict__ U, const ff* __restrict__ u0,
                                                      const float* __restrict__ gamf, float* __restrict__ s_out,
                                                      double* __restrict__ partials, const Ctl* __restrict__ ctl,
                                                      int chunk) {
     if (ctl && ctl->status != ST_RUNNING) return;
-    constexpr int TX = ResTileFF<DIM>::TX, TY = ResTileFF<DIM>::TY;
+    constexpr int TX = ResTileFF<DIM>::TX, TY = ResTileFF<DIM>::TY, PPT = ResTileFF<DIM>::PPT;
+    constexpr int NTHR = TX * TY / PPT;
+    constexpr int RSTEP = DIM == 2 ? TY / PPT : 0;     // row offset between a thread's points (2-D)
+    constexpr int XSTEP = DIM == 2 ? 0 : TX / PPT;     // column offset (1-D)
     constexpr int HY = DIM == 2 ? 2 : 0;
     constexpr int SX = TX + 4, SY = TY + 2 * HY;
     constexpr int LX = TX + 2, LY = TY + (DIM == 2 ? 2 : 0);
     __shared__ ff su[SY * SX];
     __shared__ ff sL[LY * LX];
-    __shared__ double red[2][8];
+    __shared__ ff sW[LY * LX];   // u^3 (Cahn-Hilliard)
+    __shared__ double red[2][NTHR / 32];
 
-    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int tx = threadIdx.x % (DIM == 2 ? TX : TX / PPT), ty = threadIdx.x / (DIM == 2 ? TX : TX / PPT);
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int gx = x0 + tx, gy = y0 + ty;
-    const bool inside = gx < g.nx && (DIM == 1 || gy < g.ny);
-    const int pidx = (DIM == 2 ? gy * g.nx : 0) + gx;
     const int n0 = blockIdx.z * chunk;
     const int n1 = min(g.nt, n0 + chunk);
-    const bool ch = g.cN != 0.f;
+    const bool ch = g.cN.x != 0.f;
     const bool lin1 = g.c1.x != 0.f;
+    const bool interior = x0 >= 2 && x0 + TX + 2 <= g.nx && (DIM == 1 || (y0 >= 2 && y0 + TY + 2 <= g.ny));
 
-    ff uprev = ffmk(0.f, 0.f);
-    if (inside) uprev = n0 == 0 ? u0[pidx] : U[(size_t)(n0 - 1) * g.nspace + pidx];
+    int pidx[PPT], cu[PPT], cl[PPT];
+    bool inside[PPT];
+    ff uprev[PPT];
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        const int lx = tx + q * XSTEP, ly = ty + q * RSTEP;
+        const int gx = x0 + lx, gy = y0 + ly;
+        inside[q] = gx < g.nx && (DIM == 1 || gy < g.ny);
+        pidx[q] = (DIM == 2 ? gy * g.nx : 0) + gx;
+        cu[q] = (ly + HY) * SX + lx + 2;
+        cl[q] = (DIM == 2 ? (ly + 1) * LX : 0) + lx + 1;
+        uprev[q] = ffmk(0.f, 0.f);
+        if (inside[q]) uprev[q] = n0 == 0 ? u0[pidx[q]] : U[(size_t)(n0 - 1) * g.nspace + pidx[q]];
+    }
     float acc_r2 = 0.f, acc_u2 = 0.f;
 
     for (int n = n0; n < n1; ++n) {
         const ff* un = U + (size_t)n * g.nspace;
-        for (int e = threadIdx.x; e < SX * SY; e += TX * TY) {
-            int ix = e % SX, iy = e / SX;
-            su[e] = ext_read_ff(un, x0 - 2 + ix, y0 - HY + iy, g.nx, g.ny, DIM, g.bc);
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < LX * LY; e += TX * TY) {
-            int ix = e % LX, iy = e / LX;
-            const int c = (DIM == 2 ? (iy + 1) * SX : 0) + ix + 1;
-            ff v = ff_mul(ff_d2(su[c - 1], su[c + 1], su[c]), g.ihx2);
-            if (DIM == 2) v = ff_add(v, ff_mul(ff_d2(su[c - SX], su[c + SX], su[c]), g.ihy2));
-            sL[e] = v;
-        }
-        __syncthreads();
-        if (inside) {
-            const int cl = (DIM == 2 ? (ty + 1) * LX : 0) + tx + 1;
-            const int cu = (ty + HY) * SX + tx + 2;
-            const ff L = sL[cl];
-            ff L2 = ff_mul(ff_d2(sL[cl - 1], sL[cl + 1], L), g.ihx2);
-            if (DIM == 2) L2 = ff_add(L2, ff_mul(ff_d2(sL[cl - LX], sL[cl + LX], L), g.ihy2));
-            const ff u = su[cu];
-            ff A = ff_mul(L2, g.c2);
-            if (lin1) A = ff_add(A, ff_mul(L, g.c1));
-            if (ch) {  // cN = -1: A -= Lap(u^3)
-                const ff w0 = ff_cube(u);
-                ff lw = ff_mul(ff_d2(ff_cube(su[cu - 1]), ff_cube(su[cu + 1]), w0), g.ihx2);
-                if (DIM == 2) lw = ff_add(lw, ff_mul(ff_d2(ff_cube(su[cu - SX]), ff_cube(su[cu + SX]), w0), g.ihy2));
-                A = ff_sub(A, lw);
+        if (interior) {
+            for (int e = threadIdx.x; e < SX * SY; e += NTHR) {
+                const int ix = e % SX, iy = e / SX;
+                su[e] = un[(DIM == 2 ? (y0 - HY + iy) * g.nx : 0) + x0 - 2 + ix];
             }
-            const ff r = ff_sub(ff_mul(ff_sub(uprev, u), g.inv_dt), A);
+        } else {
+            for (int e = threadIdx.x; e < SX * SY; e += NTHR) {
+                const int ix = e % SX, iy = e / SX;
+                su[e] = ext_read_ff(un, x0 - 2 + ix, y0 - HY + iy, g.nx, g.ny, DIM, g.bc);
+            }
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < LX * LY; e += NTHR) {
+            const int ix = e % LX, iy = e / LX;
+            const int c = (DIM == 2 ? (iy + 1) * SX : 0) + ix + 1;
+            sL[e] = lap_ff<DIM, SQ>(su, c, SX, g);
+            if (ch) sW[e] = ff_cube(su[c]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+            if (!inside[q]) continue;
+            const ff L = sL[cl[q]];
+            const ff u = su[cu[q]];
+            ff A = ff_mul(lap_ff<DIM, SQ>(sL, cl[q], LX, g), g.c2);
+            if (lin1) A = ff_add(A, ff_mul(L, g.c1));
+            if (ch) A = ff_add(A, ff_mul(lap_ff<DIM, SQ>(sW, cl[q], LX, g), g.cN));
+            const ff r = ff_sub(ff_mul(ff_sub(uprev[q], u), g.inv_dt), A);
             const float gm = gamf[n];
-            s_out[(size_t)n * g.nspace + pidx] = fmaf(gm, r.x, gm * r.y);
+            s_out[(size_t)n * g.nspace + pidx[q]] = fmaf(gm, r.x, gm * r.y);
             acc_r2 = fmaf(r.x, r.x, acc_r2);
             acc_u2 = fmaf(u.x, u.x, acc_u2);
-            uprev = u;
+            uprev[q] = u;
         }
         __syncthreads();
     }
@@ -121,7 +155,7 @@ __global__ void __launch_bounds__(256) k_residual_ff(GeoFF g, const ff* __restri
     __syncthreads();
     if (threadIdx.x == 0) {
         double A = 0.0, B = 0.0;
-        for (int w = 0; w < (TX * TY) / 32; ++w) { A += red[0][w]; B += red[1][w]; }
+        for (int w = 0; w < NTHR / 32; ++w) { A += red[0][w]; B += red[1][w]; }
         size_t cta = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
         partials[2 * cta] = A;
         partials[2 * cta + 1] = B;
@@ -149,13 +183,31 @@ static int grid_for(size_t n) {
     return (int)(b > 4 * 152 * 8 ? 4 * 152 * 8 : (b < 1 ? 1 : b));
 }
 
+int residual_ff_grid(const Geo& g, int& gx, int& gy, int& gz, int& chunk) {
+    const int TX = g.dim == 2 ? ResTileFF<2>::TX : ResTileFF<1>::TX, TY = g.dim == 2 ? ResTileFF<2>::TY : 1;
+    gx = (g.nx + TX - 1) / TX;
+    gy = g.dim == 2 ? (g.ny + TY - 1) / TY : 1;
+    const long tiles = (long)gx * gy;
+    long want = (608 + tiles - 1) / tiles;
+    chunk = (int)((g.nt + want - 1) / want);
+    if (chunk < 4) chunk = 4;
+    if (chunk > g.nt) chunk = g.nt;
+    gz = (g.nt + chunk - 1) / chunk;
+    return gx * gy * gz;
+}
+
 void launch_residual_ff(const GeoFF& g, const Geo& g64, const ff* U, const ff* u0, const float* gamf, float* s,
                         double* partials, const Ctl* ctl, cudaStream_t st) {
     int gx, gy, gz, chunk;
-    residual_grid(g64, gx, gy, gz, chunk);
+    residual_ff_grid(g64, gx, gy, gz, chunk);
     dim3 grid(gx, gy, gz);
-    if (g.dim == 2) k_residual_ff<2><<<grid, 256, 0, st>>>(g, U, u0, gamf, s, partials, ctl, chunk);
-    else k_residual_ff<1><<<grid, 256, 0, st>>>(g, U, u0, gamf, s, partials, ctl, chunk);
+    const bool sq = g64.dim == 1 || g64.ihx2 == g64.ihy2;
+    if (g.dim == 2) {
+        if (sq) k_residual_ff<2, true><<<grid, 256, 0, st>>>(g, U, u0, gamf, s, partials, ctl, chunk);
+        else k_residual_ff<2, false><<<grid, 256, 0, st>>>(g, U, u0, gamf, s, partials, ctl, chunk);
+    } else {
+        k_residual_ff<1, true><<<grid, 256, 0, st>>>(g, U, u0, gamf, s, partials, ctl, chunk);
+    }
 }
 void launch_f64_to_ff(const double* in, ff* out, size_t n, cudaStream_t st) {
     k_f64_to_ff<<<grid_for(n), 256, 0, st>>>(in, out, n);

@@ -64,42 +64,46 @@ __device__ __forceinline__ void dct_pre(int p, C Xp, C Xq, C wp, C wq, C& Vp, C&
 template <class T, int N> struct RowCfg {
     static constexpr int ROWS = N >= 2048 ? 1 : 2048 / N;
     static constexpr int NTH = 256;
-    static constexpr size_t SMEM = sizeof(c_t<T>) * (size_t)ROWS * N;
+    static constexpr int PADSH = 0;                                // padding measured no better (bank conflicts rose)
+    static constexpr int RS = PADSH ? N + N / 8 : N;               // padded row stride
+    static constexpr size_t SMEM = sizeof(c_t<T>) * (size_t)ROWS * RS;
 };
 
 template <class T, int N, int MODE>
 __global__ void __launch_bounds__(256) k_rows_dct(int nrows, int ny, c_t<T>* __restrict__ S, Tabs<T> tb,
                                                   SolveCoef co, const Ctl* __restrict__ ctl) {
     using C = c_t<T>;
-    constexpr int ROWS = RowCfg<T, N>::ROWS, NTH = RowCfg<T, N>::NTH;
+    constexpr int ROWS = RowCfg<T, N>::ROWS, NTH = RowCfg<T, N>::NTH, PS = RowCfg<T, N>::PADSH;
+    constexpr int RS = RowCfg<T, N>::RS;
     if (ctl && ctl->status != ST_RUNNING) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
     const int tid = threadIdx.x;
     const long r0 = (long)blockIdx.x * ROWS;
+#pragma unroll 4
     for (int e = tid; e < ROWS * N; e += NTH) {
         const int b = e / N, i = e % N;
         const long gr = r0 + b;
         C x = gr < nrows ? S[gr * N + i] : mkc(T(0), T(0));
-        buf[b * N + (MODE == MODE_INV ? i : dct_pos(i, N))] = x;
+        buf[b * RS + padi<PS>(MODE == MODE_INV ? i : dct_pos(i, N))] = x;
     }
     __syncthreads();
-    if (MODE != MODE_INV) smem_fft<C, N, -1, NTH, ROWS, 1, N>(buf, tb.twx);
+    if (MODE != MODE_INV) smem_fft<C, N, -1, NTH, ROWS, 1, RS, PS>(buf, tb.twx);
     const T c2 = T(co.c2), c1 = solve_c1<T>(co, ctl);
     for (int e = tid; e < ROWS * (N / 2 + 1); e += NTH) {
         const int b = e / (N / 2 + 1), p = e % (N / 2 + 1), q = (N - p) % N;
-        C* row = buf + b * N;
+        C* row = buf + b * RS;
         const C wp = tb.wx[p], wq = tb.wx[q];
         C Xp, Xq;
         if (MODE == MODE_INV) {
-            Xp = row[p];
-            Xq = row[q];
+            Xp = row[padi<PS>(p)];
+            Xq = row[padi<PS>(q)];
         } else {
-            dct_post(row[p], row[q], wp, wq, Xp, Xq);
+            dct_post(row[padi<PS>(p)], row[padi<PS>(q)], wp, wq, Xp, Xq);
         }
         if (MODE == MODE_FWD) {
-            row[p] = Xp;
-            row[q] = Xq;
+            row[padi<PS>(p)] = Xp;
+            row[padi<PS>(q)] = Xq;
             continue;
         }
         if (MODE == MODE_FDI) {
@@ -111,23 +115,26 @@ __global__ void __launch_bounds__(256) k_rows_dct(int nrows, int ny, c_t<T>* __r
         }
         C Vp, Vq;
         dct_pre(p, Xp, Xq, wp, wq, Vp, Vq);
-        row[p] = Vp;
-        row[q] = Vq;
+        row[padi<PS>(p)] = Vp;
+        row[padi<PS>(q)] = Vq;
     }
     __syncthreads();
     if (MODE == MODE_FWD) {
+#pragma unroll 4
         for (int e = tid; e < ROWS * N; e += NTH) {
-            const long gr = r0 + e / N;
-            if (gr < nrows) S[gr * N + e % N] = buf[e];
+            const int b = e / N, i = e % N;
+            const long gr = r0 + b;
+            if (gr < nrows) S[gr * N + i] = buf[b * RS + padi<PS>(i)];
         }
         return;
     }
-    smem_fft<C, N, +1, NTH, ROWS, 1, N>(buf, tb.twx);
+    smem_fft<C, N, +1, NTH, ROWS, 1, RS, PS>(buf, tb.twx);
     const T inv = T(1) / T(N);
+#pragma unroll 4
     for (int e = tid; e < ROWS * N; e += NTH) {
         const int b = e / N, i = e % N;
         const long gr = r0 + b;
-        if (gr < nrows) S[gr * N + i] = scalec(buf[b * N + dct_pos(i, N)], inv);
+        if (gr < nrows) S[gr * N + i] = scalec(buf[b * RS + padi<PS>(dct_pos(i, N))], inv);
     }
 }
 
@@ -136,8 +143,11 @@ __global__ void __launch_bounds__(256) k_rows_dct(int nrows, int ny, c_t<T>* __r
 // frequency k and CW consecutive x columns; buf[y][c].
 // ---------------------------------------------------------------------------
 template <class T, int N> struct ColCfg {
-    static constexpr int CW = sizeof(T) == 4 ? (N <= 512 ? 32 : 16) : (N <= 256 ? 32 : (N == 512 ? 16 : 8));
-    static constexpr int NTH = N <= 256 ? 256 : 512;
+    // 16 complex columns = 128 B (FP32) / 256 B (FP64) per row: coalesced, and
+    // small enough for several CTAs per SM.
+    static constexpr int CW = sizeof(T) == 4 ? (N <= 512 ? 16 : 8) : (N <= 256 ? 16 : 8);
+    // enough threads that each holds at most two radix-8 butterflies across a barrier
+    static constexpr int NTH = N * CW >= 8192 ? 1024 : (N * CW >= 2048 ? 512 : 256);
     static constexpr size_t SMEM = sizeof(c_t<T>) * (size_t)N * CW;
 };
 

@@ -19,7 +19,8 @@ namespace pint {
 
 template <class T, int NT> struct TimeCfg {
     static constexpr int CW = sizeof(T) == 4 ? (NT <= 512 ? 32 : 16) : (NT <= 256 ? 32 : (NT == 512 ? 16 : 8));
-    static constexpr int NTH = NT <= 256 ? 256 : 512;
+    // enough threads that each holds at most two radix-8 butterflies across a barrier
+    static constexpr int NTH = NT * CW >= 8192 ? 1024 : (NT * CW >= 2048 ? 512 : 256);
     static constexpr size_t SMEM = sizeof(c_t<T>) * ((size_t)NT * CW + NT);
 };
 
@@ -36,6 +37,7 @@ __global__ void __launch_bounds__(TimeCfg<T, NT>::NTH)
     const int tid = threadIdx.x;
     const long p0 = (long)blockIdx.x * 2 * CW;
     for (int i = tid; i < NT; i += NTH) tw[i] = twt[i];
+#pragma unroll 8
     for (int e = tid; e < NT * CW; e += NTH) {
         const int c = e % CW, n = e / CW;
         const long pa = p0 + c, pb = p0 + CW + c;
@@ -47,6 +49,7 @@ __global__ void __launch_bounds__(TimeCfg<T, NT>::NTH)
     __syncthreads();
     smem_fft<C, NT, -1, NTH, CW, CW, 1>(z, tw);
     const T half = T(0.5);
+#pragma unroll 4
     for (int e = tid; e < (NT / 2 + 1) * CW; e += NTH) {
         const int c = e % CW, k = e / CW;
         const C zk = z[k * CW + c];
@@ -74,6 +77,7 @@ __global__ void __launch_bounds__(TimeCfg<T, NT>::NTH)
     const int tid = threadIdx.x;
     const long p0 = (long)blockIdx.x * 2 * CW;
     for (int i = tid; i < NT; i += NTH) tw[i] = twt[i];
+#pragma unroll 4
     for (int e = tid; e < (NT / 2 + 1) * CW; e += NTH) {
         const int c = e % CW, k = e / CW;
         const long pa = p0 + c, pb = p0 + CW + c;
@@ -86,6 +90,7 @@ __global__ void __launch_bounds__(TimeCfg<T, NT>::NTH)
     }
     __syncthreads();
     smem_fft<C, NT, +1, NTH, CW, CW, 1>(z, tw);
+#pragma unroll 4
     for (int e = tid; e < NT * CW; e += NTH) {
         const int c = e % CW, n = e / CW;
         const C v = z[e];

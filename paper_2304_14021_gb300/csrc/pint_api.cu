@@ -120,6 +120,18 @@ struct pint_handle {
     cudaEvent_t ev[2 * NEV] = {};
     int ev_phase[NEV] = {0};
     int nev = 0;
+    // CUDA-graph execution of the iteration loop (one while-loop graph per window)
+    int use_graphs = 1;
+    int capturing = 0;                       // set while the loop body is being captured
+    unsigned long long gcond = 0;            // cudaGraphConditionalHandle of the graph being captured
+    cudaStream_t capst = nullptr;            // capture stream
+    struct GraphSlot {
+        cudaGraphExec_t exec = nullptr;
+        const void* U = nullptr;
+        const void* u0 = nullptr;
+        unsigned long long cond = 0;
+    } gslot[2];
+    int gnext = 0;
 };
 
 namespace pint {
@@ -279,9 +291,11 @@ static void derive(const pint_problem* p, pint_handle* h) {
     f.ihx2 = ff_from_double(g.ihx2);
     f.ihy2 = ff_from_double(g.ihy2);
     f.inv_dt = ff_from_double(g.inv_dt);
-    f.c2 = ff_from_double(g.c2);
-    f.c1 = ff_from_double(g.c1);
-    f.cN = (float)g.cN;
+    const bool sq = g.dim == 1 || g.ihx2 == g.ihy2;   // must match launch_residual_ff
+    const double s2 = sq ? g.ihx2 * g.ihx2 : 1.0, s1 = sq ? g.ihx2 : 1.0;
+    f.c2 = ff_from_double(g.c2 * s2);
+    f.c1 = ff_from_double(g.c1 * s1);
+    f.cN = ff_from_double(g.cN * s1);
 }
 
 static Sizes sizes_of(const pint_problem* p, pint_handle* tmp) {
@@ -361,33 +375,7 @@ template <class T> struct Impl {
         }
         return cudaSuccess;
     }
-    // PINT_MIXED_FF: float-float residual and update, FP32 transforms.
-static cudaError_t iteration_ff(pint_handle* h) {
-    const Geo& g = h->geo;
-    float* s = reinterpret_cast<float*>(h->s);
-    float2* S = reinterpret_cast<float2*>(h->S);
-    const Tabs<float>& tb = tabs_of<float>(h);
-    prof_begin(h, PH_RES);
-    launch_residual_ff(h->gff, g, h->Uff, h->u0ff, h->gamf, s, h->partials, h->ctl, h->st);
-    prof_end(h, PH_RES, 1);
-    int gx, gy, gz, chunk;
-    const int np = residual_grid(g, gx, gy, gz, chunk);
-    prof_begin(h, PH_CHECK);
-    launch_after_residual(h->partials, np, 1.0 / ((double)g.nt * g.nspace), h->ctl, h->st);
-    prof_end(h, PH_CHECK, 1);
-    prof_begin(h, PH_TFWD);
-    cudaError_t e = launch_time_fwd<float>(g.nt, g.nspace, s, S, tb.twt, h->ctl, h->st);
-    prof_end(h, PH_TFWD, 1);
-    if (e != cudaSuccess) return e;
-    if ((e = Impl<float>::spatial(h, S, tb)) != cudaSuccess) return e;
-    prof_begin(h, PH_TINV);
-    e = launch_time_inv_ff(g.nt, g.nspace, S, tb.twt, h->ginvf, h->Uff, h->ctl, h->st);
-    prof_end(h, PH_TINV, 1);
-    if (e != cudaSuccess) return e;
-    return cudaGetLastError();
-}
-
-static cudaError_t iteration(pint_handle* h, double* U, const double* u0w) {
+    static cudaError_t iteration(pint_handle* h, double* U, const double* u0w) {
         const Geo& g = h->geo;
         T* s = reinterpret_cast<T*>(h->s);
         c_t<T>* S = reinterpret_cast<c_t<T>*>(h->S);
@@ -398,7 +386,7 @@ static cudaError_t iteration(pint_handle* h, double* U, const double* u0w) {
         int gx, gy, gz, chunk;
         const int np = residual_grid(g, gx, gy, gz, chunk);
         prof_begin(h, PH_CHECK);
-        launch_after_residual(h->partials, np, 1.0 / ((double)g.nt * g.nspace), h->ctl, h->st);
+        launch_after_residual(h->partials, np, 1.0 / ((double)g.nt * g.nspace), h->ctl, h->st, h->gcond, h->capturing);
         prof_end(h, PH_CHECK, 1);
         prof_begin(h, PH_TFWD);
         cudaError_t e = launch_time_fwd<T>(g.nt, g.nspace, s, S, tb.twt, h->ctl, h->st);
@@ -427,6 +415,36 @@ static cudaError_t iteration(pint_handle* h, double* U, const double* u0w) {
     }
 };
 
+// Iteration k = 0 from the zero iterate: r_0 = b is known, so the residual
+// and the forward time transform are replaced by writing the spectrum of b.
+static cudaError_t zero_start(pint_handle* h, double* U, const double* u0w) {
+    const Geo& g = h->geo;
+    const int nk = g.nt / 2 + 1;
+    prof_begin(h, PH_TFWD);
+    if (f32_transforms(&h->p)) launch_zero_start<float>(reinterpret_cast<float2*>(h->S), u0w, g.inv_dt, g.nspace, nk, h->ctl, h->st);
+    else launch_zero_start<double>(reinterpret_cast<double2*>(h->S), u0w, g.inv_dt, g.nspace, nk, h->ctl, h->st);
+    prof_end(h, PH_TFWD, 1);
+    cudaError_t e;
+    if (f32_transforms(&h->p)) {
+        const Tabs<float>& tb = tabs_of<float>(h);
+        if ((e = Impl<float>::spatial(h, reinterpret_cast<float2*>(h->S), tb)) != cudaSuccess) return e;
+        prof_begin(h, PH_TINV);
+        if (h->p.precision == PINT_MIXED_FF)
+            e = launch_time_inv_ff(g.nt, g.nspace, reinterpret_cast<float2*>(h->S), tb.twt, h->ginvf, h->Uff, h->ctl, h->st);
+        else
+            e = launch_time_inv<float>(g.nt, g.nspace, reinterpret_cast<float2*>(h->S), tb.twt, h->ginv, U, 1, h->ctl, h->st);
+        prof_end(h, PH_TINV, 1);
+    } else {
+        const Tabs<double>& tb = tabs_of<double>(h);
+        if ((e = Impl<double>::spatial(h, reinterpret_cast<double2*>(h->S), tb)) != cudaSuccess) return e;
+        prof_begin(h, PH_TINV);
+        e = launch_time_inv<double>(g.nt, g.nspace, reinterpret_cast<double2*>(h->S), tb.twt, h->ginv, U, 1, h->ctl, h->st);
+        prof_end(h, PH_TINV, 1);
+    }
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
 // PINT_MIXED_FF: float-float residual and update, FP32 transforms.
 static cudaError_t iteration_ff(pint_handle* h) {
     const Geo& g = h->geo;
@@ -437,9 +455,9 @@ static cudaError_t iteration_ff(pint_handle* h) {
     launch_residual_ff(h->gff, g, h->Uff, h->u0ff, h->gamf, s, h->partials, h->ctl, h->st);
     prof_end(h, PH_RES, 1);
     int gx, gy, gz, chunk;
-    const int np = residual_grid(g, gx, gy, gz, chunk);
+    const int np = residual_ff_grid(g, gx, gy, gz, chunk);
     prof_begin(h, PH_CHECK);
-    launch_after_residual(h->partials, np, 1.0 / ((double)g.nt * g.nspace), h->ctl, h->st);
+    launch_after_residual(h->partials, np, 1.0 / ((double)g.nt * g.nspace), h->ctl, h->st, h->gcond, h->capturing);
     prof_end(h, PH_CHECK, 1);
     prof_begin(h, PH_TFWD);
     cudaError_t e = launch_time_fwd<float>(g.nt, g.nspace, s, S, tb.twt, h->ctl, h->st);
@@ -455,6 +473,74 @@ static cudaError_t iteration_ff(pint_handle* h) {
 
 static cudaError_t iteration(pint_handle* h, double* U, const double* u0w) {
     return f32_transforms(&h->p) ? Impl<float>::iteration(h, U, u0w) : Impl<double>::iteration(h, U, u0w);
+}
+
+// Kernels per loop body (for launch accounting in graph mode).
+static int body_launches(const pint_handle* h) { return 5 + (h->geo.dim == 2 ? 2 : 0); }
+
+// The iteration loop of one window as a CUDA graph: a while-node whose body is
+// one iteration (residual, check, time FFT, spatial stages, inverse FFT); the
+// check kernel sets the loop condition from the device status word, so the
+// whole solve of a window is one graph launch with no host round trip.  The
+// body of PINT_MIXED_FF touches handle-owned buffers only; the other modes
+// also bake U and the window's u0 in, so graphs are cached per (U, u0).
+static cudaGraphExec_t get_graph(pint_handle* h, double* U, const double* u0w) {
+    const bool ffm = h->p.precision == PINT_MIXED_FF;
+    const void* kU = ffm ? nullptr : U;
+    const void* ku0 = ffm ? nullptr : u0w;
+    for (auto& sl : h->gslot)
+        if (sl.exec && sl.U == kU && sl.u0 == ku0) return sl.exec;
+    if (!h->capst && cudaStreamCreateWithFlags(&h->capst, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle cond;
+    if (cudaGraphCreate(&graph, 0) != cudaSuccess) return nullptr;
+    bool ok = cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    ok = ok && cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp) == cudaSuccess;
+    if (ok) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        cudaStream_t saved = h->st;
+        const int prof = h->prof_on;
+        h->st = h->capst;
+        h->prof_on = 0;
+        h->capturing = 1;
+        h->gcond = (unsigned long long)cond;
+        long long saved_launches[PINT_NPHASE];
+        memcpy(saved_launches, h->launches, sizeof(saved_launches));
+        ok = cudaStreamBeginCaptureToGraph(h->capst, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+             cudaSuccess;
+        if (ok) {
+            cudaError_t e = ffm ? iteration_ff(h) : iteration(h, U, u0w);
+            cudaGraph_t outg = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(h->capst, &outg);
+            ok = e == cudaSuccess && e2 == cudaSuccess;
+        }
+        memcpy(h->launches, saved_launches, sizeof(saved_launches));
+        h->st = saved;
+        h->prof_on = prof;
+        h->capturing = 0;
+        h->gcond = 0;
+    }
+    ok = ok && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    cudaGraphDestroy(graph);
+    if (!ok) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    auto& sl = h->gslot[h->gnext];
+    h->gnext ^= 1;
+    if (sl.exec) cudaGraphExecDestroy(sl.exec);
+    sl.exec = exec;
+    sl.U = kU;
+    sl.u0 = ku0;
+    sl.cond = (unsigned long long)cond;
+    return exec;
 }
 
 }  // namespace pint
@@ -505,6 +591,9 @@ void pint_destroy(pint_handle* h) {
     cudaFree(h->ginvf);
     for (int i = 0; i < 2 * pint_handle::NEV; ++i)
         if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+    for (auto& sl : h->gslot)
+        if (sl.exec) cudaGraphExecDestroy(sl.exec);
+    if (h->capst) cudaStreamDestroy(h->capst);
     if (h->tabs_ptrs) {
         if (f32_transforms(&h->p)) delete reinterpret_cast<Tabs<float>*>(h->tabs_ptrs);
         else delete reinterpret_cast<Tabs<double>*>(h->tabs_ptrs);
@@ -578,6 +667,17 @@ int pint_profile_enable(pint_handle* h, int on) {
     return PINT_OK;
 }
 
+int pint_set_option(pint_handle* h, int option, long long value) {
+    if (!h) return PINT_EINVAL;
+    switch (option) {
+        case PINT_OPT_GRAPHS:
+            if (value != 0 && value != 1) return PINT_EINVAL;
+            h->use_graphs = (int)value;
+            return PINT_OK;
+        default: return PINT_EINVAL;
+    }
+}
+
 int pint_profile_read(pint_handle* h, pint_profile* out, int reset) {
     if (!h || !out) return PINT_EINVAL;
     PINT_CK(cudaStreamSynchronize(h->st));
@@ -615,17 +715,33 @@ int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* 
         }
         launch_begin_window(u0w, g.nspace, g.inv_dt, p.max_iter, p.tol, h->partials, h->ctl, h->st);
         prof_end(h, PH_SETUP, nl);
-        int enqueued = 0;
-        for (;;) {
-            int chunk = enqueued == 0 ? 3 : 2;
-            for (int c = 0; c < chunk; ++c) {
-                cudaError_t e = ffm ? iteration_ff(h) : iteration(h, U_dev, u0w);
-                if (e != cudaSuccess) return PINT_ECUDA;
-            }
-            enqueued += chunk;
+        cudaGraphExec_t gx = (h->use_graphs && !h->prof_on) ? get_graph(h, U_dev, u0w) : nullptr;
+        if (gx) {
+            // one graph launch runs the iteration loop of this window to its stop
+            if (p.init_guess == 2 && zero_start(h, U_dev, u0w) != cudaSuccess) return PINT_ECUDA;
+            PINT_CK(cudaGraphLaunch(gx, h->st));
             if ((rc = read_ctl(h)) != PINT_OK) return rc;
-            if (h->hctl->status != ST_RUNNING) break;
-            if (enqueued > p.max_iter + 8) return PINT_ECUDA;  // the device loop must have stopped by now
+            if (h->hctl->status == ST_RUNNING) return PINT_ECUDA;  // the loop ends only on a final status
+            const long long runs = h->hctl->iter + 1 - (p.init_guess == 2 ? 1 : 0);
+            h->launches[PH_RES] += runs;
+            h->launches[PH_CHECK] += runs;
+            h->launches[PH_TFWD] += runs;
+            for (int stg = 0; stg < (g.dim == 2 ? 3 : 1); ++stg) h->launches[PH_SP0 + stg] += runs;
+            h->launches[PH_TINV] += runs;
+        } else {
+            int enqueued = 0;
+            for (;;) {
+                int chunk = enqueued == 0 ? 3 : 2;
+                for (int c = 0; c < chunk; ++c) {
+                    cudaError_t e = enqueued == 0 && c == 0 && p.init_guess == 2 ? zero_start(h, U_dev, u0w)
+                                    : ffm ? iteration_ff(h) : iteration(h, U_dev, u0w);
+                    if (e != cudaSuccess) return PINT_ECUDA;
+                }
+                enqueued += chunk;
+                if ((rc = read_ctl(h)) != PINT_OK) return rc;
+                if (h->hctl->status != ST_RUNNING) break;
+                if (enqueued > p.max_iter + 8) return PINT_ECUDA;  // the device loop must have stopped by now
+            }
         }
         const Ctl& c = *h->hctl;
         const int k = c.iter;

@@ -104,7 +104,12 @@ constexpr int next_radix(int M) { return (M >= 3 && M != 4) ? 8 : (M == 4 || M =
 // column layouts (ESTR > 1) the batch index is fastest, for rows the
 // butterfly index.
 // ---------------------------------------------------------------------------
-template <class C, int N, int R, int NS, int DIR, int NTH, int B, int ESTR, int SSTR>
+// PADSH > 0 inserts one padding element after every 2^PADSH elements of a
+// sequence (index i is stored at i + (i >> PADSH)), which breaks the stride-R
+// shared-memory bank conflicts of the early passes on contiguous rows.
+template <int PADSH> __device__ __forceinline__ int padi(int i) { return PADSH > 0 ? i + (i >> PADSH) : i; }
+
+template <class C, int N, int R, int NS, int DIR, int NTH, int B, int ESTR, int SSTR, int PADSH = 0>
 __device__ __forceinline__ void stockham_pass(C* buf, const C* __restrict__ tw) {
     constexpr int NB = N / R;              // butterflies per sequence
     constexpr int NTASK = NB * B;
@@ -120,7 +125,7 @@ __device__ __forceinline__ void stockham_pass(C* buf, const C* __restrict__ tw) 
             int j = COL ? t / B : t % NB;
             const C* src = buf + b * SSTR;
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[q][r] = src[(j + r * NB) * ESTR];
+            for (int r = 0; r < R; ++r) v[q][r] = src[padi<PADSH>(j + r * NB) * ESTR];
         }
     }
     __syncthreads();
@@ -143,27 +148,27 @@ __device__ __forceinline__ void stockham_pass(C* buf, const C* __restrict__ tw) 
             C* dst = buf + b * SSTR;
             int base = (j / NS) * NS * R + (j % NS);
 #pragma unroll
-            for (int r = 0; r < R; ++r) dst[(base + r * NS) * ESTR] = v[q][r];
+            for (int r = 0; r < R; ++r) dst[padi<PADSH>(base + r * NS) * ESTR] = v[q][r];
         }
     }
     __syncthreads();
 }
 
-template <class C, int N, int NS, int M, int DIR, int NTH, int B, int ESTR, int SSTR>
+template <class C, int N, int NS, int M, int DIR, int NTH, int B, int ESTR, int SSTR, int PADSH>
 __device__ __forceinline__ void fft_passes(C* buf, const C* __restrict__ tw) {
     if constexpr (M > 0) {
         constexpr int R = next_radix(M);
-        stockham_pass<C, N, R, NS, DIR, NTH, B, ESTR, SSTR>(buf, tw);
-        fft_passes<C, N, NS * R, M - ilog2(R), DIR, NTH, B, ESTR, SSTR>(buf, tw);
+        stockham_pass<C, N, R, NS, DIR, NTH, B, ESTR, SSTR, PADSH>(buf, tw);
+        fft_passes<C, N, NS * R, M - ilog2(R), DIR, NTH, B, ESTR, SSTR, PADSH>(buf, tw);
     }
 }
 
 // In-place length-N FFT (N a power of two) of B sequences in shared memory.
 // The caller must __syncthreads() before (data ready); the last pass ends
 // with a barrier.
-template <class C, int N, int DIR, int NTH, int B, int ESTR, int SSTR>
+template <class C, int N, int DIR, int NTH, int B, int ESTR, int SSTR, int PADSH = 0>
 __device__ __forceinline__ void smem_fft(C* buf, const C* __restrict__ tw) {
-    fft_passes<C, N, 1, ilog2(N), DIR, NTH, B, ESTR, SSTR>(buf, tw);
+    fft_passes<C, N, 1, ilog2(N), DIR, NTH, B, ESTR, SSTR, PADSH>(buf, tw);
 }
 
 // ---------------------------------------------------------------------------

@@ -31,14 +31,16 @@ struct SolveCoef {
     int ch;
 };
 
-// Float-float form of Geo for the PINT_MIXED_FF residual (constants as hi + lo pairs).
+// Float-float form of Geo for the PINT_MIXED_FF residual (constants as hi + lo
+// pairs).  On square cells (and in 1-D) the stencil sums are unscaled and
+// c2, c1, cN already carry the factors 1/h^4, 1/h^2, 1/h^2.
 struct GeoFF {
     int nx, ny, dim, bc, nt, nspace;
-    float2 ihx2, ihy2, inv_dt, c2, c1;
-    float cN;
+    float2 ihx2, ihy2, inv_dt, c2, c1, cN;
 };
 
 int residual_grid(const Geo& g, int& gx, int& gy, int& gz, int& chunk);
+int residual_ff_grid(const Geo& g, int& gx, int& gy, int& gz, int& chunk);
 void launch_residual_ff(const GeoFF& g, const Geo& g64, const float2* U, const float2* u0, const float* gamf,
                         float* s, double* partials, const Ctl* ctl, cudaStream_t st);
 void launch_f64_to_ff(const double* in, float2* out, size_t n, cudaStream_t st);
@@ -52,7 +54,9 @@ void launch_residual(const Geo& g, const double* U, const double* u0, const doub
 int norm2_blocks(int n);
 void launch_begin_window(const double* u0, int nspace, double inv_dt, int max_iter, double tol, double* partials,
                          Ctl* ctl, cudaStream_t st);
-void launch_after_residual(const double* partials, int np, double inv_dof, Ctl* ctl, cudaStream_t st);
+// cond / use_cond: CUDA-graph while-loop condition handle (see pint_api.cu).
+void launch_after_residual(const double* partials, int np, double inv_dof, Ctl* ctl, cudaStream_t st,
+                           unsigned long long cond = 0, int use_cond = 0);
 void launch_residual_norm(const double* partials, int np, Ctl* ctl, cudaStream_t st);
 void launch_set_running(Ctl* ctl, double jbar, cudaStream_t st);
 void launch_broadcast(double* U, const double* u0, int nspace, int nt, cudaStream_t st);
@@ -74,6 +78,12 @@ cudaError_t launch_time_inv(int nt, int nspace, const c_t<T>* S, const c_t<T>* t
 template <class T>
 cudaError_t launch_spatial_stage(int stage, const Geo& g, c_t<T>* S, const Tabs<T>& tb, SolveCoef co, int fft_x,
                                  int fft_y, const Ctl* ctl, cudaStream_t st);
+
+// First iteration from the zero iterate: r = b = (u0/dt, 0, ..., 0), so the
+// alpha-scaled time transform is u0/dt at every frequency.  Writes S and
+// records rho_0 = 1 in ctl (or stops if tol >= 1).
+template <class T>
+void launch_zero_start(c_t<T>* S, const double* u0, double inv_dt, int nspace, int nk, Ctl* ctl, cudaStream_t st);
 
 // Opt-in shared memory sizes for the kernels that need more than 48 KB.
 cudaError_t configure_kernels();

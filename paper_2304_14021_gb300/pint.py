@@ -84,6 +84,8 @@ def lib() -> C.CDLL:
         L.pint_profile_enable.restype = C.c_int
         L.pint_profile_read.argtypes = [vp, C.POINTER(Profile), C.c_int]
         L.pint_profile_read.restype = C.c_int
+        L.pint_set_option.argtypes = [vp, C.c_int, C.c_longlong]
+        L.pint_set_option.restype = C.c_int
         L.pint_destroy.argtypes = [vp]
         L.pint_destroy.restype = None
         L.pint_strerror.argtypes = [C.c_int]
@@ -179,6 +181,11 @@ class Solver:
         rc = lib().pint_precond_apply(self._h, C.c_double(jbar), C.c_void_p(_ptr(r)), C.c_void_p(_ptr(delta)))
         if rc != PINT_OK:
             raise PintError(rc, "pint_precond_apply")
+
+    def set_graphs(self, on: bool = True) -> None:
+        rc = lib().pint_set_option(self._h, 1, 1 if on else 0)
+        if rc != PINT_OK:
+            raise PintError(rc, "pint_set_option")
 
     def profile_enable(self, on: bool = True) -> None:
         rc = lib().pint_profile_enable(self._h, 1 if on else 0)

@@ -246,3 +246,25 @@ def test_time_axis_extremes(nt, precision):
     U, st = run_solve(kw, u0)
     assert st["rc"] == 0
     assert O.rel_err(U, O.sequential(p, u0)) < (1e-10 if precision == "fp64" else 1e-8)
+
+
+@pytest.mark.parametrize("precision,init", [("mixed_ff", 2), ("mixed_ff", 0), ("fp64", 2), ("mixed", 0)])
+def test_graph_loop_equals_host_loop(precision, init):
+    # The CUDA-graph while-loop runs the same kernels in the same order as the
+    # host-launched loop: results and statistics are identical, bit for bit.
+    kw = full(dict(equation="linear_ch", dim=2, nx=32, ny=32, bc="neumann", eps=0.05, beta=0.5, nt=16,
+                   T=0.0125, precision=precision, tol=1e-10, init_guess=init, n_windows=2))
+    p = oprob(kw)
+    u0 = synth.u0_uniform(p.nspace, -0.05, 0.05, 6)
+    out = []
+    for graphs in (True, False, True):
+        with pint.Solver(**kw) as s:
+            s.set_graphs(graphs)
+            U = torch.zeros(p.nt, p.nspace, dtype=torch.float64, device="cuda")
+            st = s.solve(dev(u0), U)
+            st2 = s.solve(dev(u0), U)          # second solve reuses the cached graph
+            out.append((host(U), st, st2))
+    (Ua, sa, sa2), (Ub, sb, _), (Uc, _, _) = out
+    assert np.array_equal(Ua, Ub) and np.array_equal(Ua, Uc)
+    assert sa["iters"] == sb["iters"] == sa2["iters"] and sa["hist"] == sb["hist"]
+    assert O.rel_err(Ua, O.sequential(p, u0)[-p.nt:]) < (1e-10 if precision == "fp64" else 1e-8)
