@@ -36,6 +36,13 @@ WORKLOADS = {
     # The same equation on a 512x512 grid (inputs larger than L2; used for kernel profiles).
     "linear_ch_2d_512x512_nt128": dict(equation="linear_ch", dim=2, nx=512, ny=512, bc="neumann", eps=0.05,
                                        beta=0.5, T=0.1, nt=128, n_windows=1, u0="uniform0.05"),
+    # 2-D Cahn-Hilliard, Neumann, cell-centred 512x512, eps = 0.02, dt = 1e-4, 8 windows of 256 steps,
+    # u0 = 0.1 uniform[-1,1] minus its mean (adaptive window policy on).
+    "cahn_hilliard_2d_512x512_8x256": dict(equation="cahn_hilliard", dim=2, nx=512, ny=512, bc="neumann", eps=0.02,
+                                           beta=0.0, T=2048 * 1e-4, nt=256, n_windows=8, u0="ch"),
+    # The same at 128x128 (a size the CPU oracle finishes).
+    "cahn_hilliard_2d_128x128_8x256": dict(equation="cahn_hilliard", dim=2, nx=128, ny=128, bc="neumann", eps=0.02,
+                                           beta=0.0, T=2048 * 1e-4, nt=256, n_windows=8, u0="ch"),
     # 1-D biharmonic, simply supported, 64 vertices, N_t = 32, T = 0.01, u0 = sin(pi x) + 0.5 sin(3 pi x)
     "biharmonic_1d_64_nt32": dict(equation="biharmonic", dim=1, nx=64, ny=1, bc="ss", eps=1.0, beta=0.0,
                                   T=0.01, nt=32, n_windows=1, u0="sines"),
@@ -56,7 +63,7 @@ def make_u0(wl: dict, seed: int):
 
 def solver_kw(wl: dict, args, precision=None) -> dict:
     kw = {k: v for k, v in wl.items() if k != "u0"}
-    kw.update(alpha=args.alpha, tol=args.tol, max_iter=200, precision=precision or args.precision,
+    kw.update(alpha=args.alpha, tol=args.tol, max_iter=250, precision=precision or args.precision,
               init_guess=args.init)
     return kw
 
@@ -234,6 +241,8 @@ def main_gpu(args) -> None:
     u0_np = make_u0(wl, args.seed + rank)          # each replica solves its own instance
     stream = torch.cuda.current_stream()
     s = pint.Solver(stream=stream, **kw)
+    if wl["equation"] == "cahn_hilliard":
+        s.set_adaptive_windows(True)
     nt, ns = s.nt, s.nspace
     dof = nt * ns
     u0 = torch.from_numpy(u0_np).cuda()

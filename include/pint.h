@@ -100,6 +100,8 @@ typedef struct {
     double contraction;       /* geometric mean of rho_k / rho_{k-1} over the last window */
     double jbar;              /* last averaged Jacobian mean(3u^2) (Cahn-Hilliard), else 0 */
     double hist[PINT_HIST_MAX];  /* rho_0 .. rho_{iters_last} of the last window */
+    int    segments;          /* solves run (one per window, more under the adaptive window policy) */
+    int    nt_min;            /* shortest segment length used */
 } pint_stats;
 
 typedef struct pint_handle pint_handle;
@@ -170,6 +172,16 @@ int pint_profile_read(pint_handle* h, pint_profile* out, int reset);
  *    enabled (pint_profile_enable) the host-launched path is used.
  * Errors: PINT_EINVAL for an unknown option or value. */
 #define PINT_OPT_GRAPHS 1
+/*  PINT_OPT_ADAPTIVE_WINDOWS (default 0): split each window of nt steps into
+ *    power-of-two segments (>= 16 steps) chosen before each segment so that
+ *    alpha * max_p R_p^L <= 0.1, where R_p = 1/(1 + dt mu_p) and mu_p is the
+ *    spectrum of the spatial operator linearized about the segment's initial
+ *    data (for Cahn-Hilliard: eps^2 Lam^2 + (1 - mean 3u0^2) Lam).  Growing modes
+ *    (spinodal decomposition) make alpha R^L approach 1, where the iteration's
+ *    per-mode factor |alpha R^L/(1 - alpha R^L)| (Eq. 2.18) exceeds one; shorter
+ *    segments keep it small.  Enabling it builds the tables of the shorter
+ *    lengths (allocates device memory); it runs the host-launched loop. */
+#define PINT_OPT_ADAPTIVE_WINDOWS 2
 int pint_set_option(pint_handle* h, int option, long long value);
 
 /* Free everything the handle owns (NULL is allowed). */

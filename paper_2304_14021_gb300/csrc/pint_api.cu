@@ -106,6 +106,7 @@ struct pint_handle {
     void* tab = nullptr;            // tables block
     // PINT_MIXED_FF: float-float iterate and its tables
     float2* Uff = nullptr;          // nt*nspace
+    float2* Uff_cur = nullptr;      // first time level of the current segment within Uff
     float2* u0ff = nullptr;         // nspace
     float* gamf = nullptr;          // alpha^{n/nt} (FP32)
     float* ginvf = nullptr;         // alpha^{-n/nt}/nt (FP32)
@@ -132,6 +133,19 @@ struct pint_handle {
         unsigned long long cond = 0;
     } gslot[2];
     int gnext = 0;
+    // time-axis levels (segment lengths nt, nt/2, ...) for the adaptive window policy
+    struct Level {
+        int nt = 0;
+        void* tabs = nullptr;        // Tabs<T>* with twt, lam1, lam2 of this length
+        double* gam = nullptr;
+        double* ginv = nullptr;
+        float* gamf = nullptr;
+        float* ginvf = nullptr;
+        void* block = nullptr;       // device block owning this level's tables (levels >= 1)
+    } lev[11];
+    int nlev = 0;
+    int adaptive = 0;
+    std::vector<double> lamx_h, lamy_h;   // host copies of the Laplacian eigenvalues
 };
 
 namespace pint {
@@ -256,6 +270,80 @@ static int build_tables(pint_handle* h) {
             return PINT_ECUDA;
     }
     return PINT_OK;
+}
+
+// Tables of the shorter segment lengths nt/2, nt/4, ... (down to 16) used by
+// the adaptive window policy: FFT twiddles, lambda_1k, lambda_2k and the gamma
+// scalings depend on the segment length; every other table is shared.
+template <class T>
+static int build_levels(pint_handle* h) {
+    if (h->nlev > 1) return PINT_OK;
+    const pint_problem* p = &h->p;
+    const double dt = h->geo.dt;
+    auto expi = [](double turns) { return std::complex<double>(cos(2.0 * M_PI * turns), sin(2.0 * M_PI * turns)); };
+    const Tabs<T>* base = reinterpret_cast<const Tabs<T>*>(h->lev[0].tabs);
+    for (int L = p->nt / 2; L >= 16 && h->nlev < 11; L /= 2) {
+        auto& lv = h->lev[h->nlev];
+        const size_t nk = L / 2 + 1;
+        const size_t tbytes = (2 * L + 4 * nk) * sizeof(T);
+        const size_t bytes = tbytes + 2 * L * sizeof(double) + 2 * L * sizeof(float) + 256;
+        if (cudaMalloc(&lv.block, bytes) != cudaSuccess) { cudaGetLastError(); return PINT_ENOMEM; }
+        h->bytes += (long long)bytes;
+        std::vector<T> t(2 * L + 4 * nk);
+        for (int j = 0; j < L; ++j) { auto z = expi(-(double)j / L); t[2 * j] = (T)z.real(); t[2 * j + 1] = (T)z.imag(); }
+        const double a1 = pow(p->alpha, 1.0 / L);
+        for (size_t k = 0; k < nk; ++k) {
+            std::complex<double> z = a1 * expi(-(double)k / L);
+            std::complex<double> l1 = (1.0 - z) / dt, l2 = p->theta + (1.0 - p->theta) * z;
+            t[2 * L + 2 * k] = (T)l1.real();
+            t[2 * L + 2 * k + 1] = (T)l1.imag();
+            t[2 * L + 2 * nk + 2 * k] = (T)l2.real();
+            t[2 * L + 2 * nk + 2 * k + 1] = (T)l2.imag();
+        }
+        std::vector<double> g(L), gi(L);
+        std::vector<float> gf(L), gif(L);
+        for (int n = 0; n < L; ++n) {
+            g[n] = pow(p->alpha, (double)n / L);
+            gi[n] = pow(p->alpha, -(double)n / L) / L;
+            gf[n] = (float)g[n];
+            gif[n] = (float)gi[n];
+        }
+        char* b = reinterpret_cast<char*>(lv.block);
+        const size_t o_g = (tbytes + 15) / 16 * 16, o_gi = o_g + L * sizeof(double), o_gf = o_gi + L * sizeof(double),
+                     o_gif = o_gf + L * sizeof(float);
+        if (cudaMemcpy(b, t.data(), tbytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(b + o_g, g.data(), L * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(b + o_gi, gi.data(), L * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(b + o_gf, gf.data(), L * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(b + o_gif, gif.data(), L * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+            return PINT_ECUDA;
+        Tabs<T>* tb = new (std::nothrow) Tabs<T>(*base);
+        if (!tb) return PINT_ENOMEM;
+        const T* tt = reinterpret_cast<const T*>(b);
+        tb->twt = reinterpret_cast<const c_t<T>*>(tt);
+        tb->lam1 = reinterpret_cast<const c_t<T>*>(tt + 2 * L);
+        tb->lam2 = reinterpret_cast<const c_t<T>*>(tt + 2 * L + 2 * nk);
+        lv.nt = L;
+        lv.tabs = tb;
+        lv.gam = reinterpret_cast<double*>(b + o_g);
+        lv.ginv = reinterpret_cast<double*>(b + o_gi);
+        lv.gamf = reinterpret_cast<float*>(b + o_gf);
+        lv.ginvf = reinterpret_cast<float*>(b + o_gif);
+        h->nlev++;
+    }
+    return PINT_OK;
+}
+
+// Make level li (segment length lev[li].nt) the current time axis.
+static void activate_level(pint_handle* h, int li) {
+    const auto& lv = h->lev[li];
+    h->geo.nt = lv.nt;
+    h->gff.nt = lv.nt;
+    h->tabs_ptrs = lv.tabs;
+    h->gam = lv.gam;
+    h->ginv = lv.ginv;
+    h->gamf = lv.gamf;
+    h->ginvf = lv.ginvf;
 }
 
 static void derive(const pint_problem* p, pint_handle* h) {
@@ -430,7 +518,7 @@ static cudaError_t zero_start(pint_handle* h, double* U, const double* u0w) {
         if ((e = Impl<float>::spatial(h, reinterpret_cast<float2*>(h->S), tb)) != cudaSuccess) return e;
         prof_begin(h, PH_TINV);
         if (h->p.precision == PINT_MIXED_FF)
-            e = launch_time_inv_ff(g.nt, g.nspace, reinterpret_cast<float2*>(h->S), tb.twt, h->ginvf, h->Uff, h->ctl, h->st);
+            e = launch_time_inv_ff(g.nt, g.nspace, reinterpret_cast<float2*>(h->S), tb.twt, h->ginvf, h->Uff_cur, h->ctl, h->st);
         else
             e = launch_time_inv<float>(g.nt, g.nspace, reinterpret_cast<float2*>(h->S), tb.twt, h->ginv, U, 1, h->ctl, h->st);
         prof_end(h, PH_TINV, 1);
@@ -452,7 +540,7 @@ static cudaError_t iteration_ff(pint_handle* h) {
     float2* S = reinterpret_cast<float2*>(h->S);
     const Tabs<float>& tb = tabs_of<float>(h);
     prof_begin(h, PH_RES);
-    launch_residual_ff(h->gff, g, h->Uff, h->u0ff, h->gamf, s, h->partials, h->ctl, h->st);
+    launch_residual_ff(h->gff, g, h->Uff_cur, h->u0ff, h->gamf, s, h->partials, h->ctl, h->st);
     prof_end(h, PH_RES, 1);
     int gx, gy, gz, chunk;
     const int np = residual_ff_grid(g, gx, gy, gz, chunk);
@@ -465,7 +553,7 @@ static cudaError_t iteration_ff(pint_handle* h) {
     if (e != cudaSuccess) return e;
     if ((e = Impl<float>::spatial(h, S, tb)) != cudaSuccess) return e;
     prof_begin(h, PH_TINV);
-    e = launch_time_inv_ff(g.nt, g.nspace, S, tb.twt, h->ginvf, h->Uff, h->ctl, h->st);
+    e = launch_time_inv_ff(g.nt, g.nspace, S, tb.twt, h->ginvf, h->Uff_cur, h->ctl, h->st);
     prof_end(h, PH_TINV, 1);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
@@ -486,7 +574,7 @@ static int body_launches(const pint_handle* h) { return 5 + (h->geo.dim == 2 ? 2
 // also bake U and the window's u0 in, so graphs are cached per (U, u0).
 static cudaGraphExec_t get_graph(pint_handle* h, double* U, const double* u0w) {
     const bool ffm = h->p.precision == PINT_MIXED_FF;
-    const void* kU = ffm ? nullptr : U;
+    const void* kU = ffm ? (const void*)h->Uff_cur : U;
     const void* ku0 = ffm ? nullptr : u0w;
     for (auto& sl : h->gslot)
         if (sl.exec && sl.U == kU && sl.u0 == ku0) return sl.exec;
@@ -577,6 +665,12 @@ void pint_destroy(pint_handle* h) {
     cudaFree(h->ctl);
     cudaFreeHost(h->hctl);
     cudaFree(h->partials);
+    if (h->nlev > 0) activate_level(h, 0);   // the base level owns gam/ginv/gamf/ginvf and tabs_ptrs
+    for (int i = 1; i < h->nlev; ++i) {
+        cudaFree(h->lev[i].block);
+        if (f32_transforms(&h->p)) delete reinterpret_cast<Tabs<float>*>(h->lev[i].tabs);
+        else delete reinterpret_cast<Tabs<double>*>(h->lev[i].tabs);
+    }
     cudaFree(h->gam);
     cudaFree(h->ginv);
     cudaFree(h->u0buf);
@@ -644,6 +738,21 @@ int pint_create(const pint_problem* p, void* cuda_stream, pint_handle** out) {
         return rc;
     }
     h->npart = (int)z.partials;
+    h->lev[0].nt = p->nt;
+    h->lev[0].tabs = h->tabs_ptrs;
+    h->lev[0].gam = h->gam;
+    h->lev[0].ginv = h->ginv;
+    h->lev[0].gamf = h->gamf;
+    h->lev[0].ginvf = h->ginvf;
+    h->nlev = 1;
+    h->Uff_cur = h->Uff;
+    {
+        const int ny = p->dim == 2 ? p->ny : 1;
+        h->lamx_h.resize(p->nx);
+        h->lamy_h.resize(ny);
+        for (int i = 0; i < p->nx; ++i) h->lamx_h[i] = lap_eig(i, p->nx, p->bc);
+        for (int i = 0; i < ny; ++i) h->lamy_h[i] = p->dim == 2 ? lap_eig(i, ny, p->bc) : 0.0;
+    }
     *out = h;
     return PINT_OK;
 }
@@ -674,6 +783,15 @@ int pint_set_option(pint_handle* h, int option, long long value) {
             if (value != 0 && value != 1) return PINT_EINVAL;
             h->use_graphs = (int)value;
             return PINT_OK;
+        case PINT_OPT_ADAPTIVE_WINDOWS: {
+            if (value != 0 && value != 1) return PINT_EINVAL;
+            if (value) {
+                const int rc = f32_transforms(&h->p) ? build_levels<float>(h) : build_levels<double>(h);
+                if (rc != PINT_OK) return rc;
+            }
+            h->adaptive = (int)value;
+            return PINT_OK;
+        }
         default: return PINT_EINVAL;
     }
 }
@@ -690,35 +808,83 @@ int pint_profile_read(pint_handle* h, pint_profile* out, int reset) {
     return PINT_OK;
 }
 
+// Adaptive window policy (PINT_OPT_ADAPTIVE_WINDOWS): the longest segment
+// length L (a power of two, <= lmax) with alpha * G(L) <= 0.1, where
+// G(L) = max_p R_p^L and R_p = 1/(1 + dt mu_p) over the spectrum mu_p of the
+// spatial operator linearized about the segment's initial data (for
+// Cahn-Hilliard mu(Lam) = eps^2 Lam^2 + (1 - jbar0) Lam with jbar0 = mean 3 u0^2).
+// A mode with alpha R^L near 1 makes the iteration resonate (per-mode factor
+// |alpha R^L / (1 - alpha R^L)|, Eq. 2.18), so growing modes force short segments.
+static int choose_level(pint_handle* h, int lmax, double jbar0) {
+    const double dt = h->geo.dt, c2 = h->coef.c2, c1 = h->coef.ch ? 1.0 - jbar0 : h->coef.c1;
+    double mu_min = 0.0;
+    for (double lx : h->lamx_h)
+        for (double ly : h->lamy_h) {
+            const double L = lx + ly, mu = c2 * L * L + c1 * L;
+            if (mu < mu_min) mu_min = mu;
+        }
+    int li = 0;
+    while (li + 1 < h->nlev && h->lev[li].nt > lmax) ++li;
+    if (mu_min >= 0.0) return li;
+    if (1.0 + dt * mu_min <= 0.0) return h->nlev - 1;
+    const double lnR = -log1p(dt * mu_min);
+    for (; li < h->nlev; ++li)
+        if (log(h->p.alpha) + h->lev[li].nt * lnR <= log(0.1)) return li;
+    return h->nlev - 1;
+}
+
 int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* st) {
     if (!h || !u0_dev || !U_dev) return PINT_EINVAL;
     const pint_problem& p = h->p;
     const Geo& g = h->geo;
     const bool ffm = p.precision == PINT_MIXED_FF;
-    const size_t dof = (size_t)g.nt * g.nspace;
+    const int ntmax = h->lev[0].nt;
+    const size_t ns = (size_t)g.nspace, dof = (size_t)ntmax * ns;
+    const bool adapt = h->adaptive && h->nlev > 1;
     pint_stats S;
     memset(&S, 0, sizeof(S));
+    S.nt_min = ntmax;
     int rc = PINT_OK;
+    activate_level(h, 0);
     if (ffm && p.init_guess == 1) launch_f64_to_ff(U_dev, h->Uff, dof, h->st);
-    for (int w = 0; w < p.n_windows; ++w) {
-        const double* u0w = w == 0 ? u0_dev : h->u0buf;
+    const long long total = (long long)ntmax * p.n_windows;
+    long long done = 0;
+    for (int seg = 0; done < total; ++seg) {
+        const int base = (int)(done % ntmax);   // offset of this segment inside its window
+        const double* u0w = seg == 0 ? u0_dev : h->u0buf;
         prof_begin(h, PH_SETUP);
         int nl = 2;
-        if (ffm && w == 0) { launch_f64_to_ff(u0_dev, h->u0ff, g.nspace, h->st); nl++; }
+        if (ffm && seg == 0) { launch_f64_to_ff(u0_dev, h->u0ff, g.nspace, h->st); nl++; }
+        int li = 0;
+        if (adapt) {
+            // segments never cross a window boundary: at offset base the length
+            // is at most the largest power of two dividing base
+            const int lmax = base == 0 ? ntmax : (base & -base);
+            activate_level(h, 0);
+            launch_begin_window(u0w, g.nspace, g.inv_dt, p.max_iter, p.tol, h->partials, h->ctl, h->st);
+            if ((rc = read_ctl(h)) != PINT_OK) return rc;
+            const double rms = h->hctl->bnorm * g.dt;          // ||u0||_2
+            li = choose_level(h, lmax, 3.0 * rms * rms / (double)ns);
+        }
+        activate_level(h, li);
+        const int L = g.nt;
+        double* Useg = U_dev + (size_t)base * ns;
+        h->Uff_cur = ffm ? h->Uff + (size_t)base * ns : h->Uff;
+        const size_t sdof = (size_t)L * ns;
         if (p.init_guess == 2) {
-            PINT_CK(ffm ? cudaMemsetAsync(h->Uff, 0, dof * sizeof(float2), h->st)
-                        : cudaMemsetAsync(U_dev, 0, dof * sizeof(double), h->st));
-        } else if (w > 0 || p.init_guess == 0) {
-            if (ffm) launch_broadcast_ff(h->Uff, h->u0ff, g.nspace, g.nt, h->st);
-            else launch_broadcast(U_dev, u0w, g.nspace, g.nt, h->st);
+            PINT_CK(ffm ? cudaMemsetAsync(h->Uff_cur, 0, sdof * sizeof(float2), h->st)
+                        : cudaMemsetAsync(Useg, 0, sdof * sizeof(double), h->st));
+        } else if (seg > 0 || p.init_guess == 0) {
+            if (ffm) launch_broadcast_ff(h->Uff_cur, h->u0ff, g.nspace, L, h->st);
+            else launch_broadcast(Useg, u0w, g.nspace, L, h->st);
             nl++;
         }
         launch_begin_window(u0w, g.nspace, g.inv_dt, p.max_iter, p.tol, h->partials, h->ctl, h->st);
         prof_end(h, PH_SETUP, nl);
-        cudaGraphExec_t gx = (h->use_graphs && !h->prof_on) ? get_graph(h, U_dev, u0w) : nullptr;
+        cudaGraphExec_t gx = (h->use_graphs && !h->prof_on && !adapt) ? get_graph(h, Useg, u0w) : nullptr;
         if (gx) {
             // one graph launch runs the iteration loop of this window to its stop
-            if (p.init_guess == 2 && zero_start(h, U_dev, u0w) != cudaSuccess) return PINT_ECUDA;
+            if (p.init_guess == 2 && zero_start(h, Useg, u0w) != cudaSuccess) return PINT_ECUDA;
             PINT_CK(cudaGraphLaunch(gx, h->st));
             if ((rc = read_ctl(h)) != PINT_OK) return rc;
             if (h->hctl->status == ST_RUNNING) return PINT_ECUDA;  // the loop ends only on a final status
@@ -733,8 +899,8 @@ int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* 
             for (;;) {
                 int chunk = enqueued == 0 ? 3 : 2;
                 for (int c = 0; c < chunk; ++c) {
-                    cudaError_t e = enqueued == 0 && c == 0 && p.init_guess == 2 ? zero_start(h, U_dev, u0w)
-                                    : ffm ? iteration_ff(h) : iteration(h, U_dev, u0w);
+                    cudaError_t e = enqueued == 0 && c == 0 && p.init_guess == 2 ? zero_start(h, Useg, u0w)
+                                    : ffm ? iteration_ff(h) : iteration(h, Useg, u0w);
                     if (e != cudaSuccess) return PINT_ECUDA;
                 }
                 enqueued += chunk;
@@ -748,6 +914,8 @@ int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* 
         S.status = c.status;
         S.iters += k;
         S.iters_last = k;
+        S.segments = seg + 1;
+        if (L < S.nt_min) S.nt_min = L;
         S.rel_residual = c.rho;
         S.jbar = h->coef.ch ? c.jbar : 0.0;
         for (int i = 0; i <= k && i < PINT_HIST_MAX; ++i) S.hist[i] = c.hist[i];
@@ -756,18 +924,21 @@ int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* 
             rc = c.status;
             break;
         }
-        S.windows = w + 1;
-        if (w + 1 < p.n_windows) {
+        done += L;
+        S.windows = (int)(done / ntmax);
+        if (done < total) {
             if (ffm) {
-                PINT_CK(cudaMemcpyAsync(h->u0ff, h->Uff + (size_t)(g.nt - 1) * g.nspace, g.nspace * sizeof(float2),
+                PINT_CK(cudaMemcpyAsync(h->u0ff, h->Uff_cur + (size_t)(L - 1) * ns, ns * sizeof(float2),
                                         cudaMemcpyDeviceToDevice, h->st));
                 launch_ff_to_f64(h->u0ff, h->u0buf, g.nspace, h->st);
             } else {
-                PINT_CK(cudaMemcpyAsync(h->u0buf, U_dev + (size_t)(g.nt - 1) * g.nspace, g.nspace * sizeof(double),
+                PINT_CK(cudaMemcpyAsync(h->u0buf, Useg + (size_t)(L - 1) * ns, ns * sizeof(double),
                                         cudaMemcpyDeviceToDevice, h->st));
             }
         }
     }
+    activate_level(h, 0);
+    h->Uff_cur = h->Uff;
     if (ffm) {
         launch_ff_to_f64(h->Uff, U_dev, dof, h->st);
         h->launches[PH_SETUP] += 1;
@@ -785,7 +956,7 @@ int pint_solve_host(pint_handle* h, const double* u0_host, double* U_host, pint_
         if (cudaMalloc((void**)&h->hu0, ns * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return PINT_ENOMEM; }
     }
     PINT_CK(cudaMemcpyAsync(h->hu0, u0_host, ns * sizeof(double), cudaMemcpyHostToDevice, h->st));
-    if (h->p.init_guess)
+    if (h->p.init_guess == 1)
         PINT_CK(cudaMemcpyAsync(h->hU, U_host, dof * sizeof(double), cudaMemcpyHostToDevice, h->st));
     int rc = pint_solve(h, h->hu0, h->hU, st);
     if (rc != PINT_OK && rc != PINT_ENOCONV && rc != PINT_EDIVERGED) return rc;

@@ -34,12 +34,13 @@ class Problem(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("windows", C.c_int), ("iters_last", C.c_int),
                 ("rel_residual", C.c_double), ("contraction", C.c_double), ("jbar", C.c_double),
-                ("hist", C.c_double * HIST_MAX)]
+                ("hist", C.c_double * HIST_MAX), ("segments", C.c_int), ("nt_min", C.c_int)]
 
     def as_dict(self) -> dict:
         return {"status": self.status, "iters": self.iters, "windows": self.windows,
                 "iters_last": self.iters_last, "rel_residual": self.rel_residual,
-                "contraction": self.contraction, "jbar": self.jbar,
+                "contraction": self.contraction, "jbar": self.jbar, "segments": self.segments,
+                "nt_min": self.nt_min,
                 "hist": [self.hist[i] for i in range(min(self.iters_last + 1, HIST_MAX))]}
 
 
@@ -184,6 +185,11 @@ class Solver:
 
     def set_graphs(self, on: bool = True) -> None:
         rc = lib().pint_set_option(self._h, 1, 1 if on else 0)
+        if rc != PINT_OK:
+            raise PintError(rc, "pint_set_option")
+
+    def set_adaptive_windows(self, on: bool = True) -> None:
+        rc = lib().pint_set_option(self._h, 2, 1 if on else 0)
         if rc != PINT_OK:
             raise PintError(rc, "pint_set_option")
 
