@@ -102,6 +102,7 @@ typedef struct {
     double hist[PINT_HIST_MAX];  /* rho_0 .. rho_{iters_last} of the last window */
     int    segments;          /* solves run (one per window, more under the adaptive window policy) */
     int    nt_min;            /* shortest segment length used */
+    int    retries;           /* segments solved again with half the length (adaptive policy) */
 } pint_stats;
 
 typedef struct pint_handle pint_handle;
@@ -179,8 +180,10 @@ int pint_profile_read(pint_handle* h, pint_profile* out, int reset);
  *    data (for Cahn-Hilliard: eps^2 Lam^2 + (1 - mean 3u0^2) Lam).  Growing modes
  *    (spinodal decomposition) make alpha R^L approach 1, where the iteration's
  *    per-mode factor |alpha R^L/(1 - alpha R^L)| (Eq. 2.18) exceeds one; shorter
- *    segments keep it small.  Enabling it builds the tables of the shorter
- *    lengths (allocates device memory); it runs the host-launched loop. */
+ *    segments keep it small.  A segment that still diverges or stalls is solved
+ *    again from its initial data with half the length (down to 16 steps).
+ *    Enabling it builds the tables of the shorter lengths (allocates device
+ *    memory); it runs the host-launched loop. */
 #define PINT_OPT_ADAPTIVE_WINDOWS 2
 int pint_set_option(pint_handle* h, int option, long long value);
 

@@ -853,8 +853,9 @@ int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* 
         const int base = (int)(done % ntmax);   // offset of this segment inside its window
         const double* u0w = seg == 0 ? u0_dev : h->u0buf;
         prof_begin(h, PH_SETUP);
-        int nl = 2;
+        int nl = 0;
         if (ffm && seg == 0) { launch_f64_to_ff(u0_dev, h->u0ff, g.nspace, h->st); nl++; }
+        if (adapt) nl += 2;
         int li = 0;
         if (adapt) {
             // segments never cross a window boundary: at offset base the length
@@ -866,53 +867,68 @@ int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* 
             const double rms = h->hctl->bnorm * g.dt;          // ||u0||_2
             li = choose_level(h, lmax, 3.0 * rms * rms / (double)ns);
         }
-        activate_level(h, li);
-        const int L = g.nt;
-        double* Useg = U_dev + (size_t)base * ns;
-        h->Uff_cur = ffm ? h->Uff + (size_t)base * ns : h->Uff;
-        const size_t sdof = (size_t)L * ns;
-        if (p.init_guess == 2) {
-            PINT_CK(ffm ? cudaMemsetAsync(h->Uff_cur, 0, sdof * sizeof(float2), h->st)
-                        : cudaMemsetAsync(Useg, 0, sdof * sizeof(double), h->st));
-        } else if (seg > 0 || p.init_guess == 0) {
-            if (ffm) launch_broadcast_ff(h->Uff_cur, h->u0ff, g.nspace, L, h->st);
-            else launch_broadcast(Useg, u0w, g.nspace, L, h->st);
-            nl++;
-        }
-        launch_begin_window(u0w, g.nspace, g.inv_dt, p.max_iter, p.tol, h->partials, h->ctl, h->st);
         prof_end(h, PH_SETUP, nl);
-        cudaGraphExec_t gx = (h->use_graphs && !h->prof_on && !adapt) ? get_graph(h, Useg, u0w) : nullptr;
-        if (gx) {
-            // one graph launch runs the iteration loop of this window to its stop
-            if (p.init_guess == 2 && zero_start(h, Useg, u0w) != cudaSuccess) return PINT_ECUDA;
-            PINT_CK(cudaGraphLaunch(gx, h->st));
-            if ((rc = read_ctl(h)) != PINT_OK) return rc;
-            if (h->hctl->status == ST_RUNNING) return PINT_ECUDA;  // the loop ends only on a final status
-            const long long runs = h->hctl->iter + 1 - (p.init_guess == 2 ? 1 : 0);
-            h->launches[PH_RES] += runs;
-            h->launches[PH_CHECK] += runs;
-            h->launches[PH_TFWD] += runs;
-            for (int stg = 0; stg < (g.dim == 2 ? 3 : 1); ++stg) h->launches[PH_SP0 + stg] += runs;
-            h->launches[PH_TINV] += runs;
-        } else {
-            int enqueued = 0;
-            for (;;) {
-                int chunk = enqueued == 0 ? 3 : 2;
-                for (int c = 0; c < chunk; ++c) {
-                    cudaError_t e = enqueued == 0 && c == 0 && p.init_guess == 2 ? zero_start(h, Useg, u0w)
-                                    : ffm ? iteration_ff(h) : iteration(h, Useg, u0w);
-                    if (e != cudaSuccess) return PINT_ECUDA;
-                }
-                enqueued += chunk;
-                if ((rc = read_ctl(h)) != PINT_OK) return rc;
-                if (h->hctl->status != ST_RUNNING) break;
-                if (enqueued > p.max_iter + 8) return PINT_ECUDA;  // the device loop must have stopped by now
+        double* Useg = U_dev + (size_t)base * ns;
+        int L = 0;
+        // Solve the segment; under the adaptive policy a segment that diverges
+        // or stalls is solved again from the same initial data with half the length.
+        for (bool first_try = true;; first_try = false) {
+            activate_level(h, li);
+            L = g.nt;
+            h->Uff_cur = ffm ? h->Uff + (size_t)base * ns : h->Uff;
+            const size_t sdof = (size_t)L * ns;
+            prof_begin(h, PH_SETUP);
+            nl = 1;
+            if (p.init_guess == 2) {
+                PINT_CK(ffm ? cudaMemsetAsync(h->Uff_cur, 0, sdof * sizeof(float2), h->st)
+                            : cudaMemsetAsync(Useg, 0, sdof * sizeof(double), h->st));
+            } else if (seg > 0 || p.init_guess == 0 || !first_try) {
+                if (ffm) launch_broadcast_ff(h->Uff_cur, h->u0ff, g.nspace, L, h->st);
+                else launch_broadcast(Useg, u0w, g.nspace, L, h->st);
+                nl++;
             }
+            launch_begin_window(u0w, g.nspace, g.inv_dt, p.max_iter, p.tol, h->partials, h->ctl, h->st);
+            prof_end(h, PH_SETUP, nl + 1);
+            cudaGraphExec_t gx = (h->use_graphs && !h->prof_on && !adapt) ? get_graph(h, Useg, u0w) : nullptr;
+            if (gx) {
+                // one graph launch runs the iteration loop of this window to its stop
+                if (p.init_guess == 2 && zero_start(h, Useg, u0w) != cudaSuccess) return PINT_ECUDA;
+                PINT_CK(cudaGraphLaunch(gx, h->st));
+                if ((rc = read_ctl(h)) != PINT_OK) return rc;
+                if (h->hctl->status == ST_RUNNING) return PINT_ECUDA;  // the loop ends only on a final status
+                const long long runs = h->hctl->iter + 1 - (p.init_guess == 2 ? 1 : 0);
+                h->launches[PH_RES] += runs;
+                h->launches[PH_CHECK] += runs;
+                h->launches[PH_TFWD] += runs;
+                for (int stg = 0; stg < (g.dim == 2 ? 3 : 1); ++stg) h->launches[PH_SP0 + stg] += runs;
+                h->launches[PH_TINV] += runs;
+            } else {
+                int enqueued = 0;
+                for (;;) {
+                    int chunk = enqueued == 0 ? 3 : 2;
+                    for (int c = 0; c < chunk; ++c) {
+                        cudaError_t e = enqueued == 0 && c == 0 && p.init_guess == 2 ? zero_start(h, Useg, u0w)
+                                        : ffm ? iteration_ff(h) : iteration(h, Useg, u0w);
+                        if (e != cudaSuccess) return PINT_ECUDA;
+                    }
+                    enqueued += chunk;
+                    if ((rc = read_ctl(h)) != PINT_OK) return rc;
+                    if (h->hctl->status != ST_RUNNING) break;
+                    if (enqueued > p.max_iter + 8) return PINT_ECUDA;  // the device loop must have stopped by now
+                }
+            }
+            const int stt = h->hctl->status;
+            S.iters += h->hctl->iter;
+            if (adapt && stt != PINT_OK && li + 1 < h->nlev) {
+                ++li;
+                ++S.retries;
+                continue;
+            }
+            break;
         }
         const Ctl& c = *h->hctl;
         const int k = c.iter;
         S.status = c.status;
-        S.iters += k;
         S.iters_last = k;
         S.segments = seg + 1;
         if (L < S.nt_min) S.nt_min = L;

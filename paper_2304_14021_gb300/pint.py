@@ -34,13 +34,14 @@ class Problem(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("windows", C.c_int), ("iters_last", C.c_int),
                 ("rel_residual", C.c_double), ("contraction", C.c_double), ("jbar", C.c_double),
-                ("hist", C.c_double * HIST_MAX), ("segments", C.c_int), ("nt_min", C.c_int)]
+                ("hist", C.c_double * HIST_MAX), ("segments", C.c_int), ("nt_min", C.c_int),
+                ("retries", C.c_int)]
 
     def as_dict(self) -> dict:
         return {"status": self.status, "iters": self.iters, "windows": self.windows,
                 "iters_last": self.iters_last, "rel_residual": self.rel_residual,
                 "contraction": self.contraction, "jbar": self.jbar, "segments": self.segments,
-                "nt_min": self.nt_min,
+                "nt_min": self.nt_min, "retries": self.retries,
                 "hist": [self.hist[i] for i in range(min(self.iters_last + 1, HIST_MAX))]}
 
 

@@ -287,7 +287,8 @@ def test_ch_spinodal_long_window_diverges_without_policy():
 
 @pytest.mark.parametrize("precision", ["mixed_ff", "fp64"])
 def test_ch_adaptive_windows_match_oracle(precision):
-    kw = full(dict(CH_SPINODAL, precision=precision, tol=1e-10 if precision == "fp64" else 1e-9))
+    # spinodal data amplify perturbations strongly: FP64 is asked for 1e-12 to stay within 1e-10 of the oracle
+    kw = full(dict(CH_SPINODAL, precision=precision, tol=1e-12 if precision == "fp64" else 1e-9))
     p = oprob(kw)
     u0 = synth.u0_ch(p.nspace, 0)
     with pint.Solver(**kw) as s:
