@@ -187,6 +187,28 @@ int pint_profile_read(pint_handle* h, pint_profile* out, int reset);
 #define PINT_OPT_ADAPTIVE_WINDOWS 2
 int pint_set_option(pint_handle* h, int option, long long value);
 
+/* pint_residual_static: the residual of pint_residual for callers that cannot
+ * allocate device memory when they need it (a process whose device memory is
+ * already reserved by another allocator, a latency path that must not block in
+ * cudaMalloc, a program that sizes its memory once at start-up).  No handle,
+ * no allocation of any kind: the reduction scratch is a file-scope device array
+ * of PINT_STATIC_SCRATCH_BYTES that each GPU which loads the library holds until
+ * the process exits.  The paper has no counterpart; this is a deployment aid.
+ *  p:           problem (validated as in pint_create)
+ *  cuda_stream: cudaStream_t the kernels run on (NULL = legacy default stream)
+ *  u0_dev, U_dev: as in pint_residual; r_dev (nt*nx*ny doubles) may be NULL
+ *  rel_res_dev: device pointer to one double that receives ||r||_2 / ||b||_2
+ * Asynchronous: returns after enqueueing; read rel_res_dev after the stream.
+ * The first call on a device looks up the scratch array's device address (with
+ * that device current) and caches it; make that first call outside any stream
+ * capture.  All calls share the one array: calls whose kernels overlap on a GPU
+ * (concurrent streams, threads) race and must be serialized by the caller.
+ * Errors: PINT_EINVAL (bad problem or NULL pointer, or a grid whose reduction
+ * needs more partial sums than the scratch holds), PINT_ECUDA. */
+#define PINT_STATIC_SCRATCH_BYTES 262144
+int pint_residual_static(const pint_problem* p, void* cuda_stream, const double* u0_dev, const double* U_dev,
+                         double* r_dev, double* rel_res_dev);
+
 /* Free everything the handle owns (NULL is allowed). */
 void pint_destroy(pint_handle* h);
 

@@ -631,6 +631,28 @@ static cudaGraphExec_t get_graph(pint_handle* h, double* U, const double* u0w) {
     return exec;
 }
 
+// Validation and geometry for callers without a handle (pint_residual_static).
+int validate_problem(const pint_problem* p) { return validate(p); }
+
+void geometry_of(const pint_problem* p, Geo& g) {
+    g.nx = p->nx;
+    g.ny = p->dim == 2 ? p->ny : 1;
+    g.dim = p->dim;
+    g.bc = p->bc;
+    g.nt = p->nt;
+    g.nspace = g.nx * g.ny;
+    g.dt = p->T / ((double)p->nt * p->n_windows);
+    g.inv_dt = 1.0 / g.dt;
+    const double hx = grid_h(p->nx, p->bc), hy = grid_h(g.ny, p->bc);
+    g.ihx2 = 1.0 / (hx * hx);
+    g.ihy2 = p->dim == 2 ? 1.0 / (hy * hy) : 0.0;
+    switch (p->equation) {
+        case PINT_BIHARMONIC: g.c2 = 1.0; g.c1 = 0.0; g.cN = 0.0; break;
+        case PINT_LINEAR_CH: g.c2 = p->eps * p->eps; g.c1 = p->beta * p->beta; g.cN = 0.0; break;
+        default: g.c2 = p->eps * p->eps; g.c1 = 1.0; g.cN = -1.0; break;
+    }
+}
+
 }  // namespace pint
 
 using namespace pint;

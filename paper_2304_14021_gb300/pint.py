@@ -88,6 +88,8 @@ def lib() -> C.CDLL:
         L.pint_profile_read.restype = C.c_int
         L.pint_set_option.argtypes = [vp, C.c_int, C.c_longlong]
         L.pint_set_option.restype = C.c_int
+        L.pint_residual_static.argtypes = [C.POINTER(Problem), vp, vp, vp, vp, vp]
+        L.pint_residual_static.restype = C.c_int
         L.pint_destroy.argtypes = [vp]
         L.pint_destroy.restype = None
         L.pint_strerror.argtypes = [C.c_int]
@@ -117,6 +119,24 @@ def make_problem(equation="biharmonic", dim=1, nx=64, ny=1, bc="ss", eps=1.0, be
 def footprint(**kw) -> int:
     p = make_problem(**kw)
     return int(lib().pint_footprint(C.byref(p)))
+
+
+STATIC_SCRATCH_BYTES = 262144
+
+
+def residual_static(u0, U, rel_res, r=None, stream=None, **problem) -> None:
+    """pint_residual_static: residual and ||r||/||b|| without a handle and without
+    allocating (scratch in a static device array).  rel_res: a float64 CUDA
+    tensor with one element that receives the norm; asynchronous on `stream`."""
+    import torch
+    p = make_problem(**problem)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    rc = lib().pint_residual_static(C.byref(p), C.c_void_p(stream.cuda_stream), C.c_void_p(_ptr(u0)),
+                                    C.c_void_p(_ptr(U)), C.c_void_p(_ptr(r)) if r is not None else None,
+                                    C.c_void_p(_ptr(rel_res)))
+    if rc != PINT_OK:
+        raise PintError(rc, "pint_residual_static")
 
 
 def _ptr(t) -> int:
