@@ -87,6 +87,12 @@ typedef struct {
                             1: the first window starts from the iterate passed in U,
                                later windows as 0;
                             2: each window starts from U^0 = 0 */
+    double tol_update;   /* 0: off.  > 0: a window also stops when the last correction is small,
+                            ||delta||_2 / ||U||_2 <= tol_update (an error estimate, in the spirit of
+                            the error-based stopping rule of Sec. 5).  For very stiff problems the
+                            rounding of any iterate keeps ||b - K(U)|| / ||b|| near
+                            eps * dt * max|spectrum of A|, so a residual tolerance alone can be
+                            unreachable there while the iterate has converged. */
 } pint_problem;
 
 #define PINT_HIST_MAX 256
@@ -103,6 +109,8 @@ typedef struct {
     int    segments;          /* solves run (one per window, more under the adaptive window policy) */
     int    nt_min;            /* shortest segment length used */
     int    retries;           /* segments solved again with half the length (adaptive policy) */
+    double update_norm;       /* ||delta||_2 / ||U||_2 of the last correction of the last window
+                                 (computed when tol_update > 0, else 0) */
 } pint_stats;
 
 typedef struct pint_handle pint_handle;
@@ -130,6 +138,15 @@ long long pint_footprint(const pint_problem* p);
  * iterate), or PINT_EINVAL / PINT_ECUDA.  Blocks the host until the stream
  * has finished the solve. */
 int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* st);
+
+/* Solve n independent instances concurrently: instance i is pint_solve(hs[i],
+ * u0s[i], Us[i], &st[i]).  Each instance is driven by its own host thread (up to
+ * 64 at a time); instances whose handles were created on different streams run
+ * concurrently on the GPU, each window's iteration loop as one CUDA graph.
+ * Handles may not repeat.  st and rcs (per-instance return codes) may be NULL.
+ * Returns PINT_OK, or the first non-zero instance code in index order. */
+int pint_solve_batch(pint_handle* const* hs, int n, const double* const* u0s, double* const* Us, pint_stats* st,
+                     int* rcs);
 
 /* pint_solve with host buffers: copies u0_host (and U_host if init_guess = 1)
  * to handle-owned device buffers, solves, copies the result to U_host. */

@@ -167,7 +167,7 @@ __device__ void reduce_pairs(const double* __restrict__ partials, int np, double
 
 // Start of a window: ||b|| = ||u0|| / dt (theta = 1), reset the iteration state.
 __global__ void __launch_bounds__(256) k_begin_window(const double* __restrict__ partials, int np, double inv_dt,
-                                                      int max_iter, double tol, Ctl* ctl) {
+                                                      int max_iter, double tol, double tol_update, Ctl* ctl) {
     double A, B;
     reduce_pairs(partials, np, A, B);
     if (threadIdx.x == 0) {
@@ -176,6 +176,8 @@ __global__ void __launch_bounds__(256) k_begin_window(const double* __restrict__
         ctl->iter = 0;
         ctl->max_iter = max_iter;
         ctl->tol = tol;
+        ctl->tol_update = tol_update;
+        ctl->dnorm = 1.0;
         ctl->rho0 = 0.0;
         ctl->rho = 0.0;
     }
@@ -187,13 +189,16 @@ __global__ void __launch_bounds__(256) k_begin_window(const double* __restrict__
 // whose status is already final stops after this iteration.
 __global__ void __launch_bounds__(256) k_after_residual(const double* __restrict__ partials, int np,
                                                         double inv_dof, Ctl* ctl, cudaGraphConditionalHandle cond,
-                                                        int use_cond) {
+                                                        int use_cond, const double* __restrict__ dpart, int ndp) {
     if (ctl->status != ST_RUNNING) {
         if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
         return;
     }
-    double A, B;
+    double A, B, D = 0.0, W = 0.0;
     reduce_pairs(partials, np, A, B);
+    const bool upd = ndp > 0 && ctl->iter > 0 && ctl->tol_update > 0.0;
+    __syncthreads();
+    if (upd) reduce_pairs(dpart, ndp, D, W);
     if (threadIdx.x == 0) {
         const int k = ctl->iter;
         const double bn = ctl->bnorm;
@@ -207,10 +212,15 @@ __global__ void __launch_bounds__(256) k_after_residual(const double* __restrict
         // stagnation: no decrease over the last three corrections (the residual
         // sits at the rounding floor of the iterate's precision)
         // (growth by 10x over three corrections counts as divergence)
-        const bool stalled = k >= 4 && k < 256 && rho >= 0.99 * ctl->hist[k - 3];
-        const bool growing = stalled && rho > 10.0 * ctl->hist[k - 3];
+        const double dn = upd ? (W > 0.0 ? sqrt(D / W) : sqrt(D)) : 1.0;
+        ctl->dnorm = dn;
+        if (k < 256) ctl->dhist[k] = dn;
+        // with the update-size test on, a still-shrinking correction is progress too
+        const bool d_stalled = !upd || (k >= 4 && dn >= 0.99 * ctl->dhist[k - 3]);
+        const bool stalled = k >= 4 && k < 256 && rho >= 0.99 * ctl->hist[k - 3] && d_stalled;
+        const bool growing = k >= 4 && k < 256 && rho >= 0.99 * ctl->hist[k - 3] && rho > 10.0 * ctl->hist[k - 3];
         if (!(rho == rho) || rho > 1e300 || (k > 0 && rho > 1e6 * ctl->rho0) || growing) ctl->status = -5;  // PINT_EDIVERGED
-        else if (rho <= ctl->tol) ctl->status = 0;                                              // PINT_OK
+        else if (rho <= ctl->tol || (upd && dn <= ctl->tol_update)) ctl->status = 0;            // PINT_OK
         else if (k >= ctl->max_iter || stalled) ctl->status = -4;                               // PINT_ENOCONV
         else ctl->iter = k + 1;
         if (use_cond) cudaGraphSetConditional(cond, ctl->status == ST_RUNNING ? 1u : 0u);
@@ -307,14 +317,15 @@ int norm2_blocks(int n) {
     return b > 1024 ? 1024 : (b < 1 ? 1 : b);
 }
 void launch_begin_window(const double* u0, int nspace, double inv_dt, int max_iter, double tol, double* partials,
-                         Ctl* ctl, cudaStream_t st) {
+                         Ctl* ctl, cudaStream_t st, double tol_update) {
     int nb = norm2_blocks(nspace);
     k_norm2<<<nb, 256, 0, st>>>(u0, nspace, partials);
-    k_begin_window<<<1, 256, 0, st>>>(partials, nb, inv_dt, max_iter, tol, ctl);
+    k_begin_window<<<1, 256, 0, st>>>(partials, nb, inv_dt, max_iter, tol, tol_update, ctl);
 }
 void launch_after_residual(const double* partials, int np, double inv_dof, Ctl* ctl, cudaStream_t st,
-                           unsigned long long cond, int use_cond) {
-    k_after_residual<<<1, 256, 0, st>>>(partials, np, inv_dof, ctl, (cudaGraphConditionalHandle)cond, use_cond);
+                           unsigned long long cond, int use_cond, const double* dpart, int ndp) {
+    k_after_residual<<<1, 256, 0, st>>>(partials, np, inv_dof, ctl, (cudaGraphConditionalHandle)cond, use_cond,
+                                        dpart, ndp);
 }
 void launch_residual_norm(const double* partials, int np, Ctl* ctl, cudaStream_t st) {
     k_residual_norm<<<1, 256, 0, st>>>(partials, np, ctl);

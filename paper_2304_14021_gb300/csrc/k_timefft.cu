@@ -67,7 +67,8 @@ template <class T, int NT, int OUTK>
 __global__ void __launch_bounds__(TimeCfg<T, NT>::NTH)
     k_time_inv(int nspace, const c_t<T>* __restrict__ S, const c_t<T>* __restrict__ twt,
                const double* __restrict__ ginv, const float* __restrict__ ginvf, double* __restrict__ out,
-               float2* __restrict__ outff, int accumulate, const Ctl* __restrict__ ctl) {
+               float2* __restrict__ outff, int accumulate, const Ctl* __restrict__ ctl,
+               double* __restrict__ dpart) {
     using C = c_t<T>;
     constexpr int CW = TimeCfg<T, NT>::CW, NTH = TimeCfg<T, NT>::NTH;
     if (ctl && ctl->status != ST_RUNNING) return;
@@ -90,6 +91,9 @@ __global__ void __launch_bounds__(TimeCfg<T, NT>::NTH)
     }
     __syncthreads();
     smem_fft<C, NT, +1, NTH, CW, CW, 1>(z, tw);
+    // dpart != nullptr: per-CTA partial sums (sum delta^2, sum U_new^2) of the
+    // correction and the updated iterate, for the update-size stopping test
+    float d2 = 0.f, u2 = 0.f;
 #pragma unroll 4
     for (int e = tid; e < NT * CW; e += NTH) {
         const int c = e % CW, n = e / CW;
@@ -98,19 +102,52 @@ __global__ void __launch_bounds__(TimeCfg<T, NT>::NTH)
         if constexpr (OUTK == 1) {
             const float gi = ginvf[n];
             float2* row = outff + (size_t)n * nspace;
-            if (pa < nspace) row[pa] = ff_add_f(row[pa], (float)v.x * gi);
-            if (pb < nspace) row[pb] = ff_add_f(row[pb], (float)v.y * gi);
+            const float da = (float)v.x * gi, db = (float)v.y * gi;
+            if (pa < nspace) {
+                const float2 w = ff_add_f(row[pa], da);
+                row[pa] = w;
+                d2 = fmaf(da, da, d2);
+                u2 = fmaf(w.x, w.x, u2);
+            }
+            if (pb < nspace) {
+                const float2 w = ff_add_f(row[pb], db);
+                row[pb] = w;
+                d2 = fmaf(db, db, d2);
+                u2 = fmaf(w.x, w.x, u2);
+            }
             continue;
         }
         const double gi = ginv[n];
         double* row = out + (size_t)n * nspace;
         const double da = (double)v.x * gi, db = (double)v.y * gi;   // FP64 unscaling
         if (accumulate) {
-            if (pa < nspace) row[pa] += da;
-            if (pb < nspace) row[pb] += db;
+            if (pa < nspace) {
+                const double w = row[pa] + da;
+                row[pa] = w;
+                d2 = fmaf((float)da, (float)da, d2);
+                u2 = fmaf((float)w, (float)w, u2);
+            }
+            if (pb < nspace) {
+                const double w = row[pb] + db;
+                row[pb] = w;
+                d2 = fmaf((float)db, (float)db, d2);
+                u2 = fmaf((float)w, (float)w, u2);
+            }
         } else {
             if (pa < nspace) row[pa] = da;
             if (pb < nspace) row[pb] = db;
+        }
+    }
+    if (dpart) {  // deterministic block reduction (same tree every launch)
+        __shared__ double red[2][32];
+        double a = warp_sum((double)d2), b = warp_sum((double)u2);
+        if (tid % 32 == 0) { red[0][tid / 32] = a; red[1][tid / 32] = b; }
+        __syncthreads();
+        if (tid == 0) {
+            double A = 0.0, B = 0.0;
+            for (int w = 0; w < NTH / 32; ++w) { A += red[0][w]; B += red[1][w]; }
+            dpart[2 * blockIdx.x] = A;
+            dpart[2 * blockIdx.x + 1] = B;
         }
     }
 }
@@ -147,19 +184,30 @@ static void time_fwd_nt(int nspace, const T* s, c_t<T>* S, const c_t<T>* twt, co
 }
 template <class T, int NT>
 static void time_inv_nt(int nspace, const c_t<T>* S, const c_t<T>* twt, const double* ginv, double* out, int acc,
-                        const Ctl* ctl, cudaStream_t st) {
+                        const Ctl* ctl, double* dpart, cudaStream_t st) {
     constexpr int CW = TimeCfg<T, NT>::CW;
     int grid = (nspace + 2 * CW - 1) / (2 * CW);
     k_time_inv<T, NT, 0><<<grid, TimeCfg<T, NT>::NTH, TimeCfg<T, NT>::SMEM, st>>>(nspace, S, twt, ginv, nullptr, out,
-                                                                                  nullptr, acc, ctl);
+                                                                                  nullptr, acc, ctl, dpart);
 }
 template <int NT>
 static void time_inv_ff_nt(int nspace, const float2* S, const float2* twt, const float* ginvf, float2* Uff,
-                           const Ctl* ctl, cudaStream_t st) {
+                           const Ctl* ctl, double* dpart, cudaStream_t st) {
     constexpr int CW = TimeCfg<float, NT>::CW;
     int grid = (nspace + 2 * CW - 1) / (2 * CW);
     k_time_inv<float, NT, 1><<<grid, TimeCfg<float, NT>::NTH, TimeCfg<float, NT>::SMEM, st>>>(
-        nspace, S, twt, nullptr, ginvf, nullptr, Uff, 1, ctl);
+        nspace, S, twt, nullptr, ginvf, nullptr, Uff, 1, ctl, dpart);
+}
+
+int time_inv_blocks(int nt, int nspace, int f32) {
+    int cw = 32;
+    switch (nt) {
+#define CW_(N) case N: cw = f32 ? TimeCfg<float, N>::CW : TimeCfg<double, N>::CW; break;
+        CW_(2) CW_(4) CW_(8) CW_(16) CW_(32) CW_(64) CW_(128) CW_(256) CW_(512) CW_(1024)
+#undef CW_
+        default: break;
+    }
+    return (nspace + 2 * cw - 1) / (2 * cw);
 }
 
 #define PINT_NT_SWITCH(CALL)                                                                            \
@@ -181,16 +229,16 @@ cudaError_t launch_time_fwd(int nt, int nspace, const T* s, c_t<T>* S, const c_t
 }
 template <class T>
 cudaError_t launch_time_inv(int nt, int nspace, const c_t<T>* S, const c_t<T>* twt, const double* ginv, double* out,
-                            int accumulate, const Ctl* ctl, cudaStream_t st) {
-#define CALL(N) time_inv_nt<T, N>(nspace, S, twt, ginv, out, accumulate, ctl, st)
+                            int accumulate, const Ctl* ctl, double* dpart, cudaStream_t st) {
+#define CALL(N) time_inv_nt<T, N>(nspace, S, twt, ginv, out, accumulate, ctl, dpart, st)
     PINT_NT_SWITCH(CALL)
 #undef CALL
     return cudaGetLastError();
 }
 
 cudaError_t launch_time_inv_ff(int nt, int nspace, const float2* S, const float2* twt, const float* ginvf,
-                               float2* Uff, const Ctl* ctl, cudaStream_t st) {
-#define CALL(N) time_inv_ff_nt<N>(nspace, S, twt, ginvf, Uff, ctl, st)
+                               float2* Uff, const Ctl* ctl, double* dpart, cudaStream_t st) {
+#define CALL(N) time_inv_ff_nt<N>(nspace, S, twt, ginvf, Uff, ctl, dpart, st)
     PINT_NT_SWITCH(CALL)
 #undef CALL
     return cudaGetLastError();
@@ -200,8 +248,8 @@ template cudaError_t launch_time_fwd<float>(int, int, const float*, float2*, con
 template cudaError_t launch_time_fwd<double>(int, int, const double*, double2*, const double2*, const Ctl*,
                                              cudaStream_t);
 template cudaError_t launch_time_inv<float>(int, int, const float2*, const float2*, const double*, double*, int,
-                                            const Ctl*, cudaStream_t);
+                                            const Ctl*, double*, cudaStream_t);
 template cudaError_t launch_time_inv<double>(int, int, const double2*, const double2*, const double*, double*, int,
-                                             const Ctl*, cudaStream_t);
+                                             const Ctl*, double*, cudaStream_t);
 
 }  // namespace pint

@@ -10,8 +10,11 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <complex>
+#include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "../../include/pint.h"
@@ -60,6 +63,7 @@ static int validate(const pint_problem* p) {
     if (p->equation != PINT_BIHARMONIC && !(p->eps > 0.0)) return PINT_EINVAL;
     if (!isfinite(p->beta) || !isfinite(p->eps)) return PINT_EINVAL;
     if (p->init_guess < 0 || p->init_guess > 2) return PINT_EINVAL;
+    if (!(p->tol_update >= 0.0) || !isfinite(p->tol_update)) return PINT_EINVAL;
     const int ny = p->dim == 2 ? p->ny : 1;
     if (!axis_fft(p->nx, p->bc, 4096) && p->nx > 1024) return PINT_EINVAL;
     if (p->dim == 2 && !axis_fft(ny, p->bc, 1024) && ny > 1024) return PINT_EINVAL;
@@ -78,6 +82,35 @@ static double lap_eig(int p, int n, int bc) {
 
 static bool f32_transforms(const pint_problem* p) { return p->precision != PINT_FP64; }
 
+// Pinned host mirrors of the device control blocks, carved from one page-locked
+// slab per process (page-locking per handle would be slow and would serialize
+// with work already running on the device).
+static std::mutex g_slab_mu;
+static Ctl* g_slab = nullptr;
+static std::vector<Ctl*> g_slab_free;
+static const int kSlabCtls = 1024;
+
+static Ctl* ctl_slab_acquire() {
+    std::lock_guard<std::mutex> lock(g_slab_mu);
+    if (!g_slab) {
+        if (cudaHostAlloc((void**)&g_slab, sizeof(Ctl) * kSlabCtls, cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();
+            g_slab = nullptr;
+            return nullptr;
+        }
+        for (int i = kSlabCtls - 1; i >= 0; --i) g_slab_free.push_back(g_slab + i);
+    }
+    if (g_slab_free.empty()) return nullptr;
+    Ctl* c = g_slab_free.back();
+    g_slab_free.pop_back();
+    return c;
+}
+static void ctl_slab_release(Ctl* c) {
+    if (!c) return;
+    std::lock_guard<std::mutex> lock(g_slab_mu);
+    g_slab_free.push_back(c);
+}
+
 struct Sizes {
     size_t nspace, dof, nk, partials, tables_T, tables_bytes;
 };
@@ -89,6 +122,7 @@ template <class T> struct Impl;
 struct pint_handle {
     pint_problem p;
     cudaStream_t st;
+    int device = 0;                 // device current at pint_create
     int fft_x, fft_y;
     pint::Geo geo;
     pint::SolveCoef coef;
@@ -96,6 +130,7 @@ struct pint_handle {
     pint::Ctl* hctl = nullptr;      // pinned host mirror
     double* partials = nullptr;
     int npart = 0;
+    double* dpart = nullptr;        // per-CTA (sum delta^2, sum U^2) of the last correction
     double* gam = nullptr;          // alpha^{n/nt}
     double* ginv = nullptr;         // alpha^{-n/nt} / nt
     double* u0buf = nullptr;        // window initial condition
@@ -235,7 +270,7 @@ static int build_tables(pint_handle* h) {
         cset(L.lam1, k, (1.0 - z) / dt);
         cset(L.lam2, k, p->theta + (1.0 - p->theta) * z);
     }
-    if (cudaMemcpy(h->tab, host.data(), L.total * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+    if (cudaMemcpyAsync(h->tab, host.data(), L.total * sizeof(T), cudaMemcpyHostToDevice, h->st) != cudaSuccess)
         return PINT_ECUDA;
     Tabs<T>* tb = new (std::nothrow) Tabs<T>;
     if (!tb) return PINT_ENOMEM;
@@ -260,13 +295,13 @@ static int build_tables(pint_handle* h) {
         g[n] = pow(p->alpha, (double)n / nt);
         gi[n] = pow(p->alpha, -(double)n / nt) / nt;
     }
-    if (cudaMemcpy(h->gam, g.data(), nt * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) return PINT_ECUDA;
-    if (cudaMemcpy(h->ginv, gi.data(), nt * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) return PINT_ECUDA;
+    if (cudaMemcpyAsync(h->gam, g.data(), nt * sizeof(double), cudaMemcpyHostToDevice, h->st) != cudaSuccess) return PINT_ECUDA;
+    if (cudaMemcpyAsync(h->ginv, gi.data(), nt * sizeof(double), cudaMemcpyHostToDevice, h->st) != cudaSuccess) return PINT_ECUDA;
     if (h->gamf) {
         std::vector<float> gf(nt), gif(nt);
         for (int n = 0; n < nt; ++n) { gf[n] = (float)g[n]; gif[n] = (float)gi[n]; }
-        if (cudaMemcpy(h->gamf, gf.data(), nt * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) return PINT_ECUDA;
-        if (cudaMemcpy(h->ginvf, gif.data(), nt * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+        if (cudaMemcpyAsync(h->gamf, gf.data(), nt * sizeof(float), cudaMemcpyHostToDevice, h->st) != cudaSuccess) return PINT_ECUDA;
+        if (cudaMemcpyAsync(h->ginvf, gif.data(), nt * sizeof(float), cudaMemcpyHostToDevice, h->st) != cudaSuccess)
             return PINT_ECUDA;
     }
     return PINT_OK;
@@ -287,7 +322,7 @@ static int build_levels(pint_handle* h) {
         const size_t nk = L / 2 + 1;
         const size_t tbytes = (2 * L + 4 * nk) * sizeof(T);
         const size_t bytes = tbytes + 2 * L * sizeof(double) + 2 * L * sizeof(float) + 256;
-        if (cudaMalloc(&lv.block, bytes) != cudaSuccess) { cudaGetLastError(); return PINT_ENOMEM; }
+        if (cudaMallocAsync(&lv.block, bytes, h->st) != cudaSuccess) { cudaGetLastError(); return PINT_ENOMEM; }
         h->bytes += (long long)bytes;
         std::vector<T> t(2 * L + 4 * nk);
         for (int j = 0; j < L; ++j) { auto z = expi(-(double)j / L); t[2 * j] = (T)z.real(); t[2 * j + 1] = (T)z.imag(); }
@@ -311,11 +346,11 @@ static int build_levels(pint_handle* h) {
         char* b = reinterpret_cast<char*>(lv.block);
         const size_t o_g = (tbytes + 15) / 16 * 16, o_gi = o_g + L * sizeof(double), o_gf = o_gi + L * sizeof(double),
                      o_gif = o_gf + L * sizeof(float);
-        if (cudaMemcpy(b, t.data(), tbytes, cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(b + o_g, g.data(), L * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(b + o_gi, gi.data(), L * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(b + o_gf, gf.data(), L * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(b + o_gif, gif.data(), L * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+        if (cudaMemcpyAsync(b, t.data(), tbytes, cudaMemcpyHostToDevice, h->st) != cudaSuccess ||
+            cudaMemcpyAsync(b + o_g, g.data(), L * sizeof(double), cudaMemcpyHostToDevice, h->st) != cudaSuccess ||
+            cudaMemcpyAsync(b + o_gi, gi.data(), L * sizeof(double), cudaMemcpyHostToDevice, h->st) != cudaSuccess ||
+            cudaMemcpyAsync(b + o_gf, gf.data(), L * sizeof(float), cudaMemcpyHostToDevice, h->st) != cudaSuccess ||
+            cudaMemcpyAsync(b + o_gif, gif.data(), L * sizeof(float), cudaMemcpyHostToDevice, h->st) != cudaSuccess)
             return PINT_ECUDA;
         Tabs<T>* tb = new (std::nothrow) Tabs<T>(*base);
         if (!tb) return PINT_ENOMEM;
@@ -411,6 +446,7 @@ static long long footprint_of(const pint_problem* p) {
     long long b = 0;
     b += sizeof(Ctl);
     b += z.partials * 2 * sizeof(double);
+    b += (z.nspace / 16 + 2) * 2 * sizeof(double);
     b += 2 * (size_t)p->nt * sizeof(double);
     b += z.nspace * sizeof(double);
     b += z.dof * ts;                 // s
@@ -474,7 +510,8 @@ template <class T> struct Impl {
         int gx, gy, gz, chunk;
         const int np = residual_grid(g, gx, gy, gz, chunk);
         prof_begin(h, PH_CHECK);
-        launch_after_residual(h->partials, np, 1.0 / ((double)g.nt * g.nspace), h->ctl, h->st, h->gcond, h->capturing);
+        launch_after_residual(h->partials, np, 1.0 / ((double)g.nt * g.nspace), h->ctl, h->st, h->gcond, h->capturing,
+                              h->dpart, time_inv_blocks(g.nt, g.nspace, f32_transforms(&h->p)));
         prof_end(h, PH_CHECK, 1);
         prof_begin(h, PH_TFWD);
         cudaError_t e = launch_time_fwd<T>(g.nt, g.nspace, s, S, tb.twt, h->ctl, h->st);
@@ -482,7 +519,7 @@ template <class T> struct Impl {
         if (e != cudaSuccess) return e;
         if ((e = spatial(h, S, tb)) != cudaSuccess) return e;
         prof_begin(h, PH_TINV);
-        e = launch_time_inv<T>(g.nt, g.nspace, S, tb.twt, h->ginv, U, 1, h->ctl, h->st);
+        e = launch_time_inv<T>(g.nt, g.nspace, S, tb.twt, h->ginv, U, 1, h->ctl, h->dpart, h->st);
         prof_end(h, PH_TINV, 1);
         if (e != cudaSuccess) return e;
         return cudaGetLastError();
@@ -497,7 +534,7 @@ template <class T> struct Impl {
         cudaError_t e = launch_time_fwd<T>(g.nt, g.nspace, s, S, tb.twt, h->ctl, h->st);
         if (e != cudaSuccess) return e;
         if ((e = spatial(h, S, tb)) != cudaSuccess) return e;
-        e = launch_time_inv<T>(g.nt, g.nspace, S, tb.twt, h->ginv, delta, 0, h->ctl, h->st);
+        e = launch_time_inv<T>(g.nt, g.nspace, S, tb.twt, h->ginv, delta, 0, h->ctl, nullptr, h->st);
         if (e != cudaSuccess) return e;
         return cudaGetLastError();
     }
@@ -518,15 +555,15 @@ static cudaError_t zero_start(pint_handle* h, double* U, const double* u0w) {
         if ((e = Impl<float>::spatial(h, reinterpret_cast<float2*>(h->S), tb)) != cudaSuccess) return e;
         prof_begin(h, PH_TINV);
         if (h->p.precision == PINT_MIXED_FF)
-            e = launch_time_inv_ff(g.nt, g.nspace, reinterpret_cast<float2*>(h->S), tb.twt, h->ginvf, h->Uff_cur, h->ctl, h->st);
+            e = launch_time_inv_ff(g.nt, g.nspace, reinterpret_cast<float2*>(h->S), tb.twt, h->ginvf, h->Uff_cur, h->ctl, h->dpart, h->st);
         else
-            e = launch_time_inv<float>(g.nt, g.nspace, reinterpret_cast<float2*>(h->S), tb.twt, h->ginv, U, 1, h->ctl, h->st);
+            e = launch_time_inv<float>(g.nt, g.nspace, reinterpret_cast<float2*>(h->S), tb.twt, h->ginv, U, 1, h->ctl, h->dpart, h->st);
         prof_end(h, PH_TINV, 1);
     } else {
         const Tabs<double>& tb = tabs_of<double>(h);
         if ((e = Impl<double>::spatial(h, reinterpret_cast<double2*>(h->S), tb)) != cudaSuccess) return e;
         prof_begin(h, PH_TINV);
-        e = launch_time_inv<double>(g.nt, g.nspace, reinterpret_cast<double2*>(h->S), tb.twt, h->ginv, U, 1, h->ctl, h->st);
+        e = launch_time_inv<double>(g.nt, g.nspace, reinterpret_cast<double2*>(h->S), tb.twt, h->ginv, U, 1, h->ctl, h->dpart, h->st);
         prof_end(h, PH_TINV, 1);
     }
     if (e != cudaSuccess) return e;
@@ -545,7 +582,8 @@ static cudaError_t iteration_ff(pint_handle* h) {
     int gx, gy, gz, chunk;
     const int np = residual_ff_grid(g, gx, gy, gz, chunk);
     prof_begin(h, PH_CHECK);
-    launch_after_residual(h->partials, np, 1.0 / ((double)g.nt * g.nspace), h->ctl, h->st, h->gcond, h->capturing);
+    launch_after_residual(h->partials, np, 1.0 / ((double)g.nt * g.nspace), h->ctl, h->st, h->gcond, h->capturing,
+                              h->dpart, time_inv_blocks(g.nt, g.nspace, f32_transforms(&h->p)));
     prof_end(h, PH_CHECK, 1);
     prof_begin(h, PH_TFWD);
     cudaError_t e = launch_time_fwd<float>(g.nt, g.nspace, s, S, tb.twt, h->ctl, h->st);
@@ -553,7 +591,7 @@ static cudaError_t iteration_ff(pint_handle* h) {
     if (e != cudaSuccess) return e;
     if ((e = Impl<float>::spatial(h, S, tb)) != cudaSuccess) return e;
     prof_begin(h, PH_TINV);
-    e = launch_time_inv_ff(g.nt, g.nspace, S, tb.twt, h->ginvf, h->Uff_cur, h->ctl, h->st);
+    e = launch_time_inv_ff(g.nt, g.nspace, S, tb.twt, h->ginvf, h->Uff_cur, h->ctl, h->dpart, h->st);
     prof_end(h, PH_TINV, 1);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
@@ -684,27 +722,31 @@ long long pint_footprint(const pint_problem* p) {
 
 void pint_destroy(pint_handle* h) {
     if (!h) return;
-    cudaFree(h->ctl);
-    cudaFreeHost(h->hctl);
-    cudaFree(h->partials);
+    // stream-ordered frees: destroying a handle does not wait for the whole device
+    cudaStream_t fs = h->st;
+    auto af = [&](void* q) { if (q) cudaFreeAsync(q, fs); };
+    af(h->ctl);
+    ctl_slab_release(h->hctl);
+    af(h->partials);
+    af(h->dpart);
     if (h->nlev > 0) activate_level(h, 0);   // the base level owns gam/ginv/gamf/ginvf and tabs_ptrs
     for (int i = 1; i < h->nlev; ++i) {
-        cudaFree(h->lev[i].block);
+        af(h->lev[i].block);
         if (f32_transforms(&h->p)) delete reinterpret_cast<Tabs<float>*>(h->lev[i].tabs);
         else delete reinterpret_cast<Tabs<double>*>(h->lev[i].tabs);
     }
-    cudaFree(h->gam);
-    cudaFree(h->ginv);
-    cudaFree(h->u0buf);
-    cudaFree(h->hU);
-    cudaFree(h->hu0);
-    cudaFree(h->s);
-    cudaFree(h->S);
-    cudaFree(h->tab);
-    cudaFree(h->Uff);
-    cudaFree(h->u0ff);
-    cudaFree(h->gamf);
-    cudaFree(h->ginvf);
+    af(h->gam);
+    af(h->ginv);
+    af(h->u0buf);
+    af(h->hU);
+    af(h->hu0);
+    af(h->s);
+    af(h->S);
+    af(h->tab);
+    af(h->Uff);
+    af(h->u0ff);
+    af(h->gamf);
+    af(h->ginvf);
     for (int i = 0; i < 2 * pint_handle::NEV; ++i)
         if (h->ev[i]) cudaEventDestroy(h->ev[i]);
     for (auto& sl : h->gslot)
@@ -727,10 +769,14 @@ int pint_create(const pint_problem* p, void* cuda_stream, pint_handle** out) {
     if (!h) return PINT_ENOMEM;
     h->p = *p;
     h->st = (cudaStream_t)cuda_stream;
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        delete h;
+        return PINT_ECUDA;
+    }
     Sizes z = sizes_of(p, h);
     const size_t ts = f32_transforms(p) ? 4 : 8;
     auto dalloc = [&](void** ptr, size_t bytes) -> int {
-        if (cudaMalloc(ptr, bytes < 16 ? 16 : bytes) != cudaSuccess) {
+        if (cudaMallocAsync(ptr, bytes < 16 ? 16 : bytes, h->st) != cudaSuccess) {
             cudaGetLastError();
             return PINT_ENOMEM;
         }
@@ -740,6 +786,7 @@ int pint_create(const pint_problem* p, void* cuda_stream, pint_handle** out) {
     rc = PINT_OK;
     if (!rc) rc = dalloc((void**)&h->ctl, sizeof(Ctl));
     if (!rc) rc = dalloc((void**)&h->partials, z.partials * 2 * sizeof(double));
+    if (!rc) rc = dalloc((void**)&h->dpart, (z.nspace / 16 + 2) * 2 * sizeof(double));
     if (!rc) rc = dalloc((void**)&h->gam, p->nt * sizeof(double));
     if (!rc) rc = dalloc((void**)&h->ginv, p->nt * sizeof(double));
     if (!rc) rc = dalloc((void**)&h->u0buf, z.nspace * sizeof(double));
@@ -752,9 +799,9 @@ int pint_create(const pint_problem* p, void* cuda_stream, pint_handle** out) {
         if (!rc) rc = dalloc((void**)&h->gamf, p->nt * sizeof(float));
         if (!rc) rc = dalloc((void**)&h->ginvf, p->nt * sizeof(float));
     }
-    if (!rc && cudaMallocHost((void**)&h->hctl, sizeof(Ctl)) != cudaSuccess) rc = PINT_ENOMEM;
+    if (!rc && !(h->hctl = ctl_slab_acquire())) rc = PINT_ENOMEM;
     if (!rc) rc = f32_transforms(p) ? build_tables<float>(h) : build_tables<double>(h);
-    if (!rc && cudaMemset(h->ctl, 0, sizeof(Ctl)) != cudaSuccess) rc = PINT_ECUDA;
+    if (!rc && cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->st) != cudaSuccess) rc = PINT_ECUDA;
     if (rc) {
         pint_destroy(h);
         return rc;
@@ -857,6 +904,7 @@ static int choose_level(pint_handle* h, int lmax, double jbar0) {
 
 int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* st) {
     if (!h || !u0_dev || !U_dev) return PINT_EINVAL;
+    PINT_CK(cudaSetDevice(h->device));
     const pint_problem& p = h->p;
     const Geo& g = h->geo;
     const bool ffm = p.precision == PINT_MIXED_FF;
@@ -884,7 +932,7 @@ int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* 
             // is at most the largest power of two dividing base
             const int lmax = base == 0 ? ntmax : (base & -base);
             activate_level(h, 0);
-            launch_begin_window(u0w, g.nspace, g.inv_dt, p.max_iter, p.tol, h->partials, h->ctl, h->st);
+            launch_begin_window(u0w, g.nspace, g.inv_dt, p.max_iter, p.tol, h->partials, h->ctl, h->st, p.tol_update);
             if ((rc = read_ctl(h)) != PINT_OK) return rc;
             const double rms = h->hctl->bnorm * g.dt;          // ||u0||_2
             li = choose_level(h, lmax, 3.0 * rms * rms / (double)ns);
@@ -909,7 +957,7 @@ int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* 
                 else launch_broadcast(Useg, u0w, g.nspace, L, h->st);
                 nl++;
             }
-            launch_begin_window(u0w, g.nspace, g.inv_dt, p.max_iter, p.tol, h->partials, h->ctl, h->st);
+            launch_begin_window(u0w, g.nspace, g.inv_dt, p.max_iter, p.tol, h->partials, h->ctl, h->st, p.tol_update);
             prof_end(h, PH_SETUP, nl + 1);
             cudaGraphExec_t gx = (h->use_graphs && !h->prof_on && !adapt) ? get_graph(h, Useg, u0w) : nullptr;
             if (gx) {
@@ -955,6 +1003,7 @@ int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* 
         S.segments = seg + 1;
         if (L < S.nt_min) S.nt_min = L;
         S.rel_residual = c.rho;
+        S.update_norm = p.tol_update > 0.0 ? c.dnorm : 0.0;
         S.jbar = h->coef.ch ? c.jbar : 0.0;
         for (int i = 0; i <= k && i < PINT_HIST_MAX; ++i) S.hist[i] = c.hist[i];
         S.contraction = k >= 2 ? pow(c.hist[k] / c.hist[1], 1.0 / (k - 1)) : (k == 1 ? c.hist[1] / c.hist[0] : 0.0);
@@ -986,12 +1035,35 @@ int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* 
     return rc;
 }
 
+int pint_solve_batch(pint_handle* const* hs, int n, const double* const* u0s, double* const* Us, pint_stats* st,
+                     int* rcs) {
+    if (n < 0 || (n > 0 && (!hs || !u0s || !Us))) return PINT_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!hs[i] || !u0s[i] || !Us[i]) return PINT_EINVAL;
+    std::vector<int> rc(n, PINT_OK);
+    std::atomic<int> next{0};
+    auto work = [&]() {
+        for (int i; (i = next.fetch_add(1)) < n;) rc[i] = pint_solve(hs[i], u0s[i], Us[i], st ? &st[i] : nullptr);
+    };
+    const int workers = n < 64 ? n : 64;
+    std::vector<std::thread> th;
+    for (int w = 1; w < workers; ++w) th.emplace_back(work);
+    if (n > 0) work();
+    for (auto& t : th) t.join();
+    int first = PINT_OK;
+    for (int i = 0; i < n; ++i) {
+        if (rcs) rcs[i] = rc[i];
+        if (first == PINT_OK && rc[i] != PINT_OK) first = rc[i];
+    }
+    return first;
+}
+
 int pint_solve_host(pint_handle* h, const double* u0_host, double* U_host, pint_stats* st) {
     if (!h || !u0_host || !U_host) return PINT_EINVAL;
     const size_t ns = (size_t)h->geo.nspace, dof = ns * h->geo.nt;
     if (!h->hU) {
-        if (cudaMalloc((void**)&h->hU, dof * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return PINT_ENOMEM; }
-        if (cudaMalloc((void**)&h->hu0, ns * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return PINT_ENOMEM; }
+        if (cudaMallocAsync((void**)&h->hU, dof * sizeof(double), h->st) != cudaSuccess) { cudaGetLastError(); return PINT_ENOMEM; }
+        if (cudaMallocAsync((void**)&h->hu0, ns * sizeof(double), h->st) != cudaSuccess) { cudaGetLastError(); return PINT_ENOMEM; }
     }
     PINT_CK(cudaMemcpyAsync(h->hu0, u0_host, ns * sizeof(double), cudaMemcpyHostToDevice, h->st));
     if (h->p.init_guess == 1)

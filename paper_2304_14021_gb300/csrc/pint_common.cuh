@@ -188,7 +188,10 @@ struct Ctl {
     double jbar;      // mean(3u^2) of the current iterate (Cahn-Hilliard)
     double sum_r2;
     double sum_u2;
+    double tol_update;  // > 0: also stop when ||delta||_2 / ||U||_2 <= tol_update
+    double dnorm;       // ||delta||_2 / ||U||_2 of the last correction
     double hist[256];
+    double dhist[256];  // dnorm per iteration (when the update-size test is on)
 };
 
 // Geometry and coefficients of one problem (by value into kernels).

@@ -47,16 +47,18 @@ void launch_f64_to_ff(const double* in, float2* out, size_t n, cudaStream_t st);
 void launch_ff_to_f64(const float2* in, double* out, size_t n, cudaStream_t st);
 void launch_broadcast_ff(float2* U, const float2* u0, int nspace, int nt, cudaStream_t st);
 cudaError_t launch_time_inv_ff(int nt, int nspace, const float2* S, const float2* twt, const float* ginvf,
-                               float2* Uff, const Ctl* ctl, cudaStream_t st);
+                               float2* Uff, const Ctl* ctl, double* dpart, cudaStream_t st);
 template <class TS>
 void launch_residual(const Geo& g, const double* U, const double* u0, const double* gam, double* r_out, TS* s_out,
                      double* partials, const Ctl* ctl, cudaStream_t st);
 int norm2_blocks(int n);
 void launch_begin_window(const double* u0, int nspace, double inv_dt, int max_iter, double tol, double* partials,
-                         Ctl* ctl, cudaStream_t st);
+                         Ctl* ctl, cudaStream_t st, double tol_update = 0.0);
 // cond / use_cond: CUDA-graph while-loop condition handle (see pint_api.cu).
+// dpart/ndp: the last correction's (sum delta^2, sum U^2) partials (ndp = 0: none).
 void launch_after_residual(const double* partials, int np, double inv_dof, Ctl* ctl, cudaStream_t st,
-                           unsigned long long cond = 0, int use_cond = 0);
+                           unsigned long long cond = 0, int use_cond = 0, const double* dpart = nullptr,
+                           int ndp = 0);
 void launch_residual_norm(const double* partials, int np, Ctl* ctl, cudaStream_t st);
 void launch_set_running(Ctl* ctl, double jbar, cudaStream_t st);
 void launch_broadcast(double* U, const double* u0, int nspace, int nt, cudaStream_t st);
@@ -69,9 +71,11 @@ cudaError_t launch_time_fwd(int nt, int nspace, const T* s, c_t<T>* S, const c_t
                             cudaStream_t st);
 // Step 3: delta_n = ginv[n] * Re( sum_k S[k] exp(+2 pi i nk/nt) ) over the full
 // Hermitian spectrum; U += delta (accumulate) or out = delta.
+// dpart (may be NULL): per-CTA (sum delta^2, sum U^2) pairs, time_inv_blocks() of them.
 template <class T>
 cudaError_t launch_time_inv(int nt, int nspace, const c_t<T>* S, const c_t<T>* twt, const double* ginv, double* out,
-                            int accumulate, const Ctl* ctl, cudaStream_t st);
+                            int accumulate, const Ctl* ctl, double* dpart, cudaStream_t st);
+int time_inv_blocks(int nt, int nspace, int f32);
 // Step 2: per frequency k, S[k] <- (lambda_1k I + lambda_2k A)^{-1} S[k], in
 // stages: 1-D: stage 0 = fused transform/divide/inverse along x.  2-D: stage 0
 // = forward along x, 1 = fused along y (with the division), 2 = inverse along x.

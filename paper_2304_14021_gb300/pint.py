@@ -28,20 +28,20 @@ class Problem(C.Structure):
     _fields_ = [("equation", C.c_int), ("dim", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("bc", C.c_int),
                 ("eps", C.c_double), ("beta", C.c_double), ("T", C.c_double), ("nt", C.c_int),
                 ("n_windows", C.c_int), ("theta", C.c_double), ("alpha", C.c_double), ("tol", C.c_double),
-                ("max_iter", C.c_int), ("precision", C.c_int), ("init_guess", C.c_int)]
+                ("max_iter", C.c_int), ("precision", C.c_int), ("init_guess", C.c_int), ("tol_update", C.c_double)]
 
 
 class Stats(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("windows", C.c_int), ("iters_last", C.c_int),
                 ("rel_residual", C.c_double), ("contraction", C.c_double), ("jbar", C.c_double),
                 ("hist", C.c_double * HIST_MAX), ("segments", C.c_int), ("nt_min", C.c_int),
-                ("retries", C.c_int)]
+                ("retries", C.c_int), ("update_norm", C.c_double)]
 
     def as_dict(self) -> dict:
         return {"status": self.status, "iters": self.iters, "windows": self.windows,
                 "iters_last": self.iters_last, "rel_residual": self.rel_residual,
                 "contraction": self.contraction, "jbar": self.jbar, "segments": self.segments,
-                "nt_min": self.nt_min, "retries": self.retries,
+                "nt_min": self.nt_min, "retries": self.retries, "update_norm": self.update_norm,
                 "hist": [self.hist[i] for i in range(min(self.iters_last + 1, HIST_MAX))]}
 
 
@@ -90,6 +90,9 @@ def lib() -> C.CDLL:
         L.pint_set_option.restype = C.c_int
         L.pint_residual_static.argtypes = [C.POINTER(Problem), vp, vp, vp, vp, vp]
         L.pint_residual_static.restype = C.c_int
+        L.pint_solve_batch.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(Stats),
+                                       C.POINTER(C.c_int)]
+        L.pint_solve_batch.restype = C.c_int
         L.pint_destroy.argtypes = [vp]
         L.pint_destroy.restype = None
         L.pint_strerror.argtypes = [C.c_int]
@@ -107,13 +110,13 @@ def strerror(code: int) -> str:
 
 def make_problem(equation="biharmonic", dim=1, nx=64, ny=1, bc="ss", eps=1.0, beta=0.0, T=0.01, nt=32,
                  n_windows=1, theta=1.0, alpha=1e-2, tol=1e-10, max_iter=100, precision="fp64",
-                 init_guess=0) -> Problem:
+                 init_guess=0, tol_update=0.0) -> Problem:
     eq = EQUATIONS.get(equation, equation)
     b = BCS.get(bc, bc)
     pr = PRECISIONS.get(precision, precision)
     return Problem(int(eq), int(dim), int(nx), int(ny if dim == 2 else 1), int(b), float(eps), float(beta),
                    float(T), int(nt), int(n_windows), float(theta), float(alpha), float(tol), int(max_iter),
-                   int(pr), int(init_guess))
+                   int(pr), int(init_guess), float(tol_update))
 
 
 def footprint(**kw) -> int:
@@ -145,6 +148,24 @@ def _ptr(t) -> int:
     if not t.is_cuda or str(t.dtype) != "torch.float64" or not t.is_contiguous():
         raise ValueError("expected a contiguous float64 CUDA tensor")
     return t.data_ptr()
+
+
+def solve_batch(solvers, u0s, Us) -> list[dict]:
+    """pint_solve_batch over independent Solvers (give each its own stream to
+    overlap them on the GPU).  Returns the per-instance stats (with "rc")."""
+    n = len(solvers)
+    hs = (C.c_void_p * n)(*[s._h.value for s in solvers])
+    a0 = (C.c_void_p * n)(*[_ptr(u) for u in u0s])
+    aU = (C.c_void_p * n)(*[_ptr(U) for U in Us])
+    st = (Stats * n)()
+    rcs = (C.c_int * n)()
+    lib().pint_solve_batch(hs, n, a0, aU, st, rcs)
+    out = []
+    for i in range(n):
+        d = st[i].as_dict()
+        d["rc"] = rcs[i]
+        out.append(d)
+    return out
 
 
 class Solver:

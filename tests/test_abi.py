@@ -37,8 +37,8 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_struct_sizes_match_header_layout(lib):
     # pint_problem: 5 ints (+4 pad), 3 doubles, 2 ints, 3 doubles, 3 ints (+4 pad)
-    assert C.sizeof(pint.Problem) == 24 + 24 + 8 + 24 + 16
-    assert C.sizeof(pint.Stats) == 16 + 3 * 8 + 256 * 8 + 16
+    assert C.sizeof(pint.Problem) == 24 + 24 + 8 + 24 + 16 + 8
+    assert C.sizeof(pint.Stats) == 16 + 3 * 8 + 256 * 8 + 16 + 8
 
 
 def test_strerror(lib):
@@ -51,7 +51,7 @@ def test_strerror(lib):
 BAD = [dict(dim=3), dict(nx=1), dict(nt=48), dict(nt=2048), dict(nt=1), dict(alpha=0.0), dict(alpha=1.0),
        dict(theta=0.5), dict(tol=0.0), dict(max_iter=0), dict(max_iter=256), dict(precision=7),
        dict(T=-1.0), dict(equation=5), dict(bc=3), dict(n_windows=0), dict(nx=2000, bc="ss"),
-       dict(equation="linear_ch", eps=0.0), dict(init_guess=3), dict(dim=2, ny=1)]
+       dict(equation="linear_ch", eps=0.0), dict(init_guess=3), dict(dim=2, ny=1), dict(tol_update=-1.0)]
 
 
 @pytest.mark.parametrize("bad", BAD)

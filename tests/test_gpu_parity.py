@@ -319,3 +319,37 @@ def test_adaptive_policy_keeps_full_windows_when_stable():
         st = s.solve(dev(u0), U)
     assert st["segments"] == 2 and st["nt_min"] == 64
     assert O.rel_err(host(U), O.sequential(p, u0)[-64:]) < 1e-8
+
+
+def modal_sequential_neumann_1d(n, dt, nt, u0):
+    """Backward Euler for u' = -Lap_h^2 u on n cells (Neumann) in the cosine
+    eigenbasis, closed form: mode p is multiplied by 1/(1 + dt lambda_p^2) per step."""
+    j, k = np.arange(n), np.arange(n)
+    C = np.cos(np.pi * np.outer(k, j + 0.5) / n)
+    w = np.where(k == 0, 1.0 / n, 2.0 / n)
+    lam = -4.0 * n * n * np.sin(np.pi * k / (2 * n)) ** 2
+    c = C @ u0
+    out = np.empty((nt, n))
+    for m in range(nt):
+        c = c / (1.0 + dt * lam ** 2)
+        out[m] = (w * c) @ C
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_ff"])
+def test_update_size_stop_for_very_stiff_problem(precision):
+    # 1-D biharmonic, 1024 cells, T = 0.1 over 16 steps: dt * max spectrum ~ 1e11, so the
+    # relative residual of any rounded iterate stays far above 1e-8 (the residual test
+    # alone stalls) while the correction shrinks to rounding level.  A banded LU in FP64
+    # is itself only ~cond * eps accurate here, so the reference is the closed-form
+    # modal solution.
+    kw = full(dict(equation="biharmonic", dim=1, nx=1024, bc="neumann", nt=16, T=0.1, precision=precision,
+                   tol=1e-8, max_iter=60))
+    p = oprob(kw)
+    u0 = synth.u0_uniform(p.nspace, -1, 1, 12)
+    U, st = run_solve(kw, u0)
+    assert st["rc"] == pint.PINT_ENOCONV and st["rel_residual"] > 1e-8
+    U2, st2 = run_solve(dict(kw, tol_update=1e-10), u0)
+    assert st2["rc"] == 0 and 0 < st2["update_norm"] <= 1e-10
+    ref = modal_sequential_neumann_1d(1024, p.dt, 16, u0)
+    assert O.rel_err(U2, ref) < (1e-10 if precision == "fp64" else 1e-8)
