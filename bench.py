@@ -89,11 +89,12 @@ def _residual_ff_traffic(workload: str):
 def ff_residual_flops_per_dof(equation: str, dim: int) -> float:
     """FP32 flops per space-time DOF of the float-float residual kernel on square
     cells, counted from its operations (FMA = 2): accurate double-word add 20,
-    double-word multiply 10, cube 20; an unscaled Laplacian point is 2 (1-D) or
-    4 (2-D) adds plus an exact power-of-two scaling (42 / 82 flops).  The first
+    double-word multiply 10, cube 20; an unscaled Laplacian point is one TwoSum
+    chain over 3 (1-D) or 5 (2-D) terms with an FP32 error accumulator plus an
+    exact power-of-two scaling (26 / 42 flops).  The first
     Laplacian (and u^3 for Cahn-Hilliard) is evaluated on the tile plus a
     one-point halo: 514/512 (1-D), 34*18/(32*16) (2-D)."""
-    lap = 42.0 if dim == 1 else 82.0
+    lap = 26.0 if dim == 1 else 42.0
     halo = 514.0 / 512.0 if dim == 1 else (34.0 * 18.0) / (32.0 * 16.0)
     f = lap * halo + lap + 10.0     # Lap u (tile + halo), Lap(Lap u), * c2/h^4
     if equation in ("linear_ch", "cahn_hilliard"):

@@ -44,7 +44,7 @@ extern "C" {
 #define PINT_ENOCONV    -4   /* max_iter reached, or no decrease over three iterations (rounding
                                 floor); U holds the last iterate, stats are filled */
 #define PINT_EDIVERGED  -5   /* residual non-finite, grew by 1e6 over its first value, or
-                                by 10x over three iterations */
+                                grew monotonically and by 10x over three iterations */
 
 typedef enum { PINT_BIHARMONIC = 0, PINT_LINEAR_CH = 1, PINT_CAHN_HILLIARD = 2 } pint_equation;
 

@@ -211,14 +211,16 @@ __global__ void __launch_bounds__(256) k_after_residual(const double* __restrict
         if (k == 0) ctl->rho0 = rho;
         // stagnation: no decrease over the last three corrections (the residual
         // sits at the rounding floor of the iterate's precision)
-        // (growth by 10x over three corrections counts as divergence)
         const double dn = upd ? (W > 0.0 ? sqrt(D / W) : sqrt(D)) : 1.0;
         ctl->dnorm = dn;
         if (k < 256) ctl->dhist[k] = dn;
         // with the update-size test on, a still-shrinking correction is progress too
         const bool d_stalled = !upd || (k >= 4 && dn >= 0.99 * ctl->dhist[k - 3]);
         const bool stalled = k >= 4 && k < 256 && rho >= 0.99 * ctl->hist[k - 3] && d_stalled;
-        const bool growing = k >= 4 && k < 256 && rho >= 0.99 * ctl->hist[k - 3] && rho > 10.0 * ctl->hist[k - 3];
+        // divergence: monotone growth over the last three corrections and 10x overall
+        // (a single jump can be rounding noise at the residual floor)
+        const bool growing = k >= 4 && k < 256 && rho > 10.0 * ctl->hist[k - 3] && rho > ctl->hist[k - 1] &&
+                             ctl->hist[k - 1] > ctl->hist[k - 2] && ctl->hist[k - 2] > ctl->hist[k - 3];
         if (!(rho == rho) || rho > 1e300 || (k > 0 && rho > 1e6 * ctl->rho0) || growing) ctl->status = -5;  // PINT_EDIVERGED
         else if (rho <= ctl->tol || (upd && dn <= ctl->tol_update)) ctl->status = 0;            // PINT_OK
         else if (k >= ctl->max_iter || stalled) ctl->status = -4;                               // PINT_ENOCONV

@@ -5,9 +5,9 @@
 // Same operator and boundary treatment as k_residual.cu (Eq. 2.6 / 4.8 with
 // alpha = 0, theta = 1):
 //   r_n = (u_{n-1} - u_n)/dt - [c2 Lap^2 u_n + c1 Lap u_n + cN Lap(u_n^3)].
-// Every stencil sum is an accurate double-word addition, so the cancellation
-// in the differences of smooth data costs no accuracy beyond ~2^-47 of the
-// result.  Output: s = gamma_n r_n rounded to FP32 (the alpha-scaled input of
+// The stencil sums are error-free in their high words (a TwoSum chain), so the
+// cancellation in the differences of smooth data is resolved to a few 2^-48 of
+// the terms, the same order as the rounding of the stored iterate.  Output: s = gamma_n r_n rounded to FP32 (the alpha-scaled input of
 // Step 1), and per-CTA partial sums of r^2 and u^2.
 #include "ff.cuh"
 #include "pint_common.cuh"
@@ -53,15 +53,48 @@ template <> struct ResTileFF<2> { static constexpr int TX = 32, TY = 16, PPT = 2
 // unscaled (integer coefficients only) and the 1/h^2, 1/h^4 factors are folded
 // into the coefficients c1/h^2, c2/h^4, cN/h^2.  Otherwise each axis is scaled
 // by its own 1/h^2 before the sum.
-template <int DIM, bool SQ>
+// Sum of a few double-word terms: one exact TwoSum chain over the high words,
+// with the chain's rounding errors and all low words gathered in one FP32
+// accumulator, then renormalized.  Cheaper than chained double-word additions
+// (38 vs 82 flops for five terms); its error is a few 2^-48 of the terms'
+// magnitude, about the rounding already present in the stored iterate.
+struct ff_acc {
+    float s, e;
+    __device__ __forceinline__ explicit ff_acc(ff a) : s(a.x), e(a.y) {}
+    __device__ __forceinline__ void add(ff t) {
+        const ff q = two_sum(s, t.x);
+        s = q.x;
+        e = __fadd_rn(e, __fadd_rn(q.y, t.y));
+    }
+    __device__ __forceinline__ ff get() const { return two_sum(s, e); }
+};
+
+// SQ (square cells, hx == hy, and every 1-D grid): the stencil sums are taken
+// unscaled (integer coefficients only) and the 1/h^2, 1/h^4 factors are folded
+// into the coefficients c1/h^2, c2/h^4, cN/h^2.  Otherwise each axis is scaled
+// by its own 1/h^2 before the sum.
+// ACC: chained accurate double-word additions, whose error is relative to the
+// (cancelled) result; used for very stiff problems, where the stencil terms
+// exceed the result by many orders and the cheaper sum's error (relative to
+// the terms) would dominate the residual.
+template <int DIM, bool SQ, bool ACC>
 __device__ __forceinline__ ff lap_ff(const ff* __restrict__ a, int c, int sx, const GeoFF& g) {
-    if constexpr (SQ) {
+    if constexpr (SQ && ACC) {
         ff v = ff_add(a[c - 1], a[c + 1]);
         if constexpr (DIM == 2) {
             v = ff_add(v, a[c - sx]);
             v = ff_add(v, a[c + sx]);
         }
         return ff_add(v, ff_scale2(a[c], DIM == 2 ? -4.f : -2.f));
+    } else if constexpr (SQ) {
+        ff_acc acc(a[c - 1]);
+        acc.add(a[c + 1]);
+        if constexpr (DIM == 2) {
+            acc.add(a[c - sx]);
+            acc.add(a[c + sx]);
+        }
+        acc.add(ff_scale2(a[c], DIM == 2 ? -4.f : -2.f));
+        return acc.get();
     } else {
         ff v = ff_mul(ff_d2(a[c - 1], a[c + 1], a[c]), g.ihx2);
         if constexpr (DIM == 2) v = ff_add(v, ff_mul(ff_d2(a[c - sx], a[c + sx], a[c]), g.ihy2));
@@ -69,7 +102,7 @@ __device__ __forceinline__ ff lap_ff(const ff* __restrict__ a, int c, int sx, co
     }
 }
 
-template <int DIM, bool SQ>
+template <int DIM, bool SQ, bool ACC>
 __global__ void __launch_bounds__(256) k_residual_ff(GeoFF g, const ff* __restrict__ U, const ff* __restrict__ u0,
                                                      const float* __restrict__ gamf, float* __restrict__ s_out,
                                                      double* __restrict__ partials, const Ctl* __restrict__ ctl,
@@ -128,7 +161,7 @@ __global__ void __launch_bounds__(256) k_residual_ff(GeoFF g, const ff* __restri
         for (int e = threadIdx.x; e < LX * LY; e += NTHR) {
             const int ix = e % LX, iy = e / LX;
             const int c = (DIM == 2 ? (iy + 1) * SX : 0) + ix + 1;
-            sL[e] = lap_ff<DIM, SQ>(su, c, SX, g);
+            sL[e] = lap_ff<DIM, SQ, ACC>(su, c, SX, g);
             if (ch) sW[e] = ff_cube(su[c]);
         }
         __syncthreads();
@@ -137,9 +170,9 @@ __global__ void __launch_bounds__(256) k_residual_ff(GeoFF g, const ff* __restri
             if (!inside[q]) continue;
             const ff L = sL[cl[q]];
             const ff u = su[cu[q]];
-            ff A = ff_mul(lap_ff<DIM, SQ>(sL, cl[q], LX, g), g.c2);
+            ff A = ff_mul(lap_ff<DIM, SQ, ACC>(sL, cl[q], LX, g), g.c2);
             if (lin1) A = ff_add(A, ff_mul(L, g.c1));
-            if (ch) A = ff_add(A, ff_mul(lap_ff<DIM, SQ>(sW, cl[q], LX, g), g.cN));
+            if (ch) A = ff_add(A, ff_mul(lap_ff<DIM, SQ, ACC>(sW, cl[q], LX, g), g.cN));
             const ff r = ff_sub(ff_mul(ff_sub(uprev[q], u), g.inv_dt), A);
             const float gm = gamf[n];
             s_out[(size_t)n * g.nspace + pidx[q]] = fmaf(gm, r.x, gm * r.y);
@@ -166,10 +199,25 @@ __global__ void k_f64_to_ff(const double* __restrict__ in, ff* __restrict__ out,
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         out[i] = ff_from_double(in[i]);
 }
+// Exact float -> double by rebuilding the bit pattern on the integer pipes
+// (normal numbers and zero; subnormals, inf and NaN take the conversion
+// instruction).  Leaves one FP64 addition per element for hi + lo.
+__device__ __forceinline__ double f2d_exact(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) {
+        if ((b & 0x7fffffffu) == 0u) return __longlong_as_double((long long)(unsigned long long)(b & 0x80000000u) << 32);
+        return (double)f;
+    }
+    const unsigned long long d = ((unsigned long long)(b & 0x80000000u) << 32) |
+                                 ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(b & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)d);
+}
+
 __global__ void k_ff_to_f64(const ff* __restrict__ in, double* __restrict__ out, size_t n) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const ff v = in[i];
-        out[i] = (double)v.x + (double)v.y;
+        out[i] = f2d_exact(v.x) + f2d_exact(v.y);
     }
 }
 __global__ void k_broadcast_ff(ff* __restrict__ U, const ff* __restrict__ u0, int nspace, int nt) {
@@ -202,12 +250,15 @@ void launch_residual_ff(const GeoFF& g, const Geo& g64, const ff* U, const ff* u
     residual_ff_grid(g64, gx, gy, gz, chunk);
     dim3 grid(gx, gy, gz);
     const bool sq = g64.dim == 1 || g64.ihx2 == g64.ihy2;
+    const bool acc = g.accurate != 0;
+#define PINT_RFF(D, S, A) k_residual_ff<D, S, A><<<grid, 256, 0, st>>>(g, U, u0, gamf, s, partials, ctl, chunk)
     if (g.dim == 2) {
-        if (sq) k_residual_ff<2, true><<<grid, 256, 0, st>>>(g, U, u0, gamf, s, partials, ctl, chunk);
-        else k_residual_ff<2, false><<<grid, 256, 0, st>>>(g, U, u0, gamf, s, partials, ctl, chunk);
+        if (sq) { if (acc) PINT_RFF(2, true, true); else PINT_RFF(2, true, false); }
+        else PINT_RFF(2, false, false);
     } else {
-        k_residual_ff<1, true><<<grid, 256, 0, st>>>(g, U, u0, gamf, s, partials, ctl, chunk);
+        if (acc) PINT_RFF(1, true, true); else PINT_RFF(1, true, false);
     }
+#undef PINT_RFF
 }
 void launch_f64_to_ff(const double* in, ff* out, size_t n, cudaStream_t st) {
     k_f64_to_ff<<<grid_for(n), 256, 0, st>>>(in, out, n);

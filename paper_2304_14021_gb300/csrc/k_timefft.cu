@@ -94,6 +94,7 @@ __global__ void __launch_bounds__(TimeCfg<T, NT>::NTH)
     // dpart != nullptr: per-CTA partial sums (sum delta^2, sum U_new^2) of the
     // correction and the updated iterate, for the update-size stopping test
     float d2 = 0.f, u2 = 0.f;
+    const bool want = dpart != nullptr;
 #pragma unroll 4
     for (int e = tid; e < NT * CW; e += NTH) {
         const int c = e % CW, n = e / CW;
@@ -106,14 +107,18 @@ __global__ void __launch_bounds__(TimeCfg<T, NT>::NTH)
             if (pa < nspace) {
                 const float2 w = ff_add_f(row[pa], da);
                 row[pa] = w;
-                d2 = fmaf(da, da, d2);
-                u2 = fmaf(w.x, w.x, u2);
+                if (want) {
+                    d2 = fmaf(da, da, d2);
+                    u2 = fmaf(w.x, w.x, u2);
+                }
             }
             if (pb < nspace) {
                 const float2 w = ff_add_f(row[pb], db);
                 row[pb] = w;
-                d2 = fmaf(db, db, d2);
-                u2 = fmaf(w.x, w.x, u2);
+                if (want) {
+                    d2 = fmaf(db, db, d2);
+                    u2 = fmaf(w.x, w.x, u2);
+                }
             }
             continue;
         }
@@ -124,21 +129,25 @@ __global__ void __launch_bounds__(TimeCfg<T, NT>::NTH)
             if (pa < nspace) {
                 const double w = row[pa] + da;
                 row[pa] = w;
-                d2 = fmaf((float)da, (float)da, d2);
-                u2 = fmaf((float)w, (float)w, u2);
+                if (want) {
+                    d2 = fmaf((float)da, (float)da, d2);
+                    u2 = fmaf((float)w, (float)w, u2);
+                }
             }
             if (pb < nspace) {
                 const double w = row[pb] + db;
                 row[pb] = w;
-                d2 = fmaf((float)db, (float)db, d2);
-                u2 = fmaf((float)w, (float)w, u2);
+                if (want) {
+                    d2 = fmaf((float)db, (float)db, d2);
+                    u2 = fmaf((float)w, (float)w, u2);
+                }
             }
         } else {
             if (pa < nspace) row[pa] = da;
             if (pb < nspace) row[pb] = db;
         }
     }
-    if (dpart) {  // deterministic block reduction (same tree every launch)
+    if (want) {  // deterministic block reduction (same tree every launch)
         __shared__ double red[2][32];
         double a = warp_sum((double)d2), b = warp_sum((double)u2);
         if (tid % 32 == 0) { red[0][tid / 32] = a; red[1][tid / 32] = b; }

@@ -419,6 +419,11 @@ static void derive(const pint_problem* p, pint_handle* h) {
     f.c2 = ff_from_double(g.c2 * s2);
     f.c1 = ff_from_double(g.c1 * s1);
     f.cN = ff_from_double(g.cN * s1);
+    // stiffness dt * max |spectrum of the spatial operator|: above 1e7 the stencil
+    // sums use chained accurate double-word additions (see k_residual_ff.cu)
+    const double lam_max = 4.0 * g.ihx2 + (g.dim == 2 ? 4.0 * g.ihy2 : 0.0);
+    const double mu_max = g.c2 * lam_max * lam_max + (fabs(g.c1) + 2.0 * fabs(g.cN)) * lam_max;
+    f.accurate = g.dt * mu_max > 1e7 ? 1 : 0;
 }
 
 static Sizes sizes_of(const pint_problem* p, pint_handle* tmp) {
@@ -455,6 +460,10 @@ static long long footprint_of(const pint_problem* p) {
     if (p->precision == PINT_MIXED_FF) b += z.dof * 8 + z.nspace * 8 + 2 * (size_t)p->nt * 4;
     return b;
 }
+
+// Partial-sum buffer of the update-size test, or NULL when the test is off
+// (then the inverse time transform skips that reduction).
+static double* upd_part(pint_handle* h) { return h->p.tol_update > 0.0 ? h->dpart : nullptr; }
 
 // ---------------------------------------------------------------------------
 // Phase accounting
@@ -511,7 +520,7 @@ template <class T> struct Impl {
         const int np = residual_grid(g, gx, gy, gz, chunk);
         prof_begin(h, PH_CHECK);
         launch_after_residual(h->partials, np, 1.0 / ((double)g.nt * g.nspace), h->ctl, h->st, h->gcond, h->capturing,
-                              h->dpart, time_inv_blocks(g.nt, g.nspace, f32_transforms(&h->p)));
+                              upd_part(h), upd_part(h) ? time_inv_blocks(g.nt, g.nspace, f32_transforms(&h->p)) : 0);
         prof_end(h, PH_CHECK, 1);
         prof_begin(h, PH_TFWD);
         cudaError_t e = launch_time_fwd<T>(g.nt, g.nspace, s, S, tb.twt, h->ctl, h->st);
@@ -519,7 +528,7 @@ template <class T> struct Impl {
         if (e != cudaSuccess) return e;
         if ((e = spatial(h, S, tb)) != cudaSuccess) return e;
         prof_begin(h, PH_TINV);
-        e = launch_time_inv<T>(g.nt, g.nspace, S, tb.twt, h->ginv, U, 1, h->ctl, h->dpart, h->st);
+        e = launch_time_inv<T>(g.nt, g.nspace, S, tb.twt, h->ginv, U, 1, h->ctl, upd_part(h), h->st);
         prof_end(h, PH_TINV, 1);
         if (e != cudaSuccess) return e;
         return cudaGetLastError();
@@ -555,15 +564,15 @@ static cudaError_t zero_start(pint_handle* h, double* U, const double* u0w) {
         if ((e = Impl<float>::spatial(h, reinterpret_cast<float2*>(h->S), tb)) != cudaSuccess) return e;
         prof_begin(h, PH_TINV);
         if (h->p.precision == PINT_MIXED_FF)
-            e = launch_time_inv_ff(g.nt, g.nspace, reinterpret_cast<float2*>(h->S), tb.twt, h->ginvf, h->Uff_cur, h->ctl, h->dpart, h->st);
+            e = launch_time_inv_ff(g.nt, g.nspace, reinterpret_cast<float2*>(h->S), tb.twt, h->ginvf, h->Uff_cur, h->ctl, upd_part(h), h->st);
         else
-            e = launch_time_inv<float>(g.nt, g.nspace, reinterpret_cast<float2*>(h->S), tb.twt, h->ginv, U, 1, h->ctl, h->dpart, h->st);
+            e = launch_time_inv<float>(g.nt, g.nspace, reinterpret_cast<float2*>(h->S), tb.twt, h->ginv, U, 1, h->ctl, upd_part(h), h->st);
         prof_end(h, PH_TINV, 1);
     } else {
         const Tabs<double>& tb = tabs_of<double>(h);
         if ((e = Impl<double>::spatial(h, reinterpret_cast<double2*>(h->S), tb)) != cudaSuccess) return e;
         prof_begin(h, PH_TINV);
-        e = launch_time_inv<double>(g.nt, g.nspace, reinterpret_cast<double2*>(h->S), tb.twt, h->ginv, U, 1, h->ctl, h->dpart, h->st);
+        e = launch_time_inv<double>(g.nt, g.nspace, reinterpret_cast<double2*>(h->S), tb.twt, h->ginv, U, 1, h->ctl, upd_part(h), h->st);
         prof_end(h, PH_TINV, 1);
     }
     if (e != cudaSuccess) return e;
@@ -583,7 +592,7 @@ static cudaError_t iteration_ff(pint_handle* h) {
     const int np = residual_ff_grid(g, gx, gy, gz, chunk);
     prof_begin(h, PH_CHECK);
     launch_after_residual(h->partials, np, 1.0 / ((double)g.nt * g.nspace), h->ctl, h->st, h->gcond, h->capturing,
-                              h->dpart, time_inv_blocks(g.nt, g.nspace, f32_transforms(&h->p)));
+                              upd_part(h), upd_part(h) ? time_inv_blocks(g.nt, g.nspace, f32_transforms(&h->p)) : 0);
     prof_end(h, PH_CHECK, 1);
     prof_begin(h, PH_TFWD);
     cudaError_t e = launch_time_fwd<float>(g.nt, g.nspace, s, S, tb.twt, h->ctl, h->st);
@@ -591,7 +600,7 @@ static cudaError_t iteration_ff(pint_handle* h) {
     if (e != cudaSuccess) return e;
     if ((e = Impl<float>::spatial(h, S, tb)) != cudaSuccess) return e;
     prof_begin(h, PH_TINV);
-    e = launch_time_inv_ff(g.nt, g.nspace, S, tb.twt, h->ginvf, h->Uff_cur, h->ctl, h->dpart, h->st);
+    e = launch_time_inv_ff(g.nt, g.nspace, S, tb.twt, h->ginvf, h->Uff_cur, h->ctl, upd_part(h), h->st);
     prof_end(h, PH_TINV, 1);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

@@ -37,6 +37,7 @@ struct SolveCoef {
 struct GeoFF {
     int nx, ny, dim, bc, nt, nspace;
     float2 ihx2, ihy2, inv_dt, c2, c1, cN;
+    int accurate;   // 1: chained accurate double-word stencil sums (very stiff problems)
 };
 
 int residual_grid(const Geo& g, int& gx, int& gy, int& gz, int& chunk);
