@@ -202,6 +202,11 @@ int pint_profile_read(pint_handle* h, pint_profile* out, int reset);
  *    Enabling it builds the tables of the shorter lengths (allocates device
  *    memory); it runs the host-launched loop. */
 #define PINT_OPT_ADAPTIVE_WINDOWS 2
+/*  PINT_OPT_FUSED_SPATIAL (default 1): on square 2-D grids of 64 or 128 cells per
+ *    side with Neumann conditions, solve each frequency slice in one kernel (a
+ *    thread-block cluster holds the slice in shared memory) instead of three
+ *    passes over the spectrum. */
+#define PINT_OPT_FUSED_SPATIAL 3
 int pint_set_option(pint_handle* h, int option, long long value);
 
 /* pint_residual_static: the residual of pint_residual for callers that cannot

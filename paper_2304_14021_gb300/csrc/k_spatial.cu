@@ -15,8 +15,12 @@
 //    with the basis matrices held in device tables.
 // 1-D: one fused pass (transform, divide, inverse) per row.  2-D: x-forward
 // over rows, fused y pass (transform, divide, inverse) over columns, x-inverse.
+#include <cooperative_groups.h>
+
 #include "pint_common.cuh"
 #include "pint_kernels.h"
+
+namespace cg = cooperative_groups;
 
 namespace pint {
 
@@ -268,6 +272,175 @@ __global__ void __launch_bounds__(128) k_dense(int axis, int nx, int ny, int nve
 }
 
 // ---------------------------------------------------------------------------
+// Fused 2-D solve of one frequency slice (square N x N grid, cosine path): a
+// thread-block cluster of N/RB CTAs holds the slice in shared memory, CTA r
+// owning rows RB*r .. RB*r+RB-1 and, after a transpose through distributed
+// shared memory, the same range of columns.  Per slice: x forward -> transpose -> y
+// forward, divide, y inverse -> transpose back -> x inverse.  The slice is read
+// from and written to memory once (instead of three passes).
+// ---------------------------------------------------------------------------
+template <class T, int N> struct SliceCfg {
+    static constexpr int RB = 32;               // rows (and columns) per CTA
+    static constexpr int CS = N / RB;           // cluster size
+    static constexpr int NTH = 512;
+    static constexpr size_t SMEM = sizeof(c_t<T>) * 2 * (size_t)RB * N;
+};
+
+template <class T, int N>
+__global__ void __launch_bounds__(512) k_slice2d(c_t<T>* __restrict__ S, Tabs<T> tb, SolveCoef co,
+                                                 const Ctl* __restrict__ ctl) {
+    using C = c_t<T>;
+    constexpr int RB = SliceCfg<T, N>::RB, CS = SliceCfg<T, N>::CS, NTH = SliceCfg<T, N>::NTH;
+    if (ctl && ctl->status != ST_RUNNING) return;   // same decision in every CTA of the cluster
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int k = blockIdx.x / CS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* A = reinterpret_cast<C*>(smem_raw);      // [RB][N]: rows y0 .. y0+RB-1
+    C* B = A + RB * N;                          // [N][RB]: columns x0 .. x0+RB-1
+    C* slab = S + (size_t)k * N * N;
+    const int y0 = rank * RB, x0 = rank * RB;
+    const int tid = threadIdx.x;
+    // rows: load with the even/odd reordering, forward FFT, post-twiddle -> X (natural order)
+#pragma unroll 4
+    for (int e = tid; e < RB * N; e += NTH) {
+        const int r = e / N, i = e % N;
+        A[r * N + dct_pos(i, N)] = slab[(size_t)(y0 + r) * N + i];
+    }
+    __syncthreads();
+    smem_fft<C, N, -1, NTH, RB, 1, N>(A, tb.twx);
+    for (int e = tid; e < RB * (N / 2 + 1); e += NTH) {
+        const int r = e / (N / 2 + 1), p = e % (N / 2 + 1), q = (N - p) % N;
+        C Xp, Xq;
+        dct_post(A[r * N + p], A[r * N + q], tb.wx[p], tb.wx[q], Xp, Xq);
+        A[r * N + p] = Xp;
+        A[r * N + q] = Xq;
+    }
+    cluster.sync();
+    // transpose in: B[pos(y)][c] = X(y, x0 + c), rows y held by CTA y / RB
+#pragma unroll 4
+    for (int e = tid; e < N * RB; e += NTH) {
+        const int c = e % RB, y = e / RB;
+        const C* Ar = cluster.map_shared_rank(A, y / RB);
+        B[dct_pos(y, N) * RB + c] = Ar[(y % RB) * N + x0 + c];
+    }
+    cluster.sync();
+    // columns: forward FFT, divide, inverse FFT
+    smem_fft<C, N, -1, NTH, RB, RB, 1>(B, tb.twy);
+    const T c2 = T(co.c2), c1 = solve_c1<T>(co, ctl);
+    for (int e = tid; e < (N / 2 + 1) * RB; e += NTH) {
+        const int c = e % RB, p = e / RB, q = (N - p) % N;
+        const C wp = tb.wy[p], wq = tb.wy[q];
+        C Xp, Xq;
+        dct_post(B[p * RB + c], B[q * RB + c], wp, wq, Xp, Xq);
+        const T lx = tb.lamx[x0 + c];
+        Xp = cdiv(Xp, shift_den(tb, k, lx + tb.lamy[p], c2, c1));
+        Xq = cdiv(Xq, shift_den(tb, k, lx + tb.lamy[q], c2, c1));
+        C Vp, Vq;
+        dct_pre(p, Xp, Xq, wp, wq, Vp, Vq);
+        B[p * RB + c] = Vp;
+        B[q * RB + c] = Vq;
+    }
+    __syncthreads();
+    smem_fft<C, N, +1, NTH, RB, RB, 1>(B, tb.twy);
+    cluster.sync();
+    // transpose out: row y0 + r, column x from CTA x / RB (y un-reordered, 1/N of the y inverse)
+    const T inv = T(1) / T(N);
+#pragma unroll 4
+    for (int e = tid; e < RB * N; e += NTH) {
+        const int r = e / N, x = e % N;
+        const C* Br = cluster.map_shared_rank(B, x / RB);
+        A[r * N + x] = scalec(Br[dct_pos(y0 + r, N) * RB + (x % RB)], inv);
+    }
+    cluster.sync();   // every remote read of B is done before any CTA moves on or exits
+    // rows: pre-twiddle, inverse FFT, un-reorder, 1/N
+    for (int e = tid; e < RB * (N / 2 + 1); e += NTH) {
+        const int r = e / (N / 2 + 1), p = e % (N / 2 + 1), q = (N - p) % N;
+        C Vp, Vq;
+        dct_pre(p, A[r * N + p], A[r * N + q], tb.wx[p], tb.wx[q], Vp, Vq);
+        A[r * N + p] = Vp;
+        A[r * N + q] = Vq;
+    }
+    __syncthreads();
+    smem_fft<C, N, +1, NTH, RB, 1, N>(A, tb.twx);
+#pragma unroll 4
+    for (int e = tid; e < RB * N; e += NTH) {
+        const int r = e / N, i = e % N;
+        slab[(size_t)(y0 + r) * N + i] = scalec(A[r * N + dct_pos(i, N)], inv);
+    }
+}
+
+template <class T, int N>
+static cudaError_t slice2d_n(int nk, c_t<T>* S, const Tabs<T>& tb, SolveCoef co, const Ctl* ctl, cudaStream_t st) {
+    constexpr int CS = SliceCfg<T, N>::CS;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nk * CS, 1, 1);
+    cfg.blockDim = dim3(SliceCfg<T, N>::NTH, 1, 1);
+    cfg.dynamicSmemBytes = SliceCfg<T, N>::SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_slice2d<T, N>, S, tb, co, ctl);
+}
+
+// Whether a cluster of this kernel can be resident at all on the current device
+// (asked once per kernel; a device that cannot place the cluster uses the
+// three-pass path).
+template <class T, int N>
+static int slice2d_fits() {
+    static int ok = -1;
+    if (ok < 0) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(SliceCfg<T, N>::CS, 1, 1);
+        cfg.blockDim = dim3(SliceCfg<T, N>::NTH, 1, 1);
+        cfg.dynamicSmemBytes = SliceCfg<T, N>::SMEM;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = SliceCfg<T, N>::CS;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        ok = cudaOccupancyMaxActiveClusters(&n, k_slice2d<T, N>, &cfg) == cudaSuccess && n > 0;
+        cudaGetLastError();
+    }
+    return ok;
+}
+
+// Fused slices are used for 64^2 and 128^2 grids, where one kernel measured
+// about 2x (64^2) and 1.5x (128^2) faster than the three passes; at 256^2 the
+// large clusters (1-3 CTAs per SM) made it slower than three passes.
+int slice2d_supported(const Geo& g, int fft_x, int fft_y, int f32) {
+    if (g.dim != 2 || !fft_x || !fft_y || g.nx != g.ny) return 0;
+    switch (g.nx) {
+        case 64: return f32 ? slice2d_fits<float, 64>() : slice2d_fits<double, 64>();
+        case 128: return f32 ? slice2d_fits<float, 128>() : slice2d_fits<double, 128>();
+        default: return 0;
+    }
+}
+
+template <class T>
+cudaError_t launch_slice2d(const Geo& g, c_t<T>* S, const Tabs<T>& tb, SolveCoef co, const Ctl* ctl,
+                           cudaStream_t st) {
+    const int nk = g.nt / 2 + 1;
+    switch (g.nx) {
+        case 64: return slice2d_n<T, 64>(nk, S, tb, co, ctl, st);
+        case 128: return slice2d_n<T, 128>(nk, S, tb, co, ctl, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+template cudaError_t launch_slice2d<float>(const Geo&, float2*, const Tabs<float>&, SolveCoef, const Ctl*,
+                                           cudaStream_t);
+template cudaError_t launch_slice2d<double>(const Geo&, double2*, const Tabs<double>&, SolveCoef, const Ctl*,
+                                            cudaStream_t);
+
+// ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
 template <class T, int N>
@@ -297,6 +470,12 @@ cudaError_t configure_spatial_all() {
     PINT_C(1024)
 #undef PINT_R
 #undef PINT_C
+    if ((e = cudaFuncSetAttribute(k_slice2d<T, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)SliceCfg<T, 64>::SMEM)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_slice2d<T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)SliceCfg<T, 128>::SMEM)))
+        return e;
     const int dense_smem = (int)(2 * 1024 * sizeof(c_t<T>));
     if ((e = cudaFuncSetAttribute(k_dense<T, MODE_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, dense_smem)))
         return e;

@@ -158,6 +158,7 @@ struct pint_handle {
     int nev = 0;
     // CUDA-graph execution of the iteration loop (one while-loop graph per window)
     int use_graphs = 1;
+    int fuse2d = 1;                          // fused 2-D spatial kernel where supported
     int capturing = 0;                       // set while the loop body is being captured
     unsigned long long gcond = 0;            // cudaGraphConditionalHandle of the graph being captured
     cudaStream_t capst = nullptr;            // capture stream
@@ -461,6 +462,12 @@ static long long footprint_of(const pint_problem* p) {
     return b;
 }
 
+// Step 2 as one fused kernel per iteration (square 2-D grids up to 256^2).
+static bool fused_spatial(const pint_handle* h) {
+    return h->fuse2d && slice2d_supported(h->geo, h->fft_x, h->fft_y, h->p.precision != PINT_FP64);
+}
+static int spatial_launches(const pint_handle* h) { return fused_spatial(h) ? 1 : (h->geo.dim == 2 ? 3 : 1); }
+
 // Partial-sum buffer of the update-size test, or NULL when the test is off
 // (then the inverse time transform skips that reduction).
 static double* upd_part(pint_handle* h) { return h->p.tol_update > 0.0 ? h->dpart : nullptr; }
@@ -499,6 +506,12 @@ static void prof_end(pint_handle* h, int ph, int nlaunch) {
 // ---------------------------------------------------------------------------
 template <class T> struct Impl {
     static cudaError_t spatial(pint_handle* h, c_t<T>* S, const Tabs<T>& tb) {
+        if (fused_spatial(h)) {
+            prof_begin(h, PH_SP0);
+            cudaError_t e = launch_slice2d<T>(h->geo, S, tb, h->coef, h->ctl, h->st);
+            prof_end(h, PH_SP0, 1);
+            return e;
+        }
         const int nst = h->geo.dim == 2 ? 3 : 1;
         for (int stg = 0; stg < nst; ++stg) {
             prof_begin(h, PH_SP0 + stg);
@@ -861,6 +874,12 @@ int pint_set_option(pint_handle* h, int option, long long value) {
             if (value != 0 && value != 1) return PINT_EINVAL;
             h->use_graphs = (int)value;
             return PINT_OK;
+        case PINT_OPT_FUSED_SPATIAL:
+            if (value != 0 && value != 1) return PINT_EINVAL;
+            h->fuse2d = (int)value;
+            for (auto& sl : h->gslot)   // captured loops hold the old kernel choice
+                if (sl.exec) { cudaGraphExecDestroy(sl.exec); sl.exec = nullptr; }
+            return PINT_OK;
         case PINT_OPT_ADAPTIVE_WINDOWS: {
             if (value != 0 && value != 1) return PINT_EINVAL;
             if (value) {
@@ -979,7 +998,7 @@ int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* 
                 h->launches[PH_RES] += runs;
                 h->launches[PH_CHECK] += runs;
                 h->launches[PH_TFWD] += runs;
-                for (int stg = 0; stg < (g.dim == 2 ? 3 : 1); ++stg) h->launches[PH_SP0 + stg] += runs;
+                for (int stg = 0; stg < spatial_launches(h); ++stg) h->launches[PH_SP0 + stg] += runs;
                 h->launches[PH_TINV] += runs;
             } else {
                 int enqueued = 0;

@@ -90,6 +90,13 @@ cudaError_t launch_spatial_stage(int stage, const Geo& g, c_t<T>* S, const Tabs<
 template <class T>
 void launch_zero_start(c_t<T>* S, const double* u0, double inv_dt, int nspace, int nk, Ctl* ctl, cudaStream_t st);
 
+// Fused 2-D solve of every frequency slice in one kernel (thread-block cluster
+// per slice); for square grids of 64, 128 (FP32/FP64) or 256 (FP32) cells per side.
+int slice2d_supported(const Geo& g, int fft_x, int fft_y, int f32);
+template <class T>
+cudaError_t launch_slice2d(const Geo& g, c_t<T>* S, const Tabs<T>& tb, SolveCoef co, const Ctl* ctl,
+                           cudaStream_t st);
+
 // Opt-in shared memory sizes for the kernels that need more than 48 KB.
 cudaError_t configure_kernels();
 

@@ -230,6 +230,11 @@ class Solver:
         if rc != PINT_OK:
             raise PintError(rc, "pint_set_option")
 
+    def set_fused_spatial(self, on: bool = True) -> None:
+        rc = lib().pint_set_option(self._h, 3, 1 if on else 0)
+        if rc != PINT_OK:
+            raise PintError(rc, "pint_set_option")
+
     def set_adaptive_windows(self, on: bool = True) -> None:
         rc = lib().pint_set_option(self._h, 2, 1 if on else 0)
         if rc != PINT_OK:

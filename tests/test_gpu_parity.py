@@ -353,3 +353,48 @@ def test_update_size_stop_for_very_stiff_problem(precision):
     assert st2["rc"] == 0 and 0 < st2["update_norm"] <= 1e-10
     ref = modal_sequential_neumann_1d(1024, p.dt, 16, u0)
     assert O.rel_err(U2, ref) < (1e-10 if precision == "fp64" else 1e-8)
+
+
+@pytest.mark.parametrize("n", [64, 128])
+def test_fused_2d_spatial_equals_three_pass(n):
+    # The cluster-fused slice kernel and the three-pass path solve the same
+    # shifted systems: one preconditioner application agrees to FP32 rounding
+    # and full solves agree to the iteration tolerance.
+    kw = full(dict(equation="linear_ch", dim=2, nx=n, ny=n, bc="neumann", eps=0.05, beta=0.5, nt=16,
+                   T=16 * 0.1 / 128, precision="mixed_ff", tol=1e-10))
+    p = oprob(kw)
+    r = dev(synth.random_iterate(16, p.nspace, 31))
+    u0 = dev(synth.u0_uniform(p.nspace, -0.05, 0.05, 32))
+    out = {}
+    for fused in (True, False):
+        with pint.Solver(**kw) as s:
+            s.set_fused_spatial(fused)
+            d = torch.zeros_like(r)
+            s.precond_apply(r, d)
+            U = torch.zeros_like(r)
+            st = s.solve(u0, U)
+            out[fused] = (d, U, st)
+    (d1, U1, s1), (d2, U2, s2) = out[True], out[False]
+    assert ((d1 - d2).abs().max() / d2.abs().max()).item() < 1e-5
+    assert ((U1 - U2).abs().max() / U2.abs().max()).item() < 1e-8
+    assert s1["rc"] == 0 and s2["rc"] == 0
+    if n == 64:
+        assert O.rel_err(host(U1), O.sequential(p, host(u0))) < 1e-8
+
+
+def test_fused_2d_spatial_not_used_at_256():
+    # 256^2 grids always take the three passes: switching the option changes
+    # nothing, bit for bit.
+    n = 256
+    kw = full(dict(equation="linear_ch", dim=2, nx=n, ny=n, bc="neumann", eps=0.05, beta=0.5, nt=16,
+                   T=16 * 0.1 / 128, precision="mixed_ff", tol=1e-9))
+    p = oprob(kw)
+    r = dev(synth.random_iterate(16, p.nspace, 33))
+    out = []
+    for fused in (True, False):
+        with pint.Solver(**kw) as s:
+            s.set_fused_spatial(fused)
+            d = torch.zeros_like(r)
+            s.precond_apply(r, d)
+            out.append(d)
+    assert torch.equal(out[0], out[1])
