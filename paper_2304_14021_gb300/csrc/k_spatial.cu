@@ -17,8 +17,10 @@
 // over rows, fused y pass (transform, divide, inverse) over columns, x-inverse.
 #include <cooperative_groups.h>
 
+#include "../../include/pint.h"
 #include "pint_common.cuh"
 #include "pint_kernels.h"
+#include "tma.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -62,83 +64,141 @@ __device__ __forceinline__ void dct_pre(int p, C Xp, C Xq, C wp, C wq, C& Vp, C&
 }
 
 // ---------------------------------------------------------------------------
-// Rows (x axis), cosine path.  ROWS rows of length N per CTA, contiguous.
-// Row index gr = k * ny + y.
+// Rows (x axis), cosine path.  A tile is ROWS consecutive rows of length N
+// (contiguous in memory); row index gr = k * ny + y.  Persistent CTAs walk the
+// tiles with a stride of gridDim.x through a ring of STAGES shared-memory
+// buffers: tile loads are bulk asynchronous copies issued STAGES tiles ahead,
+// so they overlap the FFTs of the tiles before them.
 // ---------------------------------------------------------------------------
 template <class T, int N> struct RowCfg {
     static constexpr int ROWS = N >= 2048 ? 1 : 2048 / N;
     static constexpr int NTH = 256;
-    static constexpr int PADSH = 0;                                // padding measured no better (bank conflicts rose)
-    static constexpr int RS = PADSH ? N + N / 8 : N;               // padded row stride
-    static constexpr size_t SMEM = sizeof(c_t<T>) * (size_t)ROWS * RS;
+    static constexpr int STAGES = 2;
+    static constexpr int TILE = ROWS * N;                                   // elements
+    static constexpr size_t BAR_OFF = sizeof(c_t<T>) * (size_t)STAGES * TILE;
+    static constexpr size_t SMEM = BAR_OFF + 8 * STAGES;
+    // resident CTAs per SM the register allocation is sized for
+    static constexpr int MINB = sizeof(T) == 4 ? (N >= 2048 ? 3 : 4) : 2;
 };
 
+// Records a failed (timed out) barrier wait in the control block.
+__device__ __forceinline__ void note_timeout(const Ctl* ctl) {
+    if (ctl) atomicExch(const_cast<int*>(&ctl->status), (int)PINT_ECUDA);
+}
+
 template <class T, int N, int MODE>
-__global__ void __launch_bounds__(256) k_rows_dct(int nrows, int ny, c_t<T>* __restrict__ S, Tabs<T> tb,
+__global__ void __launch_bounds__(256, RowCfg<T, N>::MINB) k_rows_dct(int nrows, int ny, c_t<T>* __restrict__ S, Tabs<T> tb,
                                                   SolveCoef co, const Ctl* __restrict__ ctl) {
     using C = c_t<T>;
-    constexpr int ROWS = RowCfg<T, N>::ROWS, NTH = RowCfg<T, N>::NTH, PS = RowCfg<T, N>::PADSH;
-    constexpr int RS = RowCfg<T, N>::RS;
+    using Cfg = RowCfg<T, N>;
+    constexpr int ROWS = Cfg::ROWS, NTH = Cfg::NTH, STAGES = Cfg::STAGES, TILE = Cfg::TILE;
     if (ctl && ctl->status != ST_RUNNING) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);
+    C* bufs = reinterpret_cast<C*>(smem_raw);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + Cfg::BAR_OFF);
     const int tid = threadIdx.x;
-    const long r0 = (long)blockIdx.x * ROWS;
-#pragma unroll 4
-    for (int e = tid; e < ROWS * N; e += NTH) {
-        const int b = e / N, i = e % N;
-        const long gr = r0 + b;
-        C x = gr < nrows ? S[gr * N + i] : mkc(T(0), T(0));
-        buf[b * RS + padi<PS>(MODE == MODE_INV ? i : dct_pos(i, N))] = x;
+    const int ntiles = (nrows + ROWS - 1) / ROWS;
+    // thread 0: post the byte count of tile t on stage st's barrier and start its copy
+    auto issue = [&](int t, int st) {
+        const long r0 = (long)t * ROWS;
+        const uint32_t bytes = (uint32_t)(min((long)ROWS, nrows - r0) * N * sizeof(C));
+        mbar_arrive_expect_tx(&bar[st], bytes);
+        bulk_g2s(bufs + st * TILE, S + r0 * N, bytes, &bar[st]);
+    };
+    if (tid == 0) {
+        for (int st = 0; st < STAGES; ++st) mbar_init(&bar[st], 1);
+        mbar_fence_init();
+        for (int st = 0; st < STAGES; ++st)
+            if (blockIdx.x + st * gridDim.x < ntiles) issue(blockIdx.x + st * gridDim.x, st);
     }
     __syncthreads();
-    if (MODE != MODE_INV) smem_fft<C, N, -1, NTH, ROWS, 1, RS, PS>(buf, tb.twx);
     const T c2 = T(co.c2), c1 = solve_c1<T>(co, ctl);
-    for (int e = tid; e < ROWS * (N / 2 + 1); e += NTH) {
-        const int b = e / (N / 2 + 1), p = e % (N / 2 + 1), q = (N - p) % N;
-        C* row = buf + b * RS;
-        const C wp = tb.wx[p], wq = tb.wx[q];
-        C Xp, Xq;
-        if (MODE == MODE_INV) {
-            Xp = row[padi<PS>(p)];
-            Xq = row[padi<PS>(q)];
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const int st = it % STAGES;
+        C* buf = bufs + st * TILE;
+        const bool ok = mbar_wait_bounded(&bar[st], (uint32_t)(it / STAGES) & 1u);
+        if (!__syncthreads_and(ok)) {
+            // give up: record the failure, let the copies still in flight land, stop
+            if (tid == 0) {
+                note_timeout(ctl);
+                for (int k = 0; k < STAGES; ++k)
+                    if (t + k * gridDim.x < ntiles)
+                        mbar_wait_bounded(&bar[(it + k) % STAGES], (uint32_t)((it + k) / STAGES) & 1u);
+            }
+            __syncthreads();
+            return;
+        }
+        const long r0 = (long)t * ROWS;
+        // The tile arrives in natural order; the FFTs keep it swizzled (swz<1>).
+        if constexpr (MODE == MODE_INV) {
+            // pre-twiddle X -> V, read in natural order, written back swizzled
+            constexpr int NP = ROWS * (N / 2 + 1), PPT = (NP + NTH - 1) / NTH;
+            C vp[PPT], vq[PPT];
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                const int e = tid + k * NTH;
+                if (e < NP) {
+                    const int b = e / (N / 2 + 1), p = e % (N / 2 + 1), q = (N - p) % N;
+                    const C* row = buf + b * N;
+                    dct_pre(p, row[p], row[q], tb.wx[p], tb.wx[q], vp[k], vq[k]);
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                const int e = tid + k * NTH;
+                if (e < NP) {
+                    const int b = e / (N / 2 + 1), p = e % (N / 2 + 1), q = (N - p) % N;
+                    C* row = buf + b * N;
+                    row[swz<1>(p)] = vp[k];
+                    row[swz<1>(q)] = vq[k];
+                }
+            }
+            __syncthreads();
         } else {
-            dct_post(row[padi<PS>(p)], row[padi<PS>(q)], wp, wq, Xp, Xq);
+            smem_fft<C, N, -1, NTH, ROWS, 1, N, 1, true>(buf, tb.twx);
+            for (int e = tid; e < ROWS * (N / 2 + 1); e += NTH) {
+                const int b = e / (N / 2 + 1), p = e % (N / 2 + 1), q = (N - p) % N;
+                C* row = buf + b * N;
+                const int sp = swz<1>(p), sq = swz<1>(q);
+                const C wp = tb.wx[p], wq = tb.wx[q];
+                C Xp, Xq;
+                dct_post(row[sp], row[sq], wp, wq, Xp, Xq);
+                if (MODE == MODE_FDI) {
+                    const int k = (int)((r0 + b) / ny);
+                    if (r0 + b < nrows) {
+                        Xp = cdiv(Xp, shift_den(tb, k, tb.lamx[p], c2, c1));
+                        Xq = cdiv(Xq, shift_den(tb, k, tb.lamx[q], c2, c1));
+                    }
+                    dct_pre(p, Xp, Xq, wp, wq, Xp, Xq);
+                }
+                row[sp] = Xp;
+                row[sq] = Xq;
+            }
+            __syncthreads();
         }
         if (MODE == MODE_FWD) {
-            row[padi<PS>(p)] = Xp;
-            row[padi<PS>(q)] = Xq;
-            continue;
-        }
-        if (MODE == MODE_FDI) {
-            const int k = (int)((r0 + b) / ny);
-            if (r0 + b < nrows) {
-                Xp = cdiv(Xp, shift_den(tb, k, tb.lamx[p], c2, c1));
-                Xq = cdiv(Xq, shift_den(tb, k, tb.lamx[q], c2, c1));
+#pragma unroll 4
+            for (int e = tid; e < ROWS * N; e += NTH) {
+                const long gr = r0 + e / N;
+                if (gr < nrows) S[r0 * N + e] = buf[(e / N) * N + swz<1>(e % N)];
+            }
+        } else {
+            smem_fft<C, N, +1, NTH, ROWS, 1, N, 1>(buf, tb.twx);
+            const T inv = T(1) / T(N);
+#pragma unroll 4
+            for (int e = tid; e < ROWS * N; e += NTH) {
+                const int b = e / N, i = e % N;
+                const long gr = r0 + b;
+                if (gr < nrows) S[r0 * N + e] = scalec(buf[b * N + swz<1>(dct_pos(i, N))], inv);
             }
         }
-        C Vp, Vq;
-        dct_pre(p, Xp, Xq, wp, wq, Vp, Vq);
-        row[padi<PS>(p)] = Vp;
-        row[padi<PS>(q)] = Vq;
-    }
-    __syncthreads();
-    if (MODE == MODE_FWD) {
-#pragma unroll 4
-        for (int e = tid; e < ROWS * N; e += NTH) {
-            const int b = e / N, i = e % N;
-            const long gr = r0 + b;
-            if (gr < nrows) S[gr * N + i] = buf[b * RS + padi<PS>(i)];
+        __syncthreads();   // every thread is done with buf
+        if (tid == 0 && t + STAGES * gridDim.x < ntiles) {
+            fence_proxy_async_smem();
+            issue(t + STAGES * gridDim.x, st);
         }
-        return;
-    }
-    smem_fft<C, N, +1, NTH, ROWS, 1, RS, PS>(buf, tb.twx);
-    const T inv = T(1) / T(N);
-#pragma unroll 4
-    for (int e = tid; e < ROWS * N; e += NTH) {
-        const int b = e / N, i = e % N;
-        const long gr = r0 + b;
-        if (gr < nrows) S[gr * N + i] = scalec(buf[b * RS + padi<PS>(dct_pos(i, N))], inv);
     }
 }
 
@@ -443,6 +503,23 @@ template cudaError_t launch_slice2d<double>(const Geo&, double2*, const Tabs<dou
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
+// Resident CTAs of a persistent kernel on the current device: SMs x CTAs per SM.
+template <class K>
+static int persistent_ctas(K kernel, int nth, size_t smem) {
+    int dev = 0, nsm = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, nth, smem) != cudaSuccess || per < 1)
+        return 0;
+    return nsm * per;
+}
+
+// Looked up once (from the configure step, outside any stream capture).
+template <class T, int N, int MODE>
+static int rows_resident() {
+    static const int r = persistent_ctas(k_rows_dct<T, N, MODE>, RowCfg<T, N>::NTH, RowCfg<T, N>::SMEM);
+    return r;
+}
+
 template <class T, int N>
 static cudaError_t cfg_rows() {
     cudaError_t e;
@@ -451,7 +528,12 @@ static cudaError_t cfg_rows() {
         return e;
     if ((e = cudaFuncSetAttribute(k_rows_dct<T, N, MODE_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
         return e;
-    return cudaFuncSetAttribute(k_rows_dct<T, N, MODE_FDI>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if ((e = cudaFuncSetAttribute(k_rows_dct<T, N, MODE_FDI>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
+        return e;
+    if (rows_resident<T, N, MODE_FWD>() <= 0 || rows_resident<T, N, MODE_INV>() <= 0 ||
+        rows_resident<T, N, MODE_FDI>() <= 0)
+        return cudaErrorInvalidConfiguration;
+    return cudaSuccess;
 }
 template <class T, int N>
 static cudaError_t cfg_cols() {
@@ -487,21 +569,25 @@ template cudaError_t configure_spatial_all<float>();
 template cudaError_t configure_spatial_all<double>();
 
 template <class T, int N, int MODE>
-static void rows_n(int nrows, int ny, c_t<T>* S, const Tabs<T>& tb, SolveCoef co, const Ctl* ctl, cudaStream_t st) {
-    constexpr int ROWS = RowCfg<T, N>::ROWS;
-    int grid = (nrows + ROWS - 1) / ROWS;
-    k_rows_dct<T, N, MODE><<<grid, 256, RowCfg<T, N>::SMEM, st>>>(nrows, ny, S, tb, co, ctl);
+static cudaError_t rows_n(int nrows, int ny, c_t<T>* S, const Tabs<T>& tb, SolveCoef co, const Ctl* ctl,
+                          cudaStream_t st) {
+    using Cfg = RowCfg<T, N>;
+    const int resident = rows_resident<T, N, MODE>();
+    if (resident <= 0) return cudaErrorInvalidConfiguration;
+    const int ntiles = (nrows + Cfg::ROWS - 1) / Cfg::ROWS;
+    const int grid = ntiles < resident ? ntiles : resident;
+    k_rows_dct<T, N, MODE><<<grid, Cfg::NTH, Cfg::SMEM, st>>>(nrows, ny, S, tb, co, ctl);
+    return cudaSuccess;
 }
 template <class T, int MODE>
 static cudaError_t rows_dct(int nx, int nrows, int ny, c_t<T>* S, const Tabs<T>& tb, SolveCoef co, const Ctl* ctl,
                             cudaStream_t st) {
     switch (nx) {
-#define R_(N) case N: rows_n<T, N, MODE>(nrows, ny, S, tb, co, ctl, st); break;
+#define R_(N) case N: return rows_n<T, N, MODE>(nrows, ny, S, tb, co, ctl, st);
         R_(2) R_(4) R_(8) R_(16) R_(32) R_(64) R_(128) R_(256) R_(512) R_(1024) R_(2048) R_(4096)
 #undef R_
         default: return cudaErrorInvalidValue;
     }
-    return cudaSuccess;
 }
 template <class T, int N>
 static void cols_n(int nx, int nk, c_t<T>* S, const Tabs<T>& tb, SolveCoef co, const Ctl* ctl, cudaStream_t st) {

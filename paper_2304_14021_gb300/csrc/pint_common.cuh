@@ -104,12 +104,21 @@ constexpr int next_radix(int M) { return (M >= 3 && M != 4) ? 8 : (M == 4 || M =
 // column layouts (ESTR > 1) the batch index is fastest, for rows the
 // butterfly index.
 // ---------------------------------------------------------------------------
-// PADSH > 0 inserts one padding element after every 2^PADSH elements of a
-// sequence (index i is stored at i + (i >> PADSH)), which breaks the stride-R
-// shared-memory bank conflicts of the early passes on contiguous rows.
-template <int PADSH> __device__ __forceinline__ int padi(int i) { return PADSH > 0 ? i + (i >> PADSH) : i; }
+// SW = 1 (contiguous rows, ESTR = 1): element i of a sequence is stored at
+// i ^ ((i >> 4) & 15), i.e. each aligned group of 16 elements (one 128-byte
+// bank row for complex64) is permuted by its group index.  Stride-R writes of
+// the early passes then hit distinct banks; unit-stride accesses stay
+// conflict-free (a fixed XOR within each group).
+template <int SW> __device__ __forceinline__ int swz(int i) { return SW ? (i ^ ((i >> 4) & 15)) : i; }
 
-template <class C, int N, int R, int NS, int DIR, int NTH, int B, int ESTR, int SSTR, int PADSH = 0>
+// PERM (first pass only): the sequence to transform is the even/odd
+// reordering v_m = x_{2m}, v_{N-1-m} = x_{2m+1} of the natural-order data in
+// buf, read in place (element m of v sits at 2m for m < N/2, at 2N-1-2m
+// above); that input is in natural (not swizzled) order.
+// Twiddles: w^1 (and w^2 for radix 8) come from the table, the other powers
+// from at most two complex products of those.
+template <class C, int N, int R, int NS, int DIR, int NTH, int B, int ESTR, int SSTR, int SW = 0,
+          bool PERM = false>
 __device__ __forceinline__ void stockham_pass(C* buf, const C* __restrict__ tw) {
     constexpr int NB = N / R;              // butterflies per sequence
     constexpr int NTASK = NB * B;
@@ -125,7 +134,11 @@ __device__ __forceinline__ void stockham_pass(C* buf, const C* __restrict__ tw) 
             int j = COL ? t / B : t % NB;
             const C* src = buf + b * SSTR;
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[q][r] = src[padi<PADSH>(j + r * NB) * ESTR];
+            for (int r = 0; r < R; ++r) {
+                const int m = j + r * NB;
+                const int pm = PERM ? (m < N / 2 ? 2 * m : 2 * N - 1 - 2 * m) : swz<SW>(m);
+                v[q][r] = src[pm * ESTR];
+            }
         }
     }
     __syncthreads();
@@ -136,39 +149,53 @@ __device__ __forceinline__ void stockham_pass(C* buf, const C* __restrict__ tw) 
             int b = COL ? t % B : t / NB;
             int j = COL ? t / B : t % NB;
             if constexpr (NS > 1) {
-                int jm = j % NS;
-#pragma unroll
-                for (int r = 1; r < R; ++r) {
-                    C w = tw[jm * r * (N / (NS * R))];
-                    if (DIR > 0) w = conjc(w);
-                    v[q][r] = cmul(v[q][r], w);
+                constexpr int STEP = N / (NS * R);
+                const int jm = j % NS;
+                C w[R];
+                w[1] = tw[jm * STEP];
+                if (DIR > 0) w[1] = conjc(w[1]);
+                if constexpr (R == 4) {
+                    w[2] = cmul(w[1], w[1]);
+                    w[3] = cmul(w[2], w[1]);
+                } else if constexpr (R == 8) {
+                    w[2] = tw[2 * jm * STEP];
+                    if (DIR > 0) w[2] = conjc(w[2]);
+                    w[3] = cmul(w[2], w[1]);
+                    w[4] = cmul(w[2], w[2]);
+                    w[5] = cmul(w[4], w[1]);
+                    w[6] = cmul(w[4], w[2]);
+                    w[7] = cmul(w[4], w[3]);
                 }
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[q][r] = cmul(v[q][r], w[r]);
             }
             dftR<R, DIR>(v[q]);
             C* dst = buf + b * SSTR;
             int base = (j / NS) * NS * R + (j % NS);
 #pragma unroll
-            for (int r = 0; r < R; ++r) dst[padi<PADSH>(base + r * NS) * ESTR] = v[q][r];
+            for (int r = 0; r < R; ++r) dst[swz<SW>(base + r * NS) * ESTR] = v[q][r];
         }
     }
     __syncthreads();
 }
 
-template <class C, int N, int NS, int M, int DIR, int NTH, int B, int ESTR, int SSTR, int PADSH>
+template <class C, int N, int NS, int M, int DIR, int NTH, int B, int ESTR, int SSTR, int SW, bool PERM = false>
 __device__ __forceinline__ void fft_passes(C* buf, const C* __restrict__ tw) {
     if constexpr (M > 0) {
         constexpr int R = next_radix(M);
-        stockham_pass<C, N, R, NS, DIR, NTH, B, ESTR, SSTR, PADSH>(buf, tw);
-        fft_passes<C, N, NS * R, M - ilog2(R), DIR, NTH, B, ESTR, SSTR, PADSH>(buf, tw);
+        stockham_pass<C, N, R, NS, DIR, NTH, B, ESTR, SSTR, SW, PERM>(buf, tw);
+        fft_passes<C, N, NS * R, M - ilog2(R), DIR, NTH, B, ESTR, SSTR, SW, false>(buf, tw);
     }
 }
 
 // In-place length-N FFT (N a power of two) of B sequences in shared memory.
 // The caller must __syncthreads() before (data ready); the last pass ends
-// with a barrier.
-template <class C, int N, int DIR, int NTH, int B, int ESTR, int SSTR, int PADSH = 0>
+// with a barrier.  SW: swizzled row layout (see swz); the result is stored
+// swizzled.  PERM: transform the even/odd reordering of the stored
+// natural-order sequences (see stockham_pass).
+template <class C, int N, int DIR, int NTH, int B, int ESTR, int SSTR, int SW = 0, bool PERM = false>
 __device__ __forceinline__ void smem_fft(C* buf, const C* __restrict__ tw) {
-    fft_passes<C, N, 1, ilog2(N), DIR, NTH, B, ESTR, SSTR, PADSH>(buf, tw);
+    fft_passes<C, N, 1, ilog2(N), DIR, NTH, B, ESTR, SSTR, SW, PERM>(buf, tw);
 }
 
 // ---------------------------------------------------------------------------
