@@ -4,7 +4,8 @@
 //
 // Same operator and boundary treatment as k_residual.cu (Eq. 2.6 / 4.8 with
 // alpha = 0, theta = 1):
-//   r_n = (u_{n-1} - u_n)/dt - [c2 Lap^2 u_n + c1 Lap u_n + cN Lap(u_n^3)].
+//   r_n = (u_{n-1} - u_n)/dt - [c2 Lap^2 u_n + c1 Lap u_n + cN Lap(u_n^3)],
+// evaluated as dt r_n (see k_residual_ff below).
 // The stencil sums are error-free in their high words (a TwoSum chain), so the
 // cancellation in the differences of smooth data is resolved to a few 2^-48 of
 // the terms, the same order as the rounding of the stored iterate.  Output: s = gamma_n r_n rounded to FP32 (the alpha-scaled input of
@@ -12,6 +13,7 @@
 #include "ff.cuh"
 #include "pint_common.cuh"
 #include "pint_kernels.h"
+#include "tma.cuh"
 
 namespace pint {
 
@@ -102,6 +104,25 @@ __device__ __forceinline__ ff lap_ff(const ff* __restrict__ a, int c, int sx, co
     }
 }
 
+// Neumann (cell-centred) reflection of a halo index g in [-2, n+1] into [0, n).
+__device__ __forceinline__ int reflect_n(int g, int n) {
+    g = g < 0 ? -1 - g : (g >= n ? 2 * n - 1 - g : g);
+    return min(max(g, 0), n - 1);
+}
+
+// 8-byte asynchronous copy global -> shared (cp.async, cached in L1 for the
+// halo overlap between neighbouring tiles), committed as one group per level.
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// The residual is computed scaled by dt,
+//   r'_n = (u_{n-1} - u_n) - [c2' Lap^2 u_n + c1' Lap u_n + cN' Lap(u_n^3)],  c' = dt c,
+// so the time difference needs no product; s = (gamma_n / dt) r' and the norm
+// partials carry the factor 1/dt^2.  The CTA stages time level n+1 of its tile
+// (with halo) by asynchronous copies while it computes level n.
 template <int DIM, bool SQ, bool ACC>
 __global__ void __launch_bounds__(256) k_residual_ff(GeoFF g, const ff* __restrict__ U, const ff* __restrict__ u0,
                                                      const float* __restrict__ gamf, float* __restrict__ s_out,
@@ -115,18 +136,44 @@ __global__ void __launch_bounds__(256) k_residual_ff(GeoFF g, const ff* __restri
     constexpr int HY = DIM == 2 ? 2 : 0;
     constexpr int SX = TX + 4, SY = TY + 2 * HY;
     constexpr int LX = TX + 2, LY = TY + (DIM == 2 ? 2 : 0);
-    __shared__ ff su[SY * SX];
+    constexpr int TXT = DIM == 2 ? TX : NTHR, TYT = NTHR / TXT;   // thread grid of the staging loops
+    __shared__ __align__(16) ff su[2][SY * SX];
     __shared__ ff sL[LY * LX];
     __shared__ ff sW[LY * LX];   // u^3 (Cahn-Hilliard)
     __shared__ double red[2][NTHR / 32];
 
-    const int tx = threadIdx.x % (DIM == 2 ? TX : TX / PPT), ty = threadIdx.x / (DIM == 2 ? TX : TX / PPT);
+    const int tid = threadIdx.x;
+    const int tx = tid % (DIM == 2 ? TX : TX / PPT), ty = tid / (DIM == 2 ? TX : TX / PPT);
+    const int sx_t = tid % TXT, sy_t = tid / TXT;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int n0 = blockIdx.z * chunk;
     const int n1 = min(g.nt, n0 + chunk);
     const bool ch = g.cN.x != 0.f;
     const bool lin1 = g.c1.x != 0.f;
     const bool interior = x0 >= 2 && x0 + TX + 2 <= g.nx && (DIM == 1 || (y0 >= 2 && y0 + TY + 2 <= g.ny));
+    // halo values are plain (reflected) copies except on simply supported boundary tiles
+    const bool async_ok = interior || (g.bc == 1 && g.nx >= 2 && (DIM == 1 || g.ny >= 2));
+
+    auto stage = [&](int n, ff* dst) {
+        const ff* un = U + (size_t)n * g.nspace;
+        if (async_ok) {
+#pragma unroll
+            for (int iy = sy_t; iy < SY; iy += TYT) {
+                const int gy = DIM == 2 ? (interior ? y0 - HY + iy : reflect_n(y0 - HY + iy, g.ny)) : 0;
+                const ff* rowp = un + (size_t)gy * g.nx;
+#pragma unroll
+                for (int ix = sx_t; ix < SX; ix += TXT) {
+                    const int gx = interior ? x0 - 2 + ix : reflect_n(x0 - 2 + ix, g.nx);
+                    cp_async8(&dst[iy * SX + ix], rowp + gx);
+                }
+            }
+            cp_async_commit();
+        } else {
+            for (int iy = sy_t; iy < SY; iy += TYT)
+                for (int ix = sx_t; ix < SX; ix += TXT)
+                    dst[iy * SX + ix] = ext_read_ff(un, x0 - 2 + ix, y0 - HY + iy, g.nx, g.ny, DIM, g.bc);
+        }
+    };
 
     int pidx[PPT], cu[PPT], cl[PPT];
     bool inside[PPT];
@@ -143,50 +190,56 @@ __global__ void __launch_bounds__(256) k_residual_ff(GeoFF g, const ff* __restri
         if (inside[q]) uprev[q] = n0 == 0 ? u0[pidx[q]] : U[(size_t)(n0 - 1) * g.nspace + pidx[q]];
     }
     float acc_r2 = 0.f, acc_u2 = 0.f;
+    const float sdt = g.inv_dt.x;
 
+    if (n0 < n1) stage(n0, su[0]);
     for (int n = n0; n < n1; ++n) {
-        const ff* un = U + (size_t)n * g.nspace;
-        if (interior) {
-            for (int e = threadIdx.x; e < SX * SY; e += NTHR) {
-                const int ix = e % SX, iy = e / SX;
-                su[e] = un[(DIM == 2 ? (y0 - HY + iy) * g.nx : 0) + x0 - 2 + ix];
+        const ff* cur = su[(n - n0) & 1];
+        if (async_ok) cp_async_wait_all();
+        __syncthreads();                                   // level n staged; level n-1 fully consumed
+        if (n + 1 < n1) stage(n + 1, su[(n + 1 - n0) & 1]);
+#pragma unroll
+        for (int ly = sy_t; ly < LY; ly += TYT)
+#pragma unroll
+            for (int lx = sx_t; lx < LX; lx += TXT) {
+                const int c = (DIM == 2 ? (ly + 1) * SX : 0) + lx + 1;
+                sL[ly * LX + lx] = lap_ff<DIM, SQ, ACC>(cur, c, SX, g);
+                if (ch) sW[ly * LX + lx] = ff_cube(cur[c]);
             }
-        } else {
-            for (int e = threadIdx.x; e < SX * SY; e += NTHR) {
-                const int ix = e % SX, iy = e / SX;
-                su[e] = ext_read_ff(un, x0 - 2 + ix, y0 - HY + iy, g.nx, g.ny, DIM, g.bc);
-            }
-        }
         __syncthreads();
-        for (int e = threadIdx.x; e < LX * LY; e += NTHR) {
-            const int ix = e % LX, iy = e / LX;
-            const int c = (DIM == 2 ? (iy + 1) * SX : 0) + ix + 1;
-            sL[e] = lap_ff<DIM, SQ, ACC>(su, c, SX, g);
-            if (ch) sW[e] = ff_cube(su[c]);
-        }
-        __syncthreads();
+        const float gm = gamf[n] * sdt;
 #pragma unroll
         for (int q = 0; q < PPT; ++q) {
             if (!inside[q]) continue;
             const ff L = sL[cl[q]];
-            const ff u = su[cu[q]];
-            ff A = ff_mul(lap_ff<DIM, SQ, ACC>(sL, cl[q], LX, g), g.c2);
-            if (lin1) A = ff_add(A, ff_mul(L, g.c1));
-            if (ch) A = ff_add(A, ff_mul(lap_ff<DIM, SQ, ACC>(sW, cl[q], LX, g), g.cN));
-            const ff r = ff_sub(ff_mul(ff_sub(uprev[q], u), g.inv_dt), A);
-            const float gm = gamf[n];
+            const ff u = cur[cu[q]];
+            const ff lapL = lap_ff<DIM, SQ, ACC>(sL, cl[q], LX, g);
+            ff r;
+            if constexpr (SQ && !ACC) {
+                ff_acc acc(uprev[q]);
+                acc.add(ff_neg(u));
+                acc.add(ff_neg(ff_mul(lapL, g.c2)));
+                if (lin1) acc.add(ff_neg(ff_mul(L, g.c1)));
+                if (ch) acc.add(ff_neg(ff_mul(lap_ff<DIM, SQ, ACC>(sW, cl[q], LX, g), g.cN)));
+                r = acc.get();
+            } else {
+                ff A = ff_mul(lapL, g.c2);
+                if (lin1) A = ff_add(A, ff_mul(L, g.c1));
+                if (ch) A = ff_add(A, ff_mul(lap_ff<DIM, SQ, ACC>(sW, cl[q], LX, g), g.cN));
+                r = ff_sub(ff_sub(uprev[q], u), A);
+            }
             s_out[(size_t)n * g.nspace + pidx[q]] = fmaf(gm, r.x, gm * r.y);
             acc_r2 = fmaf(r.x, r.x, acc_r2);
             acc_u2 = fmaf(u.x, u.x, acc_u2);
             uprev[q] = u;
         }
-        __syncthreads();
     }
-    double a = warp_sum((double)acc_r2), b = warp_sum((double)acc_u2);
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const double idt = (double)g.inv_dt.x + (double)g.inv_dt.y;
+    double a = warp_sum((double)acc_r2) * (idt * idt), b = warp_sum((double)acc_u2);
+    const int warp = tid / 32, lane = tid % 32;
     if (lane == 0) { red[0][warp] = a; red[1][warp] = b; }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         double A = 0.0, B = 0.0;
         for (int w = 0; w < NTHR / 32; ++w) { A += red[0][w]; B += red[1][w]; }
         size_t cta = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;

@@ -11,9 +11,11 @@
 // A CTA holds CW complex columns (2*CW consecutive spatial points) times all
 // N_t time levels in shared memory: loads and stores are rows of CW
 // consecutive values per time level / frequency, i.e. coalesced.
+#include "../../include/pint.h"
 #include "ff.cuh"
 #include "pint_common.cuh"
 #include "pint_kernels.h"
+#include "tma.cuh"
 
 namespace pint {
 
@@ -161,6 +163,110 @@ __global__ void __launch_bounds__(TimeCfg<T, NT>::NTH)
     }
 }
 
+// Float-float update with the iterate tile prefetched: at entry one warp
+// starts bulk asynchronous copies of the CTA's U rows (2*CW points x N_t
+// levels) into shared memory, so they load while the spectrum is read and
+// transformed; the update U += delta then reads U from shared memory.  Needs
+// an even number of spatial points (16-byte aligned rows); N_t <= 512.
+template <int NT> struct TimeTmaCfg {
+    static constexpr int CW = 16;
+    static constexpr int NTH = NT * CW >= 8192 ? 1024 : (NT * CW >= 2048 ? 512 : 256);
+    static constexpr size_t TW_OFF = sizeof(float2) * (size_t)NT * CW;
+    static constexpr size_t U_OFF = TW_OFF + sizeof(float2) * NT;
+    static constexpr size_t BAR_OFF = U_OFF + sizeof(float2) * (size_t)NT * 2 * CW;
+    static constexpr size_t SMEM = BAR_OFF + 16;
+};
+
+template <int NT>
+__global__ void __launch_bounds__(TimeTmaCfg<NT>::NTH)
+    k_time_inv_ff_tma(int nspace, const float2* __restrict__ S, const float2* __restrict__ twt,
+                      const float* __restrict__ ginvf, float2* __restrict__ Uff, const Ctl* __restrict__ ctl,
+                      double* __restrict__ dpart) {
+    using C = float2;
+    using Cfg = TimeTmaCfg<NT>;
+    constexpr int CW = Cfg::CW, NTH = Cfg::NTH;
+    if (ctl && ctl->status != ST_RUNNING) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* z = reinterpret_cast<C*>(smem_raw);
+    C* tw = reinterpret_cast<C*>(smem_raw + Cfg::TW_OFF);
+    float2* ub = reinterpret_cast<float2*>(smem_raw + Cfg::U_OFF);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + Cfg::BAR_OFF);
+    const int tid = threadIdx.x;
+    const long p0 = (long)blockIdx.x * 2 * CW;
+    const int npts = (int)min((long)2 * CW, nspace - p0);   // even: nspace is even
+    if (tid < 32) {
+        if (tid == 0) {
+            mbar_init(bar, 1);
+            mbar_fence_init();
+            mbar_arrive_expect_tx(bar, (uint32_t)(NT * npts * sizeof(float2)));
+        }
+        __syncwarp();
+        for (int n = tid; n < NT; n += 32)
+            bulk_g2s(ub + n * 2 * CW, Uff + (size_t)n * nspace + p0, (uint32_t)(npts * sizeof(float2)), bar);
+    }
+    for (int i = tid; i < NT; i += NTH) tw[i] = twt[i];
+#pragma unroll 4
+    for (int e = tid; e < (NT / 2 + 1) * CW; e += NTH) {
+        const int c = e % CW, k = e / CW;
+        const long pa = p0 + c, pb = p0 + CW + c;
+        const C* row = S + (size_t)k * nspace;
+        C a = pa < nspace ? row[pa] : mkc(0.f, 0.f);
+        C b = pb < nspace ? row[pb] : mkc(0.f, 0.f);
+        if (k == 0 || k == NT / 2) { a.y = 0.f; b.y = 0.f; }  // real in exact arithmetic
+        z[k * CW + c] = mkc(a.x - b.y, a.y + b.x);
+        if (k > 0 && k < NT / 2) z[(NT - k) * CW + c] = mkc(a.x + b.y, b.x - a.y);
+    }
+    __syncthreads();
+    smem_fft<C, NT, +1, NTH, CW, CW, 1>(z, tw);
+    if (!__syncthreads_and(mbar_wait_bounded(bar, 0))) {
+        if (tid == 0) {
+            atomicExch(const_cast<int*>(&ctl->status), (int)PINT_ECUDA);
+            mbar_wait_bounded(bar, 0);   // let the copies in flight land before the CTA exits
+        }
+        __syncthreads();
+        return;
+    }
+    float d2 = 0.f, u2 = 0.f;
+    const bool want = dpart != nullptr;
+#pragma unroll 4
+    for (int e = tid; e < NT * CW; e += NTH) {
+        const int c = e % CW, n = e / CW;
+        const C v = z[e];
+        const long pa = p0 + c, pb = p0 + CW + c;
+        const float gi = ginvf[n];
+        float2* row = Uff + (size_t)n * nspace;
+        const float da = v.x * gi, db = v.y * gi;
+        if (pa < nspace) {
+            const float2 w = ff_add_f(ub[n * 2 * CW + c], da);
+            row[pa] = w;
+            if (want) {
+                d2 = fmaf(da, da, d2);
+                u2 = fmaf(w.x, w.x, u2);
+            }
+        }
+        if (pb < nspace) {
+            const float2 w = ff_add_f(ub[n * 2 * CW + CW + c], db);
+            row[pb] = w;
+            if (want) {
+                d2 = fmaf(db, db, d2);
+                u2 = fmaf(w.x, w.x, u2);
+            }
+        }
+    }
+    if (want) {  // deterministic block reduction (same tree every launch)
+        __shared__ double red[2][32];
+        double a = warp_sum((double)d2), b = warp_sum((double)u2);
+        if (tid % 32 == 0) { red[0][tid / 32] = a; red[1][tid / 32] = b; }
+        __syncthreads();
+        if (tid == 0) {
+            double A = 0.0, B = 0.0;
+            for (int w = 0; w < NTH / 32; ++w) { A += red[0][w]; B += red[1][w]; }
+            dpart[2 * blockIdx.x] = A;
+            dpart[2 * blockIdx.x + 1] = B;
+        }
+    }
+}
+
 template <class T, int NT>
 static cudaError_t configure_time() {
     const int sm = (int)TimeCfg<T, NT>::SMEM;
@@ -168,8 +274,13 @@ static cudaError_t configure_time() {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_time_inv<T, NT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
-    if constexpr (sizeof(T) == 4)
+    if constexpr (sizeof(T) == 4) {
         e = cudaFuncSetAttribute(k_time_inv<T, NT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        if (e != cudaSuccess) return e;
+        if constexpr (NT <= 512)
+            e = cudaFuncSetAttribute(k_time_inv_ff_tma<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)TimeTmaCfg<NT>::SMEM);
+    }
     return e;
 }
 
@@ -199,13 +310,31 @@ static void time_inv_nt(int nspace, const c_t<T>* S, const c_t<T>* twt, const do
     k_time_inv<T, NT, 0><<<grid, TimeCfg<T, NT>::NTH, TimeCfg<T, NT>::SMEM, st>>>(nspace, S, twt, ginv, nullptr, out,
                                                                                   nullptr, acc, ctl, dpart);
 }
+// The prefetching kernel serves even point counts and N_t <= 512 (it needs a control block for its status).
+static bool time_inv_ff_prefetch(int nt, int nspace, const Ctl* ctl) {
+    return ctl != nullptr && nspace % 2 == 0 && nt <= 512;
+}
+
 template <int NT>
 static void time_inv_ff_nt(int nspace, const float2* S, const float2* twt, const float* ginvf, float2* Uff,
                            const Ctl* ctl, double* dpart, cudaStream_t st) {
+    if constexpr (NT <= 512) {
+        if (time_inv_ff_prefetch(NT, nspace, ctl)) {
+            using Cfg = TimeTmaCfg<NT>;
+            const int grid = (nspace + 2 * Cfg::CW - 1) / (2 * Cfg::CW);
+            k_time_inv_ff_tma<NT><<<grid, Cfg::NTH, Cfg::SMEM, st>>>(nspace, S, twt, ginvf, Uff, ctl, dpart);
+            return;
+        }
+    }
     constexpr int CW = TimeCfg<float, NT>::CW;
     int grid = (nspace + 2 * CW - 1) / (2 * CW);
     k_time_inv<float, NT, 1><<<grid, TimeCfg<float, NT>::NTH, TimeCfg<float, NT>::SMEM, st>>>(
         nspace, S, twt, nullptr, ginvf, nullptr, Uff, 1, ctl, dpart);
+}
+
+int time_inv_ff_blocks(int nt, int nspace, const Ctl* ctl) {
+    if (time_inv_ff_prefetch(nt, nspace, ctl)) return (nspace + 31) / 32;
+    return time_inv_blocks(nt, nspace, 1);
 }
 
 int time_inv_blocks(int nt, int nspace, int f32) {

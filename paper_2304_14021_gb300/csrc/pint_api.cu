@@ -416,10 +416,11 @@ static void derive(const pint_problem* p, pint_handle* h) {
     f.ihy2 = ff_from_double(g.ihy2);
     f.inv_dt = ff_from_double(g.inv_dt);
     const bool sq = g.dim == 1 || g.ihx2 == g.ihy2;   // must match launch_residual_ff
+    // the float-float residual is evaluated scaled by dt: coefficients carry dt
     const double s2 = sq ? g.ihx2 * g.ihx2 : 1.0, s1 = sq ? g.ihx2 : 1.0;
-    f.c2 = ff_from_double(g.c2 * s2);
-    f.c1 = ff_from_double(g.c1 * s1);
-    f.cN = ff_from_double(g.cN * s1);
+    f.c2 = ff_from_double(g.c2 * s2 * g.dt);
+    f.c1 = ff_from_double(g.c1 * s1 * g.dt);
+    f.cN = ff_from_double(g.cN * s1 * g.dt);
     // stiffness dt * max |spectrum of the spatial operator|: above 1e7 the stencil
     // sums use chained accurate double-word additions (see k_residual_ff.cu)
     const double lam_max = 4.0 * g.ihx2 + (g.dim == 2 ? 4.0 * g.ihy2 : 0.0);
@@ -605,7 +606,7 @@ static cudaError_t iteration_ff(pint_handle* h) {
     const int np = residual_ff_grid(g, gx, gy, gz, chunk);
     prof_begin(h, PH_CHECK);
     launch_after_residual(h->partials, np, 1.0 / ((double)g.nt * g.nspace), h->ctl, h->st, h->gcond, h->capturing,
-                              upd_part(h), upd_part(h) ? time_inv_blocks(g.nt, g.nspace, f32_transforms(&h->p)) : 0);
+                              upd_part(h), upd_part(h) ? time_inv_ff_blocks(g.nt, g.nspace, h->ctl) : 0);
     prof_end(h, PH_CHECK, 1);
     prof_begin(h, PH_TFWD);
     cudaError_t e = launch_time_fwd<float>(g.nt, g.nspace, s, S, tb.twt, h->ctl, h->st);

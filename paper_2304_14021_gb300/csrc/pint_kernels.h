@@ -32,8 +32,9 @@ struct SolveCoef {
 };
 
 // Float-float form of Geo for the PINT_MIXED_FF residual (constants as hi + lo
-// pairs).  On square cells (and in 1-D) the stencil sums are unscaled and
-// c2, c1, cN already carry the factors 1/h^4, 1/h^2, 1/h^2.
+// pairs).  c2, c1, cN carry the factor dt (the residual is evaluated as
+// dt r); on square cells (and in 1-D) the stencil sums are unscaled and they
+// also carry the factors 1/h^4, 1/h^2, 1/h^2.
 struct GeoFF {
     int nx, ny, dim, bc, nt, nspace;
     float2 ihx2, ihy2, inv_dt, c2, c1, cN;
@@ -77,6 +78,8 @@ template <class T>
 cudaError_t launch_time_inv(int nt, int nspace, const c_t<T>* S, const c_t<T>* twt, const double* ginv, double* out,
                             int accumulate, const Ctl* ctl, double* dpart, cudaStream_t st);
 int time_inv_blocks(int nt, int nspace, int f32);
+// CTAs of launch_time_inv_ff (with the same control block argument).
+int time_inv_ff_blocks(int nt, int nspace, const Ctl* ctl);
 // Step 2: per frequency k, S[k] <- (lambda_1k I + lambda_2k A)^{-1} S[k], in
 // stages: 1-D: stage 0 = fused transform/divide/inverse along x.  2-D: stage 0
 // = forward along x, 1 = fused along y (with the division), 2 = inverse along x.
