@@ -124,7 +124,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // partials carry the factor 1/dt^2.  The CTA stages time level n+1 of its tile
 // (with halo) by asynchronous copies while it computes level n.
 template <int DIM, bool SQ, bool ACC>
-__global__ void __launch_bounds__(256) k_residual_ff(GeoFF g, const ff* __restrict__ U, const ff* __restrict__ u0,
+__global__ void __launch_bounds__(256, 5) k_residual_ff(GeoFF g, const ff* __restrict__ U, const ff* __restrict__ u0,
                                                      const float* __restrict__ gamf, float* __restrict__ s_out,
                                                      double* __restrict__ partials, const Ctl* __restrict__ ctl,
                                                      int chunk) {
@@ -136,7 +136,6 @@ __global__ void __launch_bounds__(256) k_residual_ff(GeoFF g, const ff* __restri
     constexpr int HY = DIM == 2 ? 2 : 0;
     constexpr int SX = TX + 4, SY = TY + 2 * HY;
     constexpr int LX = TX + 2, LY = TY + (DIM == 2 ? 2 : 0);
-    constexpr int TXT = DIM == 2 ? TX : NTHR, TYT = NTHR / TXT;   // thread grid of the staging loops
     __shared__ __align__(16) ff su[2][SY * SX];
     __shared__ ff sL[LY * LX];
     __shared__ ff sW[LY * LX];   // u^3 (Cahn-Hilliard)
@@ -144,7 +143,6 @@ __global__ void __launch_bounds__(256) k_residual_ff(GeoFF g, const ff* __restri
 
     const int tid = threadIdx.x;
     const int tx = tid % (DIM == 2 ? TX : TX / PPT), ty = tid / (DIM == 2 ? TX : TX / PPT);
-    const int sx_t = tid % TXT, sy_t = tid / TXT;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int n0 = blockIdx.z * chunk;
     const int n1 = min(g.nt, n0 + chunk);
@@ -154,40 +152,57 @@ __global__ void __launch_bounds__(256) k_residual_ff(GeoFF g, const ff* __restri
     // halo values are plain (reflected) copies except on simply supported boundary tiles
     const bool async_ok = interior || (g.bc == 1 && g.nx >= 2 && (DIM == 1 || g.ny >= 2));
 
+    // Per-thread work assignments, fixed for all levels (linear in the thread
+    // index, so only the last warps of a pass idle): halo-tile elements
+    // e = tid + a*NTHR of the staging copy, Laplacian points of the first pass.
+    constexpr int NST = (SX * SY + NTHR - 1) / NTHR, NLP = (LX * LY + NTHR - 1) / NTHR;
+    int goff[NST], soff[NST];            // source offset inside a level (-1: none), shared offset
+#pragma unroll
+    for (int a = 0; a < NST; ++a) {
+        const int e = tid + a * NTHR;
+        const int iy = e / SX, ix = e % SX;
+        goff[a] = -1;
+        soff[a] = e;
+        if (e < SX * SY) {
+            const int gy = DIM == 2 ? (interior ? y0 - HY + iy : reflect_n(y0 - HY + iy, g.ny)) : 0;
+            const int gx = interior ? x0 - 2 + ix : reflect_n(x0 - 2 + ix, g.nx);
+            goff[a] = gy * g.nx + gx;
+        }
+    }
+    int lc[NLP];                          // su index of the point (-1: none); its sL index is tid + a*NTHR
+#pragma unroll
+    for (int a = 0; a < NLP; ++a) {
+        const int e = tid + a * NTHR;
+        lc[a] = e < LX * LY ? (DIM == 2 ? (e / LX + 1) * SX : 0) + e % LX + 1 : -1;
+    }
     auto stage = [&](int n, ff* dst) {
         const ff* un = U + (size_t)n * g.nspace;
         if (async_ok) {
 #pragma unroll
-            for (int iy = sy_t; iy < SY; iy += TYT) {
-                const int gy = DIM == 2 ? (interior ? y0 - HY + iy : reflect_n(y0 - HY + iy, g.ny)) : 0;
-                const ff* rowp = un + (size_t)gy * g.nx;
-#pragma unroll
-                for (int ix = sx_t; ix < SX; ix += TXT) {
-                    const int gx = interior ? x0 - 2 + ix : reflect_n(x0 - 2 + ix, g.nx);
-                    cp_async8(&dst[iy * SX + ix], rowp + gx);
-                }
-            }
+            for (int a = 0; a < NST; ++a)
+                if (goff[a] >= 0) cp_async8(&dst[soff[a]], un + goff[a]);
             cp_async_commit();
         } else {
-            for (int iy = sy_t; iy < SY; iy += TYT)
-                for (int ix = sx_t; ix < SX; ix += TXT)
-                    dst[iy * SX + ix] = ext_read_ff(un, x0 - 2 + ix, y0 - HY + iy, g.nx, g.ny, DIM, g.bc);
+            for (int e = tid; e < SX * SY; e += NTHR)
+                dst[e] = ext_read_ff(un, x0 - 2 + e % SX, y0 - HY + e / SX, g.nx, g.ny, DIM, g.bc);
         }
     };
 
-    int pidx[PPT], cu[PPT], cl[PPT];
+    int cu[PPT], cl[PPT];
     bool inside[PPT];
     ff uprev[PPT];
+    float* sp[PPT];
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
         const int lx = tx + q * XSTEP, ly = ty + q * RSTEP;
         const int gx = x0 + lx, gy = y0 + ly;
         inside[q] = gx < g.nx && (DIM == 1 || gy < g.ny);
-        pidx[q] = (DIM == 2 ? gy * g.nx : 0) + gx;
+        const int pidx = (DIM == 2 ? gy * g.nx : 0) + gx;
         cu[q] = (ly + HY) * SX + lx + 2;
         cl[q] = (DIM == 2 ? (ly + 1) * LX : 0) + lx + 1;
         uprev[q] = ffmk(0.f, 0.f);
-        if (inside[q]) uprev[q] = n0 == 0 ? u0[pidx[q]] : U[(size_t)(n0 - 1) * g.nspace + pidx[q]];
+        if (inside[q]) uprev[q] = n0 == 0 ? u0[pidx] : U[(size_t)(n0 - 1) * g.nspace + pidx];
+        sp[q] = s_out + (size_t)n0 * g.nspace + pidx;
     }
     float acc_r2 = 0.f, acc_u2 = 0.f;
     const float sdt = g.inv_dt.x;
@@ -199,39 +214,39 @@ __global__ void __launch_bounds__(256) k_residual_ff(GeoFF g, const ff* __restri
         __syncthreads();                                   // level n staged; level n-1 fully consumed
         if (n + 1 < n1) stage(n + 1, su[(n + 1 - n0) & 1]);
 #pragma unroll
-        for (int ly = sy_t; ly < LY; ly += TYT)
-#pragma unroll
-            for (int lx = sx_t; lx < LX; lx += TXT) {
-                const int c = (DIM == 2 ? (ly + 1) * SX : 0) + lx + 1;
-                sL[ly * LX + lx] = lap_ff<DIM, SQ, ACC>(cur, c, SX, g);
-                if (ch) sW[ly * LX + lx] = ff_cube(cur[c]);
+        for (int a = 0; a < NLP; ++a)
+            if (lc[a] >= 0) {
+                sL[tid + a * NTHR] = lap_ff<DIM, SQ, ACC>(cur, lc[a], SX, g);
+                if (ch) sW[tid + a * NTHR] = ff_cube(cur[lc[a]]);
             }
         __syncthreads();
         const float gm = gamf[n] * sdt;
 #pragma unroll
         for (int q = 0; q < PPT; ++q) {
-            if (!inside[q]) continue;
-            const ff L = sL[cl[q]];
-            const ff u = cur[cu[q]];
-            const ff lapL = lap_ff<DIM, SQ, ACC>(sL, cl[q], LX, g);
-            ff r;
-            if constexpr (SQ && !ACC) {
-                ff_acc acc(uprev[q]);
-                acc.add(ff_neg(u));
-                acc.add(ff_neg(ff_mul(lapL, g.c2)));
-                if (lin1) acc.add(ff_neg(ff_mul(L, g.c1)));
-                if (ch) acc.add(ff_neg(ff_mul(lap_ff<DIM, SQ, ACC>(sW, cl[q], LX, g), g.cN)));
-                r = acc.get();
-            } else {
-                ff A = ff_mul(lapL, g.c2);
-                if (lin1) A = ff_add(A, ff_mul(L, g.c1));
-                if (ch) A = ff_add(A, ff_mul(lap_ff<DIM, SQ, ACC>(sW, cl[q], LX, g), g.cN));
-                r = ff_sub(ff_sub(uprev[q], u), A);
+            if (inside[q]) {
+                const ff L = sL[cl[q]];
+                const ff u = cur[cu[q]];
+                const ff lapL = lap_ff<DIM, SQ, ACC>(sL, cl[q], LX, g);
+                ff r;
+                if constexpr (SQ && !ACC) {
+                    ff_acc acc(uprev[q]);
+                    acc.add(ff_neg(u));
+                    acc.add(ff_neg(ff_mul(lapL, g.c2)));
+                    if (lin1) acc.add(ff_neg(ff_mul(L, g.c1)));
+                    if (ch) acc.add(ff_neg(ff_mul(lap_ff<DIM, SQ, ACC>(sW, cl[q], LX, g), g.cN)));
+                    r = acc.get();
+                } else {
+                    ff A = ff_mul(lapL, g.c2);
+                    if (lin1) A = ff_add(A, ff_mul(L, g.c1));
+                    if (ch) A = ff_add(A, ff_mul(lap_ff<DIM, SQ, ACC>(sW, cl[q], LX, g), g.cN));
+                    r = ff_sub(ff_sub(uprev[q], u), A);
+                }
+                *sp[q] = fmaf(gm, r.x, gm * r.y);
+                acc_r2 = fmaf(r.x, r.x, acc_r2);
+                acc_u2 = fmaf(u.x, u.x, acc_u2);
+                uprev[q] = u;
             }
-            s_out[(size_t)n * g.nspace + pidx[q]] = fmaf(gm, r.x, gm * r.y);
-            acc_r2 = fmaf(r.x, r.x, acc_r2);
-            acc_u2 = fmaf(u.x, u.x, acc_u2);
-            uprev[q] = u;
+            sp[q] += g.nspace;
         }
     }
     const double idt = (double)g.inv_dt.x + (double)g.inv_dt.y;
@@ -289,7 +304,9 @@ int residual_ff_grid(const Geo& g, int& gx, int& gy, int& gz, int& chunk) {
     gx = (g.nx + TX - 1) / TX;
     gy = g.dim == 2 ? (g.ny + TY - 1) / TY : 1;
     const long tiles = (long)gx * gy;
-    long want = (608 + tiles - 1) / tiles;
+    // one wave: 152 SMs x 5 resident CTAs (the kernel's launch bound), split over time
+    long want = 760 / tiles;
+    if (want < 1) want = 1;
     chunk = (int)((g.nt + want - 1) / want);
     if (chunk < 4) chunk = 4;
     if (chunk > g.nt) chunk = g.nt;

@@ -212,52 +212,93 @@ template <class T, int N> struct ColCfg {
     static constexpr int CW = sizeof(T) == 4 ? (N <= 512 ? 16 : 8) : (N <= 256 ? 16 : 8);
     // enough threads that each holds at most two radix-8 butterflies across a barrier
     static constexpr int NTH = N * CW >= 8192 ? 1024 : (N * CW >= 2048 ? 512 : 256);
-    static constexpr size_t SMEM = sizeof(c_t<T>) * (size_t)N * CW;
+    static constexpr size_t TILE = sizeof(c_t<T>) * (size_t)N * CW;
+    static constexpr int STAGES = 2 * TILE <= 160 * 1024 ? 2 : 1;
+    static constexpr size_t SMEM = STAGES * TILE;
 };
 
+// cp.async of one complex value (8 or 16 bytes), global -> shared.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_val(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_grp() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N_PENDING> __device__ __forceinline__ void cp_async_wait_grp() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N_PENDING) : "memory");
+}
+
+// Persistent CTAs over tiles (k, x block); with two stages the next tile is
+// fetched by asynchronous copies (landing in even/odd order) while the current
+// one is transformed.
 template <class T, int N>
 __global__ void __launch_bounds__(ColCfg<T, N>::NTH)
-    k_cols_dct_fdi(int nx, c_t<T>* __restrict__ S, Tabs<T> tb, SolveCoef co, const Ctl* __restrict__ ctl) {
+    k_cols_dct_fdi(int nx, int nk, c_t<T>* __restrict__ S, Tabs<T> tb, SolveCoef co, const Ctl* __restrict__ ctl) {
     using C = c_t<T>;
-    constexpr int CW = ColCfg<T, N>::CW, NTH = ColCfg<T, N>::NTH;
+    using Cfg = ColCfg<T, N>;
+    constexpr int CW = Cfg::CW, NTH = Cfg::NTH, STAGES = Cfg::STAGES;
     if (ctl && ctl->status != ST_RUNNING) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);
+    C* bufs = reinterpret_cast<C*>(smem_raw);
     const int tid = threadIdx.x;
-    const int k = blockIdx.y;
-    const int x0 = blockIdx.x * CW;
-    C* slab = S + (size_t)k * N * nx;
-    for (int e = tid; e < N * CW; e += NTH) {
-        const int c = e % CW, y = e / CW;
-        const int x = x0 + c;
-        buf[dct_pos(y, N) * CW + c] = x < nx ? slab[(size_t)y * nx + x] : mkc(T(0), T(0));
-    }
-    __syncthreads();
-    smem_fft<C, N, -1, NTH, CW, CW, 1>(buf, tb.twy);
-    const T c2 = T(co.c2), c1 = solve_c1<T>(co, ctl);
-    for (int e = tid; e < (N / 2 + 1) * CW; e += NTH) {
-        const int c = e % CW, p = e / CW, q = (N - p) % N;
-        const int x = x0 + c;
-        const C wp = tb.wy[p], wq = tb.wy[q];
-        C Xp, Xq;
-        dct_post(buf[p * CW + c], buf[q * CW + c], wp, wq, Xp, Xq);
-        if (x < nx) {
-            const T lx = tb.lamx[x];
-            Xp = cdiv(Xp, shift_den(tb, k, lx + tb.lamy[p], c2, c1));
-            Xq = cdiv(Xq, shift_den(tb, k, lx + tb.lamy[q], c2, c1));
+    const int nxb = (nx + CW - 1) / CW;
+    const int ntiles = nk * nxb;
+    auto stage = [&](int t, C* buf) {
+        const int k = t / nxb, x0 = (t % nxb) * CW;
+        const C* slab = S + (size_t)k * N * nx;
+        for (int e = tid; e < N * CW; e += NTH) {
+            const int c = e % CW, y = e / CW;
+            const int x = x0 + c;
+            C* d = &buf[dct_pos(y, N) * CW + c];
+            if (x < nx) cp_async_val<sizeof(C)>(d, slab + (size_t)y * nx + x);
+            else *d = mkc(T(0), T(0));
         }
-        C Vp, Vq;
-        dct_pre(p, Xp, Xq, wp, wq, Vp, Vq);
-        buf[p * CW + c] = Vp;
-        buf[q * CW + c] = Vq;
-    }
-    __syncthreads();
-    smem_fft<C, N, +1, NTH, CW, CW, 1>(buf, tb.twy);
-    const T inv = T(1) / T(N);
-    for (int e = tid; e < N * CW; e += NTH) {
-        const int c = e % CW, y = e / CW;
-        const int x = x0 + c;
-        if (x < nx) slab[(size_t)y * nx + x] = scalec(buf[dct_pos(y, N) * CW + c], inv);
+        cp_async_commit_grp();
+    };
+    const T c2 = T(co.c2), c1 = solve_c1<T>(co, ctl);
+    if (STAGES == 2) stage(blockIdx.x, bufs);
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        C* buf = bufs + (STAGES == 2 ? (it & 1) : 0) * (Cfg::TILE / sizeof(C));
+        if constexpr (STAGES == 2) {
+            if (t + gridDim.x < ntiles) {
+                stage(t + gridDim.x, bufs + ((it + 1) & 1) * (Cfg::TILE / sizeof(C)));
+                cp_async_wait_grp<1>();
+            } else {
+                cp_async_wait_grp<0>();
+            }
+        } else {
+            stage(t, buf);
+            cp_async_wait_grp<0>();
+        }
+        __syncthreads();
+        const int k = t / nxb, x0 = (t % nxb) * CW;
+        C* slab = S + (size_t)k * N * nx;
+        smem_fft<C, N, -1, NTH, CW, CW, 1>(buf, tb.twy);
+        for (int e = tid; e < (N / 2 + 1) * CW; e += NTH) {
+            const int c = e % CW, p = e / CW, q = (N - p) % N;
+            const int x = x0 + c;
+            const C wp = tb.wy[p], wq = tb.wy[q];
+            C Xp, Xq;
+            dct_post(buf[p * CW + c], buf[q * CW + c], wp, wq, Xp, Xq);
+            if (x < nx) {
+                const T lx = tb.lamx[x];
+                Xp = cdiv(Xp, shift_den(tb, k, lx + tb.lamy[p], c2, c1));
+                Xq = cdiv(Xq, shift_den(tb, k, lx + tb.lamy[q], c2, c1));
+            }
+            C Vp, Vq;
+            dct_pre(p, Xp, Xq, wp, wq, Vp, Vq);
+            buf[p * CW + c] = Vp;
+            buf[q * CW + c] = Vq;
+        }
+        __syncthreads();
+        smem_fft<C, N, +1, NTH, CW, CW, 1>(buf, tb.twy);
+        const T inv = T(1) / T(N);
+        for (int e = tid; e < N * CW; e += NTH) {
+            const int c = e % CW, y = e / CW;
+            const int x = x0 + c;
+            if (x < nx) slab[(size_t)y * nx + x] = scalec(buf[dct_pos(y, N) * CW + c], inv);
+        }
+        __syncthreads();   // buf is refilled two tiles later
     }
 }
 
@@ -536,9 +577,13 @@ static cudaError_t cfg_rows() {
     return cudaSuccess;
 }
 template <class T, int N>
+static int cols_resident();
+template <class T, int N>
 static cudaError_t cfg_cols() {
-    return cudaFuncSetAttribute(k_cols_dct_fdi<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)ColCfg<T, N>::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_cols_dct_fdi<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)ColCfg<T, N>::SMEM);
+    if (e != cudaSuccess) return e;
+    return cols_resident<T, N>() > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
 }
 
 template <class T>
@@ -590,21 +635,30 @@ static cudaError_t rows_dct(int nx, int nrows, int ny, c_t<T>* S, const Tabs<T>&
     }
 }
 template <class T, int N>
-static void cols_n(int nx, int nk, c_t<T>* S, const Tabs<T>& tb, SolveCoef co, const Ctl* ctl, cudaStream_t st) {
-    constexpr int CW = ColCfg<T, N>::CW;
-    dim3 grid((nx + CW - 1) / CW, nk);
-    k_cols_dct_fdi<T, N><<<grid, ColCfg<T, N>::NTH, ColCfg<T, N>::SMEM, st>>>(nx, S, tb, co, ctl);
+static int cols_resident() {
+    static const int r = persistent_ctas(k_cols_dct_fdi<T, N>, ColCfg<T, N>::NTH, ColCfg<T, N>::SMEM);
+    return r;
+}
+template <class T, int N>
+static cudaError_t cols_n(int nx, int nk, c_t<T>* S, const Tabs<T>& tb, SolveCoef co, const Ctl* ctl,
+                          cudaStream_t st) {
+    using Cfg = ColCfg<T, N>;
+    const int resident = cols_resident<T, N>();
+    if (resident <= 0) return cudaErrorInvalidConfiguration;
+    const int ntiles = nk * ((nx + Cfg::CW - 1) / Cfg::CW);
+    const int grid = ntiles < resident ? ntiles : resident;
+    k_cols_dct_fdi<T, N><<<grid, Cfg::NTH, Cfg::SMEM, st>>>(nx, nk, S, tb, co, ctl);
+    return cudaSuccess;
 }
 template <class T>
 static cudaError_t cols_dct(int nx, int ny, int nk, c_t<T>* S, const Tabs<T>& tb, SolveCoef co, const Ctl* ctl,
                             cudaStream_t st) {
     switch (ny) {
-#define C_(N) case N: cols_n<T, N>(nx, nk, S, tb, co, ctl, st); break;
+#define C_(N) case N: return cols_n<T, N>(nx, nk, S, tb, co, ctl, st);
         C_(2) C_(4) C_(8) C_(16) C_(32) C_(64) C_(128) C_(256) C_(512) C_(1024)
 #undef C_
         default: return cudaErrorInvalidValue;
     }
-    return cudaSuccess;
 }
 template <class T, int MODE>
 static void dense(int axis, int nx, int ny, int nk, c_t<T>* S, const Tabs<T>& tb, SolveCoef co, const Ctl* ctl,

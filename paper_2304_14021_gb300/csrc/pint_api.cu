@@ -12,6 +12,7 @@
 
 #include <atomic>
 #include <complex>
+#include <algorithm>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -436,8 +437,9 @@ static Sizes sizes_of(const pint_problem* p, pint_handle* tmp) {
     z.nk = p->nt / 2 + 1;
     int gx, gy, gz, chunk;
     const int nres = residual_grid(tmp->geo, gx, gy, gz, chunk);
+    const int nff = residual_ff_grid(tmp->geo, gx, gy, gz, chunk);
     const int nn = norm2_blocks((int)z.nspace);
-    z.partials = (size_t)(nres > nn ? nres : nn);
+    z.partials = (size_t)std::max(nres, std::max(nff, nn));
     TabLayout L = tab_layout(p, tmp->fft_x, tmp->fft_y);
     z.tables_T = L.total;
     const size_t ts = f32_transforms(p) ? 4 : 8;
