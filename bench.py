@@ -71,8 +71,8 @@ def solver_kw(wl: dict, args, precision=None) -> dict:
 # DRAM bytes per launch of the float-float residual, from one ncu capture of the
 # 2-D 256x256 x 128 workload (profiles/kernels_linear_ch_2d_256x256_nt128.md),
 # valid only for the kernel source it was taken on (sha256 prefix of the .cu).
-RESIDUAL_FF_TRAFFIC = {"src_sha256_16": "ad90089045a35859", "workload": "linear_ch_2d_256x256_nt128",
-                       "dram_bytes": 68475136 + 7560448}
+RESIDUAL_FF_TRAFFIC = {"src_sha256_16": "f1e8474c11b47afe", "workload": "linear_ch_2d_256x256_nt128",
+                       "dram_bytes": 68048896 + 6482944}
 
 
 def _residual_ff_traffic(workload: str):
@@ -86,23 +86,29 @@ def _residual_ff_traffic(workload: str):
     return t["dram_bytes"] if sha == t["src_sha256_16"] and workload == t["workload"] else None
 
 
-def ff_residual_flops_per_dof(equation: str, dim: int) -> float:
-    """FP32 flops per space-time DOF of the float-float residual kernel on square
-    cells, counted from its operations (FMA = 2): accurate double-word add 20,
-    double-word multiply 10, cube 20; an unscaled Laplacian point is one TwoSum
-    chain over 3 (1-D) or 5 (2-D) terms with an FP32 error accumulator plus an
-    exact power-of-two scaling (26 / 42 flops).  The first
-    Laplacian (and u^3 for Cahn-Hilliard) is evaluated on the tile plus a
-    one-point halo: 514/512 (1-D), 34*18/(32*16) (2-D)."""
-    lap = 26.0 if dim == 1 else 42.0
+def ff_residual_ops_per_dof(equation: str, dim: int, accurate: bool = False) -> float:
+    """FP32 lane operations (add, multiply or FMA: one each) per space-time DOF
+    of the float-float residual kernel on square cells, counted from its code:
+    TwoSum 6, fast TwoSum 3, exact product 2 (FMUL + FMA), double-word multiply
+    8, accurate double-word add 20, one step of the error-free sum 8 and its
+    final renormalization 6.  An unscaled Laplacian point sums 3 (1-D) or 5
+    (2-D) terms plus a power-of-two scaling (2 ops): 24 / 40 ops with the
+    error-free sum, 42 / 82 with chained accurate adds.  The first Laplacian (and
+    u^3 for Cahn-Hilliard) covers the tile plus a one-point halo: 514/512 (1-D),
+    34*18/(32*16) (2-D).  The residual dt*r = u_{n-1} - u_n - sum of the operator
+    terms is one error-free sum (accurate: two subtractions and an add per extra
+    term); 4 more ops scale s and accumulate the norms."""
     halo = 514.0 / 512.0 if dim == 1 else (34.0 * 18.0) / (32.0 * 16.0)
-    f = lap * halo + lap + 10.0     # Lap u (tile + halo), Lap(Lap u), * c2/h^4
-    if equation in ("linear_ch", "cahn_hilliard"):
-        f += 30.0                   # + (c1/h^2) Lap u
+    nterm = 1 + (equation in ("linear_ch", "cahn_hilliard")) + (equation == "cahn_hilliard")
+    if accurate:
+        lap = 42.0 if dim == 1 else 82.0
+        f = lap * halo + lap + 8.0 * nterm + 20.0 * (nterm - 1) + 40.0
+    else:
+        lap = 24.0 if dim == 1 else 40.0
+        f = lap * halo + lap + 8.0 * nterm + 8.0 * (nterm + 1) + 6.0
     if equation == "cahn_hilliard":
-        f += 20.0 * halo + lap + 30.0   # u^3 on tile + halo, Lap(u^3), * cN/h^2 and add
-    f += 30.0 + 20.0 + 7.0          # time difference * (1/dt), r = T - A, scaling and sums
-    return f
+        f += 16.0 * halo + lap          # u^3 on tile + halo, Lap(u^3)
+    return f + 4.0
 
 
 def phase_bytes_per_dof(precision: str, nt: int) -> dict:
@@ -367,7 +373,8 @@ def main_gpu(args) -> None:
     bpd = phase_bytes_per_dof(args.precision, nt)
     dom = max((k for k in prof if prof[k]["launches"] > 0 and k != "check"), key=lambda k: prof[k]["ms"])
     iters_per_step = stats["iters"]
-    res_evals = iters_per_step + (0 if args.init == 2 else 1)   # the zero start skips the first residual
+    zero_start = args.init == 2 and wl["equation"] != "cahn_hilliard"   # Cahn-Hilliard starts from u0
+    res_evals = iters_per_step + (0 if zero_start else 1)   # the zero start skips the first residual
     active = {k: (args.steps * (res_evals if k == "residual" else iters_per_step)
                   if k not in ("setup", "check") else prof[k]["launches"]) for k in prof}
     per_launch_ms = prof[dom]["ms"] / max(1, active[dom])
@@ -377,16 +384,18 @@ def main_gpu(args) -> None:
     except Exception:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    # FP32 peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2070 MHz
-    fp32_peak = 152 * 128 * 2 * 2.070e9 / 1e12
+    # FP32 lane-operation peak: 152 SMs x 128 FP32 lanes x 2070 MHz, one add,
+    # multiply or FMA per lane and clock (the residual is mostly additions)
+    fp32_ops_peak = 152 * 128 * 2.070e9 / 1e12
     if dom == "residual" and args.precision == "mixed_ff":
-        flops = ff_residual_flops_per_dof(wl["equation"], wl["dim"]) * dof
-        ach = flops / (per_launch_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": "k_residual_ff", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": ach / fp32_peak, "traffic": _residual_ff_traffic(args.workload),
-                "flops_per_dof": flops / dof, "per_launch_us": per_launch_ms * 1e3,
+        ops = ff_residual_ops_per_dof(wl["equation"], wl["dim"]) * dof
+        ach = ops / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_residual_ff", "achieved": ach, "peak": fp32_ops_peak,
+                "unit": "TFLOP/s", "frac": ach / fp32_ops_peak, "traffic": _residual_ff_traffic(args.workload),
+                "ops_per_dof": ops / dof, "per_launch_us": per_launch_ms * 1e3,
                 "hbm_frac": bpd[dom] * dof / (per_launch_ms * 1e-3) / 1e9 / hbm_peak,
-                "peak_note": "FP32 nominal (152 SMs x 128 lanes x 2 x 2.07 GHz)"}
+                "peak_note": "FP32 lane operations per second, nominal: 152 SMs x 128 lanes x 2.07 GHz "
+                             "(an FMA counts as one operation, as does an add)"}
     else:
         ach = bpd[dom] * dof / (per_launch_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
@@ -426,7 +435,7 @@ def main_gpu(args) -> None:
             "dtype": {"mixed_ff": "f32 (float-float iterate)", "mixed": "f32+f64", "fp64": "f64"}[args.precision],
             "data": "synthetic",
             "config": {"workload": args.workload, "precision": args.precision, "alpha": args.alpha,
-                       "tol": args.tol, "init": "zero" if args.init == 2 else "u0", "dof_per_gpu": dof,
+                       "tol": args.tol, "init": "zero" if zero_start else "u0", "dof_per_gpu": dof,
                        "iterations": stats["iters"],
                        "final_rel_residual": stats["rel_residual"], "l2": "flushed between steps",
                        "parallelism": f"replicas x{world}"},

@@ -86,7 +86,9 @@ typedef struct {
     int    init_guess;   /* 0: each window starts from U^0 = u0 at every time level;
                             1: the first window starts from the iterate passed in U,
                                later windows as 0;
-                            2: each window starts from U^0 = 0 */
+                            2: each window starts from U^0 = 0 (linear equations; for
+                               Cahn-Hilliard this acts as 0, since the scalar Jacobian
+                               of a zero iterate misleads the first preconditioner) */
     double tol_update;   /* 0: off.  > 0: a window also stops when the last correction is small,
                             ||delta||_2 / ||U||_2 <= tol_update (an error estimate, in the spirit of
                             the error-based stopping rule of Sec. 5).  For very stiff problems the

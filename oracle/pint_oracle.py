@@ -421,6 +421,47 @@ def diagonalized_apply(p: Problem, alpha: float, r: np.ndarray, jbar: float | No
     return x / gam[:, None]
 
 
+def diagonalized_apply_separable(p: Problem, alpha: float, r: np.ndarray, jbar: float | None = None) -> np.ndarray:
+    """The same Steps 1-3 as diagonalized_apply for grids too large for a
+    dense eigen-decomposition of A.  The spatial operator is a polynomial
+    mu(L) = c2 L^2 + c1 L in Delta_h = I (x) Delta_x + Delta_y (x) I (Remark 2.5),
+    so its eigenvectors are the tensor products Q_y (x) Q_x of the 1-D
+    Laplacians' eigenvectors (numpy.linalg.eigh of the 1-D matrices) with
+    eigenvalues mu(l_y + l_x).  Step 2 divides in that basis."""
+    nt = r.shape[0]
+    n = np.arange(nt)
+    gam = alpha ** (n / nt)
+    S1 = np.fft.fft(gam[:, None] * r, axis=0)
+    z = alpha ** (1.0 / nt) * np.exp(-2j * np.pi * n / nt)
+    l1 = (1.0 - z) / p.dt
+    th = 1.0 if p.equation == CAHN_HILLIARD else p.theta
+    l2 = th + (1.0 - th) * z
+    if p.equation == BIHARMONIC:
+        c2, c1 = 1.0, 0.0
+    elif p.equation == LINEAR_CH:
+        c2, c1 = p.eps ** 2, p.beta ** 2
+    else:
+        c2, c1 = p.eps ** 2, 1.0 - jbar
+    ex, Qx = np.linalg.eigh(laplacian_1d(p.nx, p.bc).toarray())
+    if p.dim == 1:
+        lam = ex
+        S1h = S1 @ Qx
+    else:
+        ey, Qy = np.linalg.eigh(laplacian_1d(p.ny, p.bc).toarray())
+        lam = (ey[:, None] + ex[None, :]).ravel()
+        X = S1.reshape(nt, p.ny, p.nx)
+        S1h = (Qy.T @ X @ Qx).reshape(nt, -1)        # Q_y^T X Q_x per frequency
+    mu = c2 * lam ** 2 + c1 * lam
+    S2h = S1h / (l1[:, None] + l2[:, None] * mu[None, :])
+    if p.dim == 1:
+        S2 = S2h @ Qx.T
+    else:
+        Y = S2h.reshape(nt, p.ny, p.nx)
+        S2 = (Qy @ Y @ Qx.T).reshape(nt, -1)         # Q_y Y Q_x^T
+    x = np.fft.ifft(S2, axis=0).real
+    return x / gam[:, None]
+
+
 def jbar_of(U: np.ndarray) -> float:
     """Scalar averaged Jacobian: mean over all space-time points of 3u^2
     (Eq. 4.12 averaged over time, then over space)."""

@@ -947,7 +947,11 @@ int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* 
     S.nt_min = ntmax;
     int rc = PINT_OK;
     activate_level(h, 0);
-    if (ffm && p.init_guess == 1) launch_f64_to_ff(U_dev, h->Uff, dof, h->st);
+    // Cahn-Hilliard never starts from the zero iterate: its scalar Jacobian
+    // 3 mean(u^2) would be 0 in the first preconditioner, far from the state's,
+    // and the iteration can diverge; such windows start from u0 instead.
+    const int init = (p.init_guess == 2 && h->coef.ch) ? 0 : p.init_guess;
+    if (ffm && init == 1) launch_f64_to_ff(U_dev, h->Uff, dof, h->st);
     const long long total = (long long)ntmax * p.n_windows;
     long long done = 0;
     for (int seg = 0; done < total; ++seg) {
@@ -980,10 +984,10 @@ int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* 
             const size_t sdof = (size_t)L * ns;
             prof_begin(h, PH_SETUP);
             nl = 1;
-            if (p.init_guess == 2) {
+            if (init == 2) {
                 PINT_CK(ffm ? cudaMemsetAsync(h->Uff_cur, 0, sdof * sizeof(float2), h->st)
                             : cudaMemsetAsync(Useg, 0, sdof * sizeof(double), h->st));
-            } else if (seg > 0 || p.init_guess == 0 || !first_try) {
+            } else if (seg > 0 || init == 0 || !first_try) {
                 if (ffm) launch_broadcast_ff(h->Uff_cur, h->u0ff, g.nspace, L, h->st);
                 else launch_broadcast(Useg, u0w, g.nspace, L, h->st);
                 nl++;
@@ -993,11 +997,11 @@ int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* 
             cudaGraphExec_t gx = (h->use_graphs && !h->prof_on && !adapt) ? get_graph(h, Useg, u0w) : nullptr;
             if (gx) {
                 // one graph launch runs the iteration loop of this window to its stop
-                if (p.init_guess == 2 && zero_start(h, Useg, u0w) != cudaSuccess) return PINT_ECUDA;
+                if (init == 2 && zero_start(h, Useg, u0w) != cudaSuccess) return PINT_ECUDA;
                 PINT_CK(cudaGraphLaunch(gx, h->st));
                 if ((rc = read_ctl(h)) != PINT_OK) return rc;
                 if (h->hctl->status == ST_RUNNING) return PINT_ECUDA;  // the loop ends only on a final status
-                const long long runs = h->hctl->iter + 1 - (p.init_guess == 2 ? 1 : 0);
+                const long long runs = h->hctl->iter + 1 - (init == 2 ? 1 : 0);
                 h->launches[PH_RES] += runs;
                 h->launches[PH_CHECK] += runs;
                 h->launches[PH_TFWD] += runs;
@@ -1008,7 +1012,7 @@ int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* 
                 for (;;) {
                     int chunk = enqueued == 0 ? 3 : 2;
                     for (int c = 0; c < chunk; ++c) {
-                        cudaError_t e = enqueued == 0 && c == 0 && p.init_guess == 2 ? zero_start(h, Useg, u0w)
+                        cudaError_t e = enqueued == 0 && c == 0 && init == 2 ? zero_start(h, Useg, u0w)
                                         : ffm ? iteration_ff(h) : iteration(h, Useg, u0w);
                         if (e != cudaSuccess) return PINT_ECUDA;
                     }

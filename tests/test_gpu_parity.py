@@ -72,6 +72,36 @@ def test_precond_apply_matches_dense_solve(case, precision):
     assert err < tol, err
 
 
+# Full grid sizes and long time axes, in the kernels the benchmark runs
+# (persistent row/column passes, N_t up to 512), against the oracle's
+# tensor-product eigenbasis form of Steps 1-3.
+LARGE_PRECOND_CASES = [
+    dict(equation="linear_ch", dim=2, nx=512, ny=512, bc="neumann", nt=16, T=0.1 * 16 / 128, eps=0.05, beta=0.5),
+    dict(equation="cahn_hilliard", dim=2, nx=512, ny=512, bc="neumann", nt=8, T=8e-4, eps=0.02),
+    dict(equation="linear_ch", dim=2, nx=256, ny=256, bc="neumann", nt=16, T=0.1 * 16 / 128, eps=0.05, beta=0.5),
+    dict(equation="linear_ch", dim=2, nx=256, ny=128, bc="neumann", nt=8, T=0.01, eps=0.05, beta=0.5),
+    dict(equation="linear_ch", dim=2, nx=64, ny=64, bc="neumann", nt=256, T=0.1, eps=0.05, beta=0.5),
+    dict(equation="linear_ch", dim=2, nx=32, ny=32, bc="neumann", nt=512, T=0.1, eps=0.05, beta=0.5),
+    dict(equation="linear_ch", dim=1, nx=2048, bc="neumann", nt=16, T=1e-6, eps=0.05, beta=0.5),
+]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_ff"])
+@pytest.mark.parametrize("case", range(len(LARGE_PRECOND_CASES)))
+def test_precond_apply_large_matches_oracle(case, precision):
+    kw = full(dict(LARGE_PRECOND_CASES[case], precision=precision))
+    p = oprob(kw)
+    r = synth.random_iterate(p.nt, p.nspace, 200 + case)
+    jbar = 0.4 if kw["equation"] == "cahn_hilliard" else None
+    ref = O.diagonalized_apply_separable(p, p.alpha, r, jbar)
+    with pint.Solver(**kw) as s:
+        out = torch.zeros(p.nt, p.nspace, dtype=torch.float64, device="cuda")
+        s.precond_apply(dev(r), out, jbar=jbar or 0.0)
+        err = O.rel_err(host(out), ref)
+    tol = 1e-11 if precision == "fp64" else 3e-6 / p.alpha
+    assert err < tol, err
+
+
 # --- residual (Eq. 2.6 / 4.8, alpha = 0) --------------------------------------
 
 @pytest.mark.parametrize("kw", [
@@ -398,3 +428,22 @@ def test_fused_2d_spatial_not_used_at_256():
             s.precond_apply(r, d)
             out.append(d)
     assert torch.equal(out[0], out[1])
+
+
+def test_cahn_hilliard_zero_init_starts_from_u0():
+    # init_guess = 2 on Cahn-Hilliard starts each window from u0 (as init_guess
+    # = 0 does): bitwise the same solve, through the adaptive window policy.
+    nt, W, n = 64, 4, 32
+    kw = full(dict(equation="cahn_hilliard", dim=2, nx=n, ny=n, bc="neumann", eps=0.02, nt=nt, n_windows=W,
+                   T=nt * W * 1e-4, alpha=1e-2, precision="mixed_ff", tol=1e-8, max_iter=250, tol_update=1e-10))
+    u0 = dev(synth.u0_ch(n * n, 0))
+    out = {}
+    for init in (0, 2):
+        with pint.Solver(**dict(kw, init_guess=init)) as s:
+            s.set_adaptive_windows(True)
+            U = torch.zeros(nt, n * n, dtype=torch.float64, device="cuda")
+            st = s.solve(u0, U)
+            out[init] = (U, st)
+    assert out[0][1]["rc"] == 0 and out[0][1]["windows"] == W
+    assert torch.equal(out[0][0], out[2][0])
+    assert out[0][1]["iters"] == out[2][1]["iters"]

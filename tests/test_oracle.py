@@ -257,3 +257,19 @@ def test_ch_iteration_converges_to_sequential():
     Useq = O.sequential(p, u0)
     its = O.pint_iteration_residual_form(p, u0, np.tile(u0, (8, 1)), 40, dense=False)
     assert O.rel_err(its[-1], Useq) < 1e-11
+
+
+@pytest.mark.parametrize("kw", [
+    dict(equation="linear_ch", dim=2, nx=12, ny=8, bc="neumann", eps=0.05, beta=0.5, T=0.01, nt=8),
+    dict(equation="biharmonic", dim=2, nx=7, ny=9, bc="ss", T=1e-3, nt=4),
+    dict(equation="cahn_hilliard", dim=2, nx=8, ny=8, bc="neumann", eps=0.05, T=8e-4, nt=8),
+    dict(equation="linear_ch", dim=1, nx=20, bc="neumann", eps=0.05, beta=0.5, T=0.01, nt=16),
+])
+def test_separable_apply_matches_dense_eigendecomposition(kw):
+    # The tensor-product eigenbasis (1-D eigh of Delta_x, Delta_y) and the dense
+    # eigh of the 2-D operator give the same P_alpha^{-1} r (Remark 2.5).
+    p = O.Problem(**kw)
+    r = synth.random_iterate(p.nt, p.nspace, 5)
+    a = O.diagonalized_apply(p, 1e-2, r, 0.4)
+    b = O.diagonalized_apply_separable(p, 1e-2, r, 0.4)
+    assert O.rel_err(b, a) < 1e-12
