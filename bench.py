@@ -271,7 +271,8 @@ def main_gpu(args) -> None:
     if args.no_graphs:
         s.set_graphs(False)
     nt, ns = s.nt, s.nspace
-    dof = nt * ns
+    nwin = wl.get("n_windows", 1)
+    dof = nt * ns * nwin                 # space-time DOF of the whole solve (all windows)
     u0 = torch.from_numpy(u0_np).cuda()
     U = torch.zeros(nt, ns, dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -371,6 +372,9 @@ def main_gpu(args) -> None:
     # Per-launch time = phase time / launches, where launches that found the
     # solve already converged (early exits at the end of a chunk) are excluded.
     bpd = phase_bytes_per_dof(args.precision, nt)
+    # DOF one launch processes: a window, or under the adaptive window policy a
+    # segment (approximated by the mean segment size of the solve)
+    dof_l = dof / max(1, stats.get("segments", 1)) if nwin > 1 or stats.get("segments", 1) > 1 else dof
     dom = max((k for k in prof if prof[k]["launches"] > 0 and k != "check"), key=lambda k: prof[k]["ms"])
     iters_per_step = stats["iters"]
     zero_start = args.init == 2 and wl["equation"] != "cahn_hilliard"   # Cahn-Hilliard starts from u0
@@ -388,16 +392,16 @@ def main_gpu(args) -> None:
     # multiply or FMA per lane and clock (the residual is mostly additions)
     fp32_ops_peak = 152 * 128 * 2.070e9 / 1e12
     if dom == "residual" and args.precision == "mixed_ff":
-        ops = ff_residual_ops_per_dof(wl["equation"], wl["dim"]) * dof
+        ops = ff_residual_ops_per_dof(wl["equation"], wl["dim"]) * dof_l
         ach = ops / (per_launch_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": "k_residual_ff", "achieved": ach, "peak": fp32_ops_peak,
                 "unit": "TFLOP/s", "frac": ach / fp32_ops_peak, "traffic": _residual_ff_traffic(args.workload),
-                "ops_per_dof": ops / dof, "per_launch_us": per_launch_ms * 1e3,
-                "hbm_frac": bpd[dom] * dof / (per_launch_ms * 1e-3) / 1e9 / hbm_peak,
+                "ops_per_dof": ops / dof_l, "per_launch_us": per_launch_ms * 1e3,
+                "hbm_frac": bpd[dom] * dof_l / (per_launch_ms * 1e-3) / 1e9 / hbm_peak,
                 "peak_note": "FP32 lane operations per second, nominal: 152 SMs x 128 lanes x 2.07 GHz "
                              "(an FMA counts as one operation, as does an add)"}
     else:
-        ach = bpd[dom] * dof / (per_launch_ms * 1e-3) / 1e9
+        ach = bpd[dom] * dof_l / (per_launch_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                 "frac": ach / hbm_peak, "traffic": None, "bytes_per_dof": bpd[dom],
                 "per_launch_us": per_launch_ms * 1e3, "peak_note": "MEASURED_PEAKS.json hbm_gbs (measured)"}
@@ -408,7 +412,7 @@ def main_gpu(args) -> None:
         t_l = v["ms"] / max(1, active[k])
         phases[k] = {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
                      "us_per_active_launch": t_l * 1e3,
-                     "hbm_frac": (bpd[k] * dof / (t_l * 1e-3) / 1e9 / hbm_peak) if bpd.get(k) else None}
+                     "hbm_frac": (bpd[k] * dof_l / (t_l * 1e-3) / 1e9 / hbm_peak) if bpd.get(k) else None}
     launches_total = sum(v["launches"] for v in launches_a.values())
 
     if rank == 0:
@@ -440,7 +444,7 @@ def main_gpu(args) -> None:
                        "final_rel_residual": stats["rel_residual"], "l2": "flushed between steps",
                        "parallelism": f"replicas x{world}"},
             "e2e": ({"value": world * dof / e2e_s, "unit": "space-time DOF/s", "h2d_bytes_per_step": ns * 8,
-                     "d2h_bytes_per_step": dof * 8} if e2e_s else None),
+                     "d2h_bytes_per_step": nt * ns * 8} if e2e_s else None),
             "gpu_launches": launches_total,
             "ms_per_step_profiled_pass": ms_b,
             "roofline": roof,

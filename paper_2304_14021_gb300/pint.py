@@ -22,6 +22,7 @@ HIST_MAX = 256
 EQUATIONS = {"biharmonic": BIHARMONIC, "linear_ch": LINEAR_CH, "cahn_hilliard": CAHN_HILLIARD}
 BCS = {"ss": BC_SIMPLY_SUPPORTED, "neumann": BC_NEUMANN}
 PRECISIONS = {"fp64": FP64, "mixed": MIXED, "mixed_ff": MIXED_FF}
+PRECISION_NAMES = {v: k for k, v in PRECISIONS.items()}
 
 
 class Problem(C.Structure):
@@ -35,13 +36,14 @@ class Stats(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("windows", C.c_int), ("iters_last", C.c_int),
                 ("rel_residual", C.c_double), ("contraction", C.c_double), ("jbar", C.c_double),
                 ("hist", C.c_double * HIST_MAX), ("segments", C.c_int), ("nt_min", C.c_int),
-                ("retries", C.c_int), ("update_norm", C.c_double)]
+                ("retries", C.c_int), ("update_norm", C.c_double), ("precision", C.c_int)]
 
     def as_dict(self) -> dict:
         return {"status": self.status, "iters": self.iters, "windows": self.windows,
                 "iters_last": self.iters_last, "rel_residual": self.rel_residual,
                 "contraction": self.contraction, "jbar": self.jbar, "segments": self.segments,
                 "nt_min": self.nt_min, "retries": self.retries, "update_norm": self.update_norm,
+                "precision": PRECISION_NAMES.get(self.precision, self.precision),
                 "hist": [self.hist[i] for i in range(min(self.iters_last + 1, HIST_MAX))]}
 
 

@@ -38,7 +38,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_struct_sizes_match_header_layout(lib):
     # pint_problem: 5 ints (+4 pad), 3 doubles, 2 ints, 3 doubles, 3 ints (+4 pad)
     assert C.sizeof(pint.Problem) == 24 + 24 + 8 + 24 + 16 + 8
-    assert C.sizeof(pint.Stats) == 16 + 3 * 8 + 256 * 8 + 16 + 8
+    assert C.sizeof(pint.Stats) == 16 + 3 * 8 + 256 * 8 + 16 + 8 + 8
 
 
 def test_strerror(lib):
@@ -83,3 +83,15 @@ def test_null_arguments_rejected(lib):
     assert lib.pint_residual(None, None, None, None, None) == pint.PINT_EINVAL
     assert lib.pint_precond_apply(None, C.c_double(0.0), None, None) == pint.PINT_EINVAL
     lib.pint_destroy(None)
+
+
+def test_precision_policy_falls_back_to_fp64_when_too_stiff():
+    # 2^-24 * dt * max|spectrum| > 1 (1-D biharmonic, 4096 cells, dt = 0.01/32):
+    # the FP32 inner solves cannot be refined, the problem runs (and is sized) in FP64.
+    stiff = dict(equation="biharmonic", dim=1, nx=4096, bc="neumann", T=0.01, nt=32, alpha=1e-2, tol=1e-8)
+    assert pint.footprint(**stiff, precision="mixed_ff") == pint.footprint(**stiff, precision="fp64")
+    assert pint.footprint(**stiff, precision="mixed") == pint.footprint(**stiff, precision="fp64")
+    # 2-D linearized CH 256^2, N_t = 128, T = 0.1: about 0.03, FP32 inner solves kept
+    mild = dict(equation="linear_ch", dim=2, nx=256, ny=256, bc="neumann", eps=0.05, beta=0.5, T=0.1, nt=128,
+                alpha=1e-2, tol=1e-8)
+    assert pint.footprint(**mild, precision="mixed_ff") < pint.footprint(**mild, precision="fp64")

@@ -447,3 +447,21 @@ def test_cahn_hilliard_zero_init_starts_from_u0():
     assert out[0][1]["rc"] == 0 and out[0][1]["windows"] == W
     assert torch.equal(out[0][0], out[2][0])
     assert out[0][1]["iters"] == out[2][1]["iters"]
+
+
+@pytest.mark.parametrize("which", [7, 9])
+def test_stiff_instances_run_in_fp64_and_converge(which):
+    # Instances of the batched workload too stiff for FP32 inner solves
+    # (1-D biharmonic 4096 cells; 1-D Cahn-Hilliard 2048 cells): they run in
+    # FP64, report it, and converge; the result matches an explicit FP64 solve.
+    x = synth.batched_instances(64, 0, alpha=1e-2)[which]
+    kw = dict(x["problem"], tol=1e-8, max_iter=250, init_guess=2, tol_update=1e-10)
+    u0 = dev(x["u0"])
+    out = {}
+    for prec in ("mixed_ff", "fp64"):
+        with pint.Solver(**dict(kw, precision=prec)) as s:
+            U = torch.zeros(kw["nt"], u0.numel(), dtype=torch.float64, device="cuda")
+            out[prec] = (U, s.solve(u0, U))
+    assert out["mixed_ff"][1]["precision"] == "fp64"
+    assert out["mixed_ff"][1]["rc"] == 0
+    assert torch.equal(out["mixed_ff"][0], out["fp64"][0])
