@@ -114,8 +114,8 @@ typedef struct {
     double update_norm;       /* ||delta||_2 / ||U||_2 of the last correction of the last window
                                  (computed when tol_update > 0, else 0) */
     int    precision;         /* pint_precision the solve ran in: the requested one, or PINT_FP64
-                                 when 2^-24 * dt * max|spectrum of A| > 1, where FP32 inner solves
-                                 cannot be refined by the outer iteration */
+                                 when 2^-24 * dt * max|spectrum of A| > 1 (0.1 for Cahn-Hilliard),
+                                 where FP32 inner solves cannot be refined by the outer iteration */
 } pint_stats;
 
 typedef struct pint_handle pint_handle;

@@ -728,13 +728,15 @@ double stiffness_of(const pint_problem* p) {
 
 // Precision a problem runs in.  The FP32 inner solves act as a preconditioner
 // refined by the outer iteration, which needs their error amplified by the
-// stiff operator, about 2^-24 * dt * max|spectrum|, to stay below one; above
-// that the FP32 rounding of the correction's high modes dominates the next
-// residual (observed: residual growth on 1-D grids of 2048-4096 points), and
-// the whole solve runs in FP64.
+// stiff operator, about 2^-24 * dt * max|spectrum|, to stay below one (0.1 for
+// Cahn-Hilliard, whose Jacobian moves between iterations); above that the FP32
+// rounding of the correction's high modes dominates the next residual
+// (observed: residual growth on 1-D grids of 1024-4096 points), and the whole
+// solve runs in FP64.
 int effective_precision(const pint_problem* p) {
     if (p->precision == PINT_FP64) return PINT_FP64;
-    return stiffness_of(p) * 0x1p-24 > 1.0 ? PINT_FP64 : p->precision;
+    const double limit = p->equation == PINT_CAHN_HILLIARD ? 0.1 : 1.0;
+    return stiffness_of(p) * 0x1p-24 > limit ? PINT_FP64 : p->precision;
 }
 
 }  // namespace pint
