@@ -194,11 +194,120 @@ __global__ void __launch_bounds__(256, RowCfg<T, N>::MINB) k_rows_dct(int nrows,
                 if (gr < nrows) S[r0 * N + e] = scalec(buf[b * N + swz<1>(dct_pos(i, N))], inv);
             }
         }
-        __syncthreads();   // every thread is done with buf
-        if (tid == 0 && t + STAGES * gridDim.x < ntiles) {
-            fence_proxy_async_smem();
-            issue(t + STAGES * gridDim.x, st);
+        fence_proxy_async_smem();   // this thread's accesses to buf precede the refill
+        __syncthreads();            // every thread is done with buf
+        if (tid == 0 && t + STAGES * gridDim.x < ntiles) issue(t + STAGES * gridDim.x, st);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Rows, warp-per-row form (128 <= N <= 512): every warp streams its own rows
+// (row r = global warp id + i * all warps) through two shared-memory stages of
+// its own, filled by bulk asynchronous copies one row ahead and completed on
+// the warp's own mbarriers.  A warp synchronizes only with itself, so the
+// warps of a CTA do not wait for one another at all.
+// ---------------------------------------------------------------------------
+template <class T, int N> struct RowWCfg {
+    static constexpr int WARPS = 8, NTH = 32 * WARPS, STAGES = 2;
+    static constexpr size_t ROWB = sizeof(c_t<T>) * N;
+    static constexpr size_t BAR_OFF = (size_t)WARPS * STAGES * ROWB;
+    static constexpr size_t SMEM = BAR_OFF + 8 * WARPS * STAGES;
+    static constexpr int MINB = sizeof(T) == 4 && N <= 256 ? 4 : 2;
+};
+template <class T, int N>
+constexpr bool rows_warp_ok = N >= 128 && N <= (sizeof(T) == 4 ? 512 : 256);
+
+template <class T, int N, int MODE>
+__global__ void __launch_bounds__(256, RowWCfg<T, N>::MINB) k_rows_dct_w(int nrows, int ny, c_t<T>* __restrict__ S,
+                                                                         Tabs<T> tb, SolveCoef co,
+                                                                         const Ctl* __restrict__ ctl) {
+    using C = c_t<T>;
+    using Cfg = RowWCfg<T, N>;
+    constexpr int STAGES = Cfg::STAGES, NP = N / 2 + 1, PPL = (NP + 31) / 32;
+    if (ctl && ctl->status != ST_RUNNING) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    C* mybuf = reinterpret_cast<C*>(smem_raw) + (size_t)warp * STAGES * N;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + Cfg::BAR_OFF) + warp * STAGES;
+    const int gw = blockIdx.x * Cfg::WARPS + warp, nw = gridDim.x * Cfg::WARPS;
+    auto issue = [&](int r, int st) {
+        mbar_arrive_expect_tx(&bar[st], (uint32_t)Cfg::ROWB);
+        bulk_g2s(mybuf + st * N, S + (size_t)r * N, (uint32_t)Cfg::ROWB, &bar[st]);
+    };
+    if (lane == 0) {
+        for (int st = 0; st < STAGES; ++st) mbar_init(&bar[st], 1);
+        mbar_fence_init();
+        for (int st = 0; st < STAGES; ++st)
+            if (gw + st * nw < nrows) issue(gw + st * nw, st);
+    }
+    __syncwarp();
+    const T c2 = T(co.c2), c1 = solve_c1<T>(co, ctl);
+    int it = 0;
+    for (int r = gw; r < nrows; r += nw, ++it) {
+        const int st = it % STAGES;
+        C* row = mybuf + st * N;
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bar[st], (uint32_t)(it / STAGES) & 1u))) {
+            if (lane == 0) {
+                note_timeout(ctl);
+                for (int k = 0; k < STAGES; ++k)
+                    if (r + k * nw < nrows) mbar_wait_bounded(&bar[(it + k) % STAGES], (uint32_t)((it + k) / STAGES) & 1u);
+            }
+            __syncwarp();
+            return;
         }
+        if constexpr (MODE == MODE_INV) {
+            // pre-twiddle X -> V, read in natural order, written back swizzled
+            C vp[PPL], vq[PPL];
+#pragma unroll
+            for (int k = 0; k < PPL; ++k) {
+                const int p = lane + 32 * k, q = (N - p) % N;
+                if (p < NP) dct_pre(p, row[p], row[q], tb.wx[p], tb.wx[q], vp[k], vq[k]);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < PPL; ++k) {
+                const int p = lane + 32 * k, q = (N - p) % N;
+                if (p < NP) {
+                    row[swz<1>(p)] = vp[k];
+                    row[swz<1>(q)] = vq[k];
+                }
+            }
+            __syncwarp();
+        } else {
+            warp_fft<C, N, -1, true, false>(row, tb.twx, lane);
+            const int k = r / ny;
+#pragma unroll
+            for (int kk = 0; kk < PPL; ++kk) {
+                const int p = lane + 32 * kk, q = (N - p) % N;
+                if (p < NP) {
+                    const int sp = swz<1>(p), sq = swz<1>(q);
+                    const C wp = tb.wx[p], wq = tb.wx[q];
+                    C Xp, Xq;
+                    dct_post(row[sp], row[sq], wp, wq, Xp, Xq);
+                    if (MODE == MODE_FDI) {
+                        Xp = cdiv(Xp, shift_den(tb, k, tb.lamx[p], c2, c1));
+                        Xq = cdiv(Xq, shift_den(tb, k, tb.lamx[q], c2, c1));
+                        dct_pre(p, Xp, Xq, wp, wq, Xp, Xq);
+                    }
+                    row[sp] = Xp;
+                    row[sq] = Xq;
+                }
+            }
+            __syncwarp();
+        }
+        C* out = S + (size_t)r * N;
+        if (MODE == MODE_FWD) {
+#pragma unroll
+            for (int i = lane; i < N; i += 32) out[i] = row[swz<1>(i)];
+        } else {
+            warp_fft<C, N, +1>(row, tb.twx, lane);
+            const T inv = T(1) / T(N);
+#pragma unroll
+            for (int i = lane; i < N; i += 32) out[i] = scalec(row[swz<1>(dct_pos(i, N))], inv);
+        }
+        fence_proxy_async_smem();   // this lane's accesses to the stage precede the refill
+        __syncwarp();
+        if (lane == 0 && r + STAGES * nw < nrows) issue(r + STAGES * nw, st);
     }
 }
 
@@ -297,6 +406,104 @@ __global__ void __launch_bounds__(ColCfg<T, N>::NTH)
             const int c = e % CW, y = e / CW;
             const int x = x0 + c;
             if (x < nx) slab[(size_t)y * nx + x] = scalec(buf[dct_pos(y, N) * CW + c], inv);
+        }
+        __syncthreads();   // buf is refilled two tiles later
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Columns, warp-per-column form (128 <= N <= 512): a tile of 16 columns sits
+// in shared memory column-major, column c at c*N with its element y at
+// swz(y) ^ c (conflict-free both for the row-wise copies in and out and for
+// the FFT passes).  Warp c transforms column c alone (forward DCT, divide,
+// inverse); the CTA synchronizes only after the tile lands and before it is
+// written back.  Persistent CTAs prefetch the next tile by cp.async.
+// ---------------------------------------------------------------------------
+template <class T, int N> struct ColWCfg {
+    static constexpr int CW = 16, NTH = 32 * CW;
+    static constexpr size_t TILE = sizeof(c_t<T>) * (size_t)N * CW;
+    static constexpr int STAGES = 2 * TILE <= 160 * 1024 ? 2 : 1;
+    static constexpr size_t SMEM = STAGES * TILE;
+    static constexpr int MINB = sizeof(T) == 4 && N <= 256 ? 2 : 1;   // 64 registers for two CTAs per SM
+};
+template <class T, int N>
+constexpr bool cols_warp_ok = N >= 128 && N <= (sizeof(T) == 4 ? 512 : 256);
+
+__device__ __forceinline__ int colw_pos(int c, int y) { return swz<1>(y) ^ c; }
+
+template <class T, int N>
+__global__ void __launch_bounds__(512, ColWCfg<T, N>::MINB) k_cols_dct_fdi_w(int nx, int nk, c_t<T>* __restrict__ S, Tabs<T> tb,
+                                                        SolveCoef co, const Ctl* __restrict__ ctl) {
+    using C = c_t<T>;
+    using Cfg = ColWCfg<T, N>;
+    constexpr int CW = Cfg::CW, NTH = Cfg::NTH, STAGES = Cfg::STAGES, NP = N / 2 + 1, PPL = (NP + 31) / 32;
+    if (ctl && ctl->status != ST_RUNNING) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* bufs = reinterpret_cast<C*>(smem_raw);
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    const int nxb = (nx + CW - 1) / CW;
+    const int ntiles = nk * nxb;
+    // copy in: element e of the tile is row y = e / CW, column c = e % CW
+    auto stage = [&](int t, C* buf) {
+        const int k = t / nxb, x0 = (t % nxb) * CW;
+        const C* slab = S + (size_t)k * N * nx;
+        for (int e = tid; e < N * CW; e += NTH) {
+            const int c = e % CW, y = e / CW;
+            C* d = &buf[c * N + colw_pos(c, y)];
+            if (x0 + c < nx) cp_async_val<sizeof(C)>(d, slab + (size_t)y * nx + x0 + c);
+            else *d = mkc(T(0), T(0));
+        }
+        cp_async_commit_grp();
+    };
+    const T c2 = T(co.c2), c1 = solve_c1<T>(co, ctl);
+    if (STAGES == 2) stage(blockIdx.x, bufs);
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        C* buf = bufs + (STAGES == 2 ? (it & 1) : 0) * (Cfg::TILE / sizeof(C));
+        if constexpr (STAGES == 2) {
+            if (t + gridDim.x < ntiles) {
+                stage(t + gridDim.x, bufs + ((it + 1) & 1) * (Cfg::TILE / sizeof(C)));
+                cp_async_wait_grp<1>();
+            } else {
+                cp_async_wait_grp<0>();
+            }
+        } else {
+            stage(t, buf);
+            cp_async_wait_grp<0>();
+        }
+        __syncthreads();
+        const int k = t / nxb, x0 = (t % nxb) * CW;
+        const int c = warp, x = x0 + c;
+        C* col = buf + c * N;
+        // forward FFT of the even/odd reordering of the stored column (key c)
+        warp_fft<C, N, -1, true, true>(col, tb.twy, lane, c);
+        if (x < nx) {
+            const T lx = tb.lamx[x];
+#pragma unroll
+            for (int kk = 0; kk < PPL; ++kk) {
+                const int p = lane + 32 * kk, q = (N - p) % N;
+                if (p < NP) {
+                    const int sp = colw_pos(c, p), sq = colw_pos(c, q);
+                    const C wp = tb.wy[p], wq = tb.wy[q];
+                    C Xp, Xq;
+                    dct_post(col[sp], col[sq], wp, wq, Xp, Xq);
+                    Xp = cdiv(Xp, shift_den(tb, k, lx + tb.lamy[p], c2, c1));
+                    Xq = cdiv(Xq, shift_den(tb, k, lx + tb.lamy[q], c2, c1));
+                    dct_pre(p, Xp, Xq, wp, wq, Xp, Xq);
+                    col[sp] = Xp;
+                    col[sq] = Xq;
+                }
+            }
+        }
+        __syncwarp();
+        warp_fft<C, N, +1>(col, tb.twy, lane, c);
+        __syncthreads();
+        // copy out, row by row (16 columns = one coalesced segment per row)
+        C* slab = S + (size_t)k * N * nx;
+        const T inv = T(1) / T(N);
+        for (int e = tid; e < N * CW; e += NTH) {
+            const int cc = e % CW, y = e / CW;
+            if (x0 + cc < nx) slab[(size_t)y * nx + x0 + cc] = scalec(buf[cc * N + colw_pos(cc, dct_pos(y, N))], inv);
         }
         __syncthreads();   // buf is refilled two tiles later
     }
@@ -561,6 +768,8 @@ static int rows_resident() {
     return r;
 }
 
+template <class T, int N, int MODE>
+static int rows_w_resident();
 template <class T, int N>
 static cudaError_t cfg_rows() {
     cudaError_t e;
@@ -574,16 +783,37 @@ static cudaError_t cfg_rows() {
     if (rows_resident<T, N, MODE_FWD>() <= 0 || rows_resident<T, N, MODE_INV>() <= 0 ||
         rows_resident<T, N, MODE_FDI>() <= 0)
         return cudaErrorInvalidConfiguration;
+    if constexpr (rows_warp_ok<T, N>) {
+        const int smw = (int)RowWCfg<T, N>::SMEM;
+        if ((e = cudaFuncSetAttribute(k_rows_dct_w<T, N, MODE_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smw)))
+            return e;
+        if ((e = cudaFuncSetAttribute(k_rows_dct_w<T, N, MODE_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smw)))
+            return e;
+        if ((e = cudaFuncSetAttribute(k_rows_dct_w<T, N, MODE_FDI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smw)))
+            return e;
+        if (rows_w_resident<T, N, MODE_FWD>() <= 0 || rows_w_resident<T, N, MODE_INV>() <= 0 ||
+            rows_w_resident<T, N, MODE_FDI>() <= 0)
+            return cudaErrorInvalidConfiguration;
+    }
     return cudaSuccess;
 }
 template <class T, int N>
 static int cols_resident();
 template <class T, int N>
+static int cols_w_resident();
+template <class T, int N>
 static cudaError_t cfg_cols() {
     cudaError_t e = cudaFuncSetAttribute(k_cols_dct_fdi<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)ColCfg<T, N>::SMEM);
     if (e != cudaSuccess) return e;
-    return cols_resident<T, N>() > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
+    if (cols_resident<T, N>() <= 0) return cudaErrorInvalidConfiguration;
+    if constexpr (cols_warp_ok<T, N>) {
+        if ((e = cudaFuncSetAttribute(k_cols_dct_fdi_w<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)ColWCfg<T, N>::SMEM)))
+            return e;
+        if (cols_w_resident<T, N>() <= 0) return cudaErrorInvalidConfiguration;
+    }
+    return cudaSuccess;
 }
 
 template <class T>
@@ -614,8 +844,23 @@ template cudaError_t configure_spatial_all<float>();
 template cudaError_t configure_spatial_all<double>();
 
 template <class T, int N, int MODE>
+static int rows_w_resident() {
+    static const int r = persistent_ctas(k_rows_dct_w<T, N, MODE>, RowWCfg<T, N>::NTH, RowWCfg<T, N>::SMEM);
+    return r;
+}
+
+template <class T, int N, int MODE>
 static cudaError_t rows_n(int nrows, int ny, c_t<T>* S, const Tabs<T>& tb, SolveCoef co, const Ctl* ctl,
                           cudaStream_t st) {
+    if constexpr (rows_warp_ok<T, N>) {
+        using W = RowWCfg<T, N>;
+        const int resident = rows_w_resident<T, N, MODE>();
+        if (resident <= 0) return cudaErrorInvalidConfiguration;
+        const int need = (nrows + W::WARPS - 1) / W::WARPS;
+        const int grid = need < resident ? need : resident;
+        k_rows_dct_w<T, N, MODE><<<grid, W::NTH, W::SMEM, st>>>(nrows, ny, S, tb, co, ctl);
+        return cudaSuccess;
+    }
     using Cfg = RowCfg<T, N>;
     const int resident = rows_resident<T, N, MODE>();
     if (resident <= 0) return cudaErrorInvalidConfiguration;
@@ -640,8 +885,22 @@ static int cols_resident() {
     return r;
 }
 template <class T, int N>
+static int cols_w_resident() {
+    static const int r = persistent_ctas(k_cols_dct_fdi_w<T, N>, ColWCfg<T, N>::NTH, ColWCfg<T, N>::SMEM);
+    return r;
+}
+template <class T, int N>
 static cudaError_t cols_n(int nx, int nk, c_t<T>* S, const Tabs<T>& tb, SolveCoef co, const Ctl* ctl,
                           cudaStream_t st) {
+    if constexpr (cols_warp_ok<T, N>) {
+        using W = ColWCfg<T, N>;
+        const int resident = cols_w_resident<T, N>();
+        if (resident <= 0) return cudaErrorInvalidConfiguration;
+        const int ntiles = nk * ((nx + W::CW - 1) / W::CW);
+        const int grid = ntiles < resident ? ntiles : resident;
+        k_cols_dct_fdi_w<T, N><<<grid, W::NTH, W::SMEM, st>>>(nx, nk, S, tb, co, ctl);
+        return cudaSuccess;
+    }
     using Cfg = ColCfg<T, N>;
     const int resident = cols_resident<T, N>();
     if (resident <= 0) return cudaErrorInvalidConfiguration;

@@ -188,6 +188,83 @@ __device__ __forceinline__ void fft_passes(C* buf, const C* __restrict__ tw) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Warp-level Stockham FFT: one sequence of length N in shared memory
+// transformed by one warp.  Element i is stored at swz<1>(i) ^ key (key < 16:
+// a further fixed permutation inside each 16-element group).  The first pass
+// may read the even/odd reordering of the stored sequence (PERM) and may read
+// natural-order input (RSW false); every write is swizzled.  Lane l owns
+// butterflies j = l + 32 q of every pass; passes are separated by __syncwarp
+// only, so the warps of a CTA run independently.
+// ---------------------------------------------------------------------------
+template <class C, int N, int R, int NS, int DIR, bool PERM, bool RSW>
+__device__ __forceinline__ void warp_pass(C* buf, const C* __restrict__ tw, int lane, int key) {
+    constexpr int NB = N / R;
+    constexpr int TPL = (NB + 31) / 32;
+    C v[TPL][R];
+#pragma unroll
+    for (int q = 0; q < TPL; ++q) {
+        const int j = lane + 32 * q;
+        if (NB % 32 == 0 || j < NB) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int m = j + r * NB;
+                const int idx = PERM ? (m < N / 2 ? 2 * m : 2 * N - 1 - 2 * m) : m;
+                v[q][r] = buf[RSW ? (swz<1>(idx) ^ key) : idx];
+            }
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < TPL; ++q) {
+        const int j = lane + 32 * q;
+        if (NB % 32 == 0 || j < NB) {
+            if constexpr (NS > 1) {
+                constexpr int STEP = N / (NS * R);
+                const int jm = j % NS;
+                C w[R];
+                w[1] = tw[jm * STEP];
+                if (DIR > 0) w[1] = conjc(w[1]);
+                if constexpr (R == 4) {
+                    w[2] = cmul(w[1], w[1]);
+                    w[3] = cmul(w[2], w[1]);
+                } else if constexpr (R == 8) {
+                    w[2] = tw[2 * jm * STEP];
+                    if (DIR > 0) w[2] = conjc(w[2]);
+                    w[3] = cmul(w[2], w[1]);
+                    w[4] = cmul(w[2], w[2]);
+                    w[5] = cmul(w[4], w[1]);
+                    w[6] = cmul(w[4], w[2]);
+                    w[7] = cmul(w[4], w[3]);
+                }
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[q][r] = cmul(v[q][r], w[r]);
+            }
+            dftR<R, DIR>(v[q]);
+            const int base = (j / NS) * NS * R + (j % NS);
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[swz<1>(base + r * NS) ^ key] = v[q][r];
+        }
+    }
+    __syncwarp();
+}
+
+template <class C, int N, int NS, int M, int DIR, bool PERM, bool RSW>
+__device__ __forceinline__ void warp_passes(C* buf, const C* __restrict__ tw, int lane, int key) {
+    if constexpr (M > 0) {
+        constexpr int R = next_radix(M);
+        warp_pass<C, N, R, NS, DIR, PERM, RSW>(buf, tw, lane, key);
+        warp_passes<C, N, NS * R, M - ilog2(R), DIR, false, true>(buf, tw, lane, key);
+    }
+}
+
+// In-place FFT of one sequence by the calling warp (all 32 lanes; data visible
+// to the warp before the call; ends with __syncwarp).
+template <class C, int N, int DIR, bool PERM = false, bool RSW = true>
+__device__ __forceinline__ void warp_fft(C* buf, const C* __restrict__ tw, int lane, int key = 0) {
+    warp_passes<C, N, 1, ilog2(N), DIR, PERM, RSW>(buf, tw, lane, key);
+}
+
 // In-place length-N FFT (N a power of two) of B sequences in shared memory.
 // The caller must __syncthreads() before (data ready); the last pass ends
 // with a barrier.  SW: swizzled row layout (see swz); the result is stored

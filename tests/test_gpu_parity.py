@@ -83,6 +83,9 @@ LARGE_PRECOND_CASES = [
     dict(equation="linear_ch", dim=2, nx=64, ny=64, bc="neumann", nt=256, T=0.1, eps=0.05, beta=0.5),
     dict(equation="linear_ch", dim=2, nx=32, ny=32, bc="neumann", nt=512, T=0.1, eps=0.05, beta=0.5),
     dict(equation="linear_ch", dim=1, nx=2048, bc="neumann", nt=16, T=1e-6, eps=0.05, beta=0.5),
+    dict(equation="linear_ch", dim=1, nx=512, bc="neumann", nt=16, T=1e-5, eps=0.05, beta=0.5),
+    dict(equation="biharmonic", dim=1, nx=256, bc="neumann", nt=32, T=1e-6),
+    dict(equation="linear_ch", dim=2, nx=128, ny=128, bc="neumann", nt=16, T=0.01, eps=0.05, beta=0.5),
 ]
 
 
