@@ -9,7 +9,7 @@
  *   linearized Cahn-Hilliard u_t = -beta^2 Lap u - eps^2 Lap^2 u  (Eq. 1.2, 3.1)
  *   Cahn-Hilliard           u_t = Lap(u^3 - u) - eps^2 Lap^2 u    (Eq. 1.3, 4.1)
  * on [0,1] or [0,1]^2, discretized by centred differences (Eq. 2.4) and
- * backward Euler (the theta-method of Eq. 2.5 with theta = 1; Eq. 4.5).
+ * backward Euler or Crank-Nicolson (the theta-method of Eq. 2.5 with theta = 1 or 1/2; Eq. 4.5).
  *
  * One outer iteration (Sec. 2.1 Eq. 2.6-2.8; Sec. 4.1 Eq. 4.11-4.14, PinT-I)
  * is computed in residual-correction form,
@@ -78,7 +78,8 @@ typedef struct {
     double T;            /* final time; dt = T / (nt * n_windows) */
     int    nt;           /* time steps per window, a power of two in [2, 1024] */
     int    n_windows;    /* consecutive windows; window w starts from the last step of window w-1 */
-    double theta;        /* theta-method parameter; only 1 (backward Euler) is accepted */
+    double theta;        /* theta-method parameter (Eq. 2.5): 1 (backward Euler), or 1/2 (Crank-Nicolson)
+                            for the linear equations; Cahn-Hilliard is backward Euler (Eq. 4.5) */
     double alpha;        /* PinT parameter alpha in (0, 1) (Eq. 2.2) */
     double tol;          /* stop when ||b - K(U)||_2 / ||b||_2 <= tol */
     int    max_iter;     /* outer iterations per window, 1..PINT_HIST_MAX */
@@ -124,7 +125,7 @@ typedef struct pint_handle pint_handle;
  * allocate the workspace on the current device.  cuda_stream is a
  * cudaStream_t (NULL = legacy default stream).  On success *out owns it all.
  * Errors: PINT_EINVAL (bad parameter: dim, sizes, nt not a power of two,
- * NEUMANN with n not a power of two, alpha not in (0,1), theta != 1, ...),
+ * NEUMANN with n not a power of two, alpha not in (0,1), theta not 1 or 1/2, ...),
  * PINT_ENOMEM, PINT_ECUDA. */
 int pint_create(const pint_problem* p, void* cuda_stream, pint_handle** out);
 

@@ -1,9 +1,10 @@
 // k_residual.cu - FP64 all-at-once residual, its norm, and the per-iteration
 // control reduction.
 //
-// Residual (Eq. 2.6 / Eq. 4.8 with alpha = 0, theta = 1):
-//   r_n = (u_{n-1} - u_n)/dt - A(u_n),   u_{-1} := u0 (the initial condition),
-//   A(u) = c2 Lap^2 u + c1 Lap u + cN Lap(u^3).
+// Residual (Eq. 2.6 / Eq. 4.8 with alpha = 0) of the theta-method:
+//   r_n = (u_{n-1} - u_n)/dt - theta A(u_n) - (1 - theta) A(u_{n-1}),
+//   u_{-1} := u0 (the initial condition),  A(u) = c2 Lap^2 u + c1 Lap u + cN Lap(u^3).
+// With U = 0 the first level is the right-hand side b_1 = u0/dt - (1-theta) A(u0).
 // Lap is the centred 3-point (1-D) / 5-point (2-D) difference of Eq. 2.4.  The
 // boundary conditions enter as reflections of the grid function: even about
 // the cell face for cell-centred Neumann (u_{-1} = u_0), odd about the
@@ -70,16 +71,18 @@ __global__ void __launch_bounds__(256) k_residual(Geo g, const double* __restric
     const int pidx = (DIM == 2 ? gy * g.nx : 0) + gx;
     const int n0 = blockIdx.z * chunk;
     const int n1 = min(g.nt, n0 + chunk);
+    const bool prev = g.th < 1.0;   // theta < 1: A(u_{n-1}) is needed, from one extra level before the chunk
 
-    double uprev = 0.0;
-    if (inside) uprev = n0 == 0 ? u0[pidx] : U[(size_t)(n0 - 1) * g.nspace + pidx];
+    double uprev = 0.0, Aprev = 0.0;
+    if (inside) uprev = n0 == 0 ? u0[pidx] : (U ? U[(size_t)(n0 - 1) * g.nspace + pidx] : 0.0);
     double acc_r2 = 0.0, acc_u2 = 0.0;
 
-    for (int n = n0; n < n1; ++n) {
-        const double* un = U + (size_t)n * g.nspace;
+    for (int n = prev ? n0 - 1 : n0; n < n1; ++n) {
+        // level n (n = -1: u0; U == nullptr: the zero iterate)
+        const double* un = n < 0 ? u0 : (U ? U + (size_t)n * g.nspace : nullptr);
         for (int e = threadIdx.x; e < SX * SY; e += TX * TY) {
             int ix = e % SX, iy = e / SX;
-            su[e] = ext_read(un, x0 - 2 + ix, y0 - HY + iy, g.nx, g.ny, DIM, g.bc);
+            su[e] = un ? ext_read(un, x0 - 2 + ix, y0 - HY + iy, g.nx, g.ny, DIM, g.bc) : 0.0;
         }
         __syncthreads();
         for (int e = threadIdx.x; e < LX * LY; e += TX * TY) {
@@ -110,13 +113,17 @@ __global__ void __launch_bounds__(256) k_residual(Geo g, const double* __restric
                 }
                 A = fma(g.cN, lw, A);
             }
-            const double r = (uprev - u) * g.inv_dt - A;
-            const size_t o = (size_t)n * g.nspace + pidx;
-            if (r_out) r_out[o] = r;
-            if (s_out) s_out[o] = (TS)(gam[n] * r);
-            acc_r2 = fma(r, r, acc_r2);
-            acc_u2 = fma(u, u, acc_u2);
-            uprev = u;
+            if (n >= n0) {
+                const double r = prev ? (uprev - u) * g.inv_dt - g.th * A - (1.0 - g.th) * Aprev
+                                      : (uprev - u) * g.inv_dt - A;
+                const size_t o = (size_t)n * g.nspace + pidx;
+                if (r_out) r_out[o] = r;
+                if (s_out) s_out[o] = (TS)(gam[n] * r);
+                acc_r2 = fma(r, r, acc_r2);
+                acc_u2 = fma(u, u, acc_u2);
+                uprev = u;
+            }
+            Aprev = A;
         }
         __syncthreads();
     }
@@ -165,13 +172,15 @@ __device__ void reduce_pairs(const double* __restrict__ partials, int np, double
     for (int w = 0; w < 8; ++w) { A += ra[w]; B += rb[w]; }
 }
 
-// Start of a window: ||b|| = ||u0|| / dt (theta = 1), reset the iteration state.
-__global__ void __launch_bounds__(256) k_begin_window(const double* __restrict__ partials, int np, double inv_dt,
+// Start of a window: ||b|| = sqrt(sum of the partials) * scale (theta = 1:
+// the partials of ||u0||^2 and scale 1/dt; theta < 1: those of ||b_1||^2 and
+// scale 1), reset the iteration state.
+__global__ void __launch_bounds__(256) k_begin_window(const double* __restrict__ partials, int np, double scale,
                                                       int max_iter, double tol, double tol_update, Ctl* ctl) {
     double A, B;
     reduce_pairs(partials, np, A, B);
     if (threadIdx.x == 0) {
-        ctl->bnorm = sqrt(A) * inv_dt;
+        ctl->bnorm = sqrt(A) * scale;
         ctl->status = ST_RUNNING;
         ctl->iter = 0;
         ctl->max_iter = max_iter;
@@ -318,11 +327,21 @@ int norm2_blocks(int n) {
     int b = (n + 255) / 256;
     return b > 1024 ? 1024 : (b < 1 ? 1 : b);
 }
-void launch_begin_window(const double* u0, int nspace, double inv_dt, int max_iter, double tol, double* partials,
-                         Ctl* ctl, cudaStream_t st, double tol_update) {
-    int nb = norm2_blocks(nspace);
-    k_norm2<<<nb, 256, 0, st>>>(u0, nspace, partials);
-    k_begin_window<<<1, 256, 0, st>>>(partials, nb, inv_dt, max_iter, tol, tol_update, ctl);
+void launch_begin_window(const Geo& g, const double* u0, int max_iter, double tol, double* partials, Ctl* ctl,
+                         cudaStream_t st, double tol_update, double* b1) {
+    if (g.th < 1.0) {
+        // b_1 = u0/dt - (1-theta) A(u0): the first level of the residual at U = 0
+        Geo g1 = g;
+        g1.nt = 1;
+        int gx, gy, gz, chunk;
+        const int np = residual_grid(g1, gx, gy, gz, chunk);
+        launch_residual<double>(g1, nullptr, u0, nullptr, b1, nullptr, partials, nullptr, st);
+        k_begin_window<<<1, 256, 0, st>>>(partials, np, 1.0, max_iter, tol, tol_update, ctl);
+        return;
+    }
+    int nb = norm2_blocks(g.nspace);
+    k_norm2<<<nb, 256, 0, st>>>(u0, g.nspace, partials);
+    k_begin_window<<<1, 256, 0, st>>>(partials, nb, g.inv_dt, max_iter, tol, tol_update, ctl);
 }
 void launch_after_residual(const double* partials, int np, double inv_dof, Ctl* ctl, cudaStream_t st,
                            unsigned long long cond, int use_cond, const double* dpart, int ndp) {

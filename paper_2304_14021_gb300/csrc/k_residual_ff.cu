@@ -3,7 +3,7 @@
 // the conversions between FP64 and float-float iterates.
 //
 // Same operator and boundary treatment as k_residual.cu (Eq. 2.6 / 4.8 with
-// alpha = 0, theta = 1):
+// alpha = 0; theta = 1 below, theta = 1/2 adds A(u_{n-1})):
 //   r_n = (u_{n-1} - u_n)/dt - [c2 Lap^2 u_n + c1 Lap u_n + cN Lap(u_n^3)],
 // evaluated as dt r_n (see k_residual_ff below).
 // The stencil sums are error-free in their high words (a TwoSum chain), so the
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(256, 5) k_residual_ff(GeoFF g, const ff* __res
         lc[a] = e < LX * LY ? (DIM == 2 ? (e / LX + 1) * SX : 0) + e % LX + 1 : -1;
     }
     auto stage = [&](int n, ff* dst) {
-        const ff* un = U + (size_t)n * g.nspace;
+        const ff* un = n < 0 ? u0 : U + (size_t)n * g.nspace;   // level -1 is the initial condition
         if (async_ok) {
 #pragma unroll
             for (int a = 0; a < NST; ++a)
@@ -206,13 +206,19 @@ __global__ void __launch_bounds__(256, 5) k_residual_ff(GeoFF g, const ff* __res
     }
     float acc_r2 = 0.f, acc_u2 = 0.f;
     const float sdt = g.inv_dt.x;
+    // theta = 1/2: A'(u_{n-1}) per point, from one extra level before the chunk
+    const bool half = g.half != 0;
+    ff Aprev[PPT];
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) Aprev[q] = ffmk(0.f, 0.f);
+    const int nfirst = half ? n0 - 1 : n0;
 
-    if (n0 < n1) stage(n0, su[0]);
-    for (int n = n0; n < n1; ++n) {
-        const ff* cur = su[(n - n0) & 1];
+    if (n0 < n1) stage(nfirst, su[0]);
+    for (int n = nfirst; n < n1; ++n) {
+        const ff* cur = su[(n - nfirst) & 1];
         if (async_ok) cp_async_wait_all();
         __syncthreads();                                   // level n staged; level n-1 fully consumed
-        if (n + 1 < n1) stage(n + 1, su[(n + 1 - n0) & 1]);
+        if (n + 1 < n1) stage(n + 1, su[(n + 1 - nfirst) & 1]);
 #pragma unroll
         for (int a = 0; a < NLP; ++a)
             if (lc[a] >= 0) {
@@ -220,6 +226,38 @@ __global__ void __launch_bounds__(256, 5) k_residual_ff(GeoFF g, const ff* __res
                 if (ch) sW[tid + a * NTHR] = ff_cube(cur[lc[a]]);
             }
         __syncthreads();
+        if (half) {
+            // Crank-Nicolson: dt r = u_{n-1} - u_n - A'(u_n) - A'(u_{n-1}), A' = dt A / 2 (linear equations)
+#pragma unroll
+            for (int q = 0; q < PPT; ++q) {
+                if (inside[q]) {
+                    const ff L = sL[cl[q]];
+                    const ff lapL = lap_ff<DIM, SQ, ACC>(sL, cl[q], LX, g);
+                    ff A = ff_mul(lapL, g.c2);
+                    if (lin1) A = ff_add(A, ff_mul(L, g.c1));
+                    if (n >= n0) {
+                        const ff u = cur[cu[q]];
+                        ff r;
+                        if constexpr (SQ && !ACC) {
+                            ff_acc acc(uprev[q]);
+                            acc.add(ff_neg(u));
+                            acc.add(ff_neg(A));
+                            acc.add(ff_neg(Aprev[q]));
+                            r = acc.get();
+                        } else {
+                            r = ff_sub(ff_sub(ff_sub(uprev[q], u), A), Aprev[q]);
+                        }
+                        *sp[q] = fmaf(gamf[n] * sdt, r.x, gamf[n] * sdt * r.y);
+                        acc_r2 = fmaf(r.x, r.x, acc_r2);
+                        acc_u2 = fmaf(u.x, u.x, acc_u2);
+                        uprev[q] = u;
+                    }
+                    Aprev[q] = A;
+                }
+                if (n >= n0) sp[q] += g.nspace;
+            }
+            continue;
+        }
         const float gm = gamf[n] * sdt;
 #pragma unroll
         for (int q = 0; q < PPT; ++q) {

@@ -55,7 +55,8 @@ static int validate(const pint_problem* p) {
     if (p->nx < 2 || (p->dim == 2 && p->ny < 2)) return PINT_EINVAL;
     if (!is_pow2(p->nt) || p->nt < 2 || p->nt > 1024) return PINT_EINVAL;
     if (p->n_windows < 1) return PINT_EINVAL;
-    if (p->theta != 1.0) return PINT_EINVAL;
+    // theta-method: backward Euler (1) for every equation, Crank-Nicolson (1/2) for the linear ones
+    if (!(p->theta == 1.0 || (p->theta == 0.5 && p->equation != PINT_CAHN_HILLIARD))) return PINT_EINVAL;
     if (!(p->alpha > 0.0 && p->alpha < 1.0)) return PINT_EINVAL;
     if (!(p->tol > 0.0) || !isfinite(p->tol)) return PINT_EINVAL;
     if (p->max_iter < 1 || p->max_iter >= PINT_HIST_MAX) return PINT_EINVAL;
@@ -135,6 +136,7 @@ struct pint_handle {
     double* gam = nullptr;          // alpha^{n/nt}
     double* ginv = nullptr;         // alpha^{-n/nt} / nt
     double* u0buf = nullptr;        // window initial condition
+    double* b1 = nullptr;           // theta < 1: first right-hand-side level u0/dt - (1-theta) A u0
     double* hU = nullptr;           // pint_solve_host buffers (lazy)
     double* hu0 = nullptr;
     void* s = nullptr;              // alpha-scaled residual, transform precision
@@ -402,6 +404,7 @@ static void derive(const pint_problem* p, pint_handle* h) {
         case PINT_LINEAR_CH: g.c2 = p->eps * p->eps; g.c1 = p->beta * p->beta; g.cN = 0.0; break;
         default: g.c2 = p->eps * p->eps; g.c1 = 1.0; g.cN = -1.0; h->coef.ch = 1; break;
     }
+    g.th = p->theta;
     h->coef.c2 = g.c2;
     h->coef.c1 = g.c1;
     h->fft_x = axis_fft(p->nx, p->bc, 4096);
@@ -417,11 +420,14 @@ static void derive(const pint_problem* p, pint_handle* h) {
     f.ihy2 = ff_from_double(g.ihy2);
     f.inv_dt = ff_from_double(g.inv_dt);
     const bool sq = g.dim == 1 || g.ihx2 == g.ihy2;   // must match launch_residual_ff
-    // the float-float residual is evaluated scaled by dt: coefficients carry dt
+    // the float-float residual is evaluated scaled by dt: coefficients carry dt,
+    // and theta (exact: 1 or 1/2), so that dt r = u_{n-1} - u_n - A'(u_n) - A'(u_{n-1})
+    // with A' = theta dt A when theta = 1/2
     const double s2 = sq ? g.ihx2 * g.ihx2 : 1.0, s1 = sq ? g.ihx2 : 1.0;
-    f.c2 = ff_from_double(g.c2 * s2 * g.dt);
-    f.c1 = ff_from_double(g.c1 * s1 * g.dt);
-    f.cN = ff_from_double(g.cN * s1 * g.dt);
+    f.c2 = ff_from_double(g.c2 * s2 * g.dt * g.th);
+    f.c1 = ff_from_double(g.c1 * s1 * g.dt * g.th);
+    f.cN = ff_from_double(g.cN * s1 * g.dt * g.th);
+    f.half = g.th < 1.0 ? 1 : 0;
     // stiffness dt * max |spectrum of the spatial operator|: above 1e7 the stencil
     // sums use chained accurate double-word additions (see k_residual_ff.cu)
     const double lam_max = 4.0 * g.ihx2 + (g.dim == 2 ? 4.0 * g.ihy2 : 0.0);
@@ -457,7 +463,7 @@ static long long footprint_of(const pint_problem* p) {
     b += z.partials * 2 * sizeof(double);
     b += (z.nspace / 16 + 2) * 2 * sizeof(double);
     b += 2 * (size_t)p->nt * sizeof(double);
-    b += z.nspace * sizeof(double);
+    b += z.nspace * sizeof(double) * (p->theta < 1.0 ? 2 : 1);
     b += z.dof * ts;                 // s
     b += z.nk * z.nspace * 2 * ts;   // S
     b += z.tables_bytes;
@@ -571,8 +577,11 @@ static cudaError_t zero_start(pint_handle* h, double* U, const double* u0w) {
     const Geo& g = h->geo;
     const int nk = g.nt / 2 + 1;
     prof_begin(h, PH_TFWD);
-    if (f32_transforms(&h->p)) launch_zero_start<float>(reinterpret_cast<float2*>(h->S), u0w, g.inv_dt, g.nspace, nk, h->ctl, h->st);
-    else launch_zero_start<double>(reinterpret_cast<double2*>(h->S), u0w, g.inv_dt, g.nspace, nk, h->ctl, h->st);
+    // spectrum of b: b_1 at every frequency (theta = 1: b_1 = u0/dt; else computed at the window start)
+    const double* b1 = g.th < 1.0 ? h->b1 : u0w;
+    const double sc = g.th < 1.0 ? 1.0 : g.inv_dt;
+    if (f32_transforms(&h->p)) launch_zero_start<float>(reinterpret_cast<float2*>(h->S), b1, sc, g.nspace, nk, h->ctl, h->st);
+    else launch_zero_start<double>(reinterpret_cast<double2*>(h->S), b1, sc, g.nspace, nk, h->ctl, h->st);
     prof_end(h, PH_TFWD, 1);
     cudaError_t e;
     if (f32_transforms(&h->p)) {
@@ -714,6 +723,7 @@ void geometry_of(const pint_problem* p, Geo& g) {
         case PINT_LINEAR_CH: g.c2 = p->eps * p->eps; g.c1 = p->beta * p->beta; g.cN = 0.0; break;
         default: g.c2 = p->eps * p->eps; g.c1 = 1.0; g.cN = -1.0; break;
     }
+    g.th = p->theta;
 }
 
 // dt * max|spectrum| of the spatial operator (for Cahn-Hilliard with the
@@ -788,6 +798,7 @@ void pint_destroy(pint_handle* h) {
     af(h->gam);
     af(h->ginv);
     af(h->u0buf);
+    af(h->b1);
     af(h->hU);
     af(h->hu0);
     af(h->s);
@@ -843,6 +854,7 @@ int pint_create(const pint_problem* p, void* cuda_stream, pint_handle** out) {
     if (!rc) rc = dalloc((void**)&h->gam, p->nt * sizeof(double));
     if (!rc) rc = dalloc((void**)&h->ginv, p->nt * sizeof(double));
     if (!rc) rc = dalloc((void**)&h->u0buf, z.nspace * sizeof(double));
+    if (!rc && p->theta < 1.0) rc = dalloc((void**)&h->b1, z.nspace * sizeof(double));
     if (!rc) rc = dalloc(&h->s, z.dof * ts);
     if (!rc) rc = dalloc(&h->S, z.nk * z.nspace * 2 * ts);
     if (!rc) rc = dalloc(&h->tab, z.tables_bytes);
@@ -969,7 +981,7 @@ int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* 
     const bool ffm = p.precision == PINT_MIXED_FF;
     const int ntmax = h->lev[0].nt;
     const size_t ns = (size_t)g.nspace, dof = (size_t)ntmax * ns;
-    const bool adapt = h->adaptive && h->nlev > 1;
+    const bool adapt = h->adaptive && h->nlev > 1 && p.theta == 1.0;   // the policy's growth factor is BE's
     pint_stats S;
     memset(&S, 0, sizeof(S));
     S.nt_min = ntmax;
@@ -995,7 +1007,7 @@ int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* 
             // is at most the largest power of two dividing base
             const int lmax = base == 0 ? ntmax : (base & -base);
             activate_level(h, 0);
-            launch_begin_window(u0w, g.nspace, g.inv_dt, p.max_iter, p.tol, h->partials, h->ctl, h->st, p.tol_update);
+            launch_begin_window(g, u0w, p.max_iter, p.tol, h->partials, h->ctl, h->st, p.tol_update, h->b1);
             if ((rc = read_ctl(h)) != PINT_OK) return rc;
             const double rms = h->hctl->bnorm * g.dt;          // ||u0||_2
             li = choose_level(h, lmax, 3.0 * rms * rms / (double)ns);
@@ -1020,7 +1032,7 @@ int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* 
                 else launch_broadcast(Useg, u0w, g.nspace, L, h->st);
                 nl++;
             }
-            launch_begin_window(u0w, g.nspace, g.inv_dt, p.max_iter, p.tol, h->partials, h->ctl, h->st, p.tol_update);
+            launch_begin_window(g, u0w, p.max_iter, p.tol, h->partials, h->ctl, h->st, p.tol_update, h->b1);
             prof_end(h, PH_SETUP, nl + 1);
             cudaGraphExec_t gx = (h->use_graphs && !h->prof_on && !adapt) ? get_graph(h, Useg, u0w) : nullptr;
             if (gx) {
@@ -1142,7 +1154,7 @@ int pint_solve_host(pint_handle* h, const double* u0_host, double* U_host, pint_
 int pint_residual(pint_handle* h, const double* u0_dev, const double* U_dev, double* r_dev, double* rel_res) {
     if (!h || !u0_dev || !U_dev) return PINT_EINVAL;
     const Geo& g = h->geo;
-    launch_begin_window(u0_dev, g.nspace, g.inv_dt, h->p.max_iter, h->p.tol, h->partials, h->ctl, h->st);
+    launch_begin_window(g, u0_dev, h->p.max_iter, h->p.tol, h->partials, h->ctl, h->st);
     launch_residual<double>(g, U_dev, u0_dev, h->gam, r_dev, nullptr, h->partials, nullptr, h->st);
     int gx, gy, gz, chunk;
     const int np = residual_grid(g, gx, gy, gz, chunk);

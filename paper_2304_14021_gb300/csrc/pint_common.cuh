@@ -304,6 +304,7 @@ struct Geo {
     int nx, ny, dim, bc, nt, nspace;
     double dt, inv_dt, ihx2, ihy2;   // 1/h^2 per axis
     double c2, c1, cN;
+    double th;                       // theta of the theta-method (1 or 1/2)
 };
 
 // Reduction helpers (deterministic: fixed shuffle tree, fixed warp order).

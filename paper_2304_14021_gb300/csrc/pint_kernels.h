@@ -39,6 +39,7 @@ struct GeoFF {
     int nx, ny, dim, bc, nt, nspace;
     float2 ihx2, ihy2, inv_dt, c2, c1, cN;
     int accurate;   // 1: chained accurate double-word stencil sums (very stiff problems)
+    int half;       // theta = 1/2: the residual also carries A'(u_{n-1})
 };
 
 int residual_grid(const Geo& g, int& gx, int& gy, int& gz, int& chunk);
@@ -54,8 +55,10 @@ template <class TS>
 void launch_residual(const Geo& g, const double* U, const double* u0, const double* gam, double* r_out, TS* s_out,
                      double* partials, const Ctl* ctl, cudaStream_t st);
 int norm2_blocks(int n);
-void launch_begin_window(const double* u0, int nspace, double inv_dt, int max_iter, double tol, double* partials,
-                         Ctl* ctl, cudaStream_t st, double tol_update = 0.0);
+// Window start: ||b|| into ctl->bnorm and the iteration state reset.  theta < 1
+// computes b_1 = u0/dt - (1-theta) A u0 (stored in b1 when b1 != nullptr).
+void launch_begin_window(const Geo& g, const double* u0, int max_iter, double tol, double* partials, Ctl* ctl,
+                         cudaStream_t st, double tol_update = 0.0, double* b1 = nullptr);
 // cond / use_cond: CUDA-graph while-loop condition handle (see pint_api.cu).
 // dpart/ndp: the last correction's (sum delta^2, sum U^2) partials (ndp = 0: none).
 void launch_after_residual(const double* partials, int np, double inv_dof, Ctl* ctl, cudaStream_t st,

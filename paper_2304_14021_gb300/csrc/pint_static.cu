@@ -88,7 +88,7 @@ extern "C" int pint_residual_static(const pint_problem* p, void* cuda_stream, co
     Ctl* ctl = reinterpret_cast<Ctl*>(base);
     double* partials = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(base) + kCtlBytes);
     // ||b|| = ||u0|| / dt: writes nb partial pairs, then ctl->bnorm (and resets ctl's other fields)
-    launch_begin_window(u0_dev, g.nspace, g.inv_dt, p->max_iter, p->tol, partials, ctl, st);
+    launch_begin_window(g, u0_dev, p->max_iter, p->tol, partials, ctl, st);
     // residual: overwrites np partial pairs (every pair read below is written first)
     launch_residual<double>(g, U_dev, u0_dev, nullptr, r_dev, nullptr, partials, nullptr, st);
     k_static_finish<<<1, 256, 0, st>>>(partials, np, ctl, rel_res_dev);

@@ -49,7 +49,7 @@ def test_strerror(lib):
 
 
 BAD = [dict(dim=3), dict(nx=1), dict(nt=48), dict(nt=2048), dict(nt=1), dict(alpha=0.0), dict(alpha=1.0),
-       dict(theta=0.5), dict(tol=0.0), dict(max_iter=0), dict(max_iter=256), dict(precision=7),
+       dict(theta=0.7), dict(theta=0.5, equation="cahn_hilliard", eps=0.05), dict(tol=0.0), dict(max_iter=0), dict(max_iter=256), dict(precision=7),
        dict(T=-1.0), dict(equation=5), dict(bc=3), dict(n_windows=0), dict(nx=2000, bc="ss"),
        dict(equation="linear_ch", eps=0.0), dict(init_guess=3), dict(dim=2, ny=1), dict(tol_update=-1.0)]
 
@@ -95,3 +95,10 @@ def test_precision_policy_falls_back_to_fp64_when_too_stiff():
     mild = dict(equation="linear_ch", dim=2, nx=256, ny=256, bc="neumann", eps=0.05, beta=0.5, T=0.1, nt=128,
                 alpha=1e-2, tol=1e-8)
     assert pint.footprint(**mild, precision="mixed_ff") < pint.footprint(**mild, precision="fp64")
+
+
+def test_crank_nicolson_accepted_for_linear_equations(lib):
+    # theta = 1/2 is accepted for the linear equations (its footprint adds the b_1 buffer)
+    kw = dict(equation="linear_ch", dim=2, nx=64, ny=64, bc="neumann", eps=0.05, beta=0.5, T=0.01, nt=32,
+              alpha=1e-2, tol=1e-8, precision="mixed_ff")
+    assert pint.footprint(**kw, theta=0.5) == pint.footprint(**kw, theta=1.0) + 64 * 64 * 8

@@ -468,3 +468,74 @@ def test_stiff_instances_run_in_fp64_and_converge(which):
     assert out["mixed_ff"][1]["precision"] == "fp64"
     assert out["mixed_ff"][1]["rc"] == 0
     assert torch.equal(out["mixed_ff"][0], out["fp64"][0])
+
+
+# --- theta = 1/2 (Crank-Nicolson, Eq. 2.5) for the linear equations ---------
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_ff"])
+@pytest.mark.parametrize("kw", [
+    dict(equation="biharmonic", dim=1, nx=64, bc="ss", nt=32, T=0.01),
+    dict(equation="linear_ch", dim=2, nx=32, ny=16, bc="neumann", nt=8, T=0.005, eps=0.05, beta=0.5),
+    dict(equation="linear_ch", dim=1, nx=256, bc="neumann", nt=16, T=1e-5, eps=0.05, beta=0.5),
+])
+def test_crank_nicolson_precond_matches_dense(kw, precision):
+    kw = full(dict(kw, theta=0.5, precision=precision))
+    p = oprob(kw)
+    r = synth.random_iterate(p.nt, p.nspace, 300)
+    ref = O.precond_dense(p, p.alpha, r) if p.nt * p.nspace <= 4096 else O.diagonalized_apply(p, p.alpha, r)
+    with pint.Solver(**kw) as s:
+        out = torch.zeros(p.nt, p.nspace, dtype=torch.float64, device="cuda")
+        s.precond_apply(dev(r), out)
+        err = O.rel_err(host(out), ref)
+    assert err < (1e-11 if precision == "fp64" else 3e-6 / p.alpha), err
+
+
+@pytest.mark.parametrize("kw", [
+    dict(equation="biharmonic", dim=1, nx=64, bc="ss", nt=32, T=0.01),
+    dict(equation="linear_ch", dim=2, nx=40, ny=24, bc="neumann", nt=8, T=0.01, eps=0.05, beta=0.5),
+])
+def test_crank_nicolson_residual_matches_oracle(kw):
+    kw = full(dict(kw, theta=0.5))
+    p = oprob(kw)
+    u0 = synth.u0_uniform(p.nspace, -1, 1, 1)
+    U = synth.random_iterate(p.nt, p.nspace, 2)
+    ref = O.residual(p, u0, U)
+    with pint.Solver(**kw) as s:
+        r = torch.empty(p.nt, p.nspace, dtype=torch.float64, device="cuda")
+        rel = s.residual(dev(u0), dev(U), r)
+    assert O.rel_err(host(r), ref) < 1e-13
+    assert abs(rel - np.linalg.norm(ref) / O.rhs_norm(p, u0)) < 1e-12 * rel
+
+
+@pytest.mark.parametrize("init", [0, 2])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_ff"])
+def test_crank_nicolson_solves_match_sequential(precision, init):
+    # 1-D biharmonic, simply supported, config 1 with theta = 1/2; and 2-D linearized CH 64^2
+    cases = [dict(tol=1e-10 if precision == "fp64" else 1e-9),
+             dict(equation="linear_ch", dim=2, nx=64, ny=64, bc="neumann", eps=0.05, beta=0.5, nt=32,
+                  T=32 * 0.1 / 128, tol=1e-11 if precision != "mixed_ff" else 1e-9)]
+    for c in cases:
+        kw = full(dict(c, theta=0.5, precision=precision, init_guess=init))
+        p = oprob(kw)
+        u0 = synth.u0_sine_modes(p.nx) if kw["dim"] == 1 else synth.u0_uniform(p.nspace, -0.05, 0.05, 0)
+        U, st = run_solve(kw, u0)
+        assert st["rc"] == 0, st
+        err = O.rel_err(U, O.sequential(p, u0))
+        assert err < (1e-10 if precision == "fp64" else 1e-8), (c, err)
+
+
+def test_crank_nicolson_static_residual_equals_handle_residual():
+    kw = full(dict(equation="linear_ch", dim=2, nx=40, ny=24, bc="neumann", nt=8, T=0.01, eps=0.05, beta=0.5,
+                   theta=0.5))
+    p = oprob(kw)
+    u0 = dev(synth.u0_uniform(p.nspace, -1, 1, 1))
+    U = dev(synth.random_iterate(p.nt, p.nspace, 2))
+    with pint.Solver(**kw) as s:
+        r1 = torch.empty_like(U)
+        rel1 = s.residual(u0, U, r1)
+    r2 = torch.empty_like(U)
+    rel2 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    pint.residual_static(u0, U, rel2, r=r2, **kw)
+    torch.cuda.synchronize()
+    assert torch.equal(r1, r2)
+    assert abs(rel2.item() - rel1) <= 1e-14 * rel1
