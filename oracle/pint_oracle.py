@@ -21,7 +21,10 @@ What is computed (section / equation numbers of the paper):
     condition (ii) in Sec. 5.1), vertex grid of n interior points,
     h = 1/(n+1), zero ghost values for u and for Delta_h u;
   - ``bc="neumann"``: homogeneous Neumann d_nu u = d_nu Laplace(u) = 0 on a
-    cell-centred grid of n cells, h = 1/n, mirror ghost values.
+    cell-centred grid of n cells, h = 1/n, mirror ghost values;
+  - ``bc="neumann_v"``: the same conditions on the paper's own vertex grid
+    (Eq. 2.4): n points x_j = j h including both ends, h = 1/(n-1), ghosts
+    u_{-1} = u_1 and u_n = u_{n-2}, so the end rows read (-2, 2)/h^2.
   2-D operators are Kronecker sums (Remark 2.5).
 * A = Delta_h^2 (biharmonic, Eq. 2.3), A = beta^2 Delta_h + eps^2 Delta_h^2
   (linearized Cahn-Hilliard, Sec. 3, Eq. 3.1).
@@ -77,7 +80,7 @@ class Problem:
     dim: int = 1
     nx: int = 16
     ny: int = 1
-    bc: str = "ss"              # "ss" (simply supported) or "neumann"
+    bc: str = "ss"              # "ss" (simply supported), "neumann" (cell-centred) or "neumann_v" (vertex)
     eps: float = 1.0
     beta: float = 0.0
     T: float = 0.01
@@ -107,6 +110,8 @@ def grid_h(n: int, bc: str) -> float:
         return 1.0 / (n + 1)
     if bc == "neumann":
         return 1.0 / n
+    if bc == "neumann_v":
+        return 1.0 / (n - 1)
     raise ValueError(bc)
 
 
@@ -114,6 +119,8 @@ def grid_points(n: int, bc: str) -> np.ndarray:
     h = grid_h(n, bc)
     if bc == "ss":
         return h * np.arange(1, n + 1)
+    if bc == "neumann_v":
+        return h * np.arange(n)
     return h * (np.arange(n) + 0.5)
 
 
@@ -128,8 +135,12 @@ def laplacian_1d(n: int, bc: str) -> sp.csr_matrix:
     if bc == "neumann":
         main[0] = -1.0
         main[-1] = -1.0
-    off = np.ones(n - 1)
-    return sp.diags([off, main, off], [-1, 0, 1], format="csr") / (h * h)
+    up = np.ones(n - 1)
+    lo = np.ones(n - 1)
+    if bc == "neumann_v":   # u_{-1} = u_1, u_n = u_{n-2}: end rows (-2, 2), not symmetric
+        up[0] = 2.0
+        lo[-1] = 2.0
+    return sp.diags([lo, main, up], [-1, 0, 1], format="csr") / (h * h)
 
 
 def laplacian(p: Problem) -> sp.csr_matrix:
@@ -395,6 +406,18 @@ def pint_iteration_paper_form(p: Problem, u0: np.ndarray, U_init: np.ndarray,
 # The paper's three diagonalized steps with library FFTs (Eq. 2.8 / 4.14)
 # ----------------------------------------------------------------------------
 
+def eig_decomposition(A: np.ndarray):
+    """A = Q diag(mu) Q^{-1}: numpy.linalg.eigh when A is symmetric, else
+    numpy.linalg.eig (the vertex-Neumann Laplacian is similar to a symmetric
+    matrix, so its spectrum is real).  Returns (mu, Q, Q^{-1})."""
+    if np.allclose(A, A.T, rtol=0.0, atol=1e-12 * np.abs(A).max()):
+        mu, Q = np.linalg.eigh(A)
+        return mu, Q, Q.T
+    mu, Q = np.linalg.eig(A)
+    mu, Q = mu.real, Q.real
+    return mu, Q, np.linalg.inv(Q)
+
+
 def diagonalized_apply(p: Problem, alpha: float, r: np.ndarray, jbar: float | None = None) -> np.ndarray:
     """delta = P_alpha^{-1} r by Steps 1-3 of Eq. 2.8 (Eq. 4.14 for CH):
     Step 1 scales by Gamma_alpha and transforms along time (numpy FFT);
@@ -413,8 +436,8 @@ def diagonalized_apply(p: Problem, alpha: float, r: np.ndarray, jbar: float | No
     th = 1.0 if p.equation == CAHN_HILLIARD else p.theta
     l2 = th + (1.0 - th) * z
     A = dense_A(p, jbar)
-    mu, Q = np.linalg.eigh(A)
-    S1h = S1 @ Q                              # coefficients in A's eigenbasis
+    mu, Q, Qi = eig_decomposition(A)
+    S1h = S1 @ Qi.T                           # coefficients in A's eigenbasis
     S2h = S1h / (l1[:, None] + l2[:, None] * mu[None, :])
     S2 = S2h @ Q.T
     x = np.fft.ifft(S2, axis=0).real
@@ -442,15 +465,15 @@ def diagonalized_apply_separable(p: Problem, alpha: float, r: np.ndarray, jbar: 
         c2, c1 = p.eps ** 2, p.beta ** 2
     else:
         c2, c1 = p.eps ** 2, 1.0 - jbar
-    ex, Qx = np.linalg.eigh(laplacian_1d(p.nx, p.bc).toarray())
+    ex, Qx, Qxi = eig_decomposition(laplacian_1d(p.nx, p.bc).toarray())
     if p.dim == 1:
         lam = ex
-        S1h = S1 @ Qx
+        S1h = S1 @ Qxi.T
     else:
-        ey, Qy = np.linalg.eigh(laplacian_1d(p.ny, p.bc).toarray())
+        ey, Qy, Qyi = eig_decomposition(laplacian_1d(p.ny, p.bc).toarray())
         lam = (ey[:, None] + ex[None, :]).ravel()
         X = S1.reshape(nt, p.ny, p.nx)
-        S1h = (Qy.T @ X @ Qx).reshape(nt, -1)        # Q_y^T X Q_x per frequency
+        S1h = (Qyi @ X @ Qxi.T).reshape(nt, -1)      # Q_y^{-1} X Q_x^{-T} per frequency
     mu = c2 * lam ** 2 + c1 * lam
     S2h = S1h / (l1[:, None] + l2[:, None] * mu[None, :])
     if p.dim == 1:
@@ -497,11 +520,15 @@ def pint_iteration_residual_form(p: Problem, u0: np.ndarray, U_init: np.ndarray,
 def laplacian_eigs_1d(n: int, bc: str) -> np.ndarray:
     """Eigenvalues of the 1-D Delta_h: -(4/h^2) sin^2(p pi / (2(n+1))), p=1..n
     (ss, sine modes sin(p pi x)); -(4/h^2) sin^2(p pi/(2n)), p=0..n-1
-    (cell-centred Neumann, modes cos(p pi x))."""
+    (cell-centred Neumann, modes cos(p pi x)); -(4/h^2) sin^2(p pi/(2(n-1))),
+    p=0..n-1 (vertex Neumann, modes cos(p pi x_j) with x_j = j h)."""
     h = grid_h(n, bc)
     if bc == "ss":
         p = np.arange(1, n + 1)
         return -(4.0 / h ** 2) * np.sin(p * np.pi / (2 * (n + 1))) ** 2
+    if bc == "neumann_v":
+        p = np.arange(n)
+        return -(4.0 / h ** 2) * np.sin(p * np.pi / (2 * (n - 1))) ** 2
     p = np.arange(n)
     return -(4.0 / h ** 2) * np.sin(p * np.pi / (2 * n)) ** 2
 

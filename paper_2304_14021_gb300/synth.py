@@ -10,9 +10,12 @@ import numpy as np
 
 
 def grid_points_1d(n: int, bc: str) -> np.ndarray:
-    """Vertex grid (n interior points of [0,1]) for "ss"; cell centres for "neumann"."""
+    """Vertex grid (n interior points of [0,1]) for "ss"; cell centres for
+    "neumann"; n vertices including both ends for "neumann_v"."""
     if bc == "ss":
         return np.arange(1, n + 1) / (n + 1)
+    if bc == "neumann_v":
+        return np.arange(n) / (n - 1)
     return (np.arange(n) + 0.5) / n
 
 

@@ -273,3 +273,67 @@ def test_separable_apply_matches_dense_eigendecomposition(kw):
     a = O.diagonalized_apply(p, 1e-2, r, 0.4)
     b = O.diagonalized_apply_separable(p, 1e-2, r, 0.4)
     assert O.rel_err(b, a) < 1e-12
+
+
+# --- vertex-centred Neumann (the paper's Delta_h, Eq. 2.4) --------------------
+
+@pytest.mark.parametrize("n", [5, 8, 13])
+def test_vertex_neumann_laplacian_spectrum_and_modes(n):
+    # End rows (-2, 2)/h^2 on n vertices, h = 1/(n-1): not symmetric, but similar
+    # to a symmetric matrix through W = diag(1/2, 1, ..., 1, 1/2); eigenpairs
+    # cos(p pi x_j), -(4/h^2) sin^2(p pi / (2(n-1))).
+    L = O.laplacian_1d(n, "neumann_v").toarray()
+    h = 1.0 / (n - 1)
+    assert L[0, 1] == 2.0 / h**2 and L[-1, -2] == 2.0 / h**2 and L[0, 0] == -2.0 / h**2
+    w = np.ones(n)
+    w[0] = w[-1] = 0.5
+    S = np.diag(np.sqrt(w)) @ L @ np.diag(1.0 / np.sqrt(w))
+    assert np.allclose(S, S.T, atol=1e-9)
+    x = synth.grid_points_1d(n, "neumann_v")
+    assert x[0] == 0.0 and x[-1] == 1.0
+    for p in range(n):
+        phi = np.cos(p * np.pi * x)
+        lam = -(4 / h**2) * np.sin(p * np.pi / (2 * (n - 1))) ** 2
+        assert np.allclose(L @ phi, lam * phi, atol=1e-9 * (abs(lam) + 1))
+    assert np.allclose(np.sort(O.laplacian_eigs_1d(n, "neumann_v")), np.sort(np.linalg.eigvals(L).real),
+                       rtol=1e-10, atol=1e-8)
+
+
+@pytest.mark.parametrize("eq", [O.BIHARMONIC, O.LINEAR_CH])
+@pytest.mark.parametrize("dim", [1, 2])
+def test_vertex_neumann_eigenmode_decay(eq, dim):
+    n, nt, T = 13, 10, 3e-4
+    p = P(equation=eq, dim=dim, nx=n, ny=9, bc="neumann_v", eps=0.05, beta=0.5, T=T, nt=nt)
+    x, y = synth.grid_points_1d(n, "neumann_v"), synth.grid_points_1d(9, "neumann_v")
+    a, b = 3, 2
+    lam = -(4 * (n - 1) ** 2) * np.sin(a * np.pi / (2 * (n - 1))) ** 2
+    phi = np.cos(a * np.pi * x)
+    if dim == 2:
+        lam += -(4 * 8**2) * np.sin(b * np.pi / 16) ** 2
+        phi = np.outer(np.cos(b * np.pi * y), np.cos(a * np.pi * x)).ravel()
+    mu = lam**2 if eq == O.BIHARMONIC else 0.25 * lam + 0.0025 * lam**2
+    U = O.sequential(p, phi)
+    expect = np.array([(1 + p.dt * mu) ** (-(k + 1)) * phi for k in range(nt)])
+    assert O.rel_err(U, expect) < 1e-11
+
+
+@pytest.mark.parametrize("theta", [1.0, 0.5])
+@pytest.mark.parametrize("dim", [1, 2])
+def test_vertex_neumann_all_at_once_and_diagonalized(theta, dim):
+    p = P(equation=O.LINEAR_CH, dim=dim, nx=7, ny=5, bc="neumann_v", eps=0.1, beta=0.4, T=2e-3, nt=6,
+          theta=theta, alpha=0.02)
+    u0 = synth.u0_uniform(p.nspace, -1, 1, 7)
+    assert O.rel_err(O.all_at_once_dense_linear(p, u0), O.sequential(p, u0)) < 1e-11
+    r = synth.random_iterate(6, p.nspace, 11)
+    d_dense = O.precond_dense(p, p.alpha, r)
+    assert O.rel_err(O.diagonalized_apply(p, p.alpha, r), d_dense) < 1e-10
+    assert O.rel_err(O.diagonalized_apply_separable(p, p.alpha, r), d_dense) < 1e-10
+
+
+def test_vertex_neumann_ch_diagonalized_and_constant_state():
+    p = P(equation=O.CAHN_HILLIARD, dim=2, nx=6, ny=5, bc="neumann_v", eps=0.1, T=3e-3, nt=8, alpha=0.02)
+    r = synth.random_iterate(8, p.nspace, 12)
+    assert O.rel_err(O.diagonalized_apply(p, p.alpha, r, 0.7), O.precond_dense(p, p.alpha, r, 0.7)) < 1e-10
+    u0 = np.full(p.nspace, 0.3)
+    U = O.sequential(p, u0)
+    assert np.abs(U - 0.3).max() < 1e-12
