@@ -53,8 +53,11 @@ typedef enum { PINT_BIHARMONIC = 0, PINT_LINEAR_CH = 1, PINT_CAHN_HILLIARD = 2 }
  *                    spatial solves in the sine basis (DST-I, dense, n <= 1024).
  *  NEUMANN:          d_nu u = d_nu Lap u = 0, cell-centred grid of n cells, h = 1/n;
  *                    spatial solves in the cosine basis (DCT-II): by FFT when n is a
- *                    power of two (x: n <= 4096, y: n <= 1024), else dense (n <= 1024). */
-typedef enum { PINT_BC_SIMPLY_SUPPORTED = 0, PINT_BC_NEUMANN = 1 } pint_bc;
+ *                    power of two (x: n <= 4096, y: n <= 1024), else dense (n <= 1024).
+ *  NEUMANN_VERTEX:   the same conditions on the vertex grid of Eq. 2.4: n points including
+ *                    both ends, h = 1/(n-1), ghosts u_{-1} = u_1; spatial solves in the
+ *                    DCT-I basis cos(p pi j/(n-1)) (dense, 3 <= n <= 1024). */
+typedef enum { PINT_BC_SIMPLY_SUPPORTED = 0, PINT_BC_NEUMANN = 1, PINT_BC_NEUMANN_VERTEX = 2 } pint_bc;
 
 /* PINT_FP64:     every step in FP64 (the plain form).
  * PINT_MIXED:    residual, alpha-scaling, unscaling and the update in FP64; the

@@ -7,7 +7,8 @@
 // With U = 0 the first level is the right-hand side b_1 = u0/dt - (1-theta) A(u0).
 // Lap is the centred 3-point (1-D) / 5-point (2-D) difference of Eq. 2.4.  The
 // boundary conditions enter as reflections of the grid function: even about
-// the cell face for cell-centred Neumann (u_{-1} = u_0), odd about the
+// the cell face for cell-centred Neumann (u_{-1} = u_0), even about the end
+// vertex for vertex-centred Neumann (u_{-1} = u_1), odd about the
 // boundary vertex for simply supported (u_{-1} = 0, u_{-2} = -u_0).  With
 // those ghost values Lap u is then correct on the ghost layer as well
 // (Neumann: Lap u mirrors; simply supported: Lap u = 0 on the boundary), so
@@ -27,6 +28,13 @@ __device__ __forceinline__ double ext_read(const double* __restrict__ u, int gx,
         if (dim == 2) {
             if (gy < 0) gy = -1 - gy;
             else if (gy >= ny) gy = 2 * ny - 1 - gy;
+        }
+    } else if (bc == 2) {  // Neumann, vertex grid: even about the end vertices 0 and n-1
+        if (gx < 0) gx = -gx;
+        else if (gx >= nx) gx = 2 * (nx - 1) - gx;
+        if (dim == 2) {
+            if (gy < 0) gy = -gy;
+            else if (gy >= ny) gy = 2 * (ny - 1) - gy;
         }
     } else {  // simply supported, vertex grid: odd about the boundary vertices -1 and n
         if (gx == -1 || gx == nx) return 0.0;

@@ -27,6 +27,13 @@ __device__ __forceinline__ ff ext_read_ff(const ff* __restrict__ u, int gx, int 
             if (gy < 0) gy = -1 - gy;
             else if (gy >= ny) gy = 2 * ny - 1 - gy;
         }
+    } else if (bc == 2) {
+        if (gx < 0) gx = -gx;
+        else if (gx >= nx) gx = 2 * (nx - 1) - gx;
+        if (dim == 2) {
+            if (gy < 0) gy = -gy;
+            else if (gy >= ny) gy = 2 * (ny - 1) - gy;
+        }
     } else {
         if (gx == -1 || gx == nx) return ffmk(0.f, 0.f);
         if (gx < -1) { gx = -2 - gx; sgn = -sgn; }
@@ -104,9 +111,11 @@ __device__ __forceinline__ ff lap_ff(const ff* __restrict__ a, int c, int sx, co
     }
 }
 
-// Neumann (cell-centred) reflection of a halo index g in [-2, n+1] into [0, n).
-__device__ __forceinline__ int reflect_n(int g, int n) {
-    g = g < 0 ? -1 - g : (g >= n ? 2 * n - 1 - g : g);
+// Neumann reflection of a halo index g in [-2, n+1] into [0, n): even about
+// the cell faces (bc 1, cell-centred) or about the end vertices (bc 2).
+__device__ __forceinline__ int reflect_n(int g, int n, int bc) {
+    if (bc == 2) g = g < 0 ? -g : (g >= n ? 2 * (n - 1) - g : g);
+    else g = g < 0 ? -1 - g : (g >= n ? 2 * n - 1 - g : g);
     return min(max(g, 0), n - 1);
 }
 
@@ -150,7 +159,8 @@ __global__ void __launch_bounds__(256, 5) k_residual_ff(GeoFF g, const ff* __res
     const bool lin1 = g.c1.x != 0.f;
     const bool interior = x0 >= 2 && x0 + TX + 2 <= g.nx && (DIM == 1 || (y0 >= 2 && y0 + TY + 2 <= g.ny));
     // halo values are plain (reflected) copies except on simply supported boundary tiles
-    const bool async_ok = interior || (g.bc == 1 && g.nx >= 2 && (DIM == 1 || g.ny >= 2));
+    const bool async_ok = interior || ((g.bc == 1 && g.nx >= 2 && (DIM == 1 || g.ny >= 2)) ||
+                                       (g.bc == 2 && g.nx >= 3 && (DIM == 1 || g.ny >= 3)));
 
     // Per-thread work assignments, fixed for all levels (linear in the thread
     // index, so only the last warps of a pass idle): halo-tile elements
@@ -164,8 +174,8 @@ __global__ void __launch_bounds__(256, 5) k_residual_ff(GeoFF g, const ff* __res
         goff[a] = -1;
         soff[a] = e;
         if (e < SX * SY) {
-            const int gy = DIM == 2 ? (interior ? y0 - HY + iy : reflect_n(y0 - HY + iy, g.ny)) : 0;
-            const int gx = interior ? x0 - 2 + ix : reflect_n(x0 - 2 + ix, g.nx);
+            const int gy = DIM == 2 ? (interior ? y0 - HY + iy : reflect_n(y0 - HY + iy, g.ny, g.bc)) : 0;
+            const int gx = interior ? x0 - 2 + ix : reflect_n(x0 - 2 + ix, g.nx, g.bc);
             goff[a] = gy * g.nx + gx;
         }
     }

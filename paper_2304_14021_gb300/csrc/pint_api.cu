@@ -51,7 +51,9 @@ static int validate(const pint_problem* p) {
     if (!p) return PINT_EINVAL;
     if (p->equation < 0 || p->equation > 2) return PINT_EINVAL;
     if (p->dim != 1 && p->dim != 2) return PINT_EINVAL;
-    if (p->bc != PINT_BC_SIMPLY_SUPPORTED && p->bc != PINT_BC_NEUMANN) return PINT_EINVAL;
+    if (p->bc != PINT_BC_SIMPLY_SUPPORTED && p->bc != PINT_BC_NEUMANN && p->bc != PINT_BC_NEUMANN_VERTEX)
+        return PINT_EINVAL;
+    if (p->bc == PINT_BC_NEUMANN_VERTEX && (p->nx < 3 || (p->dim == 2 && p->ny < 3))) return PINT_EINVAL;
     if (p->nx < 2 || (p->dim == 2 && p->ny < 2)) return PINT_EINVAL;
     if (!is_pow2(p->nt) || p->nt < 2 || p->nt > 1024) return PINT_EINVAL;
     if (p->n_windows < 1) return PINT_EINVAL;
@@ -73,12 +75,16 @@ static int validate(const pint_problem* p) {
     return PINT_OK;
 }
 
-static double grid_h(int n, int bc) { return bc == PINT_BC_SIMPLY_SUPPORTED ? 1.0 / (n + 1) : 1.0 / n; }
+static double grid_h(int n, int bc) {
+    return bc == PINT_BC_SIMPLY_SUPPORTED ? 1.0 / (n + 1) : bc == PINT_BC_NEUMANN_VERTEX ? 1.0 / (n - 1) : 1.0 / n;
+}
 
 // Eigenvalue of the 1-D Delta_h for transform index p (Sec. 2.2 spectrum).
 static double lap_eig(int p, int n, int bc) {
     const double h = grid_h(n, bc);
-    const double s = bc == PINT_BC_SIMPLY_SUPPORTED ? sin(M_PI * (p + 1) / (2.0 * (n + 1))) : sin(M_PI * p / (2.0 * n));
+    const double s = bc == PINT_BC_SIMPLY_SUPPORTED ? sin(M_PI * (p + 1) / (2.0 * (n + 1)))
+                     : bc == PINT_BC_NEUMANN_VERTEX  ? sin(M_PI * p / (2.0 * (n - 1)))
+                                                     : sin(M_PI * p / (2.0 * n));
     return -4.0 / (h * h) * s * s;
 }
 
@@ -228,6 +234,13 @@ static void dense_basis(int n, int bc, std::vector<double>& F, std::vector<doubl
             if (bc == PINT_BC_SIMPLY_SUPPORTED) {  // DST-I: sin(pi (p+1)(j+1)/(n+1)), inverse 2/(n+1) F^T
                 f = sin(M_PI * (double)((long)(p + 1) * (j + 1) % (2 * (n + 1))) / (n + 1));
                 fi = 2.0 / (n + 1) * f;
+            } else if (bc == PINT_BC_NEUMANN_VERTEX) {
+                // DCT-I: x_j = sum_p X_p cos(pi p j/(n-1)); X_p = 2/(n-1) c_p sum_j c_j x_j cos(...),
+                // c = 1/2 at the two ends, 1 inside
+                const double c = cos(M_PI * (double)(((long)p * j) % (2 * (n - 1))) / (n - 1));
+                const double cp = (p == 0 || p == n - 1) ? 0.5 : 1.0, cj = (j == 0 || j == n - 1) ? 0.5 : 1.0;
+                f = 2.0 / (n - 1) * cp * cj * c;
+                fi = c;
             } else {  // DCT-II: cos(pi p (j+1/2)/n), inverse (1 or 2)/n F^T
                 f = cos(M_PI * (double)(((long)p * (2 * j + 1)) % (4 * n)) / (2.0 * n));
                 fi = (p == 0 ? 1.0 : 2.0) / n * f;

@@ -20,7 +20,7 @@ FP64, MIXED, MIXED_FF = 0, 1, 2
 HIST_MAX = 256
 
 EQUATIONS = {"biharmonic": BIHARMONIC, "linear_ch": LINEAR_CH, "cahn_hilliard": CAHN_HILLIARD}
-BCS = {"ss": BC_SIMPLY_SUPPORTED, "neumann": BC_NEUMANN}
+BCS = {"ss": BC_SIMPLY_SUPPORTED, "neumann": BC_NEUMANN, "neumann_v": 2}
 PRECISIONS = {"fp64": FP64, "mixed": MIXED, "mixed_ff": MIXED_FF}
 PRECISION_NAMES = {v: k for k, v in PRECISIONS.items()}
 

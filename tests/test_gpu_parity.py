@@ -539,3 +539,56 @@ def test_crank_nicolson_static_residual_equals_handle_residual():
     torch.cuda.synchronize()
     assert torch.equal(r1, r2)
     assert abs(rel2.item() - rel1) <= 1e-14 * rel1
+
+
+# --- vertex-centred Neumann (Eq. 2.4; DCT-I basis) ----------------------------
+
+VERTEX_CASES = [
+    dict(equation="linear_ch", dim=1, nx=33, bc="neumann_v", nt=16, T=0.01, eps=0.05, beta=0.5),
+    dict(equation="linear_ch", dim=2, nx=17, ny=9, bc="neumann_v", nt=8, T=0.005, eps=0.05, beta=0.5),
+    dict(equation="cahn_hilliard", dim=2, nx=9, ny=9, bc="neumann_v", nt=8, T=8e-4, eps=0.05),
+    dict(equation="biharmonic", dim=1, nx=65, bc="neumann_v", nt=16, T=1e-5),
+]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_ff"])
+@pytest.mark.parametrize("case", range(len(VERTEX_CASES)))
+def test_vertex_neumann_precond_matches_dense(case, precision):
+    kw = full(dict(VERTEX_CASES[case], precision=precision))
+    p = oprob(kw)
+    r = synth.random_iterate(p.nt, p.nspace, 400 + case)
+    jbar = 0.4 if kw["equation"] == "cahn_hilliard" else None
+    ref = O.precond_dense(p, p.alpha, r, jbar) if p.nt * p.nspace <= 4096 else O.diagonalized_apply(p, p.alpha, r, jbar)
+    with pint.Solver(**kw) as s:
+        out = torch.zeros(p.nt, p.nspace, dtype=torch.float64, device="cuda")
+        s.precond_apply(dev(r), out, jbar=jbar or 0.0)
+        err = O.rel_err(host(out), ref)
+    assert err < (1e-11 if precision == "fp64" else 3e-6 / p.alpha), err
+
+
+@pytest.mark.parametrize("case", [0, 1, 2])
+def test_vertex_neumann_residual_matches_oracle(case):
+    kw = full(VERTEX_CASES[case])
+    p = oprob(kw)
+    u0 = synth.u0_uniform(p.nspace, -1, 1, 1)
+    U = synth.random_iterate(p.nt, p.nspace, 2)
+    ref = O.residual(p, u0, U)
+    with pint.Solver(**kw) as s:
+        r = torch.empty(p.nt, p.nspace, dtype=torch.float64, device="cuda")
+        rel = s.residual(dev(u0), dev(U), r)
+    assert O.rel_err(host(r), ref) < 1e-13
+    assert abs(rel - np.linalg.norm(ref) / O.rhs_norm(p, u0)) < 1e-12 * rel
+
+
+@pytest.mark.parametrize("theta", [1.0, 0.5])
+@pytest.mark.parametrize("precision", ["fp64", "mixed_ff"])
+def test_vertex_neumann_solves_match_sequential(precision, theta):
+    kw = full(dict(equation="linear_ch", dim=2, nx=33, ny=33, bc="neumann_v", eps=0.05, beta=0.5, nt=32,
+                   T=32 * 0.1 / 128, theta=theta, precision=precision, init_guess=2,
+                   tol=1e-11 if precision == "fp64" else 1e-9))
+    p = oprob(kw)
+    u0 = synth.u0_uniform(p.nspace, -0.05, 0.05, 0)
+    U, st = run_solve(kw, u0)
+    assert st["rc"] == 0, st
+    err = O.rel_err(U, O.sequential(p, u0))
+    assert err < (1e-10 if precision == "fp64" else 1e-8), err
