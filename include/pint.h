@@ -77,7 +77,8 @@ typedef struct {
     int    nx, ny;       /* grid points per axis; ny ignored (treated as 1) when dim == 1 */
     int    bc;           /* pint_bc */
     double eps;          /* interface width epsilon (linear and nonlinear CH) */
-    double beta;         /* beta of the linearized CH equation */
+    double beta;         /* beta of the linearized CH equation; A = beta|beta| Lap + eps^2 Lap^2, so
+                            beta < 0 gives the diffusive second-order term (signed beta^2) */
     double T;            /* final time; dt = T / (nt * n_windows) */
     int    nt;           /* time steps per window, a power of two in [2, 1024] */
     int    n_windows;    /* consecutive windows; window w starts from the last step of window w-1 */

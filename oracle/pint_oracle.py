@@ -26,7 +26,9 @@ What is computed (section / equation numbers of the paper):
     (Eq. 2.4): n points x_j = j h including both ends, h = 1/(n-1), ghosts
     u_{-1} = u_1 and u_n = u_{n-2}, so the end rows read (-2, 2)/h^2.
   2-D operators are Kronecker sums (Remark 2.5).
-* A = Delta_h^2 (biharmonic, Eq. 2.3), A = beta^2 Delta_h + eps^2 Delta_h^2
+* A = Delta_h^2 (biharmonic, Eq. 2.3), A = beta^2 Delta_h + eps^2 Delta_h^2 (beta^2 is
+  signed: the field beta carries its sign, beta^2 := beta |beta|, so beta < 0 gives the
+  diffusive second-order term of the general fourth-order problem of Sec. 3)
   (linearized Cahn-Hilliard, Sec. 3, Eq. 3.1).
 * The sequential theta-method solution (Eq. 2.5 with alpha = 0): this is the
   fixed point the PinT iteration converges to (Sec. 2, after Eq. 2.2; the
@@ -160,7 +162,7 @@ def operator_A(p: Problem) -> sp.csr_matrix:
     if p.equation == BIHARMONIC:
         return (L @ L).tocsr()
     if p.equation == LINEAR_CH:
-        return (p.beta ** 2 * L + p.eps ** 2 * (L @ L)).tocsr()
+        return (p.beta * abs(p.beta) * L + p.eps ** 2 * (L @ L)).tocsr()
     raise ValueError("operator_A is defined for the linear equations only")
 
 
@@ -462,7 +464,7 @@ def diagonalized_apply_separable(p: Problem, alpha: float, r: np.ndarray, jbar: 
     if p.equation == BIHARMONIC:
         c2, c1 = 1.0, 0.0
     elif p.equation == LINEAR_CH:
-        c2, c1 = p.eps ** 2, p.beta ** 2
+        c2, c1 = p.eps ** 2, p.beta * abs(p.beta)
     else:
         c2, c1 = p.eps ** 2, 1.0 - jbar
     ex, Qx, Qxi = eig_decomposition(laplacian_1d(p.nx, p.bc).toarray())
@@ -546,7 +548,7 @@ def operator_eigs(p: Problem, jbar: float | None = None) -> np.ndarray:
     if p.equation == BIHARMONIC:
         return lam ** 2
     if p.equation == LINEAR_CH:
-        return p.beta ** 2 * lam + p.eps ** 2 * lam ** 2
+        return p.beta * abs(p.beta) * lam + p.eps ** 2 * lam ** 2
     return (1.0 - jbar) * lam + p.eps ** 2 * lam ** 2
 
 

@@ -414,7 +414,7 @@ static void derive(const pint_problem* p, pint_handle* h) {
     h->coef.ch = 0;
     switch (p->equation) {
         case PINT_BIHARMONIC: g.c2 = 1.0; g.c1 = 0.0; g.cN = 0.0; break;
-        case PINT_LINEAR_CH: g.c2 = p->eps * p->eps; g.c1 = p->beta * p->beta; g.cN = 0.0; break;
+        case PINT_LINEAR_CH: g.c2 = p->eps * p->eps; g.c1 = p->beta * fabs(p->beta); g.cN = 0.0; break;   // signed beta^2
         default: g.c2 = p->eps * p->eps; g.c1 = 1.0; g.cN = -1.0; h->coef.ch = 1; break;
     }
     g.th = p->theta;
@@ -733,7 +733,7 @@ void geometry_of(const pint_problem* p, Geo& g) {
     g.ihy2 = p->dim == 2 ? 1.0 / (hy * hy) : 0.0;
     switch (p->equation) {
         case PINT_BIHARMONIC: g.c2 = 1.0; g.c1 = 0.0; g.cN = 0.0; break;
-        case PINT_LINEAR_CH: g.c2 = p->eps * p->eps; g.c1 = p->beta * p->beta; g.cN = 0.0; break;
+        case PINT_LINEAR_CH: g.c2 = p->eps * p->eps; g.c1 = p->beta * fabs(p->beta); g.cN = 0.0; break;   // signed beta^2
         default: g.c2 = p->eps * p->eps; g.c1 = 1.0; g.cN = -1.0; break;
     }
     g.th = p->theta;

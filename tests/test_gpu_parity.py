@@ -592,3 +592,22 @@ def test_vertex_neumann_solves_match_sequential(precision, theta):
     assert st["rc"] == 0, st
     err = O.rel_err(U, O.sequential(p, u0))
     assert err < (1e-10 if precision == "fp64" else 1e-8), err
+
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_ff"])
+def test_signed_beta_squared_solve_matches_sequential(precision):
+    # beta = -0.5: a diffusive second-order term (signed beta^2), 2-D Neumann 64^2
+    kw = full(dict(equation="linear_ch", dim=2, nx=64, ny=64, bc="neumann", eps=0.05, beta=-0.5, nt=32,
+                   T=32 * 0.1 / 128, precision=precision, init_guess=2, tol=1e-11 if precision == "fp64" else 1e-9))
+    p = oprob(kw)
+    u0 = synth.u0_uniform(p.nspace, -0.05, 0.05, 0)
+    U, st = run_solve(kw, u0)
+    assert st["rc"] == 0, st
+    assert O.rel_err(U, O.sequential(p, u0)) < (1e-10 if precision == "fp64" else 1e-8)
+    r = synth.random_iterate(p.nt, p.nspace, 9)
+    ref = O.diagonalized_apply_separable(p, p.alpha, r)
+    with pint.Solver(**kw) as s:
+        out = torch.zeros(p.nt, p.nspace, dtype=torch.float64, device="cuda")
+        s.precond_apply(dev(r), out)
+    assert O.rel_err(host(out), ref) < (1e-11 if precision == "fp64" else 3e-6 / p.alpha)

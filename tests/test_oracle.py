@@ -337,3 +337,29 @@ def test_vertex_neumann_ch_diagonalized_and_constant_state():
     u0 = np.full(p.nspace, 0.3)
     U = O.sequential(p, u0)
     assert np.abs(U - 0.3).max() < 1e-12
+
+
+@pytest.mark.parametrize("bc", ["ss", "neumann", "neumann_v"])
+def test_signed_beta_squared_eigenmode_decay(bc):
+    # beta < 0 carries a negative beta^2: A = -0.25 Lap + eps^2 Lap^2, every mode decays
+    # with (1 + dt mu)^(-n), mu = -0.25 lam + 0.0025 lam^2 > 0.
+    n, nt, T, mode = 24, 12, 3e-3, 3
+    p = P(equation=O.LINEAR_CH, nx=n, bc=bc, eps=0.05, beta=-0.5, T=T, nt=nt)
+    x = synth.grid_points_1d(n, bc)
+    h = O.grid_h(n, bc)
+    if bc == "ss":
+        phi = np.sin(mode * np.pi * x)
+        lam = -(4 / h**2) * np.sin(mode * np.pi / (2 * (n + 1))) ** 2
+    elif bc == "neumann":
+        phi = np.cos(mode * np.pi * x)
+        lam = -(4 / h**2) * np.sin(mode * np.pi / (2 * n)) ** 2
+    else:
+        phi = np.cos(mode * np.pi * x)
+        lam = -(4 / h**2) * np.sin(mode * np.pi / (2 * (n - 1))) ** 2
+    mu = -0.25 * lam + 0.0025 * lam**2
+    assert mu > 0
+    U = O.sequential(p, phi)
+    expect = np.array([(1 + p.dt * mu) ** (-(k + 1)) * phi for k in range(nt)])
+    assert O.rel_err(U, expect) < 1e-11
+    r = synth.random_iterate(nt, n, 3)
+    assert O.rel_err(O.diagonalized_apply(p, 0.02, r), O.precond_dense(p, 0.02, r)) < 1e-10
