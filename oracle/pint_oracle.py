@@ -72,6 +72,10 @@ from scipy.linalg import lapack
 BIHARMONIC = "biharmonic"
 LINEAR_CH = "linear_ch"
 CAHN_HILLIARD = "cahn_hilliard"
+# Cahn-Hilliard with Eyre's convex-concave splitting (PinT-II, Sec. 4.2): u^3
+# implicit, the concave -u part explicit.
+CAHN_HILLIARD_EYRE = "cahn_hilliard_eyre"
+CH_EQUATIONS = (CAHN_HILLIARD, CAHN_HILLIARD_EYRE)
 
 
 @dataclass
@@ -268,9 +272,40 @@ def sequential_ch(p: Problem, u0: np.ndarray, nsteps: int | None = None) -> np.n
     return U
 
 
+def eyre_step_newton(p: Problem, u_prev: np.ndarray, tol: float = 1e-14,
+                     max_newton: int = 60) -> tuple[np.ndarray, int]:
+    """One step of Eyre's splitting (the sequential scheme of PinT-II, Sec. 4.2):
+    F(u) = (u - u_prev)/dt - Delta_h(u^3) + Delta_h u_prev + eps^2 Delta_h^2 u = 0,
+    Newton with the exact Jacobian I/dt - Delta_h diag(3u^2) + eps^2 Delta_h^2."""
+    L = laplacian(p)
+    L2 = (L @ L).tocsr()
+    dt, e2 = p.dt, p.eps ** 2
+    n = L.shape[0]
+    I = sp.identity(n, format="csr")
+    bw = _bandwidth(p)
+    lp = L @ u_prev
+    u = u_prev.copy()
+    for it in range(1, max_newton + 1):
+        F = (u - u_prev) / dt - L @ (u ** 3) + lp + e2 * (L2 @ u)
+        J = I / dt - L @ sp.diags(3.0 * u ** 2) + e2 * L2
+        du = BandedLU(J, bw, bw).solve(-F)
+        u = u + du
+        if np.max(np.abs(du)) <= tol * max(1.0, np.max(np.abs(u))):
+            return u, it
+    raise RuntimeError("Newton did not converge in the oracle Eyre step")
+
+
 def sequential(p: Problem, u0: np.ndarray, nsteps: int | None = None) -> np.ndarray:
     if p.equation == CAHN_HILLIARD:
         return sequential_ch(p, u0, nsteps)
+    if p.equation == CAHN_HILLIARD_EYRE:
+        nsteps = p.nt * p.n_windows if nsteps is None else nsteps
+        U = np.empty((nsteps, p.nspace))
+        u = np.asarray(u0, dtype=np.float64).copy()
+        for n in range(nsteps):
+            u, _ = eyre_step_newton(p, u)
+            U[n] = u
+        return U
     return sequential_linear(p, u0, nsteps)
 
 
@@ -290,6 +325,14 @@ def residual(p: Problem, u0: np.ndarray, U: np.ndarray) -> np.ndarray:
     nt = U.shape[0]
     R = np.empty_like(U)
     prev = np.asarray(u0, dtype=np.float64)
+    if p.equation == CAHN_HILLIARD_EYRE:
+        # Eyre (PinT-II): (u_n - u_{n-1})/dt - Delta(u_n^3) + Delta u_{n-1} + eps^2 Delta^2 u_n
+        L = laplacian(p)
+        for n in range(nt):
+            u = U[n]
+            R[n] = (prev - u) / p.dt + L @ (u ** 3) - L @ prev - p.eps ** 2 * (L @ (L @ u))
+            prev = u
+        return R
     th = p.theta if p.equation != CAHN_HILLIARD else 1.0
     Aprev = spatial_operator(p, prev) if th != 1.0 else None
     for n in range(nt):
@@ -340,9 +383,16 @@ def dense_P(p: Problem, alpha: float, jbar: float | None = None, nt: int | None 
     Cahn-Hilliard C_1^(alpha) (x) I + I (x) ((1-jbar) Delta + eps^2 Delta^2)
     (Eq. 4.12).  Block index = time step, so the matrix acts on U.ravel()."""
     nt = p.nt if nt is None else nt
+    C1 = circulant_C1(nt, p.dt, alpha)
+    if p.equation == CAHN_HILLIARD_EYRE:
+        # Eq. 4.24 with a scalar Jacobian: C_1 (x) I - I (x) jbar Delta + C_3 (x) Delta + eps^2 I (x) Delta^2,
+        # C_3 = C_2 with theta = 0
+        L = laplacian(p).toarray()
+        ns = L.shape[0]
+        return (np.kron(C1, np.eye(ns)) + np.kron(np.eye(nt), p.eps ** 2 * L @ L - jbar * L)
+                + np.kron(circulant_C2(nt, 0.0, alpha), L))
     A = dense_A(p, jbar)
     I = np.eye(A.shape[0])
-    C1 = circulant_C1(nt, p.dt, alpha)
     if p.equation == CAHN_HILLIARD:
         return np.kron(C1, I) + np.kron(np.eye(nt), A)
     return np.kron(C1, I) + np.kron(circulant_C2(nt, p.theta, alpha), A)
@@ -435,6 +485,13 @@ def diagonalized_apply(p: Problem, alpha: float, r: np.ndarray, jbar: float | No
     S1 = np.fft.fft(gam[:, None] * r, axis=0)
     z = alpha ** (1.0 / nt) * np.exp(-2j * np.pi * n / nt)
     l1 = (1.0 - z) / p.dt
+    if p.equation == CAHN_HILLIARD_EYRE:
+        # Step 2 of Eq. 4.25: (lambda_1k I - jbar Delta + lambda_3k Delta + eps^2 Delta^2)^{-1},
+        # lambda_3k = alpha^{1/N_t} e^{-2 pi i k/N_t}, in the eigenbasis of Delta_h
+        lam, Q, Qi = eig_decomposition(laplacian(p).toarray())
+        den = l1[:, None] + (p.eps ** 2 * lam ** 2 - jbar * lam)[None, :] + z[:, None] * lam[None, :]
+        x = np.fft.ifft(((S1 @ Qi.T) / den) @ Q.T, axis=0).real
+        return x / gam[:, None]
     th = 1.0 if p.equation == CAHN_HILLIARD else p.theta
     l2 = th + (1.0 - th) * z
     A = dense_A(p, jbar)
@@ -459,12 +516,16 @@ def diagonalized_apply_separable(p: Problem, alpha: float, r: np.ndarray, jbar: 
     S1 = np.fft.fft(gam[:, None] * r, axis=0)
     z = alpha ** (1.0 / nt) * np.exp(-2j * np.pi * n / nt)
     l1 = (1.0 - z) / p.dt
-    th = 1.0 if p.equation == CAHN_HILLIARD else p.theta
+    th = 1.0 if p.equation in CH_EQUATIONS else p.theta
     l2 = th + (1.0 - th) * z
+    l3 = np.zeros(nt, dtype=complex)          # Eyre: the explicit Laplacian's circulant, lambda_3k
     if p.equation == BIHARMONIC:
         c2, c1 = 1.0, 0.0
     elif p.equation == LINEAR_CH:
         c2, c1 = p.eps ** 2, p.beta * abs(p.beta)
+    elif p.equation == CAHN_HILLIARD_EYRE:
+        c2, c1 = p.eps ** 2, -jbar
+        l3 = z
     else:
         c2, c1 = p.eps ** 2, 1.0 - jbar
     ex, Qx, Qxi = eig_decomposition(laplacian_1d(p.nx, p.bc).toarray())
@@ -477,7 +538,7 @@ def diagonalized_apply_separable(p: Problem, alpha: float, r: np.ndarray, jbar: 
         X = S1.reshape(nt, p.ny, p.nx)
         S1h = (Qyi @ X @ Qxi.T).reshape(nt, -1)      # Q_y^{-1} X Q_x^{-T} per frequency
     mu = c2 * lam ** 2 + c1 * lam
-    S2h = S1h / (l1[:, None] + l2[:, None] * mu[None, :])
+    S2h = S1h / (l1[:, None] + l2[:, None] * mu[None, :] + l3[:, None] * lam[None, :])
     if p.dim == 1:
         S2 = S2h @ Qx.T
     else:
@@ -485,6 +546,27 @@ def diagonalized_apply_separable(p: Problem, alpha: float, r: np.ndarray, jbar: 
         S2 = (Qy @ Y @ Qx.T).reshape(nt, -1)         # Q_y Y Q_x^T
     x = np.fft.ifft(S2, axis=0).real
     return x / gam[:, None]
+
+
+def all_at_once_newton_eyre(p: Problem, u0: np.ndarray, tol: float = 1e-13,
+                            max_newton: int = 60) -> np.ndarray:
+    """Solve the alpha = 0 all-at-once system of Eyre's scheme (Eq. 4.21 with
+    alpha = 0) by Newton with the exact block Jacobian (Eq. 4.23), densely."""
+    nt, ns = p.nt, p.nspace
+    L = laplacian(p).toarray()
+    It = np.eye(nt)
+    lin = (np.kron(circulant_C1(nt, p.dt, 0.0), np.eye(ns)) + np.kron(It, p.eps ** 2 * L @ L)
+           + np.kron(circulant_C2(nt, 0.0, 0.0), L))
+    LL = np.kron(It, L)
+    U = np.tile(u0, nt)
+    for _ in range(max_newton):
+        G = -residual(p, u0, U.reshape(nt, ns)).ravel()
+        J = lin - LL @ np.diag(3.0 * U ** 2)
+        dU = np.linalg.solve(J, -G)
+        U = U + dU
+        if np.max(np.abs(dU)) <= tol * max(1.0, np.max(np.abs(U))):
+            return U.reshape(nt, ns)
+    raise RuntimeError("dense all-at-once Newton did not converge")
 
 
 def jbar_of(U: np.ndarray) -> float:
@@ -505,7 +587,7 @@ def pint_iteration_residual_form(p: Problem, u0: np.ndarray, U_init: np.ndarray,
     out = []
     for _ in range(iters):
         r = residual(p, u0, U)
-        jb = jbar_of(U) if p.equation == CAHN_HILLIARD else None
+        jb = jbar_of(U) if p.equation in CH_EQUATIONS else None
         if dense:
             d = precond_dense(p, alpha, r, jb)
         else:

@@ -363,3 +363,64 @@ def test_signed_beta_squared_eigenmode_decay(bc):
     assert O.rel_err(U, expect) < 1e-11
     r = synth.random_iterate(nt, n, 3)
     assert O.rel_err(O.diagonalized_apply(p, 0.02, r), O.precond_dense(p, 0.02, r)) < 1e-10
+
+
+# --- Cahn-Hilliard with Eyre's splitting (PinT-II, Sec. 4.2) -------------------
+
+def _eyre(**kw):
+    d = dict(equation=O.CAHN_HILLIARD_EYRE, dim=1, nx=12, bc="neumann", eps=0.1, T=4e-3, nt=5)
+    d.update(kw)
+    return P(**d)
+
+
+def test_eyre_all_at_once_newton_equals_sequential_and_residual_vanishes():
+    p = _eyre()
+    u0 = 0.6 * np.cos(np.pi * synth.grid_points_1d(12, "neumann")) + 0.1
+    Useq = O.sequential(p, u0)
+    assert O.rel_err(O.all_at_once_newton_eyre(p, u0), Useq) < 1e-11
+    assert np.abs(O.residual(p, u0, Useq)).max() < 1e-9 * np.abs(u0).max() / p.dt
+    # at U = 0 the residual is b: b_1 = u0/dt - Delta u0, zero below
+    R0 = O.residual(p, u0, np.zeros((p.nt, p.nspace)))
+    L = O.laplacian(p)
+    assert np.allclose(R0[0], u0 / p.dt - L @ u0, rtol=1e-13, atol=1e-9)
+    assert np.abs(R0[1:]).max() == 0.0
+
+
+def test_eyre_step_is_the_split_scheme():
+    # one step solves (u - u_prev)/dt = Delta(u^3) - Delta u_prev - eps^2 Delta^2 u (convex part
+    # implicit, concave part explicit), written out with dense matrices
+    p = _eyre(nx=9, nt=1, T=1e-3)
+    u_prev = synth.u0_uniform(9, -0.8, 0.8, 5)
+    u = O.sequential(p, u_prev)[0]
+    L = O.laplacian(p).toarray()
+    lhs = (u - u_prev) / p.dt
+    rhs = L @ u ** 3 - L @ u_prev - p.eps ** 2 * L @ (L @ u)
+    assert np.allclose(lhs, rhs, rtol=1e-11, atol=1e-8)
+
+
+def test_eyre_unconditionally_energy_stable_and_mass_conserving():
+    # Eyre's scheme decreases the discrete energy for any dt (here dt = 1e-2 >> eps^2 = 1e-3)
+    p = _eyre(dim=2, nx=10, ny=10, eps=0.0316, T=0.2, nt=20)
+    u0 = synth.u0_ch(100, 3)
+    U = O.sequential(p, u0)
+    E = [O.discrete_energy(p, u0)] + [O.discrete_energy(p, u) for u in U]
+    assert all(E[i + 1] <= E[i] + 1e-12 for i in range(len(E) - 1))
+    m0 = O.discrete_mass(p, u0)
+    assert max(abs(O.discrete_mass(p, u) - m0) for u in U) < 1e-12
+
+
+def test_eyre_diagonalized_equals_dense_and_iteration_converges():
+    p = _eyre(dim=2, nx=6, ny=5, nt=8, T=3e-3, alpha=0.02)
+    r = synth.random_iterate(8, p.nspace, 13)
+    d_dense = O.precond_dense(p, p.alpha, r, 0.6)
+    assert O.rel_err(O.diagonalized_apply(p, p.alpha, r, 0.6), d_dense) < 1e-10
+    assert O.rel_err(O.diagonalized_apply_separable(p, p.alpha, r, 0.6), d_dense) < 1e-10
+    u0 = synth.u0_ch(p.nspace, 4)
+    its = O.pint_iteration_residual_form(p, u0, np.tile(u0, (p.nt, 1)), 12)
+    assert O.rel_err(its[-1], O.sequential(p, u0)) < 1e-10
+
+
+def test_eyre_constant_state_is_stationary():
+    p = _eyre(dim=2, nx=6, ny=6)
+    U = O.sequential(p, np.full(36, -0.4))
+    assert np.abs(U + 0.4).max() < 1e-13
