@@ -43,6 +43,11 @@ WORKLOADS = {
     # The same at 128x128 (a size the CPU oracle finishes).
     "cahn_hilliard_2d_128x128_8x256": dict(equation="cahn_hilliard", dim=2, nx=128, ny=128, bc="neumann", eps=0.02,
                                            beta=0.0, T=2048 * 1e-4, nt=256, n_windows=8, u0="ch"),
+    # 2-D Cahn-Hilliard with Eyre's splitting (PinT-II): Neumann 64x64, eps = 0.01, dt = 1e-5, 39 windows of
+    # 256 steps (T = 0.09984), alpha = 0.05, u0 = 0.1 uniform[-1,1] minus its mean (the paper's 2-D PinT-II demo)
+    "cahn_hilliard_eyre_2d_64x64_39x256": dict(equation="cahn_hilliard_eyre", dim=2, nx=64, ny=64, bc="neumann",
+                                               eps=0.01, beta=0.0, T=39 * 256 * 1e-5, nt=256, n_windows=39,
+                                               u0="ch", alpha=0.05),
     # 1-D biharmonic, simply supported, 64 vertices, N_t = 32, T = 0.01, u0 = sin(pi x) + 0.5 sin(3 pi x)
     "biharmonic_1d_64_nt32": dict(equation="biharmonic", dim=1, nx=64, ny=1, bc="ss", eps=1.0, beta=0.0,
                                   T=0.01, nt=32, n_windows=1, u0="sines"),
@@ -62,8 +67,8 @@ def make_u0(wl: dict, seed: int):
 
 
 def solver_kw(wl: dict, args, precision=None) -> dict:
-    kw = {k: v for k, v in wl.items() if k != "u0"}
-    kw.update(alpha=args.alpha, tol=args.tol, max_iter=250, precision=precision or args.precision,
+    kw = {k: v for k, v in wl.items() if k not in ("u0", "alpha")}
+    kw.update(alpha=wl.get("alpha", args.alpha), tol=args.tol, max_iter=250, precision=precision or args.precision,
               init_guess=args.init)
     return kw
 
@@ -99,6 +104,11 @@ def ff_residual_ops_per_dof(equation: str, dim: int, accurate: bool = False) -> 
     terms is one error-free sum (accurate: two subtractions and an add per extra
     term); 4 more ops scale s and accumulate the norms."""
     halo = 514.0 / 512.0 if dim == 1 else (34.0 * 18.0) / (32.0 * 16.0)
+    if equation == "cahn_hilliard_eyre" and not accurate:
+        # Eyre's splitting: c2 Lap^2 u_n and cN Lap(u_n^3) (multiply, multiply, accurate add), the
+        # explicit c1 Lap u_{n-1} (one multiply), one error-free sum of four terms
+        lap = 24.0 if dim == 1 else 40.0
+        return lap * halo + lap + 16.0 * halo + lap + 8.0 + 8.0 + 20.0 + 8.0 + 30.0 + 4.0
     nterm = 1 + (equation in ("linear_ch", "cahn_hilliard")) + (equation == "cahn_hilliard")
     if accurate:
         lap = 42.0 if dim == 1 else 82.0
@@ -266,7 +276,7 @@ def main_gpu(args) -> None:
     u0_np = make_u0(wl, args.seed + rank)          # each replica solves its own instance
     stream = torch.cuda.current_stream()
     s = pint.Solver(stream=stream, **kw)
-    if wl["equation"] == "cahn_hilliard":
+    if wl["equation"] in ("cahn_hilliard", "cahn_hilliard_eyre"):
         s.set_adaptive_windows(True)
     if args.no_graphs:
         s.set_graphs(False)
@@ -377,7 +387,7 @@ def main_gpu(args) -> None:
     dof_l = dof / max(1, stats.get("segments", 1)) if nwin > 1 or stats.get("segments", 1) > 1 else dof
     dom = max((k for k in prof if prof[k]["launches"] > 0 and k != "check"), key=lambda k: prof[k]["ms"])
     iters_per_step = stats["iters"]
-    zero_start = args.init == 2 and wl["equation"] != "cahn_hilliard"   # Cahn-Hilliard starts from u0
+    zero_start = args.init == 2 and not wl["equation"].startswith("cahn_hilliard")   # CH starts from u0
     res_evals = iters_per_step + (0 if zero_start else 1)   # the zero start skips the first residual
     active = {k: (args.steps * (res_evals if k == "residual" else iters_per_step)
                   if k not in ("setup", "check") else prof[k]["launches"]) for k in prof}

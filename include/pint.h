@@ -46,7 +46,10 @@ extern "C" {
 #define PINT_EDIVERGED  -5   /* residual non-finite, grew by 1e6 over its first value, or
                                 grew monotonically and by 10x over three iterations */
 
-typedef enum { PINT_BIHARMONIC = 0, PINT_LINEAR_CH = 1, PINT_CAHN_HILLIARD = 2 } pint_equation;
+/* PINT_CAHN_HILLIARD:      fully implicit backward Euler (Eq. 4.5), preconditioner of Eq. 4.14 (PinT-I);
+ * PINT_CAHN_HILLIARD_EYRE: Eyre's convex-concave splitting, u^3 implicit and the concave -u explicit
+ *                          (Sec. 4.2), preconditioner of Eq. 4.25 (PinT-II). */
+typedef enum { PINT_BIHARMONIC = 0, PINT_LINEAR_CH = 1, PINT_CAHN_HILLIARD = 2, PINT_CAHN_HILLIARD_EYRE = 3 } pint_equation;
 
 /* Boundary conditions (Sec. 5.1 lists the variants):
  *  SIMPLY_SUPPORTED: u = Lap u = 0, vertex grid of n interior points, h = 1/(n+1);

@@ -79,9 +79,10 @@ __global__ void __launch_bounds__(256) k_residual(Geo g, const double* __restric
     const int pidx = (DIM == 2 ? gy * g.nx : 0) + gx;
     const int n0 = blockIdx.z * chunk;
     const int n1 = min(g.nt, n0 + chunk);
-    const bool prev = g.th < 1.0;   // theta < 1: A(u_{n-1}) is needed, from one extra level before the chunk
+    // theta < 1 needs A(u_{n-1}); Eyre's splitting needs Lap u_{n-1}: both from one extra level before the chunk
+    const bool prev = g.th < 1.0 || g.expl;
 
-    double uprev = 0.0, Aprev = 0.0;
+    double uprev = 0.0, Aprev = 0.0, Lprev = 0.0;
     if (inside) uprev = n0 == 0 ? u0[pidx] : (U ? U[(size_t)(n0 - 1) * g.nspace + pidx] : 0.0);
     double acc_r2 = 0.0, acc_u2 = 0.0;
 
@@ -108,7 +109,7 @@ __global__ void __launch_bounds__(256) k_residual(Geo g, const double* __restric
             double L2 = (sL[cl - 1] + sL[cl + 1] - 2.0 * L) * g.ihx2;
             if (DIM == 2) L2 += (sL[cl - LX] + sL[cl + LX] - 2.0 * L) * g.ihy2;
             const double u = su[cu];
-            double A = g.c2 * L2 + g.c1 * L;
+            double A = g.c2 * L2 + (g.expl ? 0.0 : g.c1 * L);
             if (g.cN != 0.0) {
                 double w0 = u * u * u;
                 double we = su[cu + 1] * su[cu + 1] * su[cu + 1];
@@ -122,8 +123,9 @@ __global__ void __launch_bounds__(256) k_residual(Geo g, const double* __restric
                 A = fma(g.cN, lw, A);
             }
             if (n >= n0) {
-                const double r = prev ? (uprev - u) * g.inv_dt - g.th * A - (1.0 - g.th) * Aprev
-                                      : (uprev - u) * g.inv_dt - A;
+                const double r = g.expl ? (uprev - u) * g.inv_dt - A - g.c1 * Lprev
+                                 : prev ? (uprev - u) * g.inv_dt - g.th * A - (1.0 - g.th) * Aprev
+                                        : (uprev - u) * g.inv_dt - A;
                 const size_t o = (size_t)n * g.nspace + pidx;
                 if (r_out) r_out[o] = r;
                 if (s_out) s_out[o] = (TS)(gam[n] * r);
@@ -132,6 +134,7 @@ __global__ void __launch_bounds__(256) k_residual(Geo g, const double* __restric
                 uprev = u;
             }
             Aprev = A;
+            Lprev = L;
         }
         __syncthreads();
     }
@@ -337,8 +340,8 @@ int norm2_blocks(int n) {
 }
 void launch_begin_window(const Geo& g, const double* u0, int max_iter, double tol, double* partials, Ctl* ctl,
                          cudaStream_t st, double tol_update, double* b1) {
-    if (g.th < 1.0) {
-        // b_1 = u0/dt - (1-theta) A(u0): the first level of the residual at U = 0
+    if (g.th < 1.0 || g.expl) {
+        // b_1 = u0/dt - (1-theta) A(u0) (Eyre: u0/dt - Lap u0): the first level of the residual at U = 0
         Geo g1 = g;
         g1.nt = 1;
         int gx, gy, gz, chunk;

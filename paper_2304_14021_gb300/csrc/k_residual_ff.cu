@@ -3,7 +3,8 @@
 // the conversions between FP64 and float-float iterates.
 //
 // Same operator and boundary treatment as k_residual.cu (Eq. 2.6 / 4.8 with
-// alpha = 0; theta = 1 below, theta = 1/2 adds A(u_{n-1})):
+// alpha = 0; theta = 1 below, theta = 1/2 adds A(u_{n-1}), Eyre's splitting
+// takes the Laplacian term at u_{n-1}):
 //   r_n = (u_{n-1} - u_n)/dt - [c2 Lap^2 u_n + c1 Lap u_n + cN Lap(u_n^3)],
 // evaluated as dt r_n (see k_residual_ff below).
 // The stencil sums are error-free in their high words (a TwoSum chain), so the
@@ -132,7 +133,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // so the time difference needs no product; s = (gamma_n / dt) r' and the norm
 // partials carry the factor 1/dt^2.  The CTA stages time level n+1 of its tile
 // (with halo) by asynchronous copies while it computes level n.
-template <int DIM, bool SQ, bool ACC>
+template <int DIM, bool SQ, bool ACC, bool USEP>
 __global__ void __launch_bounds__(256, 5) k_residual_ff(GeoFF g, const ff* __restrict__ U, const ff* __restrict__ u0,
                                                      const float* __restrict__ gamf, float* __restrict__ s_out,
                                                      double* __restrict__ partials, const Ctl* __restrict__ ctl,
@@ -216,12 +217,14 @@ __global__ void __launch_bounds__(256, 5) k_residual_ff(GeoFF g, const ff* __res
     }
     float acc_r2 = 0.f, acc_u2 = 0.f;
     const float sdt = g.inv_dt.x;
-    // theta = 1/2: A'(u_{n-1}) per point, from one extra level before the chunk
-    const bool half = g.half != 0;
-    ff Aprev[PPT];
+    // theta = 1/2: A'(u_{n-1}) per point; Eyre's splitting: Lap u_{n-1} per point;
+    // both from one extra level before the chunk
+    const bool expl = g.expl != 0;
+    constexpr bool usep = USEP;   // theta = 1/2 or Eyre (a separate instantiation keeps the default path lean)
+    ff Aprev[PPT], Lprev[PPT];
 #pragma unroll
-    for (int q = 0; q < PPT; ++q) Aprev[q] = ffmk(0.f, 0.f);
-    const int nfirst = half ? n0 - 1 : n0;
+    for (int q = 0; q < PPT; ++q) Aprev[q] = Lprev[q] = ffmk(0.f, 0.f);
+    const int nfirst = usep ? n0 - 1 : n0;
 
     if (n0 < n1) stage(nfirst, su[0]);
     for (int n = nfirst; n < n1; ++n) {
@@ -236,26 +239,29 @@ __global__ void __launch_bounds__(256, 5) k_residual_ff(GeoFF g, const ff* __res
                 if (ch) sW[tid + a * NTHR] = ff_cube(cur[lc[a]]);
             }
         __syncthreads();
-        if (half) {
-            // Crank-Nicolson: dt r = u_{n-1} - u_n - A'(u_n) - A'(u_{n-1}), A' = dt A / 2 (linear equations)
+        if constexpr (usep) {
+            // Crank-Nicolson: dt r = u_{n-1} - u_n - A'(u_n) - A'(u_{n-1}), A' = dt A / 2 (linear equations);
+            // Eyre: dt r = u_{n-1} - u_n - dt (c2 Lap^2 u_n + cN Lap u_n^3) - dt c1 Lap u_{n-1}
 #pragma unroll
             for (int q = 0; q < PPT; ++q) {
                 if (inside[q]) {
                     const ff L = sL[cl[q]];
                     const ff lapL = lap_ff<DIM, SQ, ACC>(sL, cl[q], LX, g);
                     ff A = ff_mul(lapL, g.c2);
-                    if (lin1) A = ff_add(A, ff_mul(L, g.c1));
+                    if (lin1 && !expl) A = ff_add(A, ff_mul(L, g.c1));
+                    if (ch) A = ff_add(A, ff_mul(lap_ff<DIM, SQ, ACC>(sW, cl[q], LX, g), g.cN));
                     if (n >= n0) {
                         const ff u = cur[cu[q]];
+                        const ff B = expl ? ff_mul(Lprev[q], g.c1) : Aprev[q];
                         ff r;
                         if constexpr (SQ && !ACC) {
                             ff_acc acc(uprev[q]);
                             acc.add(ff_neg(u));
                             acc.add(ff_neg(A));
-                            acc.add(ff_neg(Aprev[q]));
+                            acc.add(ff_neg(B));
                             r = acc.get();
                         } else {
-                            r = ff_sub(ff_sub(ff_sub(uprev[q], u), A), Aprev[q]);
+                            r = ff_sub(ff_sub(ff_sub(uprev[q], u), A), B);
                         }
                         *sp[q] = fmaf(gamf[n] * sdt, r.x, gamf[n] * sdt * r.y);
                         acc_r2 = fmaf(r.x, r.x, acc_r2);
@@ -263,6 +269,7 @@ __global__ void __launch_bounds__(256, 5) k_residual_ff(GeoFF g, const ff* __res
                         uprev[q] = u;
                     }
                     Aprev[q] = A;
+                    Lprev[q] = L;
                 }
                 if (n >= n0) sp[q] += g.nspace;
             }
@@ -369,7 +376,12 @@ void launch_residual_ff(const GeoFF& g, const Geo& g64, const ff* U, const ff* u
     dim3 grid(gx, gy, gz);
     const bool sq = g64.dim == 1 || g64.ihx2 == g64.ihy2;
     const bool acc = g.accurate != 0;
-#define PINT_RFF(D, S, A) k_residual_ff<D, S, A><<<grid, 256, 0, st>>>(g, U, u0, gamf, s, partials, ctl, chunk)
+    const bool usep = g.half || g.expl;
+#define PINT_RFF(D, S, A)                                                                                      \
+    do {                                                                                                       \
+        if (usep) k_residual_ff<D, S, A, true><<<grid, 256, 0, st>>>(g, U, u0, gamf, s, partials, ctl, chunk);  \
+        else k_residual_ff<D, S, A, false><<<grid, 256, 0, st>>>(g, U, u0, gamf, s, partials, ctl, chunk);      \
+    } while (0)
     if (g.dim == 2) {
         if (sq) { if (acc) PINT_RFF(2, true, true); else PINT_RFF(2, true, false); }
         else PINT_RFF(2, false, false);

@@ -32,12 +32,17 @@ template <class T>
 __device__ __forceinline__ c_t<T> shift_den(const Tabs<T>& tb, int k, T Lam, T c2, T c1) {
     const T mu = c2 * Lam * Lam + c1 * Lam;
     const c_t<T> l1 = tb.lam1[k], l2 = tb.lam2[k];
-    return mkc(l1.x + l2.x * mu, l1.y + l2.y * mu);
+    c_t<T> d = mkc(l1.x + l2.x * mu, l1.y + l2.y * mu);
+    if (tb.dte != T(0)) {   // PinT-II: + lambda_3k Lam, lambda_3k = alpha^{1/N_t} e^{-2 pi i k/N_t} = 1 - dt lambda_1k
+        d.x += (T(1) - tb.dte * l1.x) * Lam;
+        d.y -= tb.dte * l1.y * Lam;
+    }
+    return d;
 }
 
 template <class T>
 __device__ __forceinline__ T solve_c1(SolveCoef co, const Ctl* ctl) {
-    return co.ch ? T(1.0 - ctl->jbar) : T(co.c1);
+    return co.ch ? T(co.c1 - ctl->jbar) : T(co.c1);
 }
 
 // position of x_i in the even/odd reordered sequence v (v_j = x_2j, v_{n-1-j} = x_{2j+1})

@@ -49,7 +49,7 @@ static int axis_fft(int n, int bc, int nmax_fft) { return bc == PINT_BC_NEUMANN 
 
 static int validate(const pint_problem* p) {
     if (!p) return PINT_EINVAL;
-    if (p->equation < 0 || p->equation > 2) return PINT_EINVAL;
+    if (p->equation < 0 || p->equation > 3) return PINT_EINVAL;
     if (p->dim != 1 && p->dim != 2) return PINT_EINVAL;
     if (p->bc != PINT_BC_SIMPLY_SUPPORTED && p->bc != PINT_BC_NEUMANN && p->bc != PINT_BC_NEUMANN_VERTEX)
         return PINT_EINVAL;
@@ -58,7 +58,8 @@ static int validate(const pint_problem* p) {
     if (!is_pow2(p->nt) || p->nt < 2 || p->nt > 1024) return PINT_EINVAL;
     if (p->n_windows < 1) return PINT_EINVAL;
     // theta-method: backward Euler (1) for every equation, Crank-Nicolson (1/2) for the linear ones
-    if (!(p->theta == 1.0 || (p->theta == 0.5 && p->equation != PINT_CAHN_HILLIARD))) return PINT_EINVAL;
+    const bool chq = p->equation == PINT_CAHN_HILLIARD || p->equation == PINT_CAHN_HILLIARD_EYRE;
+    if (!(p->theta == 1.0 || (p->theta == 0.5 && !chq))) return PINT_EINVAL;
     if (!(p->alpha > 0.0 && p->alpha < 1.0)) return PINT_EINVAL;
     if (!(p->tol > 0.0) || !isfinite(p->tol)) return PINT_EINVAL;
     if (p->max_iter < 1 || p->max_iter >= PINT_HIST_MAX) return PINT_EINVAL;
@@ -89,6 +90,10 @@ static double lap_eig(int p, int n, int bc) {
 }
 
 static bool f32_transforms(const pint_problem* p) { return p->precision != PINT_FP64; }
+
+// The first right-hand-side level b_1 involves u0 beyond u0/dt (theta < 1, or
+// Eyre's explicit Laplacian): it is computed once per window and kept.
+static bool needs_b1(const pint_problem* p) { return p->theta < 1.0 || p->equation == PINT_CAHN_HILLIARD_EYRE; }
 
 // Pinned host mirrors of the device control blocks, carved from one page-locked
 // slab per process (page-locking per handle would be slow and would serialize
@@ -305,6 +310,7 @@ static int build_tables(pint_handle* h) {
     tb->lamy = base + L.lamy;
     tb->lam1 = reinterpret_cast<const c_t<T>*>(base + L.lam1);
     tb->lam2 = reinterpret_cast<const c_t<T>*>(base + L.lam2);
+    tb->dte = p->equation == PINT_CAHN_HILLIARD_EYRE ? (T)h->geo.dt : T(0);
     h->tabs_ptrs = tb;
     // gamma tables (always FP64: the scaling and unscaling are FP64 steps)
     std::vector<double> g(nt), gi(nt);
@@ -418,8 +424,9 @@ static void derive(const pint_problem* p, pint_handle* h) {
         default: g.c2 = p->eps * p->eps; g.c1 = 1.0; g.cN = -1.0; h->coef.ch = 1; break;
     }
     g.th = p->theta;
+    g.expl = p->equation == PINT_CAHN_HILLIARD_EYRE ? 1 : 0;
     h->coef.c2 = g.c2;
-    h->coef.c1 = g.c1;
+    h->coef.c1 = g.expl ? 0.0 : g.c1;   // Eyre: the Laplacian term is explicit (lambda_3k in Step 2)
     h->fft_x = axis_fft(p->nx, p->bc, 4096);
     h->fft_y = p->dim == 2 ? axis_fft(g.ny, p->bc, 1024) : 1;
     GeoFF& f = h->gff;
@@ -441,6 +448,7 @@ static void derive(const pint_problem* p, pint_handle* h) {
     f.c1 = ff_from_double(g.c1 * s1 * g.dt * g.th);
     f.cN = ff_from_double(g.cN * s1 * g.dt * g.th);
     f.half = g.th < 1.0 ? 1 : 0;
+    f.expl = g.expl;
     // stiffness dt * max |spectrum of the spatial operator|: above 1e7 the stencil
     // sums use chained accurate double-word additions (see k_residual_ff.cu)
     const double lam_max = 4.0 * g.ihx2 + (g.dim == 2 ? 4.0 * g.ihy2 : 0.0);
@@ -476,7 +484,7 @@ static long long footprint_of(const pint_problem* p) {
     b += z.partials * 2 * sizeof(double);
     b += (z.nspace / 16 + 2) * 2 * sizeof(double);
     b += 2 * (size_t)p->nt * sizeof(double);
-    b += z.nspace * sizeof(double) * (p->theta < 1.0 ? 2 : 1);
+    b += z.nspace * sizeof(double) * (needs_b1(p) ? 2 : 1);
     b += z.dof * ts;                 // s
     b += z.nk * z.nspace * 2 * ts;   // S
     b += z.tables_bytes;
@@ -591,8 +599,9 @@ static cudaError_t zero_start(pint_handle* h, double* U, const double* u0w) {
     const int nk = g.nt / 2 + 1;
     prof_begin(h, PH_TFWD);
     // spectrum of b: b_1 at every frequency (theta = 1: b_1 = u0/dt; else computed at the window start)
-    const double* b1 = g.th < 1.0 ? h->b1 : u0w;
-    const double sc = g.th < 1.0 ? 1.0 : g.inv_dt;
+    const bool nb = g.th < 1.0 || g.expl;
+    const double* b1 = nb ? h->b1 : u0w;
+    const double sc = nb ? 1.0 : g.inv_dt;
     if (f32_transforms(&h->p)) launch_zero_start<float>(reinterpret_cast<float2*>(h->S), b1, sc, g.nspace, nk, h->ctl, h->st);
     else launch_zero_start<double>(reinterpret_cast<double2*>(h->S), b1, sc, g.nspace, nk, h->ctl, h->st);
     prof_end(h, PH_TFWD, 1);
@@ -737,6 +746,7 @@ void geometry_of(const pint_problem* p, Geo& g) {
         default: g.c2 = p->eps * p->eps; g.c1 = 1.0; g.cN = -1.0; break;
     }
     g.th = p->theta;
+    g.expl = p->equation == PINT_CAHN_HILLIARD_EYRE ? 1 : 0;
 }
 
 // dt * max|spectrum| of the spatial operator (for Cahn-Hilliard with the
@@ -758,7 +768,7 @@ double stiffness_of(const pint_problem* p) {
 // solve runs in FP64.
 int effective_precision(const pint_problem* p) {
     if (p->precision == PINT_FP64) return PINT_FP64;
-    const double limit = p->equation == PINT_CAHN_HILLIARD ? 0.1 : 1.0;
+    const double limit = (p->equation == PINT_CAHN_HILLIARD || p->equation == PINT_CAHN_HILLIARD_EYRE) ? 0.1 : 1.0;
     return stiffness_of(p) * 0x1p-24 > limit ? PINT_FP64 : p->precision;
 }
 
@@ -867,7 +877,7 @@ int pint_create(const pint_problem* p, void* cuda_stream, pint_handle** out) {
     if (!rc) rc = dalloc((void**)&h->gam, p->nt * sizeof(double));
     if (!rc) rc = dalloc((void**)&h->ginv, p->nt * sizeof(double));
     if (!rc) rc = dalloc((void**)&h->u0buf, z.nspace * sizeof(double));
-    if (!rc && p->theta < 1.0) rc = dalloc((void**)&h->b1, z.nspace * sizeof(double));
+    if (!rc && needs_b1(p)) rc = dalloc((void**)&h->b1, z.nspace * sizeof(double));
     if (!rc) rc = dalloc(&h->s, z.dof * ts);
     if (!rc) rc = dalloc(&h->S, z.nk * z.nspace * 2 * ts);
     if (!rc) rc = dalloc(&h->tab, z.tables_bytes);
@@ -965,22 +975,29 @@ int pint_profile_read(pint_handle* h, pint_profile* out, int reset) {
 // length L (a power of two, <= lmax) with alpha * G(L) <= 0.1, where
 // G(L) = max_p R_p^L and R_p = 1/(1 + dt mu_p) over the spectrum mu_p of the
 // spatial operator linearized about the segment's initial data (for
-// Cahn-Hilliard mu(Lam) = eps^2 Lam^2 + (1 - jbar0) Lam with jbar0 = mean 3 u0^2).
+// Cahn-Hilliard mu(Lam) = eps^2 Lam^2 + (1 - jbar0) Lam with jbar0 = mean 3 u0^2;
+// Eyre's splitting has its own factor, below).
 // A mode with alpha R^L near 1 makes the iteration resonate (per-mode factor
 // |alpha R^L / (1 - alpha R^L)|, Eq. 2.18), so growing modes force short segments.
 static int choose_level(pint_handle* h, int lmax, double jbar0) {
-    const double dt = h->geo.dt, c2 = h->coef.c2, c1 = h->coef.ch ? 1.0 - jbar0 : h->coef.c1;
-    double mu_min = 0.0;
+    // per-step amplification of mode Lam of the scheme linearized about the data:
+    //   backward Euler:  R = 1 / (1 + dt mu),  mu = c2 Lam^2 + c1 Lam (c1 = 1 - jbar0 for CH);
+    //   Eyre splitting:  R = (1 - dt Lam) / (1 + dt (c2 Lam^2 - jbar0 Lam))
+    const bool eyre = h->geo.expl != 0;
+    const double dt = h->geo.dt, c2 = h->coef.c2, c1 = h->coef.ch ? h->coef.c1 - jbar0 : h->coef.c1;
+    double lnR = 0.0;
+    bool unstable = false;
     for (double lx : h->lamx_h)
         for (double ly : h->lamy_h) {
-            const double L = lx + ly, mu = c2 * L * L + c1 * L;
-            if (mu < mu_min) mu_min = mu;
+            const double L = lx + ly, den = 1.0 + dt * (c2 * L * L + c1 * L);
+            if (den <= 0.0) { unstable = true; continue; }
+            const double num = eyre ? 1.0 - dt * L : 1.0;
+            lnR = fmax(lnR, log(fabs(num) / den));
         }
     int li = 0;
     while (li + 1 < h->nlev && h->lev[li].nt > lmax) ++li;
-    if (mu_min >= 0.0) return li;
-    if (1.0 + dt * mu_min <= 0.0) return h->nlev - 1;
-    const double lnR = -log1p(dt * mu_min);
+    if (unstable) return h->nlev - 1;
+    if (lnR <= 0.0) return li;
     for (; li < h->nlev; ++li)
         if (log(h->p.alpha) + h->lev[li].nt * lnR <= log(0.1)) return li;
     return h->nlev - 1;

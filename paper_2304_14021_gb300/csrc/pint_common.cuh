@@ -305,6 +305,7 @@ struct Geo {
     double dt, inv_dt, ihx2, ihy2;   // 1/h^2 per axis
     double c2, c1, cN;
     double th;                       // theta of the theta-method (1 or 1/2)
+    int expl;                        // 1: the c1 Laplacian term acts on u_{n-1} (Eyre splitting)
 };
 
 // Reduction helpers (deterministic: fixed shuffle tree, fixed warp order).

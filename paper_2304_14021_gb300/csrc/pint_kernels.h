@@ -22,10 +22,12 @@ template <class T> struct Tabs {
     const T* lamy;       // ny
     const c_t<T>* lam1;  // nt/2+1: lambda_1k of Lemma 2.1
     const c_t<T>* lam2;  // nt/2+1: lambda_2k
+    T dte;               // Eyre splitting (PinT-II): dt, so that lambda_3k = 1 - dt lambda_1k; else 0
 };
 
 // Coefficients of the shifted spatial solve: mu(Lam) = c2 Lam^2 + c1 Lam,
-// c1 = 1 - jbar (read from ctl) when ch != 0.
+// c1 - jbar (jbar read from ctl) when ch != 0: 1 - jbar for PinT-I, -jbar
+// for PinT-II (whose explicit Laplacian enters as lambda_3k Lam).
 struct SolveCoef {
     double c2, c1;
     int ch;
@@ -40,6 +42,7 @@ struct GeoFF {
     float2 ihx2, ihy2, inv_dt, c2, c1, cN;
     int accurate;   // 1: chained accurate double-word stencil sums (very stiff problems)
     int half;       // theta = 1/2: the residual also carries A'(u_{n-1})
+    int expl;       // Eyre splitting: the c1 Laplacian term acts on u_{n-1}
 };
 
 int residual_grid(const Geo& g, int& gx, int& gy, int& gz, int& chunk);

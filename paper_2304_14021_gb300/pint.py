@@ -19,7 +19,8 @@ BC_SIMPLY_SUPPORTED, BC_NEUMANN = 0, 1
 FP64, MIXED, MIXED_FF = 0, 1, 2
 HIST_MAX = 256
 
-EQUATIONS = {"biharmonic": BIHARMONIC, "linear_ch": LINEAR_CH, "cahn_hilliard": CAHN_HILLIARD}
+EQUATIONS = {"biharmonic": BIHARMONIC, "linear_ch": LINEAR_CH, "cahn_hilliard": CAHN_HILLIARD,
+             "cahn_hilliard_eyre": 3}
 BCS = {"ss": BC_SIMPLY_SUPPORTED, "neumann": BC_NEUMANN, "neumann_v": 2}
 PRECISIONS = {"fp64": FP64, "mixed": MIXED, "mixed_ff": MIXED_FF}
 PRECISION_NAMES = {v: k for k, v in PRECISIONS.items()}

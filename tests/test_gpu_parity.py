@@ -611,3 +611,73 @@ def test_signed_beta_squared_solve_matches_sequential(precision):
         out = torch.zeros(p.nt, p.nspace, dtype=torch.float64, device="cuda")
         s.precond_apply(dev(r), out)
     assert O.rel_err(host(out), ref) < (1e-11 if precision == "fp64" else 3e-6 / p.alpha)
+
+
+# --- Cahn-Hilliard with Eyre's splitting (PinT-II, Sec. 4.2) ------------------
+
+EYRE_CASES = [
+    dict(equation="cahn_hilliard_eyre", dim=1, nx=64, bc="neumann", nt=16, T=1.6e-3, eps=0.05),
+    dict(equation="cahn_hilliard_eyre", dim=2, nx=16, ny=16, bc="neumann", nt=8, T=8e-4, eps=0.05),
+    dict(equation="cahn_hilliard_eyre", dim=2, nx=12, ny=10, bc="neumann_v", nt=8, T=8e-4, eps=0.05),
+]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_ff"])
+@pytest.mark.parametrize("case", range(len(EYRE_CASES)))
+def test_eyre_precond_matches_dense(case, precision):
+    kw = full(dict(EYRE_CASES[case], precision=precision))
+    p = oprob(kw)
+    r = synth.random_iterate(p.nt, p.nspace, 500 + case)
+    ref = O.precond_dense(p, p.alpha, r, 0.4)
+    with pint.Solver(**kw) as s:
+        out = torch.zeros(p.nt, p.nspace, dtype=torch.float64, device="cuda")
+        s.precond_apply(dev(r), out, jbar=0.4)
+        err = O.rel_err(host(out), ref)
+    assert err < (1e-11 if precision == "fp64" else 3e-6 / p.alpha), err
+
+
+@pytest.mark.parametrize("case", range(len(EYRE_CASES)))
+def test_eyre_residual_matches_oracle(case):
+    kw = full(EYRE_CASES[case])
+    p = oprob(kw)
+    u0 = synth.u0_uniform(p.nspace, -1, 1, 1)
+    U = synth.random_iterate(p.nt, p.nspace, 2)
+    ref = O.residual(p, u0, U)
+    with pint.Solver(**kw) as s:
+        r = torch.empty(p.nt, p.nspace, dtype=torch.float64, device="cuda")
+        rel = s.residual(dev(u0), dev(U), r)
+    assert O.rel_err(host(r), ref) < 1e-13
+    assert abs(rel - np.linalg.norm(ref) / O.rhs_norm(p, u0)) < 1e-12 * rel
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_ff"])
+def test_eyre_windows_match_sequential(precision):
+    # 2-D, Neumann 32^2, eps = 0.05, dt = 1e-4, 3 windows of 16 steps; mass and energy
+    nt, W = 16, 3
+    kw = full(dict(equation="cahn_hilliard_eyre", dim=2, nx=32, ny=32, bc="neumann", eps=0.05, nt=nt, n_windows=W,
+                   T=nt * W * 1e-4, alpha=1e-2, precision=precision, tol=1e-11))
+    p = oprob(kw)
+    u0 = synth.u0_ch(p.nspace, 0)
+    U, st = run_solve(kw, u0)
+    assert st["rc"] == 0 and st["windows"] == W, st
+    err = O.rel_err(U, O.sequential(p, u0)[-nt:])
+    assert err < (1e-10 if precision == "fp64" else 1e-8), err
+    m0 = O.discrete_mass(p, u0)
+    assert max(abs(O.discrete_mass(p, u) - m0) for u in U) < 1e-12
+    E = [O.discrete_energy(p, u) for u in U]
+    assert all(E[i + 1] <= E[i] + 1e-13 for i in range(len(E) - 1))
+
+
+def test_eyre_adaptive_long_run_matches_oracle():
+    # spinodal data over 4 windows of 64 steps with the adaptive window policy
+    nt, W, n = 64, 4, 24
+    kw = full(dict(equation="cahn_hilliard_eyre", dim=2, nx=n, ny=n, bc="neumann", eps=0.03, nt=nt, n_windows=W,
+                   T=nt * W * 1e-4, alpha=1e-2, precision="mixed_ff", tol=1e-9, max_iter=200, tol_update=1e-11))
+    p = oprob(kw)
+    u0 = synth.u0_ch(n * n, 1)
+    with pint.Solver(**kw) as s:
+        s.set_adaptive_windows(True)
+        U = torch.zeros(nt, n * n, dtype=torch.float64, device="cuda")
+        st = s.solve(dev(u0), U)
+    assert st["rc"] == 0 and st["windows"] == W, st
+    assert O.rel_err(host(U), O.sequential(p, u0)[-nt:]) < 1e-7
