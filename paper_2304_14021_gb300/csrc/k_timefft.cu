@@ -267,6 +267,180 @@ __global__ void __launch_bounds__(TimeTmaCfg<NT>::NTH)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Long time axes (1024 < N_t <= 65536): four-step FFT with N_t = N1 N2.  The
+// signal of the spatial point pair (2j, 2j+1) is the complex column
+// z_j[n] = s[n][2j] + i s[n][2j+1] (the float2 / double2 view of a row).
+// With n = n1 N2 + n2 and k = k1 + N1 k2,
+//   Z_k = sum_n2 e^{-2 pi i n2 k2/N2} [ e^{-2 pi i n2 k1/N} sum_n1 z_{n1 N2+n2} e^{-2 pi i n1 k1/N1} ].
+// Pass A transforms over n1 (rows n1 N2 + n2) and applies e^{-2 pi i n2 k1/N};
+// pass B transforms over n2 (rows k1 N2 + n2) and leaves Z_{k1+N1 k2} at row
+// k1 N2 + k2.  Both work in place in a complex workspace of N_t x nspace/2;
+// unpack forms the half spectrum of the real signals (pairs k, N-k) in
+// natural order.  The inverse mirrors it (pack, pass B', pass A' + update).
+// ---------------------------------------------------------------------------
+static void long_split(int nt, int& n1, int& n2) {
+    int l = 0;
+    while ((1 << l) < nt) ++l;
+    n2 = 1 << ((l + 1) / 2);
+    n1 = nt / n2;
+}
+
+// One pass: CTA = (o, column block).  MAP 0: element m sits in row m*N2 + o;
+// MAP 1: row o*N2 + m.  TW: multiply element m by e^{-/+ 2 pi i o m / N}
+// after the transform (sign of DIR).
+template <class T, int NL, int DIR, bool TW, int MAP>
+__global__ void __launch_bounds__(TimeCfg<T, NL>::NTH)
+    k_time_long_pass(int ncol, int n2, int N, c_t<T>* __restrict__ z, const c_t<T>* __restrict__ twN,
+                     const Ctl* __restrict__ ctl) {
+    using C = c_t<T>;
+    constexpr int CW = TimeCfg<T, NL>::CW, NTH = TimeCfg<T, NL>::NTH;
+    if (ctl && ctl->status != ST_RUNNING) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    C* tw = buf + NL * CW;
+    const int tid = threadIdx.x;
+    const int o = blockIdx.y;
+    const int j0 = blockIdx.x * CW;
+    const int step = N / NL;
+    for (int i = tid; i < NL; i += NTH) tw[i] = twN[(size_t)i * step];
+    for (int e = tid; e < NL * CW; e += NTH) {
+        const int c = e % CW, m = e / CW;
+        const size_t row = MAP == 0 ? (size_t)m * n2 + o : (size_t)o * n2 + m;
+        buf[e] = j0 + c < ncol ? z[row * ncol + j0 + c] : mkc(T(0), T(0));
+    }
+    __syncthreads();
+    smem_fft<C, NL, DIR, NTH, CW, CW, 1>(buf, tw);
+    for (int e = tid; e < NL * CW; e += NTH) {
+        const int c = e % CW, m = e / CW;
+        if (j0 + c >= ncol) continue;
+        C v = buf[e];
+        if (TW) {
+            C w = twN[((size_t)o * m) % N];
+            if (DIR > 0) w = conjc(w);
+            v = cmul(v, w);
+        }
+        const size_t row = MAP == 0 ? (size_t)m * n2 + o : (size_t)o * n2 + m;
+        z[row * ncol + j0 + c] = v;
+    }
+}
+
+// Row of Z_k in the workspace after pass B.
+__device__ __forceinline__ size_t long_pos(int k, int n1, int n2) { return (size_t)(k % n1) * n2 + k / n1; }
+
+// S[k][2j], S[k][2j+1] (k = 0..N/2) from Z_k and Z_{N-k}.
+template <class T>
+__global__ void k_time_long_unpack(int N, int n1, int n2, int ncol, const c_t<T>* __restrict__ z, c_t<T>* __restrict__ S,
+                                   const Ctl* __restrict__ ctl) {
+    using C = c_t<T>;
+    if (ctl && ctl->status != ST_RUNNING) return;
+    const size_t total = (size_t)(N / 2 + 1) * ncol;
+    const T half = T(0.5);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(i / ncol), j = (int)(i % ncol);
+        const C zk = z[long_pos(k, n1, n2) * ncol + j];
+        const C zr = z[long_pos((N - k) % N, n1, n2) * ncol + j];
+        C* row = S + (size_t)k * 2 * ncol;
+        row[2 * j] = mkc(half * (zk.x + zr.x), half * (zk.y - zr.y));
+        row[2 * j + 1] = mkc(half * (zk.y + zr.y), half * (zr.x - zk.x));
+    }
+}
+
+// Z_k = S_a[k] + i S_b[k] over the full Hermitian spectrum, into the workspace rows of pass B.
+template <class T>
+__global__ void k_time_long_pack(int N, int n1, int n2, int ncol, const c_t<T>* __restrict__ S, c_t<T>* __restrict__ z,
+                                 const Ctl* __restrict__ ctl) {
+    using C = c_t<T>;
+    if (ctl && ctl->status != ST_RUNNING) return;
+    const size_t total = (size_t)N * ncol;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(i / ncol), j = (int)(i % ncol);
+        const int kk = k <= N / 2 ? k : N - k;
+        const C* row = S + (size_t)kk * 2 * ncol;
+        C a = row[2 * j], b = row[2 * j + 1];
+        if (kk == 0 || kk == N / 2) { a.y = T(0); b.y = T(0); }   // real in exact arithmetic
+        if (k > N / 2) { a.y = -a.y; b.y = -b.y; }
+        z[long_pos(k, n1, n2) * ncol + j] = mkc(a.x - b.y, a.y + b.x);
+    }
+}
+
+// Pass A' (inverse over k1, rows m*N2 + o) and the output: x[n] scaled by
+// ginv[n] (which holds alpha^{-n/N}/N); OUTK as in k_time_inv.
+template <class T, int NL, int OUTK>
+__global__ void __launch_bounds__(TimeCfg<T, NL>::NTH)
+    k_time_long_out(int ncol, int n2, int N, const c_t<T>* __restrict__ z, const c_t<T>* __restrict__ twN,
+                    const double* __restrict__ ginv, const float* __restrict__ ginvf, double* __restrict__ out,
+                    float2* __restrict__ outff, int accumulate, const Ctl* __restrict__ ctl, double* __restrict__ dpart) {
+    using C = c_t<T>;
+    constexpr int CW = TimeCfg<T, NL>::CW, NTH = TimeCfg<T, NL>::NTH;
+    if (ctl && ctl->status != ST_RUNNING) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    C* tw = buf + NL * CW;
+    const int tid = threadIdx.x;
+    const int o = blockIdx.y;
+    const int j0 = blockIdx.x * CW;
+    const int step = N / NL;
+    const int nspace = 2 * ncol;
+    for (int i = tid; i < NL; i += NTH) tw[i] = twN[(size_t)i * step];
+    for (int e = tid; e < NL * CW; e += NTH) {
+        const int c = e % CW, m = e / CW;
+        buf[e] = j0 + c < ncol ? z[((size_t)m * n2 + o) * ncol + j0 + c] : mkc(T(0), T(0));
+    }
+    __syncthreads();
+    smem_fft<C, NL, +1, NTH, CW, CW, 1>(buf, tw);
+    float d2 = 0.f, u2 = 0.f;
+    const bool want = dpart != nullptr;
+    for (int e = tid; e < NL * CW; e += NTH) {
+        const int c = e % CW, m = e / CW;
+        const int j = j0 + c;
+        if (j >= ncol) continue;
+        const size_t n = (size_t)m * n2 + o;
+        const C v = buf[e];
+        if constexpr (OUTK == 1) {
+            const float gi = ginvf[n];
+            float2* row = outff + n * nspace;
+            const float da = (float)v.x * gi, db = (float)v.y * gi;
+            const float2 wa = ff_add_f(row[2 * j], da), wb = ff_add_f(row[2 * j + 1], db);
+            row[2 * j] = wa;
+            row[2 * j + 1] = wb;
+            if (want) {
+                d2 = fmaf(da, da, fmaf(db, db, d2));
+                u2 = fmaf(wa.x, wa.x, fmaf(wb.x, wb.x, u2));
+            }
+        } else {
+            const double gi = ginv[n];
+            double* row = out + n * nspace;
+            const double da = (double)v.x * gi, db = (double)v.y * gi;
+            if (accumulate) {
+                const double wa = row[2 * j] + da, wb = row[2 * j + 1] + db;
+                row[2 * j] = wa;
+                row[2 * j + 1] = wb;
+                if (want) {
+                    d2 = fmaf((float)da, (float)da, fmaf((float)db, (float)db, d2));
+                    u2 = fmaf((float)wa, (float)wa, fmaf((float)wb, (float)wb, u2));
+                }
+            } else {
+                row[2 * j] = da;
+                row[2 * j + 1] = db;
+            }
+        }
+    }
+    if (want) {
+        __shared__ double red[2][32];
+        double a = warp_sum((double)d2), b = warp_sum((double)u2);
+        if (tid % 32 == 0) { red[0][tid / 32] = a; red[1][tid / 32] = b; }
+        __syncthreads();
+        if (tid == 0) {
+            double A = 0.0, B = 0.0;
+            for (int w = 0; w < NTH / 32; ++w) { A += red[0][w]; B += red[1][w]; }
+            const size_t cta = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+            dpart[2 * cta] = A;
+            dpart[2 * cta + 1] = B;
+        }
+    }
+}
+
 template <class T, int NT>
 static cudaError_t configure_time() {
     const int sm = (int)TimeCfg<T, NT>::SMEM;
@@ -284,9 +458,30 @@ static cudaError_t configure_time() {
     return e;
 }
 
+template <class T, int NL>
+static cudaError_t configure_long() {
+    const int sm = (int)TimeCfg<T, NL>::SMEM;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_time_long_pass<T, NL, -1, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_time_long_pass<T, NL, -1, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_time_long_pass<T, NL, +1, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_time_long_out<T, NL, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
+        return e;
+    if constexpr (sizeof(T) == 4)
+        if ((e = cudaFuncSetAttribute(k_time_long_out<T, NL, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
+            return e;
+    return cudaSuccess;
+}
+
 template <class T>
 cudaError_t configure_time_all() {
     cudaError_t e;
+    if ((e = configure_long<T, 32>()) || (e = configure_long<T, 64>()) || (e = configure_long<T, 128>()) ||
+        (e = configure_long<T, 256>()))
+        return e;
 #define PINT_CFG(NT) if ((e = configure_time<T, NT>()) != cudaSuccess) return e;
     PINT_CFG(2) PINT_CFG(4) PINT_CFG(8) PINT_CFG(16) PINT_CFG(32) PINT_CFG(64) PINT_CFG(128) PINT_CFG(256)
     PINT_CFG(512) PINT_CFG(1024)
@@ -332,12 +527,100 @@ static void time_inv_ff_nt(int nspace, const float2* S, const float2* twt, const
         nspace, S, twt, nullptr, ginvf, nullptr, Uff, 1, ctl, dpart);
 }
 
+// ---- long time axes: host side ----
+template <class T, int NL>
+static void long_pass_nl(int pass, int ncol, int n1, int n2, int N, c_t<T>* z, const c_t<T>* twN, const Ctl* ctl,
+                         cudaStream_t st) {
+    using Cfg = TimeCfg<T, NL>;
+    dim3 grid((ncol + Cfg::CW - 1) / Cfg::CW, pass == 0 ? n2 : n1);
+    if (pass == 0) k_time_long_pass<T, NL, -1, true, 0><<<grid, Cfg::NTH, Cfg::SMEM, st>>>(ncol, n2, N, z, twN, ctl);
+    else if (pass == 1) k_time_long_pass<T, NL, -1, false, 1><<<grid, Cfg::NTH, Cfg::SMEM, st>>>(ncol, n2, N, z, twN, ctl);
+    else k_time_long_pass<T, NL, +1, true, 1><<<grid, Cfg::NTH, Cfg::SMEM, st>>>(ncol, n2, N, z, twN, ctl);
+}
+template <class T>
+static cudaError_t long_pass(int pass, int nl, int ncol, int n1, int n2, int N, c_t<T>* z, const c_t<T>* twN,
+                             const Ctl* ctl, cudaStream_t st) {
+    switch (nl) {
+        case 32: long_pass_nl<T, 32>(pass, ncol, n1, n2, N, z, twN, ctl, st); break;
+        case 64: long_pass_nl<T, 64>(pass, ncol, n1, n2, N, z, twN, ctl, st); break;
+        case 128: long_pass_nl<T, 128>(pass, ncol, n1, n2, N, z, twN, ctl, st); break;
+        case 256: long_pass_nl<T, 256>(pass, ncol, n1, n2, N, z, twN, ctl, st); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
+}
+static int grid1d(size_t n) {
+    size_t b = (n + 255) / 256;
+    return (int)(b > 4 * 152 * 8 ? 4 * 152 * 8 : (b < 1 ? 1 : b));
+}
+
+template <class T>
+static cudaError_t time_fwd_long(int nt, int nspace, T* s, c_t<T>* S, const c_t<T>* twt, const Ctl* ctl,
+                                 cudaStream_t st) {
+    int n1, n2;
+    long_split(nt, n1, n2);
+    const int ncol = nspace / 2;
+    c_t<T>* z = reinterpret_cast<c_t<T>*>(s);   // s is consumed here: the workspace is s itself
+    cudaError_t e;
+    if ((e = long_pass<T>(0, n1, ncol, n1, n2, nt, z, twt, ctl, st))) return e;
+    if ((e = long_pass<T>(1, n2, ncol, n1, n2, nt, z, twt, ctl, st))) return e;
+    k_time_long_unpack<T><<<grid1d((size_t)(nt / 2 + 1) * ncol), 256, 0, st>>>(nt, n1, n2, ncol, z, S, ctl);
+    return cudaGetLastError();
+}
+
+template <class T, int NL, int OUTK>
+static void long_out_nl(int ncol, int n1, int n2, int N, const c_t<T>* z, const c_t<T>* twN, const double* ginv,
+                        const float* ginvf, double* out, float2* outff, int acc, const Ctl* ctl, double* dpart,
+                        cudaStream_t st) {
+    using Cfg = TimeCfg<T, NL>;
+    dim3 grid((ncol + Cfg::CW - 1) / Cfg::CW, n2);
+    k_time_long_out<T, NL, OUTK><<<grid, Cfg::NTH, Cfg::SMEM, st>>>(ncol, n2, N, z, twN, ginv, ginvf, out, outff,
+                                                                   acc, ctl, dpart);
+}
+template <class T, int OUTK>
+static cudaError_t time_inv_long(int nt, int nspace, const c_t<T>* S, const c_t<T>* twt, void* work,
+                                 const double* ginv, const float* ginvf, double* out, float2* outff, int acc,
+                                 const Ctl* ctl, double* dpart, cudaStream_t st) {
+    if (!work) return cudaErrorInvalidValue;
+    int n1, n2;
+    long_split(nt, n1, n2);
+    const int ncol = nspace / 2;
+    c_t<T>* z = reinterpret_cast<c_t<T>*>(work);
+    k_time_long_pack<T><<<grid1d((size_t)nt * ncol), 256, 0, st>>>(nt, n1, n2, ncol, S, z, ctl);
+    cudaError_t e;
+    if ((e = long_pass<T>(2, n2, ncol, n1, n2, nt, z, twt, ctl, st))) return e;
+    switch (n1) {
+        case 32: long_out_nl<T, 32, OUTK>(ncol, n1, n2, nt, z, twt, ginv, ginvf, out, outff, acc, ctl, dpart, st); break;
+        case 64: long_out_nl<T, 64, OUTK>(ncol, n1, n2, nt, z, twt, ginv, ginvf, out, outff, acc, ctl, dpart, st); break;
+        case 128: long_out_nl<T, 128, OUTK>(ncol, n1, n2, nt, z, twt, ginv, ginvf, out, outff, acc, ctl, dpart, st); break;
+        case 256: long_out_nl<T, 256, OUTK>(ncol, n1, n2, nt, z, twt, ginv, ginvf, out, outff, acc, ctl, dpart, st); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// CTAs (dpart pairs) of the output pass of a long time axis.
+static int time_long_blocks(int nt, int nspace, int f32) {
+    int n1, n2;
+    long_split(nt, n1, n2);
+    int cw = 32;
+    switch (n1) {
+#define CW_(N) case N: cw = f32 ? TimeCfg<float, N>::CW : TimeCfg<double, N>::CW; break;
+        CW_(32) CW_(64) CW_(128) CW_(256)
+#undef CW_
+        default: break;
+    }
+    return (nspace / 2 + cw - 1) / cw * n2;
+}
+
 int time_inv_ff_blocks(int nt, int nspace, const Ctl* ctl) {
+    if (nt > 1024) return time_long_blocks(nt, nspace, 1);
     if (time_inv_ff_prefetch(nt, nspace, ctl)) return (nspace + 31) / 32;
     return time_inv_blocks(nt, nspace, 1);
 }
 
 int time_inv_blocks(int nt, int nspace, int f32) {
+    if (nt > 1024) return time_long_blocks(nt, nspace, f32);
     int cw = 32;
     switch (nt) {
 #define CW_(N) case N: cw = f32 ? TimeCfg<float, N>::CW : TimeCfg<double, N>::CW; break;
@@ -360,6 +643,7 @@ int time_inv_blocks(int nt, int nspace, int f32) {
 template <class T>
 cudaError_t launch_time_fwd(int nt, int nspace, const T* s, c_t<T>* S, const c_t<T>* twt, const Ctl* ctl,
                             cudaStream_t st) {
+    if (nt > 1024) return time_fwd_long<T>(nt, nspace, const_cast<T*>(s), S, twt, ctl, st);
 #define CALL(N) time_fwd_nt<T, N>(nspace, s, S, twt, ctl, st)
     PINT_NT_SWITCH(CALL)
 #undef CALL
@@ -367,7 +651,9 @@ cudaError_t launch_time_fwd(int nt, int nspace, const T* s, c_t<T>* S, const c_t
 }
 template <class T>
 cudaError_t launch_time_inv(int nt, int nspace, const c_t<T>* S, const c_t<T>* twt, const double* ginv, double* out,
-                            int accumulate, const Ctl* ctl, double* dpart, cudaStream_t st) {
+                            int accumulate, const Ctl* ctl, double* dpart, cudaStream_t st, void* work) {
+    if (nt > 1024)
+        return time_inv_long<T, 0>(nt, nspace, S, twt, work, ginv, nullptr, out, nullptr, accumulate, ctl, dpart, st);
 #define CALL(N) time_inv_nt<T, N>(nspace, S, twt, ginv, out, accumulate, ctl, dpart, st)
     PINT_NT_SWITCH(CALL)
 #undef CALL
@@ -375,7 +661,9 @@ cudaError_t launch_time_inv(int nt, int nspace, const c_t<T>* S, const c_t<T>* t
 }
 
 cudaError_t launch_time_inv_ff(int nt, int nspace, const float2* S, const float2* twt, const float* ginvf,
-                               float2* Uff, const Ctl* ctl, double* dpart, cudaStream_t st) {
+                               float2* Uff, const Ctl* ctl, double* dpart, cudaStream_t st, void* work) {
+    if (nt > 1024)
+        return time_inv_long<float, 1>(nt, nspace, S, twt, work, nullptr, ginvf, nullptr, Uff, 1, ctl, dpart, st);
 #define CALL(N) time_inv_ff_nt<N>(nspace, S, twt, ginvf, Uff, ctl, dpart, st)
     PINT_NT_SWITCH(CALL)
 #undef CALL
@@ -386,8 +674,8 @@ template cudaError_t launch_time_fwd<float>(int, int, const float*, float2*, con
 template cudaError_t launch_time_fwd<double>(int, int, const double*, double2*, const double2*, const Ctl*,
                                              cudaStream_t);
 template cudaError_t launch_time_inv<float>(int, int, const float2*, const float2*, const double*, double*, int,
-                                            const Ctl*, double*, cudaStream_t);
+                                            const Ctl*, double*, cudaStream_t, void*);
 template cudaError_t launch_time_inv<double>(int, int, const double2*, const double2*, const double*, double*, int,
-                                             const Ctl*, double*, cudaStream_t);
+                                             const Ctl*, double*, cudaStream_t, void*);
 
 }  // namespace pint

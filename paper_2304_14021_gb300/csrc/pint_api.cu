@@ -55,7 +55,9 @@ static int validate(const pint_problem* p) {
         return PINT_EINVAL;
     if (p->bc == PINT_BC_NEUMANN_VERTEX && (p->nx < 3 || (p->dim == 2 && p->ny < 3))) return PINT_EINVAL;
     if (p->nx < 2 || (p->dim == 2 && p->ny < 2)) return PINT_EINVAL;
-    if (!is_pow2(p->nt) || p->nt < 2 || p->nt > 1024) return PINT_EINVAL;
+    if (!is_pow2(p->nt) || p->nt < 2 || p->nt > 65536) return PINT_EINVAL;
+    // time axes beyond 1024 steps take the four-step FFT, which pairs neighbouring spatial points
+    if (p->nt > 1024 && ((long)p->nx * (p->dim == 2 ? p->ny : 1)) % 2 != 0) return PINT_EINVAL;
     if (p->n_windows < 1) return PINT_EINVAL;
     // theta-method: backward Euler (1) for every equation, Crank-Nicolson (1/2) for the linear ones
     const bool chq = p->equation == PINT_CAHN_HILLIARD || p->equation == PINT_CAHN_HILLIARD_EYRE;
@@ -482,7 +484,8 @@ static long long footprint_of(const pint_problem* p) {
     long long b = 0;
     b += sizeof(Ctl);
     b += z.partials * 2 * sizeof(double);
-    b += (z.nspace / 16 + 2) * 2 * sizeof(double);
+    b += std::max<size_t>(z.nspace / 16 + 2, (size_t)time_inv_blocks(p->nt, (int)z.nspace, f32_transforms(p))) * 2 *
+         sizeof(double);
     b += 2 * (size_t)p->nt * sizeof(double);
     b += z.nspace * sizeof(double) * (needs_b1(p) ? 2 : 1);
     b += z.dof * ts;                 // s
@@ -571,7 +574,7 @@ template <class T> struct Impl {
         if (e != cudaSuccess) return e;
         if ((e = spatial(h, S, tb)) != cudaSuccess) return e;
         prof_begin(h, PH_TINV);
-        e = launch_time_inv<T>(g.nt, g.nspace, S, tb.twt, h->ginv, U, 1, h->ctl, upd_part(h), h->st);
+        e = launch_time_inv<T>(g.nt, g.nspace, S, tb.twt, h->ginv, U, 1, h->ctl, upd_part(h), h->st, h->s);
         prof_end(h, PH_TINV, 1);
         if (e != cudaSuccess) return e;
         return cudaGetLastError();
@@ -586,7 +589,7 @@ template <class T> struct Impl {
         cudaError_t e = launch_time_fwd<T>(g.nt, g.nspace, s, S, tb.twt, h->ctl, h->st);
         if (e != cudaSuccess) return e;
         if ((e = spatial(h, S, tb)) != cudaSuccess) return e;
-        e = launch_time_inv<T>(g.nt, g.nspace, S, tb.twt, h->ginv, delta, 0, h->ctl, nullptr, h->st);
+        e = launch_time_inv<T>(g.nt, g.nspace, S, tb.twt, h->ginv, delta, 0, h->ctl, nullptr, h->st, h->s);
         if (e != cudaSuccess) return e;
         return cudaGetLastError();
     }
@@ -611,15 +614,15 @@ static cudaError_t zero_start(pint_handle* h, double* U, const double* u0w) {
         if ((e = Impl<float>::spatial(h, reinterpret_cast<float2*>(h->S), tb)) != cudaSuccess) return e;
         prof_begin(h, PH_TINV);
         if (h->p.precision == PINT_MIXED_FF)
-            e = launch_time_inv_ff(g.nt, g.nspace, reinterpret_cast<float2*>(h->S), tb.twt, h->ginvf, h->Uff_cur, h->ctl, upd_part(h), h->st);
+            e = launch_time_inv_ff(g.nt, g.nspace, reinterpret_cast<float2*>(h->S), tb.twt, h->ginvf, h->Uff_cur, h->ctl, upd_part(h), h->st, h->s);
         else
-            e = launch_time_inv<float>(g.nt, g.nspace, reinterpret_cast<float2*>(h->S), tb.twt, h->ginv, U, 1, h->ctl, upd_part(h), h->st);
+            e = launch_time_inv<float>(g.nt, g.nspace, reinterpret_cast<float2*>(h->S), tb.twt, h->ginv, U, 1, h->ctl, upd_part(h), h->st, h->s);
         prof_end(h, PH_TINV, 1);
     } else {
         const Tabs<double>& tb = tabs_of<double>(h);
         if ((e = Impl<double>::spatial(h, reinterpret_cast<double2*>(h->S), tb)) != cudaSuccess) return e;
         prof_begin(h, PH_TINV);
-        e = launch_time_inv<double>(g.nt, g.nspace, reinterpret_cast<double2*>(h->S), tb.twt, h->ginv, U, 1, h->ctl, upd_part(h), h->st);
+        e = launch_time_inv<double>(g.nt, g.nspace, reinterpret_cast<double2*>(h->S), tb.twt, h->ginv, U, 1, h->ctl, upd_part(h), h->st, h->s);
         prof_end(h, PH_TINV, 1);
     }
     if (e != cudaSuccess) return e;
@@ -647,7 +650,7 @@ static cudaError_t iteration_ff(pint_handle* h) {
     if (e != cudaSuccess) return e;
     if ((e = Impl<float>::spatial(h, S, tb)) != cudaSuccess) return e;
     prof_begin(h, PH_TINV);
-    e = launch_time_inv_ff(g.nt, g.nspace, S, tb.twt, h->ginvf, h->Uff_cur, h->ctl, upd_part(h), h->st);
+    e = launch_time_inv_ff(g.nt, g.nspace, S, tb.twt, h->ginvf, h->Uff_cur, h->ctl, upd_part(h), h->st, h->s);
     prof_end(h, PH_TINV, 1);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
@@ -873,7 +876,8 @@ int pint_create(const pint_problem* p, void* cuda_stream, pint_handle** out) {
     rc = PINT_OK;
     if (!rc) rc = dalloc((void**)&h->ctl, sizeof(Ctl));
     if (!rc) rc = dalloc((void**)&h->partials, z.partials * 2 * sizeof(double));
-    if (!rc) rc = dalloc((void**)&h->dpart, (z.nspace / 16 + 2) * 2 * sizeof(double));
+    const size_t ndp = std::max<size_t>(z.nspace / 16 + 2, (size_t)time_inv_blocks(p->nt, (int)z.nspace, f32_transforms(p)));
+    if (!rc) rc = dalloc((void**)&h->dpart, ndp * 2 * sizeof(double));
     if (!rc) rc = dalloc((void**)&h->gam, p->nt * sizeof(double));
     if (!rc) rc = dalloc((void**)&h->ginv, p->nt * sizeof(double));
     if (!rc) rc = dalloc((void**)&h->u0buf, z.nspace * sizeof(double));

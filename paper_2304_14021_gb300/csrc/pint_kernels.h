@@ -53,7 +53,7 @@ void launch_f64_to_ff(const double* in, float2* out, size_t n, cudaStream_t st);
 void launch_ff_to_f64(const float2* in, double* out, size_t n, cudaStream_t st);
 void launch_broadcast_ff(float2* U, const float2* u0, int nspace, int nt, cudaStream_t st);
 cudaError_t launch_time_inv_ff(int nt, int nspace, const float2* S, const float2* twt, const float* ginvf,
-                               float2* Uff, const Ctl* ctl, double* dpart, cudaStream_t st);
+                               float2* Uff, const Ctl* ctl, double* dpart, cudaStream_t st, void* work = nullptr);
 template <class TS>
 void launch_residual(const Geo& g, const double* U, const double* u0, const double* gam, double* r_out, TS* s_out,
                      double* partials, const Ctl* ctl, cudaStream_t st);
@@ -82,7 +82,7 @@ cudaError_t launch_time_fwd(int nt, int nspace, const T* s, c_t<T>* S, const c_t
 // dpart (may be NULL): per-CTA (sum delta^2, sum U^2) pairs, time_inv_blocks() of them.
 template <class T>
 cudaError_t launch_time_inv(int nt, int nspace, const c_t<T>* S, const c_t<T>* twt, const double* ginv, double* out,
-                            int accumulate, const Ctl* ctl, double* dpart, cudaStream_t st);
+                            int accumulate, const Ctl* ctl, double* dpart, cudaStream_t st, void* work = nullptr);
 int time_inv_blocks(int nt, int nspace, int f32);
 // CTAs of launch_time_inv_ff (with the same control block argument).
 int time_inv_ff_blocks(int nt, int nspace, const Ctl* ctl);

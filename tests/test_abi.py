@@ -48,7 +48,7 @@ def test_strerror(lib):
     assert "unknown" in pint.strerror(-99)
 
 
-BAD = [dict(dim=3), dict(nx=1), dict(nt=48), dict(nt=2048), dict(nt=1), dict(alpha=0.0), dict(alpha=1.0),
+BAD = [dict(dim=3), dict(nx=1), dict(nt=48), dict(nt=131072), dict(nt=2048, nx=63), dict(nt=1), dict(alpha=0.0), dict(alpha=1.0),
        dict(theta=0.7), dict(theta=0.5, equation="cahn_hilliard", eps=0.05), dict(tol=0.0), dict(max_iter=0), dict(max_iter=256), dict(precision=7),
        dict(T=-1.0), dict(equation=5), dict(bc=3), dict(n_windows=0), dict(nx=2000, bc="ss"),
        dict(equation="linear_ch", eps=0.0), dict(init_guess=3), dict(dim=2, ny=1), dict(tol_update=-1.0)]
@@ -102,3 +102,9 @@ def test_crank_nicolson_accepted_for_linear_equations(lib):
     kw = dict(equation="linear_ch", dim=2, nx=64, ny=64, bc="neumann", eps=0.05, beta=0.5, T=0.01, nt=32,
               alpha=1e-2, tol=1e-8, precision="mixed_ff")
     assert pint.footprint(**kw, theta=0.5) == pint.footprint(**kw, theta=1.0) + 64 * 64 * 8
+
+
+def test_long_time_axis_accepted_for_even_point_counts(lib):
+    kw = dict(equation="linear_ch", dim=1, nx=64, bc="neumann", eps=0.05, beta=0.5, T=1.0, alpha=1e-2, tol=1e-8)
+    for nt in (2048, 65536):
+        assert pint.footprint(**kw, nt=nt) > 0

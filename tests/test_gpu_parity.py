@@ -681,3 +681,35 @@ def test_eyre_adaptive_long_run_matches_oracle():
         st = s.solve(dev(u0), U)
     assert st["rc"] == 0 and st["windows"] == W, st
     assert O.rel_err(host(U), O.sequential(p, u0)[-nt:]) < 1e-7
+
+
+
+# --- long time axes (four-step time FFT, N_t > 1024) --------------------------
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_ff"])
+@pytest.mark.parametrize("nt", [2048, 8192, 65536])
+def test_long_time_axis_precond_matches_oracle(nt, precision):
+    kw = full(dict(equation="linear_ch", dim=1, nx=32, bc="neumann", eps=0.05, beta=0.5, nt=nt, T=nt * 1e-5,
+                   precision=precision))
+    p = oprob(kw)
+    r = synth.random_iterate(p.nt, p.nspace, 600)
+    ref = O.diagonalized_apply(p, p.alpha, r)
+    with pint.Solver(**kw) as s:
+        out = torch.zeros(p.nt, p.nspace, dtype=torch.float64, device="cuda")
+        s.precond_apply(dev(r), out)
+        err = O.rel_err(host(out), ref)
+    assert err < (1e-10 if precision == "fp64" else 3e-6 / p.alpha), err
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_ff"])
+def test_long_time_axis_solves_match_sequential(precision):
+    # 1-D linearized CH on 64 cells over 4096 steps, and 2-D 16^2 over 2048 steps
+    for kw in (dict(equation="linear_ch", dim=1, nx=64, bc="neumann", eps=0.05, beta=0.5, nt=4096, T=0.04),
+               dict(equation="biharmonic", dim=2, nx=16, ny=16, bc="neumann", nt=2048, T=2e-3)):
+        kw = full(dict(kw, precision=precision, init_guess=2, tol=1e-10 if precision == "fp64" else 1e-9,
+                       tol_update=1e-12))
+        p = oprob(kw)
+        u0 = synth.u0_uniform(p.nspace, -0.05, 0.05, 0)
+        U, st = run_solve(kw, u0)
+        assert st["rc"] == 0, st
+        assert O.rel_err(U, O.sequential(p, u0)) < (1e-9 if precision == "fp64" else 1e-8)
