@@ -220,6 +220,15 @@ int pint_profile_read(pint_handle* h, pint_profile* out, int reset);
  *    thread-block cluster holds the slice in shared memory) instead of three
  *    passes over the spectrum. */
 #define PINT_OPT_FUSED_SPATIAL 3
+/*  PINT_OPT_KRYLOV (default 0 = off): for the linear equations, wrap the
+ *    preconditioner in restarted flexible GMRES(value), 1 <= value <= 30:
+ *    right-preconditioned by P_alpha^{-1}, minimizing ||b - K U||_2, with K
+ *    applied in FP64 and the basis in FP64 ((2 value + 1) vectors of nt*nx*ny
+ *    doubles, allocated here).  The iterate is FP64 in every precision (a
+ *    PINT_MIXED_FF handle then runs as PINT_MIXED).  pint_stats.iters counts
+ *    preconditioner applications.  Errors: PINT_EINVAL (value out of range, or
+ *    Cahn-Hilliard), PINT_ENOMEM. */
+#define PINT_OPT_KRYLOV 4
 int pint_set_option(pint_handle* h, int option, long long value);
 
 /* pint_residual_static: the residual of pint_residual for callers that cannot

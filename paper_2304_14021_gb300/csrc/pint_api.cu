@@ -198,6 +198,13 @@ struct pint_handle {
     int nlev = 0;
     int adaptive = 0;
     std::vector<double> lamx_h, lamy_h;   // host copies of the Laplacian eigenvalues
+    // outer flexible GMRES (PINT_OPT_KRYLOV): restart length and FP64 work vectors
+    int krylov = 0;
+    double* kv = nullptr;      // (krylov + 1) basis vectors of nt * nspace
+    double* kz = nullptr;      // krylov preconditioned vectors P^{-1} v_j
+    double* kzero = nullptr;   // nspace zeros (the initial condition of K applied alone)
+    double* kpart = nullptr;   // dot-product partial sums
+    double* kcoef = nullptr;   // device copy of combination coefficients
 };
 
 namespace pint {
@@ -815,6 +822,11 @@ void pint_destroy(pint_handle* h) {
     ctl_slab_release(h->hctl);
     af(h->partials);
     af(h->dpart);
+    af(h->kv);
+    af(h->kz);
+    af(h->kzero);
+    af(h->kpart);
+    af(h->kcoef);
     if (h->nlev > 0) activate_level(h, 0);   // the base level owns gam/ginv/gamf/ginvf and tabs_ptrs
     for (int i = 1; i < h->nlev; ++i) {
         af(h->lev[i].block);
@@ -950,6 +962,29 @@ int pint_set_option(pint_handle* h, int option, long long value) {
             for (auto& sl : h->gslot)   // captured loops hold the old kernel choice
                 if (sl.exec) { cudaGraphExecDestroy(sl.exec); sl.exec = nullptr; }
             return PINT_OK;
+        case PINT_OPT_KRYLOV: {
+            if (value < 0 || value > kMaxKrylov) return PINT_EINVAL;
+            if (value > 0 && h->coef.ch) return PINT_EINVAL;   // linear equations only
+            const size_t dof = (size_t)h->p.nt * h->geo.nspace;
+            for (double* q : {h->kv, h->kz, h->kzero, h->kpart, h->kcoef})
+                if (q) cudaFreeAsync(q, h->st);
+            h->kv = h->kz = h->kzero = h->kpart = h->kcoef = nullptr;
+            h->krylov = 0;
+            if (value == 0) return PINT_OK;
+            auto al = [&](double** ptr, size_t count) {
+                if (cudaMallocAsync((void**)ptr, count * sizeof(double), h->st) != cudaSuccess) {
+                    cudaGetLastError();
+                    return false;
+                }
+                return true;
+            };
+            if (!al(&h->kv, (value + 1) * dof) || !al(&h->kz, value * dof) || !al(&h->kzero, h->geo.nspace) ||
+                !al(&h->kpart, (size_t)krylov_dot_blocks(dof) * (kMaxKrylov + 1)) || !al(&h->kcoef, kMaxKrylov + 1))
+                return PINT_ENOMEM;
+            if (cudaMemsetAsync(h->kzero, 0, h->geo.nspace * sizeof(double), h->st) != cudaSuccess) return PINT_ECUDA;
+            h->krylov = (int)value;
+            return PINT_OK;
+        }
         case PINT_OPT_ADAPTIVE_WINDOWS: {
             if (value != 0 && value != 1) return PINT_EINVAL;
             if (value) {
@@ -1007,12 +1042,127 @@ static int choose_level(pint_handle* h, int lmax, double jbar0) {
     return h->nlev - 1;
 }
 
+// Restarted flexible GMRES around P_alpha^{-1} (right preconditioning) for the
+// linear equations: minimizes ||b - K U||_2 over U0 + span{P^{-1} v_j}, with
+// K applied by the FP64 residual kernel (K z = -residual(z) at u0 = 0) and the
+// preconditioner in the handle's precision.  Classical Gram-Schmidt applied
+// twice; the preconditioned vectors are kept (flexible form), since complex64
+// inner solves are not an exactly fixed linear map.  Fills hctl's status,
+// iteration count (preconditioner applications), rho and history.
+static int krylov_dots(pint_handle* h, const double* w, const double* V, int nv, size_t n, double* out) {
+    const int nb = krylov_dot_blocks(n);
+    launch_multi_dot(w, V, n, nv, n, h->kpart, h->st);
+    std::vector<double> part((size_t)nb * nv);
+    PINT_CK(cudaMemcpyAsync(part.data(), h->kpart, part.size() * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    PINT_CK(cudaStreamSynchronize(h->st));
+    for (int i = 0; i < nv; ++i) {
+        double a = 0.0;
+        for (int b = 0; b < nb; ++b) a += part[(size_t)b * nv + i];
+        out[i] = a;
+    }
+    return PINT_OK;
+}
+static int krylov_axpy(pint_handle* h, double* w, const double* V, int nv, size_t n, const double* c) {
+    PINT_CK(cudaMemcpyAsync(h->kcoef, c, nv * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    launch_multi_axpy(w, V, n, nv, h->kcoef, n, h->st);
+    PINT_CK(cudaStreamSynchronize(h->st));   // c is host memory reused by the caller
+    return PINT_OK;
+}
+
+static int gmres_window(pint_handle* h, double* U, const double* u0w) {
+    const Geo& g = h->geo;
+    const pint_problem& p = h->p;
+    const size_t n = (size_t)g.nt * g.nspace;
+    const int m = h->krylov;
+    double* V = h->kv;
+    double* Z = h->kz;
+    int rc = read_ctl(h);
+    if (rc != PINT_OK) return rc;
+    const double bn = h->hctl->bnorm > 0.0 ? h->hctl->bnorm : 1.0;
+    Ctl& c = *h->hctl;
+    int iters = 0, nh = 0;
+    auto record = [&](double rho) {
+        if (nh < PINT_HIST_MAX) c.hist[nh] = rho;
+        ++nh;
+        c.rho = rho;
+    };
+    std::vector<double> H((size_t)(m + 1) * m, 0.0), gv(m + 1), cs(m), sn(m), y(m), hcol(m + 1), tmp(m + 1);
+    for (;;) {
+        // r0 = b - K U into v_0
+        launch_residual<double>(g, U, u0w, nullptr, V, nullptr, h->partials, nullptr, h->st);
+        double beta2;
+        if ((rc = krylov_dots(h, V, V, 1, n, &beta2)) != PINT_OK) return rc;
+        const double beta = sqrt(beta2);
+        record(beta / bn);
+        if (!(beta / bn == beta / bn)) { c.status = PINT_EDIVERGED; break; }
+        if (beta / bn <= p.tol) { c.status = PINT_OK; break; }
+        if (iters >= p.max_iter) { c.status = PINT_ENOCONV; break; }
+        launch_scale_copy(V, V, 1.0 / beta, n, h->st);
+        std::fill(gv.begin(), gv.end(), 0.0);
+        gv[0] = beta;
+        int j = 0;
+        bool done = false;
+        for (; j < m && iters < p.max_iter; ++j) {
+            double* vj = V + (size_t)j * n;
+            double* zj = Z + (size_t)j * n;
+            double* w = V + (size_t)(j + 1) * n;
+            cudaError_t e = f32_transforms(&h->p) ? Impl<float>::precond(h, 0.0, vj, zj) : Impl<double>::precond(h, 0.0, vj, zj);
+            if (e != cudaSuccess) return PINT_ECUDA;
+            ++iters;
+            launch_residual<double>(g, zj, h->kzero, nullptr, w, nullptr, h->partials, nullptr, h->st);
+            launch_scale_copy(w, w, -1.0, n, h->st);   // w = K z_j
+            std::fill(hcol.begin(), hcol.end(), 0.0);
+            for (int pass = 0; pass < 2; ++pass) {     // classical Gram-Schmidt, twice
+                if ((rc = krylov_dots(h, w, V, j + 1, n, tmp.data())) != PINT_OK) return rc;
+                for (int i = 0; i <= j; ++i) {
+                    hcol[i] += tmp[i];
+                    tmp[i] = -tmp[i];
+                }
+                if ((rc = krylov_axpy(h, w, V, j + 1, n, tmp.data())) != PINT_OK) return rc;
+            }
+            double hn2;
+            if ((rc = krylov_dots(h, w, w, 1, n, &hn2)) != PINT_OK) return rc;
+            hcol[j + 1] = sqrt(hn2);
+            if (hcol[j + 1] > 0.0) launch_scale_copy(w, w, 1.0 / hcol[j + 1], n, h->st);
+            // apply the previous Givens rotations to the new column, then a new one
+            for (int i = 0; i < j; ++i) {
+                const double a = cs[i] * hcol[i] + sn[i] * hcol[i + 1];
+                hcol[i + 1] = -sn[i] * hcol[i] + cs[i] * hcol[i + 1];
+                hcol[i] = a;
+            }
+            const double r = hypot(hcol[j], hcol[j + 1]);
+            cs[j] = r > 0.0 ? hcol[j] / r : 1.0;
+            sn[j] = r > 0.0 ? hcol[j + 1] / r : 0.0;
+            hcol[j] = r;
+            hcol[j + 1] = 0.0;
+            gv[j + 1] = -sn[j] * gv[j];
+            gv[j] = cs[j] * gv[j];
+            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i];
+            record(fabs(gv[j + 1]) / bn);
+            if (fabs(gv[j + 1]) / bn <= p.tol) { ++j; done = true; break; }
+        }
+        // y = R^{-1} g (back substitution), U += Z y
+        for (int i = j - 1; i >= 0; --i) {
+            double a = gv[i];
+            for (int k = i + 1; k < j; ++k) a -= H[(size_t)i * m + k] * y[k];
+            y[i] = a / H[(size_t)i * m + i];
+        }
+        if (j > 0 && (rc = krylov_axpy(h, U, Z, j, n, y.data())) != PINT_OK) return rc;
+        if (nh > 0) --nh;   // the true residual of the update is recorded at the top of the loop
+    }
+    c.iter = iters;   // preconditioner applications; hist holds one residual per application plus the first
+    c.dnorm = 0.0;
+    c.jbar = 0.0;
+    return PINT_OK;
+}
+
 int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* st) {
     if (!h || !u0_dev || !U_dev) return PINT_EINVAL;
     PINT_CK(cudaSetDevice(h->device));
     const pint_problem& p = h->p;
     const Geo& g = h->geo;
-    const bool ffm = p.precision == PINT_MIXED_FF;
+    const bool kry = h->krylov > 0;   // outer GMRES: FP64 iterate in U_dev (a float-float request acts as mixed)
+    const bool ffm = p.precision == PINT_MIXED_FF && !kry;
     const int ntmax = h->lev[0].nt;
     const size_t ns = (size_t)g.nspace, dof = (size_t)ntmax * ns;
     const bool adapt = h->adaptive && h->nlev > 1 && p.theta == 1.0;   // the policy's growth factor is BE's
@@ -1068,8 +1218,10 @@ int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* 
             }
             launch_begin_window(g, u0w, p.max_iter, p.tol, h->partials, h->ctl, h->st, p.tol_update, h->b1);
             prof_end(h, PH_SETUP, nl + 1);
-            cudaGraphExec_t gx = (h->use_graphs && !h->prof_on && !adapt) ? get_graph(h, Useg, u0w) : nullptr;
-            if (gx) {
+            cudaGraphExec_t gx = (h->use_graphs && !h->prof_on && !adapt && !kry) ? get_graph(h, Useg, u0w) : nullptr;
+            if (kry) {
+                if ((rc = gmres_window(h, Useg, u0w)) != PINT_OK) return rc;
+            } else if (gx) {
                 // one graph launch runs the iteration loop of this window to its stop
                 if (init == 2 && zero_start(h, Useg, u0w) != cudaSuccess) return PINT_ECUDA;
                 PINT_CK(cudaGraphLaunch(gx, h->st));

@@ -84,6 +84,17 @@ template <class T>
 cudaError_t launch_time_inv(int nt, int nspace, const c_t<T>* S, const c_t<T>* twt, const double* ginv, double* out,
                             int accumulate, const Ctl* ctl, double* dpart, cudaStream_t st, void* work = nullptr);
 int time_inv_blocks(int nt, int nspace, int f32);
+
+// Vector kernels of the outer flexible GMRES (k_krylov.cu).  At most
+// kMaxKrylov basis vectors per restart.
+constexpr int kMaxKrylov = 30;
+int krylov_dot_blocks(size_t n);
+// partials[b * nv + i]: CTA b's part of w . v_i for v_i = V + i * ld, i < nv (krylov_dot_blocks(n) CTAs)
+void launch_multi_dot(const double* w, const double* V, size_t ld, int nv, size_t n, double* partials,
+                      cudaStream_t st);
+// w += sum_i c[i] v_i (c on the device)
+void launch_multi_axpy(double* w, const double* V, size_t ld, int nv, const double* c, size_t n, cudaStream_t st);
+void launch_scale_copy(double* y, const double* x, double a, size_t n, cudaStream_t st);
 // CTAs of launch_time_inv_ff (with the same control block argument).
 int time_inv_ff_blocks(int nt, int nspace, const Ctl* ctl);
 // Step 2: per frequency k, S[k] <- (lambda_1k I + lambda_2k A)^{-1} S[k], in

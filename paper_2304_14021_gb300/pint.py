@@ -238,6 +238,12 @@ class Solver:
         if rc != PINT_OK:
             raise PintError(rc, "pint_set_option")
 
+    def set_krylov(self, restart: int) -> None:
+        """Outer flexible GMRES(restart) around the preconditioner (linear equations); 0 turns it off."""
+        rc = lib().pint_set_option(self._h, 4, int(restart))
+        if rc != PINT_OK:
+            raise PintError(rc, "pint_set_option")
+
     def set_adaptive_windows(self, on: bool = True) -> None:
         rc = lib().pint_set_option(self._h, 2, 1 if on else 0)
         if rc != PINT_OK:

@@ -713,3 +713,50 @@ def test_long_time_axis_solves_match_sequential(precision):
         U, st = run_solve(kw, u0)
         assert st["rc"] == 0, st
         assert O.rel_err(U, O.sequential(p, u0)) < (1e-9 if precision == "fp64" else 1e-8)
+
+
+# --- outer flexible GMRES around P_alpha^{-1} (SURVEY f-4, second part) ------
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_ff"])
+def test_gmres_matches_sequential_and_needs_fewer_applications(precision):
+    # alpha = 0.25: the stationary iteration contracts slowly; GMRES(10) reaches the
+    # same solution with fewer preconditioner applications
+    kw = full(dict(equation="linear_ch", dim=2, nx=64, ny=64, bc="neumann", eps=0.05, beta=0.5, nt=32,
+                   T=32 * 0.1 / 128, alpha=0.25, precision=precision, tol=1e-10, max_iter=200, init_guess=2))
+    p = oprob(kw)
+    u0 = synth.u0_uniform(p.nspace, -0.05, 0.05, 0)
+    ref = O.sequential(p, u0)
+    res = {}
+    for kry in (0, 10):
+        with pint.Solver(**kw) as s:
+            if kry:
+                s.set_krylov(kry)
+            U = torch.zeros(p.nt, p.nspace, dtype=torch.float64, device="cuda")
+            st = s.solve(dev(u0), U, check=False)
+        res[kry] = (host(U), st)
+    Ug, sg = res[10]
+    assert sg["rc"] == 0, sg
+    assert sg["rel_residual"] <= 1e-10
+    assert O.rel_err(Ug, ref) < 1e-9
+    if res[0][1]["rc"] == 0:
+        assert sg["iters"] < res[0][1]["iters"], (sg["iters"], res[0][1]["iters"])
+
+
+def test_gmres_windows_and_crank_nicolson():
+    kw = full(dict(equation="biharmonic", dim=1, nx=64, bc="ss", nt=32, n_windows=3, T=0.03, theta=0.5,
+                   alpha=0.1, precision="mixed", tol=1e-10, max_iter=100))
+    p = oprob(kw)
+    u0 = synth.u0_sine_modes(64)
+    with pint.Solver(**kw) as s:
+        s.set_krylov(8)
+        U = torch.zeros(p.nt, p.nspace, dtype=torch.float64, device="cuda")
+        st = s.solve(dev(u0), U)
+    assert st["rc"] == 0 and st["windows"] == 3
+    assert O.rel_err(host(U), O.sequential(p, u0)[-p.nt:]) < 1e-9
+
+
+def test_gmres_rejected_for_cahn_hilliard():
+    kw = full(dict(equation="cahn_hilliard", dim=1, nx=32, bc="neumann", eps=0.05, nt=8, T=8e-4))
+    with pint.Solver(**kw) as s:
+        with pytest.raises(pint.PintError):
+            s.set_krylov(5)
