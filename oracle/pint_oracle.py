@@ -548,6 +548,64 @@ def diagonalized_apply_separable(p: Problem, alpha: float, r: np.ndarray, jbar: 
     return x / gam[:, None]
 
 
+def jtilde_of(U: np.ndarray) -> np.ndarray:
+    """Space-varying averaged Jacobian of Eq. 4.12: J~(x) = mean over the time
+    levels of 3 u_n(x)^2 (one value per spatial point)."""
+    return 3.0 * np.mean(np.asarray(U) ** 2, axis=0)
+
+
+def dense_P_varying(p: Problem, alpha: float, jt: np.ndarray, nt: int | None = None) -> np.ndarray:
+    """P_alpha with the space-varying Jacobian (Eq. 4.12 / 4.24):
+    PinT-I  C_1 (x) I + I (x) (Delta_h (I - J~) + eps^2 Delta_h^2);
+    PinT-II C_1 (x) I + I (x) (eps^2 Delta_h^2 - Delta_h J~) + C_3 (x) Delta_h."""
+    nt = p.nt if nt is None else nt
+    L = laplacian(p).toarray()
+    ns = L.shape[0]
+    C1 = circulant_C1(nt, p.dt, alpha)
+    Jd = np.diag(jt)
+    if p.equation == CAHN_HILLIARD_EYRE:
+        return (np.kron(C1, np.eye(ns)) + np.kron(np.eye(nt), p.eps ** 2 * L @ L - L @ Jd)
+                + np.kron(circulant_C2(nt, 0.0, alpha), L))
+    return np.kron(C1, np.eye(ns)) + np.kron(np.eye(nt), L @ (np.eye(ns) - Jd) + p.eps ** 2 * L @ L)
+
+
+def diagonalized_apply_varying(p: Problem, alpha: float, r: np.ndarray, jt: np.ndarray) -> np.ndarray:
+    """Steps 1-3 of Eq. 4.14 (4.25 for PinT-II) with the space-varying J~: Step 2
+    is a dense solve per frequency of lambda_1k I + Delta_h (I - J~) + eps^2 Delta_h^2
+    (PinT-II: lambda_1k I - Delta_h J~ + lambda_3k Delta_h + eps^2 Delta_h^2)."""
+    nt = r.shape[0]
+    n = np.arange(nt)
+    gam = alpha ** (n / nt)
+    S1 = np.fft.fft(gam[:, None] * r, axis=0)
+    z = alpha ** (1.0 / nt) * np.exp(-2j * np.pi * n / nt)
+    l1 = (1.0 - z) / p.dt
+    L = laplacian(p).toarray()
+    ns = L.shape[0]
+    Jd = np.diag(jt)
+    S2 = np.empty_like(S1)
+    for k in range(nt):
+        if p.equation == CAHN_HILLIARD_EYRE:
+            M = l1[k] * np.eye(ns) - L @ Jd + z[k] * L + p.eps ** 2 * L @ L
+        else:
+            M = l1[k] * np.eye(ns) + L @ (np.eye(ns) - Jd) + p.eps ** 2 * L @ L
+        S2[k] = np.linalg.solve(M, S1[k])
+    x = np.fft.ifft(S2, axis=0).real
+    return x / gam[:, None]
+
+
+def pint_iteration_varying(p: Problem, u0: np.ndarray, U_init: np.ndarray, iters: int,
+                           alpha: float | None = None) -> list[np.ndarray]:
+    """The residual-form iteration with the space-varying J~ recomputed from
+    each iterate (paper-literal PinT-I / PinT-II).  Returns [U^1, ..., U^iters]."""
+    alpha = p.alpha if alpha is None else alpha
+    U = U_init.copy()
+    out = []
+    for _ in range(iters):
+        U = U + diagonalized_apply_varying(p, alpha, residual(p, u0, U), jtilde_of(U))
+        out.append(U)
+    return out
+
+
 def all_at_once_newton_eyre(p: Problem, u0: np.ndarray, tol: float = 1e-13,
                             max_newton: int = 60) -> np.ndarray:
     """Solve the alpha = 0 all-at-once system of Eyre's scheme (Eq. 4.21 with
