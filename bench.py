@@ -282,6 +282,8 @@ def main_gpu(args) -> None:
     s = pint.Solver(stream=stream, **kw)
     if wl["equation"] in ("cahn_hilliard", "cahn_hilliard_eyre"):
         s.set_adaptive_windows(True)
+        if args.varying_jacobian:
+            s.set_varying_jacobian(args.varying_jacobian)
     if args.no_graphs:
         s.set_graphs(False)
     nt, ns = s.nt, s.nspace
@@ -452,9 +454,10 @@ def main_gpu(args) -> None:
             "vs_baseline": None,
             "dtype": {"mixed_ff": "f32 (float-float iterate)", "mixed": "f32+f64", "fp64": "f64"}[args.precision],
             "data": "synthetic",
-            "config": {"workload": args.workload, "precision": args.precision, "alpha": args.alpha,
+            "config": {"workload": args.workload, "precision": args.precision, "alpha": wl.get("alpha", args.alpha),
                        "tol": args.tol, "init": "zero" if zero_start else "u0", "dof_per_gpu": dof,
-                       "iterations": stats["iters"],
+                       "iterations": stats["iters"], "segments": stats.get("segments"),
+                       "varying_jacobian": args.varying_jacobian or None,
                        "final_rel_residual": stats["rel_residual"], "l2": "flushed between steps",
                        "parallelism": f"replicas x{world}"},
             "e2e": ({"value": world * dof / e2e_s, "unit": "space-time DOF/s", "h2d_bytes_per_step": ns * 8,
@@ -636,6 +639,8 @@ def main() -> None:
     ap.add_argument("--serve-max-requests", type=int, default=300)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-budget", type=float, default=8.0)
+    ap.add_argument("--varying-jacobian", type=int, default=0,
+                    help="Cahn-Hilliard: inner GMRES length of the space-varying Jacobian in Step 2 (0 = scalar mean)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-worker", action="store_true")
     args = ap.parse_args()

@@ -229,6 +229,15 @@ int pint_profile_read(pint_handle* h, pint_profile* out, int reset);
  *    preconditioner applications.  Errors: PINT_EINVAL (value out of range, or
  *    Cahn-Hilliard), PINT_ENOMEM. */
 #define PINT_OPT_KRYLOV 4
+/*  PINT_OPT_VARYING_JACOBIAN (default 0 = off): for Cahn-Hilliard (PinT-I and
+ *    PinT-II), Step 2 uses the space-varying averaged Jacobian of Eq. 4.12,
+ *    J~(x) = mean over the time levels of 3 u(x)^2, instead of its scalar mean:
+ *    one cycle of flexible GMRES(value), 1 <= value <= 30, per outer iteration,
+ *    over all frequencies at once, right-preconditioned by the scalar-J divide
+ *    and stopped at a relative inner residual of 1e-4.  Work memory: (2 value + 3)
+ *    half spectra.  The iteration loop runs host-launched (no CUDA graph).
+ *    Errors: PINT_EINVAL (value out of range, or a linear equation), PINT_ENOMEM. */
+#define PINT_OPT_VARYING_JACOBIAN 5
 int pint_set_option(pint_handle* h, int option, long long value);
 
 /* pint_residual_static: the residual of pint_residual for callers that cannot

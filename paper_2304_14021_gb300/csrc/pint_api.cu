@@ -205,6 +205,14 @@ struct pint_handle {
     double* kzero = nullptr;   // nspace zeros (the initial condition of K applied alone)
     double* kpart = nullptr;   // dot-product partial sums
     double* kcoef = nullptr;   // device copy of combination coefficients
+    // space-varying Jacobian (PINT_OPT_VARYING_JACOBIAN): inner GMRES length and work vectors
+    int vary = 0;
+    void* jbuf = nullptr;      // rhs, solution, (vary + 1) basis and vary preconditioned spectra
+    void* jt = nullptr;        // J~(x), one per spatial point
+    double* jpart = nullptr;   // complex dot partial sums
+    double* jcoef = nullptr;   // complex coefficients
+    double vary_tol = 1e-4;    // relative residual of the inner solve
+    long long inner_iters = 0; // inner GMRES iterations (statistics)
 };
 
 namespace pint {
@@ -561,6 +569,110 @@ template <class T> struct Impl {
         }
         return cudaSuccess;
     }
+    // Step 2 with the space-varying Jacobian J~(x) (Eq. 4.12): one cycle of
+    // flexible GMRES on the block-diagonal system M_k x_k = S1_k over all
+    // frequencies at once, right-preconditioned by the scalar-J-bar divide,
+    // started from that divide's result.  Complex dot products in FP64,
+    // reduced on the host in a fixed order.
+    static int cdots(pint_handle* h, const c_t<T>* w, const c_t<T>* V, int nv, size_t n, std::complex<double>* out) {
+        const int nb = cdot_blocks(n);
+        launch_cmulti_dot<T>(w, V, n, nv, n, h->jpart, h->st);
+        std::vector<double> part((size_t)nb * nv * 2);
+        if (cudaMemcpyAsync(part.data(), h->jpart, part.size() * sizeof(double), cudaMemcpyDeviceToHost, h->st) ||
+            cudaStreamSynchronize(h->st))
+            return PINT_ECUDA;
+        for (int i = 0; i < nv; ++i) {
+            double a = 0.0, b = 0.0;
+            for (int q = 0; q < nb; ++q) { a += part[((size_t)q * nv + i) * 2]; b += part[((size_t)q * nv + i) * 2 + 1]; }
+            out[i] = std::complex<double>(a, b);
+        }
+        return PINT_OK;
+    }
+    static int caxpy(pint_handle* h, c_t<T>* w, const c_t<T>* V, int nv, size_t n, const std::complex<double>* c) {
+        if (cudaMemcpyAsync(h->jcoef, c, nv * 2 * sizeof(double), cudaMemcpyHostToDevice, h->st)) return PINT_ECUDA;
+        launch_cmulti_axpy<T>(w, V, n, nv, h->jcoef, n, h->st);
+        return cudaStreamSynchronize(h->st) ? PINT_ECUDA : PINT_OK;
+    }
+    static cudaError_t step2_varying(pint_handle* h, c_t<T>* S, const Tabs<T>& tb, const double* U, const float2* uff) {
+        cudaError_t e = cudaMemcpyAsync(h->hctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->st);
+        if (e != cudaSuccess || (e = cudaStreamSynchronize(h->st)) != cudaSuccess) return e;
+        if (h->hctl->status != ST_RUNNING) return cudaSuccess;    // the iteration has stopped
+        using C = c_t<T>;
+        const Geo& g = h->geo;
+        const int nk = g.nt / 2 + 1, m = h->vary;
+        const size_t n = (size_t)nk * g.nspace;
+        C* B = reinterpret_cast<C*>(h->jbuf);
+        C* X = B + n;
+        C* V = X + n;
+        C* Z = V + (size_t)(m + 1) * n;
+        T* jt = reinterpret_cast<T*>(h->jt);
+        const double c1 = g.expl ? 0.0 : 1.0;
+        launch_jtilde<T>(U, uff, g.nt, g.nspace, jt, h->st);
+        launch_caxpby<T>(B, 1.0, S, 0.0, nullptr, n, h->st);
+        launch_caxpby<T>(X, 1.0, S, 0.0, nullptr, n, h->st);
+        if ((e = spatial(h, X, tb)) != cudaSuccess) return e;           // x0 = P^{-1} S1
+        launch_apply_M<T>(g, nk, X, V, jt, tb, h->coef.c2, c1, h->st);
+        launch_caxpby<T>(V, -1.0, V, 1.0, B, n, h->st);                // r0 = S1 - M x0
+        std::complex<double> bb, rr;
+        if (cdots(h, B, B, 1, n, &bb) || cdots(h, V, V, 1, n, &rr)) return cudaErrorUnknown;
+        const double bn = sqrt(bb.real()), beta = sqrt(rr.real());
+        if (!(beta > h->vary_tol * bn)) {
+            launch_caxpby<T>(S, 1.0, X, 0.0, nullptr, n, h->st);
+            return cudaGetLastError();
+        }
+        launch_caxpby<T>(V, 1.0 / beta, V, 0.0, nullptr, n, h->st);
+        std::vector<std::complex<double>> H((size_t)(m + 1) * m), gv(m + 1), sn(m), hcol(m + 1), tmp(m + 1), y(m);
+        std::vector<double> cs(m);
+        gv[0] = beta;
+        int j = 0;
+        for (; j < m; ++j) {
+            C* vj = V + (size_t)j * n;
+            C* zj = Z + (size_t)j * n;
+            C* w = V + (size_t)(j + 1) * n;
+            launch_caxpby<T>(zj, 1.0, vj, 0.0, nullptr, n, h->st);
+            if ((e = spatial(h, zj, tb)) != cudaSuccess) return e;       // z_j = P^{-1} v_j
+            launch_apply_M<T>(g, nk, zj, w, jt, tb, h->coef.c2, c1, h->st);
+            ++h->inner_iters;
+            std::fill(hcol.begin(), hcol.end(), std::complex<double>(0.0));
+            for (int pass = 0; pass < 2; ++pass) {                          // classical Gram-Schmidt, twice
+                if (cdots(h, w, V, j + 1, n, tmp.data())) return cudaErrorUnknown;
+                for (int i = 0; i <= j; ++i) { hcol[i] += tmp[i]; tmp[i] = -tmp[i]; }
+                if (caxpy(h, w, V, j + 1, n, tmp.data())) return cudaErrorUnknown;
+            }
+            std::complex<double> ww;
+            if (cdots(h, w, w, 1, n, &ww)) return cudaErrorUnknown;
+            const double hn = sqrt(ww.real());
+            hcol[j + 1] = hn;
+            if (hn > 0.0) launch_caxpby<T>(w, 1.0 / hn, w, 0.0, nullptr, n, h->st);
+            for (int i = 0; i < j; ++i) {                                   // previous rotations
+                const std::complex<double> a = cs[i] * hcol[i] + sn[i] * hcol[i + 1];
+                hcol[i + 1] = -std::conj(sn[i]) * hcol[i] + cs[i] * hcol[i + 1];
+                hcol[i] = a;
+            }
+            const double na = std::abs(hcol[j]), r = hypot(na, std::abs(hcol[j + 1]));
+            if (r == 0.0) { cs[j] = 1.0; sn[j] = 0.0; }
+            else if (na == 0.0) { cs[j] = 0.0; sn[j] = std::conj(hcol[j + 1]) / r; }
+            else { cs[j] = na / r; sn[j] = (hcol[j] / na) * std::conj(hcol[j + 1]) / r; }
+            hcol[j] = cs[j] * hcol[j] + sn[j] * hcol[j + 1];
+            hcol[j + 1] = 0.0;
+            gv[j + 1] = -std::conj(sn[j]) * gv[j];
+            gv[j] = cs[j] * gv[j];
+            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i];
+            if (std::abs(gv[j + 1]) <= h->vary_tol * bn) { ++j; break; }
+        }
+        for (int i = j - 1; i >= 0; --i) {
+            std::complex<double> a = gv[i];
+            for (int k = i + 1; k < j; ++k) a -= H[(size_t)i * m + k] * y[k];
+            y[i] = a / H[(size_t)i * m + i];
+        }
+        if (j > 0 && caxpy(h, X, Z, j, n, y.data())) return cudaErrorUnknown;
+        launch_caxpby<T>(S, 1.0, X, 0.0, nullptr, n, h->st);
+        return cudaGetLastError();
+    }
+    static cudaError_t step2(pint_handle* h, c_t<T>* S, const Tabs<T>& tb, const double* U, const float2* uff) {
+        if (h->vary > 0 && h->coef.ch) return step2_varying(h, S, tb, U, uff);
+        return spatial(h, S, tb);
+    }
     static cudaError_t iteration(pint_handle* h, double* U, const double* u0w) {
         const Geo& g = h->geo;
         T* s = reinterpret_cast<T*>(h->s);
@@ -579,7 +691,7 @@ template <class T> struct Impl {
         cudaError_t e = launch_time_fwd<T>(g.nt, g.nspace, s, S, tb.twt, h->ctl, h->st);
         prof_end(h, PH_TFWD, 1);
         if (e != cudaSuccess) return e;
-        if ((e = spatial(h, S, tb)) != cudaSuccess) return e;
+        if ((e = step2(h, S, tb, U, nullptr)) != cudaSuccess) return e;
         prof_begin(h, PH_TINV);
         e = launch_time_inv<T>(g.nt, g.nspace, S, tb.twt, h->ginv, U, 1, h->ctl, upd_part(h), h->st, h->s);
         prof_end(h, PH_TINV, 1);
@@ -655,7 +767,7 @@ static cudaError_t iteration_ff(pint_handle* h) {
     cudaError_t e = launch_time_fwd<float>(g.nt, g.nspace, s, S, tb.twt, h->ctl, h->st);
     prof_end(h, PH_TFWD, 1);
     if (e != cudaSuccess) return e;
-    if ((e = Impl<float>::spatial(h, S, tb)) != cudaSuccess) return e;
+    if ((e = Impl<float>::step2(h, S, tb, nullptr, h->Uff_cur)) != cudaSuccess) return e;
     prof_begin(h, PH_TINV);
     e = launch_time_inv_ff(g.nt, g.nspace, S, tb.twt, h->ginvf, h->Uff_cur, h->ctl, upd_part(h), h->st, h->s);
     prof_end(h, PH_TINV, 1);
@@ -827,6 +939,10 @@ void pint_destroy(pint_handle* h) {
     af(h->kzero);
     af(h->kpart);
     af(h->kcoef);
+    af(h->jbuf);
+    af(h->jt);
+    af(h->jpart);
+    af(h->jcoef);
     if (h->nlev > 0) activate_level(h, 0);   // the base level owns gam/ginv/gamf/ginvf and tabs_ptrs
     for (int i = 1; i < h->nlev; ++i) {
         af(h->lev[i].block);
@@ -983,6 +1099,28 @@ int pint_set_option(pint_handle* h, int option, long long value) {
                 return PINT_ENOMEM;
             if (cudaMemsetAsync(h->kzero, 0, h->geo.nspace * sizeof(double), h->st) != cudaSuccess) return PINT_ECUDA;
             h->krylov = (int)value;
+            return PINT_OK;
+        }
+        case PINT_OPT_VARYING_JACOBIAN: {
+            if (value < 0 || value > kMaxKrylov) return PINT_EINVAL;
+            if (value > 0 && !h->coef.ch) return PINT_EINVAL;   // Cahn-Hilliard only
+            for (void* q : {h->jbuf, h->jt, (void*)h->jpart, (void*)h->jcoef})
+                if (q) cudaFreeAsync(q, h->st);
+            h->jbuf = h->jt = nullptr;
+            h->jpart = h->jcoef = nullptr;
+            h->vary = 0;
+            if (value == 0) return PINT_OK;
+            const size_t tsz = f32_transforms(&h->p) ? 4 : 8;
+            const size_t n = (size_t)(h->p.nt / 2 + 1) * h->geo.nspace;
+            auto al = [&](void** ptr, size_t bytes) {
+                if (cudaMallocAsync(ptr, bytes, h->st) != cudaSuccess) { cudaGetLastError(); return false; }
+                return true;
+            };
+            if (!al(&h->jbuf, (size_t)(2 * value + 3) * n * 2 * tsz) || !al(&h->jt, h->geo.nspace * tsz) ||
+                !al((void**)&h->jpart, (size_t)cdot_blocks(n) * (kMaxKrylov + 1) * 2 * sizeof(double)) ||
+                !al((void**)&h->jcoef, (kMaxKrylov + 1) * 2 * sizeof(double)))
+                return PINT_ENOMEM;
+            h->vary = (int)value;
             return PINT_OK;
         }
         case PINT_OPT_ADAPTIVE_WINDOWS: {
@@ -1218,7 +1356,7 @@ int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* 
             }
             launch_begin_window(g, u0w, p.max_iter, p.tol, h->partials, h->ctl, h->st, p.tol_update, h->b1);
             prof_end(h, PH_SETUP, nl + 1);
-            cudaGraphExec_t gx = (h->use_graphs && !h->prof_on && !adapt && !kry) ? get_graph(h, Useg, u0w) : nullptr;
+            cudaGraphExec_t gx = (h->use_graphs && !h->prof_on && !adapt && !kry && !h->vary) ? get_graph(h, Useg, u0w) : nullptr;
             if (kry) {
                 if ((rc = gmres_window(h, Useg, u0w)) != PINT_OK) return rc;
             } else if (gx) {

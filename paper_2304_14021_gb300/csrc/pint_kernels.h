@@ -95,6 +95,23 @@ void launch_multi_dot(const double* w, const double* V, size_t ld, int nv, size_
 // w += sum_i c[i] v_i (c on the device)
 void launch_multi_axpy(double* w, const double* V, size_t ld, int nv, const double* c, size_t n, cudaStream_t st);
 void launch_scale_copy(double* y, const double* x, double a, size_t n, cudaStream_t st);
+
+// Space-varying averaged Jacobian and the inner solve of Step 2 (k_jacobian.cu).
+int cdot_blocks(size_t n);
+template <class T>
+void launch_jtilde(const double* U, const float2* uff, int nt, int nspace, T* jt, cudaStream_t st);
+// W[k] = lambda_1k Y[k] + lambda_2k (c2 Lap^2 Y[k] + Lap((c1 - J~) Y[k])) + lambda_3k Lap Y[k], k < nk
+template <class T>
+void launch_apply_M(const Geo& g, int nk, const c_t<T>* Y, c_t<T>* W, const T* jt, const Tabs<T>& tb, double c2,
+                    double c1, cudaStream_t st);
+// partials[(b nv + i) 2 + {re, im}] of <v_i, w> (cdot_blocks(n) CTAs)
+template <class T>
+void launch_cmulti_dot(const c_t<T>* w, const c_t<T>* V, size_t ld, int nv, size_t n, double* partials,
+                       cudaStream_t st);
+template <class T>
+void launch_cmulti_axpy(c_t<T>* w, const c_t<T>* V, size_t ld, int nv, const double* c, size_t n, cudaStream_t st);
+template <class T>
+void launch_caxpby(c_t<T>* z, double a, const c_t<T>* x, double b, const c_t<T>* y, size_t n, cudaStream_t st);
 // CTAs of launch_time_inv_ff (with the same control block argument).
 int time_inv_ff_blocks(int nt, int nspace, const Ctl* ctl);
 // Step 2: per frequency k, S[k] <- (lambda_1k I + lambda_2k A)^{-1} S[k], in

@@ -238,6 +238,12 @@ class Solver:
         if rc != PINT_OK:
             raise PintError(rc, "pint_set_option")
 
+    def set_varying_jacobian(self, inner: int) -> None:
+        """Space-varying averaged Jacobian in Step 2 (Cahn-Hilliard), inner GMRES length; 0 turns it off."""
+        rc = lib().pint_set_option(self._h, 5, int(inner))
+        if rc != PINT_OK:
+            raise PintError(rc, "pint_set_option")
+
     def set_krylov(self, restart: int) -> None:
         """Outer flexible GMRES(restart) around the preconditioner (linear equations); 0 turns it off."""
         rc = lib().pint_set_option(self._h, 4, int(restart))

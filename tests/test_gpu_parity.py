@@ -760,3 +760,57 @@ def test_gmres_rejected_for_cahn_hilliard():
     with pint.Solver(**kw) as s:
         with pytest.raises(pint.PintError):
             s.set_krylov(5)
+
+
+# --- space-varying averaged Jacobian in Step 2 (SURVEY f-1) -------------------
+
+def _separated_1d(n, eps):
+    x = synth.grid_points_1d(n, "neumann")
+    return np.tanh((x - 0.5) / (np.sqrt(2) * eps)) + 0.05 * np.cos(3 * np.pi * x)
+
+
+@pytest.mark.parametrize("eq", ["cahn_hilliard", "cahn_hilliard_eyre"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed_ff"])
+def test_varying_jacobian_solve_matches_sequential_with_fewer_iterations(eq, precision):
+    n, nt, eps = 64, 16, 0.04
+    kw = full(dict(equation=eq, dim=1, nx=n, bc="neumann", eps=eps, nt=nt, T=nt * 5e-4, alpha=1e-2,
+                   precision=precision, tol=1e-10 if precision == "fp64" else 1e-9, max_iter=200))
+    p = oprob(kw)
+    u0 = _separated_1d(n, eps)
+    ref = O.sequential(p, u0)
+    out = {}
+    for inner in (0, 8):
+        with pint.Solver(**kw) as s:
+            if inner:
+                s.set_varying_jacobian(inner)
+            U = torch.zeros(nt, n, dtype=torch.float64, device="cuda")
+            st = s.solve(dev(u0), U, check=False)
+        out[inner] = (host(U), st)
+    Uv, sv = out[8]
+    assert sv["rc"] == 0, sv
+    assert O.rel_err(Uv, ref) < (1e-9 if precision == "fp64" else 1e-8)
+    if out[0][1]["rc"] == 0:
+        assert sv["iters"] < out[0][1]["iters"], (sv["iters"], out[0][1]["iters"])
+
+
+def test_varying_jacobian_2d_windows_mass_energy():
+    nt, W, n = 16, 3, 32
+    kw = full(dict(equation="cahn_hilliard", dim=2, nx=n, ny=n, bc="neumann", eps=0.05, nt=nt, n_windows=W,
+                   T=nt * W * 1e-4, alpha=1e-2, precision="mixed_ff", tol=1e-9, max_iter=200))
+    p = oprob(kw)
+    u0 = synth.u0_ch(p.nspace, 0)
+    with pint.Solver(**kw) as s:
+        s.set_varying_jacobian(6)
+        U = torch.zeros(nt, n * n, dtype=torch.float64, device="cuda")
+        st = s.solve(dev(u0), U)
+    assert st["rc"] == 0 and st["windows"] == W
+    Uh = host(U)
+    assert O.rel_err(Uh, O.sequential(p, u0)[-nt:]) < 1e-8
+    m0 = O.discrete_mass(p, u0)
+    assert max(abs(O.discrete_mass(p, u) - m0) for u in Uh) < 1e-12
+
+
+def test_varying_jacobian_rejected_for_linear_equations():
+    with pint.Solver(**full({})) as s:
+        with pytest.raises(pint.PintError):
+            s.set_varying_jacobian(4)
