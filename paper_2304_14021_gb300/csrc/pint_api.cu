@@ -211,6 +211,7 @@ struct pint_handle {
     void* jt = nullptr;        // J~(x), one per spatial point
     double* jpart = nullptr;   // complex dot partial sums
     double* jcoef = nullptr;   // complex coefficients
+    double* jcoef_h = nullptr; // pinned host staging of the coefficients
     double vary_tol = 1e-4;    // relative residual of the inner solve
     long long inner_iters = 0; // inner GMRES iterations (statistics)
 };
@@ -588,10 +589,16 @@ template <class T> struct Impl {
         }
         return PINT_OK;
     }
+    // w += sum_i c_i v_i.  The coefficients go through pinned staging, refilled
+    // only after the previous copy from it has run (the stream is idle here after
+    // the dot products, so the wait is short).
     static int caxpy(pint_handle* h, c_t<T>* w, const c_t<T>* V, int nv, size_t n, const std::complex<double>* c) {
-        if (cudaMemcpyAsync(h->jcoef, c, nv * 2 * sizeof(double), cudaMemcpyHostToDevice, h->st)) return PINT_ECUDA;
+        if (cudaStreamSynchronize(h->st) != cudaSuccess) return PINT_ECUDA;
+        memcpy(h->jcoef_h, c, nv * 2 * sizeof(double));
+        if (cudaMemcpyAsync(h->jcoef, h->jcoef_h, nv * 2 * sizeof(double), cudaMemcpyHostToDevice, h->st))
+            return PINT_ECUDA;
         launch_cmulti_axpy<T>(w, V, n, nv, h->jcoef, n, h->st);
-        return cudaStreamSynchronize(h->st) ? PINT_ECUDA : PINT_OK;
+        return PINT_OK;
     }
     static cudaError_t step2_varying(pint_handle* h, c_t<T>* S, const Tabs<T>& tb, const double* U, const float2* uff) {
         cudaError_t e = cudaMemcpyAsync(h->hctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->st);
@@ -633,17 +640,30 @@ template <class T> struct Impl {
             if ((e = spatial(h, zj, tb)) != cudaSuccess) return e;       // z_j = P^{-1} v_j
             launch_apply_M<T>(g, nk, zj, w, jt, tb, h->coef.c2, c1, h->st);
             ++h->inner_iters;
-            std::fill(hcol.begin(), hcol.end(), std::complex<double>(0.0));
-            for (int pass = 0; pass < 2; ++pass) {                          // classical Gram-Schmidt, twice
-                if (cdots(h, w, V, j + 1, n, tmp.data())) return cudaErrorUnknown;
-                for (int i = 0; i <= j; ++i) { hcol[i] += tmp[i]; tmp[i] = -tmp[i]; }
+            // classical Gram-Schmidt: <v_i, w> for i <= j and <w, w> in one pass (w is v_{j+1});
+            // ||w - sum h_i v_i||^2 = <w, w> - sum |h_i|^2, re-orthogonalized when that cancels
+            if (cdots(h, w, V, j + 2, n, tmp.data())) return cudaErrorUnknown;
+            double ww = tmp[j + 1].real(), hh = 0.0;
+            for (int i = 0; i <= j; ++i) { hcol[i] = tmp[i]; hh += std::norm(tmp[i]); }
+            double hn2 = ww - hh;
+            if (!(hn2 > 1e-4 * ww)) {
+                for (int i = 0; i <= j; ++i) tmp[i] = -hcol[i];
                 if (caxpy(h, w, V, j + 1, n, tmp.data())) return cudaErrorUnknown;
+                if (cdots(h, w, V, j + 2, n, tmp.data())) return cudaErrorUnknown;
+                hh = 0.0;
+                for (int i = 0; i <= j; ++i) { hcol[i] += tmp[i]; hh += std::norm(tmp[i]); }
+                hn2 = tmp[j + 1].real() - hh;
+                for (int i = 0; i <= j; ++i) tmp[i] = -tmp[i];
+            } else {
+                for (int i = 0; i <= j; ++i) tmp[i] = -hcol[i];
             }
-            std::complex<double> ww;
-            if (cdots(h, w, w, 1, n, &ww)) return cudaErrorUnknown;
-            const double hn = sqrt(ww.real());
+            const double hn = sqrt(fmax(hn2, 0.0));
             hcol[j + 1] = hn;
-            if (hn > 0.0) launch_caxpby<T>(w, 1.0 / hn, w, 0.0, nullptr, n, h->st);
+            // w = (w - sum h_i v_i) / hn in one pass (w itself is term j+1)
+            const double sc = hn > 0.0 ? 1.0 / hn : 1.0;
+            for (int i = 0; i <= j; ++i) tmp[i] *= sc;
+            tmp[j + 1] = sc - 1.0;
+            if (caxpy(h, w, V, j + 2, n, tmp.data())) return cudaErrorUnknown;
             for (int i = 0; i < j; ++i) {                                   // previous rotations
                 const std::complex<double> a = cs[i] * hcol[i] + sn[i] * hcol[i + 1];
                 hcol[i + 1] = -std::conj(sn[i]) * hcol[i] + cs[i] * hcol[i + 1];
@@ -943,6 +963,7 @@ void pint_destroy(pint_handle* h) {
     af(h->jt);
     af(h->jpart);
     af(h->jcoef);
+    if (h->jcoef_h) cudaFreeHost(h->jcoef_h);
     if (h->nlev > 0) activate_level(h, 0);   // the base level owns gam/ginv/gamf/ginvf and tabs_ptrs
     for (int i = 1; i < h->nlev; ++i) {
         af(h->lev[i].block);
@@ -1106,6 +1127,7 @@ int pint_set_option(pint_handle* h, int option, long long value) {
             if (value > 0 && !h->coef.ch) return PINT_EINVAL;   // Cahn-Hilliard only
             for (void* q : {h->jbuf, h->jt, (void*)h->jpart, (void*)h->jcoef})
                 if (q) cudaFreeAsync(q, h->st);
+            if (h->jcoef_h) { cudaStreamSynchronize(h->st); cudaFreeHost(h->jcoef_h); h->jcoef_h = nullptr; }
             h->jbuf = h->jt = nullptr;
             h->jpart = h->jcoef = nullptr;
             h->vary = 0;
@@ -1118,7 +1140,8 @@ int pint_set_option(pint_handle* h, int option, long long value) {
             };
             if (!al(&h->jbuf, (size_t)(2 * value + 3) * n * 2 * tsz) || !al(&h->jt, h->geo.nspace * tsz) ||
                 !al((void**)&h->jpart, (size_t)cdot_blocks(n) * (kMaxKrylov + 1) * 2 * sizeof(double)) ||
-                !al((void**)&h->jcoef, (kMaxKrylov + 1) * 2 * sizeof(double)))
+                !al((void**)&h->jcoef, (kMaxKrylov + 1) * 2 * sizeof(double)) ||
+                cudaMallocHost((void**)&h->jcoef_h, (kMaxKrylov + 2) * 2 * sizeof(double)) != cudaSuccess)
                 return PINT_ENOMEM;
             h->vary = (int)value;
             return PINT_OK;
