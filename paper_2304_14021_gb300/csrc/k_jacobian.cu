@@ -91,49 +91,56 @@ __global__ void __launch_bounds__(256) k_apply_M(Geo g, int nk, const c_t<T>* __
 }
 
 constexpr int kCDotThreads = 256;
+constexpr int kGroup = 4;   // vectors handled per launch (register accumulators)
 
-// partials[(b * nv + i) * 2 + {0,1}] = CTA b's part of <v_i, w> = sum conj(v_i) w (FP64).
-template <class T>
+// partials[(b * ldp + i0 + i) * 2 + {0,1}] = CTA b's part of <v_i, w> = sum conj(v_i) w (FP64), i < G.
+template <class T, int G>
 __global__ void __launch_bounds__(kCDotThreads) k_cmulti_dot(const c_t<T>* __restrict__ w, const c_t<T>* __restrict__ V,
-                                                            size_t ld, int nv, size_t n, double* __restrict__ partials) {
-    __shared__ double red[kCDotThreads / 32][kMaxKrylov + 1][2];
-    double re[kMaxKrylov + 1], im[kMaxKrylov + 1];
-    for (int i = 0; i < nv; ++i) re[i] = im[i] = 0.0;
+                                                            size_t ld, size_t n, int ldp, int i0,
+                                                            double* __restrict__ partials) {
+    __shared__ double red[kCDotThreads / 32][G][2];
+    double re[G], im[G];
+#pragma unroll
+    for (int i = 0; i < G; ++i) re[i] = im[i] = 0.0;
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
         const double wr = w[e].x, wi = w[e].y;
-        for (int i = 0; i < nv; ++i) {
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
             const c_t<T> v = V[i * ld + e];
             re[i] = fma((double)v.x, wr, fma((double)v.y, wi, re[i]));
             im[i] = fma((double)v.x, wi, fma(-(double)v.y, wr, im[i]));
         }
     }
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    for (int i = 0; i < nv; ++i) {
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
         const double a = warp_sum(re[i]), b = warp_sum(im[i]);
         if (lane == 0) { red[warp][i][0] = a; red[warp][i][1] = b; }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    if (threadIdx.x < G) {
+        const int i = threadIdx.x;
         double a = 0.0, b = 0.0;
         for (int q = 0; q < kCDotThreads / 32; ++q) { a += red[q][i][0]; b += red[q][i][1]; }
-        partials[((size_t)blockIdx.x * nv + i) * 2] = a;
-        partials[((size_t)blockIdx.x * nv + i) * 2 + 1] = b;
+        partials[((size_t)blockIdx.x * ldp + i0 + i) * 2] = a;
+        partials[((size_t)blockIdx.x * ldp + i0 + i) * 2 + 1] = b;
     }
 }
 
-// w += sum_i c_i v_i with complex coefficients c (FP64 pairs on the device).
-template <class T>
-__global__ void k_cmulti_axpy(c_t<T>* __restrict__ w, const c_t<T>* __restrict__ V, size_t ld, int nv,
+// w += sum_i c_i v_i, i < G, complex coefficients c (FP64 pairs on the device).
+template <class T, int G>
+__global__ void k_cmulti_axpy(c_t<T>* __restrict__ w, const c_t<T>* __restrict__ V, size_t ld,
                               const double* __restrict__ c, size_t n) {
-    __shared__ double cs[kMaxKrylov + 1][2];
-    for (int i = threadIdx.x; i < nv; i += blockDim.x) { cs[i][0] = c[2 * i]; cs[i][1] = c[2 * i + 1]; }
-    __syncthreads();
+    double cr[G], ci[G];
+#pragma unroll
+    for (int i = 0; i < G; ++i) { cr[i] = c[2 * i]; ci[i] = c[2 * i + 1]; }
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
         double xr = w[e].x, xi = w[e].y;
-        for (int i = 0; i < nv; ++i) {
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
             const c_t<T> v = V[i * ld + e];
-            xr += cs[i][0] * v.x - cs[i][1] * v.y;
-            xi += cs[i][0] * v.y + cs[i][1] * v.x;
+            xr += cr[i] * v.x - ci[i] * v.y;
+            xi += cr[i] * v.y + ci[i] * v.x;
         }
         w[e] = mkc((T)xr, (T)xi);
     }
@@ -171,14 +178,35 @@ void launch_apply_M(const Geo& g, int nk, const c_t<T>* Y, c_t<T>* W, const T* j
         k_apply_M<T, 1><<<grid, 256, 0, st>>>(g, nk, Y, W, jt, tb, (T)c2, (T)c1);
     }
 }
+// Groups of up to kGroup vectors per launch, register accumulators.  Note:
+// w may itself be one of the v_i (the axpy reads w[e] before writing it).
 template <class T>
 void launch_cmulti_dot(const c_t<T>* w, const c_t<T>* V, size_t ld, int nv, size_t n, double* partials,
                        cudaStream_t st) {
-    k_cmulti_dot<T><<<grid_n(n), kCDotThreads, 0, st>>>(w, V, ld, nv, n, partials);
+    const int nb = grid_n(n);
+    for (int i0 = 0; i0 < nv; i0 += kGroup) {
+        const c_t<T>* Vi = V + (size_t)i0 * ld;
+        switch (nv - i0 >= kGroup ? kGroup : nv - i0) {
+            case 1: k_cmulti_dot<T, 1><<<nb, kCDotThreads, 0, st>>>(w, Vi, ld, n, nv, i0, partials); break;
+            case 2: k_cmulti_dot<T, 2><<<nb, kCDotThreads, 0, st>>>(w, Vi, ld, n, nv, i0, partials); break;
+            case 3: k_cmulti_dot<T, 3><<<nb, kCDotThreads, 0, st>>>(w, Vi, ld, n, nv, i0, partials); break;
+            default: k_cmulti_dot<T, 4><<<nb, kCDotThreads, 0, st>>>(w, Vi, ld, n, nv, i0, partials); break;
+        }
+    }
 }
 template <class T>
 void launch_cmulti_axpy(c_t<T>* w, const c_t<T>* V, size_t ld, int nv, const double* c, size_t n, cudaStream_t st) {
-    k_cmulti_axpy<T><<<grid_n(n), 256, 0, st>>>(w, V, ld, nv, c, n);
+    const int nb = grid_n(n);
+    for (int i0 = 0; i0 < nv; i0 += kGroup) {
+        const c_t<T>* Vi = V + (size_t)i0 * ld;
+        const double* ci = c + 2 * i0;
+        switch (nv - i0 >= kGroup ? kGroup : nv - i0) {
+            case 1: k_cmulti_axpy<T, 1><<<nb, 256, 0, st>>>(w, Vi, ld, ci, n); break;
+            case 2: k_cmulti_axpy<T, 2><<<nb, 256, 0, st>>>(w, Vi, ld, ci, n); break;
+            case 3: k_cmulti_axpy<T, 3><<<nb, 256, 0, st>>>(w, Vi, ld, ci, n); break;
+            default: k_cmulti_axpy<T, 4><<<nb, 256, 0, st>>>(w, Vi, ld, ci, n); break;
+        }
+    }
 }
 template <class T>
 void launch_caxpby(c_t<T>* z, double a, const c_t<T>* x, double b, const c_t<T>* y, size_t n, cudaStream_t st) {

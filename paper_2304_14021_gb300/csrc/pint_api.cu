@@ -659,11 +659,9 @@ template <class T> struct Impl {
             }
             const double hn = sqrt(fmax(hn2, 0.0));
             hcol[j + 1] = hn;
-            // w = (w - sum h_i v_i) / hn in one pass (w itself is term j+1)
-            const double sc = hn > 0.0 ? 1.0 / hn : 1.0;
-            for (int i = 0; i <= j; ++i) tmp[i] *= sc;
-            tmp[j + 1] = sc - 1.0;
-            if (caxpy(h, w, V, j + 2, n, tmp.data())) return cudaErrorUnknown;
+            // w = (w - sum h_i v_i) / hn
+            if (caxpy(h, w, V, j + 1, n, tmp.data())) return cudaErrorUnknown;
+            if (hn > 0.0) launch_caxpby<T>(w, 1.0 / hn, w, 0.0, nullptr, n, h->st);
             for (int i = 0; i < j; ++i) {                                   // previous rotations
                 const std::complex<double> a = cs[i] * hcol[i] + sn[i] * hcol[i + 1];
                 hcol[i + 1] = -std::conj(sn[i]) * hcol[i] + cs[i] * hcol[i + 1];
