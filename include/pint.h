@@ -121,9 +121,10 @@ typedef struct {
     int    retries;           /* segments solved again with half the length (adaptive policy) */
     double update_norm;       /* ||delta||_2 / ||U||_2 of the last correction of the last window
                                  (computed when tol_update > 0, else 0) */
-    int    precision;         /* pint_precision the solve ran in: the requested one, or PINT_FP64
-                                 when 2^-24 * dt * max|spectrum of A| > 1 (0.1 for Cahn-Hilliard),
-                                 where FP32 inner solves cannot be refined by the outer iteration */
+    int    precision;         /* pint_precision the solve ran in.  With amp = 2^-24 dt max|spectrum of A|:
+                                 the requested one up to amp 1 (0.1 for Cahn-Hilliard); for the linear
+                                 equations PINT_MIXED (FP64 residual and iterate) up to amp 1e3; beyond,
+                                 PINT_FP64, where FP32 inner solves cannot be refined */
 } pint_stats;
 
 typedef struct pint_handle pint_handle;

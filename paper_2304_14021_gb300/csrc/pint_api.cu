@@ -901,15 +901,21 @@ double stiffness_of(const pint_problem* p) {
 
 // Precision a problem runs in.  The FP32 inner solves act as a preconditioner
 // refined by the outer iteration, which needs their error amplified by the
-// stiff operator, about 2^-24 * dt * max|spectrum|, to stay below one (0.1 for
-// Cahn-Hilliard, whose Jacobian moves between iterations); above that the FP32
-// rounding of the correction's high modes dominates the next residual
-// (observed: residual growth on 1-D grids of 1024-4096 points), and the whole
-// solve runs in FP64.
+// stiff operator, amp = 2^-24 dt max|spectrum|, to stay small:
+//  * linear equations: as requested up to amp 1; up to amp 1e3 with an FP64
+//    residual and iterate (PINT_MIXED: the float-float iterate's own rounding
+//    floor, 2^-49 dt max|spectrum|, would then stall the stop tests); beyond,
+//    FP64 throughout (the FP32 rounding of the correction's high modes then
+//    dominates the next residual: observed residual growth of 1e7 on a 1-D
+//    biharmonic of 4096 cells at amp 8e4);
+//  * Cahn-Hilliard, whose Jacobian moves between iterations: as requested up to
+//    amp 0.1, FP64 beyond (observed divergence at 0.87).
 int effective_precision(const pint_problem* p) {
     if (p->precision == PINT_FP64) return PINT_FP64;
-    const double limit = (p->equation == PINT_CAHN_HILLIARD || p->equation == PINT_CAHN_HILLIARD_EYRE) ? 0.1 : 1.0;
-    return stiffness_of(p) * 0x1p-24 > limit ? PINT_FP64 : p->precision;
+    const double amp = stiffness_of(p) * 0x1p-24;
+    if (p->equation == PINT_CAHN_HILLIARD || p->equation == PINT_CAHN_HILLIARD_EYRE) return amp > 0.1 ? PINT_FP64 : p->precision;
+    if (amp <= 1.0) return p->precision;
+    return amp <= 1e3 ? PINT_MIXED : PINT_FP64;
 }
 
 }  // namespace pint

@@ -95,6 +95,10 @@ def test_precision_policy_falls_back_to_fp64_when_too_stiff():
     mild = dict(equation="linear_ch", dim=2, nx=256, ny=256, bc="neumann", eps=0.05, beta=0.5, T=0.1, nt=128,
                 alpha=1e-2, tol=1e-8)
     assert pint.footprint(**mild, precision="mixed_ff") < pint.footprint(**mild, precision="fp64")
+    # 2-D biharmonic 512^2, dt = 0.01/256: amp about 10, a float-float request runs as PINT_MIXED
+    mid = dict(equation="biharmonic", dim=2, nx=512, ny=512, bc="neumann", T=0.01, nt=256, alpha=1e-2, tol=1e-8)
+    assert pint.footprint(**mid, precision="mixed_ff") == pint.footprint(**mid, precision="mixed")
+    assert pint.footprint(**mid, precision="mixed") < pint.footprint(**mid, precision="fp64")
 
 
 def test_crank_nicolson_accepted_for_linear_equations(lib):
