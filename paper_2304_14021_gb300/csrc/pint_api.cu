@@ -797,8 +797,6 @@ static cudaError_t iteration(pint_handle* h, double* U, const double* u0w) {
     return f32_transforms(&h->p) ? Impl<float>::iteration(h, U, u0w) : Impl<double>::iteration(h, U, u0w);
 }
 
-// Kernels per loop body (for launch accounting in graph mode).
-static int body_launches(const pint_handle* h) { return 5 + (h->geo.dim == 2 ? 2 : 0); }
 
 // The iteration loop of one window as a CUDA graph: a while-node whose body is
 // one iteration (residual, check, time FFT, spatial stages, inverse FFT); the
@@ -1266,7 +1264,6 @@ static int gmres_window(pint_handle* h, double* U, const double* u0w) {
         std::fill(gv.begin(), gv.end(), 0.0);
         gv[0] = beta;
         int j = 0;
-        bool done = false;
         for (; j < m && iters < p.max_iter; ++j) {
             double* vj = V + (size_t)j * n;
             double* zj = Z + (size_t)j * n;
@@ -1304,7 +1301,7 @@ static int gmres_window(pint_handle* h, double* U, const double* u0w) {
             gv[j] = cs[j] * gv[j];
             for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i];
             record(fabs(gv[j + 1]) / bn);
-            if (fabs(gv[j + 1]) / bn <= p.tol) { ++j; done = true; break; }
+            if (fabs(gv[j + 1]) / bn <= p.tol) { ++j; break; }
         }
         // y = R^{-1} g (back substitution), U += Z y
         for (int i = j - 1; i >= 0; --i) {
