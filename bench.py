@@ -53,6 +53,10 @@ WORKLOADS = {
     # u0 iid uniform[-0.05, 0.05]
     "linear_ch_1d_128_nt65536": dict(equation="linear_ch", dim=1, nx=128, ny=1, bc="neumann", eps=0.05, beta=0.5,
                                      T=0.3, nt=65536, n_windows=1, u0="uniform0.05"),
+    # 1-D biharmonic over about a million steps (the paper's dt = 1e-6 case): Neumann 64 cells (h = 1/64),
+    # N_t = 2^20 (three-pass time FFT), T = 1.048576, alpha = 1e-3, u0 iid uniform[-0.05, 0.05]
+    "biharmonic_1d_64_nt1048576": dict(equation="biharmonic", dim=1, nx=64, ny=1, bc="neumann", eps=1.0, beta=0.0,
+                                       T=(1 << 20) * 1e-6, nt=1 << 20, n_windows=1, u0="uniform0.05", alpha=1e-3),
     # 1-D biharmonic, simply supported, 64 vertices, N_t = 32, T = 0.01, u0 = sin(pi x) + 0.5 sin(3 pi x)
     "biharmonic_1d_64_nt32": dict(equation="biharmonic", dim=1, nx=64, ny=1, bc="ss", eps=1.0, beta=0.0,
                                   T=0.01, nt=32, n_windows=1, u0="sines"),

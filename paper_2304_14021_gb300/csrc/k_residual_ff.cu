@@ -318,6 +318,203 @@ __global__ void __launch_bounds__(256, 5) k_residual_ff(GeoFF g, const ff* __res
     }
 }
 
+// ---------------------------------------------------------------------------
+// Narrow 1-D grids (nx <= 256): a tile is TN consecutive time levels of the
+// whole row (TN a multiple of the warp count, about 1024 points), staged by
+// asynchronous copies one tile ahead (the rows of a tile are contiguous in
+// U).  Stage row j holds level n0-1+j (row 0 is level n0-1, u0 for the first
+// tile); only the nx points of a row are kept and the two ghost points on
+// each side are read through the boundary's even / odd extension (row_at).
+// The Laplacian of a row extends the same way (its ghost values equal the
+// extension of its interior values for all three boundary conditions), so
+// each warp works on its own run of rows with no block barrier between the
+// passes: Lap u of the row into a private buffer, then the residual.  The
+// arithmetic per point, and the order of its sums, is that of k_residual_ff.
+// Persistent CTAs (grid-stride over tiles); one pair of norm partials each.
+// ---------------------------------------------------------------------------
+constexpr int kNarrowNx = 256;
+constexpr int kNarrowThreads = 256;
+constexpr int kNarrowWarps = kNarrowThreads / 32;
+constexpr int kNarrowMaxTn = 64;
+static int narrow_tn(int nx) {
+    int tn = (1024 / nx + kNarrowWarps - 1) / kNarrowWarps * kNarrowWarps;
+    return tn < kNarrowWarps ? kNarrowWarps : (tn > kNarrowMaxTn ? kNarrowMaxTn : tn);
+}
+// Rows of private buffer per warp: Lap u of the row, of the previous row (theta = 1/2, Eyre), u^3 (Cahn-Hilliard).
+static int narrow_wrows(bool usep, bool ch) { return 1 + (usep ? 1 : 0) + (ch ? 1 : 0); }
+static size_t narrow_smem(int nx, int tn, int wrows) {
+    return sizeof(ff) * ((size_t)2 * (tn + 1) * nx + (size_t)kNarrowWarps * wrows * nx);
+}
+
+// Row value at index i in [-2, nx+1]: the stored value inside, the extension of the boundary condition outside.
+__device__ __forceinline__ ff row_at(const ff* __restrict__ a, int i, int nx, int bc) {
+    if (i >= 0 && i < nx) return a[i];
+    if (bc == 1) return a[i < 0 ? -1 - i : 2 * nx - 1 - i];
+    if (bc == 2) return a[i < 0 ? -i : 2 * (nx - 1) - i];
+    if (i == -1 || i == nx) return ffmk(0.f, 0.f);
+    const ff v = a[i < 0 ? -2 - i : 2 * nx - i];
+    return ffmk(-v.x, -v.y);
+}
+// Unscaled 1-D Laplacian sum a[x-1] + a[x+1] - 2 a[x] in the summation order of lap_ff<1, true, ACC>.
+template <bool ACC>
+__device__ __forceinline__ ff lap_row(const ff* __restrict__ a, int x, int nx, int bc) {
+    const ff l = row_at(a, x - 1, nx, bc), r = row_at(a, x + 1, nx, bc), c = a[x];
+    if constexpr (ACC) {
+        return ff_add(ff_add(l, r), ff_scale2(c, -2.f));
+    } else {
+        ff_acc acc(l);
+        acc.add(r);
+        acc.add(ff_scale2(c, -2.f));
+        return acc.get();
+    }
+}
+
+template <bool ACC, bool USEP>
+__global__ void __launch_bounds__(kNarrowThreads, 2)
+    k_residual_ff_narrow(GeoFF g, const ff* __restrict__ U, const ff* __restrict__ u0, const float* __restrict__ gamf,
+                         float* __restrict__ s_out, double* __restrict__ partials, const Ctl* __restrict__ ctl, int tn,
+                         int wrows) {
+    if (ctl && ctl->status != ST_RUNNING) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nx = g.nx, bc = g.bc, rows = tn + 1;
+    ff* stg = reinterpret_cast<ff*>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    ff* wbuf = stg + (size_t)2 * rows * nx + (size_t)warp * wrows * nx;
+    ff* Lc = wbuf;                         // Lap u of the current row
+    ff* Lp = USEP ? wbuf + nx : nullptr;   // Lap u of the previous row
+    const bool ch = g.cN.x != 0.f;
+    ff* Wr = ch ? wbuf + (size_t)(USEP ? 2 : 1) * nx : nullptr;   // u^3 of the current row
+    const bool lin1 = g.c1.x != 0.f;
+    const bool expl = g.expl != 0;
+    const float sdt = g.inv_dt.x;
+    __shared__ double red[2][kNarrowWarps];
+    float acc_r2 = 0.f, acc_u2 = 0.f;
+    const int ntiles = (g.nt + tn - 1) / tn;
+    const int rpw = tn / kNarrowWarps;     // rows per warp
+    auto stage = [&](int t, ff* dst) {
+        const int n0 = t * tn;
+        const int cnt = min(tn, g.nt - n0) * nx;
+        const ff* r0 = n0 == 0 ? u0 : U + (size_t)(n0 - 1) * g.nspace;
+        for (int x = tid; x < nx; x += kNarrowThreads) cp_async8(&dst[x], r0 + x);
+        const ff* src = U + (size_t)n0 * g.nspace;
+        for (int e = tid; e < cnt; e += kNarrowThreads) cp_async8(&dst[nx + e], src + e);
+        cp_async_commit();
+    };
+    if (blockIdx.x < ntiles) stage(blockIdx.x, stg);
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const ff* cur = stg + (size_t)(it & 1) * rows * nx;
+        if (t + (int)gridDim.x < ntiles) {
+            stage(t + gridDim.x, stg + (size_t)((it + 1) & 1) * rows * nx);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncthreads();                   // tile t is in shared memory
+        const int n0 = t * tn;
+        const int nlev = min(tn, g.nt - n0);
+        const int jb = 1 + warp * rpw, je = min(jb + rpw, nlev + 1);
+        if (USEP && jb < je) {
+            const ff* uq = cur + (size_t)(jb - 1) * nx;
+            for (int x = lane; x < nx; x += 32) Lp[x] = lap_row<ACC>(uq, x, nx, bc);
+        }
+        for (int j = jb; j < je; ++j) {
+            const ff* uj = cur + (size_t)j * nx;
+            const ff* uq = uj - nx;
+            for (int x = lane; x < nx; x += 32) {
+                Lc[x] = lap_row<ACC>(uj, x, nx, bc);
+                if (ch) Wr[x] = ff_cube(uj[x]);
+            }
+            __syncwarp();
+            const int n = n0 - 1 + j;
+            const float gm = gamf[n] * sdt;
+            float* srow = s_out + (size_t)n * g.nspace;
+            for (int x = lane; x < nx; x += 32) {
+                const ff u = uj[x], up = uq[x], L = Lc[x];
+                const ff lapL = lap_row<ACC>(Lc, x, nx, bc);
+                ff r;
+                if constexpr (USEP) {
+                    ff A = ff_mul(lapL, g.c2);
+                    if (lin1 && !expl) A = ff_add(A, ff_mul(L, g.c1));
+                    if (ch) A = ff_add(A, ff_mul(lap_row<ACC>(Wr, x, nx, bc), g.cN));
+                    ff B;
+                    if (expl) {
+                        B = ff_mul(Lp[x], g.c1);
+                    } else {
+                        B = ff_mul(lap_row<ACC>(Lp, x, nx, bc), g.c2);
+                        if (lin1) B = ff_add(B, ff_mul(Lp[x], g.c1));
+                    }
+                    if constexpr (!ACC) {
+                        ff_acc acc(up);
+                        acc.add(ff_neg(u));
+                        acc.add(ff_neg(A));
+                        acc.add(ff_neg(B));
+                        r = acc.get();
+                    } else {
+                        r = ff_sub(ff_sub(ff_sub(up, u), A), B);
+                    }
+                } else if constexpr (!ACC) {
+                    ff_acc acc(up);
+                    acc.add(ff_neg(u));
+                    acc.add(ff_neg(ff_mul(lapL, g.c2)));
+                    if (lin1) acc.add(ff_neg(ff_mul(L, g.c1)));
+                    if (ch) acc.add(ff_neg(ff_mul(lap_row<ACC>(Wr, x, nx, bc), g.cN)));
+                    r = acc.get();
+                } else {
+                    ff A = ff_mul(lapL, g.c2);
+                    if (lin1) A = ff_add(A, ff_mul(L, g.c1));
+                    if (ch) A = ff_add(A, ff_mul(lap_row<ACC>(Wr, x, nx, bc), g.cN));
+                    r = ff_sub(ff_sub(up, u), A);
+                }
+                srow[x] = fmaf(gm, r.x, gm * r.y);
+                acc_r2 = fmaf(r.x, r.x, acc_r2);
+                acc_u2 = fmaf(u.x, u.x, acc_u2);
+            }
+            __syncwarp();                  // Lc (and Wr) are rewritten for the next row
+            if constexpr (USEP) {
+                ff* tmp = Lp;
+                Lp = Lc;
+                Lc = tmp;
+            }
+        }
+        __syncthreads();                   // the stage of tile t is refilled two tiles later
+    }
+    const double idt = (double)g.inv_dt.x + (double)g.inv_dt.y;
+    double a2 = warp_sum((double)acc_r2) * (idt * idt), b2 = warp_sum((double)acc_u2);
+    if (lane == 0) { red[0][warp] = a2; red[1][warp] = b2; }
+    __syncthreads();
+    if (tid == 0) {
+        double A = 0.0, B = 0.0;
+        for (int w = 0; w < kNarrowWarps; ++w) { A += red[0][w]; B += red[1][w]; }
+        partials[2 * blockIdx.x] = A;
+        partials[2 * blockIdx.x + 1] = B;
+    }
+}
+
+// Persistent grid of the narrow kernel: resident CTAs per SM at its shared memory use (at most 4).
+static int narrow_grid(const Geo& g, int tn) {
+    const size_t sm = narrow_smem(g.nx, tn, narrow_wrows(true, true));
+    int per = (int)((220 * 1024) / (sm + 1024));
+    per = per < 1 ? 1 : (per > 4 ? 4 : per);
+    const long tiles = (g.nt + tn - 1) / tn;
+    const long want = 152L * per;
+    return (int)(tiles < want ? tiles : want);
+}
+
+cudaError_t configure_residual_ff() {
+    const int sm = (int)narrow_smem(kNarrowNx, narrow_tn(kNarrowNx), narrow_wrows(true, true));
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_residual_ff_narrow<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_residual_ff_narrow<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_residual_ff_narrow<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
+        return e;
+    return cudaFuncSetAttribute(k_residual_ff_narrow<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+}
+
+static bool narrow_1d(const Geo& g) { return g.dim == 1 && g.nx <= kNarrowNx; }
+
 __global__ void k_f64_to_ff(const double* __restrict__ in, ff* __restrict__ out, size_t n) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         out[i] = ff_from_double(in[i]);
@@ -355,6 +552,12 @@ static int grid_for(size_t n) {
 }
 
 int residual_ff_grid(const Geo& g, int& gx, int& gy, int& gz, int& chunk) {
+    if (narrow_1d(g)) {
+        chunk = narrow_tn(g.nx);
+        gx = narrow_grid(g, chunk);
+        gy = gz = 1;
+        return gx;
+    }
     const int TX = g.dim == 2 ? ResTileFF<2>::TX : ResTileFF<1>::TX, TY = g.dim == 2 ? ResTileFF<2>::TY : 1;
     gx = (g.nx + TX - 1) / TX;
     gy = g.dim == 2 ? (g.ny + TY - 1) / TY : 1;
@@ -377,6 +580,16 @@ void launch_residual_ff(const GeoFF& g, const Geo& g64, const ff* U, const ff* u
     const bool sq = g64.dim == 1 || g64.ihx2 == g64.ihy2;
     const bool acc = g.accurate != 0;
     const bool usep = g.half || g.expl;
+    if (narrow_1d(g64)) {
+        const int wrows = narrow_wrows(usep, g.cN.x != 0.f);
+        const size_t sm = narrow_smem(g64.nx, chunk, wrows);
+#define PINT_RFN(A, P) \
+    k_residual_ff_narrow<A, P><<<gx, kNarrowThreads, sm, st>>>(g, U, u0, gamf, s, partials, ctl, chunk, wrows)
+        if (acc) { if (usep) PINT_RFN(true, true); else PINT_RFN(true, false); }
+        else { if (usep) PINT_RFN(false, true); else PINT_RFN(false, false); }
+#undef PINT_RFN
+        return;
+    }
 #define PINT_RFF(D, S, A)                                                                                      \
     do {                                                                                                       \
         if (usep) k_residual_ff<D, S, A, true><<<grid, 256, 0, st>>>(g, U, u0, gamf, s, partials, ctl, chunk);  \

@@ -268,30 +268,54 @@ __global__ void __launch_bounds__(TimeTmaCfg<NT>::NTH)
 }
 
 // ---------------------------------------------------------------------------
-// Long time axes (1024 < N_t <= 65536): four-step FFT with N_t = N1 N2.  The
-// signal of the spatial point pair (2j, 2j+1) is the complex column
+// Long time axes (1024 < N_t <= 2^20): multi-pass (four-step) FFT with
+// N_t = f_0 f_1 ... f_{S-1}, S = 2 or 3 factors of 32..256.  The signal of the
+// spatial point pair (2j, 2j+1) is the complex column
 // z_j[n] = s[n][2j] + i s[n][2j+1] (the float2 / double2 view of a row).
-// With n = n1 N2 + n2 and k = k1 + N1 k2,
-//   Z_k = sum_n2 e^{-2 pi i n2 k2/N2} [ e^{-2 pi i n2 k1/N} sum_n1 z_{n1 N2+n2} e^{-2 pi i n1 k1/N1} ].
-// Pass A transforms over n1 (rows n1 N2 + n2) and applies e^{-2 pi i n2 k1/N};
-// pass B transforms over n2 (rows k1 N2 + n2) and leaves Z_{k1+N1 k2} at row
-// k1 N2 + k2.  Both work in place in a complex workspace of N_t x nspace/2;
-// unpack forms the half spectrum of the real signals (pairs k, N-k) in
-// natural order.  The inverse mirrors it (pack, pass B', pass A' + update).
+// Digits: n = sum_s n_s istr_s with istr_s = prod_{j>s} f_j (n_0 most
+// significant), k = sum_s k_s P_s with P_s = prod_{j<s} f_j (k_0 least
+// significant).  In n k mod N only the products n_j k_i with i <= j survive, so
+//   forward pass s transforms over n_s (stride istr_s) into k_s and multiplies
+//   by e^{-2 pi i k_s P_s (sum_{j>s} n_j istr_j) / N};
+// the storage slot of digit s holds n_s and then k_s, so after the last pass
+// Z_k sits in row sum_s k_s istr_s (long_pos).  The inverse runs the passes
+// from s = S-1 down to 0 with the opposite sign; the twiddle that pass s-1
+// needs, e^{+2 pi i k_{s-1} P_{s-1} (sum_{j>=s} n_j istr_j) / N}, is applied at
+// the end of pass s, and pass 0 writes x_n in natural order.  All passes work
+// in place in a complex workspace of N_t x nspace/2; unpack forms the half
+// spectrum of the real signals (pairs k, N-k) in natural order and pack
+// rebuilds the full one.
 // ---------------------------------------------------------------------------
-static void long_split(int nt, int& n1, int& n2) {
+struct LongPlan {
+    int S;
+    int f[3], istr[3], P[3];
+};
+static LongPlan long_plan(int nt) {
     int l = 0;
     while ((1 << l) < nt) ++l;
-    n2 = 1 << ((l + 1) / 2);
-    n1 = nt / n2;
+    LongPlan pl{};
+    pl.S = l > 16 ? 3 : 2;
+    const int base = l / pl.S, rem = l % pl.S;
+    // ascending factors: f_0, the output pass of the inverse, is the smallest
+    for (int i = 0; i < pl.S; ++i) pl.f[i] = 1 << (base + (i >= pl.S - rem ? 1 : 0));
+    for (int i = 0; i < pl.S; ++i) {
+        pl.istr[i] = 1;
+        for (int j = i + 1; j < pl.S; ++j) pl.istr[i] *= pl.f[j];
+        pl.P[i] = 1;
+        for (int j = 0; j < i; ++j) pl.P[i] *= pl.f[j];
+    }
+    return pl;
 }
 
-// One pass: CTA = (o, column block).  MAP 0: element m sits in row m*N2 + o;
-// MAP 1: row o*N2 + m.  TW: multiply element m by e^{-/+ 2 pi i o m / N}
-// after the transform (sign of DIR).
-template <class T, int NL, int DIR, bool TW, int MAP>
+// One pass over digit s: CTA = (o, column block), o in [0, N/NL); element m of
+// the transform sits in row (o / istr) NL istr + m istr + o % istr.
+// DIR < 0 (forward), TW: multiply element m (= k_s) by
+//   e^{-2 pi i (o % istr) m / (NL istr)}.
+// DIR > 0 (inverse), TW: multiply element m (= n_s) by
+//   e^{+2 pi i k_{s-1} (m istr + o % istr) / (fprev NL istr)},  k_{s-1} = (o / istr) % fprev.
+template <class T, int NL, int DIR, bool TW>
 __global__ void __launch_bounds__(TimeCfg<T, NL>::NTH)
-    k_time_long_pass(int ncol, int n2, int N, c_t<T>* __restrict__ z, const c_t<T>* __restrict__ twN,
+    k_time_long_pass(int ncol, int istr, int fprev, int N, c_t<T>* __restrict__ z, const c_t<T>* __restrict__ twN,
                      const Ctl* __restrict__ ctl) {
     using C = c_t<T>;
     constexpr int CW = TimeCfg<T, NL>::CW, NTH = TimeCfg<T, NL>::NTH;
@@ -303,10 +327,12 @@ __global__ void __launch_bounds__(TimeCfg<T, NL>::NTH)
     const int o = blockIdx.y;
     const int j0 = blockIdx.x * CW;
     const int step = N / NL;
+    const int ohi = o / istr, olo = o % istr;
+    const size_t base = (size_t)ohi * NL * istr + olo;
     for (int i = tid; i < NL; i += NTH) tw[i] = twN[(size_t)i * step];
     for (int e = tid; e < NL * CW; e += NTH) {
         const int c = e % CW, m = e / CW;
-        const size_t row = MAP == 0 ? (size_t)m * n2 + o : (size_t)o * n2 + m;
+        const size_t row = base + (size_t)m * istr;
         buf[e] = j0 + c < ncol ? z[row * ncol + j0 + c] : mkc(T(0), T(0));
     }
     __syncthreads();
@@ -316,21 +342,28 @@ __global__ void __launch_bounds__(TimeCfg<T, NL>::NTH)
         if (j0 + c >= ncol) continue;
         C v = buf[e];
         if (TW) {
-            C w = twN[((size_t)o * m) % N];
+            size_t idx;
+            if (DIR < 0) idx = ((size_t)olo * m * (size_t)(N / (NL * istr))) % (size_t)N;
+            else idx = ((size_t)(ohi % fprev) * ((size_t)m * istr + olo) * (size_t)(N / (fprev * NL * istr))) % (size_t)N;
+            C w = twN[idx];
             if (DIR > 0) w = conjc(w);
             v = cmul(v, w);
         }
-        const size_t row = MAP == 0 ? (size_t)m * n2 + o : (size_t)o * n2 + m;
+        const size_t row = base + (size_t)m * istr;
         z[row * ncol + j0 + c] = v;
     }
 }
 
-// Row of Z_k in the workspace after pass B.
-__device__ __forceinline__ size_t long_pos(int k, int n1, int n2) { return (size_t)(k % n1) * n2 + k / n1; }
+// Row of Z_k in the workspace after the last forward pass.
+__device__ __forceinline__ size_t long_pos(int k, const LongPlan& pl) {
+    size_t r = 0;
+    for (int i = 0; i < pl.S; ++i) r += (size_t)((k / pl.P[i]) % pl.f[i]) * pl.istr[i];
+    return r;
+}
 
 // S[k][2j], S[k][2j+1] (k = 0..N/2) from Z_k and Z_{N-k}.
 template <class T>
-__global__ void k_time_long_unpack(int N, int n1, int n2, int ncol, const c_t<T>* __restrict__ z, c_t<T>* __restrict__ S,
+__global__ void k_time_long_unpack(int N, LongPlan pl, int ncol, const c_t<T>* __restrict__ z, c_t<T>* __restrict__ S,
                                    const Ctl* __restrict__ ctl) {
     using C = c_t<T>;
     if (ctl && ctl->status != ST_RUNNING) return;
@@ -338,17 +371,17 @@ __global__ void k_time_long_unpack(int N, int n1, int n2, int ncol, const c_t<T>
     const T half = T(0.5);
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const int k = (int)(i / ncol), j = (int)(i % ncol);
-        const C zk = z[long_pos(k, n1, n2) * ncol + j];
-        const C zr = z[long_pos((N - k) % N, n1, n2) * ncol + j];
+        const C zk = z[long_pos(k, pl) * ncol + j];
+        const C zr = z[long_pos((N - k) % N, pl) * ncol + j];
         C* row = S + (size_t)k * 2 * ncol;
         row[2 * j] = mkc(half * (zk.x + zr.x), half * (zk.y - zr.y));
         row[2 * j + 1] = mkc(half * (zk.y + zr.y), half * (zr.x - zk.x));
     }
 }
 
-// Z_k = S_a[k] + i S_b[k] over the full Hermitian spectrum, into the workspace rows of pass B.
+// Z_k = S_a[k] + i S_b[k] over the full Hermitian spectrum, into the workspace rows of the last forward pass.
 template <class T>
-__global__ void k_time_long_pack(int N, int n1, int n2, int ncol, const c_t<T>* __restrict__ S, c_t<T>* __restrict__ z,
+__global__ void k_time_long_pack(int N, LongPlan pl, int ncol, const c_t<T>* __restrict__ S, c_t<T>* __restrict__ z,
                                  const Ctl* __restrict__ ctl) {
     using C = c_t<T>;
     if (ctl && ctl->status != ST_RUNNING) return;
@@ -360,15 +393,16 @@ __global__ void k_time_long_pack(int N, int n1, int n2, int ncol, const c_t<T>* 
         C a = row[2 * j], b = row[2 * j + 1];
         if (kk == 0 || kk == N / 2) { a.y = T(0); b.y = T(0); }   // real in exact arithmetic
         if (k > N / 2) { a.y = -a.y; b.y = -b.y; }
-        z[long_pos(k, n1, n2) * ncol + j] = mkc(a.x - b.y, a.y + b.x);
+        z[long_pos(k, pl) * ncol + j] = mkc(a.x - b.y, a.y + b.x);
     }
 }
 
-// Pass A' (inverse over k1, rows m*N2 + o) and the output: x[n] scaled by
-// ginv[n] (which holds alpha^{-n/N}/N); OUTK as in k_time_inv.
+// Inverse pass 0 (over k_0, rows m*istr0 + o, istr0 = N / f_0) and the output:
+// x[n] at n = m*istr0 + o scaled by ginv[n] (which holds alpha^{-n/N}/N); OUTK
+// as in k_time_inv.
 template <class T, int NL, int OUTK>
 __global__ void __launch_bounds__(TimeCfg<T, NL>::NTH)
-    k_time_long_out(int ncol, int n2, int N, const c_t<T>* __restrict__ z, const c_t<T>* __restrict__ twN,
+    k_time_long_out(int ncol, int istr0, int N, const c_t<T>* __restrict__ z, const c_t<T>* __restrict__ twN,
                     const double* __restrict__ ginv, const float* __restrict__ ginvf, double* __restrict__ out,
                     float2* __restrict__ outff, int accumulate, const Ctl* __restrict__ ctl, double* __restrict__ dpart) {
     using C = c_t<T>;
@@ -385,7 +419,7 @@ __global__ void __launch_bounds__(TimeCfg<T, NL>::NTH)
     for (int i = tid; i < NL; i += NTH) tw[i] = twN[(size_t)i * step];
     for (int e = tid; e < NL * CW; e += NTH) {
         const int c = e % CW, m = e / CW;
-        buf[e] = j0 + c < ncol ? z[((size_t)m * n2 + o) * ncol + j0 + c] : mkc(T(0), T(0));
+        buf[e] = j0 + c < ncol ? z[((size_t)m * istr0 + o) * ncol + j0 + c] : mkc(T(0), T(0));
     }
     __syncthreads();
     smem_fft<C, NL, +1, NTH, CW, CW, 1>(buf, tw);
@@ -395,7 +429,7 @@ __global__ void __launch_bounds__(TimeCfg<T, NL>::NTH)
         const int c = e % CW, m = e / CW;
         const int j = j0 + c;
         if (j >= ncol) continue;
-        const size_t n = (size_t)m * n2 + o;
+        const size_t n = (size_t)m * istr0 + o;
         const C v = buf[e];
         if constexpr (OUTK == 1) {
             const float gi = ginvf[n];
@@ -462,11 +496,11 @@ template <class T, int NL>
 static cudaError_t configure_long() {
     const int sm = (int)TimeCfg<T, NL>::SMEM;
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_time_long_pass<T, NL, -1, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
+    if ((e = cudaFuncSetAttribute(k_time_long_pass<T, NL, -1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
         return e;
-    if ((e = cudaFuncSetAttribute(k_time_long_pass<T, NL, -1, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
+    if ((e = cudaFuncSetAttribute(k_time_long_pass<T, NL, -1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
         return e;
-    if ((e = cudaFuncSetAttribute(k_time_long_pass<T, NL, +1, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
+    if ((e = cudaFuncSetAttribute(k_time_long_pass<T, NL, +1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
         return e;
     if ((e = cudaFuncSetAttribute(k_time_long_out<T, NL, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
         return e;
@@ -528,23 +562,25 @@ static void time_inv_ff_nt(int nspace, const float2* S, const float2* twt, const
 }
 
 // ---- long time axes: host side ----
+// Forward pass s (kind 0: with twiddle, 1: the last, without) or inverse pass
+// s >= 1 (kind 2: with the twiddle of pass s-1).
 template <class T, int NL>
-static void long_pass_nl(int pass, int ncol, int n1, int n2, int N, c_t<T>* z, const c_t<T>* twN, const Ctl* ctl,
-                         cudaStream_t st) {
+static void long_pass_nl(int kind, int ncol, int istr, int fprev, int N, c_t<T>* z, const c_t<T>* twN,
+                         const Ctl* ctl, cudaStream_t st) {
     using Cfg = TimeCfg<T, NL>;
-    dim3 grid((ncol + Cfg::CW - 1) / Cfg::CW, pass == 0 ? n2 : n1);
-    if (pass == 0) k_time_long_pass<T, NL, -1, true, 0><<<grid, Cfg::NTH, Cfg::SMEM, st>>>(ncol, n2, N, z, twN, ctl);
-    else if (pass == 1) k_time_long_pass<T, NL, -1, false, 1><<<grid, Cfg::NTH, Cfg::SMEM, st>>>(ncol, n2, N, z, twN, ctl);
-    else k_time_long_pass<T, NL, +1, true, 1><<<grid, Cfg::NTH, Cfg::SMEM, st>>>(ncol, n2, N, z, twN, ctl);
+    dim3 grid((ncol + Cfg::CW - 1) / Cfg::CW, N / NL);
+    if (kind == 0) k_time_long_pass<T, NL, -1, true><<<grid, Cfg::NTH, Cfg::SMEM, st>>>(ncol, istr, 1, N, z, twN, ctl);
+    else if (kind == 1) k_time_long_pass<T, NL, -1, false><<<grid, Cfg::NTH, Cfg::SMEM, st>>>(ncol, istr, 1, N, z, twN, ctl);
+    else k_time_long_pass<T, NL, +1, true><<<grid, Cfg::NTH, Cfg::SMEM, st>>>(ncol, istr, fprev, N, z, twN, ctl);
 }
 template <class T>
-static cudaError_t long_pass(int pass, int nl, int ncol, int n1, int n2, int N, c_t<T>* z, const c_t<T>* twN,
+static cudaError_t long_pass(int kind, int nl, int ncol, int istr, int fprev, int N, c_t<T>* z, const c_t<T>* twN,
                              const Ctl* ctl, cudaStream_t st) {
     switch (nl) {
-        case 32: long_pass_nl<T, 32>(pass, ncol, n1, n2, N, z, twN, ctl, st); break;
-        case 64: long_pass_nl<T, 64>(pass, ncol, n1, n2, N, z, twN, ctl, st); break;
-        case 128: long_pass_nl<T, 128>(pass, ncol, n1, n2, N, z, twN, ctl, st); break;
-        case 256: long_pass_nl<T, 256>(pass, ncol, n1, n2, N, z, twN, ctl, st); break;
+        case 32: long_pass_nl<T, 32>(kind, ncol, istr, fprev, N, z, twN, ctl, st); break;
+        case 64: long_pass_nl<T, 64>(kind, ncol, istr, fprev, N, z, twN, ctl, st); break;
+        case 128: long_pass_nl<T, 128>(kind, ncol, istr, fprev, N, z, twN, ctl, st); break;
+        case 256: long_pass_nl<T, 256>(kind, ncol, istr, fprev, N, z, twN, ctl, st); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaSuccess;
@@ -557,24 +593,23 @@ static int grid1d(size_t n) {
 template <class T>
 static cudaError_t time_fwd_long(int nt, int nspace, T* s, c_t<T>* S, const c_t<T>* twt, const Ctl* ctl,
                                  cudaStream_t st) {
-    int n1, n2;
-    long_split(nt, n1, n2);
+    const LongPlan pl = long_plan(nt);
     const int ncol = nspace / 2;
     c_t<T>* z = reinterpret_cast<c_t<T>*>(s);   // s is consumed here: the workspace is s itself
     cudaError_t e;
-    if ((e = long_pass<T>(0, n1, ncol, n1, n2, nt, z, twt, ctl, st))) return e;
-    if ((e = long_pass<T>(1, n2, ncol, n1, n2, nt, z, twt, ctl, st))) return e;
-    k_time_long_unpack<T><<<grid1d((size_t)(nt / 2 + 1) * ncol), 256, 0, st>>>(nt, n1, n2, ncol, z, S, ctl);
+    for (int i = 0; i < pl.S; ++i)
+        if ((e = long_pass<T>(i + 1 < pl.S ? 0 : 1, pl.f[i], ncol, pl.istr[i], 1, nt, z, twt, ctl, st))) return e;
+    k_time_long_unpack<T><<<grid1d((size_t)(nt / 2 + 1) * ncol), 256, 0, st>>>(nt, pl, ncol, z, S, ctl);
     return cudaGetLastError();
 }
 
 template <class T, int NL, int OUTK>
-static void long_out_nl(int ncol, int n1, int n2, int N, const c_t<T>* z, const c_t<T>* twN, const double* ginv,
+static void long_out_nl(int ncol, int istr0, int N, const c_t<T>* z, const c_t<T>* twN, const double* ginv,
                         const float* ginvf, double* out, float2* outff, int acc, const Ctl* ctl, double* dpart,
                         cudaStream_t st) {
     using Cfg = TimeCfg<T, NL>;
-    dim3 grid((ncol + Cfg::CW - 1) / Cfg::CW, n2);
-    k_time_long_out<T, NL, OUTK><<<grid, Cfg::NTH, Cfg::SMEM, st>>>(ncol, n2, N, z, twN, ginv, ginvf, out, outff,
+    dim3 grid((ncol + Cfg::CW - 1) / Cfg::CW, istr0);
+    k_time_long_out<T, NL, OUTK><<<grid, Cfg::NTH, Cfg::SMEM, st>>>(ncol, istr0, N, z, twN, ginv, ginvf, out, outff,
                                                                    acc, ctl, dpart);
 }
 template <class T, int OUTK>
@@ -582,18 +617,19 @@ static cudaError_t time_inv_long(int nt, int nspace, const c_t<T>* S, const c_t<
                                  const double* ginv, const float* ginvf, double* out, float2* outff, int acc,
                                  const Ctl* ctl, double* dpart, cudaStream_t st) {
     if (!work) return cudaErrorInvalidValue;
-    int n1, n2;
-    long_split(nt, n1, n2);
+    const LongPlan pl = long_plan(nt);
     const int ncol = nspace / 2;
     c_t<T>* z = reinterpret_cast<c_t<T>*>(work);
-    k_time_long_pack<T><<<grid1d((size_t)nt * ncol), 256, 0, st>>>(nt, n1, n2, ncol, S, z, ctl);
+    k_time_long_pack<T><<<grid1d((size_t)nt * ncol), 256, 0, st>>>(nt, pl, ncol, S, z, ctl);
     cudaError_t e;
-    if ((e = long_pass<T>(2, n2, ncol, n1, n2, nt, z, twt, ctl, st))) return e;
-    switch (n1) {
-        case 32: long_out_nl<T, 32, OUTK>(ncol, n1, n2, nt, z, twt, ginv, ginvf, out, outff, acc, ctl, dpart, st); break;
-        case 64: long_out_nl<T, 64, OUTK>(ncol, n1, n2, nt, z, twt, ginv, ginvf, out, outff, acc, ctl, dpart, st); break;
-        case 128: long_out_nl<T, 128, OUTK>(ncol, n1, n2, nt, z, twt, ginv, ginvf, out, outff, acc, ctl, dpart, st); break;
-        case 256: long_out_nl<T, 256, OUTK>(ncol, n1, n2, nt, z, twt, ginv, ginvf, out, outff, acc, ctl, dpart, st); break;
+    for (int i = pl.S - 1; i >= 1; --i)
+        if ((e = long_pass<T>(2, pl.f[i], ncol, pl.istr[i], pl.f[i - 1], nt, z, twt, ctl, st))) return e;
+    const int istr0 = pl.istr[0];
+    switch (pl.f[0]) {
+        case 32: long_out_nl<T, 32, OUTK>(ncol, istr0, nt, z, twt, ginv, ginvf, out, outff, acc, ctl, dpart, st); break;
+        case 64: long_out_nl<T, 64, OUTK>(ncol, istr0, nt, z, twt, ginv, ginvf, out, outff, acc, ctl, dpart, st); break;
+        case 128: long_out_nl<T, 128, OUTK>(ncol, istr0, nt, z, twt, ginv, ginvf, out, outff, acc, ctl, dpart, st); break;
+        case 256: long_out_nl<T, 256, OUTK>(ncol, istr0, nt, z, twt, ginv, ginvf, out, outff, acc, ctl, dpart, st); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -601,16 +637,15 @@ static cudaError_t time_inv_long(int nt, int nspace, const c_t<T>* S, const c_t<
 
 // CTAs (dpart pairs) of the output pass of a long time axis.
 static int time_long_blocks(int nt, int nspace, int f32) {
-    int n1, n2;
-    long_split(nt, n1, n2);
+    const LongPlan pl = long_plan(nt);
     int cw = 32;
-    switch (n1) {
+    switch (pl.f[0]) {
 #define CW_(N) case N: cw = f32 ? TimeCfg<float, N>::CW : TimeCfg<double, N>::CW; break;
         CW_(32) CW_(64) CW_(128) CW_(256)
 #undef CW_
         default: break;
     }
-    return (nspace / 2 + cw - 1) / cw * n2;
+    return (nspace / 2 + cw - 1) / cw * pl.istr[0];
 }
 
 int time_inv_ff_blocks(int nt, int nspace, const Ctl* ctl) {

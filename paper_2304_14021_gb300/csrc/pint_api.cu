@@ -27,6 +27,7 @@ namespace pint {
 
 template <class T> cudaError_t configure_time_all();
 template <class T> cudaError_t configure_spatial_all();
+cudaError_t configure_residual_ff();
 
 cudaError_t configure_kernels() {
     static int done = -1;  // per process: the attributes are per device function
@@ -38,6 +39,7 @@ cudaError_t configure_kernels() {
     if ((e = configure_time_all<double>()) != cudaSuccess) return e;
     if ((e = configure_spatial_all<float>()) != cudaSuccess) return e;
     if ((e = configure_spatial_all<double>()) != cudaSuccess) return e;
+    if ((e = configure_residual_ff()) != cudaSuccess) return e;
     done = dev;
     return cudaSuccess;
 }
@@ -55,7 +57,7 @@ static int validate(const pint_problem* p) {
         return PINT_EINVAL;
     if (p->bc == PINT_BC_NEUMANN_VERTEX && (p->nx < 3 || (p->dim == 2 && p->ny < 3))) return PINT_EINVAL;
     if (p->nx < 2 || (p->dim == 2 && p->ny < 2)) return PINT_EINVAL;
-    if (!is_pow2(p->nt) || p->nt < 2 || p->nt > 65536) return PINT_EINVAL;
+    if (!is_pow2(p->nt) || p->nt < 2 || p->nt > (1 << 20)) return PINT_EINVAL;
     // time axes beyond 1024 steps take the four-step FFT, which pairs neighbouring spatial points
     if (p->nt > 1024 && ((long)p->nx * (p->dim == 2 ? p->ny : 1)) % 2 != 0) return PINT_EINVAL;
     if (p->n_windows < 1) return PINT_EINVAL;

@@ -48,7 +48,7 @@ def test_strerror(lib):
     assert "unknown" in pint.strerror(-99)
 
 
-BAD = [dict(dim=3), dict(nx=1), dict(nt=48), dict(nt=131072), dict(nt=2048, nx=63), dict(nt=1), dict(alpha=0.0), dict(alpha=1.0),
+BAD = [dict(dim=3), dict(nx=1), dict(nt=48), dict(nt=1 << 21), dict(nt=2048, nx=63), dict(nt=1), dict(alpha=0.0), dict(alpha=1.0),
        dict(theta=0.7), dict(theta=0.5, equation="cahn_hilliard", eps=0.05), dict(tol=0.0), dict(max_iter=0), dict(max_iter=256), dict(precision=7),
        dict(T=-1.0), dict(equation=5), dict(bc=3), dict(n_windows=0), dict(nx=2000, bc="ss"),
        dict(equation="linear_ch", eps=0.0), dict(init_guess=3), dict(dim=2, ny=1), dict(tol_update=-1.0)]
@@ -110,5 +110,5 @@ def test_crank_nicolson_accepted_for_linear_equations(lib):
 
 def test_long_time_axis_accepted_for_even_point_counts(lib):
     kw = dict(equation="linear_ch", dim=1, nx=64, bc="neumann", eps=0.05, beta=0.5, T=1.0, alpha=1e-2, tol=1e-8)
-    for nt in (2048, 65536):
+    for nt in (2048, 65536, 131072, 1 << 20):
         assert pint.footprint(**kw, nt=nt) > 0

@@ -104,6 +104,37 @@ def test_sequential_step_matches_library_sparse_solve():
         assert np.allclose(U[k], u, rtol=1e-12, atol=1e-14)
 
 
+@pytest.mark.parametrize("theta", [1.0, 0.5])
+def test_sequential_at_selected_steps_matches_stepping(theta):
+    # u_n = M^n u_0 by binary powering equals stepping the recurrence n times
+    p = P(equation=O.LINEAR_CH, dim=2, nx=6, ny=5, bc="neumann", eps=0.05, beta=0.5, T=4e-3, nt=40, theta=theta)
+    u0 = synth.u0_uniform(30, -0.05, 0.05, 5)
+    U = O.sequential(p, u0)
+    steps = [1, 2, 5, 17, 40]
+    Us = O.sequential_linear_at(p, u0, steps)
+    for i, n in enumerate(steps):
+        assert O.rel_err(Us[i], U[n - 1]) < 1e-12
+
+
+def test_sequential_at_long_axis_eigenmode_closed_form():
+    # 1-D biharmonic, cell-centred Neumann, 64 cells, dt = 1e-6 over 2^20 steps:
+    # a cosine mode decays by (1 + dt lambda^2)^{-n}, the constant mode stays put
+    n, nt = 64, 1 << 20
+    p = P(equation=O.BIHARMONIC, nx=n, bc="neumann", T=nt * 1e-6, nt=nt)
+    x = synth.grid_points_1d(n, "neumann")
+    h = 1.0 / n
+    steps = [1, 1000, 1 << 19, 1 << 20]
+    for mode in (1, 2):
+        phi = np.cos(mode * np.pi * x)
+        lam = -(4 / h**2) * np.sin(mode * np.pi / (2 * n)) ** 2
+        Us = O.sequential_linear_at(p, 0.3 + phi, steps)
+        for i, k in enumerate(steps):
+            ex = 0.3 + (1 + p.dt * lam**2) ** (-k) * phi
+            # M carries about cond(I + dt A) eps = 3e-14 of rounding, compounded over up
+            # to 2^20 steps (1.2e-10 seen); a wrong power or step is off by O(1e-2) or more
+            assert np.abs(Us[i] - ex).max() < 1e-9
+
+
 # --- all-at-once system (Eq. 2.6-2.7) vs sequential --------------------------
 
 @pytest.mark.parametrize("theta", [1.0, 0.5])
@@ -113,6 +144,19 @@ def test_all_at_once_dense_equals_sequential(theta, eq, bc, dim):
     p = P(equation=eq, dim=dim, nx=6, ny=5, bc=bc, eps=0.1, beta=0.4, T=2e-3, nt=6, theta=theta)
     u0 = synth.u0_uniform(p.nspace, -1, 1, 7)
     assert O.rel_err(O.all_at_once_dense_linear(p, u0), O.sequential(p, u0)) < 1e-11
+
+
+def test_ch_newton_step_at_rounding_floor_solves_the_step():
+    # eps = 0.1, 128 cells, dt = 1e-4 (cond(J) ~ 4e3): the 1e-14 update test is out of
+    # reach, the rounding-floor stop ends Newton; the step equation then holds to rounding
+    p = P(equation=O.CAHN_HILLIARD, nx=128, bc="neumann", eps=0.1, T=1e-4, nt=1)
+    x = synth.grid_points_1d(128, "neumann")
+    u0 = 0.75 * np.sin(2 * np.pi * x) + 0.25 * np.cos(4 * np.pi * x)
+    u, it = O.ch_step_newton(p, u0)
+    L = O.laplacian(p)
+    F = (u - u0) / p.dt - L @ (u ** 3 - u) + p.eps ** 2 * (L @ (L @ u))
+    scale = np.abs(u0 / p.dt).max() + np.abs(p.eps ** 2 * (L @ (L @ u))).max()
+    assert it <= 10 and np.abs(F).max() < 1e-12 * scale
 
 
 def test_ch_all_at_once_newton_equals_sequential():
