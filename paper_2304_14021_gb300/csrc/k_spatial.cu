@@ -26,7 +26,17 @@ namespace cg = cooperative_groups;
 
 namespace pint {
 
-enum { MODE_FWD = 0, MODE_INV = 1, MODE_FDI = 2 };
+enum { MODE_FWD = 0, MODE_INV = 1, MODE_FDI = 2, MODE_PACK = 3 };
+
+// Destination of MODE_PACK (1-D rows on a long time axis): the solved row
+// S2[k] goes straight into the workspace of the inverse time transform as
+// z[long_pos(k)][j] = S2[k][2j] + i S2[k][2j+1] and, for 0 < k < N_t/2, its
+// Hermitian partner z[long_pos(N_t - k)][j] = conj(S2[k][2j]) + i conj(S2[k][2j+1]).
+template <class T> struct PackDst {
+    c_t<T>* z;
+    LongPlan pl;
+    int nt;
+};
 
 template <class T>
 __device__ __forceinline__ c_t<T> shift_den(const Tabs<T>& tb, int k, T Lam, T c2, T c1) {
@@ -93,7 +103,7 @@ __device__ __forceinline__ void note_timeout(const Ctl* ctl) {
 
 template <class T, int N, int MODE>
 __global__ void __launch_bounds__(256, RowCfg<T, N>::MINB) k_rows_dct(int nrows, int ny, c_t<T>* __restrict__ S, Tabs<T> tb,
-                                                  SolveCoef co, const Ctl* __restrict__ ctl) {
+                                                  SolveCoef co, const Ctl* __restrict__ ctl, PackDst<T> pd) {
     using C = c_t<T>;
     using Cfg = RowCfg<T, N>;
     constexpr int ROWS = Cfg::ROWS, NTH = Cfg::NTH, STAGES = Cfg::STAGES, TILE = Cfg::TILE;
@@ -170,7 +180,7 @@ __global__ void __launch_bounds__(256, RowCfg<T, N>::MINB) k_rows_dct(int nrows,
                 const C wp = tb.wx[p], wq = tb.wx[q];
                 C Xp, Xq;
                 dct_post(row[sp], row[sq], wp, wq, Xp, Xq);
-                if (MODE == MODE_FDI) {
+                if (MODE == MODE_FDI || MODE == MODE_PACK) {
                     const int k = (int)((r0 + b) / ny);
                     if (r0 + b < nrows) {
                         Xp = cdiv(Xp, shift_den(tb, k, tb.lamx[p], c2, c1));
@@ -192,11 +202,27 @@ __global__ void __launch_bounds__(256, RowCfg<T, N>::MINB) k_rows_dct(int nrows,
         } else {
             smem_fft<C, N, +1, NTH, ROWS, 1, N, 1>(buf, tb.twx);
             const T inv = T(1) / T(N);
+            if constexpr (MODE == MODE_PACK) {
+                constexpr int NC = N / 2;
+                const int half = pd.nt / 2;
+                for (int e = tid; e < ROWS * NC; e += NTH) {
+                    const int b = e / NC, j = e % NC;
+                    const long k = r0 + b;
+                    if (k >= nrows) continue;
+                    C a = scalec(buf[b * N + swz<1>(dct_pos(2 * j, N))], inv);
+                    C c = scalec(buf[b * N + swz<1>(dct_pos(2 * j + 1, N))], inv);
+                    if (k == 0 || k == half) { a.y = T(0); c.y = T(0); }   // real in exact arithmetic
+                    pd.z[(size_t)long_pos((int)k, pd.pl) * NC + j] = mkc(a.x - c.y, a.y + c.x);
+                    if (k > 0 && k < half)
+                        pd.z[(size_t)long_pos(pd.nt - (int)k, pd.pl) * NC + j] = mkc(a.x + c.y, c.x - a.y);
+                }
+            } else {
 #pragma unroll 4
-            for (int e = tid; e < ROWS * N; e += NTH) {
-                const int b = e / N, i = e % N;
-                const long gr = r0 + b;
-                if (gr < nrows) S[r0 * N + e] = scalec(buf[b * N + swz<1>(dct_pos(i, N))], inv);
+                for (int e = tid; e < ROWS * N; e += NTH) {
+                    const int b = e / N, i = e % N;
+                    const long gr = r0 + b;
+                    if (gr < nrows) S[r0 * N + e] = scalec(buf[b * N + swz<1>(dct_pos(i, N))], inv);
+                }
             }
         }
         fence_proxy_async_smem();   // this thread's accesses to buf precede the refill
@@ -785,8 +811,10 @@ static cudaError_t cfg_rows() {
         return e;
     if ((e = cudaFuncSetAttribute(k_rows_dct<T, N, MODE_FDI>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
         return e;
+    if ((e = cudaFuncSetAttribute(k_rows_dct<T, N, MODE_PACK>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
+        return e;
     if (rows_resident<T, N, MODE_FWD>() <= 0 || rows_resident<T, N, MODE_INV>() <= 0 ||
-        rows_resident<T, N, MODE_FDI>() <= 0)
+        rows_resident<T, N, MODE_FDI>() <= 0 || rows_resident<T, N, MODE_PACK>() <= 0)
         return cudaErrorInvalidConfiguration;
     if constexpr (rows_warp_ok<T, N>) {
         const int smw = (int)RowWCfg<T, N>::SMEM;
@@ -871,9 +899,40 @@ static cudaError_t rows_n(int nrows, int ny, c_t<T>* S, const Tabs<T>& tb, Solve
     if (resident <= 0) return cudaErrorInvalidConfiguration;
     const int ntiles = (nrows + Cfg::ROWS - 1) / Cfg::ROWS;
     const int grid = ntiles < resident ? ntiles : resident;
-    k_rows_dct<T, N, MODE><<<grid, Cfg::NTH, Cfg::SMEM, st>>>(nrows, ny, S, tb, co, ctl);
+    k_rows_dct<T, N, MODE><<<grid, Cfg::NTH, Cfg::SMEM, st>>>(nrows, ny, S, tb, co, ctl, PackDst<T>{});
     return cudaSuccess;
 }
+template <class T, int N>
+static cudaError_t pack_solve_n(int nt, const c_t<T>* S, c_t<T>* z, const LongSolve<T>& ls, const Ctl* ctl,
+                                cudaStream_t st) {
+    using Cfg = RowCfg<T, N>;
+    const int resident = rows_resident<T, N, MODE_PACK>();
+    if (resident <= 0) return cudaErrorInvalidConfiguration;
+    const int nrows = nt / 2 + 1;
+    const int ntiles = (nrows + Cfg::ROWS - 1) / Cfg::ROWS;
+    const int grid = ntiles < resident ? ntiles : resident;
+    const PackDst<T> pd{z, long_plan(nt), nt};
+    k_rows_dct<T, N, MODE_PACK><<<grid, Cfg::NTH, Cfg::SMEM, st>>>(nrows, 1, const_cast<c_t<T>*>(S), *ls.tb, ls.co,
+                                                                   ctl, pd);
+    return cudaSuccess;
+}
+template <class T>
+cudaError_t launch_long_pack_solve(int nt, const c_t<T>* S, c_t<T>* z, const LongSolve<T>& ls, const Ctl* ctl,
+                                   cudaStream_t st) {
+    cudaError_t e;
+    switch (ls.nx) {
+#define P_(N) case N: e = pack_solve_n<T, N>(nt, S, z, ls, ctl, st); break;
+        P_(2) P_(4) P_(8) P_(16) P_(32) P_(64) P_(128) P_(256) P_(512) P_(1024) P_(2048) P_(4096)
+#undef P_
+        default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+template cudaError_t launch_long_pack_solve<float>(int, const float2*, float2*, const LongSolve<float>&, const Ctl*,
+                                                   cudaStream_t);
+template cudaError_t launch_long_pack_solve<double>(int, const double2*, double2*, const LongSolve<double>&,
+                                                    const Ctl*, cudaStream_t);
 template <class T, int MODE>
 static cudaError_t rows_dct(int nx, int nrows, int ny, c_t<T>* S, const Tabs<T>& tb, SolveCoef co, const Ctl* ctl,
                             cudaStream_t st) {

@@ -286,11 +286,7 @@ __global__ void __launch_bounds__(TimeTmaCfg<NT>::NTH)
 // spectrum of the real signals (pairs k, N-k) in natural order and pack
 // rebuilds the full one.
 // ---------------------------------------------------------------------------
-struct LongPlan {
-    int S;
-    int f[3], istr[3], P[3];
-};
-static LongPlan long_plan(int nt) {
+LongPlan long_plan(int nt) {
     int l = 0;
     while ((1 << l) < nt) ++l;
     LongPlan pl{};
@@ -303,6 +299,12 @@ static LongPlan long_plan(int nt) {
         for (int j = i + 1; j < pl.S; ++j) pl.istr[i] *= pl.f[j];
         pl.P[i] = 1;
         for (int j = 0; j < i; ++j) pl.P[i] *= pl.f[j];
+    }
+    auto lg = [](int v) { int l = 0; while ((1 << l) < v) ++l; return l; };
+    for (int i = 0; i < pl.S; ++i) {
+        pl.lf[i] = lg(pl.f[i]);
+        pl.listr[i] = lg(pl.istr[i]);
+        pl.lP[i] = lg(pl.P[i]);
     }
     return pl;
 }
@@ -342,9 +344,9 @@ __global__ void __launch_bounds__(TimeCfg<T, NL>::NTH)
         if (j0 + c >= ncol) continue;
         C v = buf[e];
         if (TW) {
-            size_t idx;
-            if (DIR < 0) idx = ((size_t)olo * m * (size_t)(N / (NL * istr))) % (size_t)N;
-            else idx = ((size_t)(ohi % fprev) * ((size_t)m * istr + olo) * (size_t)(N / (fprev * NL * istr))) % (size_t)N;
+            // both exponents stay below N: olo < istr, m < NL; k_{s-1} < fprev, m istr + olo < NL istr
+            const int idx = DIR < 0 ? olo * m * (N / (NL * istr))
+                                    : (ohi % fprev) * (m * istr + olo) * (N / (fprev * NL * istr));
             C w = twN[idx];
             if (DIR > 0) w = conjc(w);
             v = cmul(v, w);
@@ -354,12 +356,11 @@ __global__ void __launch_bounds__(TimeCfg<T, NL>::NTH)
     }
 }
 
-// Row of Z_k in the workspace after the last forward pass.
-__device__ __forceinline__ size_t long_pos(int k, const LongPlan& pl) {
-    size_t r = 0;
-    for (int i = 0; i < pl.S; ++i) r += (size_t)((k / pl.P[i]) % pl.f[i]) * pl.istr[i];
-    return r;
-}
+// Row-block mapping of the unpack / pack kernels: thread t of a CTA of
+// kPackThreads takes column j = t % ncol of row kk = t / ncol of each group of
+// RB = kPackThreads / ncol rows (ncol <= kPackThreads), or columns j, j +
+// kPackThreads, ... of one row (ncol > kPackThreads); no division per element.
+constexpr int kPackThreads = 256;
 
 // S[k][2j], S[k][2j+1] (k = 0..N/2) from Z_k and Z_{N-k}.
 template <class T>
@@ -367,15 +368,20 @@ __global__ void k_time_long_unpack(int N, LongPlan pl, int ncol, const c_t<T>* _
                                    const Ctl* __restrict__ ctl) {
     using C = c_t<T>;
     if (ctl && ctl->status != ST_RUNNING) return;
-    const size_t total = (size_t)(N / 2 + 1) * ncol;
+    const int K = N / 2 + 1;
     const T half = T(0.5);
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const int k = (int)(i / ncol), j = (int)(i % ncol);
-        const C zk = z[long_pos(k, pl) * ncol + j];
-        const C zr = z[long_pos((N - k) % N, pl) * ncol + j];
+    const int rb = ncol <= kPackThreads ? kPackThreads / ncol : 1;
+    const int t = threadIdx.x, kk = ncol <= kPackThreads ? t / ncol : 0, j0 = ncol <= kPackThreads ? t % ncol : t;
+    if (kk >= rb) return;
+    for (int k = blockIdx.x * rb + kk; k < K; k += gridDim.x * rb) {
+        const C* zrk = z + (size_t)long_pos(k, pl) * ncol;
+        const C* zrr = z + (size_t)long_pos((N - k) & (N - 1), pl) * ncol;
         C* row = S + (size_t)k * 2 * ncol;
-        row[2 * j] = mkc(half * (zk.x + zr.x), half * (zk.y - zr.y));
-        row[2 * j + 1] = mkc(half * (zk.y + zr.y), half * (zr.x - zk.x));
+        for (int j = j0; j < ncol; j += kPackThreads) {
+            const C zk = zrk[j], zr = zrr[j];
+            row[2 * j] = mkc(half * (zk.x + zr.x), half * (zk.y - zr.y));
+            row[2 * j + 1] = mkc(half * (zk.y + zr.y), half * (zr.x - zk.x));
+        }
     }
 }
 
@@ -385,15 +391,19 @@ __global__ void k_time_long_pack(int N, LongPlan pl, int ncol, const c_t<T>* __r
                                  const Ctl* __restrict__ ctl) {
     using C = c_t<T>;
     if (ctl && ctl->status != ST_RUNNING) return;
-    const size_t total = (size_t)N * ncol;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const int k = (int)(i / ncol), j = (int)(i % ncol);
+    const int rb = ncol <= kPackThreads ? kPackThreads / ncol : 1;
+    const int t = threadIdx.x, kr = ncol <= kPackThreads ? t / ncol : 0, j0 = ncol <= kPackThreads ? t % ncol : t;
+    if (kr >= rb) return;
+    for (int k = blockIdx.x * rb + kr; k < N; k += gridDim.x * rb) {
         const int kk = k <= N / 2 ? k : N - k;
         const C* row = S + (size_t)kk * 2 * ncol;
-        C a = row[2 * j], b = row[2 * j + 1];
-        if (kk == 0 || kk == N / 2) { a.y = T(0); b.y = T(0); }   // real in exact arithmetic
-        if (k > N / 2) { a.y = -a.y; b.y = -b.y; }
-        z[long_pos(k, pl) * ncol + j] = mkc(a.x - b.y, a.y + b.x);
+        C* zr = z + (size_t)long_pos(k, pl) * ncol;
+        for (int j = j0; j < ncol; j += kPackThreads) {
+            C a = row[2 * j], b = row[2 * j + 1];
+            if (kk == 0 || kk == N / 2) { a.y = T(0); b.y = T(0); }   // real in exact arithmetic
+            if (k > N / 2) { a.y = -a.y; b.y = -b.y; }
+            zr[j] = mkc(a.x - b.y, a.y + b.x);
+        }
     }
 }
 
@@ -585,9 +595,11 @@ static cudaError_t long_pass(int kind, int nl, int ncol, int istr, int fprev, in
     }
     return cudaSuccess;
 }
-static int grid1d(size_t n) {
-    size_t b = (n + 255) / 256;
-    return (int)(b > 4 * 152 * 8 ? 4 * 152 * 8 : (b < 1 ? 1 : b));
+// CTAs of the unpack / pack kernels for `rows` rows of ncol columns (grid-stride beyond 8 waves).
+static int pack_grid(int rows, int ncol) {
+    const int rb = ncol <= kPackThreads ? kPackThreads / ncol : 1;
+    const long b = (rows + rb - 1) / rb;
+    return (int)(b > 8L * 152 * 8 ? 8L * 152 * 8 : (b < 1 ? 1 : b));
 }
 
 template <class T>
@@ -599,7 +611,7 @@ static cudaError_t time_fwd_long(int nt, int nspace, T* s, c_t<T>* S, const c_t<
     cudaError_t e;
     for (int i = 0; i < pl.S; ++i)
         if ((e = long_pass<T>(i + 1 < pl.S ? 0 : 1, pl.f[i], ncol, pl.istr[i], 1, nt, z, twt, ctl, st))) return e;
-    k_time_long_unpack<T><<<grid1d((size_t)(nt / 2 + 1) * ncol), 256, 0, st>>>(nt, pl, ncol, z, S, ctl);
+    k_time_long_unpack<T><<<pack_grid(nt / 2 + 1, ncol), kPackThreads, 0, st>>>(nt, pl, ncol, z, S, ctl);
     return cudaGetLastError();
 }
 
@@ -615,13 +627,17 @@ static void long_out_nl(int ncol, int istr0, int N, const c_t<T>* z, const c_t<T
 template <class T, int OUTK>
 static cudaError_t time_inv_long(int nt, int nspace, const c_t<T>* S, const c_t<T>* twt, void* work,
                                  const double* ginv, const float* ginvf, double* out, float2* outff, int acc,
-                                 const Ctl* ctl, double* dpart, cudaStream_t st) {
+                                 const Ctl* ctl, double* dpart, cudaStream_t st, const LongSolve<T>* ls) {
     if (!work) return cudaErrorInvalidValue;
     const LongPlan pl = long_plan(nt);
     const int ncol = nspace / 2;
     c_t<T>* z = reinterpret_cast<c_t<T>*>(work);
-    k_time_long_pack<T><<<grid1d((size_t)nt * ncol), 256, 0, st>>>(nt, pl, ncol, S, z, ctl);
     cudaError_t e;
+    if (ls) {
+        if ((e = launch_long_pack_solve<T>(nt, S, z, *ls, ctl, st))) return e;
+    } else {
+        k_time_long_pack<T><<<pack_grid(nt, ncol), kPackThreads, 0, st>>>(nt, pl, ncol, S, z, ctl);
+    }
     for (int i = pl.S - 1; i >= 1; --i)
         if ((e = long_pass<T>(2, pl.f[i], ncol, pl.istr[i], pl.f[i - 1], nt, z, twt, ctl, st))) return e;
     const int istr0 = pl.istr[0];
@@ -647,6 +663,10 @@ static int time_long_blocks(int nt, int nspace, int f32) {
     }
     return (nspace / 2 + cw - 1) / cw * pl.istr[0];
 }
+
+// passes + unpack; pack (or pack with the fused spatial solve) + passes 1.. + output pass
+int time_fwd_launches(int nt) { return nt > 1024 ? long_plan(nt).S + 1 : 1; }
+int time_inv_launches(int nt) { return nt > 1024 ? long_plan(nt).S + 1 : 1; }
 
 int time_inv_ff_blocks(int nt, int nspace, const Ctl* ctl) {
     if (nt > 1024) return time_long_blocks(nt, nspace, 1);
@@ -686,9 +706,12 @@ cudaError_t launch_time_fwd(int nt, int nspace, const T* s, c_t<T>* S, const c_t
 }
 template <class T>
 cudaError_t launch_time_inv(int nt, int nspace, const c_t<T>* S, const c_t<T>* twt, const double* ginv, double* out,
-                            int accumulate, const Ctl* ctl, double* dpart, cudaStream_t st, void* work) {
+                            int accumulate, const Ctl* ctl, double* dpart, cudaStream_t st, void* work,
+                            const LongSolve<T>* ls) {
     if (nt > 1024)
-        return time_inv_long<T, 0>(nt, nspace, S, twt, work, ginv, nullptr, out, nullptr, accumulate, ctl, dpart, st);
+        return time_inv_long<T, 0>(nt, nspace, S, twt, work, ginv, nullptr, out, nullptr, accumulate, ctl, dpart, st,
+                                   ls);
+    if (ls) return cudaErrorInvalidValue;
 #define CALL(N) time_inv_nt<T, N>(nspace, S, twt, ginv, out, accumulate, ctl, dpart, st)
     PINT_NT_SWITCH(CALL)
 #undef CALL
@@ -696,9 +719,11 @@ cudaError_t launch_time_inv(int nt, int nspace, const c_t<T>* S, const c_t<T>* t
 }
 
 cudaError_t launch_time_inv_ff(int nt, int nspace, const float2* S, const float2* twt, const float* ginvf,
-                               float2* Uff, const Ctl* ctl, double* dpart, cudaStream_t st, void* work) {
+                               float2* Uff, const Ctl* ctl, double* dpart, cudaStream_t st, void* work,
+                               const LongSolve<float>* ls) {
     if (nt > 1024)
-        return time_inv_long<float, 1>(nt, nspace, S, twt, work, nullptr, ginvf, nullptr, Uff, 1, ctl, dpart, st);
+        return time_inv_long<float, 1>(nt, nspace, S, twt, work, nullptr, ginvf, nullptr, Uff, 1, ctl, dpart, st, ls);
+    if (ls) return cudaErrorInvalidValue;
 #define CALL(N) time_inv_ff_nt<N>(nspace, S, twt, ginvf, Uff, ctl, dpart, st)
     PINT_NT_SWITCH(CALL)
 #undef CALL
@@ -709,8 +734,8 @@ template cudaError_t launch_time_fwd<float>(int, int, const float*, float2*, con
 template cudaError_t launch_time_fwd<double>(int, int, const double*, double2*, const double2*, const Ctl*,
                                              cudaStream_t);
 template cudaError_t launch_time_inv<float>(int, int, const float2*, const float2*, const double*, double*, int,
-                                            const Ctl*, double*, cudaStream_t, void*);
+                                            const Ctl*, double*, cudaStream_t, void*, const LongSolve<float>*);
 template cudaError_t launch_time_inv<double>(int, int, const double2*, const double2*, const double*, double*, int,
-                                             const Ctl*, double*, cudaStream_t, void*);
+                                             const Ctl*, double*, cudaStream_t, void*, const LongSolve<double>*);
 
 }  // namespace pint

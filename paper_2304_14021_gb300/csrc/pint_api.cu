@@ -517,7 +517,15 @@ static long long footprint_of(const pint_problem* p) {
 static bool fused_spatial(const pint_handle* h) {
     return h->fuse2d && slice2d_supported(h->geo, h->fft_x, h->fft_y, h->p.precision != PINT_FP64);
 }
-static int spatial_launches(const pint_handle* h) { return fused_spatial(h) ? 1 : (h->geo.dim == 2 ? 3 : 1); }
+// 1-D long time axes on the cosine path: Step 2 rides on the pack of the
+// inverse time transform (not with the space-varying Jacobian, whose inner
+// solve works on the half spectrum itself).
+static bool long_fused(const pint_handle* h) {
+    return h->geo.dim == 1 && h->geo.nt > 1024 && h->fft_x && !(h->vary > 0 && h->coef.ch);
+}
+static int spatial_launches(const pint_handle* h) {
+    return long_fused(h) ? 0 : fused_spatial(h) ? 1 : (h->geo.dim == 2 ? 3 : 1);
+}
 
 // Partial-sum buffer of the update-size test, or NULL when the test is off
 // (then the inverse time transform skips that reduction).
@@ -709,12 +717,15 @@ template <class T> struct Impl {
         prof_end(h, PH_CHECK, 1);
         prof_begin(h, PH_TFWD);
         cudaError_t e = launch_time_fwd<T>(g.nt, g.nspace, s, S, tb.twt, h->ctl, h->st);
-        prof_end(h, PH_TFWD, 1);
+        prof_end(h, PH_TFWD, time_fwd_launches(g.nt));
         if (e != cudaSuccess) return e;
-        if ((e = step2(h, S, tb, U, nullptr)) != cudaSuccess) return e;
+        const bool lf = long_fused(h);
+        const LongSolve<T> ls{&tb, h->coef, g.nx};
+        if (!lf && (e = step2(h, S, tb, U, nullptr)) != cudaSuccess) return e;
         prof_begin(h, PH_TINV);
-        e = launch_time_inv<T>(g.nt, g.nspace, S, tb.twt, h->ginv, U, 1, h->ctl, upd_part(h), h->st, h->s);
-        prof_end(h, PH_TINV, 1);
+        e = launch_time_inv<T>(g.nt, g.nspace, S, tb.twt, h->ginv, U, 1, h->ctl, upd_part(h), h->st, h->s,
+                               lf ? &ls : nullptr);
+        prof_end(h, PH_TINV, time_inv_launches(g.nt));
         if (e != cudaSuccess) return e;
         return cudaGetLastError();
     }
@@ -727,8 +738,11 @@ template <class T> struct Impl {
         launch_scale_cast<T>(r, h->gam, s, g.nspace, g.nt, h->st);
         cudaError_t e = launch_time_fwd<T>(g.nt, g.nspace, s, S, tb.twt, h->ctl, h->st);
         if (e != cudaSuccess) return e;
-        if ((e = spatial(h, S, tb)) != cudaSuccess) return e;
-        e = launch_time_inv<T>(g.nt, g.nspace, S, tb.twt, h->ginv, delta, 0, h->ctl, nullptr, h->st, h->s);
+        const bool lf = long_fused(h);
+        const LongSolve<T> ls{&tb, h->coef, g.nx};
+        if (!lf && (e = spatial(h, S, tb)) != cudaSuccess) return e;
+        e = launch_time_inv<T>(g.nt, g.nspace, S, tb.twt, h->ginv, delta, 0, h->ctl, nullptr, h->st, h->s,
+                               lf ? &ls : nullptr);
         if (e != cudaSuccess) return e;
         return cudaGetLastError();
     }
@@ -748,21 +762,27 @@ static cudaError_t zero_start(pint_handle* h, double* U, const double* u0w) {
     else launch_zero_start<double>(reinterpret_cast<double2*>(h->S), b1, sc, g.nspace, nk, h->ctl, h->st);
     prof_end(h, PH_TFWD, 1);
     cudaError_t e;
+    const bool lf = long_fused(h);
     if (f32_transforms(&h->p)) {
         const Tabs<float>& tb = tabs_of<float>(h);
-        if ((e = Impl<float>::spatial(h, reinterpret_cast<float2*>(h->S), tb)) != cudaSuccess) return e;
+        const LongSolve<float> ls{&tb, h->coef, g.nx};
+        if (!lf && (e = Impl<float>::spatial(h, reinterpret_cast<float2*>(h->S), tb)) != cudaSuccess) return e;
         prof_begin(h, PH_TINV);
         if (h->p.precision == PINT_MIXED_FF)
-            e = launch_time_inv_ff(g.nt, g.nspace, reinterpret_cast<float2*>(h->S), tb.twt, h->ginvf, h->Uff_cur, h->ctl, upd_part(h), h->st, h->s);
+            e = launch_time_inv_ff(g.nt, g.nspace, reinterpret_cast<float2*>(h->S), tb.twt, h->ginvf, h->Uff_cur, h->ctl,
+                                   upd_part(h), h->st, h->s, lf ? &ls : nullptr);
         else
-            e = launch_time_inv<float>(g.nt, g.nspace, reinterpret_cast<float2*>(h->S), tb.twt, h->ginv, U, 1, h->ctl, upd_part(h), h->st, h->s);
-        prof_end(h, PH_TINV, 1);
+            e = launch_time_inv<float>(g.nt, g.nspace, reinterpret_cast<float2*>(h->S), tb.twt, h->ginv, U, 1, h->ctl,
+                                       upd_part(h), h->st, h->s, lf ? &ls : nullptr);
+        prof_end(h, PH_TINV, time_inv_launches(g.nt));
     } else {
         const Tabs<double>& tb = tabs_of<double>(h);
-        if ((e = Impl<double>::spatial(h, reinterpret_cast<double2*>(h->S), tb)) != cudaSuccess) return e;
+        const LongSolve<double> ls{&tb, h->coef, g.nx};
+        if (!lf && (e = Impl<double>::spatial(h, reinterpret_cast<double2*>(h->S), tb)) != cudaSuccess) return e;
         prof_begin(h, PH_TINV);
-        e = launch_time_inv<double>(g.nt, g.nspace, reinterpret_cast<double2*>(h->S), tb.twt, h->ginv, U, 1, h->ctl, upd_part(h), h->st, h->s);
-        prof_end(h, PH_TINV, 1);
+        e = launch_time_inv<double>(g.nt, g.nspace, reinterpret_cast<double2*>(h->S), tb.twt, h->ginv, U, 1, h->ctl,
+                                    upd_part(h), h->st, h->s, lf ? &ls : nullptr);
+        prof_end(h, PH_TINV, time_inv_launches(g.nt));
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
@@ -785,12 +805,15 @@ static cudaError_t iteration_ff(pint_handle* h) {
     prof_end(h, PH_CHECK, 1);
     prof_begin(h, PH_TFWD);
     cudaError_t e = launch_time_fwd<float>(g.nt, g.nspace, s, S, tb.twt, h->ctl, h->st);
-    prof_end(h, PH_TFWD, 1);
+    prof_end(h, PH_TFWD, time_fwd_launches(g.nt));
     if (e != cudaSuccess) return e;
-    if ((e = Impl<float>::step2(h, S, tb, nullptr, h->Uff_cur)) != cudaSuccess) return e;
+    const bool lf = long_fused(h);
+    const LongSolve<float> ls{&tb, h->coef, g.nx};
+    if (!lf && (e = Impl<float>::step2(h, S, tb, nullptr, h->Uff_cur)) != cudaSuccess) return e;
     prof_begin(h, PH_TINV);
-    e = launch_time_inv_ff(g.nt, g.nspace, S, tb.twt, h->ginvf, h->Uff_cur, h->ctl, upd_part(h), h->st, h->s);
-    prof_end(h, PH_TINV, 1);
+    e = launch_time_inv_ff(g.nt, g.nspace, S, tb.twt, h->ginvf, h->Uff_cur, h->ctl, upd_part(h), h->st, h->s,
+                           lf ? &ls : nullptr);
+    prof_end(h, PH_TINV, time_inv_launches(g.nt));
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -1394,9 +1417,9 @@ int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* 
                 const long long runs = h->hctl->iter + 1 - (init == 2 ? 1 : 0);
                 h->launches[PH_RES] += runs;
                 h->launches[PH_CHECK] += runs;
-                h->launches[PH_TFWD] += runs;
+                h->launches[PH_TFWD] += runs * time_fwd_launches(g.nt);
                 for (int stg = 0; stg < spatial_launches(h); ++stg) h->launches[PH_SP0 + stg] += runs;
-                h->launches[PH_TINV] += runs;
+                h->launches[PH_TINV] += runs * time_inv_launches(g.nt);
             } else {
                 int enqueued = 0;
                 for (;;) {

@@ -45,6 +45,36 @@ struct GeoFF {
     int expl;       // Eyre splitting: the c1 Laplacian term acts on u_{n-1}
 };
 
+// Factorization of a long time axis (N_t > 1024) for the multi-pass FFT of
+// k_timefft.cu: N_t = f_0 ... f_{S-1}, istr_s = prod_{j>s} f_j,
+// P_s = prod_{j<s} f_j, all powers of two (lf, listr, lP their logarithms).
+struct LongPlan {
+    int S;
+    int f[3], istr[3], P[3];
+    int lf[3], listr[3], lP[3];
+};
+LongPlan long_plan(int nt);
+#ifdef __CUDACC__
+// Workspace row of Z_k after the last forward pass: sum_s k_s istr_s, k = sum_s k_s P_s.
+__device__ __forceinline__ int long_pos(int k, const LongPlan& pl) {
+    int r = 0;
+    for (int i = 0; i < pl.S; ++i) r += ((k >> pl.lP[i]) & (pl.f[i] - 1)) << pl.listr[i];
+    return r;
+}
+#endif
+// 1-D long axes: the spatial solve of Step 2 done by the pack of the inverse
+// time transform (one pass over the half spectrum instead of two).
+template <class T> struct LongSolve {
+    const Tabs<T>* tb;
+    SolveCoef co;
+    int nx;
+};
+// Rows of N = nx points on the cosine (FFT) path: S[k] solved and written as the pack
+// workspace rows z[long_pos(k)], z[long_pos(N_t - k)] (k = 0..N_t/2).
+template <class T>
+cudaError_t launch_long_pack_solve(int nt, const c_t<T>* S, c_t<T>* z, const LongSolve<T>& ls, const Ctl* ctl,
+                                   cudaStream_t st);
+
 int residual_grid(const Geo& g, int& gx, int& gy, int& gz, int& chunk);
 int residual_ff_grid(const Geo& g, int& gx, int& gy, int& gz, int& chunk);
 void launch_residual_ff(const GeoFF& g, const Geo& g64, const float2* U, const float2* u0, const float* gamf,
@@ -53,7 +83,8 @@ void launch_f64_to_ff(const double* in, float2* out, size_t n, cudaStream_t st);
 void launch_ff_to_f64(const float2* in, double* out, size_t n, cudaStream_t st);
 void launch_broadcast_ff(float2* U, const float2* u0, int nspace, int nt, cudaStream_t st);
 cudaError_t launch_time_inv_ff(int nt, int nspace, const float2* S, const float2* twt, const float* ginvf,
-                               float2* Uff, const Ctl* ctl, double* dpart, cudaStream_t st, void* work = nullptr);
+                               float2* Uff, const Ctl* ctl, double* dpart, cudaStream_t st, void* work = nullptr,
+                               const LongSolve<float>* ls = nullptr);
 template <class TS>
 void launch_residual(const Geo& g, const double* U, const double* u0, const double* gam, double* r_out, TS* s_out,
                      double* partials, const Ctl* ctl, cudaStream_t st);
@@ -80,10 +111,15 @@ cudaError_t launch_time_fwd(int nt, int nspace, const T* s, c_t<T>* S, const c_t
 // Step 3: delta_n = ginv[n] * Re( sum_k S[k] exp(+2 pi i nk/nt) ) over the full
 // Hermitian spectrum; U += delta (accumulate) or out = delta.
 // dpart (may be NULL): per-CTA (sum delta^2, sum U^2) pairs, time_inv_blocks() of them.
+// ls (N_t > 1024, 1-D, may be NULL): solve Step 2 on the way (S then holds the unsolved spectrum).
 template <class T>
 cudaError_t launch_time_inv(int nt, int nspace, const c_t<T>* S, const c_t<T>* twt, const double* ginv, double* out,
-                            int accumulate, const Ctl* ctl, double* dpart, cudaStream_t st, void* work = nullptr);
+                            int accumulate, const Ctl* ctl, double* dpart, cudaStream_t st, void* work = nullptr,
+                            const LongSolve<T>* ls = nullptr);
 int time_inv_blocks(int nt, int nspace, int f32);
+// Kernel launches of one forward / inverse time transform (several passes beyond 1024 steps).
+int time_fwd_launches(int nt);
+int time_inv_launches(int nt);
 
 // Vector kernels of the outer flexible GMRES (k_krylov.cu).  At most
 // kMaxKrylov basis vectors per restart.
