@@ -83,7 +83,8 @@ typedef struct {
     double beta;         /* beta of the linearized CH equation; A = beta|beta| Lap + eps^2 Lap^2, so
                             beta < 0 gives the diffusive second-order term (signed beta^2) */
     double T;            /* final time; dt = T / (nt * n_windows) */
-    int    nt;           /* time steps per window, a power of two in [2, 1024] */
+    int    nt;           /* time steps per window, a power of two in [2, 2^20]; above 1024 the number of
+                            spatial points must be even (the multi-pass time FFT pairs neighbouring points) */
     int    n_windows;    /* consecutive windows; window w starts from the last step of window w-1 */
     double theta;        /* theta-method parameter (Eq. 2.5): 1 (backward Euler), or 1/2 (Crank-Nicolson)
                             for the linear equations; Cahn-Hilliard is backward Euler (Eq. 4.5) */
