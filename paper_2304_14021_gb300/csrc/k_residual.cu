@@ -210,6 +210,7 @@ __global__ void __launch_bounds__(256) k_begin_window(const double* __restrict__
 __global__ void __launch_bounds__(256) k_after_residual(const double* __restrict__ partials, int np,
                                                         double inv_dof, Ctl* ctl, cudaGraphConditionalHandle cond,
                                                         int use_cond, const double* __restrict__ dpart, int ndp) {
+    pdl_wait();
     if (ctl->status != ST_RUNNING) {
         if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
         return;
@@ -356,8 +357,8 @@ void launch_begin_window(const Geo& g, const double* u0, int max_iter, double to
 }
 void launch_after_residual(const double* partials, int np, double inv_dof, Ctl* ctl, cudaStream_t st,
                            unsigned long long cond, int use_cond, const double* dpart, int ndp) {
-    k_after_residual<<<1, 256, 0, st>>>(partials, np, inv_dof, ctl, (cudaGraphConditionalHandle)cond, use_cond,
-                                        dpart, ndp);
+    launch_pdl(k_after_residual, dim3(1), dim3(256), 0, st, partials, np, inv_dof, ctl, (cudaGraphConditionalHandle)cond,
+               use_cond, dpart, ndp);
 }
 void launch_residual_norm(const double* partials, int np, Ctl* ctl, cudaStream_t st) {
     k_residual_norm<<<1, 256, 0, st>>>(partials, np, ctl);

@@ -138,6 +138,7 @@ __global__ void __launch_bounds__(256, 5) k_residual_ff(GeoFF g, const ff* __res
                                                      const float* __restrict__ gamf, float* __restrict__ s_out,
                                                      double* __restrict__ partials, const Ctl* __restrict__ ctl,
                                                      int chunk) {
+    pdl_wait();
     if (ctl && ctl->status != ST_RUNNING) return;
     constexpr int TX = ResTileFF<DIM>::TX, TY = ResTileFF<DIM>::TY, PPT = ResTileFF<DIM>::PPT;
     constexpr int NTHR = TX * TY / PPT;
@@ -374,6 +375,7 @@ __global__ void __launch_bounds__(kNarrowThreads, 2)
     k_residual_ff_narrow(GeoFF g, const ff* __restrict__ U, const ff* __restrict__ u0, const float* __restrict__ gamf,
                          float* __restrict__ s_out, double* __restrict__ partials, const Ctl* __restrict__ ctl, int tn,
                          int wrows) {
+    pdl_wait();
     if (ctl && ctl->status != ST_RUNNING) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nx = g.nx, bc = g.bc, rows = tn + 1;
@@ -584,7 +586,8 @@ void launch_residual_ff(const GeoFF& g, const Geo& g64, const ff* U, const ff* u
         const int wrows = narrow_wrows(usep, g.cN.x != 0.f);
         const size_t sm = narrow_smem(g64.nx, chunk, wrows);
 #define PINT_RFN(A, P) \
-    k_residual_ff_narrow<A, P><<<gx, kNarrowThreads, sm, st>>>(g, U, u0, gamf, s, partials, ctl, chunk, wrows)
+    launch_pdl(k_residual_ff_narrow<A, P>, dim3(gx), dim3(kNarrowThreads), sm, st, g, U, u0, gamf, s, partials, ctl, \
+               chunk, wrows)
         if (acc) { if (usep) PINT_RFN(true, true); else PINT_RFN(true, false); }
         else { if (usep) PINT_RFN(false, true); else PINT_RFN(false, false); }
 #undef PINT_RFN
@@ -592,8 +595,10 @@ void launch_residual_ff(const GeoFF& g, const Geo& g64, const ff* U, const ff* u
     }
 #define PINT_RFF(D, S, A)                                                                                      \
     do {                                                                                                       \
-        if (usep) k_residual_ff<D, S, A, true><<<grid, 256, 0, st>>>(g, U, u0, gamf, s, partials, ctl, chunk);  \
-        else k_residual_ff<D, S, A, false><<<grid, 256, 0, st>>>(g, U, u0, gamf, s, partials, ctl, chunk);      \
+        if (usep) launch_pdl(k_residual_ff<D, S, A, true>, grid, dim3(256), 0, st, g, U, u0, gamf, s, partials, \
+                             ctl, chunk);                                                                       \
+        else launch_pdl(k_residual_ff<D, S, A, false>, grid, dim3(256), 0, st, g, U, u0, gamf, s, partials, ctl,  \
+                        chunk);                                                                                  \
     } while (0)
     if (g.dim == 2) {
         if (sq) { if (acc) PINT_RFF(2, true, true); else PINT_RFF(2, true, false); }

@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(256, RowCfg<T, N>::MINB) k_rows_dct(int nrows,
     using C = c_t<T>;
     using Cfg = RowCfg<T, N>;
     constexpr int ROWS = Cfg::ROWS, NTH = Cfg::NTH, STAGES = Cfg::STAGES, TILE = Cfg::TILE;
+    pdl_wait();
     if (ctl && ctl->status != ST_RUNNING) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* bufs = reinterpret_cast<C*>(smem_raw);
@@ -255,6 +256,7 @@ __global__ void __launch_bounds__(256, RowWCfg<T, N>::MINB) k_rows_dct_w(int nro
     using C = c_t<T>;
     using Cfg = RowWCfg<T, N>;
     constexpr int STAGES = Cfg::STAGES, NP = N / 2 + 1, PPL = (NP + 31) / 32;
+    pdl_wait();
     if (ctl && ctl->status != ST_RUNNING) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -376,6 +378,7 @@ __global__ void __launch_bounds__(ColCfg<T, N>::NTH)
     using C = c_t<T>;
     using Cfg = ColCfg<T, N>;
     constexpr int CW = Cfg::CW, NTH = Cfg::NTH, STAGES = Cfg::STAGES;
+    pdl_wait();
     if (ctl && ctl->status != ST_RUNNING) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* bufs = reinterpret_cast<C*>(smem_raw);
@@ -468,6 +471,7 @@ __global__ void __launch_bounds__(512, ColWCfg<T, N>::MINB) k_cols_dct_fdi_w(int
     using C = c_t<T>;
     using Cfg = ColWCfg<T, N>;
     constexpr int CW = Cfg::CW, NTH = Cfg::NTH, STAGES = Cfg::STAGES, NP = N / 2 + 1, PPL = (NP + 31) / 32;
+    pdl_wait();
     if (ctl && ctl->status != ST_RUNNING) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* bufs = reinterpret_cast<C*>(smem_raw);
@@ -891,7 +895,7 @@ static cudaError_t rows_n(int nrows, int ny, c_t<T>* S, const Tabs<T>& tb, Solve
         if (resident <= 0) return cudaErrorInvalidConfiguration;
         const int need = (nrows + W::WARPS - 1) / W::WARPS;
         const int grid = need < resident ? need : resident;
-        k_rows_dct_w<T, N, MODE><<<grid, W::NTH, W::SMEM, st>>>(nrows, ny, S, tb, co, ctl);
+        launch_pdl(k_rows_dct_w<T, N, MODE>, dim3(grid), dim3(W::NTH), W::SMEM, st, nrows, ny, S, tb, co, ctl);
         return cudaSuccess;
     }
     using Cfg = RowCfg<T, N>;
@@ -899,7 +903,8 @@ static cudaError_t rows_n(int nrows, int ny, c_t<T>* S, const Tabs<T>& tb, Solve
     if (resident <= 0) return cudaErrorInvalidConfiguration;
     const int ntiles = (nrows + Cfg::ROWS - 1) / Cfg::ROWS;
     const int grid = ntiles < resident ? ntiles : resident;
-    k_rows_dct<T, N, MODE><<<grid, Cfg::NTH, Cfg::SMEM, st>>>(nrows, ny, S, tb, co, ctl, PackDst<T>{});
+    launch_pdl(k_rows_dct<T, N, MODE>, dim3(grid), dim3(Cfg::NTH), Cfg::SMEM, st, nrows, ny, S, tb, co, ctl,
+               PackDst<T>{});
     return cudaSuccess;
 }
 template <class T, int N>
@@ -962,7 +967,7 @@ static cudaError_t cols_n(int nx, int nk, c_t<T>* S, const Tabs<T>& tb, SolveCoe
         if (resident <= 0) return cudaErrorInvalidConfiguration;
         const int ntiles = nk * ((nx + W::CW - 1) / W::CW);
         const int grid = ntiles < resident ? ntiles : resident;
-        k_cols_dct_fdi_w<T, N><<<grid, W::NTH, W::SMEM, st>>>(nx, nk, S, tb, co, ctl);
+        launch_pdl(k_cols_dct_fdi_w<T, N>, dim3(grid), dim3(W::NTH), W::SMEM, st, nx, nk, S, tb, co, ctl);
         return cudaSuccess;
     }
     using Cfg = ColCfg<T, N>;
@@ -970,7 +975,7 @@ static cudaError_t cols_n(int nx, int nk, c_t<T>* S, const Tabs<T>& tb, SolveCoe
     if (resident <= 0) return cudaErrorInvalidConfiguration;
     const int ntiles = nk * ((nx + Cfg::CW - 1) / Cfg::CW);
     const int grid = ntiles < resident ? ntiles : resident;
-    k_cols_dct_fdi<T, N><<<grid, Cfg::NTH, Cfg::SMEM, st>>>(nx, nk, S, tb, co, ctl);
+    launch_pdl(k_cols_dct_fdi<T, N>, dim3(grid), dim3(Cfg::NTH), Cfg::SMEM, st, nx, nk, S, tb, co, ctl);
     return cudaSuccess;
 }
 template <class T>

@@ -32,6 +32,7 @@ __global__ void __launch_bounds__(TimeCfg<T, NT>::NTH)
                const Ctl* __restrict__ ctl) {
     using C = c_t<T>;
     constexpr int CW = TimeCfg<T, NT>::CW, NTH = TimeCfg<T, NT>::NTH;
+    pdl_wait();
     if (ctl && ctl->status != ST_RUNNING) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* z = reinterpret_cast<C*>(smem_raw);
@@ -73,6 +74,7 @@ __global__ void __launch_bounds__(TimeCfg<T, NT>::NTH)
                double* __restrict__ dpart) {
     using C = c_t<T>;
     constexpr int CW = TimeCfg<T, NT>::CW, NTH = TimeCfg<T, NT>::NTH;
+    pdl_wait();
     if (ctl && ctl->status != ST_RUNNING) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* z = reinterpret_cast<C*>(smem_raw);
@@ -185,6 +187,7 @@ __global__ void __launch_bounds__(TimeTmaCfg<NT>::NTH)
     using C = float2;
     using Cfg = TimeTmaCfg<NT>;
     constexpr int CW = Cfg::CW, NTH = Cfg::NTH;
+    pdl_wait();
     if (ctl && ctl->status != ST_RUNNING) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* z = reinterpret_cast<C*>(smem_raw);
@@ -539,7 +542,7 @@ template <class T, int NT>
 static void time_fwd_nt(int nspace, const T* s, c_t<T>* S, const c_t<T>* twt, const Ctl* ctl, cudaStream_t st) {
     constexpr int CW = TimeCfg<T, NT>::CW;
     int grid = (nspace + 2 * CW - 1) / (2 * CW);
-    k_time_fwd<T, NT><<<grid, TimeCfg<T, NT>::NTH, TimeCfg<T, NT>::SMEM, st>>>(nspace, s, S, twt, ctl);
+    launch_pdl(k_time_fwd<T, NT>, dim3(grid), dim3(TimeCfg<T, NT>::NTH), TimeCfg<T, NT>::SMEM, st, nspace, s, S, twt, ctl);
 }
 template <class T, int NT>
 static void time_inv_nt(int nspace, const c_t<T>* S, const c_t<T>* twt, const double* ginv, double* out, int acc,
@@ -561,7 +564,8 @@ static void time_inv_ff_nt(int nspace, const float2* S, const float2* twt, const
         if (time_inv_ff_prefetch(NT, nspace, ctl)) {
             using Cfg = TimeTmaCfg<NT>;
             const int grid = (nspace + 2 * Cfg::CW - 1) / (2 * Cfg::CW);
-            k_time_inv_ff_tma<NT><<<grid, Cfg::NTH, Cfg::SMEM, st>>>(nspace, S, twt, ginvf, Uff, ctl, dpart);
+            launch_pdl(k_time_inv_ff_tma<NT>, dim3(grid), dim3(Cfg::NTH), Cfg::SMEM, st, nspace, S, twt, ginvf, Uff, ctl,
+                       dpart);
             return;
         }
     }
