@@ -257,6 +257,29 @@ def run_cpu_worker(workload: str, alpha: float, budget_s: float, seed: int = 0) 
 
 
 # ----------------------------------------------------------------------------
+# Replicas (N > 1): host-side pieces, also exercised by the CPU gloo tests
+# ----------------------------------------------------------------------------
+def replica_seed(seed: int, rank: int) -> int:
+    """Input seed of a replica: every rank solves its own instance of the workload."""
+    return seed + rank
+
+
+def max_over_ranks(x: float, dist, device: str) -> float:
+    """The largest of the ranks' values (the slowest rank's time); x itself on one rank."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world: int, dof_per_rank: int, seconds: float) -> float:
+    """Space-time DOF/s of the whole job: all ranks' DOF over the slowest rank's time."""
+    return world * dof_per_rank / seconds
+
+
+# ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
 def main_gpu(args) -> None:
@@ -282,7 +305,7 @@ def main_gpu(args) -> None:
 
     wl = WORKLOADS[args.workload]
     kw = solver_kw(wl, args)
-    u0_np = make_u0(wl, args.seed + rank)          # each replica solves its own instance
+    u0_np = make_u0(wl, replica_seed(args.seed, rank))   # each replica solves its own instance
     stream = torch.cuda.current_stream()
     s = pint.Solver(stream=stream, **kw)
     if wl["equation"] in ("cahn_hilliard", "cahn_hilliard_eyre"):
@@ -341,10 +364,7 @@ def main_gpu(args) -> None:
     s.profile_enable(False)
     ms = statistics.mean(times)
     ms_b = statistics.mean(times_b)
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
 
     # End to end through the host-buffer entry point: H2D of u0 and D2H of U inside.
     e2e_s = None
@@ -359,11 +379,7 @@ def main_gpu(args) -> None:
             t0 = time.perf_counter()
             s.solve_host(u0_host, U_host)
             e2e_times.append(time.perf_counter() - t0)
-        e2e_s = statistics.mean(e2e_times)
-        if dist:
-            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(statistics.mean(e2e_times), dist, "cuda")
 
     # The other precision forms on the same input (fewer steps): plain FP64 and
     # FP64-residual mixed.
@@ -448,7 +464,7 @@ def main_gpu(args) -> None:
                        "sample": f"failed: {ex}"}
         out = {
             "metric": "space-time DOF/s at rel. residual 1e-8",
-            "value": world * dof / (ms * 1e-3),
+            "value": whole_job_value(world, dof, ms * 1e-3),
             "unit": "space-time DOF/s",
             "n_gpus": world,
             "steps": args.steps,
@@ -465,7 +481,8 @@ def main_gpu(args) -> None:
                        "varying_jacobian": args.varying_jacobian or None,
                        "final_rel_residual": stats["rel_residual"], "l2": "flushed between steps",
                        "parallelism": f"replicas x{world}"},
-            "e2e": ({"value": world * dof / e2e_s, "unit": "space-time DOF/s", "h2d_bytes_per_step": ns * 8,
+            "e2e": ({"value": whole_job_value(world, dof, e2e_s), "unit": "space-time DOF/s",
+                     "h2d_bytes_per_step": ns * 8,
                      "d2h_bytes_per_step": nt * ns * 8} if e2e_s else None),
             "gpu_launches": launches_total,
             "ms_per_step_profiled_pass": ms_b,
