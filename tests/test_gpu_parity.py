@@ -170,6 +170,50 @@ def test_linear_ch_2d_solve(precision, alpha, init):
     assert err < (1e-10 if precision == "fp64" else 1e-8), err
 
 
+def test_config2_full_size_in_the_benchmark_configuration():
+    # The benchmark's workload exactly: 2-D linCH 256^2 x 128, T = 0.1, float-float, zero start, the
+    # CUDA-graph loop, rel. residual 1e-8, alpha 1e-2 and 1e-3; against the oracle's sequential solution
+    # (banded LU) and the oracle's own residual of the returned iterate.
+    kw0 = dict(equation="linear_ch", dim=2, nx=256, ny=256, bc="neumann", eps=0.05, beta=0.5, nt=128, T=0.1,
+               precision="mixed_ff", tol=1e-8, init_guess=2, max_iter=250)
+    p = oprob(full(kw0))
+    u0 = synth.u0_uniform(p.nspace, -0.05, 0.05, 0)
+    ref = O.sequential(p, u0)
+    bn = O.rhs_norm(p, u0)
+    for alpha in (1e-2, 1e-3):
+        kw = full(dict(kw0, alpha=alpha))
+        U, st = run_solve(kw, u0)
+        assert st["rc"] == 0 and st["rel_residual"] <= 1e-8, st
+        rho = np.linalg.norm(O.residual(oprob(kw), u0, U)) / bn
+        # the float-float residual resolves r to about 2^-48 of its terms (dt ||A|| ~ 5e5 times |u|/dt), so
+        # the reported rho agrees with the FP64 oracle's to ~1e-11 absolute (2.4e-12 seen at rho 6.6e-10)
+        assert rho <= 1.01e-8 and abs(rho - st["rel_residual"]) <= 1e-11, (rho, st["rel_residual"])
+        assert O.rel_err(U, ref) < 1e-8
+
+
+def test_config3_full_size_last_window_properties():
+    # 2-D CH 512^2, eps = 0.02, dt = 1e-4, 8 windows of 256 steps with the adaptive window policy: the
+    # sequential oracle is out of reach here, so the returned last window is checked by properties that
+    # hold at any size: the oracle's per-step residual of its own levels, zero mass, decreasing energy.
+    kw = full(dict(equation="cahn_hilliard", dim=2, nx=512, ny=512, bc="neumann", eps=0.02, nt=256, n_windows=8,
+                   T=2048 * 1e-4, alpha=1e-2, precision="mixed_ff", tol=1e-8, max_iter=250))
+    p = oprob(kw)
+    u0 = synth.u0_ch(p.nspace, 0)
+    with pint.Solver(**kw) as s:
+        s.set_adaptive_windows(True)
+        U = torch.zeros(p.nt, p.nspace, dtype=torch.float64, device="cuda")
+        st = s.solve(dev(u0), U, check=False)
+        U = host(U)
+    assert st["rc"] == 0 and st["windows"] == 8, st
+    # levels 2..256 of the window solve the backward-Euler steps from level 1
+    sub = O.Problem(equation=O.CAHN_HILLIARD, dim=2, nx=512, ny=512, bc="neumann", eps=0.02, T=255 * p.dt, nt=255)
+    rho = np.linalg.norm(O.residual(sub, U[0], U[1:])) / O.rhs_norm(sub, U[0])
+    assert rho < 1e-7, rho
+    assert max(abs(O.discrete_mass(p, u)) for u in U) < 1e-12
+    E = [O.discrete_energy(p, u) for u in U]
+    assert all(E[i + 1] <= E[i] * (1 + 1e-12) for i in range(len(E) - 1))
+
+
 @pytest.mark.parametrize("precision", ["mixed", "mixed_ff"])
 def test_biharmonic_1d_fft_long_rows_mixed(precision):
     kw = full(dict(equation="biharmonic", dim=1, nx=4096, bc="neumann", nt=16, T=1e-9, precision=precision,
