@@ -46,7 +46,7 @@ What is computed (section / equation numbers of the paper):
   Thm 2.4; Thm 3.3 for its linearized-CH bound), discrete energy and mass
   (Eq. 1.5).
 
-Readings of the paper taken here (each is listed in the design doc):
+Readings of the paper taken here:
 
 * The diagonal of D_1 (Lemma 2.1) is computed from the DFT convention used in
   Step 1: with forward transform exp(-2 pi i n k / N_t) it is

@@ -833,7 +833,7 @@ def test_narrow_1d_residual_solves_match_sequential(case):
     assert O.rel_err(U, O.sequential(p, u0)[-p.nt:]) < 1e-8
 
 
-# --- outer flexible GMRES around P_alpha^{-1} (SURVEY f-4, second part) ------
+# --- outer flexible GMRES around P_alpha^{-1} ----------------------------------
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_ff"])
 def test_gmres_matches_sequential_and_needs_fewer_applications(precision):
@@ -880,7 +880,7 @@ def test_gmres_rejected_for_cahn_hilliard():
             s.set_krylov(5)
 
 
-# --- space-varying averaged Jacobian in Step 2 (SURVEY f-1) -------------------
+# --- space-varying averaged Jacobian in Step 2 (Eq. 4.12) ----------------------
 
 def _separated_1d(n, eps):
     x = synth.grid_points_1d(n, "neumann")
