@@ -86,8 +86,8 @@ def solver_kw(wl: dict, args, precision=None) -> dict:
 # DRAM bytes per launch of the float-float residual, from one ncu capture of the
 # 2-D 256x256 x 128 workload (profiles/kernels_linear_ch_2d_256x256_nt128.md),
 # valid only for the kernel source it was taken on (sha256 prefix of the .cu).
-RESIDUAL_FF_TRAFFIC = {"src_sha256_16": "0ebff7401ee9d559", "workload": "linear_ch_2d_256x256_nt128",
-                       "dram_bytes": 68205312 + 6457600}
+RESIDUAL_FF_TRAFFIC = {"src_sha256_16": "f2beb509f59f81f0", "workload": "linear_ch_2d_256x256_nt128",
+                       "dram_bytes": 68294656 + 5862912}
 
 
 def _residual_ff_traffic(workload: str):

@@ -321,17 +321,18 @@ __global__ void __launch_bounds__(256, 5) k_residual_ff(GeoFF g, const ff* __res
 
 // ---------------------------------------------------------------------------
 // Narrow 1-D grids (nx <= 256): a tile is TN consecutive time levels of the
-// whole row (TN a multiple of the warp count, about 1024 points), staged by
-// asynchronous copies one tile ahead (the rows of a tile are contiguous in
-// U).  Stage row j holds level n0-1+j (row 0 is level n0-1, u0 for the first
-// tile); only the nx points of a row are kept and the two ghost points on
-// each side are read through the boundary's even / odd extension (row_at).
-// The Laplacian of a row extends the same way (its ghost values equal the
-// extension of its interior values for all three boundary conditions), so
-// each warp works on its own run of rows with no block barrier between the
-// passes: Lap u of the row into a private buffer, then the residual.  The
-// arithmetic per point, and the order of its sums, is that of k_residual_ff.
-// Persistent CTAs (grid-stride over tiles); one pair of norm partials each.
+// whole row (TN a multiple of the warp count, about 1024 points), staged one
+// tile ahead by asynchronous copies.  Stage row j holds level n0-1+j (row 0
+// is level n0-1, u0 for the first tile) with two ghost points on each side,
+// filled from the row by the boundary condition's even / odd extension once
+// the tile has landed; the Laplacian rows carry one ghost point per side,
+// which equals the same extension of their own interior values for all
+// three boundary conditions.  The stencils then read shared memory with no
+// boundary test.  Each warp works on its own run of rows with no block
+// barrier between the passes (Lap u of the row into a private buffer, its
+// ghosts, then the residual).  The arithmetic per point, and the order of its
+// sums, is that of k_residual_ff.  Persistent CTAs (grid-stride over tiles);
+// one pair of norm partials each.
 // ---------------------------------------------------------------------------
 constexpr int kNarrowNx = 256;
 constexpr int kNarrowThreads = 256;
@@ -344,11 +345,12 @@ static int narrow_tn(int nx) {
 // Rows of private buffer per warp: Lap u of the row, of the previous row (theta = 1/2, Eyre), u^3 (Cahn-Hilliard).
 static int narrow_wrows(bool usep, bool ch) { return 1 + (usep ? 1 : 0) + (ch ? 1 : 0); }
 static size_t narrow_smem(int nx, int tn, int wrows) {
-    return sizeof(ff) * ((size_t)2 * (tn + 1) * nx + (size_t)kNarrowWarps * wrows * nx);
+    return sizeof(ff) * ((size_t)2 * (tn + 1) * (nx + 4) + (size_t)kNarrowWarps * wrows * (nx + 2));
 }
 
-// Row value at index i in [-2, nx+1]: the stored value inside, the extension of the boundary condition outside.
-__device__ __forceinline__ ff row_at(const ff* __restrict__ a, int i, int nx, int bc) {
+// Value at index i in [-2, nx+1] of a row whose interior a[0..nx) is stored:
+// the boundary condition's extension outside.
+__device__ __forceinline__ ff row_ext(const ff* __restrict__ a, int i, int nx, int bc) {
     if (i >= 0 && i < nx) return a[i];
     if (bc == 1) return a[i < 0 ? -1 - i : 2 * nx - 1 - i];
     if (bc == 2) return a[i < 0 ? -i : 2 * (nx - 1) - i];
@@ -356,10 +358,10 @@ __device__ __forceinline__ ff row_at(const ff* __restrict__ a, int i, int nx, in
     const ff v = a[i < 0 ? -2 - i : 2 * nx - i];
     return ffmk(-v.x, -v.y);
 }
-// Unscaled 1-D Laplacian sum a[x-1] + a[x+1] - 2 a[x] in the summation order of lap_ff<1, true, ACC>.
+// Unscaled 1-D Laplacian sum a[x-1] + a[x+1] - 2 a[x] (ghosts stored) in the summation order of lap_ff<1, true, ACC>.
 template <bool ACC>
-__device__ __forceinline__ ff lap_row(const ff* __restrict__ a, int x, int nx, int bc) {
-    const ff l = row_at(a, x - 1, nx, bc), r = row_at(a, x + 1, nx, bc), c = a[x];
+__device__ __forceinline__ ff lap_row(const ff* __restrict__ a, int x) {
+    const ff l = a[x - 1], r = a[x + 1], c = a[x];
     if constexpr (ACC) {
         return ff_add(ff_add(l, r), ff_scale2(c, -2.f));
     } else {
@@ -379,13 +381,14 @@ __global__ void __launch_bounds__(kNarrowThreads, 2)
     if (ctl && ctl->status != ST_RUNNING) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nx = g.nx, bc = g.bc, rows = tn + 1;
+    const int SXN = nx + 4, LXN = nx + 2;           // padded row lengths (stage: 2 ghosts, Laplacian: 1)
     ff* stg = reinterpret_cast<ff*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    ff* wbuf = stg + (size_t)2 * rows * nx + (size_t)warp * wrows * nx;
-    ff* Lc = wbuf;                         // Lap u of the current row
-    ff* Lp = USEP ? wbuf + nx : nullptr;   // Lap u of the previous row
+    ff* wbuf = stg + (size_t)2 * rows * SXN + (size_t)warp * wrows * LXN;
+    ff* Lc = wbuf + 1;                              // Lap u of the current row (index 0 = x 0)
+    ff* Lp = USEP ? wbuf + LXN + 1 : nullptr;       // Lap u of the previous row
     const bool ch = g.cN.x != 0.f;
-    ff* Wr = ch ? wbuf + (size_t)(USEP ? 2 : 1) * nx : nullptr;   // u^3 of the current row
+    ff* Wr = ch ? wbuf + (size_t)(USEP ? 2 : 1) * LXN + 1 : nullptr;   // u^3 of the current row
     const bool lin1 = g.c1.x != 0.f;
     const bool expl = g.expl != 0;
     const float sdt = g.inv_dt.x;
@@ -393,21 +396,39 @@ __global__ void __launch_bounds__(kNarrowThreads, 2)
     float acc_r2 = 0.f, acc_u2 = 0.f;
     const int ntiles = (g.nt + tn - 1) / tn;
     const int rpw = tn / kNarrowWarps;     // rows per warp
+    // one warp per staged row: the row's interior, at offset 2 of its padded slot
     auto stage = [&](int t, ff* dst) {
         const int n0 = t * tn;
-        const int cnt = min(tn, g.nt - n0) * nx;
-        const ff* r0 = n0 == 0 ? u0 : U + (size_t)(n0 - 1) * g.nspace;
-        for (int x = tid; x < nx; x += kNarrowThreads) cp_async8(&dst[x], r0 + x);
-        const ff* src = U + (size_t)n0 * g.nspace;
-        for (int e = tid; e < cnt; e += kNarrowThreads) cp_async8(&dst[nx + e], src + e);
+        const int nrows = min(tn, g.nt - n0) + 1;
+        for (int j = warp; j < nrows; j += kNarrowWarps) {
+            const int lev = n0 - 1 + j;
+            const ff* src = lev < 0 ? u0 : U + (size_t)lev * g.nspace;
+            ff* d = dst + (size_t)j * SXN + 2;
+            for (int x = lane; x < nx; x += 32) cp_async8(&d[x], src + x);
+        }
         cp_async_commit();
+    };
+    // ghosts of a row from its interior (i = -2, -1, nx, nx+1)
+    auto ghost2 = [&](ff* row, int k) {
+        const int i = k < 2 ? k - 2 : nx + k - 2;
+        row[i] = row_ext(row, i, nx, bc);
+    };
+    // Lap u of a staged row (interior) and its one ghost per side; the calling warp only
+    auto lap_of = [&](const ff* ur, ff* L) {
+        for (int x = lane; x < nx; x += 32) L[x] = lap_row<ACC>(ur, x);
+        __syncwarp();
+        if (lane < 2) {
+            const int i = lane == 0 ? -1 : nx;
+            L[i] = row_ext(L, i, nx, bc);
+        }
+        __syncwarp();
     };
     if (blockIdx.x < ntiles) stage(blockIdx.x, stg);
     int it = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
-        const ff* cur = stg + (size_t)(it & 1) * rows * nx;
+        ff* cur = stg + (size_t)(it & 1) * rows * SXN;
         if (t + (int)gridDim.x < ntiles) {
-            stage(t + gridDim.x, stg + (size_t)((it + 1) & 1) * rows * nx);
+            stage(t + gridDim.x, stg + (size_t)((it + 1) & 1) * rows * SXN);
             asm volatile("cp.async.wait_group 1;" ::: "memory");
         } else {
             asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -415,35 +436,38 @@ __global__ void __launch_bounds__(kNarrowThreads, 2)
         __syncthreads();                   // tile t is in shared memory
         const int n0 = t * tn;
         const int nlev = min(tn, g.nt - n0);
+        for (int e = tid; e < (nlev + 1) * 4; e += kNarrowThreads) ghost2(cur + (size_t)(e >> 2) * SXN + 2, e & 3);
+        __syncthreads();                   // ghosts in place
         const int jb = 1 + warp * rpw, je = min(jb + rpw, nlev + 1);
-        if (USEP && jb < je) {
-            const ff* uq = cur + (size_t)(jb - 1) * nx;
-            for (int x = lane; x < nx; x += 32) Lp[x] = lap_row<ACC>(uq, x, nx, bc);
-        }
+        if (USEP && jb < je) lap_of(cur + (size_t)(jb - 1) * SXN + 2, Lp);
         for (int j = jb; j < je; ++j) {
-            const ff* uj = cur + (size_t)j * nx;
-            const ff* uq = uj - nx;
-            for (int x = lane; x < nx; x += 32) {
-                Lc[x] = lap_row<ACC>(uj, x, nx, bc);
-                if (ch) Wr[x] = ff_cube(uj[x]);
+            const ff* uj = cur + (size_t)j * SXN + 2;
+            const ff* uq = uj - SXN;
+            if (ch) {
+                for (int x = lane; x < nx; x += 32) Wr[x] = ff_cube(uj[x]);
+                __syncwarp();
+                if (lane < 2) {
+                    const int i = lane == 0 ? -1 : nx;
+                    Wr[i] = row_ext(Wr, i, nx, bc);
+                }
             }
-            __syncwarp();
+            lap_of(uj, Lc);
             const int n = n0 - 1 + j;
             const float gm = gamf[n] * sdt;
             float* srow = s_out + (size_t)n * g.nspace;
             for (int x = lane; x < nx; x += 32) {
                 const ff u = uj[x], up = uq[x], L = Lc[x];
-                const ff lapL = lap_row<ACC>(Lc, x, nx, bc);
+                const ff lapL = lap_row<ACC>(Lc, x);
                 ff r;
                 if constexpr (USEP) {
                     ff A = ff_mul(lapL, g.c2);
                     if (lin1 && !expl) A = ff_add(A, ff_mul(L, g.c1));
-                    if (ch) A = ff_add(A, ff_mul(lap_row<ACC>(Wr, x, nx, bc), g.cN));
+                    if (ch) A = ff_add(A, ff_mul(lap_row<ACC>(Wr, x), g.cN));
                     ff B;
                     if (expl) {
                         B = ff_mul(Lp[x], g.c1);
                     } else {
-                        B = ff_mul(lap_row<ACC>(Lp, x, nx, bc), g.c2);
+                        B = ff_mul(lap_row<ACC>(Lp, x), g.c2);
                         if (lin1) B = ff_add(B, ff_mul(Lp[x], g.c1));
                     }
                     if constexpr (!ACC) {
@@ -460,12 +484,12 @@ __global__ void __launch_bounds__(kNarrowThreads, 2)
                     acc.add(ff_neg(u));
                     acc.add(ff_neg(ff_mul(lapL, g.c2)));
                     if (lin1) acc.add(ff_neg(ff_mul(L, g.c1)));
-                    if (ch) acc.add(ff_neg(ff_mul(lap_row<ACC>(Wr, x, nx, bc), g.cN)));
+                    if (ch) acc.add(ff_neg(ff_mul(lap_row<ACC>(Wr, x), g.cN)));
                     r = acc.get();
                 } else {
                     ff A = ff_mul(lapL, g.c2);
                     if (lin1) A = ff_add(A, ff_mul(L, g.c1));
-                    if (ch) A = ff_add(A, ff_mul(lap_row<ACC>(Wr, x, nx, bc), g.cN));
+                    if (ch) A = ff_add(A, ff_mul(lap_row<ACC>(Wr, x), g.cN));
                     r = ff_sub(ff_sub(up, u), A);
                 }
                 srow[x] = fmaf(gm, r.x, gm * r.y);
