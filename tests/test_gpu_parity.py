@@ -760,6 +760,21 @@ def test_long_time_axis_solves_match_sequential(precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed_ff"])
+@pytest.mark.parametrize("eq", ["cahn_hilliard", "cahn_hilliard_eyre"])
+def test_long_axis_cahn_hilliard_fused_pack_solve(eq, precision):
+    # 1-D Cahn-Hilliard over 2048 steps: the spatial solve rides on the pack of the long inverse
+    # transform, with the scalar Jacobian (PinT-I) or the lambda_3 term (PinT-II) in its divisor
+    nt = 2048
+    kw = full(dict(equation=eq, dim=1, nx=64, bc="neumann", eps=0.05, nt=nt, T=nt * 2e-6, alpha=1e-2,
+                   precision=precision, tol=1e-10 if precision == "fp64" else 1e-9, tol_update=1e-12))
+    p = oprob(kw)
+    u0 = synth.u0_ch(64, 3)
+    U, st = run_solve(kw, u0)
+    assert st["rc"] == 0, st
+    assert O.rel_err(U, O.sequential(p, u0)) < (1e-9 if precision == "fp64" else 1e-8)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_ff"])
 @pytest.mark.parametrize("nt", [131072, 1 << 20])
 def test_three_pass_time_axis_precond_matches_oracle(nt, precision):
     # N_t beyond 65536 takes three transform passes (2^17 = 32*64*64, 2^20 = 64*128*128)
