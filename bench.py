@@ -202,10 +202,17 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # CPU oracle (reference arm and cpu_baseline): run single-threaded in a child
 # ----------------------------------------------------------------------------
-def cpu_worker(workload: str, alpha: float, budget_s: float, seed: int) -> dict:
+def cpu_worker(workload: str, alpha: float, budget_s: float, seed: int, samples: int = 1) -> dict:
     """Time the oracle's sequential solve on a bounded sample of the workload:
     the banded LU factorization plus as many time steps as fit in budget_s,
-    extrapolated to the full N_t-step solve (DOF/s)."""
+    extrapolated to the full N_t-step solve (DOF/s).  With samples > 1 the
+    whole measurement is repeated that many times in this process and every
+    sample's extrapolated solve time is returned (`seconds_samples`)."""
+    if samples > 1:
+        runs = [cpu_worker(workload, alpha, budget_s, seed) for _ in range(samples)]
+        out = dict(runs[-1])
+        out["seconds_samples"] = [r["seconds_full_solve"] for r in runs]
+        return out
     import numpy as np
     import scipy.sparse as sp
 
@@ -247,11 +254,11 @@ def cpu_worker(workload: str, alpha: float, budget_s: float, seed: int) -> dict:
     return {"value": dof / total, "seconds_full_solve": total, "sample": sample, "cores": 1}
 
 
-def run_cpu_worker(workload: str, alpha: float, budget_s: float, seed: int = 0) -> dict:
+def run_cpu_worker(workload: str, alpha: float, budget_s: float, seed: int = 0, samples: int = 1) -> dict:
     env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", "--workload", workload,
-           "--alpha", str(alpha), "--cpu-budget", str(budget_s), "--seed", str(seed)]
+           "--alpha", str(alpha), "--cpu-budget", str(budget_s), "--seed", str(seed), "--cpu-samples", str(samples)]
     r = subprocess.run(cmd, capture_output=True, text=True, env=env, cwd=ROOT)
     if r.returncode != 0:
         raise RuntimeError(f"cpu worker failed: {r.stderr[-2000:]}")
@@ -616,16 +623,20 @@ def main_serving(args) -> None:
     print(json.dumps(out), flush=True)
 
 
+REFERENCE_TOTAL_S = 150.0   # wall-time target of the whole reference-arm run
+
+
 def main_reference(args) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    times, res = [], None
-    for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        res = run_cpu_worker(args.workload, args.alpha, args.cpu_budget, args.seed)
-        if i >= args.warmup:
-            times.append(res["seconds_full_solve"])
+    # All warm-up and timed samples run in one single-threaded worker process; each
+    # sample's time-step budget shrinks with their number so that the whole run
+    # stays within about three minutes (each sample also pays the LU factorization).
+    n = args.warmup + args.steps
+    budget = max(0.3, min(args.cpu_budget, REFERENCE_TOTAL_S / n - 2.0))
+    res = run_cpu_worker(args.workload, args.alpha, budget, args.seed, samples=n)
+    times = res["seconds_samples"][args.warmup:] if n > 1 else [res["seconds_full_solve"]]
     wl = WORKLOADS[args.workload]
     dof = wl["nx"] * (wl["ny"] if wl["dim"] == 2 else 1) * wl["nt"]
     secs = statistics.mean(times)
@@ -667,9 +678,10 @@ def main() -> None:
                     help="Cahn-Hilliard: inner GMRES length of the space-varying Jacobian in Step 2 (0 = scalar mean)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-worker", action="store_true")
+    ap.add_argument("--cpu-samples", type=int, default=1)
     args = ap.parse_args()
     if args.cpu_worker:
-        print(json.dumps(cpu_worker(args.workload, args.alpha, args.cpu_budget, args.seed)))
+        print(json.dumps(cpu_worker(args.workload, args.alpha, args.cpu_budget, args.seed, args.cpu_samples)))
         return
     if args.impl == "reference":
         main_reference(args)
