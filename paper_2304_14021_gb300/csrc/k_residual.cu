@@ -215,38 +215,58 @@ __global__ void __launch_bounds__(256) k_after_residual(const double* __restrict
         if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
         return;
     }
+    // Thread 0 loads the control fields of the decision first, so that their
+    // latency overlaps the partial-sum loads instead of trailing the stores.
+    int k = 0, max_iter = 0;
+    double bn = 0.0, tol = 0.0, tol_upd = 0.0, rho0 = 0.0, h1 = 0.0, h2 = 0.0, h3 = 0.0, dh3 = 0.0;
+    if (threadIdx.x == 0) {
+        k = ctl->iter;
+        max_iter = ctl->max_iter;
+        bn = ctl->bnorm;
+        tol = ctl->tol;
+        tol_upd = ctl->tol_update;
+        rho0 = ctl->rho0;
+        if (k >= 4 && k < 256) {
+            h1 = ctl->hist[k - 1];
+            h2 = ctl->hist[k - 2];
+            h3 = ctl->hist[k - 3];
+            dh3 = ctl->dhist[k - 3];
+        }
+    }
     double A, B, D = 0.0, W = 0.0;
     reduce_pairs(partials, np, A, B);
     const bool upd = ndp > 0 && ctl->iter > 0 && ctl->tol_update > 0.0;
     __syncthreads();
     if (upd) reduce_pairs(dpart, ndp, D, W);
     if (threadIdx.x == 0) {
-        const int k = ctl->iter;
-        const double bn = ctl->bnorm;
         const double rho = bn > 0.0 ? sqrt(A) / bn : sqrt(A);
         ctl->sum_r2 = A;
         ctl->sum_u2 = B;
         ctl->rho = rho;
         ctl->jbar = 3.0 * B * inv_dof;
         if (k < 256) ctl->hist[k] = rho;
-        if (k == 0) ctl->rho0 = rho;
+        if (k == 0) {
+            ctl->rho0 = rho;
+            rho0 = rho;
+        }
         // stagnation: no decrease over the last three corrections (the residual
         // sits at the rounding floor of the iterate's precision)
         const double dn = upd ? (W > 0.0 ? sqrt(D / W) : sqrt(D)) : 1.0;
         ctl->dnorm = dn;
         if (k < 256) ctl->dhist[k] = dn;
         // with the update-size test on, a still-shrinking correction is progress too
-        const bool d_stalled = !upd || (k >= 4 && dn >= 0.99 * ctl->dhist[k - 3]);
-        const bool stalled = k >= 4 && k < 256 && rho >= 0.99 * ctl->hist[k - 3] && d_stalled;
+        const bool d_stalled = !upd || (k >= 4 && dn >= 0.99 * dh3);
+        const bool stalled = k >= 4 && k < 256 && rho >= 0.99 * h3 && d_stalled;
         // divergence: monotone growth over the last three corrections and 10x overall
         // (a single jump can be rounding noise at the residual floor)
-        const bool growing = k >= 4 && k < 256 && rho > 10.0 * ctl->hist[k - 3] && rho > ctl->hist[k - 1] &&
-                             ctl->hist[k - 1] > ctl->hist[k - 2] && ctl->hist[k - 2] > ctl->hist[k - 3];
-        if (!(rho == rho) || rho > 1e300 || (k > 0 && rho > 1e6 * ctl->rho0) || growing) ctl->status = -5;  // PINT_EDIVERGED
-        else if (rho <= ctl->tol || (upd && dn <= ctl->tol_update)) ctl->status = 0;            // PINT_OK
-        else if (k >= ctl->max_iter || stalled) ctl->status = -4;                               // PINT_ENOCONV
-        else ctl->iter = k + 1;
-        if (use_cond) cudaGraphSetConditional(cond, ctl->status == ST_RUNNING ? 1u : 0u);
+        const bool growing = k >= 4 && k < 256 && rho > 10.0 * h3 && rho > h1 && h1 > h2 && h2 > h3;
+        int status = ST_RUNNING;
+        if (!(rho == rho) || rho > 1e300 || (k > 0 && rho > 1e6 * rho0) || growing) status = -5;  // PINT_EDIVERGED
+        else if (rho <= tol || (upd && dn <= tol_upd)) status = 0;                                // PINT_OK
+        else if (k >= max_iter || stalled) status = -4;                                           // PINT_ENOCONV
+        if (status == ST_RUNNING) ctl->iter = k + 1;
+        else ctl->status = status;
+        if (use_cond) cudaGraphSetConditional(cond, status == ST_RUNNING ? 1u : 0u);
     }
 }
 
