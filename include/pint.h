@@ -18,7 +18,8 @@
  * approximation; P_alpha^{-1} is applied by the three steps of Eq. 2.8:
  * alpha-scaled FFT along time, one shifted spatial solve per frequency, inverse
  * FFT and unscaling.  For Cahn-Hilliard the averaged Jacobian of Eq. 4.12 is
- * the scalar mean of 3u^2 over all space-time points.
+ * the scalar mean of 3u^2 over all space-time points, or with
+ * PINT_OPT_VARYING_JACOBIAN the paper's time average of 3u^2 at each point.
  *
  * Memory: every pointer named *_dev is a CUDA device pointer in the current
  * device's primary context; *_host pointers are host memory.  Arrays are FP64,
@@ -182,7 +183,9 @@ int pint_precond_apply(pint_handle* h, double jbar, const double* r_dev, double*
 /* Per-phase accounting of the kernels a handle launches.  Phases:
  *  0 residual (+ alpha-scaling)      1 convergence check (reduction, status)
  *  2 time FFT (Step 1)               3,4,5 spatial solve stages (Step 2; 1-D uses 3 only)
- *  6 inverse time FFT + unscale + update (Step 3)     7 window set-up
+ *  6 inverse time FFT + unscale + update (Step 3; on 1-D time axes beyond 1024
+ *    steps it also carries Step 2's row solves, and phases 3-5 stay empty)
+ *  7 window set-up
  * launches[] is always counted; ms[] (device time between CUDA events
  * recorded on the handle's stream around each phase) only while enabled. */
 #define PINT_NPHASE 8
