@@ -830,6 +830,9 @@ NARROW_1D_CASES = [
     dict(equation="biharmonic", nx=200, bc="ss", nt=64, T=0.01),
     dict(equation="linear_ch", nx=256, bc="neumann", eps=0.05, beta=0.5, nt=64, T=0.01),
     dict(equation="linear_ch", nx=300, bc="neumann", eps=0.05, beta=0.5, nt=64, T=0.01),   # wide tile
+    dict(equation="linear_ch", nx=2, bc="neumann", eps=0.05, beta=0.5, nt=128, T=0.01),     # 64-level tiles
+    dict(equation="biharmonic", nx=3, bc="ss", nt=8, T=1e-3),
+    dict(equation="linear_ch", nx=3, bc="neumann_v", eps=0.05, beta=0.5, nt=16, T=0.01, theta=0.5),
 ]
 
 
