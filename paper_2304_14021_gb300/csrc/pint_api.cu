@@ -1343,8 +1343,9 @@ static int gmres_window(pint_handle* h, double* U, const double* u0w) {
     return PINT_OK;
 }
 
-int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* st) {
-    if (!h || !u0_dev || !U_dev) return PINT_EINVAL;
+// The solve; with U_host, the device-to-host copy of the result is queued
+// before the final synchronization, so it needs no round trip of its own.
+static int solve_impl(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* st, double* U_host) {
     PINT_CK(cudaSetDevice(h->device));
     const pint_problem& p = h->p;
     const Geo& g = h->geo;
@@ -1357,6 +1358,7 @@ int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* 
     memset(&S, 0, sizeof(S));
     S.nt_min = ntmax;
     int rc = PINT_OK;
+    bool converted = false;   // float-float result already converted to U_dev
     activate_level(h, 0);
     // Cahn-Hilliard never starts from the zero iterate: its scalar Jacobian
     // 3 mean(u^2) would be 0 in the first preconditioner, far from the state's,
@@ -1412,6 +1414,14 @@ int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* 
                 // one graph launch runs the iteration loop of this window to its stop
                 if (init == 2 && zero_start(h, Useg, u0w) != cudaSuccess) return PINT_ECUDA;
                 PINT_CK(cudaGraphLaunch(gx, h->st));
+                if (ffm && done + L >= total) {
+                    // the last window: queue the result's conversion (and copy) ahead of the
+                    // status read, so that one synchronization covers all of it
+                    launch_ff_to_f64(h->Uff, U_dev, dof, h->st);
+                    h->launches[PH_SETUP] += 1;
+                    converted = true;
+                    if (U_host) PINT_CK(cudaMemcpyAsync(U_host, U_dev, dof * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+                }
                 if ((rc = read_ctl(h)) != PINT_OK) return rc;
                 if (h->hctl->status == ST_RUNNING) return PINT_ECUDA;  // the loop ends only on a final status
                 const long long runs = h->hctl->iter + 1 - (init == 2 ? 1 : 0);
@@ -1475,13 +1485,21 @@ int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* 
     }
     activate_level(h, 0);
     h->Uff_cur = h->Uff;
-    if (ffm) {
-        launch_ff_to_f64(h->Uff, U_dev, dof, h->st);
-        h->launches[PH_SETUP] += 1;
-        PINT_CK(cudaStreamSynchronize(h->st));
+    if (!converted) {
+        if (ffm) {
+            launch_ff_to_f64(h->Uff, U_dev, dof, h->st);
+            h->launches[PH_SETUP] += 1;
+        }
+        if (U_host) PINT_CK(cudaMemcpyAsync(U_host, U_dev, dof * sizeof(double), cudaMemcpyDeviceToHost, h->st));
     }
+    PINT_CK(cudaStreamSynchronize(h->st));
     if (st) *st = S;
     return rc;
+}
+
+int pint_solve(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* st) {
+    if (!h || !u0_dev || !U_dev) return PINT_EINVAL;
+    return solve_impl(h, u0_dev, U_dev, st, nullptr);
 }
 
 int pint_solve_batch(pint_handle* const* hs, int n, const double* const* u0s, double* const* Us, pint_stats* st,
@@ -1517,11 +1535,7 @@ int pint_solve_host(pint_handle* h, const double* u0_host, double* U_host, pint_
     PINT_CK(cudaMemcpyAsync(h->hu0, u0_host, ns * sizeof(double), cudaMemcpyHostToDevice, h->st));
     if (h->p.init_guess == 1)
         PINT_CK(cudaMemcpyAsync(h->hU, U_host, dof * sizeof(double), cudaMemcpyHostToDevice, h->st));
-    int rc = pint_solve(h, h->hu0, h->hU, st);
-    if (rc != PINT_OK && rc != PINT_ENOCONV && rc != PINT_EDIVERGED) return rc;
-    PINT_CK(cudaMemcpyAsync(U_host, h->hU, dof * sizeof(double), cudaMemcpyDeviceToHost, h->st));
-    PINT_CK(cudaStreamSynchronize(h->st));
-    return rc;
+    return solve_impl(h, h->hu0, h->hU, st, U_host);
 }
 
 int pint_residual(pint_handle* h, const double* u0_dev, const double* U_dev, double* r_dev, double* rel_res) {
