@@ -62,7 +62,6 @@ Readings of the paper taken here:
 """
 from __future__ import annotations
 
-import math
 from dataclasses import dataclass, field
 
 import numpy as np
