@@ -66,7 +66,15 @@ typedef enum { PINT_BC_SIMPLY_SUPPORTED = 0, PINT_BC_NEUMANN = 1, PINT_BC_NEUMAN
 /* PINT_FP64:     every step in FP64 (the plain form).
  * PINT_MIXED:    residual, alpha-scaling, unscaling and the update in FP64; the
  *                time FFTs and the spatial shifted solves in FP32 / complex64, so
- *                the outer iteration is an iterative refinement.
+ *                the outer iteration is an iterative refinement.  For the linear
+ *                equations on square cells (and in 1-D) the residual and its
+ *                alpha-scaling run on the integer pipes in block fixed point: the
+ *                FP64 iterate is converted per tile and time level to 64-bit integers
+ *                in a common binary unit, the stencil sums are exact, and the
+ *                products with the coefficients and with gamma_n/dt use their full
+ *                53-bit mantissas, so every rounding lies below 2^-56 of the largest
+ *                term (finer than the same sums in FP64); the scaled residual is
+ *                rounded once to FP32 (see PINT_OPT_FX_RESIDUAL).
  * PINT_MIXED_FF: as PINT_MIXED, but the iterate and the residual are kept in
  *                float-float (two FP32 words, about 48 significant bits, error-free
  *                stencil sums) on the FP32 pipes, and the alpha-scaling/unscaling is
@@ -170,8 +178,9 @@ int pint_solve_host(pint_handle* h, const double* u0_host, double* U_host, pint_
 
 /* All-at-once residual of one window (Eq. 2.6 / Eq. 4.8 with alpha = 0):
  * r = b - K(U), b = (u0/dt, 0, ..., 0).  r_dev (nt*nx*ny doubles) may be NULL;
- * *rel_res (may be NULL) receives ||r||_2 / ||b||_2.  Computed in FP64 in
- * both precisions. */
+ * *rel_res (may be NULL) receives ||r||_2 / ||b||_2.  Computed in FP64
+ * arithmetic, or on a PINT_MIXED handle with PINT_OPT_FX_RESIDUAL in exact
+ * block fixed point with FP64-accurate products; written in FP64. */
 int pint_residual(pint_handle* h, const double* u0_dev, const double* U_dev,
                   double* r_dev, double* rel_res);
 
@@ -243,6 +252,11 @@ int pint_profile_read(pint_handle* h, pint_profile* out, int reset);
  *    half spectra.  The iteration loop runs host-launched (no CUDA graph).
  *    Errors: PINT_EINVAL (value out of range, or a linear equation), PINT_ENOMEM. */
 #define PINT_OPT_VARYING_JACOBIAN 5
+/*  PINT_OPT_FX_RESIDUAL (default 1 where supported): on a PINT_MIXED handle of a
+ *    linear equation with square cells (or in 1-D), evaluate the residual (and
+ *    pint_residual) in block fixed point on the integer pipes; 0 = the FP64
+ *    residual kernel.  Errors: PINT_EINVAL for value 1 where it is not supported. */
+#define PINT_OPT_FX_RESIDUAL 6
 int pint_set_option(pint_handle* h, int option, long long value);
 
 /* pint_residual_static: the residual of pint_residual for callers that cannot

@@ -740,7 +740,12 @@ def thm_bound_biharmonic(alpha: float) -> float:
 def thm_bound_linear_ch(p: Problem, alpha: float | None = None) -> float:
     """Theorem 3.3 (theta = 1): rho = |alpha| R^{N_t}(z*) / (1 - |alpha| R^{N_t}(z*)),
     R(z*) = 1/(1 + phi(z*)), phi(z) = -beta^2 z + (eps^2/dt) z^2,
-    z* = beta^2 dt / (2 eps^2)."""
+    z* = beta^2 dt / (2 eps^2).  The theorem concerns the anti-diffusive
+    second-order term (beta^2 >= 0 in u_t = -beta^2 Lap u - eps^2 Lap^2 u);
+    under the signed reading (beta < 0 gives the diffusive term) its maximizer
+    z* does not exist, so beta < 0 is rejected."""
+    if p.beta < 0:
+        raise ValueError("Theorem 3.3 bound is defined for beta >= 0 only")
     alpha = p.alpha if alpha is None else alpha
     zs = p.beta ** 2 * p.dt / (2 * p.eps ** 2)
     phi = -p.beta ** 2 * zs + (p.eps ** 2 / p.dt) * zs ** 2

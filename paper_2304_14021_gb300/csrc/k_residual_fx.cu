@@ -1,0 +1,344 @@
+// k_residual_fx.cu - the all-at-once residual of the linear equations in
+// block fixed point on the integer pipes, FP64-accurate, for PINT_MIXED.
+//
+// Residual (Eq. 2.6 with alpha = 0; theta-method of Eq. 2.5, theta = 1 or 1/2),
+// evaluated scaled by dt:
+//   dt r_n = u_{n-1} - u_n - theta dt A(u_n) - (1 - theta) dt A(u_{n-1}),
+//   A(u) = c2 Lap^2 u + c1 Lap u     (biharmonic: c1 = 0; linearized CH: c1 = beta|beta|, c2 = eps^2),
+// on square cells (and every 1-D grid), where h^2 Lap and h^4 Lap^2 have
+// integer stencils.  Each time level of a CTA's tile (halo 2, boundary
+// conditions as reflections, as in k_residual.cu) is converted from the FP64
+// iterate to 64-bit integers in the tile's unit 2^(E-56), E the tile's
+// largest binary exponent, so both Laplacian passes are exact integer sums.
+// The products with dt c1/h^2 and dt c2/h^4 use the coefficients' full
+// 53-bit mantissas (fx.cuh); the terms are aligned to the largest one's unit
+// and added exactly.  The result is then scaled by gamma_n/dt (Step 1's
+// alpha-scaling, again from the FP64 factor's full mantissa) and rounded once
+// to FP32, the input of the complex64 time transform.  Per CTA, the partial
+// sum of r^2 feeds the convergence check.
+//
+// ROUT (pint_residual): the residual itself is written in FP64 and its
+// square summed in FP64.
+#include "fx.cuh"
+#include "pint_common.cuh"
+#include "pint_kernels.h"
+
+namespace pint {
+
+template <int DIM> struct FxTile;
+template <> struct FxTile<1> { static constexpr int TX = 512, TY = 1, PPT = 2; };
+template <> struct FxTile<2> { static constexpr int TX = 32, TY = 16, PPT = 2; };
+constexpr int kFxThreads = 256;
+constexpr int kFxMinBlocks = 4;
+
+// Source of halo element (gx, gy) of a time level: its offset within the
+// level, or -1 for a zero (simply supported boundary vertex, or beyond the
+// grid); *neg = 1 when the reflection is odd.  Same rules as ext_read in
+// k_residual.cu.
+__device__ __forceinline__ int fx_src(int gx, int gy, int nx, int ny, int dim, int bc, uint32_t* neg) {
+    uint32_t s = 0;
+    if (bc == 1) {
+        if (gx < 0) gx = -1 - gx;
+        else if (gx >= nx) gx = 2 * nx - 1 - gx;
+        if (dim == 2) {
+            if (gy < 0) gy = -1 - gy;
+            else if (gy >= ny) gy = 2 * ny - 1 - gy;
+        }
+    } else if (bc == 2) {
+        if (gx < 0) gx = -gx;
+        else if (gx >= nx) gx = 2 * (nx - 1) - gx;
+        if (dim == 2) {
+            if (gy < 0) gy = -gy;
+            else if (gy >= ny) gy = 2 * (ny - 1) - gy;
+        }
+    } else {
+        if (gx == -1 || gx == nx) return -1;
+        if (gx < -1) { gx = -2 - gx; s ^= 1u; }
+        else if (gx > nx) { gx = 2 * nx - gx; s ^= 1u; }
+        if (dim == 2) {
+            if (gy == -1 || gy == ny) return -1;
+            if (gy < -1) { gy = -2 - gy; s ^= 1u; }
+            else if (gy > ny) { gy = 2 * ny - gy; s ^= 1u; }
+        }
+    }
+    if (gx < 0 || gx >= nx || (dim == 2 && (gy < 0 || gy >= ny))) return -1;
+    *neg = s << 31;
+    return (dim == 2 ? gy * nx : 0) + gx;
+}
+
+// Unscaled Laplacian stencil (3 or 5 points) at index c of an integer tile with row stride sx.
+template <int DIM>
+__device__ __forceinline__ int64_t fx_lap(const int64_t* __restrict__ a, int c, int sx) {
+    if constexpr (DIM == 2) return a[c - 1] + a[c + 1] + a[c - sx] + a[c + sx] - 4 * a[c];
+    else return a[c - 1] + a[c + 1] - 2 * a[c];
+}
+
+template <int DIM, bool HALF, bool ROUT>
+__global__ void __launch_bounds__(kFxThreads, kFxMinBlocks)
+    k_residual_fx(GeoFX g, const double* __restrict__ U, const double* __restrict__ u0,
+                  const double* __restrict__ gdt, const float* __restrict__ igamf, float* __restrict__ s_out,
+                  double* __restrict__ r_out, double* __restrict__ partials, const Ctl* __restrict__ ctl, int chunk) {
+    pdl_wait();
+    if (ctl && ctl->status != ST_RUNNING) return;
+    constexpr int TX = FxTile<DIM>::TX, TY = FxTile<DIM>::TY, PPT = FxTile<DIM>::PPT;
+    constexpr int NTHR = kFxThreads, NW = NTHR / 32;
+    constexpr int RSTEP = DIM == 2 ? TY / PPT : 0, XSTEP = DIM == 2 ? 0 : TX / PPT;
+    constexpr int HY = DIM == 2 ? 2 : 0;
+    constexpr int SX = TX + 4, SY = TY + 2 * HY;
+    constexpr int LX = TX + 2, LY = TY + (DIM == 2 ? 2 : 0);
+    constexpr int NST = (SX * SY + NTHR - 1) / NTHR, NLP = (LX * LY + NTHR - 1) / NTHR;
+    __shared__ int64_t sfx[2][SY * SX];
+    __shared__ int64_t sL[2][LY * LX];
+    __shared__ int smax[2][NW];
+    __shared__ double red[NW];
+
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    const int tx = tid % (DIM == 2 ? TX : TX / PPT), ty = tid / (DIM == 2 ? TX : TX / PPT);
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int n0 = blockIdx.z * chunk;
+    const int n1 = min(g.nt, n0 + chunk);
+    const int nfirst = HALF ? n0 - 1 : n0;
+
+    // staging map (fixed for all levels): this thread loads elements tid + a NTHR
+    int goff[NST];
+    uint32_t gneg[NST];
+#pragma unroll
+    for (int a = 0; a < NST; ++a) {
+        const int e = tid + a * NTHR;
+        goff[a] = -1;
+        gneg[a] = 0;
+        if (e < SX * SY) goff[a] = fx_src(x0 - 2 + e % SX, y0 - HY + e / SX, g.nx, g.ny, DIM, g.bc, &gneg[a]);
+    }
+    int lc[NLP];
+#pragma unroll
+    for (int a = 0; a < NLP; ++a) {
+        const int e = tid + a * NTHR;
+        lc[a] = e < LX * LY ? (DIM == 2 ? (e / LX + 1) * SX : 0) + e % LX + 1 : -1;
+    }
+    uint32_t rhi[NST], rlo[NST];
+    auto load = [&](int n) {
+        const double* un = n < 0 ? u0 : U + (size_t)n * g.nspace;
+#pragma unroll
+        for (int a = 0; a < NST; ++a) {
+            if (goff[a] >= 0) {
+                const unsigned long long v = __ldg(reinterpret_cast<const unsigned long long*>(un + goff[a]));
+                rhi[a] = (uint32_t)(v >> 32) ^ gneg[a];
+                rlo[a] = (uint32_t)v;
+            } else {
+                rhi[a] = 0u;
+                rlo[a] = 0u;
+            }
+        }
+    };
+    auto expmax = [&]() {
+        int f = 0;
+#pragma unroll
+        for (int a = 0; a < NST; ++a) f = max(f, fx_expfield(rhi[a]));
+        return (int)__reduce_max_sync(0xffffffffu, (unsigned)f);
+    };
+
+    int cu[PPT], cl[PPT];
+    bool inside[PPT];
+    size_t po[PPT];
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        const int lx = tx + q * XSTEP, ly = ty + q * RSTEP;
+        const int gx = x0 + lx, gy = y0 + ly;
+        inside[q] = gx < g.nx && (DIM == 1 || gy < g.ny);
+        po[q] = (size_t)(DIM == 2 ? gy * g.nx : 0) + gx;
+        cu[q] = (ly + HY) * SX + lx + 2;
+        cl[q] = (DIM == 2 ? (ly + 1) * LX : 0) + lx + 1;
+    }
+    // previous level per point, in its own unit 2^(Ep-56) (theta = 1/2: with its two Laplacians)
+    int64_t up[PPT], L1p[PPT], L2p[PPT];
+    int Ep[PPT];
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        up[q] = L1p[q] = L2p[q] = 0;
+        Ep[q] = -1022;
+        if (!HALF && inside[q]) {
+            const double* src = n0 == 0 ? u0 : U + (size_t)(n0 - 1) * g.nspace;
+            const unsigned long long v = __ldg(reinterpret_cast<const unsigned long long*>(src + po[q]));
+            const uint32_t hi = (uint32_t)(v >> 32);
+            Ep[q] = fx_tile_exp(max(fx_expfield(hi), 1));
+            up[q] = fx_from_f64(hi, (uint32_t)v, Ep[q]);
+        }
+    }
+
+    if (n0 < n1) {
+        load(nfirst);
+        const int f = expmax();
+        if (lane == 0) smax[0][warp] = f;
+    }
+    __syncthreads();
+    float acc = 0.f;
+    double accd = 0.0;
+    for (int n = nfirst; n < n1; ++n) {
+        const int b = (n - nfirst) & 1;
+        int fmax = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) fmax = max(fmax, smax[b][w]);
+        const bool bad = fmax == 0x7FF;   // an infinity or NaN in the tile
+        const int E = fx_tile_exp(max(fmax, 1));
+#pragma unroll
+        for (int a = 0; a < NST; ++a)
+            if (tid + a * NTHR < SX * SY) sfx[b][tid + a * NTHR] = fx_from_f64(rhi[a], rlo[a], E);
+        if (n + 1 < n1) load(n + 1);
+        __syncthreads();
+#pragma unroll
+        for (int a = 0; a < NLP; ++a)
+            if (lc[a] >= 0) sL[b][tid + a * NTHR] = fx_lap<DIM>(sfx[b], lc[a], SX);
+        if (n + 1 < n1) {
+            const int f = expmax();
+            if (lane == 0) smax[b ^ 1][warp] = f;
+        }
+        __syncthreads();
+        uint64_t gm = 0;
+        int gq = 0;
+        float ig = 0.f;
+        if (!ROUT && n >= n0) {
+            fx_align(__double_as_longlong(gdt[n]), gm, gq);
+            ig = igamf[n];
+        }
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+            if (!inside[q]) continue;
+            const int64_t L1 = sL[b][cl[q]];
+            const int64_t L2 = fx_lap<DIM>(sL[b], cl[q], LX);
+            const int64_t un = sfx[b][cu[q]];
+            if (HALF && n < n0) {
+                up[q] = un;
+                L1p[q] = L1;
+                L2p[q] = L2;
+                Ep[q] = E;
+                continue;
+            }
+            const int Em = max(E, Ep[q]);
+            // (u_{n-1} - u_n) in unit 2^(Em-59)
+            const int64_t D3 = (fx_shr(up[q], Em - Ep[q]) - fx_shr(un, Em - E)) * 8;
+            const int XD = Em - 59;
+            int64_t L1s = L1, L2s = L2;
+            int Ek = E;
+            if constexpr (HALF) {
+                L1s = fx_shr(L1, Em - E) + fx_shr(L1p[q], Em - Ep[q]);
+                L2s = fx_shr(L2, Em - E) + fx_shr(L2p[q], Em - Ep[q]);
+                Ek = Em;
+            }
+            const int64_t P2 = fx_mul(L2s, g.k2);
+            const int X2 = g.k2.q + Ek - 1;
+            const int64_t P1 = fx_mul(L1s, g.k1);
+            const int X1 = g.k1.q + Ek - 1;
+            int X = max(XD, X2);
+            if (g.lin1) X = max(X, X1);
+            int64_t R = fx_shr(D3, X - XD);
+            const int64_t t2 = fx_shr(P2, X - X2);
+            R -= g.k2.neg ? -t2 : t2;
+            if (g.lin1) {
+                const int64_t t1 = fx_shr(P1, X - X1);
+                R -= g.k1.neg ? -t1 : t1;
+            }
+            const size_t o = (size_t)n * g.nspace + po[q];
+            if constexpr (ROUT) {
+                const double r = bad ? __longlong_as_double(0x7FF8000000000000ll) : ldexp((double)R, X) * g.inv_dt;
+                if (r_out) r_out[o] = r;
+                accd = fma(r, r, accd);
+            } else {
+                const float sv = bad ? __int_as_float(0x7FC00000) : fx_to_f32_scaled(R, X, gm, gq);
+                s_out[o] = sv;
+                const float rv = sv * ig;
+                acc = fmaf(rv, rv, acc);
+            }
+            up[q] = un;
+            Ep[q] = E;
+            if constexpr (HALF) {
+                L1p[q] = L1;
+                L2p[q] = L2;
+            }
+        }
+    }
+    // deterministic block reduction of sum r^2 (sum u^2 is not needed for the linear equations)
+    double a = warp_sum(ROUT ? accd : (double)acc);
+    if (lane == 0) red[warp] = a;
+    __syncthreads();
+    if (tid == 0) {
+        double A = 0.0;
+        for (int w = 0; w < NW; ++w) A += red[w];
+        const size_t cta = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        partials[2 * cta] = A;
+        partials[2 * cta + 1] = 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+static FxCoef fx_coef(double c) {
+    FxCoef k{0u, 0u, 0, 0};
+    if (c == 0.0) return k;
+    k.neg = c < 0.0;
+    int e;
+    const double f = frexp(fabs(c), &e);
+    const uint64_t m = (uint64_t)ldexp(f, 53);
+    k.mh = (uint32_t)(m >> 32);
+    k.ml = (uint32_t)m;
+    k.q = e - 53;
+    return k;
+}
+
+int residual_fx_supported(const Geo& g) {
+    return g.cN == 0.0 && !g.expl && (g.dim == 1 || g.ihx2 == g.ihy2) && (g.th == 1.0 || g.th == 0.5);
+}
+
+GeoFX make_geo_fx(const Geo& g) {
+    GeoFX f{};
+    f.nx = g.nx;
+    f.ny = g.ny;
+    f.dim = g.dim;
+    f.bc = g.bc;
+    f.nt = g.nt;
+    f.nspace = g.nspace;
+    f.half = g.th < 1.0 ? 1 : 0;
+    f.inv_dt = g.inv_dt;
+    // dt theta c / h^2 and dt theta c2 / h^4 (theta = 1/2 is a power of two: exact)
+    f.k1 = fx_coef(g.dt * g.th * g.c1 * g.ihx2);
+    f.k2 = fx_coef(g.dt * g.th * g.c2 * g.ihx2 * g.ihx2);
+    f.lin1 = g.c1 != 0.0 ? 1 : 0;
+    return f;
+}
+
+int residual_fx_grid(const Geo& g, int& gx, int& gy, int& gz, int& chunk) {
+    const int TX = g.dim == 2 ? FxTile<2>::TX : FxTile<1>::TX, TY = g.dim == 2 ? FxTile<2>::TY : 1;
+    gx = (g.nx + TX - 1) / TX;
+    gy = g.dim == 2 ? (g.ny + TY - 1) / TY : 1;
+    const long tiles = (long)gx * gy;
+    // one wave of 152 SMs x the kernel's resident CTAs, split over time
+    long want = (152L * kFxMinBlocks) / tiles;
+    if (want < 1) want = 1;
+    chunk = (int)((g.nt + want - 1) / want);
+    if (chunk < 4) chunk = 4;
+    if (chunk > g.nt) chunk = g.nt;
+    gz = (g.nt + chunk - 1) / chunk;
+    return gx * gy * gz;
+}
+
+cudaError_t launch_residual_fx(const GeoFX& f, const Geo& g, const double* U, const double* u0, const double* gdt,
+                               const float* igamf, float* s, double* r_out, double* partials, const Ctl* ctl,
+                               cudaStream_t st, int rout_mode) {
+    int gx, gy, gz, chunk;
+    residual_fx_grid(g, gx, gy, gz, chunk);
+    const dim3 grid(gx, gy, gz), blk(kFxThreads);
+#define PINT_RFX(D, H, R)                                                                                    \
+    return launch_pdl(k_residual_fx<D, H, R>, grid, blk, 0, st, f, U, u0, gdt, igamf, s, r_out, partials, ctl, \
+                      chunk)
+    const bool rout = rout_mode != 0;
+    if (g.dim == 2) {
+        if (rout) { if (f.half) PINT_RFX(2, true, true); else PINT_RFX(2, false, true); }
+        else { if (f.half) PINT_RFX(2, true, false); else PINT_RFX(2, false, false); }
+    } else {
+        if (rout) { if (f.half) PINT_RFX(1, true, true); else PINT_RFX(1, false, true); }
+        else { if (f.half) PINT_RFX(1, true, false); else PINT_RFX(1, false, false); }
+    }
+#undef PINT_RFX
+}
+
+}  // namespace pint

@@ -150,6 +150,10 @@ struct pint_handle {
     double* dpart = nullptr;        // per-CTA (sum delta^2, sum U^2) of the last correction
     double* gam = nullptr;          // alpha^{n/nt}
     double* ginv = nullptr;         // alpha^{-n/nt} / nt
+    double* gdt = nullptr;          // PINT_MIXED: gamma_n / dt (the alpha-scaling of the fixed-point residual)
+    float* igamf = nullptr;         // PINT_MIXED: 1 / gamma_n (its norm partials)
+    pint::GeoFX gfx;                // block fixed-point residual geometry
+    int use_fx = 0;                 // PINT_MIXED with the block fixed-point residual (linear, square cells)
     double* u0buf = nullptr;        // window initial condition
     double* b1 = nullptr;           // theta < 1: first right-hand-side level u0/dt - (1-theta) A u0
     double* hU = nullptr;           // pint_solve_host buffers (lazy)
@@ -195,6 +199,8 @@ struct pint_handle {
         double* ginv = nullptr;
         float* gamf = nullptr;
         float* ginvf = nullptr;
+        double* gdt = nullptr;
+        float* igamf = nullptr;
         void* block = nullptr;       // device block owning this level's tables (levels >= 1)
     } lev[11];
     int nlev = 0;
@@ -340,6 +346,14 @@ static int build_tables(pint_handle* h) {
     }
     if (cudaMemcpyAsync(h->gam, g.data(), nt * sizeof(double), cudaMemcpyHostToDevice, h->st) != cudaSuccess) return PINT_ECUDA;
     if (cudaMemcpyAsync(h->ginv, gi.data(), nt * sizeof(double), cudaMemcpyHostToDevice, h->st) != cudaSuccess) return PINT_ECUDA;
+    if (h->gdt) {
+        std::vector<double> gd(nt);
+        std::vector<float> ig(nt);
+        for (int n = 0; n < nt; ++n) { gd[n] = g[n] * h->geo.inv_dt; ig[n] = (float)(1.0 / g[n]); }
+        if (cudaMemcpyAsync(h->gdt, gd.data(), nt * sizeof(double), cudaMemcpyHostToDevice, h->st) != cudaSuccess ||
+            cudaMemcpyAsync(h->igamf, ig.data(), nt * sizeof(float), cudaMemcpyHostToDevice, h->st) != cudaSuccess)
+            return PINT_ECUDA;
+    }
     if (h->gamf) {
         std::vector<float> gf(nt), gif(nt);
         for (int n = 0; n < nt; ++n) { gf[n] = (float)g[n]; gif[n] = (float)gi[n]; }
@@ -364,7 +378,7 @@ static int build_levels(pint_handle* h) {
         auto& lv = h->lev[h->nlev];
         const size_t nk = L / 2 + 1;
         const size_t tbytes = (2 * L + 4 * nk) * sizeof(T);
-        const size_t bytes = tbytes + 2 * L * sizeof(double) + 2 * L * sizeof(float) + 256;
+        const size_t bytes = tbytes + 3 * L * sizeof(double) + 3 * L * sizeof(float) + 256;
         if (cudaMallocAsync(&lv.block, bytes, h->st) != cudaSuccess) { cudaGetLastError(); return PINT_ENOMEM; }
         h->bytes += (long long)bytes;
         std::vector<T> t(2 * L + 4 * nk);
@@ -378,22 +392,27 @@ static int build_levels(pint_handle* h) {
             t[2 * L + 2 * nk + 2 * k] = (T)l2.real();
             t[2 * L + 2 * nk + 2 * k + 1] = (T)l2.imag();
         }
-        std::vector<double> g(L), gi(L);
-        std::vector<float> gf(L), gif(L);
+        std::vector<double> g(L), gi(L), gd(L);
+        std::vector<float> gf(L), gif(L), ig(L);
         for (int n = 0; n < L; ++n) {
             g[n] = pow(p->alpha, (double)n / L);
             gi[n] = pow(p->alpha, -(double)n / L) / L;
             gf[n] = (float)g[n];
             gif[n] = (float)gi[n];
+            gd[n] = g[n] * h->geo.inv_dt;
+            ig[n] = (float)(1.0 / g[n]);
         }
         char* b = reinterpret_cast<char*>(lv.block);
         const size_t o_g = (tbytes + 15) / 16 * 16, o_gi = o_g + L * sizeof(double), o_gf = o_gi + L * sizeof(double),
-                     o_gif = o_gf + L * sizeof(float);
+                     o_gif = o_gf + L * sizeof(float), o_gd = (o_gif + L * sizeof(float) + 15) / 16 * 16,
+                     o_ig = o_gd + L * sizeof(double);
         if (cudaMemcpyAsync(b, t.data(), tbytes, cudaMemcpyHostToDevice, h->st) != cudaSuccess ||
             cudaMemcpyAsync(b + o_g, g.data(), L * sizeof(double), cudaMemcpyHostToDevice, h->st) != cudaSuccess ||
             cudaMemcpyAsync(b + o_gi, gi.data(), L * sizeof(double), cudaMemcpyHostToDevice, h->st) != cudaSuccess ||
             cudaMemcpyAsync(b + o_gf, gf.data(), L * sizeof(float), cudaMemcpyHostToDevice, h->st) != cudaSuccess ||
-            cudaMemcpyAsync(b + o_gif, gif.data(), L * sizeof(float), cudaMemcpyHostToDevice, h->st) != cudaSuccess)
+            cudaMemcpyAsync(b + o_gif, gif.data(), L * sizeof(float), cudaMemcpyHostToDevice, h->st) != cudaSuccess ||
+            cudaMemcpyAsync(b + o_gd, gd.data(), L * sizeof(double), cudaMemcpyHostToDevice, h->st) != cudaSuccess ||
+            cudaMemcpyAsync(b + o_ig, ig.data(), L * sizeof(float), cudaMemcpyHostToDevice, h->st) != cudaSuccess)
             return PINT_ECUDA;
         Tabs<T>* tb = new (std::nothrow) Tabs<T>(*base);
         if (!tb) return PINT_ENOMEM;
@@ -407,6 +426,8 @@ static int build_levels(pint_handle* h) {
         lv.ginv = reinterpret_cast<double*>(b + o_gi);
         lv.gamf = reinterpret_cast<float*>(b + o_gf);
         lv.ginvf = reinterpret_cast<float*>(b + o_gif);
+        lv.gdt = reinterpret_cast<double*>(b + o_gd);
+        lv.igamf = reinterpret_cast<float*>(b + o_ig);
         h->nlev++;
     }
     return PINT_OK;
@@ -422,6 +443,9 @@ static void activate_level(pint_handle* h, int li) {
     h->ginv = lv.ginv;
     h->gamf = lv.gamf;
     h->ginvf = lv.ginvf;
+    h->gdt = lv.gdt;
+    h->igamf = lv.igamf;
+    h->gfx.nt = lv.nt;
 }
 
 static void derive(const pint_problem* p, pint_handle* h) {
@@ -474,6 +498,7 @@ static void derive(const pint_problem* p, pint_handle* h) {
     const double lam_max = 4.0 * g.ihx2 + (g.dim == 2 ? 4.0 * g.ihy2 : 0.0);
     const double mu_max = g.c2 * lam_max * lam_max + (fabs(g.c1) + 2.0 * fabs(g.cN)) * lam_max;
     f.accurate = g.dt * mu_max > 1e7 ? 1 : 0;
+    h->gfx = make_geo_fx(g);
 }
 
 static Sizes sizes_of(const pint_problem* p, pint_handle* tmp) {
@@ -485,8 +510,9 @@ static Sizes sizes_of(const pint_problem* p, pint_handle* tmp) {
     int gx, gy, gz, chunk;
     const int nres = residual_grid(tmp->geo, gx, gy, gz, chunk);
     const int nff = residual_ff_grid(tmp->geo, gx, gy, gz, chunk);
+    const int nfx = residual_fx_grid(tmp->geo, gx, gy, gz, chunk);
     const int nn = norm2_blocks((int)z.nspace);
-    z.partials = (size_t)std::max(nres, std::max(nff, nn));
+    z.partials = (size_t)std::max(std::max(nres, nfx), std::max(nff, nn));
     TabLayout L = tab_layout(p, tmp->fft_x, tmp->fft_y);
     z.tables_T = L.total;
     const size_t ts = f32_transforms(p) ? 4 : 8;
@@ -510,6 +536,7 @@ static long long footprint_of(const pint_problem* p) {
     b += z.nk * z.nspace * 2 * ts;   // S
     b += z.tables_bytes;
     if (p->precision == PINT_MIXED_FF) b += z.dof * 8 + z.nspace * 8 + 2 * (size_t)p->nt * 4;
+    if (p->precision == PINT_MIXED) b += (size_t)p->nt * (sizeof(double) + sizeof(float));
     return b;
 }
 
@@ -707,10 +734,18 @@ template <class T> struct Impl {
         c_t<T>* S = reinterpret_cast<c_t<T>*>(h->S);
         const Tabs<T>& tb = tabs_of<T>(h);
         prof_begin(h, PH_RES);
-        launch_residual<T>(g, U, u0w, h->gam, nullptr, s, h->partials, h->ctl, h->st);
+        int gx, gy, gz, chunk, np;
+        if (std::is_same<T, float>::value && h->use_fx) {
+            // FP64-accurate residual and alpha-scaling in block fixed point (integer pipes)
+            cudaError_t e = launch_residual_fx(h->gfx, g, U, u0w, h->gdt, h->igamf, reinterpret_cast<float*>(s),
+                                               nullptr, h->partials, h->ctl, h->st, 0);
+            if (e != cudaSuccess) return e;
+            np = residual_fx_grid(g, gx, gy, gz, chunk);
+        } else {
+            launch_residual<T>(g, U, u0w, h->gam, nullptr, s, h->partials, h->ctl, h->st);
+            np = residual_grid(g, gx, gy, gz, chunk);
+        }
         prof_end(h, PH_RES, 1);
-        int gx, gy, gz, chunk;
-        const int np = residual_grid(g, gx, gy, gz, chunk);
         prof_begin(h, PH_CHECK);
         launch_after_residual(h->partials, np, 1.0 / ((double)g.nt * g.nspace), h->ctl, h->st, h->gcond, h->capturing,
                               upd_part(h), upd_part(h) ? time_inv_blocks(g.nt, g.nspace, f32_transforms(&h->p)) : 0);
@@ -999,6 +1034,8 @@ void pint_destroy(pint_handle* h) {
     }
     af(h->gam);
     af(h->ginv);
+    af(h->gdt);
+    af(h->igamf);
     af(h->u0buf);
     af(h->b1);
     af(h->hU);
@@ -1061,6 +1098,11 @@ int pint_create(const pint_problem* p, void* cuda_stream, pint_handle** out) {
     if (!rc) rc = dalloc(&h->s, z.dof * ts);
     if (!rc) rc = dalloc(&h->S, z.nk * z.nspace * 2 * ts);
     if (!rc) rc = dalloc(&h->tab, z.tables_bytes);
+    if (!rc && p->precision == PINT_MIXED) {
+        rc = dalloc((void**)&h->gdt, p->nt * sizeof(double));
+        if (!rc) rc = dalloc((void**)&h->igamf, p->nt * sizeof(float));
+        h->use_fx = residual_fx_supported(h->geo);
+    }
     if (!rc && p->precision == PINT_MIXED_FF) {
         rc = dalloc((void**)&h->Uff, z.dof * sizeof(float2));
         if (!rc) rc = dalloc((void**)&h->u0ff, z.nspace * sizeof(float2));
@@ -1081,6 +1123,8 @@ int pint_create(const pint_problem* p, void* cuda_stream, pint_handle** out) {
     h->lev[0].ginv = h->ginv;
     h->lev[0].gamf = h->gamf;
     h->lev[0].ginvf = h->ginvf;
+    h->lev[0].gdt = h->gdt;
+    h->lev[0].igamf = h->igamf;
     h->nlev = 1;
     h->Uff_cur = h->Uff;
     {
@@ -1119,6 +1163,13 @@ int pint_set_option(pint_handle* h, int option, long long value) {
         case PINT_OPT_GRAPHS:
             if (value != 0 && value != 1) return PINT_EINVAL;
             h->use_graphs = (int)value;
+            return PINT_OK;
+        case PINT_OPT_FX_RESIDUAL:
+            if (value != 0 && value != 1) return PINT_EINVAL;
+            if (value && !(h->p.precision == PINT_MIXED && residual_fx_supported(h->geo))) return PINT_EINVAL;
+            h->use_fx = (int)value;
+            for (auto& sl : h->gslot)   // captured loops hold the old kernel choice
+                if (sl.exec) { cudaGraphExecDestroy(sl.exec); sl.exec = nullptr; }
             return PINT_OK;
         case PINT_OPT_FUSED_SPATIAL:
             if (value != 0 && value != 1) return PINT_EINVAL;
@@ -1542,9 +1593,15 @@ int pint_residual(pint_handle* h, const double* u0_dev, const double* U_dev, dou
     if (!h || !u0_dev || !U_dev) return PINT_EINVAL;
     const Geo& g = h->geo;
     launch_begin_window(g, u0_dev, h->p.max_iter, h->p.tol, h->partials, h->ctl, h->st);
-    launch_residual<double>(g, U_dev, u0_dev, h->gam, r_dev, nullptr, h->partials, nullptr, h->st);
-    int gx, gy, gz, chunk;
-    const int np = residual_grid(g, gx, gy, gz, chunk);
+    int gx, gy, gz, chunk, np;
+    if (h->use_fx) {
+        PINT_CK(launch_residual_fx(h->gfx, g, U_dev, u0_dev, nullptr, nullptr, nullptr, r_dev, h->partials, nullptr,
+                                   h->st, 1));
+        np = residual_fx_grid(g, gx, gy, gz, chunk);
+    } else {
+        launch_residual<double>(g, U_dev, u0_dev, h->gam, r_dev, nullptr, h->partials, nullptr, h->st);
+        np = residual_grid(g, gx, gy, gz, chunk);
+    }
     launch_residual_norm(h->partials, np, h->ctl, h->st);
     PINT_CK(cudaGetLastError());
     int rc = read_ctl(h);

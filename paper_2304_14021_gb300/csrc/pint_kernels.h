@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include "fx.cuh"
 #include "pint_common.cuh"
 
 namespace pint {
@@ -44,6 +45,26 @@ struct GeoFF {
     int half;       // theta = 1/2: the residual also carries A'(u_{n-1})
     int expl;       // Eyre splitting: the c1 Laplacian term acts on u_{n-1}
 };
+
+// Geometry of the block fixed-point residual (k_residual_fx.cu): the products
+// theta dt c1 / h^2 and theta dt c2 / h^4 as exact mantissa / exponent pairs.
+struct GeoFX {
+    int nx, ny, dim, bc, nt, nspace;
+    int half;       // theta = 1/2: A(u_{n-1}) enters too
+    int lin1;       // c1 != 0 (the Laplacian term is present)
+    FxCoef k1, k2;
+    double inv_dt;
+};
+// Linear equations (no u^3 term), theta 1 or 1/2, square cells or 1-D.
+int residual_fx_supported(const Geo& g);
+GeoFX make_geo_fx(const Geo& g);
+int residual_fx_grid(const Geo& g, int& gx, int& gy, int& gz, int& chunk);
+// rout_mode 0: s = gamma_n r rounded to FP32 (gdt[n] = gamma_n / dt, igamf[n] = 1/gamma_n);
+// rout_mode 1: r in FP64 into r_out (may be nullptr: norm only; s, gdt, igamf unused).
+// Per-CTA (sum r^2, 0) pairs in partials.
+cudaError_t launch_residual_fx(const GeoFX& f, const Geo& g, const double* U, const double* u0, const double* gdt,
+                               const float* igamf, float* s, double* r_out, double* partials, const Ctl* ctl,
+                               cudaStream_t st, int rout_mode);
 
 // Factorization of a long time axis (N_t > 1024) for the multi-pass FFT of
 // k_timefft.cu: N_t = f_0 ... f_{S-1}, istr_s = prod_{j>s} f_j,

@@ -250,6 +250,12 @@ class Solver:
         if rc != PINT_OK:
             raise PintError(rc, "pint_set_option")
 
+    def set_fx_residual(self, on: bool = True) -> None:
+        """PINT_MIXED, linear equations: block fixed-point residual on the integer pipes (on) or FP64 kernel."""
+        rc = lib().pint_set_option(self._h, 6, 1 if on else 0)
+        if rc != PINT_OK:
+            raise PintError(rc, "pint_set_option")
+
     def set_adaptive_windows(self, on: bool = True) -> None:
         rc = lib().pint_set_option(self._h, 2, 1 if on else 0)
         if rc != PINT_OK:

@@ -277,6 +277,38 @@ def test_ch_mass_conserved_energy_decreasing_2d():
     assert E[-1] < E[0]
 
 
+@pytest.mark.parametrize("case", ["1d", "2d_x", "2d_y"])
+def test_discrete_energy_closed_form_cosine_mode(case):
+    # One cosine mode a cos(p pi x) on the cell-centred grid (h = 1/n, x_i = (i + 1/2) h) with 0 < 4p < 2n:
+    # sum_i cos^2 = n/2, sum_i cos^4 = 3n/8, and the face differences are
+    # -2a sin(p pi h/2) sin(p pi j/n), j = 1..n-1, whose squares sum to 2 n a^2 sin^2(p pi/(2n)).
+    # So the bulk part is (3a^4/8 - a^2 + 1)/4 and the gradient part eps^2 n^2 a^2 sin^2(p pi/(2n)),
+    # in 1-D and 2-D alike (a mode constant along the other axis), which fixes the weight between the
+    # two sums, the power of h, and the face sums of each axis.
+    n, pm, a, eps = 16, 3, 0.7, 0.05
+    x = (np.arange(n) + 0.5) / n
+    mode = a * np.cos(pm * np.pi * x)
+    if case == "1d":
+        p, u = P(equation=O.CAHN_HILLIARD, dim=1, nx=n, bc="neumann", eps=eps), mode
+    elif case == "2d_x":
+        p, u = P(equation=O.CAHN_HILLIARD, dim=2, nx=n, ny=n, bc="neumann", eps=eps), np.tile(mode, n)
+    else:
+        p, u = P(equation=O.CAHN_HILLIARD, dim=2, nx=n, ny=n, bc="neumann", eps=eps), np.repeat(mode, n)
+    bulk = (3 * a**4 / 8 - a**2 + 1) / 4
+    grad = eps**2 * n**2 * a**2 * np.sin(pm * np.pi / (2 * n)) ** 2
+    assert abs(O.discrete_energy(p, u) - (bulk + grad)) < 1e-14
+    # the constant states +-1 have zero energy; the constant 0 has h^d sum 1/4 = 1/4
+    assert abs(O.discrete_energy(p, np.ones(p.nspace))) < 1e-15
+    assert abs(O.discrete_energy(p, np.zeros(p.nspace)) - 0.25) < 1e-15
+
+
+def test_thm33_bound_rejects_negative_beta():
+    # Theorem 3.3's maximizer z* = beta^2 dt/(2 eps^2) belongs to the anti-diffusive term (beta >= 0)
+    with pytest.raises(ValueError):
+        O.thm_bound_linear_ch(P(equation=O.LINEAR_CH, dim=1, nx=16, bc="neumann", beta=-0.5, eps=0.05,
+                                T=0.1, nt=16))
+
+
 def test_ch_constant_state_is_stationary():
     p = P(equation=O.CAHN_HILLIARD, dim=2, nx=8, ny=8, bc="neumann", eps=0.02, T=1e-3, nt=5)
     u0 = np.full(64, 0.3)
