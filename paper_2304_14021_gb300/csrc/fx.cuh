@@ -82,6 +82,83 @@ FX_HD int64_t fx_mul(int64_t L, const FxCoef& c) {
     return L < 0 ? -(int64_t)P : (int64_t)P;
 }
 
+// floor(L M / 2^55) (to within one unit) for |L| < 2^62 and 0 <= M < 2^53,
+// M = mh 2^31 + ml (mh < 2^22, ml < 2^31): signed 32x32 products only, so no
+// absolute value or negation is needed.  L M = Lh mh 2^63 + (Lh ml 2^32 +
+// Ll mh 2^31 + Ll ml) with L = Lh 2^32 + Ll (Lh signed, Ll unsigned); the low
+// word of Ll ml is dropped before the final floor, which can lower the result
+// by one unit.  |result| < 2^60.
+FX_HD int64_t fx_mul_s(int64_t L, int32_t mh, int32_t ml) {
+    const int32_t Lh = (int32_t)(L >> 32);
+    const uint32_t Ll = (uint32_t)L;
+    const int64_t top = (int64_t)Lh * mh;                          // < 2^52
+    const int64_t W = (int64_t)Lh * ml;                            // |W| < 2^61
+    const uint64_t V = (uint64_t)Ll * (uint32_t)mh;                // < 2^54
+    const uint64_t Zh = fx_umulhi(Ll, (uint32_t)ml);               // floor(Ll ml / 2^32) < 2^31
+    // (Lh ml 2^32 + Ll mh 2^31 + Ll ml) / 2^55 = (2W + V + Ll ml / 2^31) / 2^24
+    const int64_t mid = 2 * W + (int64_t)V + (int64_t)(Zh << 1);
+    return (top << 8) + (mid >> 24);
+}
+
+// 64-bit right shift with the PTX semantics for amounts >= 64 (the result
+// is 0): unsigned; and arithmetic (sign fill).
+FX_HD uint64_t fx_shr_u(uint64_t v, uint32_t s) {
+#if defined(__CUDA_ARCH__)
+    uint64_t r;
+    asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(v), "r"(s));
+    return r;
+#else
+    return s >= 64 ? 0 : v >> s;
+#endif
+}
+FX_HD int64_t fx_sar(int64_t v, uint32_t s) {
+#if defined(__CUDA_ARCH__)
+    int64_t r;
+    asm("shr.s64 %0, %1, %2;" : "=l"(r) : "l"(v), "r"(s));
+    return r;
+#else
+    return s >= 64 ? (v < 0 ? -1 : 0) : v >> s;
+#endif
+}
+
+// trunc(|u| 2^(56-E)) with the sign of u, for a finite u with |u| < 2^E and
+// E >= -958 (so that zeros and subnormals shift out to 0).
+FX_HD int64_t fx_from_f64_fast(uint32_t hi, uint32_t lo, int E) {
+    // significand << 3, i.e. (2^52 + frac) << 3, built from the words
+    const uint32_t h3 = (((hi << 3) | (lo >> 29)) & 0x7FFFFFu) | 0x800000u;
+    const uint64_t m3 = ((uint64_t)h3 << 32) | (uint64_t)(lo << 3);
+    const uint64_t v = fx_shr_u(m3, (uint32_t)(1022 + E - fx_expfield(hi)));
+    const int64_t sm = (int64_t)(int32_t)hi >> 31;   // 0 or -1
+    return ((int64_t)v ^ sm) - sm;
+}
+
+// Nearest float to R 2^X g, g = (gh 2^32 + gl) 2^gq with gh >= 2^31, and
+// F = 2^(96 + X + gq) given as two float factors f1 f2 (each a power of two
+// in the normal range).  The top 64 bits of |R| g (normalized) are formed to
+// within three units and rounded once to FP32 through a 32-bit integer with a
+// sticky bit (round to odd, then to nearest), so the result is the correctly
+// rounded value except within 2^-40 of a tie.
+FX_HD float fx_to_f32_fast(int64_t R, uint32_t gh, uint32_t gl, float f1, float f2) {
+    if (R == 0) return 0.0f;
+    const uint64_t a0 = (uint64_t)(R < 0 ? -R : R);
+    const int lz = fx_clz64(a0);
+    const uint64_t a = a0 << lz;
+    const uint32_t ah = (uint32_t)(a >> 32), al = (uint32_t)a;
+    const uint64_t P = (uint64_t)ah * gh + fx_umulhi(ah, gl) + fx_umulhi(al, gh);
+    const uint32_t u = (uint32_t)(P >> 32) | ((uint32_t)P != 0u ? 1u : 0u);
+#if defined(__CUDA_ARCH__)
+    float f = __uint2float_rn(u);
+    const float p2 = __int_as_float((127 - lz) << 23);
+#else
+    float f = (float)u;
+    const uint32_t pb = (uint32_t)(127 - lz) << 23;
+    float p2;
+    __builtin_memcpy(&p2, &pb, 4);
+#endif
+    f = f * p2 * f1 * f2;
+    return R < 0 ? -f : f;
+}
+
 // Arithmetic right shift by s >= 0 (floor), saturating at 63.
 FX_HD int64_t fx_shr(int64_t v, int s) { return v >> (s > 63 ? 63 : s); }
 

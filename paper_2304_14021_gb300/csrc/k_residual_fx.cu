@@ -73,6 +73,15 @@ __device__ __forceinline__ int64_t fx_lap(const int64_t* __restrict__ a, int c, 
     else return a[c - 1] + a[c + 1] - 2 * a[c];
 }
 
+// 2^k as the product of two floats in the normal range (k within +-252).
+__device__ __forceinline__ void fx_pow2_pair(int k, float& f1, float& f2) {
+    int k1 = k >> 1, k2 = k - k1;
+    k1 = min(max(k1, -126), 127);
+    k2 = min(max(k2, -126), 127);
+    f1 = __int_as_float((k1 + 127) << 23);
+    f2 = __int_as_float((k2 + 127) << 23);
+}
+
 template <int DIM, bool HALF, bool ROUT>
 __global__ void __launch_bounds__(kFxThreads, kFxMinBlocks)
     k_residual_fx(GeoFX g, const double* __restrict__ U, const double* __restrict__ u0,
@@ -90,6 +99,7 @@ __global__ void __launch_bounds__(kFxThreads, kFxMinBlocks)
     __shared__ int64_t sfx[2][SY * SX];
     __shared__ int64_t sL[2][LY * LX];
     __shared__ int smax[2][NW];
+    __shared__ int smaxp[NW];
     __shared__ double red[NW];
 
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
@@ -149,28 +159,41 @@ __global__ void __launch_bounds__(kFxThreads, kFxMinBlocks)
         cu[q] = (ly + HY) * SX + lx + 2;
         cl[q] = (DIM == 2 ? (ly + 1) * LX : 0) + lx + 1;
     }
-    // previous level per point, in its own unit 2^(Ep-56) (theta = 1/2: with its two Laplacians)
+    // previous level per point in the tile-uniform unit 2^(Ep-56) (theta = 1/2: with its two Laplacians)
     int64_t up[PPT], L1p[PPT], L2p[PPT];
-    int Ep[PPT];
+    uint32_t uph[PPT], upl[PPT];
+    int fp = 0;
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
         up[q] = L1p[q] = L2p[q] = 0;
-        Ep[q] = -1022;
+        uph[q] = upl[q] = 0u;
         if (!HALF && inside[q]) {
             const double* src = n0 == 0 ? u0 : U + (size_t)(n0 - 1) * g.nspace;
             const unsigned long long v = __ldg(reinterpret_cast<const unsigned long long*>(src + po[q]));
-            const uint32_t hi = (uint32_t)(v >> 32);
-            Ep[q] = fx_tile_exp(max(fx_expfield(hi), 1));
-            up[q] = fx_from_f64(hi, (uint32_t)v, Ep[q]);
+            uph[q] = (uint32_t)(v >> 32);
+            upl[q] = (uint32_t)v;
+            fp = max(fp, fx_expfield(uph[q]));
         }
     }
-
     if (n0 < n1) {
         load(nfirst);
         const int f = expmax();
-        if (lane == 0) smax[0][warp] = f;
+        const int f2 = (int)__reduce_max_sync(0xffffffffu, (unsigned)fp);
+        if (lane == 0) {
+            smax[0][warp] = f;
+            smaxp[warp] = f2;
+        }
     }
     __syncthreads();
+    int Ep = -958;
+    if (!HALF) {
+        int f = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) f = max(f, smaxp[w]);
+        Ep = max(fx_tile_exp(f), -958);
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) up[q] = fx_from_f64_fast(uph[q], upl[q], Ep);
+    }
     float acc = 0.f;
     double accd = 0.0;
     for (int n = nfirst; n < n1; ++n) {
@@ -179,10 +202,10 @@ __global__ void __launch_bounds__(kFxThreads, kFxMinBlocks)
 #pragma unroll
         for (int w = 0; w < NW; ++w) fmax = max(fmax, smax[b][w]);
         const bool bad = fmax == 0x7FF;   // an infinity or NaN in the tile
-        const int E = fx_tile_exp(max(fmax, 1));
+        const int E = max(fx_tile_exp(fmax), -958);
 #pragma unroll
         for (int a = 0; a < NST; ++a)
-            if (tid + a * NTHR < SX * SY) sfx[b][tid + a * NTHR] = fx_from_f64(rhi[a], rlo[a], E);
+            if (tid + a * NTHR < SX * SY) sfx[b][tid + a * NTHR] = fx_from_f64_fast(rhi[a], rlo[a], E);
         if (n + 1 < n1) load(n + 1);
         __syncthreads();
 #pragma unroll
@@ -193,49 +216,53 @@ __global__ void __launch_bounds__(kFxThreads, kFxMinBlocks)
             if (lane == 0) smax[b ^ 1][warp] = f;
         }
         __syncthreads();
-        uint64_t gm = 0;
-        int gq = 0;
-        float ig = 0.f;
-        if (!ROUT && n >= n0) {
-            fx_align(__double_as_longlong(gdt[n]), gm, gq);
+        if (HALF && n < n0) {
+#pragma unroll
+            for (int q = 0; q < PPT; ++q) {
+                up[q] = sfx[b][cu[q]];
+                L1p[q] = sL[b][cl[q]];
+                L2p[q] = fx_lap<DIM>(sL[b], cl[q], LX);
+            }
+            Ep = E;
+            continue;
+        }
+        // level-uniform exponents: terms in unit 2^X, X = Q + Em - 1
+        const int Em = max(E, Ep);
+        const uint32_t dE = (uint32_t)(Em - E), dEp = (uint32_t)(Em - Ep);
+        const bool same = dE == 0u && dEp == 0u;
+        const int X = g.Q + Em - 1;
+        uint32_t gh = 0u, gl = 0u;
+        float f1 = 0.f, f2 = 0.f, ig = 0.f;
+        if (!ROUT) {
+            const unsigned long long gb = (unsigned long long)__double_as_longlong(gdt[n]);
+            const int gex = (int)((gb >> 52) & 0x7FF);
+            const unsigned long long gm = ((gb & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 11;
+            gh = (uint32_t)(gm >> 32);
+            gl = (uint32_t)gm;
+            fx_pow2_pair(96 + X + gex - 1086, f1, f2);
             ig = igamf[n];
         }
 #pragma unroll
         for (int q = 0; q < PPT; ++q) {
             if (!inside[q]) continue;
+            const int64_t un = sfx[b][cu[q]];
             const int64_t L1 = sL[b][cl[q]];
             const int64_t L2 = fx_lap<DIM>(sL[b], cl[q], LX);
-            const int64_t un = sfx[b][cu[q]];
-            if (HALF && n < n0) {
-                up[q] = un;
-                L1p[q] = L1;
-                L2p[q] = L2;
-                Ep[q] = E;
-                continue;
+            int64_t D, L1s, L2s;
+            if (same) {
+                D = up[q] - un;
+                L1s = HALF ? (L1 + L1p[q]) >> 1 : L1;
+                L2s = HALF ? (L2 + L2p[q]) >> 1 : L2;
+            } else {
+                D = fx_sar(up[q], dEp) - fx_sar(un, dE);
+                L1s = HALF ? (fx_sar(L1, dE) + fx_sar(L1p[q], dEp)) >> 1 : fx_sar(L1, dE);
+                L2s = HALF ? (fx_sar(L2, dE) + fx_sar(L2p[q], dEp)) >> 1 : fx_sar(L2, dE);
             }
-            const int Em = max(E, Ep[q]);
-            // (u_{n-1} - u_n) in unit 2^(Em-59)
-            const int64_t D3 = (fx_shr(up[q], Em - Ep[q]) - fx_shr(un, Em - E)) * 8;
-            const int XD = Em - 59;
-            int64_t L1s = L1, L2s = L2;
-            int Ek = E;
-            if constexpr (HALF) {
-                L1s = fx_shr(L1, Em - E) + fx_shr(L1p[q], Em - Ep[q]);
-                L2s = fx_shr(L2, Em - E) + fx_shr(L2p[q], Em - Ep[q]);
-                Ek = Em;
-            }
-            const int64_t P2 = fx_mul(L2s, g.k2);
-            const int X2 = g.k2.q + Ek - 1;
-            const int64_t P1 = fx_mul(L1s, g.k1);
-            const int X1 = g.k1.q + Ek - 1;
-            int X = max(XD, X2);
-            if (g.lin1) X = max(X, X1);
-            int64_t R = fx_shr(D3, X - XD);
-            const int64_t t2 = fx_shr(P2, X - X2);
-            R -= g.k2.neg ? -t2 : t2;
+            int64_t R = g.sD >= 0 ? D * ((int64_t)1 << g.sD) : fx_sar(D, (uint32_t)(-g.sD));
+            R -= fx_mul_s(L2s, g.mh2, g.ml2);
             if (g.lin1) {
-                const int64_t t1 = fx_shr(P1, X - X1);
-                R -= g.k1.neg ? -t1 : t1;
+                const int64_t t1 = fx_mul_s(L1s, g.mh1, g.ml1);
+                R = g.neg1 ? R + t1 : R - t1;
             }
             const size_t o = (size_t)n * g.nspace + po[q];
             if constexpr (ROUT) {
@@ -243,18 +270,18 @@ __global__ void __launch_bounds__(kFxThreads, kFxMinBlocks)
                 if (r_out) r_out[o] = r;
                 accd = fma(r, r, accd);
             } else {
-                const float sv = bad ? __int_as_float(0x7FC00000) : fx_to_f32_scaled(R, X, gm, gq);
+                const float sv = bad ? __int_as_float(0x7FC00000) : fx_to_f32_fast(R, gh, gl, f1, f2);
                 s_out[o] = sv;
                 const float rv = sv * ig;
                 acc = fmaf(rv, rv, acc);
             }
             up[q] = un;
-            Ep[q] = E;
             if constexpr (HALF) {
                 L1p[q] = L1;
                 L2p[q] = L2;
             }
         }
+        Ep = E;
     }
     // deterministic block reduction of sum r^2 (sum u^2 is not needed for the linear equations)
     double a = warp_sum(ROUT ? accd : (double)acc);
@@ -272,23 +299,16 @@ __global__ void __launch_bounds__(kFxThreads, kFxMinBlocks)
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-static FxCoef fx_coef(double c) {
-    FxCoef k{0u, 0u, 0, 0};
-    if (c == 0.0) return k;
-    k.neg = c < 0.0;
-    int e;
-    const double f = frexp(fabs(c), &e);
-    const uint64_t m = (uint64_t)ldexp(f, 53);
-    k.mh = (uint32_t)(m >> 32);
-    k.ml = (uint32_t)m;
-    k.q = e - 53;
-    return k;
-}
-
 int residual_fx_supported(const Geo& g) {
     return g.cN == 0.0 && !g.expl && (g.dim == 1 || g.ihx2 == g.ihy2) && (g.th == 1.0 || g.th == 0.5);
 }
 
+// Coefficients in one binary frame 2^Q: M_i = round(|c_i| 2^-Q) < 2^53, where
+// c1 = dt c1/h^2 and c2 = dt c2/h^4 (theta = 1/2 halves the two levels' sums of
+// the Laplacians instead).  Q is the smallest exponent that keeps the largest
+// M below 2^53 (every product |L| M / 2^55 below 2^60 for |L| < 2^62), and at
+// least -58, so that the time difference (below 2^57 in the level unit)
+// enters as D 2^sD, sD = -55 - Q <= 3.
 GeoFX make_geo_fx(const Geo& g) {
     GeoFX f{};
     f.nx = g.nx;
@@ -299,10 +319,21 @@ GeoFX make_geo_fx(const Geo& g) {
     f.nspace = g.nspace;
     f.half = g.th < 1.0 ? 1 : 0;
     f.inv_dt = g.inv_dt;
-    // dt theta c / h^2 and dt theta c2 / h^4 (theta = 1/2 is a power of two: exact)
-    f.k1 = fx_coef(g.dt * g.th * g.c1 * g.ihx2);
-    f.k2 = fx_coef(g.dt * g.th * g.c2 * g.ihx2 * g.ihx2);
-    f.lin1 = g.c1 != 0.0 ? 1 : 0;
+    const double c1 = g.dt * g.c1 * g.ihx2, c2 = g.dt * g.c2 * g.ihx2 * g.ihx2;
+    const double cmax = fmax(fabs(c1), fabs(c2));
+    int e = -2000;
+    if (cmax > 0.0) frexp(cmax, &e);
+    f.Q = e - 53 > -58 ? e - 53 : -58;
+    f.sD = -55 - f.Q;
+    auto split = [&](double c, int32_t& mh, int32_t& ml) {
+        const uint64_t M = (uint64_t)llrint(ldexp(fabs(c), -f.Q));
+        mh = (int32_t)(M >> 31);
+        ml = (int32_t)(M & 0x7FFFFFFFull);
+    };
+    split(c1, f.mh1, f.ml1);
+    split(c2, f.mh2, f.ml2);
+    f.lin1 = c1 != 0.0 ? 1 : 0;
+    f.neg1 = c1 < 0.0 ? 1 : 0;
     return f;
 }
 

@@ -19,6 +19,18 @@
 
 namespace pint {
 
+// Exact FP32 -> FP64 conversion by bit assembly on the integer pipes (the
+// conversion instruction runs at the FP64 rate); zeros, subnormals, infinities
+// and NaNs take the conversion instruction.  For T = double it is the identity.
+__device__ __forceinline__ double f32_to_f64_exact(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t e = (b >> 23) & 0xFFu;
+    if (e - 1u >= 0xFEu) return (double)f;
+    const uint32_t hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b >> 3) & 0xFFFFFu);
+    return __hiloint2double((int)hi, (int)(b << 29));
+}
+__device__ __forceinline__ double f32_to_f64_exact(double d) { return d; }
+
 template <class T, int NT> struct TimeCfg {
     static constexpr int CW = sizeof(T) == 4 ? (NT <= 512 ? 32 : 16) : (NT <= 256 ? 32 : (NT == 512 ? 16 : 8));
     // enough threads that each holds at most two radix-8 butterflies across a barrier
@@ -128,25 +140,30 @@ __global__ void __launch_bounds__(TimeCfg<T, NT>::NTH)
         }
         const double gi = ginv[n];
         double* row = out + (size_t)n * nspace;
-        const double da = (double)v.x * gi, db = (double)v.y * gi;   // FP64 unscaling
         if (accumulate) {
+            // FP64 unscaling and update in one FP64 fused multiply-add, U + x gamma_n^{-1}/N_t (one
+            // rounding); the FP32 transform output enters exactly (conversion by bit assembly)
+            const double xa = f32_to_f64_exact(v.x), xb = f32_to_f64_exact(v.y);
             if (pa < nspace) {
-                const double w = row[pa] + da;
+                const double w = fma(xa, gi, row[pa]);
                 row[pa] = w;
                 if (want) {
-                    d2 = fmaf((float)da, (float)da, d2);
+                    const float da = (float)v.x * (float)gi;
+                    d2 = fmaf(da, da, d2);
                     u2 = fmaf((float)w, (float)w, u2);
                 }
             }
             if (pb < nspace) {
-                const double w = row[pb] + db;
+                const double w = fma(xb, gi, row[pb]);
                 row[pb] = w;
                 if (want) {
-                    d2 = fmaf((float)db, (float)db, d2);
+                    const float db = (float)v.y * (float)gi;
+                    d2 = fmaf(db, db, d2);
                     u2 = fmaf((float)w, (float)w, u2);
                 }
             }
         } else {
+            const double da = (double)v.x * gi, db = (double)v.y * gi;   // FP64 unscaling
             if (pa < nspace) row[pa] = da;
             if (pb < nspace) row[pb] = db;
         }

@@ -47,12 +47,14 @@ struct GeoFF {
 };
 
 // Geometry of the block fixed-point residual (k_residual_fx.cu): the products
-// theta dt c1 / h^2 and theta dt c2 / h^4 as exact mantissa / exponent pairs.
+// dt c1 / h^2 and dt c2 / h^4 as integer mantissas in one binary frame.
 struct GeoFX {
     int nx, ny, dim, bc, nt, nspace;
     int half;       // theta = 1/2: A(u_{n-1}) enters too
     int lin1;       // c1 != 0 (the Laplacian term is present)
-    FxCoef k1, k2;
+    int neg1;       // c1 < 0 (signed beta^2)
+    int Q, sD;      // common binary frame of the coefficients; time-difference shift
+    int32_t mh1, ml1, mh2, ml2;   // M_i = mh_i 2^31 + ml_i = round(|c_i| 2^-Q)
     double inv_dt;
 };
 // Linear equations (no u^3 term), theta 1 or 1/2, square cells or 1-D.
