@@ -6,8 +6,15 @@ One step = one pint_solve of the workload from the initial iterate (zero by defa
 ||b - K(U)|| / ||b|| <= tol: residual, alpha-scaled time FFT, spatial shifted
 solves, inverse FFT + update, repeated until the tolerance is met.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed_ff|mixed|fp64]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|mixed_ff|fp64]
                   [--alpha A] [--init 0|2] [--workload NAME] [--impl ours|reference]
+
+The headline is the mixed form: complex64 time transforms and shifted spatial
+solves, with the residual, the alpha-scaling and unscaling and the update in
+FP64 (the residual and its scaling exactly in block fixed point on the integer
+pipes).  The plain FP64 form and the float-float form are timed beside it, and
+every timed solve's result is compared with the oracle's sequential solution,
+computed once in a separate process outside the timed region.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle
 (sequential backward Euler with banded LU) on a bounded sample of the same
@@ -18,6 +25,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -83,22 +91,48 @@ def solver_kw(wl: dict, args, precision=None) -> dict:
     return kw
 
 
-# DRAM bytes per launch of the float-float residual, from one ncu capture of the
-# 2-D 256x256 x 128 workload (profiles/kernels_linear_ch_2d_256x256_nt128.md),
-# valid only for the kernel source it was taken on (sha256 prefix of the .cu).
-RESIDUAL_FF_TRAFFIC = {"src_sha256_16": "f2beb509f59f81f0", "workload": "linear_ch_2d_256x256_nt128",
-                       "dram_bytes": 68294656 + 5862912}
+# DRAM bytes per launch of a kernel, from one ncu capture of the named workload,
+# valid only for the source file's contents it was taken on (sha256 prefix).
+KERNEL_TRAFFIC = {
+    ("residual", "mixed_ff"): {"src": "k_residual_ff.cu", "src_sha256_16": "f2beb509f59f81f0",
+                               "workload": "linear_ch_2d_256x256_nt128", "dram_bytes": 68294656 + 5862912},
+}
 
 
-def _residual_ff_traffic(workload: str):
+def _kernel_traffic(phase: str, precision: str, workload: str):
     import hashlib
-    path = os.path.join(ROOT, "paper_2304_14021_gb300", "csrc", "k_residual_ff.cu")
+    t = KERNEL_TRAFFIC.get((phase, precision))
+    if t is None or t["workload"] != workload:
+        return None
+    path = os.path.join(ROOT, "paper_2304_14021_gb300", "csrc", t["src"])
     try:
         sha = hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
     except OSError:
         return None
-    t = RESIDUAL_FF_TRAFFIC
-    return t["dram_bytes"] if sha == t["src_sha256_16"] and workload == t["workload"] else None
+    return t["dram_bytes"] if sha == t["src_sha256_16"] else None
+
+
+def host_cpu() -> dict:
+    """Core count and CPU model of the host the CPU baseline runs on."""
+    model = None
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.processor() or platform.machine(),
+            "machine": platform.machine()}
 
 
 def ff_residual_ops_per_dof(equation: str, dim: int, accurate: bool = False) -> float:
@@ -129,6 +163,9 @@ def ff_residual_ops_per_dof(equation: str, dim: int, accurate: bool = False) -> 
     if equation == "cahn_hilliard":
         f += 16.0 * halo + lap          # u^3 on tile + halo, Lap(u^3)
     return f + 4.0
+
+
+STEP_PHASES = ("time_fwd", "spatial0", "spatial1", "spatial2", "time_inv")
 
 
 def phase_bytes_per_dof(precision: str, nt: int) -> dict:
@@ -165,7 +202,7 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={CLOCK_Q}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.idx), "-lms", "50"], stdout=self.f,
+                                          "-i", str(self.idx), "-lms", "10"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -291,6 +328,61 @@ def whole_job_value(world: int, dof_per_rank: int, seconds: float) -> float:
 # ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
+ORACLE_MAX_BAND_WORK = 3e10   # nspace * bandwidth^2 above which the sequential oracle is not run here
+
+
+def oracle_solution_worker(workload: str, seed: int, out_path: str) -> dict:
+    """The oracle's sequential solution of the workload's input (linear equations:
+    backward Euler with banded LU), saved to out_path (.npy), for the error of
+    every timed GPU solve against it.  Runs in its own process."""
+    import numpy as np
+
+    from oracle import pint_oracle as O
+    wl = WORKLOADS[workload]
+    p = O.Problem(**{k: wl[k] for k in ("equation", "dim", "nx", "ny", "bc", "eps", "beta", "T", "nt",
+                                         "n_windows")})
+    u0 = make_u0(wl, seed)
+    t0 = time.perf_counter()
+    U = O.sequential(p, u0)[-p.nt:]
+    np.save(out_path, U)
+    return {"seconds": time.perf_counter() - t0}
+
+
+def oracle_feasible(wl: dict) -> bool:
+    if wl["equation"] not in ("linear_ch", "biharmonic") or wl.get("n_windows", 1) != 1:
+        return False
+    ns = wl["nx"] * (wl["ny"] if wl["dim"] == 2 else 1)
+    bw = 2 if wl["dim"] == 1 else 2 * wl["nx"]
+    return ns * bw * bw <= ORACLE_MAX_BAND_WORK and ns * wl["nt"] <= 2**24
+
+
+def start_oracle_worker(workload: str, seed: int):
+    path = os.path.join(tempfile.gettempdir(), f"pint_oracle_{workload}_{seed}_{os.getpid()}.npy")
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-worker", "--workload", workload, "--seed", str(seed),
+           "--oracle-out", path]
+    proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env, cwd=ROOT)
+    return proc, path
+
+
+def finish_oracle_worker(handle):
+    """The oracle solution (numpy array) or the reason it is missing."""
+    import numpy as np
+    proc, path = handle
+    out, err = proc.communicate()
+    if proc.returncode != 0:
+        return None, f"oracle worker failed: {err[-500:]}"
+    try:
+        ref = np.load(path)
+        info = json.loads(out.strip().splitlines()[-1])
+    finally:
+        try:
+            os.remove(path)
+        except OSError:
+            pass
+    return ref, info
+
+
 def main_gpu(args) -> None:
     import numpy as np
     import torch
@@ -300,6 +392,10 @@ def main_gpu(args) -> None:
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    wl = WORKLOADS[args.workload]
+    seed = replica_seed(args.seed, rank)       # each replica solves its own instance
+    # the oracle's sequential solution, computed in its own process while the GPU is timed
+    oracle = start_oracle_worker(args.workload, seed) if (oracle_feasible(wl) and not args.no_oracle) else None
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -312,17 +408,21 @@ def main_gpu(args) -> None:
     if dist:
         dist.barrier()
 
-    wl = WORKLOADS[args.workload]
     kw = solver_kw(wl, args)
-    u0_np = make_u0(wl, replica_seed(args.seed, rank))   # each replica solves its own instance
+    u0_np = make_u0(wl, seed)
     stream = torch.cuda.current_stream()
-    s = pint.Solver(stream=stream, **kw)
-    if wl["equation"] in ("cahn_hilliard", "cahn_hilliard_eyre"):
-        s.set_adaptive_windows(True)
-        if args.varying_jacobian:
-            s.set_varying_jacobian(args.varying_jacobian)
-    if args.no_graphs:
-        s.set_graphs(False)
+
+    def make_solver(kwargs):
+        sv = pint.Solver(stream=stream, **kwargs)
+        if wl["equation"] in ("cahn_hilliard", "cahn_hilliard_eyre"):
+            sv.set_adaptive_windows(True)
+            if args.varying_jacobian:
+                sv.set_varying_jacobian(args.varying_jacobian)
+        if args.no_graphs:
+            sv.set_graphs(False)
+        return sv
+
+    s = make_solver(kw)
     nt, ns = s.nt, s.nspace
     nwin = wl.get("n_windows", 1)
     dof = nt * ns * nwin                 # space-time DOF of the whole solve (all windows)
@@ -334,19 +434,21 @@ def main_gpu(args) -> None:
     for _ in range(args.warmup):
         stats = s.solve(u0, U)
 
-    def timed_steps(k):
-        ts = []
+    def timed_steps(sv, k):
+        ts, st_ = [], None
         for _ in range(k):
             flush.zero_()                                # L2 flush outside the timed events
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            st_ = s.solve(u0, U)
+            st_ = sv.solve(u0, U)
             e1.record(stream)
             e1.synchronize()
             ts.append(e0.elapsed_time(e1))
         return ts, st_
 
+    # Clocks are sampled over every timed pass below (headline, profiled pass,
+    # precision forms, the second alpha).
     clocks = ClockSampler(local)
     clocks.start()
     # Pass A (the reported value): the production path, each window's iteration
@@ -355,25 +457,50 @@ def main_gpu(args) -> None:
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    times, stats = timed_steps(args.steps)
+    times, stats = timed_steps(s, args.steps)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     launches_a = s.profile_read(reset=True)
+    U_head = U.cpu().numpy()
     # Pass B (per-kernel durations for the roofline): the same steps with CUDA
     # events recorded on the solver's stream around every kernel phase (this
     # uses the host-launched loop, whose kernels are the same).
     s.profile_enable(True)
     s.profile_read(reset=True)
     torch.cuda.synchronize()
-    times_b, _ = timed_steps(args.steps)
+    times_b, _ = timed_steps(s, args.steps)
     torch.cuda.synchronize()
-    clk = clocks.stop()
     prof = s.profile_read(reset=True)
     s.profile_enable(False)
     ms = statistics.mean(times)
     ms_b = statistics.mean(times_b)
     ms = max_over_ranks(ms, dist, "cuda")
+
+    # The other precision forms and the second alpha on the same input, each
+    # with its own warm-up and timed repeats; results kept for the error check.
+    variants, results = {}, {"headline": U_head}
+    if not args.no_variants:
+        alpha0 = wl.get("alpha", args.alpha)
+        runs = [(prec, alpha0) for prec in ("fp64", "mixed", "mixed_ff") if prec != args.precision]
+        if "alpha" not in wl:
+            runs += [(prec, a) for prec in (args.precision,) for a in (1e-3,) if a != alpha0]
+        for prec, a in runs:
+            name = prec if a == alpha0 else f"{prec}_alpha{a:g}"
+            kwv = dict(solver_kw(wl, args, prec), alpha=a)
+            sv = make_solver(kwv)
+            try:
+                for _ in range(2):
+                    sv.solve(u0, U)
+                tv, st_v = timed_steps(sv, args.variant_steps)
+            finally:
+                sv.close()
+            results[name] = U.cpu().numpy()
+            mv = statistics.mean(tv)
+            variants[name] = {"precision": prec, "alpha": a, "ms_per_step": mv, "value": dof / (mv * 1e-3),
+                              "timed_steps": len(tv), "iterations": st_v["iters"],
+                              "final_rel_residual": st_v["rel_residual"]}
+    clk = clocks.stop()
 
     # End to end through the host-buffer entry point: H2D of u0 and D2H of U inside.
     e2e_s = None
@@ -390,67 +517,48 @@ def main_gpu(args) -> None:
             e2e_times.append(time.perf_counter() - t0)
         e2e_s = max_over_ranks(statistics.mean(e2e_times), dist, "cuda")
 
-    # The other precision forms on the same input (fewer steps): plain FP64 and
-    # FP64-residual mixed.
-    variants = {}
-    if not args.no_variants:
-        for prec in ("fp64", "mixed", "mixed_ff"):
-            if prec == args.precision:
-                continue
-            with pint.Solver(stream=stream, **solver_kw(wl, args, prec)) as sv:
-                for _ in range(2):
-                    st_v = sv.solve(u0, U)
-                tv = []
-                for _ in range(3):
-                    flush.zero_()
-                    e0 = torch.cuda.Event(enable_timing=True)
-                    e1 = torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    st_v = sv.solve(u0, U)
-                    e1.record(stream)
-                    e1.synchronize()
-                    tv.append(e0.elapsed_time(e1))
-            mv = statistics.mean(tv)
-            variants[prec] = {"ms_per_step": mv, "value": dof / (mv * 1e-3), "iterations": st_v["iters"],
-                              "final_rel_residual": st_v["rel_residual"]}
-
-    # Roofline of the dominant phase (largest device time in the timed region).
-    # Per-launch time = phase time / launches, where launches that found the
-    # solve already converged (early exits at the end of a chunk) are excluded.
+    # Per-phase times and the rooflines.  Per-launch time = phase time / launches
+    # that did work (launches that found the solve already converged are excluded).
     bpd = phase_bytes_per_dof(args.precision, nt)
     # DOF one launch processes: a window, or under the adaptive window policy a
     # segment (approximated by the mean segment size of the solve)
     dof_l = dof / max(1, stats.get("segments", 1)) if nwin > 1 or stats.get("segments", 1) > 1 else dof
-    dom = max((k for k in prof if prof[k]["launches"] > 0 and k != "check"), key=lambda k: prof[k]["ms"])
     iters_per_step = stats["iters"]
     zero_start = args.init == 2 and not wl["equation"].startswith("cahn_hilliard")   # CH starts from u0
     res_evals = iters_per_step + (0 if zero_start else 1)   # the zero start skips the first residual
     active = {k: (args.steps * (res_evals if k == "residual" else iters_per_step)
                   if k not in ("setup", "check") else prof[k]["launches"]) for k in prof}
+    dom = max((k for k in prof if prof[k]["launches"] > 0 and k != "check"), key=lambda k: prof[k]["ms"])
     per_launch_ms = prof[dom]["ms"] / max(1, active[dom])
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peak_src = "MEASURED_PEAKS.json hbm_gbs (measured)"
     except Exception:
-        pass
+        peak_src = "fallback 6800 GB/s (MEASURED_PEAKS.json absent)"
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    # FP32 lane-operation peak: 152 SMs x 128 FP32 lanes x 2070 MHz, one add,
-    # multiply or FMA per lane and clock (the residual is mostly additions)
-    fp32_ops_peak = 152 * 128 * 2.070e9 / 1e12
+    ach = bpd[dom] * dof_l / (per_launch_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+            "traffic": _kernel_traffic(dom, args.precision, args.workload), "bytes_per_dof": bpd[dom],
+            "per_launch_us": per_launch_ms * 1e3, "peak_note": peak_src}
     if dom == "residual" and args.precision == "mixed_ff":
+        # secondary: FP32 lane-operation occupancy of the float-float residual (nominal peak)
+        fp32_ops_peak = 152 * 128 * 2.070e9 / 1e12
         ops = ff_residual_ops_per_dof(wl["equation"], wl["dim"]) * dof_l
-        ach = ops / (per_launch_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": "k_residual_ff", "achieved": ach, "peak": fp32_ops_peak,
-                "unit": "TFLOP/s", "frac": ach / fp32_ops_peak, "traffic": _residual_ff_traffic(args.workload),
-                "ops_per_dof": ops / dof_l, "per_launch_us": per_launch_ms * 1e3,
-                "hbm_frac": bpd[dom] * dof_l / (per_launch_ms * 1e-3) / 1e9 / hbm_peak,
-                "peak_note": "FP32 lane operations per second, nominal: 152 SMs x 128 lanes x 2.07 GHz "
-                             "(an FMA counts as one operation, as does an add)"}
-    else:
-        ach = bpd[dom] * dof_l / (per_launch_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                "frac": ach / hbm_peak, "traffic": None, "bytes_per_dof": bpd[dom],
-                "per_launch_us": per_launch_ms * 1e3, "peak_note": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+        roof["fp32_issue"] = {"achieved": ops / (per_launch_ms * 1e-3) / 1e12, "peak": fp32_ops_peak,
+                              "unit": "T FP32 lane ops/s", "ops_per_dof": ops / dof_l,
+                              "note": "nominal 152 SMs x 128 lanes x 2.07 GHz"}
+    # The diagonalized step (Steps 1-3 of Eq. 2.8: time FFT, spatial solves,
+    # inverse FFT with the unscaling and update) against the strict minimum of
+    # one read of the residual and one write of the correction: 8 B/DOF in the
+    # mixed forms, 16 in FP64.
+    step_ms_iter = sum(prof[k]["ms"] for k in STEP_PHASES) / max(1, args.steps * iters_per_step)
+    step_bytes = (8 if args.precision in ("mixed", "mixed_ff") else 16) * dof_l
+    roof["diag_step_us_per_iteration"] = step_ms_iter * 1e3
+    roof["diag_step_bytes_per_dof"] = step_bytes / dof_l
+    roof["diag_step_frac"] = step_bytes / (step_ms_iter * 1e-3) / 1e9 / hbm_peak
+    roof["diag_step_kernel_bytes_frac"] = (sum(bpd[k] for k in STEP_PHASES if prof[k]["launches"] > 0) * dof_l
+                                           / (step_ms_iter * 1e-3) / 1e9 / hbm_peak)
     phases = {}
     for k, v in prof.items():
         if v["launches"] == 0:
@@ -462,15 +570,25 @@ def main_gpu(args) -> None:
     launches_total = sum(v["launches"] for v in launches_a.values())
 
     if rank == 0:
+        errs, oracle_info = None, None
+        if oracle is not None:
+            ref, oracle_info = finish_oracle_worker(oracle)
+            if ref is not None:
+                errs = {name: float(np.max(np.abs(Ux - ref)) / np.max(np.abs(ref))) for name, Ux in results.items()}
+                for name, v in variants.items():
+                    v["err_vs_oracle"] = errs.get(name)
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
+            hc = host_cpu()
             try:
                 cpu = run_cpu_worker(args.workload, args.alpha, args.cpu_budget, args.seed)
                 cpu = {"value": cpu["value"], "unit": "space-time DOF/s", "cores": cpu["cores"], "kind": "oracle",
-                       "sample": cpu["sample"]}
+                       "sample": cpu["sample"], **hc}
             except Exception as ex:  # report, do not hide
                 cpu = {"value": None, "unit": "space-time DOF/s", "cores": 1, "kind": "oracle",
-                       "sample": f"failed: {ex}"}
+                       "sample": f"failed: {ex}", **hc}
+        dtype = {"mixed_ff": "f32 (float-float iterate)", "mixed": "f64 residual/scaling/update + c64 transforms",
+                 "fp64": "f64"}[args.precision]
         out = {
             "metric": "space-time DOF/s at rel. residual 1e-8",
             "value": whole_job_value(world, dof, ms * 1e-3),
@@ -482,7 +600,7 @@ def main_gpu(args) -> None:
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": {"mixed_ff": "f32 (float-float iterate)", "mixed": "f32+f64", "fp64": "f64"}[args.precision],
+            "dtype": dtype,
             "data": "synthetic",
             "config": {"workload": args.workload, "precision": args.precision, "alpha": wl.get("alpha", args.alpha),
                        "tol": args.tol, "init": "zero" if zero_start else "u0", "dof_per_gpu": dof,
@@ -490,6 +608,8 @@ def main_gpu(args) -> None:
                        "varying_jacobian": args.varying_jacobian or None,
                        "final_rel_residual": stats["rel_residual"], "l2": "flushed between steps",
                        "parallelism": f"replicas x{world}"},
+            "err_vs_oracle": (errs or {}).get("headline"),
+            "oracle": oracle_info if oracle is not None else "not run (size or equation outside the CPU oracle's reach)",
             "e2e": ({"value": whole_job_value(world, dof, e2e_s), "unit": "space-time DOF/s",
                      "h2d_bytes_per_step": ns * 8,
                      "d2h_bytes_per_step": nt * ns * 8} if e2e_s else None),
@@ -503,10 +623,11 @@ def main_gpu(args) -> None:
             "cpu_baseline": cpu,
         }
         print(json.dumps(out), flush=True)
+    elif oracle is not None:
+        finish_oracle_worker(oracle)
     s.close()
     if dist:
         dist.destroy_process_group()
-    _ = np
 
 
 def _sync_time(torch, fn):
@@ -600,7 +721,10 @@ def main_serving(args) -> None:
             dt = t_next - time.perf_counter()
             if dt > 0:
                 time.sleep(dt)
-            futs.append(srv.submit(x["u0"], **x["problem"]))
+            f = srv.submit(x["u0"], **x["problem"])
+            # the solution's bytes go back to the admission budget as soon as it is done
+            f.add_done_callback(lambda fu: fu.result().release() if fu.exception() is None else None)
+            futs.append(f)
         res = [f.result() for f in futs]
         rep = srv.report(res)
         srv.close()
@@ -647,7 +771,7 @@ def main_reference(args) -> None:
            "dtype": "f64", "data": "synthetic",
            "config": {"workload": args.workload, "precision": "fp64 (oracle)", "alpha": args.alpha},
            "cpu_baseline": {"value": v, "unit": "space-time DOF/s", "cores": 1, "kind": "oracle",
-                            "sample": res["sample"]},
+                            "sample": res["sample"], **host_cpu()},
            "e2e": {"value": v, "unit": "space-time DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -658,7 +782,12 @@ def main() -> None:
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed_ff", choices=["mixed_ff", "mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_ff", "fp64"])
+    ap.add_argument("--variant-steps", type=int, default=10,
+                    help="timed repeats of each other precision form and of the second alpha")
+    ap.add_argument("--no-oracle", action="store_true", help="skip the oracle's sequential solution (error check)")
+    ap.add_argument("--oracle-worker", action="store_true")
+    ap.add_argument("--oracle-out", default="")
     ap.add_argument("--init", type=int, default=2, choices=[0, 2],
                     help="initial iterate: 0 = u0 at every level, 2 = zero")
     ap.add_argument("--no-e2e", action="store_true")
@@ -682,6 +811,9 @@ def main() -> None:
     args = ap.parse_args()
     if args.cpu_worker:
         print(json.dumps(cpu_worker(args.workload, args.alpha, args.cpu_budget, args.seed, args.cpu_samples)))
+        return
+    if args.oracle_worker:
+        print(json.dumps(oracle_solution_worker(args.workload, args.seed, args.oracle_out)))
         return
     if args.impl == "reference":
         main_reference(args)

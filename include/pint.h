@@ -277,7 +277,7 @@ int pint_set_option(pint_handle* h, int option, long long value);
  * (concurrent streams, threads) race and must be serialized by the caller.
  * Errors: PINT_EINVAL (bad problem or NULL pointer, or a grid whose reduction
  * needs more partial sums than the scratch holds), PINT_ECUDA. */
-#define PINT_STATIC_SCRATCH_BYTES 262144
+#define PINT_STATIC_SCRATCH_BYTES 278528
 int pint_residual_static(const pint_problem* p, void* cuda_stream, const double* u0_dev, const double* U_dev,
                          double* r_dev, double* rel_res_dev);
 

@@ -100,6 +100,32 @@ FX_HD int64_t fx_mul_s(int64_t L, int32_t mh, int32_t ml) {
     return (top << 8) + (mid >> 24);
 }
 
+// Bits S .. S+63 of the exact 128-bit product L M (L signed, 0 <= M < 2^63), i.e.
+// floor(L M / 2^S), for 0 <= S <= 63 when that quotient fits in 64 bits.  S is
+// the same for every thread of a block (a uniform branch picks the word pair).
+FX_HD int64_t fx_mul_shr(int64_t L, int64_t M, int S) {
+#if defined(__CUDA_ARCH__)
+    const uint64_t lo = (uint64_t)L * (uint64_t)M;
+    const int64_t hi = __mul64hi(L, M);
+    const uint32_t w0 = (uint32_t)lo, w1 = (uint32_t)(lo >> 32), w2 = (uint32_t)hi, w3 = (uint32_t)((uint64_t)hi >> 32);
+    uint32_t rx, ry;
+    if (S < 32) {
+        rx = __funnelshift_r(w0, w1, S);
+        ry = __funnelshift_r(w1, w2, S);
+    } else {
+        rx = __funnelshift_r(w1, w2, S - 32);
+        ry = __funnelshift_r(w2, w3, S - 32);
+    }
+    return (int64_t)(((uint64_t)ry << 32) | rx);
+#else
+    const __int128 p = (__int128)L * (__int128)M;
+    return (int64_t)(p >> S);
+#endif
+}
+
+// Significant bits of |v| (0 for v = 0).
+FX_HD int fx_bits(int64_t v) { return 64 - fx_clz64((uint64_t)(v < 0 ? -v : v)); }
+
 // 64-bit right shift with the PTX semantics for amounts >= 64 (the result
 // is 0): unsigned; and arithmetic (sign fill).
 FX_HD uint64_t fx_shr_u(uint64_t v, uint32_t s) {

@@ -96,10 +96,12 @@ __global__ void __launch_bounds__(kFxThreads, kFxMinBlocks)
     constexpr int SX = TX + 4, SY = TY + 2 * HY;
     constexpr int LX = TX + 2, LY = TY + (DIM == 2 ? 2 : 0);
     constexpr int NST = (SX * SY + NTHR - 1) / NTHR, NLP = (LX * LY + NTHR - 1) / NTHR;
+    constexpr int L2GROW = DIM == 2 ? 3 : 2;     // |Lap L1| <= 8 max|L1| (2-D), 4 max|L1| (1-D)
     __shared__ int64_t sfx[2][SY * SX];
     __shared__ int64_t sL[2][LY * LX];
     __shared__ int smax[2][NW];
     __shared__ int smaxp[NW];
+    __shared__ int sbL[NW], sbD[NW];
     __shared__ double red[NW];
 
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
@@ -185,7 +187,7 @@ __global__ void __launch_bounds__(kFxThreads, kFxMinBlocks)
         }
     }
     __syncthreads();
-    int Ep = -958;
+    int Ep = -958, bL1p = 0;
     if (!HALF) {
         int f = 0;
 #pragma unroll
@@ -207,15 +209,48 @@ __global__ void __launch_bounds__(kFxThreads, kFxMinBlocks)
         for (int a = 0; a < NST; ++a)
             if (tid + a * NTHR < SX * SY) sfx[b][tid + a * NTHR] = fx_from_f64_fast(rhi[a], rlo[a], E);
         if (n + 1 < n1) load(n + 1);
+        // level-uniform unit: both levels in 2^(Em-56)
+        const int Em = max(E, Ep);
+        const uint32_t dE = (uint32_t)(Em - E), dEp = (uint32_t)(Em - Ep);
+        const bool same = dE == 0u && dEp == 0u;
         __syncthreads();
+        // first Laplacian pass, with the tile's largest |L1| and |u_{n-1} - u_n| (as bit counts)
+        // v ^ (v >> 63) is |v| or |v| - 1: the bits of the OR of those, plus one, bound every |v|
+        uint64_t orl = 0, ord = 0;
 #pragma unroll
         for (int a = 0; a < NLP; ++a)
-            if (lc[a] >= 0) sL[b][tid + a * NTHR] = fx_lap<DIM>(sfx[b], lc[a], SX);
+            if (lc[a] >= 0) {
+                const int64_t v = fx_lap<DIM>(sfx[b], lc[a], SX);
+                sL[b][tid + a * NTHR] = v;
+                orl |= (uint64_t)(v ^ (v >> 63));
+            }
+        if (!(HALF && n < n0)) {
+#pragma unroll
+            for (int q = 0; q < PPT; ++q)
+                if (inside[q]) {
+                    const int64_t un = sfx[b][cu[q]];
+                    const int64_t D = same ? up[q] - un : fx_sar(up[q], dEp) - fx_sar(un, dE);
+                    ord |= (uint64_t)(D ^ (D >> 63));
+                }
+        }
+        int bl = orl ? 65 - fx_clz64(orl) : 0, bd = ord ? 65 - fx_clz64(ord) : 0;
+        bl = (int)__reduce_max_sync(0xffffffffu, (unsigned)bl);
+        bd = (int)__reduce_max_sync(0xffffffffu, (unsigned)bd);
+        if (lane == 0) {
+            sbL[warp] = bl;
+            sbD[warp] = bd;
+        }
         if (n + 1 < n1) {
             const int f = expmax();
             if (lane == 0) smax[b ^ 1][warp] = f;
         }
         __syncthreads();
+        int bL1 = 0, bD = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            bL1 = max(bL1, sbL[w]);
+            bD = max(bD, sbD[w]);
+        }
         if (HALF && n < n0) {
 #pragma unroll
             for (int q = 0; q < PPT; ++q) {
@@ -224,13 +259,20 @@ __global__ void __launch_bounds__(kFxThreads, kFxMinBlocks)
                 L2p[q] = fx_lap<DIM>(sL[b], cl[q], LX);
             }
             Ep = E;
+            bL1p = bL1;
             continue;
         }
-        // level-uniform exponents: terms in unit 2^X, X = Q + Em - 1
-        const int Em = max(E, Ep);
-        const uint32_t dE = (uint32_t)(Em - E), dEp = (uint32_t)(Em - Ep);
-        const bool same = dE == 0u && dEp == 0u;
-        const int X = g.Q + Em - 1;
+        // Terms in the unit 2^(Q+Em-56) of the exact products L M: c2 L2, c1 L1 and D 2^-Q.  Their
+        // largest magnitude in this tile, 2^emax, sets the output unit 2^X, X = Q + Em - 56 + S with
+        // S = emax - 60 (>= 0): every term is then resolved to 2^-60 of the largest one.
+        // bits of the Laplacian sums as used (a shift to the unit Em only lowers them)
+        const int bL = HALF ? max(bL1, bL1p) + 1 : bL1;
+        const int e2 = bL + L2GROW + g.bM2, e1 = bL + g.bM1, eD = bD - g.Q;
+        int emax = max(e2, eD);
+        if (g.lin1) emax = max(emax, e1);
+        const int S = max(emax - 60, 0);
+        const int X = g.Q + Em - 56 + S;
+        const int kD = -g.Q - S;                              // D 2^-Q in units 2^S
         uint32_t gh = 0u, gl = 0u;
         float f1 = 0.f, f2 = 0.f, ig = 0.f;
         if (!ROUT) {
@@ -246,22 +288,25 @@ __global__ void __launch_bounds__(kFxThreads, kFxMinBlocks)
         for (int q = 0; q < PPT; ++q) {
             if (!inside[q]) continue;
             const int64_t un = sfx[b][cu[q]];
-            const int64_t L1 = sL[b][cl[q]];
-            const int64_t L2 = fx_lap<DIM>(sL[b], cl[q], LX);
-            int64_t D, L1s, L2s;
+            const int64_t L1o = sL[b][cl[q]];
+            const int64_t L2o = fx_lap<DIM>(sL[b], cl[q], LX);
+            int64_t D, L1 = L1o, L2 = L2o;
             if (same) {
                 D = up[q] - un;
-                L1s = HALF ? (L1 + L1p[q]) >> 1 : L1;
-                L2s = HALF ? (L2 + L2p[q]) >> 1 : L2;
             } else {
                 D = fx_sar(up[q], dEp) - fx_sar(un, dE);
-                L1s = HALF ? (fx_sar(L1, dE) + fx_sar(L1p[q], dEp)) >> 1 : fx_sar(L1, dE);
-                L2s = HALF ? (fx_sar(L2, dE) + fx_sar(L2p[q], dEp)) >> 1 : fx_sar(L2, dE);
+                L1 = fx_sar(L1o, dE);
+                L2 = fx_sar(L2o, dE);
             }
-            int64_t R = g.sD >= 0 ? D * ((int64_t)1 << g.sD) : fx_sar(D, (uint32_t)(-g.sD));
-            R -= fx_mul_s(L2s, g.mh2, g.ml2);
+            int64_t L1s = L1, L2s = L2;
+            if constexpr (HALF) {
+                L1s += same ? L1p[q] : fx_sar(L1p[q], dEp);
+                L2s += same ? L2p[q] : fx_sar(L2p[q], dEp);
+            }
+            int64_t R = kD >= 0 ? (D << kD) : fx_sar(D, (uint32_t)(-kD));
+            R -= fx_mul_shr(L2s, g.M2, S);
             if (g.lin1) {
-                const int64_t t1 = fx_mul_s(L1s, g.mh1, g.ml1);
+                const int64_t t1 = fx_mul_shr(L1s, g.M1, S);
                 R = g.neg1 ? R + t1 : R - t1;
             }
             const size_t o = (size_t)n * g.nspace + po[q];
@@ -277,11 +322,12 @@ __global__ void __launch_bounds__(kFxThreads, kFxMinBlocks)
             }
             up[q] = un;
             if constexpr (HALF) {
-                L1p[q] = L1;
-                L2p[q] = L2;
+                L1p[q] = L1o;
+                L2p[q] = L2o;
             }
         }
         Ep = E;
+        bL1p = bL1;
     }
     // deterministic block reduction of sum r^2 (sum u^2 is not needed for the linear equations)
     double a = warp_sum(ROUT ? accd : (double)acc);
@@ -304,11 +350,9 @@ int residual_fx_supported(const Geo& g) {
 }
 
 // Coefficients in one binary frame 2^Q: M_i = round(|c_i| 2^-Q) < 2^53, where
-// c1 = dt c1/h^2 and c2 = dt c2/h^4 (theta = 1/2 halves the two levels' sums of
-// the Laplacians instead).  Q is the smallest exponent that keeps the largest
-// M below 2^53 (every product |L| M / 2^55 below 2^60 for |L| < 2^62), and at
-// least -58, so that the time difference (below 2^57 in the level unit)
-// enters as D 2^sD, sD = -55 - Q <= 3.
+// c1 = theta dt c1/h^2 and c2 = theta dt c2/h^4 (theta = 1/2 is exact).  The
+// products L M are exact; the kernel picks per tile and level how many low
+// bits of them to drop.
 GeoFX make_geo_fx(const Geo& g) {
     GeoFX f{};
     f.nx = g.nx;
@@ -319,19 +363,18 @@ GeoFX make_geo_fx(const Geo& g) {
     f.nspace = g.nspace;
     f.half = g.th < 1.0 ? 1 : 0;
     f.inv_dt = g.inv_dt;
-    const double c1 = g.dt * g.c1 * g.ihx2, c2 = g.dt * g.c2 * g.ihx2 * g.ihx2;
+    const double c1 = g.th * g.dt * g.c1 * g.ihx2, c2 = g.th * g.dt * g.c2 * g.ihx2 * g.ihx2;
     const double cmax = fmax(fabs(c1), fabs(c2));
     int e = -2000;
     if (cmax > 0.0) frexp(cmax, &e);
-    f.Q = e - 53 > -58 ? e - 53 : -58;
-    f.sD = -55 - f.Q;
-    auto split = [&](double c, int32_t& mh, int32_t& ml) {
-        const uint64_t M = (uint64_t)llrint(ldexp(fabs(c), -f.Q));
-        mh = (int32_t)(M >> 31);
-        ml = (int32_t)(M & 0x7FFFFFFFull);
+    f.Q = e - 53 > -1000 ? e - 53 : -1000;
+    auto mant = [&](double c, int64_t& M, int& bits) {
+        M = (int64_t)llrint(ldexp(fabs(c), -f.Q));
+        bits = 0;
+        for (int64_t t = M; t; t >>= 1) ++bits;
     };
-    split(c1, f.mh1, f.ml1);
-    split(c2, f.mh2, f.ml2);
+    mant(c1, f.M1, f.bM1);
+    mant(c2, f.M2, f.bM2);
     f.lin1 = c1 != 0.0 ? 1 : 0;
     f.neg1 = c1 < 0.0 ? 1 : 0;
     return f;

@@ -53,8 +53,9 @@ struct GeoFX {
     int half;       // theta = 1/2: A(u_{n-1}) enters too
     int lin1;       // c1 != 0 (the Laplacian term is present)
     int neg1;       // c1 < 0 (signed beta^2)
-    int Q, sD;      // common binary frame of the coefficients; time-difference shift
-    int32_t mh1, ml1, mh2, ml2;   // M_i = mh_i 2^31 + ml_i = round(|c_i| 2^-Q)
+    int Q;          // common binary frame of the coefficients
+    int bM1, bM2;   // significant bits of M1, M2
+    int64_t M1, M2; // round(|c_i| 2^-Q) < 2^53
     double inv_dt;
 };
 // Linear equations (no u^3 term), theta 1 or 1/2, square cells or 1-D.

@@ -22,6 +22,11 @@ static __device__ __align__(256) unsigned char g_static_scratch[PINT_STATIC_SCRA
 
 static constexpr size_t kCtlBytes = (sizeof(Ctl) + 255) / 256 * 256;
 static constexpr size_t kMaxPairs = (PINT_STATIC_SCRATCH_BYTES - kCtlBytes) / (2 * sizeof(double));
+// The largest residual grid pint_create accepts: a 2-D grid of 4096 x 1024 points (the largest
+// FFT axes) in 32 x 8 tiles with all time levels in one CTA, 128 * 128 CTAs; 1-D grids need at
+// most about 4 x 152.  Every accepted problem therefore fits the scratch.
+static constexpr size_t kLargestResidualGrid = (4096 / 32) * (1024 / 8);
+static_assert(kMaxPairs >= kLargestResidualGrid, "static scratch too small for the largest residual grid");
 
 // ||r|| / ||b|| from the residual's partial sums and ctl->bnorm, written to out.
 __global__ void k_static_finish(const double* __restrict__ partials, int np, const Ctl* __restrict__ ctl,

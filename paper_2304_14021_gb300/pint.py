@@ -127,7 +127,7 @@ def footprint(**kw) -> int:
     return int(lib().pint_footprint(C.byref(p)))
 
 
-STATIC_SCRATCH_BYTES = 262144
+STATIC_SCRATCH_BYTES = 278528
 
 
 def residual_static(u0, U, rel_res, r=None, stream=None, **problem) -> None:

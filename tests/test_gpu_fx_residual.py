@@ -78,7 +78,7 @@ def test_fx_residual_matches_oracle_and_fp64_kernel_on_random_iterates(case):
     assert np.max(np.abs(out["mixed"][0] - out["fp64"][0])) <= 1e-13 * scale
 
 
-@pytest.mark.parametrize("case", [0, 2, 3, 4, 6])
+@pytest.mark.parametrize("case", [0, 2, 3, 4, 6, 7])
 def test_fx_residual_at_the_sequential_solution_is_fp64_rounding(case):
     # At the sequential solution r = b - K(U) vanishes up to rounding.  The sums that
     # form it reach max|u| (1/dt + ||A||_inf) (the stencil terms, before they cancel):
@@ -99,6 +99,32 @@ def test_fx_residual_at_the_sequential_solution_is_fp64_rounding(case):
             errs[prec] = np.max(np.abs(host(r) - ref)) / scale
     assert errs["mixed"] < 1e-14, errs
     assert errs["fp64"] < 1e-14, errs
+    # and no worse than the FP64 kernel itself (both measured against the oracle's own rounding)
+    assert errs["mixed"] <= 2.0 * errs["fp64"] + 1e-17, errs
+
+
+@pytest.mark.parametrize("nx", [512, 1024])
+def test_fx_residual_stiff_smooth_problem_converges_like_fp64(nx):
+    # 1-D biharmonic, Neumann, T = 0.01 over 16 steps: dt ||A|| ~ 1e9-1e10 (PINT_MIXED by the precision
+    # policy).  The solution is smooth, so the residual's terms are far below their worst-case bounds:
+    # the fixed-point residual must resolve them relative to their actual size, as FP64 does, or the
+    # iteration stalls above its rounding floor.
+    kw = full(dict(equation="biharmonic", dim=1, nx=nx, bc="neumann", nt=16, T=0.01, tol=1e-10, tol_update=1e-9,
+                   init_guess=2, max_iter=60))
+    p = oprob(kw)
+    x = (np.arange(nx) + 0.5) / nx
+    u0 = np.cos(np.pi * x) + 0.5 * np.cos(3 * np.pi * x) - 0.25 * np.cos(7 * np.pi * x)
+    res = {}
+    for fx in (True, False):
+        with pint.Solver(**kw) as s:
+            s.set_fx_residual(fx)
+            U = torch.zeros(p.nt, p.nspace, dtype=torch.float64, device="cuda")
+            st = s.solve(dev(u0), U, check=False)
+            res[fx] = (host(U), st)
+    st_fx, st_64 = res[True][1], res[False][1]
+    assert st_fx["rc"] == 0 and st_64["rc"] == 0, (st_fx, st_64)
+    assert st_fx["iters"] <= st_64["iters"] + 2, (st_fx["hist"], st_64["hist"])
+    assert O.rel_err(res[True][0], res[False][0]) < 1e-8
 
 
 @pytest.mark.parametrize("alpha", [1e-2, 1e-3])

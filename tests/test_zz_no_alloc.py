@@ -23,6 +23,11 @@ CASES = [
     dict(equation="linear_ch", dim=2, nx=64, ny=48, bc="neumann", eps=0.05, beta=0.5, T=0.005, nt=16),
     dict(equation="cahn_hilliard", dim=2, nx=40, ny=40, bc="neumann", eps=0.05, T=8e-4, nt=8),
     dict(equation="biharmonic", dim=1, nx=64, ny=1, bc="ss", T=0.01, nt=32),
+    # Crank-Nicolson and Eyre's splitting: the first level of ||b|| then comes from a one-level residual
+    dict(equation="linear_ch", dim=2, nx=48, ny=32, bc="neumann", eps=0.05, beta=0.5, T=0.005, nt=8, theta=0.5),
+    dict(equation="cahn_hilliard_eyre", dim=2, nx=32, ny=32, bc="neumann", eps=0.05, T=8e-4, nt=8),
+    # the largest grid the library accepts (4096 x 1024 points): its residual grid is the largest
+    dict(equation="linear_ch", dim=2, nx=4096, ny=1024, bc="neumann", eps=0.05, beta=0.5, T=1e-6, nt=2),
 ]
 
 
