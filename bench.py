@@ -420,6 +420,8 @@ def main_gpu(args) -> None:
                 sv.set_varying_jacobian(args.varying_jacobian)
         if args.no_graphs:
             sv.set_graphs(False)
+        if args.time_gemm != -1:
+            sv.set_time_gemm(args.time_gemm)
         return sv
 
     s = make_solver(kw)
@@ -607,6 +609,9 @@ def main_gpu(args) -> None:
                        "iterations": stats["iters"], "segments": stats.get("segments"),
                        "varying_jacobian": args.varying_jacobian or None,
                        "final_rel_residual": stats["rel_residual"], "l2": "flushed between steps",
+                       "time_transforms": {0: "fft", 1: "tensor-core DFT (step 1), fft (step 3)",
+                                           2: "fft (step 1), tensor-core DFT (step 3)",
+                                           3: "tensor-core DFT (steps 1, 3)"}[stats.get("time_gemm", 0)],
                        "parallelism": f"replicas x{world}"},
             "err_vs_oracle": (errs or {}).get("headline"),
             "oracle": oracle_info if oracle is not None else "not run (size or equation outside the CPU oracle's reach)",
@@ -786,6 +791,8 @@ def main() -> None:
     ap.add_argument("--variant-steps", type=int, default=10,
                     help="timed repeats of each other precision form and of the second alpha")
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle's sequential solution (error check)")
+    ap.add_argument("--time-gemm", type=int, default=-1, choices=[-1, 0, 1],
+                    help="time transforms: -1 chosen by measurement per handle, 0 FFT, 1 tensor-core DFT products")
     ap.add_argument("--oracle-worker", action="store_true")
     ap.add_argument("--oracle-out", default="")
     ap.add_argument("--init", type=int, default=2, choices=[0, 2],

@@ -135,6 +135,8 @@ typedef struct {
                                  the requested one up to amp 1 (0.1 for Cahn-Hilliard); for the linear
                                  equations PINT_MIXED (FP64 residual and iterate) up to amp 1e3; beyond,
                                  PINT_FP64, where FP32 inner solves cannot be refined */
+    int    time_gemm;         /* time transforms on the tensor cores (PINT_OPT_TIME_GEMM): bit 0 Step 1,
+                                 bit 1 Step 3, in the last window solved */
 } pint_stats;
 
 typedef struct pint_handle pint_handle;
@@ -257,7 +259,29 @@ int pint_profile_read(pint_handle* h, pint_profile* out, int reset);
  *    pint_residual) in block fixed point on the integer pipes; 0 = the FP64
  *    residual kernel.  Errors: PINT_EINVAL for value 1 where it is not supported. */
 #define PINT_OPT_FX_RESIDUAL 6
+/*  PINT_OPT_LOG_INVARIANTS (default 0): after each window (or segment) of a solve,
+ *    record for every time level its mass h^d sum_i u_i and its discrete energy
+ *    E_h(u) = h^d sum_i (u_i^2 - 1)^2 / 4 + (eps^2/2) h^(d-2) sum over the grid's interior faces
+ *    of (u_j - u_i)^2 (the Cahn-Hilliard functional of Sec. 1, Eq. 1.5; both are conserved /
+ *    non-increasing along the backward-Euler solution, Sec. 5.3-5.4), reduced on the device in a
+ *    fixed order.  Read them with pint_invariants.  Enabling allocates n_windows * nt pairs.
+ *    Errors: PINT_EINVAL, PINT_ENOMEM. */
+#define PINT_OPT_LOG_INVARIANTS 7
+/*  PINT_OPT_TIME_GEMM (default -1): for N_t = 64 or 128 with FP32 transforms and a point count
+ *    divisible by 4, Steps 1 and 3 can run as dense DFT matrix products on the tensor cores
+ *    (split-FP16 operands, FP32 accumulation, about 2^-22 of each point's largest value) instead
+ *    of FFTs.  -1: chosen by measurement on the first pint_solve (each direction timed both
+ *    ways on this handle's sizes); 0: FFT; 1: matrix products (Step 3 only for PINT_MIXED, whose
+ *    FP64 update it carries).  pint_stats.time_gemm reports the choice.
+ *    Errors: PINT_EINVAL (value out of range, or 1 where unsupported). */
+#define PINT_OPT_TIME_GEMM 8
 int pint_set_option(pint_handle* h, int option, long long value);
+
+/* Copy the invariants recorded by the last pint_solve (PINT_OPT_LOG_INVARIANTS) into
+ * mass_host[i], energy_host[i], i = 0 .. min(cap, levels) - 1, for time levels 1, 2, ... of
+ * the whole solve (all windows).  Returns the number of levels recorded (>= 0), or PINT_EINVAL
+ * (logging not enabled, bad arguments) / PINT_ECUDA.  Synchronizes the handle's stream. */
+int pint_invariants(pint_handle* h, double* mass_host, double* energy_host, long long cap);
 
 /* pint_residual_static: the residual of pint_residual for callers that cannot
  * allocate device memory when they need it (a process whose device memory is

@@ -322,6 +322,57 @@ __global__ void k_scale_cast(const double* __restrict__ r, const double* __restr
         s[i] = (TS)(gam[i / nspace] * r[i]);
 }
 
+// Cahn-Hilliard invariants of each time level of a window (Sec. 1, Eq. 1.5),
+// one CTA per level, deterministic (fixed per-thread order and tree):
+//   out[2n]     = h^d sum_i u_i                                   (mass)
+//   out[2n + 1] = h^d sum_i (u_i^2 - 1)^2 / 4
+//                 + (eps^2 / 2) h^(d-2) sum over interior faces (u_j - u_i)^2   (discrete energy)
+// U is FP64, or float-float (hi, lo) for the PINT_MIXED_FF iterate.
+__device__ __forceinline__ double inv_val(const double* U, size_t i) { return U[i]; }
+__device__ __forceinline__ double inv_val(const float2* U, size_t i) {
+    const float2 v = U[i];
+    return (double)v.x + (double)v.y;
+}
+template <class T>
+__global__ void __launch_bounds__(256) k_invariants(const T* __restrict__ U, int nx, int ny, int dim, double hd,
+                                                    double gcoef, double* __restrict__ out) {
+    __shared__ double rm[8], re[8], rg[8];
+    const int n = blockIdx.x;
+    const size_t ns = (size_t)nx * (dim == 2 ? ny : 1);
+    const T* u = U + (size_t)n * ns;
+    double m = 0.0, e = 0.0, gsum = 0.0;
+    for (size_t i = threadIdx.x; i < ns; i += 256) {
+        const double v = inv_val(u, i);
+        const int x = (int)(i % nx);
+        m += v;
+        const double w = v * v - 1.0;
+        e = fma(0.25 * w, w, e);
+        if (x + 1 < nx) {
+            const double d = inv_val(u, i + 1) - v;
+            gsum = fma(d, d, gsum);
+        }
+        if (dim == 2 && i + nx < ns) {
+            const double d = inv_val(u, i + nx) - v;
+            gsum = fma(d, d, gsum);
+        }
+    }
+    m = warp_sum(m);
+    e = warp_sum(e);
+    gsum = warp_sum(gsum);
+    if (threadIdx.x % 32 == 0) {
+        rm[threadIdx.x / 32] = m;
+        re[threadIdx.x / 32] = e;
+        rg[threadIdx.x / 32] = gsum;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double M = 0.0, Eb = 0.0, G = 0.0;
+        for (int w = 0; w < 8; ++w) { M += rm[w]; Eb += re[w]; G += rg[w]; }
+        out[2 * n] = hd * M;
+        out[2 * n + 1] = hd * Eb + gcoef * G;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
@@ -409,5 +460,15 @@ void launch_scale_cast(const double* r, const double* gam, TS* s, int nspace, in
 }
 template void launch_scale_cast<float>(const double*, const double*, float*, int, int, cudaStream_t);
 template void launch_scale_cast<double>(const double*, const double*, double*, int, int, cudaStream_t);
+
+template <class T>
+void launch_invariants(const T* U, int nlev, const Geo& g, double eps, double h, double* out, cudaStream_t st) {
+    if (nlev <= 0) return;
+    const double hd = g.dim == 2 ? h * h : h;
+    const double gcoef = 0.5 * eps * eps * (g.dim == 2 ? 1.0 : 1.0 / h);   // (eps^2/2) h^(d-2)
+    k_invariants<T><<<nlev, 256, 0, st>>>(U, g.nx, g.ny, g.dim, hd, gcoef, out);
+}
+template void launch_invariants<double>(const double*, int, const Geo&, double, double, double*, cudaStream_t);
+template void launch_invariants<float2>(const float2*, int, const Geo&, double, double, double*, cudaStream_t);
 
 }  // namespace pint

@@ -28,6 +28,7 @@ namespace pint {
 template <class T> cudaError_t configure_time_all();
 template <class T> cudaError_t configure_spatial_all();
 cudaError_t configure_residual_ff();
+cudaError_t configure_time_gemm();
 
 cudaError_t configure_kernels() {
     static int done = -1;  // per process: the attributes are per device function
@@ -40,6 +41,7 @@ cudaError_t configure_kernels() {
     if ((e = configure_spatial_all<float>()) != cudaSuccess) return e;
     if ((e = configure_spatial_all<double>()) != cudaSuccess) return e;
     if ((e = configure_residual_ff()) != cudaSuccess) return e;
+    if ((e = configure_time_gemm()) != cudaSuccess) return e;
     done = dev;
     return cudaSuccess;
 }
@@ -154,6 +156,11 @@ struct pint_handle {
     float* igamf = nullptr;         // PINT_MIXED: 1 / gamma_n (its norm partials)
     pint::GeoFX gfx;                // block fixed-point residual geometry
     int use_fx = 0;                 // PINT_MIXED with the block fixed-point residual (linear, square cells)
+    // time transforms as DFT matrix products on the tensor cores (k_timegemm.cu)
+    int tgemm_mode = -1;            // -1: chosen by measurement on the first solve, 0: off, 1: on
+    int gemm_fwd = 0, gemm_inv = 0; // in use for Step 1 / Step 3 (FP64 update)
+    int tgemm_tuned = 0;
+    void* wgemm = nullptr;          // FP16 DFT tables (hi, lo) of both directions for N_t = p.nt
     double* u0buf = nullptr;        // window initial condition
     double* b1 = nullptr;           // theta < 1: first right-hand-side level u0/dt - (1-theta) A u0
     double* hU = nullptr;           // pint_solve_host buffers (lazy)
@@ -222,6 +229,10 @@ struct pint_handle {
     double* jcoef_h = nullptr; // pinned host staging of the coefficients
     double vary_tol = 1e-4;    // relative residual of the inner solve
     long long inner_iters = 0; // inner GMRES iterations (statistics)
+    // per-level invariants (PINT_OPT_LOG_INVARIANTS): (mass, energy) of every time level solved
+    int log_inv = 0;
+    double* inv_dev = nullptr;  // n_windows * nt pairs
+    long long inv_count = 0;    // levels logged by the last solve
 };
 
 namespace pint {
@@ -537,6 +548,7 @@ static long long footprint_of(const pint_problem* p) {
     b += z.tables_bytes;
     if (p->precision == PINT_MIXED_FF) b += z.dof * 8 + z.nspace * 8 + 2 * (size_t)p->nt * 4;
     if (p->precision == PINT_MIXED) b += (size_t)p->nt * (sizeof(double) + sizeof(float));
+    if (f32_transforms(p) && time_gemm_supported(p->nt, (int)z.nspace)) b += (size_t)4 * p->nt * p->nt * 2;
     return b;
 }
 
@@ -590,6 +602,26 @@ static void prof_end(pint_handle* h, int ph, int nlaunch) {
 // ---------------------------------------------------------------------------
 // The iteration
 // ---------------------------------------------------------------------------
+// Whether the tensor-core transforms apply to the current time axis (the table
+// is built for the handle's N_t; shorter adaptive segments use the FFT).
+static bool gemm_ok(const pint_handle* h) {
+    return h->wgemm && h->geo.nt == h->p.nt && time_gemm_supported(h->geo.nt, h->geo.nspace);
+}
+static bool use_gemm_fwd(const pint_handle* h) { return h->gemm_fwd && gemm_ok(h); }
+static bool use_gemm_inv(const pint_handle* h) {
+    return h->gemm_inv && gemm_ok(h) && h->p.precision == PINT_MIXED;
+}
+// Step 1 on the FP32 path: DFT matrix product or FFT
+static cudaError_t tfwd_f32(pint_handle* h, const float* s, float2* S) {
+    const Geo& g = h->geo;
+    if (use_gemm_fwd(h)) return launch_time_gemm(0, g.nt, g.nspace, s, S, h->wgemm, nullptr, h->ctl, nullptr, h->st);
+    return launch_time_fwd<float>(g.nt, g.nspace, s, S, tabs_of<float>(h).twt, h->ctl, h->st);
+}
+// CTAs writing update-size partials in Step 3 of PINT_MIXED
+static int tinv_blocks(pint_handle* h) {
+    return use_gemm_inv(h) ? time_gemm_blocks(h->geo.nspace) : time_inv_blocks(h->geo.nt, h->geo.nspace, 1);
+}
+
 template <class T> struct Impl {
     static cudaError_t spatial(pint_handle* h, c_t<T>* S, const Tabs<T>& tb) {
         if (fused_spatial(h)) {
@@ -747,20 +779,33 @@ template <class T> struct Impl {
         }
         prof_end(h, PH_RES, 1);
         prof_begin(h, PH_CHECK);
+        const int ndp = !upd_part(h) ? 0 : std::is_same<T, float>::value ? tinv_blocks(h)
+                                                                          : time_inv_blocks(g.nt, g.nspace, 0);
         launch_after_residual(h->partials, np, 1.0 / ((double)g.nt * g.nspace), h->ctl, h->st, h->gcond, h->capturing,
-                              upd_part(h), upd_part(h) ? time_inv_blocks(g.nt, g.nspace, f32_transforms(&h->p)) : 0);
+                              upd_part(h), ndp);
         prof_end(h, PH_CHECK, 1);
         prof_begin(h, PH_TFWD);
-        cudaError_t e = launch_time_fwd<T>(g.nt, g.nspace, s, S, tb.twt, h->ctl, h->st);
-        prof_end(h, PH_TFWD, time_fwd_launches(g.nt));
+        cudaError_t e;
+        if constexpr (std::is_same<T, float>::value) {
+            e = tfwd_f32(h, s, S);
+            prof_end(h, PH_TFWD, use_gemm_fwd(h) ? 1 : time_fwd_launches(g.nt));
+        } else {
+            e = launch_time_fwd<T>(g.nt, g.nspace, s, S, tb.twt, h->ctl, h->st);
+            prof_end(h, PH_TFWD, time_fwd_launches(g.nt));
+        }
         if (e != cudaSuccess) return e;
         const bool lf = long_fused(h);
         const LongSolve<T> ls{&tb, h->coef, g.nx};
         if (!lf && (e = step2(h, S, tb, U, nullptr)) != cudaSuccess) return e;
         prof_begin(h, PH_TINV);
-        e = launch_time_inv<T>(g.nt, g.nspace, S, tb.twt, h->ginv, U, 1, h->ctl, upd_part(h), h->st, h->s,
-                               lf ? &ls : nullptr);
-        prof_end(h, PH_TINV, time_inv_launches(g.nt));
+        if (std::is_same<T, float>::value && use_gemm_inv(h)) {
+            e = launch_time_gemm(1, g.nt, g.nspace, S, U, h->wgemm, h->ginv, h->ctl, upd_part(h), h->st);
+            prof_end(h, PH_TINV, 1);
+        } else {
+            e = launch_time_inv<T>(g.nt, g.nspace, S, tb.twt, h->ginv, U, 1, h->ctl, upd_part(h), h->st, h->s,
+                                   lf ? &ls : nullptr);
+            prof_end(h, PH_TINV, time_inv_launches(g.nt));
+        }
         if (e != cudaSuccess) return e;
         return cudaGetLastError();
     }
@@ -771,13 +816,21 @@ template <class T> struct Impl {
         const Tabs<T>& tb = tabs_of<T>(h);
         launch_set_running(h->ctl, jbar, h->st);
         launch_scale_cast<T>(r, h->gam, s, g.nspace, g.nt, h->st);
-        cudaError_t e = launch_time_fwd<T>(g.nt, g.nspace, s, S, tb.twt, h->ctl, h->st);
+        cudaError_t e;
+        if constexpr (std::is_same<T, float>::value) e = tfwd_f32(h, s, S);
+        else e = launch_time_fwd<T>(g.nt, g.nspace, s, S, tb.twt, h->ctl, h->st);
         if (e != cudaSuccess) return e;
         const bool lf = long_fused(h);
         const LongSolve<T> ls{&tb, h->coef, g.nx};
         if (!lf && (e = spatial(h, S, tb)) != cudaSuccess) return e;
-        e = launch_time_inv<T>(g.nt, g.nspace, S, tb.twt, h->ginv, delta, 0, h->ctl, nullptr, h->st, h->s,
-                               lf ? &ls : nullptr);
+        if (std::is_same<T, float>::value && use_gemm_inv(h)) {
+            // the matrix-product inverse accumulates: delta = 0 + P^{-1} r
+            if ((e = cudaMemsetAsync(delta, 0, (size_t)g.nt * g.nspace * sizeof(double), h->st)) != cudaSuccess) return e;
+            e = launch_time_gemm(1, g.nt, g.nspace, S, delta, h->wgemm, h->ginv, h->ctl, nullptr, h->st);
+        } else {
+            e = launch_time_inv<T>(g.nt, g.nspace, S, tb.twt, h->ginv, delta, 0, h->ctl, nullptr, h->st, h->s,
+                                   lf ? &ls : nullptr);
+        }
         if (e != cudaSuccess) return e;
         return cudaGetLastError();
     }
@@ -806,10 +859,12 @@ static cudaError_t zero_start(pint_handle* h, double* U, const double* u0w) {
         if (h->p.precision == PINT_MIXED_FF)
             e = launch_time_inv_ff(g.nt, g.nspace, reinterpret_cast<float2*>(h->S), tb.twt, h->ginvf, h->Uff_cur, h->ctl,
                                    upd_part(h), h->st, h->s, lf ? &ls : nullptr);
+        else if (use_gemm_inv(h))
+            e = launch_time_gemm(1, g.nt, g.nspace, h->S, U, h->wgemm, h->ginv, h->ctl, upd_part(h), h->st);
         else
             e = launch_time_inv<float>(g.nt, g.nspace, reinterpret_cast<float2*>(h->S), tb.twt, h->ginv, U, 1, h->ctl,
                                        upd_part(h), h->st, h->s, lf ? &ls : nullptr);
-        prof_end(h, PH_TINV, time_inv_launches(g.nt));
+        prof_end(h, PH_TINV, (h->p.precision != PINT_MIXED_FF && use_gemm_inv(h)) ? 1 : time_inv_launches(g.nt));
     } else {
         const Tabs<double>& tb = tabs_of<double>(h);
         const LongSolve<double> ls{&tb, h->coef, g.nx};
@@ -839,8 +894,8 @@ static cudaError_t iteration_ff(pint_handle* h) {
                               upd_part(h), upd_part(h) ? time_inv_ff_blocks(g.nt, g.nspace, h->ctl) : 0);
     prof_end(h, PH_CHECK, 1);
     prof_begin(h, PH_TFWD);
-    cudaError_t e = launch_time_fwd<float>(g.nt, g.nspace, s, S, tb.twt, h->ctl, h->st);
-    prof_end(h, PH_TFWD, time_fwd_launches(g.nt));
+    cudaError_t e = tfwd_f32(h, s, S);
+    prof_end(h, PH_TFWD, use_gemm_fwd(h) ? 1 : time_fwd_launches(g.nt));
     if (e != cudaSuccess) return e;
     const bool lf = long_fused(h);
     const LongSolve<float> ls{&tb, h->coef, g.nx};
@@ -1025,6 +1080,8 @@ void pint_destroy(pint_handle* h) {
     af(h->jt);
     af(h->jpart);
     af(h->jcoef);
+    af(h->inv_dev);
+    af(h->wgemm);
     if (h->jcoef_h) cudaFreeHost(h->jcoef_h);
     if (h->nlev > 0) activate_level(h, 0);   // the base level owns gam/ginv/gamf/ginvf and tabs_ptrs
     for (int i = 1; i < h->nlev; ++i) {
@@ -1109,6 +1166,15 @@ int pint_create(const pint_problem* p, void* cuda_stream, pint_handle** out) {
         if (!rc) rc = dalloc((void**)&h->gamf, p->nt * sizeof(float));
         if (!rc) rc = dalloc((void**)&h->ginvf, p->nt * sizeof(float));
     }
+    if (!rc && f32_transforms(p) && time_gemm_supported(p->nt, (int)z.nspace)) {
+        std::vector<uint16_t> wt;
+        time_gemm_tables(p->nt, wt);
+        rc = dalloc(&h->wgemm, wt.size() * sizeof(uint16_t));
+        if (!rc && cudaMemcpyAsync(h->wgemm, wt.data(), wt.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, h->st) !=
+                       cudaSuccess)
+            rc = PINT_ECUDA;
+        if (!rc) cudaStreamSynchronize(h->st);   // the host vector goes out of scope
+    }
     if (!rc && !(h->hctl = ctl_slab_acquire())) rc = PINT_ENOMEM;
     if (!rc) rc = f32_transforms(p) ? build_tables<float>(h) : build_tables<double>(h);
     if (!rc && cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->st) != cudaSuccess) rc = PINT_ECUDA;
@@ -1163,6 +1229,15 @@ int pint_set_option(pint_handle* h, int option, long long value) {
         case PINT_OPT_GRAPHS:
             if (value != 0 && value != 1) return PINT_EINVAL;
             h->use_graphs = (int)value;
+            return PINT_OK;
+        case PINT_OPT_TIME_GEMM:
+            if (value < -1 || value > 1) return PINT_EINVAL;
+            if (value == 1 && !h->wgemm) return PINT_EINVAL;
+            h->tgemm_mode = (int)value;
+            h->tgemm_tuned = value >= 0 ? 1 : 0;
+            h->gemm_fwd = h->gemm_inv = value == 1 ? 1 : 0;
+            for (auto& sl : h->gslot)   // captured loops hold the old kernel choice
+                if (sl.exec) { cudaGraphExecDestroy(sl.exec); sl.exec = nullptr; }
             return PINT_OK;
         case PINT_OPT_FX_RESIDUAL:
             if (value != 0 && value != 1) return PINT_EINVAL;
@@ -1222,6 +1297,18 @@ int pint_set_option(pint_handle* h, int option, long long value) {
                 cudaMallocHost((void**)&h->jcoef_h, (kMaxKrylov + 2) * 2 * sizeof(double)) != cudaSuccess)
                 return PINT_ENOMEM;
             h->vary = (int)value;
+            return PINT_OK;
+        }
+        case PINT_OPT_LOG_INVARIANTS: {
+            if (value != 0 && value != 1) return PINT_EINVAL;
+            if (value && !h->inv_dev) {
+                const size_t n = (size_t)h->p.n_windows * h->p.nt * 2;
+                if (cudaMallocAsync((void**)&h->inv_dev, n * sizeof(double), h->st) != cudaSuccess) {
+                    cudaGetLastError();
+                    return PINT_ENOMEM;
+                }
+            }
+            h->log_inv = (int)value;
             return PINT_OK;
         }
         case PINT_OPT_ADAPTIVE_WINDOWS: {
@@ -1394,6 +1481,56 @@ static int gmres_window(pint_handle* h, double* U, const double* u0w) {
     return PINT_OK;
 }
 
+// Choose, by measurement on this handle's sizes, between the FFT kernels and the
+// tensor-core DFT products for Step 1 and (PINT_MIXED) Step 3: each variant runs
+// twice to warm up and five times timed with CUDA events on the handle's
+// stream; the faster one is kept for the handle's life.
+static int tune_time_gemm(pint_handle* h) {
+    h->tgemm_tuned = 1;
+    if (!h->wgemm || !time_gemm_supported(h->p.nt, h->geo.nspace)) return PINT_OK;
+    const Geo& g = h->geo;
+    const size_t dof = (size_t)g.nt * g.nspace;
+    double* tU = nullptr;
+    if (cudaMallocAsync((void**)&tU, dof * sizeof(double), h->st) != cudaSuccess) {
+        cudaGetLastError();
+        return PINT_OK;   // keep the FFT
+    }
+    PINT_CK(cudaMemsetAsync(tU, 0, dof * sizeof(double), h->st));
+    cudaEvent_t e0, e1;
+    PINT_CK(cudaEventCreate(&e0));
+    PINT_CK(cudaEventCreate(&e1));
+    const Tabs<float>& tb = tabs_of<float>(h);
+    float* s = reinterpret_cast<float*>(h->s);
+    float2* S = reinterpret_cast<float2*>(h->S);
+    auto timeit = [&](auto fn) -> float {
+        launch_set_running(h->ctl, 0.0, h->st);
+        fn();
+        fn();
+        cudaEventRecord(e0, h->st);
+        for (int i = 0; i < 5; ++i) fn();
+        cudaEventRecord(e1, h->st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return cudaGetLastError() == cudaSuccess ? ms : 1e30f;
+    };
+    const float ff = timeit([&] { launch_time_fwd<float>(g.nt, g.nspace, s, S, tb.twt, h->ctl, h->st); });
+    const float gf = timeit([&] { launch_time_gemm(0, g.nt, g.nspace, s, S, h->wgemm, nullptr, h->ctl, nullptr, h->st); });
+    h->gemm_fwd = gf < ff ? 1 : 0;
+    if (h->p.precision == PINT_MIXED) {
+        const float fi = timeit([&] {
+            launch_time_inv<float>(g.nt, g.nspace, S, tb.twt, h->ginv, tU, 1, h->ctl, nullptr, h->st, h->s, nullptr);
+        });
+        const float gi = timeit([&] { launch_time_gemm(1, g.nt, g.nspace, S, tU, h->wgemm, h->ginv, h->ctl, nullptr, h->st); });
+        h->gemm_inv = gi < fi ? 1 : 0;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(tU, h->st);
+    PINT_CK(cudaStreamSynchronize(h->st));
+    return PINT_OK;
+}
+
 // The solve; with U_host, the device-to-host copy of the result is queued
 // before the final synchronization, so it needs no round trip of its own.
 static int solve_impl(pint_handle* h, const double* u0_dev, double* U_dev, pint_stats* st, double* U_host) {
@@ -1411,6 +1548,7 @@ static int solve_impl(pint_handle* h, const double* u0_dev, double* U_dev, pint_
     int rc = PINT_OK;
     bool converted = false;   // float-float result already converted to U_dev
     activate_level(h, 0);
+    if (!h->tgemm_tuned && h->tgemm_mode == -1 && (rc = tune_time_gemm(h)) != PINT_OK) return rc;
     // Cahn-Hilliard never starts from the zero iterate: its scalar Jacobian
     // 3 mean(u^2) would be 0 in the first preconditioner, far from the state's,
     // and the iteration can diverge; such windows start from u0 instead.
@@ -1418,6 +1556,7 @@ static int solve_impl(pint_handle* h, const double* u0_dev, double* U_dev, pint_
     if (ffm && init == 1) launch_f64_to_ff(U_dev, h->Uff, dof, h->st);
     const long long total = (long long)ntmax * p.n_windows;
     long long done = 0;
+    h->inv_count = 0;
     for (int seg = 0; done < total; ++seg) {
         const int base = (int)(done % ntmax);   // offset of this segment inside its window
         const double* u0w = seg == 0 ? u0_dev : h->u0buf;
@@ -1478,9 +1617,9 @@ static int solve_impl(pint_handle* h, const double* u0_dev, double* U_dev, pint_
                 const long long runs = h->hctl->iter + 1 - (init == 2 ? 1 : 0);
                 h->launches[PH_RES] += runs;
                 h->launches[PH_CHECK] += runs;
-                h->launches[PH_TFWD] += runs * time_fwd_launches(g.nt);
+                h->launches[PH_TFWD] += runs * (use_gemm_fwd(h) ? 1 : time_fwd_launches(g.nt));
                 for (int stg = 0; stg < spatial_launches(h); ++stg) h->launches[PH_SP0 + stg] += runs;
-                h->launches[PH_TINV] += runs * time_inv_launches(g.nt);
+                h->launches[PH_TINV] += runs * (use_gemm_inv(h) ? 1 : time_inv_launches(g.nt));
             } else {
                 int enqueued = 0;
                 for (;;) {
@@ -1514,12 +1653,21 @@ static int solve_impl(pint_handle* h, const double* u0_dev, double* U_dev, pint_
         S.rel_residual = c.rho;
         S.update_norm = p.tol_update > 0.0 ? c.dnorm : 0.0;
         S.precision = p.precision;
+        S.time_gemm = (use_gemm_fwd(h) ? 1 : 0) | (use_gemm_inv(h) ? 2 : 0);
         S.jbar = h->coef.ch ? c.jbar : 0.0;
         for (int i = 0; i <= k && i < PINT_HIST_MAX; ++i) S.hist[i] = c.hist[i];
         S.contraction = k >= 2 ? pow(c.hist[k] / c.hist[1], 1.0 / (k - 1)) : (k == 1 ? c.hist[1] / c.hist[0] : 0.0);
         if (c.status != PINT_OK) {
             rc = c.status;
             break;
+        }
+        if (h->log_inv) {
+            // mass and discrete energy of the segment's L levels (time levels done+1 .. done+L)
+            const double hh = grid_h(p.nx, p.bc);
+            if (ffm) launch_invariants<float2>(h->Uff_cur, L, g, p.eps, hh, h->inv_dev + 2 * done, h->st);
+            else launch_invariants<double>(Useg, L, g, p.eps, hh, h->inv_dev + 2 * done, h->st);
+            h->launches[PH_SETUP] += 1;
+            h->inv_count = done + L;
         }
         done += L;
         S.windows = (int)(done / ntmax);
@@ -1608,6 +1756,22 @@ int pint_residual(pint_handle* h, const double* u0_dev, const double* U_dev, dou
     if (rc != PINT_OK) return rc;
     if (rel_res) *rel_res = h->hctl->rho;
     return PINT_OK;
+}
+
+int pint_invariants(pint_handle* h, double* mass_host, double* energy_host, long long cap) {
+    if (!h || cap < 0 || (cap > 0 && (!mass_host || !energy_host))) return PINT_EINVAL;
+    if (!h->log_inv || !h->inv_dev) return PINT_EINVAL;
+    const long long n = h->inv_count < cap ? h->inv_count : cap;
+    if (n > 0) {
+        std::vector<double> buf((size_t)n * 2);
+        PINT_CK(cudaMemcpyAsync(buf.data(), h->inv_dev, buf.size() * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+        PINT_CK(cudaStreamSynchronize(h->st));
+        for (long long i = 0; i < n; ++i) {
+            mass_host[i] = buf[2 * i];
+            energy_host[i] = buf[2 * i + 1];
+        }
+    }
+    return (int)(h->inv_count > 0x7fffffff ? 0x7fffffff : h->inv_count);
 }
 
 int pint_precond_apply(pint_handle* h, double jbar, const double* r_dev, double* delta_dev) {

@@ -40,6 +40,33 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 }
 
 
+// Exact FP32 -> FP64 conversion by bit assembly on the integer pipes (the
+// conversion instruction would run on the FP64 pipe).  Normal numbers rebias
+// the exponent; zeros, subnormals (normalized here), infinities and NaNs are
+// handled by the same integer operations.  For T = double it is the identity.
+__device__ __forceinline__ double f32_to_f64_exact(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t sgn = b & 0x80000000u, e = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
+    uint32_t hi, lo;
+    if (e - 1u < 0xFEu) {            // normal
+        hi = sgn | ((e + 896u) << 20) | (m >> 3);
+        lo = m << 29;
+    } else if (e == 0xFFu) {         // infinity / NaN
+        hi = sgn | 0x7FF00000u | (m >> 3);
+        lo = m << 29;
+    } else if (m == 0u) {            // zero
+        hi = sgn;
+        lo = 0u;
+    } else {                         // subnormal: m 2^-149 with the leading bit of m at position p
+        const int p = 31 - __clz((int)m);
+        const uint32_t mn = (m << (23 - p)) & 0x7FFFFFu;   // fraction bits after the leading one
+        hi = sgn | ((uint32_t)(p + 874) << 20) | (mn >> 3);
+        lo = mn << 29;
+    }
+    return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ double f32_to_f64_exact(double d) { return d; }
+
 template <class T> struct cplx_of;
 template <> struct cplx_of<float> { using type = float2; };
 template <> struct cplx_of<double> { using type = double2; };

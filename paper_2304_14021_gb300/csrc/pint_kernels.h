@@ -2,6 +2,9 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
 
 #include "fx.cuh"
 #include "pint_common.cuh"
@@ -193,6 +196,22 @@ int slice2d_supported(const Geo& g, int fft_x, int fft_y, int f32);
 template <class T>
 cudaError_t launch_slice2d(const Geo& g, c_t<T>* S, const Tabs<T>& tb, SolveCoef co, const Ctl* ctl,
                            cudaStream_t st);
+
+// Per-level Cahn-Hilliard mass and discrete energy (Eq. 1.5) of nlev levels of U
+// (FP64 or float-float), one (mass, energy) pair per level into out.
+template <class T>
+void launch_invariants(const T* U, int nlev, const Geo& g, double eps, double h, double* out, cudaStream_t st);
+
+// Steps 1 and 3 as DFT matrix products on the tensor cores (k_timegemm.cu), for
+// N_t = 64 or 128 and a point count divisible by 4.  Tables: FP16 hi and lo parts of
+// the forward and inverse matrices (time_gemm_tables).  inv = 0: src = s (FP32
+// [n][p]), dst = S (complex64 half spectrum); inv = 1: src = S, dst = U (FP64),
+// U += gamma^{-1} x / N_t, with (sum delta^2, sum U^2) per CTA in dpart (may be NULL).
+int time_gemm_supported(int nt, int nspace);
+int time_gemm_blocks(int nspace);
+void time_gemm_tables(int nt, std::vector<uint16_t>& out);
+cudaError_t launch_time_gemm(int inv, int nt, int nspace, const void* src, void* dst, const void* wtab,
+                             const double* ginv, Ctl* ctl, double* dpart, cudaStream_t st);
 
 // Opt-in shared memory sizes for the kernels that need more than 48 KB.
 cudaError_t configure_kernels();

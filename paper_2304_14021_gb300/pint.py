@@ -37,14 +37,14 @@ class Stats(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("windows", C.c_int), ("iters_last", C.c_int),
                 ("rel_residual", C.c_double), ("contraction", C.c_double), ("jbar", C.c_double),
                 ("hist", C.c_double * HIST_MAX), ("segments", C.c_int), ("nt_min", C.c_int),
-                ("retries", C.c_int), ("update_norm", C.c_double), ("precision", C.c_int)]
+                ("retries", C.c_int), ("update_norm", C.c_double), ("precision", C.c_int), ("time_gemm", C.c_int)]
 
     def as_dict(self) -> dict:
         return {"status": self.status, "iters": self.iters, "windows": self.windows,
                 "iters_last": self.iters_last, "rel_residual": self.rel_residual,
                 "contraction": self.contraction, "jbar": self.jbar, "segments": self.segments,
                 "nt_min": self.nt_min, "retries": self.retries, "update_norm": self.update_norm,
-                "precision": PRECISION_NAMES.get(self.precision, self.precision),
+                "precision": PRECISION_NAMES.get(self.precision, self.precision), "time_gemm": self.time_gemm,
                 "hist": [self.hist[i] for i in range(min(self.iters_last + 1, HIST_MAX))]}
 
 
@@ -75,6 +75,8 @@ def lib() -> C.CDLL:
         vp, dp = C.c_void_p, C.POINTER(C.c_double)
         L.pint_create.argtypes = [C.POINTER(Problem), vp, C.POINTER(vp)]
         L.pint_create.restype = C.c_int
+        L.pint_invariants.argtypes = [vp, dp, dp, C.c_longlong]
+        L.pint_invariants.restype = C.c_int
         L.pint_footprint.argtypes = [C.POINTER(Problem)]
         L.pint_footprint.restype = C.c_longlong
         L.pint_solve.argtypes = [vp, vp, vp, C.POINTER(Stats)]
@@ -250,11 +252,36 @@ class Solver:
         if rc != PINT_OK:
             raise PintError(rc, "pint_set_option")
 
+    def set_time_gemm(self, mode: int) -> None:
+        """Steps 1 and 3 as tensor-core DFT products: -1 chosen by measurement, 0 FFT, 1 matrix products."""
+        rc = lib().pint_set_option(self._h, 8, int(mode))
+        if rc != PINT_OK:
+            raise PintError(rc, "pint_set_option")
+
     def set_fx_residual(self, on: bool = True) -> None:
         """PINT_MIXED, linear equations: block fixed-point residual on the integer pipes (on) or FP64 kernel."""
         rc = lib().pint_set_option(self._h, 6, 1 if on else 0)
         if rc != PINT_OK:
             raise PintError(rc, "pint_set_option")
+
+    def set_log_invariants(self, on: bool = True) -> None:
+        """Record each time level's mass and discrete energy during pint_solve (read with invariants())."""
+        rc = lib().pint_set_option(self._h, 7, 1 if on else 0)
+        if rc != PINT_OK:
+            raise PintError(rc, "pint_set_option")
+
+    def invariants(self):
+        """(mass, energy) numpy arrays over all time levels of the last solve (pint_invariants)."""
+        import numpy as np
+        n = lib().pint_invariants(self._h, None, None, 0)
+        if n < 0:
+            raise PintError(n, "pint_invariants")
+        m, e = np.zeros(n), np.zeros(n)
+        rc = lib().pint_invariants(self._h, m.ctypes.data_as(C.POINTER(C.c_double)),
+                                   e.ctypes.data_as(C.POINTER(C.c_double)), n)
+        if rc < 0:
+            raise PintError(rc, "pint_invariants")
+        return m, e
 
     def set_adaptive_windows(self, on: bool = True) -> None:
         rc = lib().pint_set_option(self._h, 2, 1 if on else 0)

@@ -94,7 +94,7 @@ def test_precision_policy_falls_back_to_fp64_when_too_stiff():
     # 2-D linearized CH 256^2, N_t = 128, T = 0.1: about 0.03, FP32 inner solves kept
     mild = dict(equation="linear_ch", dim=2, nx=256, ny=256, bc="neumann", eps=0.05, beta=0.5, T=0.1, nt=128,
                 alpha=1e-2, tol=1e-8)
-    assert pint.footprint(**mild, precision="mixed_ff") < pint.footprint(**mild, precision="fp64")
+    assert pint.footprint(**mild, precision="mixed") < pint.footprint(**mild, precision="fp64")
     # 2-D biharmonic 512^2, dt = 0.01/256: amp about 10, a float-float request runs as PINT_MIXED
     mid = dict(equation="biharmonic", dim=2, nx=512, ny=512, bc="neumann", T=0.01, nt=256, alpha=1e-2, tol=1e-8)
     assert pint.footprint(**mid, precision="mixed_ff") == pint.footprint(**mid, precision="mixed")

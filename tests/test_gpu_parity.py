@@ -211,10 +211,17 @@ def test_config3_full_size_last_window_properties():
     u0 = synth.u0_ch(p.nspace, 0)
     with pint.Solver(**kw) as s:
         s.set_adaptive_windows(True)
+        s.set_log_invariants(True)
         U = torch.zeros(p.nt, p.nspace, dtype=torch.float64, device="cuda")
         st = s.solve(dev(u0), U, check=False)
+        mass, energy = s.invariants()
         U = host(U)
     assert st["rc"] == 0 and st["windows"] == 8, st
+    # all 2048 time levels of the 8 windows, recorded on the device (Eq. 1.5 invariants)
+    assert len(mass) == 2048
+    assert np.max(np.abs(mass - O.discrete_mass(p, u0))) < 1e-12
+    assert all(energy[i + 1] <= energy[i] * (1 + 1e-12) for i in range(len(energy) - 1))
+    assert energy[-1] < 0.5 * O.discrete_energy(p, u0)
     # levels 2..256 of the window solve the backward-Euler steps from level 1
     sub = O.Problem(equation=O.CAHN_HILLIARD, dim=2, nx=512, ny=512, bc="neumann", eps=0.02, T=255 * p.dt, nt=255)
     rho = np.linalg.norm(O.residual(sub, U[0], U[1:])) / O.rhs_norm(sub, U[0])
@@ -254,6 +261,35 @@ def test_cahn_hilliard_2d_windows(precision):
     E = [O.discrete_energy(p, u) for u in U]
     assert all(E[i + 1] <= E[i] + 1e-13 for i in range(len(E) - 1))
     assert 0.0 < st["jbar"] < 3.0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_ff"])
+def test_invariants_logged_on_device_match_oracle(precision):
+    # Per-level mass and discrete energy (Eq. 1.5) recorded by the device during the solve: every level
+    # of all windows; the last window's levels equal the oracle's invariants of the returned iterate,
+    # the earlier windows' those of the sequential solution.
+    nt, W = 16, 3
+    kw = full(dict(equation="cahn_hilliard", dim=2, nx=32, ny=32, bc="neumann", eps=0.05, nt=nt, n_windows=W,
+                   T=nt * W * 1e-4, alpha=1e-2, precision=precision, tol=1e-11))
+    p = oprob(kw)
+    u0 = synth.u0_ch(p.nspace, 0)
+    with pint.Solver(**kw) as s:
+        s.set_log_invariants(True)
+        U = torch.zeros(p.nt, p.nspace, dtype=torch.float64, device="cuda")
+        st = s.solve(dev(u0), U, check=False)
+        mass, energy = s.invariants()
+        U = host(U)
+    assert st["rc"] == 0 and len(mass) == nt * W
+    Em = [O.discrete_energy(p, u) for u in U]
+    Mm = [O.discrete_mass(p, u) for u in U]
+    assert np.max(np.abs(np.array(Mm) - mass[-nt:])) < 1e-15
+    assert np.max(np.abs(np.array(Em) - energy[-nt:]) / np.array(Em)) < 1e-13
+    Useq = O.sequential(p, u0)
+    Es = np.array([O.discrete_energy(p, u) for u in Useq])
+    tol = 1e-10 if precision == "fp64" else 1e-8
+    assert np.max(np.abs(Es - energy) / Es) < tol
+    assert np.max(np.abs(mass - O.discrete_mass(p, u0))) < 1e-12
+    assert all(energy[i + 1] <= energy[i] + 1e-13 for i in range(len(energy) - 1))
 
 
 def test_float_float_floor_stops_as_stagnation():

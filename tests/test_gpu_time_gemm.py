@@ -1,0 +1,106 @@
+"""Steps 1 and 3 as DFT matrix products on the tensor cores (PINT_OPT_TIME_GEMM)
+against the oracle: single preconditioner applications (Eq. 2.8) and full
+solves, N_t = 64 and 128, full and ragged point tiles, both mixed forms."""
+import numpy as np
+import pytest
+
+from oracle import pint_oracle as O
+from paper_2304_14021_gb300 import build_lib, pint, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build_lib.build()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def full(kw):
+    d = dict(equation="linear_ch", dim=2, nx=64, ny=64, bc="neumann", eps=0.05, beta=0.5, T=0.1, nt=128, n_windows=1,
+             theta=1.0, alpha=1e-2, tol=1e-10, max_iter=100, precision="mixed", init_guess=2)
+    d.update(kw)
+    if d["dim"] == 1:
+        d["ny"] = 1
+    return d
+
+
+def oprob(kw):
+    keys = ("equation", "dim", "nx", "ny", "bc", "eps", "beta", "T", "nt", "n_windows", "theta", "alpha")
+    return O.Problem(**{k: kw[k] for k in keys if k in kw})
+
+
+CASES = [
+    dict(nx=256, ny=256, nt=128),                              # config 2's grid
+    dict(nx=64, ny=64, nt=64, T=0.05),
+    dict(nx=36, ny=20, nt=128, T=0.1),                         # 720 points: a ragged last tile (80 points)
+    dict(dim=1, nx=512, nt=64, T=1e-5),
+    dict(equation="biharmonic", dim=2, nx=32, ny=32, bc="ss", nt=128, T=1e-3),
+    dict(equation="cahn_hilliard", nx=64, ny=64, nt=64, T=64e-4, eps=0.05),
+]
+
+
+@pytest.mark.parametrize("precision", ["mixed", "mixed_ff"])
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_gemm_precond_matches_oracle(case, precision):
+    kw = full(dict(CASES[case], precision=precision))
+    p = oprob(kw)
+    r = synth.random_iterate(p.nt, p.nspace, 300 + case)
+    jbar = 0.4 if kw["equation"] == "cahn_hilliard" else None
+    ref = O.diagonalized_apply_separable(p, p.alpha, r, jbar) if kw["bc"] == "neumann" else \
+        O.diagonalized_apply(p, p.alpha, r, jbar)
+    outs = {}
+    for mode in (1, 0):
+        with pint.Solver(**kw) as s:
+            s.set_time_gemm(mode)
+            out = torch.zeros(p.nt, p.nspace, dtype=torch.float64, device="cuda")
+            s.precond_apply(dev(r), out, jbar=jbar or 0.0)
+            outs[mode] = out.cpu().numpy()
+    # the same tolerance as the FFT path: complex64-level transforms amplified by up to 1/alpha
+    for mode, out in outs.items():
+        assert O.rel_err(out, ref) < 3e-6 / p.alpha, (mode, O.rel_err(out, ref))
+    # and of the same size as the FFT's own error
+    assert O.rel_err(outs[1], ref) < 4.0 * O.rel_err(outs[0], ref) + 1e-7
+
+
+@pytest.mark.parametrize("precision", ["mixed", "mixed_ff"])
+@pytest.mark.parametrize("case", [0, 2, 5])
+def test_gemm_solve_matches_sequential(case, precision):
+    kw = full(dict(CASES[case], precision=precision, tol=1e-10 if precision == "mixed" else 1e-9))
+    p = oprob(kw)
+    u0 = synth.u0_ch(p.nspace, 7) if kw["equation"] == "cahn_hilliard" else synth.u0_uniform(p.nspace, -0.05, 0.05, 7)
+    res = {}
+    for mode in (1, 0):
+        with pint.Solver(**kw) as s:
+            s.set_time_gemm(mode)
+            U = torch.zeros(p.nt, p.nspace, dtype=torch.float64, device="cuda")
+            st = s.solve(dev(u0), U, check=False)
+            assert st["rc"] == 0, st
+            assert st["time_gemm"] == (0 if mode == 0 else (3 if precision == "mixed" else 1)), st["time_gemm"]
+            res[mode] = (U.cpu().numpy(), st)
+    seq = O.sequential(p, u0)[-p.nt:]
+    assert O.rel_err(res[1][0], seq) < 1e-8
+    assert res[1][1]["iters"] <= res[0][1]["iters"] + 1
+
+
+def test_gemm_choice_by_measurement_is_reported():
+    kw = full(dict(nx=256, ny=256, nt=128, tol=1e-8))
+    p = oprob(kw)
+    u0 = synth.u0_uniform(p.nspace, -0.05, 0.05, 0)
+    with pint.Solver(**kw) as s:
+        U = torch.zeros(p.nt, p.nspace, dtype=torch.float64, device="cuda")
+        st = s.solve(dev(u0), U, check=False)
+    assert st["rc"] == 0 and st["time_gemm"] in (0, 1, 2, 3)
+
+
+def test_gemm_option_rejected_where_unsupported():
+    with pint.Solver(**full(dict(nt=256, T=0.2))) as s:
+        with pytest.raises(pint.PintError):
+            s.set_time_gemm(1)
+    with pint.Solver(**full(dict(precision="fp64"))) as s:
+        with pytest.raises(pint.PintError):
+            s.set_time_gemm(1)
