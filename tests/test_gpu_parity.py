@@ -263,6 +263,39 @@ def test_cahn_hilliard_2d_windows(precision):
     assert 0.0 < st["jbar"] < 3.0
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_config3_schedule_64x64_matches_oracle_sequential_newton(precision):
+    # Config 3's Cahn-Hilliard run (eps = 0.02, dt = 1e-4, 8 windows of 256 steps, adaptive segments)
+    # at 64 x 64, against the oracle's sequential Newton solution (Eq. 4.5; stored by
+    # tests/golden/make_ch_config3_64.py): the final state at sampled points, and the mass and energy
+    # of every 16th of the 2048 levels from the device's invariant log.
+    with open(os.path.join(GOLDEN, "ch_config3_64x64.json")) as f:
+        gold = json.load(f)
+    c = gold["case"]
+    kw = full(dict(equation="cahn_hilliard", dim=2, nx=c["nx"], ny=c["ny"], bc="neumann", eps=c["eps"], nt=c["nt"],
+                   n_windows=c["n_windows"], T=c["nt"] * c["n_windows"] * c["dt"], alpha=1e-2, precision=precision,
+                   tol=1e-11, max_iter=250))
+    p = oprob(kw)
+    u0 = synth.u0_ch(p.nspace, 0)
+    with pint.Solver(**kw) as s:
+        s.set_adaptive_windows(True)
+        s.set_log_invariants(True)
+        U = torch.zeros(p.nt, p.nspace, dtype=torch.float64, device="cuda")
+        st = s.solve(dev(u0), U, check=False)
+        mass, energy = s.invariants()
+        U = host(U)
+    assert st["rc"] == 0 and st["windows"] == c["n_windows"], st
+    final = np.array(gold["window_ends"][-1]["values"])
+    got = U[-1][:: gold["sample_every_point"]]
+    err_u = np.max(np.abs(got - final)) / np.max(np.abs(final))
+    lv = np.array(gold["levels"]) - 1
+    err_e = np.max(np.abs(energy[lv] - np.array(gold["energy"])) / np.array(gold["energy"]))
+    err_m = np.max(np.abs(mass[lv] - np.array(gold["mass"])))
+    print(f"config-3 schedule 64^2 {precision}: state {err_u:.2e} energy {err_e:.2e} mass {err_m:.2e} "
+          f"segments {st['segments']} iterations {st['iters']}")
+    assert err_u < 1e-8 and err_e < 1e-9 and err_m < 1e-12, (err_u, err_e, err_m)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_ff"])
 def test_invariants_logged_on_device_match_oracle(precision):
     # Per-level mass and discrete energy (Eq. 1.5) recorded by the device during the solve: every level

@@ -572,3 +572,28 @@ def test_paper_pint1_example_essentially_converged_after_four_iterations():
     ev = err(O.pint_iteration_varying(p, u0, Ui, its)[-1])
     es = err(O.pint_iteration_residual_form(p, u0, Ui, its, dense=False)[-1])
     assert ev < 5e-3 and ev < es, (ev, es)
+
+
+def test_golden_config3_64_fixture_is_consistent():
+    # The stored oracle values of the 64 x 64 Cahn-Hilliard schedule (written by
+    # tests/golden/make_ch_config3_64.py from oracle/ only) keep the invariants the oracle is pinned
+    # to: zero mass (u0 has zero mean), energy decreasing from level to level and below E(u0).
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "ch_config3_64x64.json")
+    with open(path) as f:
+        g = json.load(f)
+    c = g["case"]
+    p = P(equation=O.CAHN_HILLIARD, dim=2, nx=c["nx"], ny=c["ny"], bc="neumann", eps=c["eps"],
+          T=c["nt"] * c["n_windows"] * c["dt"], nt=c["nt"], n_windows=c["n_windows"])
+    u0 = synth.u0_ch(p.nspace, 0)
+    assert max(abs(m) for m in g["mass"]) < 1e-12
+    E = g["energy"]
+    assert all(E[i + 1] <= E[i] for i in range(len(E) - 1)) and E[0] < O.discrete_energy(p, u0)
+    assert len(g["window_ends"]) == c["n_windows"] and all(len(w["values"]) == p.nspace // g["sample_every_point"]
+                                                            for w in g["window_ends"])
+    # the first stored level is reproduced by the oracle's own step (a cheap end-to-end check of the file)
+    u = u0.copy()
+    for _ in range(g["levels"][0]):
+        u, _ = O.ch_step_newton(p, u)
+    assert abs(O.discrete_energy(p, u) - E[0]) < 1e-13 * E[0]
