@@ -96,6 +96,8 @@ def solver_kw(wl: dict, args, precision=None) -> dict:
 KERNEL_TRAFFIC = {
     ("residual", "mixed_ff"): {"src": "k_residual_ff.cu", "src_sha256_16": "f2beb509f59f81f0",
                                "workload": "linear_ch_2d_256x256_nt128", "dram_bytes": 68294656 + 5862912},
+    ("residual", "mixed"): {"src": "k_residual_fx.cu", "src_sha256_16": "39b6eb98e300d77e",
+                            "workload": "linear_ch_2d_256x256_nt128", "dram_bytes": 67896064 + 7118592},
 }
 
 
@@ -383,6 +385,41 @@ def finish_oracle_worker(handle):
     return ref, info
 
 
+def short_serving_sample(args, stream) -> dict:
+    """p50/p99 latency and DOF/s of a served Poisson stream at two rates (about a
+    second each), requests drawn from the batched-instance distribution."""
+    import numpy as np
+
+    from paper_2304_14021_gb300 import serve, synth
+    pool = synth.batched_instances(64, args.seed + 1, alpha=args.alpha, max_dof=2**22)
+    rng = np.random.default_rng(args.seed)
+    srv = serve.Server(hbm_budget_bytes=150e9, max_slots=32, precision=args.precision, tol=args.tol,
+                       tol_update=args.tol_update)
+
+    def stream_at(rate, n):
+        t_next = time.perf_counter()
+        futs = []
+        for _ in range(n):
+            x = pool[int(rng.integers(0, len(pool)))]
+            t_next += rng.exponential(1.0 / rate)
+            dt = t_next - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            f = srv.submit(x["u0"], **x["problem"])
+            f.add_done_callback(lambda fu: fu.result().release() if fu.exception() is None else None)
+            futs.append(f)
+        res = [f.result() for f in futs]
+        rep = srv.report(res)
+        return {"rate_req_s": rate, "n": rep["n"], "p50_ms": rep["p50_s"] * 1e3, "p99_ms": rep["p99_s"] * 1e3,
+                "dof_per_s": rep["dof_per_s"], "failed": rep["failed"]}
+
+    stream_at(200, 64)                                   # warm-up: solver entries and graphs per shape
+    rows = [stream_at(100, 100), stream_at(1000, 300)]
+    srv.close()
+    return {"precision": args.precision, "slots": 32, "hbm_budget_bytes": 150e9, "rates": rows,
+            "requests": "batched-instance distribution (dof <= 2^22), seeded"}
+
+
 def main_gpu(args) -> None:
     import numpy as np
     import torch
@@ -519,6 +556,20 @@ def main_gpu(args) -> None:
             e2e_times.append(time.perf_counter() - t0)
         e2e_s = max_over_ranks(statistics.mean(e2e_times), dist, "cuda")
 
+    # Solve latency of the headline workload over the timed steps, and a short
+    # serving sample: Poisson arrivals at two rates drawn from the batched
+    # distribution, continuous batching with admission by HBM footprint.
+    lat_sorted = sorted(times)
+
+    def pct(v, q):
+        return v[min(len(v) - 1, int(q * len(v)))]
+
+    latency = {"p50_ms": pct(lat_sorted, 0.5), "p99_ms": pct(lat_sorted, 0.99), "max_ms": lat_sorted[-1],
+               "solves": len(lat_sorted)}
+    serving = None
+    if not args.no_serving and world == 1:
+        serving = short_serving_sample(args, stream)
+
     # Per-phase times and the rooflines.  Per-launch time = phase time / launches
     # that did work (launches that found the solve already converged are excluded).
     bpd = phase_bytes_per_dof(args.precision, nt)
@@ -613,6 +664,8 @@ def main_gpu(args) -> None:
                                            2: "fft (step 1), tensor-core DFT (step 3)",
                                            3: "tensor-core DFT (steps 1, 3)"}[stats.get("time_gemm", 0)],
                        "parallelism": f"replicas x{world}"},
+            "latency": latency,
+            "serving": serving,
             "err_vs_oracle": (errs or {}).get("headline"),
             "oracle": oracle_info if oracle is not None else "not run (size or equation outside the CPU oracle's reach)",
             "e2e": ({"value": whole_job_value(world, dof, e2e_s), "unit": "space-time DOF/s",
@@ -791,6 +844,7 @@ def main() -> None:
     ap.add_argument("--variant-steps", type=int, default=10,
                     help="timed repeats of each other precision form and of the second alpha")
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle's sequential solution (error check)")
+    ap.add_argument("--no-serving", action="store_true", help="skip the short serving sample of the headline line")
     ap.add_argument("--time-gemm", type=int, default=-1, choices=[-1, 0, 1],
                     help="time transforms: -1 chosen by measurement per handle, 0 FFT, 1 tensor-core DFT products")
     ap.add_argument("--oracle-worker", action="store_true")

@@ -254,10 +254,12 @@ int pint_profile_read(pint_handle* h, pint_profile* out, int reset);
  *    half spectra.  The iteration loop runs host-launched (no CUDA graph).
  *    Errors: PINT_EINVAL (value out of range, or a linear equation), PINT_ENOMEM. */
 #define PINT_OPT_VARYING_JACOBIAN 5
-/*  PINT_OPT_FX_RESIDUAL (default 1 where supported): on a PINT_MIXED handle of a
- *    linear equation with square cells (or in 1-D), evaluate the residual (and
- *    pint_residual) in block fixed point on the integer pipes; 0 = the FP64
- *    residual kernel.  Errors: PINT_EINVAL for value 1 where it is not supported. */
+/*  PINT_OPT_FX_RESIDUAL: on a PINT_MIXED handle of a linear equation with square cells
+ *    (or in 1-D), evaluate the residual (and pint_residual) in block fixed point on the
+ *    integer pipes; 0 = the FP64 residual kernel.  Default 1 where supported and not stiff
+ *    (2^-24 dt max|spectrum| <= 1): for stiffer problems the fixed-point residual reports the
+ *    true residual of the FP64-rounded iterate, whose floor can exceed the tolerances, so the
+ *    FP64 kernel is the default there.  Errors: PINT_EINVAL for value 1 where unsupported. */
 #define PINT_OPT_FX_RESIDUAL 6
 /*  PINT_OPT_LOG_INVARIANTS (default 0): after each window (or segment) of a solve,
  *    record for every time level its mass h^d sum_i u_i and its discrete energy

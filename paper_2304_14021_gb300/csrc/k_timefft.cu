@@ -137,18 +137,18 @@ __global__ void __launch_bounds__(TimeCfg<T, NT>::NTH)
                 const double w = fma(xa, gi, row[pa]);
                 row[pa] = w;
                 if (want) {
-                    const float da = (float)v.x * (float)gi;
+                    const float da = (float)v.x * f64_to_f32_trunc(gi), wf = f64_to_f32_trunc(w);
                     d2 = fmaf(da, da, d2);
-                    u2 = fmaf((float)w, (float)w, u2);
+                    u2 = fmaf(wf, wf, u2);
                 }
             }
             if (pb < nspace) {
                 const double w = fma(xb, gi, row[pb]);
                 row[pb] = w;
                 if (want) {
-                    const float db = (float)v.y * (float)gi;
+                    const float db = (float)v.y * f64_to_f32_trunc(gi), wf = f64_to_f32_trunc(w);
                     d2 = fmaf(db, db, d2);
-                    u2 = fmaf((float)w, (float)w, u2);
+                    u2 = fmaf(wf, wf, u2);
                 }
             }
         } else {

@@ -229,9 +229,9 @@ __global__ void __launch_bounds__(256, 1)
                         const double w = fma(f32_to_f64_exact(v[i] * sc), ginv[n], uo[i]);
                         __stcs(U + (size_t)n * nspace + p, w);
                         if (want) {
-                            const float dl = v[i] * sc * (float)ginv[n];
+                            const float dl = v[i] * sc * f64_to_f32_trunc(ginv[n]), wf = f64_to_f32_trunc(w);
                             d2 = fmaf(dl, dl, d2);
-                            u2 = fmaf((float)w, (float)w, u2);
+                            u2 = fmaf(wf, wf, u2);
                         }
                     }
                 }

@@ -66,6 +66,18 @@ __device__ __forceinline__ double f32_to_f64_exact(float f) {
     return __hiloint2double((int)hi, (int)lo);
 }
 __device__ __forceinline__ double f32_to_f64_exact(double d) { return d; }
+// FP64 -> FP32 by truncating the significand on the integer pipes (for norm
+// partial sums only: no rounding, values outside the float range go to 0 or
+// infinity); keeps the conversion instruction off the FP64 pipe.
+__device__ __forceinline__ float f64_to_f32_trunc(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+    const int e = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+    const uint32_t sgn = hi & 0x80000000u;
+    if (e <= 0) return __uint_as_float(sgn);
+    if (e >= 255) return __uint_as_float(sgn | 0x7F800000u);
+    return __uint_as_float(sgn | ((uint32_t)e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+}
 
 template <class T> struct cplx_of;
 template <> struct cplx_of<float> { using type = float2; };
