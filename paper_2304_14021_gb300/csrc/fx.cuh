@@ -8,12 +8,13 @@
 // additions, and the few products with the problem's coefficients are formed
 // from 32x32-bit integer products with the coefficients' full 53-bit
 // mantissas.  Every rounding is a truncation at 2^-57 or below of the largest
-// term's bound, finer than the rounding of the same sums in FP64.
+// term in the tile, as fine as the rounding of the same sums in FP64.
 //
 // All helpers are __host__ __device__ so that their arithmetic can be checked
 // on the CPU against 128-bit integer and long double references.
 #pragma once
 
+#include <math.h>
 #include <stdint.h>
 
 #if defined(__CUDACC__)
@@ -23,20 +24,6 @@
 #endif
 
 namespace pint {
-
-// |c| = m * 2^q with m = mh * 2^32 + ml in [2^52, 2^53) (c's mantissa), neg = sign; c = 0: m = 0.
-struct FxCoef {
-    uint32_t mh, ml;
-    int q, neg;
-};
-
-FX_HD uint32_t fx_umulhi(uint32_t a, uint32_t b) {
-#if defined(__CUDA_ARCH__)
-    return __umulhi(a, b);
-#else
-    return (uint32_t)(((uint64_t)a * b) >> 32);
-#endif
-}
 
 FX_HD int fx_clz64(uint64_t a) {
 #if defined(__CUDA_ARCH__)
@@ -53,78 +40,36 @@ FX_HD int fx_expfield(uint32_t hi) { return (int)((hi >> 20) & 0x7FFu); }
 // |u| < 2^E with E = f - 1022.
 FX_HD int fx_tile_exp(int f) { return f - 1022; }
 
-// trunc(|u| 2^(56-E)) with the sign of u, for a finite u with |u| < 2^E.
-// The result has magnitude < 2^56.  Zeros and subnormals give 0.
-FX_HD int64_t fx_from_f64(uint32_t hi, uint32_t lo, int E) {
-    const int ex = fx_expfield(hi);
-    const uint64_t m = ((uint64_t)((hi & 0xFFFFFu) | 0x100000u) << 32) | lo;   // 53-bit significand
-    // |u| = m 2^(ex-1075), in units 2^(E-56): m 2^(ex-1019-E); ex <= E+1022, so the left shift is at most 3
-    int s = 1022 + E - ex;       // right shift of m << 3
-    s = s < 0 ? 0 : (s > 63 ? 63 : s);
-    uint64_t v = (m << 3) >> s;
-    if (ex == 0) v = 0;
-    const int64_t r = (int64_t)v;
-    return (hi >> 31) ? -r : r;
-}
-
-// floor(|L| m / 2^55) with the sign of L, for |L| < 2^62 and m < 2^53 (so the
-// result is below 2^60 in magnitude).  Exact: |L| m = A 2^64 + (B + C) 2^32 + al ml,
-// and the dropped low word of al ml cannot carry across the 2^23 boundary of
-// the integer B + C + hi(al ml).
-FX_HD int64_t fx_mul(int64_t L, const FxCoef& c) {
-    const uint64_t a = (uint64_t)(L < 0 ? -L : L);
-    const uint32_t ah = (uint32_t)(a >> 32), al = (uint32_t)a;
-    const uint64_t A = (uint64_t)ah * c.mh;
-    const uint64_t B = (uint64_t)ah * c.ml;
-    const uint64_t C = (uint64_t)al * c.mh;
-    const uint64_t mid = B + C + fx_umulhi(al, c.ml);
-    const uint64_t P = (A << 9) + (mid >> 23);
-    return L < 0 ? -(int64_t)P : (int64_t)P;
-}
-
-// floor(L M / 2^55) (to within one unit) for |L| < 2^62 and 0 <= M < 2^53,
-// M = mh 2^31 + ml (mh < 2^22, ml < 2^31): signed 32x32 products only, so no
-// absolute value or negation is needed.  L M = Lh mh 2^63 + (Lh ml 2^32 +
-// Ll mh 2^31 + Ll ml) with L = Lh 2^32 + Ll (Lh signed, Ll unsigned); the low
-// word of Ll ml is dropped before the final floor, which can lower the result
-// by one unit.  |result| < 2^60.
-FX_HD int64_t fx_mul_s(int64_t L, int32_t mh, int32_t ml) {
-    const int32_t Lh = (int32_t)(L >> 32);
-    const uint32_t Ll = (uint32_t)L;
-    const int64_t top = (int64_t)Lh * mh;                          // < 2^52
-    const int64_t W = (int64_t)Lh * ml;                            // |W| < 2^61
-    const uint64_t V = (uint64_t)Ll * (uint32_t)mh;                // < 2^54
-    const uint64_t Zh = fx_umulhi(Ll, (uint32_t)ml);               // floor(Ll ml / 2^32) < 2^31
-    // (Lh ml 2^32 + Ll mh 2^31 + Ll ml) / 2^55 = (2W + V + Ll ml / 2^31) / 2^24
-    const int64_t mid = 2 * W + (int64_t)V + (int64_t)(Zh << 1);
-    return (top << 8) + (mid >> 24);
+// The low word of (hi:lo) >> s, 0 <= s < 32.
+FX_HD uint32_t fx_funnel_r(uint32_t lo, uint32_t hi, int s) {
+#if defined(__CUDA_ARCH__)
+    return __funnelshift_r(lo, hi, s);
+#else
+    return (uint32_t)((((uint64_t)hi << 32) | lo) >> s);
+#endif
 }
 
 // Bits S .. S+63 of the exact 128-bit product L M (L signed, 0 <= M < 2^63), i.e.
 // floor(L M / 2^S), for 0 <= S <= 63 when that quotient fits in 64 bits.  S is
 // the same for every thread of a block (a uniform branch picks the word pair).
 FX_HD int64_t fx_mul_shr(int64_t L, int64_t M, int S) {
-#if defined(__CUDA_ARCH__)
     const uint64_t lo = (uint64_t)L * (uint64_t)M;
+#if defined(__CUDA_ARCH__)
     const int64_t hi = __mul64hi(L, M);
+#else
+    const int64_t hi = (int64_t)(((__int128)L * (__int128)M) >> 64);
+#endif
     const uint32_t w0 = (uint32_t)lo, w1 = (uint32_t)(lo >> 32), w2 = (uint32_t)hi, w3 = (uint32_t)((uint64_t)hi >> 32);
     uint32_t rx, ry;
     if (S < 32) {
-        rx = __funnelshift_r(w0, w1, S);
-        ry = __funnelshift_r(w1, w2, S);
+        rx = fx_funnel_r(w0, w1, S);
+        ry = fx_funnel_r(w1, w2, S);
     } else {
-        rx = __funnelshift_r(w1, w2, S - 32);
-        ry = __funnelshift_r(w2, w3, S - 32);
+        rx = fx_funnel_r(w1, w2, S - 32);
+        ry = fx_funnel_r(w2, w3, S - 32);
     }
     return (int64_t)(((uint64_t)ry << 32) | rx);
-#else
-    const __int128 p = (__int128)L * (__int128)M;
-    return (int64_t)(p >> S);
-#endif
 }
-
-// Significant bits of |v| (0 for v = 0).
-FX_HD int fx_bits(int64_t v) { return 64 - fx_clz64((uint64_t)(v < 0 ? -v : v)); }
 
 // 64-bit right shift with the PTX semantics for amounts >= 64 (the result
 // is 0): unsigned; and arithmetic (sign fill).
@@ -158,84 +103,36 @@ FX_HD int64_t fx_from_f64_fast(uint32_t hi, uint32_t lo, int E) {
     return ((int64_t)v ^ sm) - sm;
 }
 
-// Nearest float to R 2^X g, g = (gh 2^32 + gl) 2^gq with gh >= 2^31, and
-// F = 2^(96 + X + gq) given as two float factors f1 f2 (each a power of two
-// in the normal range).  The top 64 bits of |R| g (normalized) are formed to
-// within three units and rounded once to FP32 through a 32-bit integer with a
-// sticky bit (round to odd, then to nearest), so the result is the correctly
-// rounded value except within 2^-40 of a tie.
-FX_HD float fx_to_f32_fast(int64_t R, uint32_t gh, uint32_t gl, float f1, float f2) {
-    if (R == 0) return 0.0f;
-    const uint64_t a0 = (uint64_t)(R < 0 ? -R : R);
-    const int lz = fx_clz64(a0);
-    const uint64_t a = a0 << lz;
-    const uint32_t ah = (uint32_t)(a >> 32), al = (uint32_t)a;
-    const uint64_t P = (uint64_t)ah * gh + fx_umulhi(ah, gl) + fx_umulhi(al, gh);
-    const uint32_t u = (uint32_t)(P >> 32) | ((uint32_t)P != 0u ? 1u : 0u);
+// R (Gh + Gl) f1 f2 in FP32, for an integer R (|R| < 2^63), Gh + Gl a
+// float-float factor (Gh an integer below 2^24, |Gl| <= 1, together a 53-bit
+// mantissa to 2^-48) and f1, f2 powers of two in the normal range.  R is split
+// exactly into hi 2^32 + lo (lo the signed low word), both halves are
+// converted with one rounding each and recombined with one FMA, so
+// v = R (1 + d) with |d| <= 5 2^-25 (|d| <= 2^-24 when |R| < 2^31); the
+// product with Gh + Gl adds one rounding (2^-24) and the powers of two are
+// exact: the result is within 7 2^-25 relative of R (Gh + Gl) f1 f2 (under 4
+// ulp of FP32) while it stays in the normal range.
+FX_HD float fx_to_f32_pair(int64_t R, float Gh, float Gl, float f1, float f2) {
+    const int32_t lo = (int32_t)(uint32_t)(uint64_t)R;
+    const int32_t hi = (int32_t)(uint32_t)((uint64_t)R >> 32) - (lo >> 31);   // R = hi 2^32 + lo
 #if defined(__CUDA_ARCH__)
-    float f = __uint2float_rn(u);
-    const float p2 = __int_as_float((127 - lz) << 23);
+    const float v = __fmaf_rn(__int2float_rn(hi), 4294967296.0f, __int2float_rn(lo));
+    return __fmul_rn(__fmul_rn(__fmaf_rn(v, Gh, __fmul_rn(v, Gl)), f1), f2);
 #else
-    float f = (float)u;
-    const uint32_t pb = (uint32_t)(127 - lz) << 23;
-    float p2;
-    __builtin_memcpy(&p2, &pb, 4);
-#endif
-    f = f * p2 * f1 * f2;
-    return R < 0 ? -f : f;
-}
-
-// Arithmetic right shift by s >= 0 (floor), saturating at 63.
-FX_HD int64_t fx_shr(int64_t v, int s) { return v >> (s > 63 ? 63 : s); }
-
-// Nearest float to R 2^X g, where g = gm 2^gq with gm in [2^63, 2^64) (g's
-// mantissa left-aligned).  The product R g is formed to 2^-62 relative
-// before the single rounding to FP32 (round to nearest even; overflow gives
-// infinity, results below the normal range give zero).
-FX_HD float fx_to_f32_scaled(int64_t R, int X, uint64_t gm, int gq) {
-    if (R == 0) return 0.0f;
-    const uint32_t sign = R < 0 ? 0x80000000u : 0u;
-    uint64_t a = (uint64_t)(R < 0 ? -R : R);
-    const int lz = fx_clz64(a);
-    a <<= lz;                                           // [2^63, 2^64)
-    const uint32_t ah = (uint32_t)(a >> 32), al = (uint32_t)a, gh = (uint32_t)(gm >> 32), gl = (uint32_t)gm;
-    // top word of a gm (al gl and the low words of the cross products dropped: < 3 units)
-    const uint64_t P = (uint64_t)ah * gh + fx_umulhi(ah, gl) + fx_umulhi(al, gh);   // [2^62, 2^64)
-    const int top = (P >> 63) ? 63 : 62;
-    int sh = top - 23;
-    uint64_t mnt = P >> sh;                              // 24 bits
-    const uint64_t rem = P & ((1ull << sh) - 1), half = 1ull << (sh - 1);
-    if (rem > half || (rem == half && (mnt & 1ull))) ++mnt;
-    if (mnt == (1ull << 24)) {
-        mnt >>= 1;
-        ++sh;
-    }
-    // R 2^X g = a gm 2^(X - lz + gq) ~ P 2^(64 + X - lz + gq) = mnt 2^(sh + 64 + X - lz + gq)
-    const int be = sh + 64 + X - lz + gq + 23 + 127;
-    uint32_t bits;
-    if (be >= 255) bits = sign | 0x7F800000u;
-    else if (be <= 0) bits = sign;
-    else bits = sign | ((uint32_t)be << 23) | ((uint32_t)mnt & 0x7FFFFFu);
-#if defined(__CUDA_ARCH__)
-    return __uint_as_float(bits);
-#else
-    float f;
-    __builtin_memcpy(&f, &bits, 4);
-    return f;
+    const float v = fmaf((float)hi, 4294967296.0f, (float)lo);
+    return fmaf(v, Gh, v * Gl) * f1 * f2;
 #endif
 }
 
-// Left-aligned mantissa and exponent of a positive finite double g given its
-// bits: g = gm 2^gq, gm in [2^63, 2^64).  (g = 0 gives gm = 0.)
-FX_HD void fx_align(uint64_t gbits, uint64_t& gm, int& gq) {
-    const int ex = (int)((gbits >> 52) & 0x7FF);
-    if (ex == 0) {
-        gm = 0;
-        gq = 0;
-        return;
-    }
-    gm = ((gbits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 11;
-    gq = ex - 1075 - 11;
+// Float-float mantissa of a positive normal double g given its bits:
+// g = (Gh + Gl) 2^(e - 1046), e the biased exponent field, Gh the top 24
+// bits of the 53-bit significand (an integer in [2^23, 2^24)) and Gl the
+// remaining 29 bits / 2^29 rounded to FP32 (|Gl| < 1, error <= 2^-25).
+FX_HD void fx_split_f64(uint64_t gbits, float& Gh, float& Gl, int& e) {
+    e = (int)((gbits >> 52) & 0x7FF);
+    const uint64_t m = (gbits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    Gh = (float)(uint32_t)(m >> 29);
+    Gl = (float)(uint32_t)(m & 0x1FFFFFFFu) * (1.0f / 536870912.0f);
 }
 
 }  // namespace pint

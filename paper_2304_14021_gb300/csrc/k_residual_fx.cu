@@ -19,6 +19,8 @@
 //
 // ROUT (pint_residual): the residual itself is written in FP64 and its
 // square summed in FP64.
+#include <atomic>
+
 #include "fx.cuh"
 #include "pint_common.cuh"
 #include "pint_kernels.h"
@@ -29,7 +31,9 @@ template <int DIM> struct FxTile;
 template <> struct FxTile<1> { static constexpr int TX = 512, TY = 1, PPT = 2; };
 template <> struct FxTile<2> { static constexpr int TX = 32, TY = 16, PPT = 2; };
 constexpr int kFxThreads = 256;
-constexpr int kFxMinBlocks = 4;
+// Resident CTAs per SM the launch bounds guarantee (theta = 1/2 carries the
+// previous level's two Laplacians per point and needs more registers).
+template <bool HALF> struct FxBlocks { static constexpr int value = HALF ? 4 : 4; };
 
 // Source of halo element (gx, gy) of a time level: its offset within the
 // level, or -1 for a zero (simply supported boundary vertex, or beyond the
@@ -82,15 +86,20 @@ __device__ __forceinline__ void fx_pow2_pair(int k, float& f1, float& f2) {
     f2 = __int_as_float((k2 + 127) << 23);
 }
 
+// The work is the list of (tile, level) units, tile-major; CTA c of C takes the
+// contiguous units [c U / C, (c+1) U / C), which may span the end of one tile's
+// levels and the start of the next tile's: every CTA gets the same number of
+// levels to within one, whatever the tile count.
 template <int DIM, bool HALF, bool ROUT>
-__global__ void __launch_bounds__(kFxThreads, kFxMinBlocks)
+__global__ void __launch_bounds__(kFxThreads, FxBlocks<HALF>::value)
     k_residual_fx(GeoFX g, const double* __restrict__ U, const double* __restrict__ u0,
                   const double* __restrict__ gdt, const float* __restrict__ igamf, float* __restrict__ s_out,
-                  double* __restrict__ r_out, double* __restrict__ partials, const Ctl* __restrict__ ctl, int chunk) {
+                  double* __restrict__ r_out, double* __restrict__ partials, const Ctl* __restrict__ ctl) {
     pdl_wait();
     if (ctl && ctl->status != ST_RUNNING) return;
     constexpr int TX = FxTile<DIM>::TX, TY = FxTile<DIM>::TY, PPT = FxTile<DIM>::PPT;
     constexpr int NTHR = kFxThreads, NW = NTHR / 32;
+    static_assert((NW & (NW - 1)) == 0 && NW <= 32, "per-warp maxima are reduced by one warp");
     constexpr int RSTEP = DIM == 2 ? TY / PPT : 0, XSTEP = DIM == 2 ? 0 : TX / PPT;
     constexpr int HY = DIM == 2 ? 2 : 0;
     constexpr int SX = TX + 4, SY = TY + 2 * HY;
@@ -106,228 +115,230 @@ __global__ void __launch_bounds__(kFxThreads, kFxMinBlocks)
 
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     const int tx = tid % (DIM == 2 ? TX : TX / PPT), ty = tid / (DIM == 2 ? TX : TX / PPT);
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int n0 = blockIdx.z * chunk;
-    const int n1 = min(g.nt, n0 + chunk);
-    const int nfirst = HALF ? n0 - 1 : n0;
-
-    // staging map (fixed for all levels): this thread loads elements tid + a NTHR
-    int goff[NST];
-    uint32_t gneg[NST];
-#pragma unroll
-    for (int a = 0; a < NST; ++a) {
-        const int e = tid + a * NTHR;
-        goff[a] = -1;
-        gneg[a] = 0;
-        if (e < SX * SY) goff[a] = fx_src(x0 - 2 + e % SX, y0 - HY + e / SX, g.nx, g.ny, DIM, g.bc, &gneg[a]);
-    }
     int lc[NLP];
 #pragma unroll
     for (int a = 0; a < NLP; ++a) {
         const int e = tid + a * NTHR;
         lc[a] = e < LX * LY ? (DIM == 2 ? (e / LX + 1) * SX : 0) + e % LX + 1 : -1;
     }
-    uint32_t rhi[NST], rlo[NST];
-    auto load = [&](int n) {
-        const double* un = n < 0 ? u0 : U + (size_t)n * g.nspace;
-#pragma unroll
-        for (int a = 0; a < NST; ++a) {
-            if (goff[a] >= 0) {
-                const unsigned long long v = __ldg(reinterpret_cast<const unsigned long long*>(un + goff[a]));
-                rhi[a] = (uint32_t)(v >> 32) ^ gneg[a];
-                rlo[a] = (uint32_t)v;
-            } else {
-                rhi[a] = 0u;
-                rlo[a] = 0u;
-            }
-        }
-    };
-    auto expmax = [&]() {
-        int f = 0;
-#pragma unroll
-        for (int a = 0; a < NST; ++a) f = max(f, fx_expfield(rhi[a]));
-        return (int)__reduce_max_sync(0xffffffffu, (unsigned)f);
-    };
-
-    int cu[PPT], cl[PPT];
-    bool inside[PPT];
-    size_t po[PPT];
-#pragma unroll
-    for (int q = 0; q < PPT; ++q) {
-        const int lx = tx + q * XSTEP, ly = ty + q * RSTEP;
-        const int gx = x0 + lx, gy = y0 + ly;
-        inside[q] = gx < g.nx && (DIM == 1 || gy < g.ny);
-        po[q] = (size_t)(DIM == 2 ? gy * g.nx : 0) + gx;
-        cu[q] = (ly + HY) * SX + lx + 2;
-        cl[q] = (DIM == 2 ? (ly + 1) * LX : 0) + lx + 1;
-    }
-    // previous level per point in the tile-uniform unit 2^(Ep-56) (theta = 1/2: with its two Laplacians)
-    int64_t up[PPT], L1p[PPT], L2p[PPT];
-    uint32_t uph[PPT], upl[PPT];
-    int fp = 0;
-#pragma unroll
-    for (int q = 0; q < PPT; ++q) {
-        up[q] = L1p[q] = L2p[q] = 0;
-        uph[q] = upl[q] = 0u;
-        if (!HALF && inside[q]) {
-            const double* src = n0 == 0 ? u0 : U + (size_t)(n0 - 1) * g.nspace;
-            const unsigned long long v = __ldg(reinterpret_cast<const unsigned long long*>(src + po[q]));
-            uph[q] = (uint32_t)(v >> 32);
-            upl[q] = (uint32_t)v;
-            fp = max(fp, fx_expfield(uph[q]));
-        }
-    }
-    if (n0 < n1) {
-        load(nfirst);
-        const int f = expmax();
-        const int f2 = (int)__reduce_max_sync(0xffffffffu, (unsigned)fp);
-        if (lane == 0) {
-            smax[0][warp] = f;
-            smaxp[warp] = f2;
-        }
-    }
-    __syncthreads();
-    int Ep = -958, bL1p = 0;
-    if (!HALF) {
-        int f = 0;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) f = max(f, smaxp[w]);
-        Ep = max(fx_tile_exp(f), -958);
-#pragma unroll
-        for (int q = 0; q < PPT; ++q) up[q] = fx_from_f64_fast(uph[q], upl[q], Ep);
-    }
+    const int tiles_x = (g.nx + TX - 1) / TX;
+    const long long units = (long long)tiles_x * (DIM == 2 ? (g.ny + TY - 1) / TY : 1) * g.nt;
+    const long long ub = units * blockIdx.x / gridDim.x, ue = units * (blockIdx.x + 1) / gridDim.x;
     float acc = 0.f;
     double accd = 0.0;
-    for (int n = nfirst; n < n1; ++n) {
-        const int b = (n - nfirst) & 1;
-        int fmax = 0;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) fmax = max(fmax, smax[b][w]);
-        const bool bad = fmax == 0x7FF;   // an infinity or NaN in the tile
-        const int E = max(fx_tile_exp(fmax), -958);
-#pragma unroll
-        for (int a = 0; a < NST; ++a)
-            if (tid + a * NTHR < SX * SY) sfx[b][tid + a * NTHR] = fx_from_f64_fast(rhi[a], rlo[a], E);
-        if (n + 1 < n1) load(n + 1);
-        // level-uniform unit: both levels in 2^(Em-56)
-        const int Em = max(E, Ep);
-        const uint32_t dE = (uint32_t)(Em - E), dEp = (uint32_t)(Em - Ep);
-        const bool same = dE == 0u && dEp == 0u;
+    for (long long u = ub; u < ue;) {
+        // one segment: levels n0 .. n1-1 of one tile
+        const int tile = (int)(u / g.nt);
+        const int n0 = (int)(u - (long long)tile * g.nt);
+        const int n1 = (int)min((long long)g.nt, n0 + (ue - u));
+        u += n1 - n0;
+        const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
+        const int nfirst = HALF ? n0 - 1 : n0;
+        // the previous segment's last level is done with the shared buffers
         __syncthreads();
-        // first Laplacian pass, with the tile's largest |L1| and |u_{n-1} - u_n| (as bit counts)
-        // v ^ (v >> 63) is |v| or |v| - 1: the bits of the OR of those, plus one, bound every |v|
-        uint64_t orl = 0, ord = 0;
+
+        // staging map (fixed for the segment's levels): this thread loads elements tid + a NTHR
+        int goff[NST];
+        uint32_t gneg[NST];
 #pragma unroll
-        for (int a = 0; a < NLP; ++a)
-            if (lc[a] >= 0) {
-                const int64_t v = fx_lap<DIM>(sfx[b], lc[a], SX);
-                sL[b][tid + a * NTHR] = v;
-                orl |= (uint64_t)(v ^ (v >> 63));
-            }
-        if (!(HALF && n < n0)) {
+        for (int a = 0; a < NST; ++a) {
+            const int e = tid + a * NTHR;
+            goff[a] = -1;
+            gneg[a] = 0;
+            if (e < SX * SY) goff[a] = fx_src(x0 - 2 + e % SX, y0 - HY + e / SX, g.nx, g.ny, DIM, g.bc, &gneg[a]);
+        }
+        uint32_t rhi[NST], rlo[NST];
+        auto load = [&](int n) {
+            const double* un = n < 0 ? u0 : U + (size_t)n * g.nspace;
 #pragma unroll
-            for (int q = 0; q < PPT; ++q)
-                if (inside[q]) {
-                    const int64_t un = sfx[b][cu[q]];
-                    const int64_t D = same ? up[q] - un : fx_sar(up[q], dEp) - fx_sar(un, dE);
-                    ord |= (uint64_t)(D ^ (D >> 63));
+            for (int a = 0; a < NST; ++a) {
+                if (goff[a] >= 0) {
+                    const unsigned long long v = __ldg(reinterpret_cast<const unsigned long long*>(un + goff[a]));
+                    rhi[a] = (uint32_t)(v >> 32) ^ gneg[a];
+                    rlo[a] = (uint32_t)v;
+                } else {
+                    rhi[a] = 0u;
+                    rlo[a] = 0u;
                 }
+            }
+        };
+        auto expmax = [&]() {
+            int f = 0;
+#pragma unroll
+            for (int a = 0; a < NST; ++a) f = max(f, fx_expfield(rhi[a]));
+            return (int)__reduce_max_sync(0xffffffffu, (unsigned)f);
+        };
+
+        int cu[PPT], cl[PPT];
+        bool inside[PPT];
+        size_t po[PPT];
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+            const int lx = tx + q * XSTEP, ly = ty + q * RSTEP;
+            const int gx = x0 + lx, gy = y0 + ly;
+            inside[q] = gx < g.nx && (DIM == 1 || gy < g.ny);
+            po[q] = (size_t)(DIM == 2 ? gy * g.nx : 0) + gx;
+            cu[q] = (ly + HY) * SX + lx + 2;
+            cl[q] = (DIM == 2 ? (ly + 1) * LX : 0) + lx + 1;
         }
-        int bl = orl ? 65 - fx_clz64(orl) : 0, bd = ord ? 65 - fx_clz64(ord) : 0;
-        bl = (int)__reduce_max_sync(0xffffffffu, (unsigned)bl);
-        bd = (int)__reduce_max_sync(0xffffffffu, (unsigned)bd);
-        if (lane == 0) {
-            sbL[warp] = bl;
-            sbD[warp] = bd;
+        // previous level per point in the tile-uniform unit 2^(Ep-56) (theta = 1/2: with its two Laplacians)
+        int64_t up[PPT], L1p[PPT], L2p[PPT];
+        uint32_t uph[PPT], upl[PPT];
+        int fp = 0;
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+            up[q] = L1p[q] = L2p[q] = 0;
+            uph[q] = upl[q] = 0u;
+            if (!HALF && inside[q]) {
+                const double* src = n0 == 0 ? u0 : U + (size_t)(n0 - 1) * g.nspace;
+                const unsigned long long v = __ldg(reinterpret_cast<const unsigned long long*>(src + po[q]));
+                uph[q] = (uint32_t)(v >> 32);
+                upl[q] = (uint32_t)v;
+                fp = max(fp, fx_expfield(uph[q]));
+            }
         }
-        if (n + 1 < n1) {
+        if (n0 < n1) {
+            load(nfirst);
             const int f = expmax();
-            if (lane == 0) smax[b ^ 1][warp] = f;
+            const int f2 = (int)__reduce_max_sync(0xffffffffu, (unsigned)fp);
+            if (lane == 0) {
+                smax[0][warp] = f;
+                smaxp[warp] = f2;
+            }
         }
         __syncthreads();
-        int bL1 = 0, bD = 0;
+        int Ep = -958, bL1p = 0;
+        if (!HALF) {
+            int f = 0;
 #pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            bL1 = max(bL1, sbL[w]);
-            bD = max(bD, sbD[w]);
+            for (int w = 0; w < NW; ++w) f = max(f, smaxp[w]);
+            Ep = max(fx_tile_exp(f), -958);
+#pragma unroll
+            for (int q = 0; q < PPT; ++q) up[q] = fx_from_f64_fast(uph[q], upl[q], Ep);
         }
-        if (HALF && n < n0) {
+        for (int n = nfirst; n < n1; ++n) {
+            const int b = (n - nfirst) & 1;
+            // the warps' maxima: lane w reads warp w's, one redux over the warp
+            const int fmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)smax[b][lane & (NW - 1)]);
+            const bool bad = fmax == 0x7FF;   // an infinity or NaN in the tile
+            const int E = max(fx_tile_exp(fmax), -958);
+#pragma unroll
+            for (int a = 0; a < NST; ++a)
+                if (tid + a * NTHR < SX * SY) sfx[b][tid + a * NTHR] = fx_from_f64_fast(rhi[a], rlo[a], E);
+            if (n + 1 < n1) load(n + 1);
+            // level-uniform unit: both levels in 2^(Em-56)
+            const int Em = max(E, Ep);
+            const uint32_t dE = (uint32_t)(Em - E), dEp = (uint32_t)(Em - Ep);
+            const bool same = dE == 0u && dEp == 0u;
+            __syncthreads();
+            // first Laplacian pass, with the tile's largest |L1| and |u_{n-1} - u_n| (as bit counts)
+            // v ^ (v >> 63) is |v| or |v| - 1: the bits of the OR of those, plus one, bound every |v|
+            uint64_t orl = 0, ord = 0;
+#pragma unroll
+            for (int a = 0; a < NLP; ++a)
+                if (lc[a] >= 0) {
+                    const int64_t v = fx_lap<DIM>(sfx[b], lc[a], SX);
+                    sL[b][tid + a * NTHR] = v;
+                    orl |= (uint64_t)(v ^ (v >> 63));
+                }
+            if (!(HALF && n < n0)) {
+#pragma unroll
+                for (int q = 0; q < PPT; ++q)
+                    if (inside[q]) {
+                        const int64_t un = sfx[b][cu[q]];
+                        const int64_t D = same ? up[q] - un : fx_sar(up[q], dEp) - fx_sar(un, dE);
+                        ord |= (uint64_t)(D ^ (D >> 63));
+                    }
+            }
+            int bl = orl ? 65 - fx_clz64(orl) : 0, bd = ord ? 65 - fx_clz64(ord) : 0;
+            bl = (int)__reduce_max_sync(0xffffffffu, (unsigned)bl);
+            bd = (int)__reduce_max_sync(0xffffffffu, (unsigned)bd);
+            if (lane == 0) {
+                sbL[warp] = bl;
+                sbD[warp] = bd;
+            }
+            if (n + 1 < n1) {
+                const int f = expmax();
+                if (lane == 0) smax[b ^ 1][warp] = f;
+            }
+            __syncthreads();
+            const int bL1 = (int)__reduce_max_sync(0xffffffffu, (unsigned)sbL[lane & (NW - 1)]);
+            const int bD = (int)__reduce_max_sync(0xffffffffu, (unsigned)sbD[lane & (NW - 1)]);
+            if (HALF && n < n0) {
+#pragma unroll
+                for (int q = 0; q < PPT; ++q) {
+                    up[q] = sfx[b][cu[q]];
+                    L1p[q] = sL[b][cl[q]];
+                    L2p[q] = fx_lap<DIM>(sL[b], cl[q], LX);
+                }
+                Ep = E;
+                bL1p = bL1;
+                continue;
+            }
+            // Terms in the unit 2^(Q+Em-56) of the exact products L M: c2 L2, c1 L1 and D 2^-Q.  Their
+            // largest magnitude in this tile, 2^emax, sets the output unit 2^X, X = Q + Em - 56 + S with
+            // S = emax - 60 (>= 0): every term is then resolved to 2^-60 of the largest one.
+            // bits of the Laplacian sums as used (a shift to the unit Em only lowers them)
+            const int bL = HALF ? max(bL1, bL1p) + 1 : bL1;
+            const int e2 = bL + L2GROW + g.bM2, e1 = bL + g.bM1, eD = bD - g.Q;
+            int emax = max(e2, eD);
+            if (g.lin1) emax = max(emax, e1);
+            const int S = max(emax - 60, 0);
+            const int X = g.Q + Em - 56 + S;
+            const int kD = -g.Q - S;                              // D 2^-Q in units 2^S
+            float Gh = 0.f, Gl = 0.f, f1 = 0.f, f2 = 0.f, ig = 0.f;
+            if (!ROUT) {
+                // gamma_n / dt = (Gh + Gl) 2^(gex - 1046); the output is R 2^X gamma_n / dt
+                int gex;
+                fx_split_f64((uint64_t)__double_as_longlong(__ldg(gdt + n)), Gh, Gl, gex);
+                fx_pow2_pair(X + gex - 1046, f1, f2);
+                ig = __ldg(igamf + n);
+            }
 #pragma unroll
             for (int q = 0; q < PPT; ++q) {
-                up[q] = sfx[b][cu[q]];
-                L1p[q] = sL[b][cl[q]];
-                L2p[q] = fx_lap<DIM>(sL[b], cl[q], LX);
+                if (!inside[q]) continue;
+                const int64_t un = sfx[b][cu[q]];
+                const int64_t L1o = sL[b][cl[q]];
+                const int64_t L2o = fx_lap<DIM>(sL[b], cl[q], LX);
+                int64_t D, L1 = L1o, L2 = L2o;
+                if (same) {
+                    D = up[q] - un;
+                } else {
+                    D = fx_sar(up[q], dEp) - fx_sar(un, dE);
+                    L1 = fx_sar(L1o, dE);
+                    L2 = fx_sar(L2o, dE);
+                }
+                int64_t L1s = L1, L2s = L2;
+                if constexpr (HALF) {
+                    L1s += same ? L1p[q] : fx_sar(L1p[q], dEp);
+                    L2s += same ? L2p[q] : fx_sar(L2p[q], dEp);
+                }
+                int64_t R = kD >= 0 ? (D << kD) : fx_sar(D, (uint32_t)(-kD));
+                R -= fx_mul_shr(L2s, g.M2, S);
+                if (g.lin1) {
+                    const int64_t t1 = fx_mul_shr(L1s, g.M1, S);
+                    R = g.neg1 ? R + t1 : R - t1;
+                }
+                const size_t o = (size_t)n * g.nspace + po[q];
+                if constexpr (ROUT) {
+                    const double r = bad ? __longlong_as_double(0x7FF8000000000000ll) : ldexp((double)R, X) * g.inv_dt;
+                    if (r_out) r_out[o] = r;
+                    accd = fma(r, r, accd);
+                } else {
+                    const float sv = bad ? __int_as_float(0x7FC00000) : fx_to_f32_pair(R, Gh, Gl, f1, f2);
+                    s_out[o] = sv;
+                    const float rv = sv * ig;
+                    acc = fmaf(rv, rv, acc);
+                }
+                up[q] = un;
+                if constexpr (HALF) {
+                    L1p[q] = L1o;
+                    L2p[q] = L2o;
+                }
             }
             Ep = E;
             bL1p = bL1;
-            continue;
         }
-        // Terms in the unit 2^(Q+Em-56) of the exact products L M: c2 L2, c1 L1 and D 2^-Q.  Their
-        // largest magnitude in this tile, 2^emax, sets the output unit 2^X, X = Q + Em - 56 + S with
-        // S = emax - 60 (>= 0): every term is then resolved to 2^-60 of the largest one.
-        // bits of the Laplacian sums as used (a shift to the unit Em only lowers them)
-        const int bL = HALF ? max(bL1, bL1p) + 1 : bL1;
-        const int e2 = bL + L2GROW + g.bM2, e1 = bL + g.bM1, eD = bD - g.Q;
-        int emax = max(e2, eD);
-        if (g.lin1) emax = max(emax, e1);
-        const int S = max(emax - 60, 0);
-        const int X = g.Q + Em - 56 + S;
-        const int kD = -g.Q - S;                              // D 2^-Q in units 2^S
-        uint32_t gh = 0u, gl = 0u;
-        float f1 = 0.f, f2 = 0.f, ig = 0.f;
-        if (!ROUT) {
-            const unsigned long long gb = (unsigned long long)__double_as_longlong(gdt[n]);
-            const int gex = (int)((gb >> 52) & 0x7FF);
-            const unsigned long long gm = ((gb & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 11;
-            gh = (uint32_t)(gm >> 32);
-            gl = (uint32_t)gm;
-            fx_pow2_pair(96 + X + gex - 1086, f1, f2);
-            ig = igamf[n];
-        }
-#pragma unroll
-        for (int q = 0; q < PPT; ++q) {
-            if (!inside[q]) continue;
-            const int64_t un = sfx[b][cu[q]];
-            const int64_t L1o = sL[b][cl[q]];
-            const int64_t L2o = fx_lap<DIM>(sL[b], cl[q], LX);
-            int64_t D, L1 = L1o, L2 = L2o;
-            if (same) {
-                D = up[q] - un;
-            } else {
-                D = fx_sar(up[q], dEp) - fx_sar(un, dE);
-                L1 = fx_sar(L1o, dE);
-                L2 = fx_sar(L2o, dE);
-            }
-            int64_t L1s = L1, L2s = L2;
-            if constexpr (HALF) {
-                L1s += same ? L1p[q] : fx_sar(L1p[q], dEp);
-                L2s += same ? L2p[q] : fx_sar(L2p[q], dEp);
-            }
-            int64_t R = kD >= 0 ? (D << kD) : fx_sar(D, (uint32_t)(-kD));
-            R -= fx_mul_shr(L2s, g.M2, S);
-            if (g.lin1) {
-                const int64_t t1 = fx_mul_shr(L1s, g.M1, S);
-                R = g.neg1 ? R + t1 : R - t1;
-            }
-            const size_t o = (size_t)n * g.nspace + po[q];
-            if constexpr (ROUT) {
-                const double r = bad ? __longlong_as_double(0x7FF8000000000000ll) : ldexp((double)R, X) * g.inv_dt;
-                if (r_out) r_out[o] = r;
-                accd = fma(r, r, accd);
-            } else {
-                const float sv = bad ? __int_as_float(0x7FC00000) : fx_to_f32_fast(R, gh, gl, f1, f2);
-                s_out[o] = sv;
-                const float rv = sv * ig;
-                acc = fmaf(rv, rv, acc);
-            }
-            up[q] = un;
-            if constexpr (HALF) {
-                L1p[q] = L1o;
-                L2p[q] = L2o;
-            }
-        }
-        Ep = E;
-        bL1p = bL1;
     }
     // deterministic block reduction of sum r^2 (sum u^2 is not needed for the linear equations)
     double a = warp_sum(ROUT ? accd : (double)acc);
@@ -336,9 +347,8 @@ __global__ void __launch_bounds__(kFxThreads, kFxMinBlocks)
     if (tid == 0) {
         double A = 0.0;
         for (int w = 0; w < NW; ++w) A += red[w];
-        const size_t cta = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-        partials[2 * cta] = A;
-        partials[2 * cta + 1] = 0.0;
+        partials[2 * blockIdx.x] = A;
+        partials[2 * blockIdx.x + 1] = 0.0;
     }
 }
 
@@ -380,19 +390,34 @@ GeoFX make_geo_fx(const Geo& g) {
     return f;
 }
 
+// SMs of the current device (looked up once per device).
+static int fx_sm_count() {
+    static std::atomic<int> cached[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    int v = cached[dev].load(std::memory_order_relaxed);
+    if (v < 1) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) v = 152;
+        cached[dev].store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+
+// One resident wave (SMs x the CTAs per SM that the launch bounds guarantee),
+// at least 4 levels per CTA.  gx = CTAs, gy = gz = 1, chunk = units per CTA
+// (rounded up).  Returns the CTA count, which is also the number of partials.
 int residual_fx_grid(const Geo& g, int& gx, int& gy, int& gz, int& chunk) {
     const int TX = g.dim == 2 ? FxTile<2>::TX : FxTile<1>::TX, TY = g.dim == 2 ? FxTile<2>::TY : 1;
-    gx = (g.nx + TX - 1) / TX;
-    gy = g.dim == 2 ? (g.ny + TY - 1) / TY : 1;
-    const long tiles = (long)gx * gy;
-    // one wave of 152 SMs x the kernel's resident CTAs, split over time
-    long want = (152L * kFxMinBlocks) / tiles;
-    if (want < 1) want = 1;
-    chunk = (int)((g.nt + want - 1) / want);
-    if (chunk < 4) chunk = 4;
-    if (chunk > g.nt) chunk = g.nt;
-    gz = (g.nt + chunk - 1) / chunk;
-    return gx * gy * gz;
+    const long long tiles = (long long)((g.nx + TX - 1) / TX) * (g.dim == 2 ? (g.ny + TY - 1) / TY : 1);
+    const long long units = tiles * g.nt;
+    long long c = (long long)fx_sm_count() * (g.th < 1.0 ? FxBlocks<true>::value : FxBlocks<false>::value);
+    const long long cmax = (units + 3) / 4;
+    if (c > cmax) c = cmax;
+    if (c < 1) c = 1;
+    gx = (int)c;
+    gy = gz = 1;
+    chunk = (int)((units + c - 1) / c);
+    return gx;
 }
 
 cudaError_t launch_residual_fx(const GeoFX& f, const Geo& g, const double* U, const double* u0, const double* gdt,
@@ -400,10 +425,9 @@ cudaError_t launch_residual_fx(const GeoFX& f, const Geo& g, const double* U, co
                                cudaStream_t st, int rout_mode) {
     int gx, gy, gz, chunk;
     residual_fx_grid(g, gx, gy, gz, chunk);
-    const dim3 grid(gx, gy, gz), blk(kFxThreads);
-#define PINT_RFX(D, H, R)                                                                                    \
-    return launch_pdl(k_residual_fx<D, H, R>, grid, blk, 0, st, f, U, u0, gdt, igamf, s, r_out, partials, ctl, \
-                      chunk)
+    const dim3 grid(gx), blk(kFxThreads);
+#define PINT_RFX(D, H, R) \
+    return launch_pdl(k_residual_fx<D, H, R>, grid, blk, 0, st, f, U, u0, gdt, igamf, s, r_out, partials, ctl)
     const bool rout = rout_mode != 0;
     if (g.dim == 2) {
         if (rout) { if (f.half) PINT_RFX(2, true, true); else PINT_RFX(2, false, true); }
