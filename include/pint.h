@@ -250,8 +250,10 @@ int pint_profile_read(pint_handle* h, pint_profile* out, int reset);
  *    J~(x) = mean over the time levels of 3 u(x)^2, instead of its scalar mean:
  *    one cycle of flexible GMRES(value), 1 <= value <= 30, per outer iteration,
  *    over all frequencies at once, right-preconditioned by the scalar-J divide
- *    and stopped at a relative inner residual of 1e-4.  Work memory: (2 value + 3)
- *    half spectra.  The iteration loop runs host-launched (no CUDA graph).
+ *    and stopped at a relative inner residual of 1e-4.  Work memory: (2 value + 2)
+ *    half spectra.  The cycle runs on the device with no host round trip (its
+ *    Hessenberg matrix, rotations and stop test in one-CTA kernels), so the
+ *    iteration loop is captured in a CUDA graph like the scalar-Jacobian one.
  *    Errors: PINT_EINVAL (value out of range, or a linear equation), PINT_ENOMEM. */
 #define PINT_OPT_VARYING_JACOBIAN 5
 /*  PINT_OPT_FX_RESIDUAL: on a PINT_MIXED handle of a linear equation with square cells

@@ -4,7 +4,9 @@
 // every frequency slice of the spectrum,
 //   M_k y = lambda_1k y + lambda_2k (c2 Lap^2 y + Lap((c1 - J~) y)) + lambda_3k Lap y,
 // (PinT-I: c1 = 1, lambda_3k = 0; PinT-II: c1 = 0, lambda_3k = 1 - dt lambda_1k),
-// and the complex vector kernels of the inner flexible GMRES that solves it.
+// and the kernels of the inner flexible GMRES that solves it: complex vector
+// kernels and the small one-CTA steps that keep its Hessenberg matrix, Givens
+// rotations and stop test on the device.
 #include "ff.cuh"
 #include "pint_common.cuh"
 #include "pint_kernels.h"
@@ -39,8 +41,10 @@ __device__ __forceinline__ int refl_index(int g, int n, int bc, float& sgn) {
 // One CTA: a 32 x 8 tile of one frequency slice k = blockIdx.z (1-D: 256 x 1).
 template <class T, int DIM>
 __global__ void __launch_bounds__(256) k_apply_M(Geo g, int nk, const c_t<T>* __restrict__ Y, c_t<T>* __restrict__ W,
-                                                 const T* __restrict__ jt, Tabs<T> tb, T c2, T c1) {
+                                                 const T* __restrict__ jt, Tabs<T> tb, T c2, T c1,
+                                                 const int* __restrict__ skip, const c_t<T>* __restrict__ B) {
     using C = c_t<T>;
+    if (skip && *skip) return;
     constexpr int TX = DIM == 2 ? 32 : 256, TY = DIM == 2 ? 8 : 1, HY = DIM == 2 ? 2 : 0;
     constexpr int SX = TX + 4, SY = TY + 2 * HY, LX = TX + 2, LY = TY + (DIM == 2 ? 2 : 0);
     __shared__ C sy[SY * SX];   // y
@@ -87,7 +91,8 @@ __global__ void __launch_bounds__(256) k_apply_M(Geo g, int nk, const c_t<T>* __
     const C l1 = tb.lam1[k], l2 = tb.lam2[k];
     C w = cmul(l1, sy[cu]) + cmul(l2, op);
     if (tb.dte != T(0)) w = w + cmul(mkc(T(1) - tb.dte * l1.x, -tb.dte * l1.y), L);   // lambda_3k Lap y
-    W[(size_t)k * g.nspace + (DIM == 2 ? gy * g.nx : 0) + gx] = w;
+    const size_t o = (size_t)k * g.nspace + (DIM == 2 ? gy * g.nx : 0) + gx;
+    W[o] = B ? B[o] - w : w;
 }
 
 constexpr int kCDotThreads = 256;
@@ -97,24 +102,27 @@ constexpr int kGroup = 4;   // vectors handled per launch (register accumulators
 template <class T, int G>
 __global__ void __launch_bounds__(kCDotThreads) k_cmulti_dot(const c_t<T>* __restrict__ w, const c_t<T>* __restrict__ V,
                                                             size_t ld, size_t n, int ldp, int i0,
-                                                            double* __restrict__ partials) {
+                                                            double* __restrict__ partials, const int* __restrict__ skip) {
+    if (skip && *skip) return;
     __shared__ double red[kCDotThreads / 32][G][2];
-    double re[G], im[G];
+    // each thread accumulates its strided elements in the vectors' own precision
+    // (complex64: FP32, a few hundred terms at most); the CTA sum is taken in FP64
+    T re[G], im[G];
 #pragma unroll
-    for (int i = 0; i < G; ++i) re[i] = im[i] = 0.0;
+    for (int i = 0; i < G; ++i) re[i] = im[i] = T(0);
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        const double wr = w[e].x, wi = w[e].y;
+        const c_t<T> we = w[e];
 #pragma unroll
         for (int i = 0; i < G; ++i) {
             const c_t<T> v = V[i * ld + e];
-            re[i] = fma((double)v.x, wr, fma((double)v.y, wi, re[i]));
-            im[i] = fma((double)v.x, wi, fma(-(double)v.y, wr, im[i]));
+            re[i] = fma(v.x, we.x, fma(v.y, we.y, re[i]));
+            im[i] = fma(v.x, we.y, fma(-v.y, we.x, im[i]));
         }
     }
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
 #pragma unroll
     for (int i = 0; i < G; ++i) {
-        const double a = warp_sum(re[i]), b = warp_sum(im[i]);
+        const double a = warp_sum((double)re[i]), b = warp_sum((double)im[i]);
         if (lane == 0) { red[warp][i][0] = a; red[warp][i][1] = b; }
     }
     __syncthreads();
@@ -127,33 +135,175 @@ __global__ void __launch_bounds__(kCDotThreads) k_cmulti_dot(const c_t<T>* __res
     }
 }
 
-// w += sum_i c_i v_i, i < G, complex coefficients c (FP64 pairs on the device).
+// out = (w + sum_i c_i v_i) * post, i < G, complex coefficients c (FP64 pairs
+// on the device), arithmetic in the vectors' precision; out = w and post = 1
+// when null; with nlim only the terms i0 + i < *nlim (the other vectors are not read).
 template <class T, int G>
 __global__ void k_cmulti_axpy(c_t<T>* __restrict__ w, const c_t<T>* __restrict__ V, size_t ld,
-                              const double* __restrict__ c, size_t n) {
-    double cr[G], ci[G];
+                              const double* __restrict__ c, size_t n, const int* __restrict__ skip,
+                              const int* __restrict__ nlim, int i0, c_t<T>* __restrict__ out,
+                              const double* __restrict__ post) {
+    if (skip && *skip) return;
+    const int ng = nlim ? max(0, min(G, *nlim - i0)) : G;
+    const T ps = post ? (T)*post : T(1);
+    if (!out) out = w;
+    if (ng <= 0 && out == w && !post) return;
+    T cr[G], ci[G];
 #pragma unroll
-    for (int i = 0; i < G; ++i) { cr[i] = c[2 * i]; ci[i] = c[2 * i + 1]; }
+    for (int i = 0; i < G; ++i) {
+        cr[i] = i < ng ? (T)c[2 * i] : T(0);
+        ci[i] = i < ng ? (T)c[2 * i + 1] : T(0);
+    }
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        double xr = w[e].x, xi = w[e].y;
+        T xr = w[e].x, xi = w[e].y;
 #pragma unroll
         for (int i = 0; i < G; ++i) {
+            if (i >= ng) break;
             const c_t<T> v = V[i * ld + e];
-            xr += cr[i] * v.x - ci[i] * v.y;
-            xi += cr[i] * v.y + ci[i] * v.x;
+            xr = fma(cr[i], v.x, fma(-ci[i], v.y, xr));
+            xi = fma(cr[i], v.y, fma(ci[i], v.x, xi));
         }
-        w[e] = mkc((T)xr, (T)xi);
+        out[e] = mkc(xr * ps, xi * ps);
     }
 }
 
-// z = a x + b y (real scalars; y may be nullptr)
+// z = a x + b y (real scalars; y may be nullptr; a = *sdev when sdev is given)
 template <class T>
 __global__ void k_caxpby(c_t<T>* __restrict__ z, T a, const c_t<T>* __restrict__ x, T b, const c_t<T>* __restrict__ y,
-                         size_t n) {
+                         size_t n, const int* __restrict__ skip, const double* __restrict__ sdev) {
+    if (skip && *skip) return;
+    if (sdev) a = (T)*sdev;
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
         c_t<T> v = scalec(x[e], a);
         if (y) v = v + scalec(y[e], b);
         z[e] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Scalar steps of the inner flexible GMRES, one CTA each.
+// ---------------------------------------------------------------------------
+constexpr int kGmThreads = 256;
+
+__device__ __forceinline__ double2 gm_mul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ double2 gm_conj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 gm_scale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 gm_add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 gm_sub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double gm_abs(double2 a) { return hypot(a.x, a.y); }
+__device__ __forceinline__ double gm_norm(double2 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ double2 gm_div(double2 a, double2 b) {
+    const double d = gm_norm(b);
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+// out[i] = sum over the nb CTAs, in CTA order, of the partials of vector i < nv:
+// warp w adds the values v = w, w + 8, ... (re and im of each vector), each
+// lane a fixed strided subset, then a fixed shuffle tree.
+__device__ void gm_reduce(const double* __restrict__ part, int nb, int nv, double2* out) {
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    double* o = reinterpret_cast<double*>(out);
+    for (int v = warp; v < 2 * nv; v += kGmThreads / 32) {
+        double a = 0.0;
+        for (int q = lane; q < nb; q += 32) a += part[((size_t)q * nv + v / 2) * 2 + (v & 1)];
+        a = warp_sum(a);
+        if (lane == 0) o[v] = a;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kGmThreads) k_gm_init(const double* __restrict__ part_bb,
+                                                        const double* __restrict__ part_rr, int nb,
+                                                        const Ctl* __restrict__ octl, GmState* s, double tol) {
+    __shared__ double2 bb[1], rr[1];
+    gm_reduce(part_bb, nb, 1, bb);
+    gm_reduce(part_rr, nb, 1, rr);
+    if (threadIdx.x != 0) return;
+    const double bn = sqrt(fmax(bb[0].x, 0.0)), beta = sqrt(fmax(rr[0].x, 0.0));
+    const bool run = octl->status == ST_RUNNING && beta > tol * bn;
+    s->ictl.jbar = octl->jbar;
+    s->ictl.status = run ? ST_RUNNING : 0;   // 0: stopped
+    s->skip = run ? 0 : 1;
+    s->skip_re = 1;
+    s->j = 0;
+    s->bn = bn;
+    s->scale = run ? 1.0 / beta : 1.0;
+    s->gv[0] = make_double2(beta, 0.0);
+}
+
+__global__ void __launch_bounds__(kGmThreads) k_gm_orth1(const double* __restrict__ part, int nb, int j, GmState* s) {
+    if (s->skip) return;
+    gm_reduce(part, nb, j + 2, s->tmp);
+    if (threadIdx.x != 0) return;
+    const double ww = s->tmp[j + 1].x;
+    double hh = 0.0;
+    for (int i = 0; i <= j; ++i) {
+        s->hcol[i] = s->tmp[i];
+        hh += gm_norm(s->tmp[i]);
+        s->coef[i] = gm_scale(s->tmp[i], -1.0);
+    }
+    const double hn2 = ww - hh;
+    // ||w - sum h_i v_i||^2 = <w, w> - sum |h_i|^2 cancels: project once more
+    s->reorth = hn2 > 1e-4 * ww ? 0 : 1;
+    s->skip_re = s->reorth ? 0 : 1;
+    s->hn2 = hn2;
+}
+
+__global__ void __launch_bounds__(kGmThreads) k_gm_orth2(const double* __restrict__ part, int nb, int j, GmState* s,
+                                                         double tol) {
+    if (s->skip) return;
+    if (s->reorth) gm_reduce(part, nb, j + 2, s->tmp);
+    if (threadIdx.x != 0) return;
+    double hn2 = s->hn2;
+    if (s->reorth) {
+        double hh = 0.0;
+        for (int i = 0; i <= j; ++i) {
+            s->hcol[i] = gm_add(s->hcol[i], s->tmp[i]);
+            hh += gm_norm(s->tmp[i]);
+            s->coef[i] = gm_scale(s->tmp[i], -1.0);
+        }
+        hn2 = s->tmp[j + 1].x - hh;
+    }
+    s->skip_re = 1;
+    const double hn = sqrt(fmax(hn2, 0.0));
+    s->scale = hn > 0.0 ? 1.0 / hn : 1.0;
+    double2* hc = s->hcol;
+    hc[j + 1] = make_double2(hn, 0.0);
+    for (int i = 0; i < j; ++i) {   // the previous rotations
+        const double2 a = gm_add(gm_scale(hc[i], s->cs[i]), gm_mul(s->sn[i], hc[i + 1]));
+        hc[i + 1] = gm_sub(gm_scale(hc[i + 1], s->cs[i]), gm_mul(gm_conj(s->sn[i]), hc[i]));
+        hc[i] = a;
+    }
+    const double na = gm_abs(hc[j]), r = hypot(na, gm_abs(hc[j + 1]));
+    if (r == 0.0) {
+        s->cs[j] = 1.0;
+        s->sn[j] = make_double2(0.0, 0.0);
+    } else if (na == 0.0) {
+        s->cs[j] = 0.0;
+        s->sn[j] = gm_scale(gm_conj(hc[j + 1]), 1.0 / r);
+    } else {
+        s->cs[j] = na / r;
+        s->sn[j] = gm_scale(gm_mul(gm_scale(hc[j], 1.0 / na), gm_conj(hc[j + 1])), 1.0 / r);
+    }
+    hc[j] = gm_add(gm_scale(hc[j], s->cs[j]), gm_mul(s->sn[j], hc[j + 1]));
+    hc[j + 1] = make_double2(0.0, 0.0);
+    s->gv[j + 1] = gm_scale(gm_mul(gm_conj(s->sn[j]), s->gv[j]), -1.0);
+    s->gv[j] = gm_scale(s->gv[j], s->cs[j]);
+    for (int i = 0; i <= j; ++i) s->H[i * kMaxKrylov + j] = hc[i];
+    s->j = j + 1;
+    if (gm_abs(s->gv[j + 1]) <= tol * s->bn) {
+        s->skip = 1;
+        s->ictl.status = 0;
+    }
+}
+
+__global__ void k_gm_solve(GmState* s) {
+    if (threadIdx.x != 0) return;
+    const int j = s->j;
+    for (int i = j - 1; i >= 0; --i) {
+        double2 a = s->gv[i];
+        for (int k = i + 1; k < j; ++k) a = gm_sub(a, gm_mul(s->H[i * kMaxKrylov + k], s->coef[k]));
+        s->coef[i] = gm_div(a, s->H[i * kMaxKrylov + i]);
     }
 }
 
@@ -169,57 +319,76 @@ void launch_jtilde(const double* U, const float2* uff, int nt, int nspace, T* jt
 }
 template <class T>
 void launch_apply_M(const Geo& g, int nk, const c_t<T>* Y, c_t<T>* W, const T* jt, const Tabs<T>& tb, double c2,
-                    double c1, cudaStream_t st) {
+                    double c1, const int* skip, const c_t<T>* B, cudaStream_t st) {
     if (g.dim == 2) {
         dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, nk);
-        k_apply_M<T, 2><<<grid, 256, 0, st>>>(g, nk, Y, W, jt, tb, (T)c2, (T)c1);
+        k_apply_M<T, 2><<<grid, 256, 0, st>>>(g, nk, Y, W, jt, tb, (T)c2, (T)c1, skip, B);
     } else {
         dim3 grid((g.nx + 255) / 256, 1, nk);
-        k_apply_M<T, 1><<<grid, 256, 0, st>>>(g, nk, Y, W, jt, tb, (T)c2, (T)c1);
+        k_apply_M<T, 1><<<grid, 256, 0, st>>>(g, nk, Y, W, jt, tb, (T)c2, (T)c1, skip, B);
     }
 }
 // Groups of up to kGroup vectors per launch, register accumulators.  Note:
 // w may itself be one of the v_i (the axpy reads w[e] before writing it).
 template <class T>
 void launch_cmulti_dot(const c_t<T>* w, const c_t<T>* V, size_t ld, int nv, size_t n, double* partials,
-                       cudaStream_t st) {
+                       const int* skip, cudaStream_t st) {
     const int nb = grid_n(n);
     for (int i0 = 0; i0 < nv; i0 += kGroup) {
         const c_t<T>* Vi = V + (size_t)i0 * ld;
         switch (nv - i0 >= kGroup ? kGroup : nv - i0) {
-            case 1: k_cmulti_dot<T, 1><<<nb, kCDotThreads, 0, st>>>(w, Vi, ld, n, nv, i0, partials); break;
-            case 2: k_cmulti_dot<T, 2><<<nb, kCDotThreads, 0, st>>>(w, Vi, ld, n, nv, i0, partials); break;
-            case 3: k_cmulti_dot<T, 3><<<nb, kCDotThreads, 0, st>>>(w, Vi, ld, n, nv, i0, partials); break;
-            default: k_cmulti_dot<T, 4><<<nb, kCDotThreads, 0, st>>>(w, Vi, ld, n, nv, i0, partials); break;
+            case 1: k_cmulti_dot<T, 1><<<nb, kCDotThreads, 0, st>>>(w, Vi, ld, n, nv, i0, partials, skip); break;
+            case 2: k_cmulti_dot<T, 2><<<nb, kCDotThreads, 0, st>>>(w, Vi, ld, n, nv, i0, partials, skip); break;
+            case 3: k_cmulti_dot<T, 3><<<nb, kCDotThreads, 0, st>>>(w, Vi, ld, n, nv, i0, partials, skip); break;
+            default: k_cmulti_dot<T, 4><<<nb, kCDotThreads, 0, st>>>(w, Vi, ld, n, nv, i0, partials, skip); break;
         }
     }
 }
 template <class T>
-void launch_cmulti_axpy(c_t<T>* w, const c_t<T>* V, size_t ld, int nv, const double* c, size_t n, cudaStream_t st) {
+void launch_cmulti_axpy(c_t<T>* w, const c_t<T>* V, size_t ld, int nv, const double* c, size_t n, const int* skip,
+                        const int* nlim, cudaStream_t st, c_t<T>* out, const double* post) {
     const int nb = grid_n(n);
     for (int i0 = 0; i0 < nv; i0 += kGroup) {
         const c_t<T>* Vi = V + (size_t)i0 * ld;
         const double* ci = c + 2 * i0;
+        // the first group reads w and writes out; later groups update out in place; the last one scales
+        c_t<T>* src = i0 == 0 ? w : (out ? out : w);
+        const double* ps = i0 + kGroup >= nv ? post : nullptr;
         switch (nv - i0 >= kGroup ? kGroup : nv - i0) {
-            case 1: k_cmulti_axpy<T, 1><<<nb, 256, 0, st>>>(w, Vi, ld, ci, n); break;
-            case 2: k_cmulti_axpy<T, 2><<<nb, 256, 0, st>>>(w, Vi, ld, ci, n); break;
-            case 3: k_cmulti_axpy<T, 3><<<nb, 256, 0, st>>>(w, Vi, ld, ci, n); break;
-            default: k_cmulti_axpy<T, 4><<<nb, 256, 0, st>>>(w, Vi, ld, ci, n); break;
+            case 1: k_cmulti_axpy<T, 1><<<nb, 256, 0, st>>>(src, Vi, ld, ci, n, skip, nlim, i0, out, ps); break;
+            case 2: k_cmulti_axpy<T, 2><<<nb, 256, 0, st>>>(src, Vi, ld, ci, n, skip, nlim, i0, out, ps); break;
+            case 3: k_cmulti_axpy<T, 3><<<nb, 256, 0, st>>>(src, Vi, ld, ci, n, skip, nlim, i0, out, ps); break;
+            default: k_cmulti_axpy<T, 4><<<nb, 256, 0, st>>>(src, Vi, ld, ci, n, skip, nlim, i0, out, ps); break;
         }
     }
 }
 template <class T>
-void launch_caxpby(c_t<T>* z, double a, const c_t<T>* x, double b, const c_t<T>* y, size_t n, cudaStream_t st) {
-    k_caxpby<T><<<grid_n(n), 256, 0, st>>>(z, (T)a, x, (T)b, y, n);
+void launch_caxpby(c_t<T>* z, double a, const c_t<T>* x, double b, const c_t<T>* y, size_t n, const int* skip,
+                   const double* sdev, cudaStream_t st) {
+    k_caxpby<T><<<grid_n(n), 256, 0, st>>>(z, (T)a, x, (T)b, y, n, skip, sdev);
 }
+void launch_gm_init(const double* part_bb, const double* part_rr, int nb, const Ctl* octl, GmState* s, double tol,
+                    cudaStream_t st) {
+    k_gm_init<<<1, kGmThreads, 0, st>>>(part_bb, part_rr, nb, octl, s, tol);
+}
+void launch_gm_orth1(const double* part, int nb, int j, GmState* s, cudaStream_t st) {
+    k_gm_orth1<<<1, kGmThreads, 0, st>>>(part, nb, j, s);
+}
+void launch_gm_orth2(const double* part, int nb, int j, GmState* s, double tol, cudaStream_t st) {
+    k_gm_orth2<<<1, kGmThreads, 0, st>>>(part, nb, j, s, tol);
+}
+void launch_gm_solve(GmState* s, cudaStream_t st) { k_gm_solve<<<1, 32, 0, st>>>(s); }
 
 #define PINT_INST(T)                                                                                              \
     template void launch_jtilde<T>(const double*, const float2*, int, int, T*, cudaStream_t);                      \
     template void launch_apply_M<T>(const Geo&, int, const c_t<T>*, c_t<T>*, const T*, const Tabs<T>&, double,    \
-                                    double, cudaStream_t);                                                        \
-    template void launch_cmulti_dot<T>(const c_t<T>*, const c_t<T>*, size_t, int, size_t, double*, cudaStream_t); \
-    template void launch_cmulti_axpy<T>(c_t<T>*, const c_t<T>*, size_t, int, const double*, size_t, cudaStream_t); \
-    template void launch_caxpby<T>(c_t<T>*, double, const c_t<T>*, double, const c_t<T>*, size_t, cudaStream_t);
+                                    double, const int*, const c_t<T>*, cudaStream_t);                             \
+    template void launch_cmulti_dot<T>(const c_t<T>*, const c_t<T>*, size_t, int, size_t, double*, const int*,     \
+                                       cudaStream_t);                                                             \
+    template void launch_cmulti_axpy<T>(c_t<T>*, const c_t<T>*, size_t, int, const double*, size_t, const int*,    \
+                                        const int*, cudaStream_t, c_t<T>*, const double*);                        \
+    template void launch_caxpby<T>(c_t<T>*, double, const c_t<T>*, double, const c_t<T>*, size_t, const int*,      \
+                                   const double*, cudaStream_t);
 PINT_INST(float)
 PINT_INST(double)
 #undef PINT_INST

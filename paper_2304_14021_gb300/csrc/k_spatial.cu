@@ -11,8 +11,10 @@
 //    complex data (the real and imaginary parts are transformed independently)
 //    X_p = (w_p V_p + conj(w_p) V_{n-p}) / 2 with w_p = exp(-i pi p / 2n), and
 //    its inverse V_p = conj(w_p) (X_p - i X_{n-p}); both pair p with n - p.
-//  * dense (simply supported DST-I, or any n <= 1024): X = F x, x = F^{-1} X
-//    with the basis matrices held in device tables.
+//  * sine (simply supported, n + 1 a power of two): DST-I by one complex FFT
+//    of length 2(n+1) of the odd extension (k_dst.cu);
+//  * dense (any other n <= 1024, and the vertex-centred DCT-I): X = F x,
+//    x = F^{-1} X with the basis matrices held in device tables.
 // 1-D: one fused pass (transform, divide, inverse) per row.  2-D: x-forward
 // over rows, fused y pass (transform, divide, inverse) over columns, x-inverse.
 #include <cooperative_groups.h>
@@ -20,13 +22,12 @@
 #include "../../include/pint.h"
 #include "pint_common.cuh"
 #include "pint_kernels.h"
+#include "spatial.cuh"
 #include "tma.cuh"
 
 namespace cg = cooperative_groups;
 
 namespace pint {
-
-enum { MODE_FWD = 0, MODE_INV = 1, MODE_FDI = 2, MODE_PACK = 3 };
 
 // Destination of MODE_PACK (1-D rows on a long time axis): the solved row
 // S2[k] goes straight into the workspace of the inverse time transform as
@@ -37,23 +38,6 @@ template <class T> struct PackDst {
     LongPlan pl;
     int nt;
 };
-
-template <class T>
-__device__ __forceinline__ c_t<T> shift_den(const Tabs<T>& tb, int k, T Lam, T c2, T c1) {
-    const T mu = c2 * Lam * Lam + c1 * Lam;
-    const c_t<T> l1 = tb.lam1[k], l2 = tb.lam2[k];
-    c_t<T> d = mkc(l1.x + l2.x * mu, l1.y + l2.y * mu);
-    if (tb.dte != T(0)) {   // PinT-II: + lambda_3k Lam, lambda_3k = alpha^{1/N_t} e^{-2 pi i k/N_t} = 1 - dt lambda_1k
-        d.x += (T(1) - tb.dte * l1.x) * Lam;
-        d.y -= tb.dte * l1.y * Lam;
-    }
-    return d;
-}
-
-template <class T>
-__device__ __forceinline__ T solve_c1(SolveCoef co, const Ctl* ctl) {
-    return co.ch ? T(co.c1 - ctl->jbar) : T(co.c1);
-}
 
 // position of x_i in the even/odd reordered sequence v (v_j = x_2j, v_{n-1-j} = x_{2j+1})
 __device__ __forceinline__ int dct_pos(int i, int n) { return (i & 1) ? n - 1 - (i >> 1) : (i >> 1); }
@@ -760,7 +744,7 @@ static int slice2d_fits() {
 // about 2x (64^2) and 1.5x (128^2) faster than the three passes; at 256^2 the
 // large clusters (1-3 CTAs per SM) made it slower than three passes.
 int slice2d_supported(const Geo& g, int fft_x, int fft_y, int f32) {
-    if (g.dim != 2 || !fft_x || !fft_y || g.nx != g.ny) return 0;
+    if (g.dim != 2 || fft_x != 1 || fft_y != 1 || g.nx != g.ny) return 0;
     switch (g.nx) {
         case 64: return f32 ? slice2d_fits<float, 64>() : slice2d_fits<double, 64>();
         case 128: return f32 ? slice2d_fits<float, 128>() : slice2d_fits<double, 128>();
@@ -996,6 +980,12 @@ static void dense(int axis, int nx, int ny, int nk, c_t<T>* S, const Tabs<T>& tb
     k_dense<T, MODE><<<nvec, 128, 2 * n * sizeof(c_t<T>), st>>>(axis, nx, ny, nvec, S, tb, co, ctl);
 }
 
+// Sine path of one axis (k_dst.cu).
+template <class T, int MODE, int AXIS>
+cudaError_t dst_axis(int n, int nx, int ny, long nlines, c_t<T>* S, const Tabs<T>& tb, SolveCoef co, const Ctl* ctl,
+                     cudaStream_t st);
+
+// Axis kinds (fft_x, fft_y): 1 = cosine FFT path, 2 = sine (DST-I) FFT path, 0 = dense.
 template <class T>
 cudaError_t launch_spatial_stage(int stage, const Geo& g, c_t<T>* S, const Tabs<T>& tb, SolveCoef co, int fft_x,
                                  int fft_y, const Ctl* ctl, cudaStream_t st) {
@@ -1004,16 +994,20 @@ cudaError_t launch_spatial_stage(int stage, const Geo& g, c_t<T>* S, const Tabs<
     cudaError_t e = cudaSuccess;
     if (g.dim == 1) {
         if (stage != 0) return cudaSuccess;
-        if (fft_x) e = rows_dct<T, MODE_FDI>(g.nx, nk, 1, S, tb, co, ctl, st);
+        if (fft_x == 1) e = rows_dct<T, MODE_FDI>(g.nx, nk, 1, S, tb, co, ctl, st);
+        else if (fft_x == 2) e = dst_axis<T, MODE_FDI, 0>(g.nx, g.nx, 1, nk, S, tb, co, ctl, st);
         else dense<T, MODE_FDI>(0, g.nx, 1, nk, S, tb, co, ctl, st);
     } else if (stage == 0) {
-        if (fft_x) e = rows_dct<T, MODE_FWD>(g.nx, nk * ny, ny, S, tb, co, ctl, st);
+        if (fft_x == 1) e = rows_dct<T, MODE_FWD>(g.nx, nk * ny, ny, S, tb, co, ctl, st);
+        else if (fft_x == 2) e = dst_axis<T, MODE_FWD, 0>(g.nx, g.nx, ny, (long)nk * ny, S, tb, co, ctl, st);
         else dense<T, MODE_FWD>(0, g.nx, ny, nk, S, tb, co, ctl, st);
     } else if (stage == 1) {
-        if (fft_y) e = cols_dct<T>(g.nx, ny, nk, S, tb, co, ctl, st);
+        if (fft_y == 1) e = cols_dct<T>(g.nx, ny, nk, S, tb, co, ctl, st);
+        else if (fft_y == 2) e = dst_axis<T, MODE_FDI, 1>(ny, g.nx, ny, (long)nk * g.nx, S, tb, co, ctl, st);
         else dense<T, MODE_FDI>(1, g.nx, ny, nk, S, tb, co, ctl, st);
     } else {
-        if (fft_x) e = rows_dct<T, MODE_INV>(g.nx, nk * ny, ny, S, tb, co, ctl, st);
+        if (fft_x == 1) e = rows_dct<T, MODE_INV>(g.nx, nk * ny, ny, S, tb, co, ctl, st);
+        else if (fft_x == 2) e = dst_axis<T, MODE_INV, 0>(g.nx, g.nx, ny, (long)nk * ny, S, tb, co, ctl, st);
         else dense<T, MODE_INV>(0, g.nx, ny, nk, S, tb, co, ctl, st);
     }
     if (e != cudaSuccess) return e;

@@ -41,18 +41,62 @@ __global__ void __launch_bounds__(TimeCfg<T, NT>::NTH)
     const int tid = threadIdx.x;
     const long p0 = (long)blockIdx.x * 2 * CW;
     for (int i = tid; i < NT; i += NTH) tw[i] = twt[i];
+    // complex64 transforms on rows of a multiple of 4 points: 128-bit loads of 4
+    // residual values and 128-bit stores of 2 spectrum values per thread (the
+    // groups of 4 are then all inside the grid or all outside)
+    const bool vec = sizeof(T) == 4 && (nspace & 3) == 0;
+    if constexpr (sizeof(T) == 4) {
+        if (vec) {
+            constexpr int CQ = CW / 4;
+#pragma unroll 4
+            for (int e = tid; e < NT * CQ; e += NTH) {
+                const int c = (e % CQ) * 4, n = e / CQ;
+                const long pa = p0 + c, pb = p0 + CW + c;
+                const T* row = s + (size_t)n * nspace;
+                const float4 a = pa < nspace ? __ldg(reinterpret_cast<const float4*>(row + pa)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 b = pb < nspace ? __ldg(reinterpret_cast<const float4*>(row + pb)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                C* zz = z + n * CW + c;
+                zz[0] = mkc(a.x, b.x);
+                zz[1] = mkc(a.y, b.y);
+                zz[2] = mkc(a.z, b.z);
+                zz[3] = mkc(a.w, b.w);
+            }
+        }
+    }
+    if (!vec) {
 #pragma unroll 8
-    for (int e = tid; e < NT * CW; e += NTH) {
-        const int c = e % CW, n = e / CW;
-        const long pa = p0 + c, pb = p0 + CW + c;
-        const T* row = s + (size_t)n * nspace;
-        T a = pa < nspace ? row[pa] : T(0);
-        T b = pb < nspace ? row[pb] : T(0);
-        z[e] = mkc(a, b);
+        for (int e = tid; e < NT * CW; e += NTH) {
+            const int c = e % CW, n = e / CW;
+            const long pa = p0 + c, pb = p0 + CW + c;
+            const T* row = s + (size_t)n * nspace;
+            T a = pa < nspace ? row[pa] : T(0);
+            T b = pb < nspace ? row[pb] : T(0);
+            z[e] = mkc(a, b);
+        }
     }
     __syncthreads();
     smem_fft<C, NT, -1, NTH, CW, CW, 1>(z, tw);
     const T half = T(0.5);
+    if constexpr (sizeof(T) == 4) {
+        if (vec) {
+            constexpr int CH = CW / 2;
+#pragma unroll 4
+            for (int e = tid; e < (NT / 2 + 1) * CH; e += NTH) {
+                const int c = (e % CH) * 2, k = e / CH, kr = (NT - k) % NT;
+                const C zk0 = z[k * CW + c], zk1 = z[k * CW + c + 1];
+                const C zr0 = z[kr * CW + c], zr1 = z[kr * CW + c + 1];
+                const long pa = p0 + c, pb = p0 + CW + c;
+                C* row = S + (size_t)k * nspace;
+                if (pa < nspace)
+                    *reinterpret_cast<float4*>(row + pa) = make_float4(half * (zk0.x + zr0.x), half * (zk0.y - zr0.y),
+                                                                       half * (zk1.x + zr1.x), half * (zk1.y - zr1.y));
+                if (pb < nspace)
+                    *reinterpret_cast<float4*>(row + pb) = make_float4(half * (zk0.y + zr0.y), half * (zr0.x - zk0.x),
+                                                                       half * (zk1.y + zr1.y), half * (zr1.x - zk1.x));
+            }
+            return;
+        }
+    }
 #pragma unroll 4
     for (int e = tid; e < (NT / 2 + 1) * CW; e += NTH) {
         const int c = e % CW, k = e / CW;
@@ -83,16 +127,41 @@ __global__ void __launch_bounds__(TimeCfg<T, NT>::NTH)
     const int tid = threadIdx.x;
     const long p0 = (long)blockIdx.x * 2 * CW;
     for (int i = tid; i < NT; i += NTH) tw[i] = twt[i];
+    // complex64 spectrum and FP64 iterate on rows of an even number of points:
+    // 128-bit accesses of two points per thread (pairs all inside or all outside)
+    const bool vec = sizeof(T) == 4 && OUTK == 0 && (nspace & 1) == 0;
+    if constexpr (sizeof(T) == 4 && OUTK == 0) {
+        if (vec) {
+            constexpr int CH = CW / 2;
 #pragma unroll 4
-    for (int e = tid; e < (NT / 2 + 1) * CW; e += NTH) {
-        const int c = e % CW, k = e / CW;
-        const long pa = p0 + c, pb = p0 + CW + c;
-        const C* row = S + (size_t)k * nspace;
-        C a = pa < nspace ? row[pa] : mkc(T(0), T(0));
-        C b = pb < nspace ? row[pb] : mkc(T(0), T(0));
-        if (k == 0 || k == NT / 2) { a.y = T(0); b.y = T(0); }  // real in exact arithmetic
-        z[k * CW + c] = mkc(a.x - b.y, a.y + b.x);
-        if (k > 0 && k < NT / 2) z[(NT - k) * CW + c] = mkc(a.x + b.y, b.x - a.y);
+            for (int e = tid; e < (NT / 2 + 1) * CH; e += NTH) {
+                const int c = (e % CH) * 2, k = e / CH;
+                const long pa = p0 + c, pb = p0 + CW + c;
+                const C* row = S + (size_t)k * nspace;
+                float4 A = pa < nspace ? __ldg(reinterpret_cast<const float4*>(row + pa)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                float4 B = pb < nspace ? __ldg(reinterpret_cast<const float4*>(row + pb)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                if (k == 0 || k == NT / 2) { A.y = A.w = 0.f; B.y = B.w = 0.f; }  // real in exact arithmetic
+                z[k * CW + c] = mkc(A.x - B.y, A.y + B.x);
+                z[k * CW + c + 1] = mkc(A.z - B.w, A.w + B.z);
+                if (k > 0 && k < NT / 2) {
+                    z[(NT - k) * CW + c] = mkc(A.x + B.y, B.x - A.y);
+                    z[(NT - k) * CW + c + 1] = mkc(A.z + B.w, B.z - A.w);
+                }
+            }
+        }
+    }
+    if (!vec) {
+#pragma unroll 4
+        for (int e = tid; e < (NT / 2 + 1) * CW; e += NTH) {
+            const int c = e % CW, k = e / CW;
+            const long pa = p0 + c, pb = p0 + CW + c;
+            const C* row = S + (size_t)k * nspace;
+            C a = pa < nspace ? row[pa] : mkc(T(0), T(0));
+            C b = pb < nspace ? row[pb] : mkc(T(0), T(0));
+            if (k == 0 || k == NT / 2) { a.y = T(0); b.y = T(0); }  // real in exact arithmetic
+            z[k * CW + c] = mkc(a.x - b.y, a.y + b.x);
+            if (k > 0 && k < NT / 2) z[(NT - k) * CW + c] = mkc(a.x + b.y, b.x - a.y);
+        }
     }
     __syncthreads();
     smem_fft<C, NT, +1, NTH, CW, CW, 1>(z, tw);
@@ -100,8 +169,46 @@ __global__ void __launch_bounds__(TimeCfg<T, NT>::NTH)
     // correction and the updated iterate, for the update-size stopping test
     float d2 = 0.f, u2 = 0.f;
     const bool want = dpart != nullptr;
+    if constexpr (sizeof(T) == 4 && OUTK == 0) {
+        if (vec && accumulate) {
+            // U + x gamma_n^{-1}/N_t, two points per 128-bit access
+            constexpr int CH = CW / 2;
 #pragma unroll 4
-    for (int e = tid; e < NT * CW; e += NTH) {
+            for (int e = tid; e < NT * CH; e += NTH) {
+                const int c = (e % CH) * 2, n = e / CH;
+                const C v0 = z[n * CW + c], v1 = z[n * CW + c + 1];
+                const long pa = p0 + c, pb = p0 + CW + c;
+                const double gi = ginv[n];
+                double* row = out + (size_t)n * nspace;
+                if (pa < nspace) {
+                    double2* q = reinterpret_cast<double2*>(row + pa);
+                    const double2 u = __ldcs(q);
+                    const double2 w = make_double2(fma(f32_to_f64_exact(v0.x), gi, u.x), fma(f32_to_f64_exact(v1.x), gi, u.y));
+                    __stcs(q, w);
+                    if (want) {
+                        const float g32 = f64_to_f32_trunc(gi), da0 = v0.x * g32, da1 = v1.x * g32;
+                        const float w0 = f64_to_f32_trunc(w.x), w1 = f64_to_f32_trunc(w.y);
+                        d2 = fmaf(da1, da1, fmaf(da0, da0, d2));
+                        u2 = fmaf(w1, w1, fmaf(w0, w0, u2));
+                    }
+                }
+                if (pb < nspace) {
+                    double2* q = reinterpret_cast<double2*>(row + pb);
+                    const double2 u = __ldcs(q);
+                    const double2 w = make_double2(fma(f32_to_f64_exact(v0.y), gi, u.x), fma(f32_to_f64_exact(v1.y), gi, u.y));
+                    __stcs(q, w);
+                    if (want) {
+                        const float g32 = f64_to_f32_trunc(gi), db0 = v0.y * g32, db1 = v1.y * g32;
+                        const float w0 = f64_to_f32_trunc(w.x), w1 = f64_to_f32_trunc(w.y);
+                        d2 = fmaf(db1, db1, fmaf(db0, db0, d2));
+                        u2 = fmaf(w1, w1, fmaf(w0, w0, u2));
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll 4
+    for (int e = tid; e < (vec && accumulate ? 0 : NT * CW); e += NTH) {
         const int c = e % CW, n = e / CW;
         const C v = z[e];
         const long pa = p0 + c, pb = p0 + CW + c;

@@ -49,7 +49,14 @@ cudaError_t configure_kernels() {
 static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 // Per-axis transform path: 1 = FFT-based cosine transform, 0 = dense basis.
-static int axis_fft(int n, int bc, int nmax_fft) { return bc == PINT_BC_NEUMANN && is_pow2(n) && n >= 2 && n <= nmax_fft; }
+// Transform path of one axis: 1 = cosine FFT (cell-centred Neumann, n a power
+// of two up to nmax_fft), 2 = sine FFT (simply supported, n + 1 a power of two,
+// 3 <= n <= 4095), 0 = dense basis tables (n <= 1024).
+static int axis_fft(int n, int bc, int nmax_fft) {
+    if (bc == PINT_BC_NEUMANN && is_pow2(n) && n >= 2 && n <= nmax_fft) return 1;
+    if (bc == PINT_BC_SIMPLY_SUPPORTED && dst_axis_supported(n)) return 2;
+    return 0;
+}
 
 static int validate(const pint_problem* p) {
     if (!p) return PINT_EINVAL;
@@ -222,13 +229,11 @@ struct pint_handle {
     double* kcoef = nullptr;   // device copy of combination coefficients
     // space-varying Jacobian (PINT_OPT_VARYING_JACOBIAN): inner GMRES length and work vectors
     int vary = 0;
-    void* jbuf = nullptr;      // rhs, solution, (vary + 1) basis and vary preconditioned spectra
+    void* jbuf = nullptr;      // solution, (vary + 1) basis and vary preconditioned spectra
     void* jt = nullptr;        // J~(x), one per spatial point
     double* jpart = nullptr;   // complex dot partial sums
-    double* jcoef = nullptr;   // complex coefficients
-    double* jcoef_h = nullptr; // pinned host staging of the coefficients
+    pint::GmState* gms = nullptr;    // device state of the inner GMRES cycle
     double vary_tol = 1e-4;    // relative residual of the inner solve
-    long long inner_iters = 0; // inner GMRES iterations (statistics)
     // per-level invariants (PINT_OPT_LOG_INVARIANTS): (mass, energy) of every time level solved
     int log_inv = 0;
     double* inv_dev = nullptr;  // n_windows * nt pairs
@@ -241,7 +246,7 @@ template <class T> static Tabs<T>& tabs_of(pint_handle* h) { return *reinterpret
 
 // Layout of the tables block (elements of T; complex = 2 T).
 struct TabLayout {
-    size_t twt, twx, twy, wx, wy, fx, ix, fy, iy, lamx, lamy, lam1, lam2, total;
+    size_t twt, twx, twy, wx, wy, fx, ix, fy, iy, dsx, dsy, lamx, lamy, lam1, lam2, total;
 };
 static TabLayout tab_layout(const pint_problem* p, int fft_x, int fft_y) {
     TabLayout L{};
@@ -258,6 +263,8 @@ static TabLayout tab_layout(const pint_problem* p, int fft_x, int fft_y) {
     const bool dy = p->dim == 2 && !fft_y;
     L.fy = take(dy ? ny * ny : 0);
     L.iy = take(dy ? ny * ny : 0);
+    L.dsx = take(fft_x == 2 ? 4 * (nx + 1) : 0);
+    L.dsy = take(p->dim == 2 && fft_y == 2 ? 4 * (ny + 1) : 0);
     L.lamx = take(nx);
     L.lamy = take(ny);
     L.lam1 = take(2 * (nt / 2 + 1));
@@ -319,6 +326,10 @@ static int build_tables(pint_handle* h) {
         dense_basis(ny, p->bc, F, Fi);
         for (size_t i = 0; i < F.size(); ++i) { host[L.fy + i] = (T)F[i]; host[L.iy + i] = (T)Fi[i]; }
     }
+    if (h->fft_x == 2)
+        for (int j = 0; j < 2 * (nx + 1); ++j) cset(L.dsx, j, expi(-(double)j / (2.0 * (nx + 1))));
+    if (p->dim == 2 && h->fft_y == 2)
+        for (int j = 0; j < 2 * (ny + 1); ++j) cset(L.dsy, j, expi(-(double)j / (2.0 * (ny + 1))));
     for (int i = 0; i < nx; ++i) host[L.lamx + i] = (T)lap_eig(i, nx, p->bc);
     for (int i = 0; i < ny; ++i) host[L.lamy + i] = p->dim == 2 ? (T)lap_eig(i, ny, p->bc) : T(0);
     // Lemma 2.1 with the forward transform exp(-2 pi i nk/nt):
@@ -343,6 +354,8 @@ static int build_tables(pint_handle* h) {
     tb->ix = base + L.ix;
     tb->fy = base + L.fy;
     tb->iy = base + L.iy;
+    tb->dsx = reinterpret_cast<const c_t<T>*>(base + L.dsx);
+    tb->dsy = reinterpret_cast<const c_t<T>*>(base + L.dsy);
     tb->lamx = base + L.lamx;
     tb->lamy = base + L.lamy;
     tb->lam1 = reinterpret_cast<const c_t<T>*>(base + L.lam1);
@@ -560,7 +573,7 @@ static bool fused_spatial(const pint_handle* h) {
 // inverse time transform (not with the space-varying Jacobian, whose inner
 // solve works on the half spectrum itself).
 static bool long_fused(const pint_handle* h) {
-    return h->geo.dim == 1 && h->geo.nt > 1024 && h->fft_x && !(h->vary > 0 && h->coef.ch);
+    return h->geo.dim == 1 && h->geo.nt > 1024 && h->fft_x == 1 && !(h->vary > 0 && h->coef.ch);
 }
 static int spatial_launches(const pint_handle* h) {
     return long_fused(h) ? 0 : fused_spatial(h) ? 1 : (h->geo.dim == 2 ? 3 : 1);
@@ -623,17 +636,20 @@ static int tinv_blocks(pint_handle* h) {
 }
 
 template <class T> struct Impl {
-    static cudaError_t spatial(pint_handle* h, c_t<T>* S, const Tabs<T>& tb) {
+    // Step 2's scalar-Jacobian divide of every frequency slice; the kernels read
+    // status and jbar from ctl (the handle's control word unless given).
+    static cudaError_t spatial(pint_handle* h, c_t<T>* S, const Tabs<T>& tb, const Ctl* ctl = nullptr) {
+        if (!ctl) ctl = h->ctl;
         if (fused_spatial(h)) {
             prof_begin(h, PH_SP0);
-            cudaError_t e = launch_slice2d<T>(h->geo, S, tb, h->coef, h->ctl, h->st);
+            cudaError_t e = launch_slice2d<T>(h->geo, S, tb, h->coef, ctl, h->st);
             prof_end(h, PH_SP0, 1);
             return e;
         }
         const int nst = h->geo.dim == 2 ? 3 : 1;
         for (int stg = 0; stg < nst; ++stg) {
             prof_begin(h, PH_SP0 + stg);
-            cudaError_t e = launch_spatial_stage<T>(stg, h->geo, S, tb, h->coef, h->fft_x, h->fft_y, h->ctl, h->st);
+            cudaError_t e = launch_spatial_stage<T>(stg, h->geo, S, tb, h->coef, h->fft_x, h->fft_y, ctl, h->st);
             prof_end(h, PH_SP0 + stg, 1);
             if (e != cudaSuccess) return e;
         }
@@ -642,118 +658,54 @@ template <class T> struct Impl {
     // Step 2 with the space-varying Jacobian J~(x) (Eq. 4.12): one cycle of
     // flexible GMRES on the block-diagonal system M_k x_k = S1_k over all
     // frequencies at once, right-preconditioned by the scalar-J-bar divide,
-    // started from that divide's result.  Complex dot products in FP64,
-    // reduced on the host in a fixed order.
-    static int cdots(pint_handle* h, const c_t<T>* w, const c_t<T>* V, int nv, size_t n, std::complex<double>* out) {
-        const int nb = cdot_blocks(n);
-        launch_cmulti_dot<T>(w, V, n, nv, n, h->jpart, h->st);
-        std::vector<double> part((size_t)nb * nv * 2);
-        if (cudaMemcpyAsync(part.data(), h->jpart, part.size() * sizeof(double), cudaMemcpyDeviceToHost, h->st) ||
-            cudaStreamSynchronize(h->st))
-            return PINT_ECUDA;
-        for (int i = 0; i < nv; ++i) {
-            double a = 0.0, b = 0.0;
-            for (int q = 0; q < nb; ++q) { a += part[((size_t)q * nv + i) * 2]; b += part[((size_t)q * nv + i) * 2 + 1]; }
-            out[i] = std::complex<double>(a, b);
-        }
-        return PINT_OK;
-    }
-    // w += sum_i c_i v_i.  The coefficients go through pinned staging, refilled
-    // only after the previous copy from it has run (the stream is idle here after
-    // the dot products, so the wait is short).
-    static int caxpy(pint_handle* h, c_t<T>* w, const c_t<T>* V, int nv, size_t n, const std::complex<double>* c) {
-        if (cudaStreamSynchronize(h->st) != cudaSuccess) return PINT_ECUDA;
-        memcpy(h->jcoef_h, c, nv * 2 * sizeof(double));
-        if (cudaMemcpyAsync(h->jcoef, h->jcoef_h, nv * 2 * sizeof(double), cudaMemcpyHostToDevice, h->st))
-            return PINT_ECUDA;
-        launch_cmulti_axpy<T>(w, V, n, nv, h->jcoef, n, h->st);
-        return PINT_OK;
-    }
+    // started from that divide's result.  Complex dot products: per-thread sums
+    // in the vectors' precision, CTA and grid sums in FP64.  The cycle runs
+    // entirely on the device: one-CTA kernels add the dot products' partials in
+    // a fixed order and keep the Hessenberg matrix, the rotations and the stop
+    // test (GmState); the launch sequence is the same for every cycle (vector
+    // kernels skip once the cycle has stopped), so it can be captured.
     static cudaError_t step2_varying(pint_handle* h, c_t<T>* S, const Tabs<T>& tb, const double* U, const float2* uff) {
-        cudaError_t e = cudaMemcpyAsync(h->hctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->st);
-        if (e != cudaSuccess || (e = cudaStreamSynchronize(h->st)) != cudaSuccess) return e;
-        if (h->hctl->status != ST_RUNNING) return cudaSuccess;    // the iteration has stopped
         using C = c_t<T>;
         const Geo& g = h->geo;
         const int nk = g.nt / 2 + 1, m = h->vary;
         const size_t n = (size_t)nk * g.nspace;
-        C* B = reinterpret_cast<C*>(h->jbuf);
-        C* X = B + n;
+        const int nb = cdot_blocks(n);
+        C* X = reinterpret_cast<C*>(h->jbuf);   // the right-hand side S1 stays in S until the end
         C* V = X + n;
         C* Z = V + (size_t)(m + 1) * n;
         T* jt = reinterpret_cast<T*>(h->jt);
+        GmState* gs = h->gms;
+        const int* skip = &gs->skip;
+        const double* coef = reinterpret_cast<const double*>(gs->coef);
         const double c1 = g.expl ? 0.0 : 1.0;
+        cudaError_t e;
         launch_jtilde<T>(U, uff, g.nt, g.nspace, jt, h->st);
-        launch_caxpby<T>(B, 1.0, S, 0.0, nullptr, n, h->st);
-        launch_caxpby<T>(X, 1.0, S, 0.0, nullptr, n, h->st);
+        launch_caxpby<T>(X, 1.0, S, 0.0, nullptr, n, nullptr, nullptr, h->st);
         if ((e = spatial(h, X, tb)) != cudaSuccess) return e;           // x0 = P^{-1} S1
-        launch_apply_M<T>(g, nk, X, V, jt, tb, h->coef.c2, c1, h->st);
-        launch_caxpby<T>(V, -1.0, V, 1.0, B, n, h->st);                // r0 = S1 - M x0
-        std::complex<double> bb, rr;
-        if (cdots(h, B, B, 1, n, &bb) || cdots(h, V, V, 1, n, &rr)) return cudaErrorUnknown;
-        const double bn = sqrt(bb.real()), beta = sqrt(rr.real());
-        if (!(beta > h->vary_tol * bn)) {
-            launch_caxpby<T>(S, 1.0, X, 0.0, nullptr, n, h->st);
-            return cudaGetLastError();
-        }
-        launch_caxpby<T>(V, 1.0 / beta, V, 0.0, nullptr, n, h->st);
-        std::vector<std::complex<double>> H((size_t)(m + 1) * m), gv(m + 1), sn(m), hcol(m + 1), tmp(m + 1), y(m);
-        std::vector<double> cs(m);
-        gv[0] = beta;
-        int j = 0;
-        for (; j < m; ++j) {
+        launch_apply_M<T>(g, nk, X, V, jt, tb, h->coef.c2, c1, nullptr, S, h->st);   // r0 = S1 - M x0
+        launch_cmulti_dot<T>(S, S, n, 1, n, h->jpart, nullptr, h->st);
+        launch_cmulti_dot<T>(V, V, n, 1, n, h->jpart + 2 * (size_t)nb, nullptr, h->st);
+        launch_gm_init(h->jpart, h->jpart + 2 * (size_t)nb, nb, h->ctl, gs, h->vary_tol, h->st);
+        launch_caxpby<T>(V, 1.0, V, 0.0, nullptr, n, skip, &gs->scale, h->st);   // v_0 = r0 / ||r0||
+        for (int j = 0; j < m; ++j) {
             C* vj = V + (size_t)j * n;
             C* zj = Z + (size_t)j * n;
             C* w = V + (size_t)(j + 1) * n;
-            launch_caxpby<T>(zj, 1.0, vj, 0.0, nullptr, n, h->st);
-            if ((e = spatial(h, zj, tb)) != cudaSuccess) return e;       // z_j = P^{-1} v_j
-            launch_apply_M<T>(g, nk, zj, w, jt, tb, h->coef.c2, c1, h->st);
-            ++h->inner_iters;
+            launch_caxpby<T>(zj, 1.0, vj, 0.0, nullptr, n, skip, nullptr, h->st);
+            if ((e = spatial(h, zj, tb, &gs->ictl)) != cudaSuccess) return e;   // z_j = P^{-1} v_j
+            launch_apply_M<T>(g, nk, zj, w, jt, tb, h->coef.c2, c1, skip, nullptr, h->st);
             // classical Gram-Schmidt: <v_i, w> for i <= j and <w, w> in one pass (w is v_{j+1});
-            // ||w - sum h_i v_i||^2 = <w, w> - sum |h_i|^2, re-orthogonalized when that cancels
-            if (cdots(h, w, V, j + 2, n, tmp.data())) return cudaErrorUnknown;
-            double ww = tmp[j + 1].real(), hh = 0.0;
-            for (int i = 0; i <= j; ++i) { hcol[i] = tmp[i]; hh += std::norm(tmp[i]); }
-            double hn2 = ww - hh;
-            if (!(hn2 > 1e-4 * ww)) {
-                for (int i = 0; i <= j; ++i) tmp[i] = -hcol[i];
-                if (caxpy(h, w, V, j + 1, n, tmp.data())) return cudaErrorUnknown;
-                if (cdots(h, w, V, j + 2, n, tmp.data())) return cudaErrorUnknown;
-                hh = 0.0;
-                for (int i = 0; i <= j; ++i) { hcol[i] += tmp[i]; hh += std::norm(tmp[i]); }
-                hn2 = tmp[j + 1].real() - hh;
-                for (int i = 0; i <= j; ++i) tmp[i] = -tmp[i];
-            } else {
-                for (int i = 0; i <= j; ++i) tmp[i] = -hcol[i];
-            }
-            const double hn = sqrt(fmax(hn2, 0.0));
-            hcol[j + 1] = hn;
-            // w = (w - sum h_i v_i) / hn
-            if (caxpy(h, w, V, j + 1, n, tmp.data())) return cudaErrorUnknown;
-            if (hn > 0.0) launch_caxpby<T>(w, 1.0 / hn, w, 0.0, nullptr, n, h->st);
-            for (int i = 0; i < j; ++i) {                                   // previous rotations
-                const std::complex<double> a = cs[i] * hcol[i] + sn[i] * hcol[i + 1];
-                hcol[i + 1] = -std::conj(sn[i]) * hcol[i] + cs[i] * hcol[i + 1];
-                hcol[i] = a;
-            }
-            const double na = std::abs(hcol[j]), r = hypot(na, std::abs(hcol[j + 1]));
-            if (r == 0.0) { cs[j] = 1.0; sn[j] = 0.0; }
-            else if (na == 0.0) { cs[j] = 0.0; sn[j] = std::conj(hcol[j + 1]) / r; }
-            else { cs[j] = na / r; sn[j] = (hcol[j] / na) * std::conj(hcol[j + 1]) / r; }
-            hcol[j] = cs[j] * hcol[j] + sn[j] * hcol[j + 1];
-            hcol[j + 1] = 0.0;
-            gv[j + 1] = -std::conj(sn[j]) * gv[j];
-            gv[j] = cs[j] * gv[j];
-            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i];
-            if (std::abs(gv[j + 1]) <= h->vary_tol * bn) { ++j; break; }
+            // a second pass when ||w - sum h_i v_i||^2 = <w, w> - sum |h_i|^2 cancels
+            launch_cmulti_dot<T>(w, V, n, j + 2, n, h->jpart, skip, h->st);
+            launch_gm_orth1(h->jpart, nb, j, gs, h->st);
+            launch_cmulti_axpy<T>(w, V, n, j + 1, coef, n, &gs->skip_re, nullptr, h->st);
+            launch_cmulti_dot<T>(w, V, n, j + 2, n, h->jpart, &gs->skip_re, h->st);
+            launch_gm_orth2(h->jpart, nb, j, gs, h->vary_tol, h->st);
+            // v_{j+1} = (w - sum h_i v_i) / h_{j+1,j}
+            launch_cmulti_axpy<T>(w, V, n, j + 1, coef, n, skip, nullptr, h->st, nullptr, &gs->scale);
         }
-        for (int i = j - 1; i >= 0; --i) {
-            std::complex<double> a = gv[i];
-            for (int k = i + 1; k < j; ++k) a -= H[(size_t)i * m + k] * y[k];
-            y[i] = a / H[(size_t)i * m + i];
-        }
-        if (j > 0 && caxpy(h, X, Z, j, n, y.data())) return cudaErrorUnknown;
-        launch_caxpby<T>(S, 1.0, X, 0.0, nullptr, n, h->st);
+        launch_gm_solve(gs, h->st);
+        launch_cmulti_axpy<T>(X, Z, n, m, coef, n, nullptr, &gs->j, h->st, S);   // S2 = x0 + Z y
         return cudaGetLastError();
     }
     static cudaError_t step2(pint_handle* h, c_t<T>* S, const Tabs<T>& tb, const double* U, const float2* uff) {
@@ -1079,10 +1031,9 @@ void pint_destroy(pint_handle* h) {
     af(h->jbuf);
     af(h->jt);
     af(h->jpart);
-    af(h->jcoef);
+    af(h->gms);
     af(h->inv_dev);
     af(h->wgemm);
-    if (h->jcoef_h) cudaFreeHost(h->jcoef_h);
     if (h->nlev > 0) activate_level(h, 0);   // the base level owns gam/ginv/gamf/ginvf and tabs_ptrs
     for (int i = 1; i < h->nlev; ++i) {
         af(h->lev[i].block);
@@ -1133,7 +1084,12 @@ int pint_create(const pint_problem* p, void* cuda_stream, pint_handle** out) {
         delete h;
         return PINT_ECUDA;
     }
-    Sizes z = sizes_of(p, h);
+    Sizes z = sizes_of(p, h);   // also derives the geometry and the axis paths
+    if ((h->fft_x == 2 && configure_dst(p->nx, 0, f32_transforms(p)) != cudaSuccess) ||
+        (p->dim == 2 && h->fft_y == 2 && configure_dst(p->ny, 1, f32_transforms(p)) != cudaSuccess)) {
+        delete h;
+        return PINT_ECUDA;
+    }
     const size_t ts = f32_transforms(p) ? 4 : 8;
     auto dalloc = [&](void** ptr, size_t bytes) -> int {
         if (cudaMallocAsync(ptr, bytes < 16 ? 16 : bytes, h->st) != cudaSuccess) {
@@ -1282,11 +1238,13 @@ int pint_set_option(pint_handle* h, int option, long long value) {
         case PINT_OPT_VARYING_JACOBIAN: {
             if (value < 0 || value > kMaxKrylov) return PINT_EINVAL;
             if (value > 0 && !h->coef.ch) return PINT_EINVAL;   // Cahn-Hilliard only
-            for (void* q : {h->jbuf, h->jt, (void*)h->jpart, (void*)h->jcoef})
+            for (auto& sl : h->gslot)   // captured loops hold the old Step 2
+                if (sl.exec) { cudaGraphExecDestroy(sl.exec); sl.exec = nullptr; }
+            for (void* q : {h->jbuf, h->jt, (void*)h->jpart, (void*)h->gms})
                 if (q) cudaFreeAsync(q, h->st);
-            if (h->jcoef_h) { cudaStreamSynchronize(h->st); cudaFreeHost(h->jcoef_h); h->jcoef_h = nullptr; }
             h->jbuf = h->jt = nullptr;
-            h->jpart = h->jcoef = nullptr;
+            h->jpart = nullptr;
+            h->gms = nullptr;
             h->vary = 0;
             if (value == 0) return PINT_OK;
             const size_t tsz = f32_transforms(&h->p) ? 4 : 8;
@@ -1295,10 +1253,9 @@ int pint_set_option(pint_handle* h, int option, long long value) {
                 if (cudaMallocAsync(ptr, bytes, h->st) != cudaSuccess) { cudaGetLastError(); return false; }
                 return true;
             };
-            if (!al(&h->jbuf, (size_t)(2 * value + 3) * n * 2 * tsz) || !al(&h->jt, h->geo.nspace * tsz) ||
+            if (!al(&h->jbuf, (size_t)(2 * value + 2) * n * 2 * tsz) || !al(&h->jt, h->geo.nspace * tsz) ||
                 !al((void**)&h->jpart, (size_t)cdot_blocks(n) * (kMaxKrylov + 1) * 2 * sizeof(double)) ||
-                !al((void**)&h->jcoef, (kMaxKrylov + 1) * 2 * sizeof(double)) ||
-                cudaMallocHost((void**)&h->jcoef_h, (kMaxKrylov + 2) * 2 * sizeof(double)) != cudaSuccess)
+                !al((void**)&h->gms, sizeof(GmState)))
                 return PINT_ENOMEM;
             h->vary = (int)value;
             return PINT_OK;
@@ -1601,7 +1558,7 @@ static int solve_impl(pint_handle* h, const double* u0_dev, double* U_dev, pint_
             }
             launch_begin_window(g, u0w, p.max_iter, p.tol, h->partials, h->ctl, h->st, p.tol_update, h->b1);
             prof_end(h, PH_SETUP, nl + 1);
-            cudaGraphExec_t gx = (h->use_graphs && !h->prof_on && !adapt && !kry && !h->vary) ? get_graph(h, Useg, u0w) : nullptr;
+            cudaGraphExec_t gx = (h->use_graphs && !h->prof_on && !adapt && !kry) ? get_graph(h, Useg, u0w) : nullptr;
             if (kry) {
                 if ((rc = gmres_window(h, Useg, u0w)) != PINT_OK) return rc;
             } else if (gx) {

@@ -22,6 +22,8 @@ template <class T> struct Tabs {
     const T* ix;         // nx*nx dense inverse basis [j][p]
     const T* fy;         // ny*ny
     const T* iy;         // ny*ny
+    const c_t<T>* dsx;   // 2(nx+1): exp(-2 pi i j / (2(nx+1)))   (sine path)
+    const c_t<T>* dsy;   // 2(ny+1)
     const T* lamx;       // nx:  eigenvalues of the 1-D Laplacian along x
     const T* lamy;       // ny
     const c_t<T>* lam1;  // nt/2+1: lambda_1k of Lemma 2.1
@@ -160,21 +162,63 @@ void launch_multi_axpy(double* w, const double* V, size_t ld, int nv, const doub
 void launch_scale_copy(double* y, const double* x, double a, size_t n, cudaStream_t st);
 
 // Space-varying averaged Jacobian and the inner solve of Step 2 (k_jacobian.cu).
+// Every vector kernel below takes an optional device flag `skip`: when it is
+// nonzero at launch the kernel does nothing (the inner cycle has stopped), so
+// that one fixed launch sequence serves every cycle and can be captured.
 int cdot_blocks(size_t n);
 template <class T>
 void launch_jtilde(const double* U, const float2* uff, int nt, int nspace, T* jt, cudaStream_t st);
 // W[k] = lambda_1k Y[k] + lambda_2k (c2 Lap^2 Y[k] + Lap((c1 - J~) Y[k])) + lambda_3k Lap Y[k], k < nk
+// (W = B - that, when B is given)
 template <class T>
 void launch_apply_M(const Geo& g, int nk, const c_t<T>* Y, c_t<T>* W, const T* jt, const Tabs<T>& tb, double c2,
-                    double c1, cudaStream_t st);
+                    double c1, const int* skip, const c_t<T>* B, cudaStream_t st);
 // partials[(b nv + i) 2 + {re, im}] of <v_i, w> (cdot_blocks(n) CTAs)
 template <class T>
 void launch_cmulti_dot(const c_t<T>* w, const c_t<T>* V, size_t ld, int nv, size_t n, double* partials,
-                       cudaStream_t st);
+                       const int* skip, cudaStream_t st);
+// out = (w + sum_{i < nv} c_i v_i) * post (out = w and post = 1 when null); with nlim, only
+// the terms i < *nlim (the others are not read)
 template <class T>
-void launch_cmulti_axpy(c_t<T>* w, const c_t<T>* V, size_t ld, int nv, const double* c, size_t n, cudaStream_t st);
+void launch_cmulti_axpy(c_t<T>* w, const c_t<T>* V, size_t ld, int nv, const double* c, size_t n, const int* skip,
+                        const int* nlim, cudaStream_t st, c_t<T>* out = nullptr, const double* post = nullptr);
+// z = a x + b y (y may be null); with sdev, a is *sdev instead
 template <class T>
-void launch_caxpby(c_t<T>* z, double a, const c_t<T>* x, double b, const c_t<T>* y, size_t n, cudaStream_t st);
+void launch_caxpby(c_t<T>* z, double a, const c_t<T>* x, double b, const c_t<T>* y, size_t n, const int* skip,
+                   const double* sdev, cudaStream_t st);
+
+// Device state of one cycle of the inner flexible GMRES (classical Gram-Schmidt
+// with a conditional second pass, complex Givens rotations, FP64 scalars).  The
+// small kernels below update it from the dot products' per-CTA partials, which
+// they add in a fixed order, so the cycle is deterministic and needs no host
+// round trip.
+struct GmState {
+    Ctl ictl;            // control word of the cycle's spatial solves: jbar, and status ST_RUNNING while it runs
+    int skip;            // nonzero once the cycle has stopped (converged, or the outer iteration has stopped)
+    int skip_re;         // nonzero: this step's second Gram-Schmidt pass is skipped
+    int j;               // inner iterations completed
+    int reorth;
+    double bn;           // ||S1||
+    double hn2;
+    double scale;        // the factor the next normalization applies
+    double cs[kMaxKrylov];
+    double2 sn[kMaxKrylov];
+    double2 gv[kMaxKrylov + 1];
+    double2 H[kMaxKrylov * kMaxKrylov];   // upper triangle, row i, column j at i * kMaxKrylov + j
+    double2 hcol[kMaxKrylov + 1];
+    double2 coef[kMaxKrylov + 1];        // axpy coefficients (re, im), also the final y
+    double2 tmp[kMaxKrylov + 2];
+};
+// Start: ||S1|| and ||r0|| from two single-vector partial sets; stop at once when
+// the outer iteration has stopped or ||r0|| <= tol ||S1||.
+void launch_gm_init(const double* part_bb, const double* part_rr, int nb, const Ctl* octl, GmState* s, double tol,
+                    cudaStream_t st);
+// Step j, first pass: h_i = <v_i, w>, i <= j, and <w, w> from partials of j + 2 vectors.
+void launch_gm_orth1(const double* part, int nb, int j, GmState* s, cudaStream_t st);
+// Step j, second pass (if taken), the norm, the rotations and the stop test.
+void launch_gm_orth2(const double* part, int nb, int j, GmState* s, double tol, cudaStream_t st);
+// y = H^{-1} g over the completed steps, into coef.
+void launch_gm_solve(GmState* s, cudaStream_t st);
 // CTAs of launch_time_inv_ff (with the same control block argument).
 int time_inv_ff_blocks(int nt, int nspace, const Ctl* ctl);
 // Step 2: per frequency k, S[k] <- (lambda_1k I + lambda_2k A)^{-1} S[k], in
@@ -193,6 +237,12 @@ void launch_zero_start(c_t<T>* S, const double* u0, double inv_dt, int nspace, i
 // Fused 2-D solve of every frequency slice in one kernel (thread-block cluster
 // per slice); for square grids of 64, 128 (FP32/FP64) or 256 (FP32) cells per side.
 int slice2d_supported(const Geo& g, int fft_x, int fft_y, int f32);
+// Sine path of a simply supported axis of n points: n + 1 a power of two, 3 <= n <= 4095.
+int dst_axis_supported(int n);
+// Shared-memory attributes and resident-CTA counts of the sine-path kernels of
+// an axis of n points (axis 0: rows, 1: columns; f32: complex64 transforms).
+// Called outside any stream capture before the first launch.
+cudaError_t configure_dst(int n, int axis, int f32);
 template <class T>
 cudaError_t launch_slice2d(const Geo& g, c_t<T>* S, const Tabs<T>& tb, SolveCoef co, const Ctl* ctl,
                            cudaStream_t st);

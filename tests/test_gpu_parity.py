@@ -96,6 +96,13 @@ LARGE_PRECOND_CASES = [
     dict(equation="linear_ch", dim=1, nx=512, bc="neumann", nt=16, T=1e-5, eps=0.05, beta=0.5),
     dict(equation="biharmonic", dim=1, nx=256, bc="neumann", nt=32, T=1e-6),
     dict(equation="linear_ch", dim=2, nx=128, ny=128, bc="neumann", nt=16, T=0.01, eps=0.05, beta=0.5),
+    # simply supported axes with n + 1 a power of two: the sine (DST-I) FFT path, up to 4095 points
+    dict(equation="biharmonic", dim=1, nx=2047, bc="ss", nt=16, T=1e-7),
+    dict(equation="linear_ch", dim=1, nx=4095, bc="ss", nt=8, T=1e-8, eps=0.05, beta=0.5),
+    dict(equation="linear_ch", dim=2, nx=127, ny=63, bc="ss", nt=16, T=1e-4, eps=0.05, beta=0.5),
+    dict(equation="cahn_hilliard", dim=2, nx=255, ny=255, bc="ss", nt=8, T=8e-5, eps=0.02),
+    dict(equation="biharmonic", dim=2, nx=31, ny=1023, bc="ss", nt=4, T=1e-8),
+    dict(equation="biharmonic", dim=2, nx=2047, ny=7, bc="ss", nt=2, T=1e-9),
 ]
 
 
@@ -113,6 +120,29 @@ def test_precond_apply_large_matches_oracle(case, precision):
         err = O.rel_err(host(out), ref)
     tol = 1e-11 if precision == "fp64" else 3e-6 / p.alpha
     assert err < tol, err
+
+
+# Full solves through the sine path (simply supported axes with n + 1 a power
+# of two) against the sequential oracle.
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("kw", [
+    dict(equation="biharmonic", dim=1, nx=63, bc="ss", nt=32, T=0.01),
+    dict(equation="linear_ch", dim=2, nx=31, ny=63, bc="ss", nt=16, T=0.01, eps=0.05, beta=0.5),
+    dict(equation="biharmonic", dim=1, nx=1023, bc="ss", nt=8, T=1e-8),
+])
+def test_sine_path_solve_matches_sequential(kw, precision):
+    kw = full(dict(kw, precision=precision, tol=1e-11))
+    p = oprob(kw)
+    x = (np.arange(p.nx) + 1.0) / (p.nx + 1)
+    if p.dim == 1:
+        u0 = np.sin(np.pi * x) + 0.5 * np.sin(3 * np.pi * x)
+    else:
+        y = (np.arange(p.ny) + 1.0) / (p.ny + 1)
+        u0 = (np.outer(np.sin(np.pi * y), np.sin(2 * np.pi * x))
+              + 0.3 * np.outer(np.sin(3 * np.pi * y), np.sin(np.pi * x))).ravel()
+    U, st = run_solve(kw, u0)
+    assert st["rc"] == 0, st
+    assert O.rel_err(U, O.sequential(p, u0)) < 1e-9
 
 
 # --- residual (Eq. 2.6 / 4.8, alpha = 0) --------------------------------------
