@@ -49,9 +49,10 @@ FX_HD uint32_t fx_funnel_r(uint32_t lo, uint32_t hi, int s) {
 #endif
 }
 
-// Bits S .. S+63 of the exact 128-bit product L M (L signed, 0 <= M < 2^63), i.e.
-// floor(L M / 2^S), for 0 <= S <= 63 when that quotient fits in 64 bits.  S is
-// the same for every thread of a block (a uniform branch picks the word pair).
+// floor(L M / 2^S) for L signed, 0 <= M < 2^63 and S >= 0, whenever the
+// quotient fits in 64 bits (S >= 127: the sign word).  The exact 128-bit
+// product is formed from its four 32-bit words and the window selected by S;
+// S is the same for every thread of a block (uniform branches pick the words).
 FX_HD int64_t fx_mul_shr(int64_t L, int64_t M, int S) {
     const uint64_t lo = (uint64_t)L * (uint64_t)M;
 #if defined(__CUDA_ARCH__)
@@ -60,13 +61,22 @@ FX_HD int64_t fx_mul_shr(int64_t L, int64_t M, int S) {
     const int64_t hi = (int64_t)(((__int128)L * (__int128)M) >> 64);
 #endif
     const uint32_t w0 = (uint32_t)lo, w1 = (uint32_t)(lo >> 32), w2 = (uint32_t)hi, w3 = (uint32_t)((uint64_t)hi >> 32);
+    const uint32_t ws = (uint32_t)((int32_t)w3 >> 31);
     uint32_t rx, ry;
     if (S < 32) {
         rx = fx_funnel_r(w0, w1, S);
         ry = fx_funnel_r(w1, w2, S);
-    } else {
+    } else if (S < 64) {
         rx = fx_funnel_r(w1, w2, S - 32);
         ry = fx_funnel_r(w2, w3, S - 32);
+    } else if (S < 96) {
+        rx = fx_funnel_r(w2, w3, S - 64);
+        ry = fx_funnel_r(w3, ws, S - 64);
+    } else if (S < 128) {
+        rx = fx_funnel_r(w3, ws, S - 96);
+        ry = ws;
+    } else {
+        rx = ry = ws;
     }
     return (int64_t)(((uint64_t)ry << 32) | rx);
 }

@@ -1,18 +1,21 @@
 // k_residual_fx.cu - the all-at-once residual of the linear equations in
 // block fixed point on the integer pipes, FP64-accurate, for PINT_MIXED.
 //
-// Residual (Eq. 2.6 with alpha = 0; theta-method of Eq. 2.5, theta = 1 or 1/2),
-// evaluated scaled by dt:
+// Residual (Eq. 2.6 with alpha = 0; theta-method of Eq. 2.5, theta = 1 or 1/2;
+// Eq. 4.8 for Cahn-Hilliard, theta = 1), evaluated scaled by dt:
 //   dt r_n = u_{n-1} - u_n - theta dt A(u_n) - (1 - theta) dt A(u_{n-1}),
-//   A(u) = c2 Lap^2 u + c1 Lap u     (biharmonic: c1 = 0; linearized CH: c1 = beta|beta|, c2 = eps^2),
+//   A(u) = c2 Lap^2 u + c1 Lap u + cN Lap(u^3)
+//   (biharmonic: c1 = 0; linearized CH: c1 = beta|beta|, c2 = eps^2; CH: c1 = 1, cN = -1),
 // on square cells (and every 1-D grid), where h^2 Lap and h^4 Lap^2 have
 // integer stencils.  Each time level of a CTA's tile (halo 2, boundary
 // conditions as reflections, as in k_residual.cu) is converted from the FP64
 // iterate to 64-bit integers in the tile's unit 2^(E-56), E the tile's
 // largest binary exponent, so both Laplacian passes are exact integer sums.
-// The products with dt c1/h^2 and dt c2/h^4 use the coefficients' full
-// 53-bit mantissas (fx.cuh); the terms are aligned to the largest one's unit
-// and added exactly.  The result is then scaled by gamma_n/dt (Step 1's
+// The products with dt c1/h^2, dt c2/h^4 and dt cN/h^2 use each coefficient's
+// full 53-bit mantissa (fx.cuh); the terms are aligned to the largest one's
+// unit and added exactly.  The cube u^3 is formed per point from the level's
+// integers by two exact 128-bit products, each truncated to 2^-56 of its bound,
+// and its Laplacian is again an exact integer sum.  The result is then scaled by gamma_n/dt (Step 1's
 // alpha-scaling, again from the FP64 factor's full mantissa) and rounded once
 // to FP32, the input of the complex64 time transform.  Per CTA, the partial
 // sum of r^2 feeds the convergence check.
@@ -90,7 +93,7 @@ __device__ __forceinline__ void fx_pow2_pair(int k, float& f1, float& f2) {
 // contiguous units [c U / C, (c+1) U / C), which may span the end of one tile's
 // levels and the start of the next tile's: every CTA gets the same number of
 // levels to within one, whatever the tile count.
-template <int DIM, bool HALF, bool ROUT>
+template <int DIM, bool HALF, bool ROUT, bool CUBE>
 __global__ void __launch_bounds__(kFxThreads, FxBlocks<HALF>::value)
     k_residual_fx(GeoFX g, const double* __restrict__ U, const double* __restrict__ u0,
                   const double* __restrict__ gdt, const float* __restrict__ igamf, float* __restrict__ s_out,
@@ -106,12 +109,15 @@ __global__ void __launch_bounds__(kFxThreads, FxBlocks<HALF>::value)
     constexpr int LX = TX + 2, LY = TY + (DIM == 2 ? 2 : 0);
     constexpr int NST = (SX * SY + NTHR - 1) / NTHR, NLP = (LX * LY + NTHR - 1) / NTHR;
     constexpr int L2GROW = DIM == 2 ? 3 : 2;     // |Lap L1| <= 8 max|L1| (2-D), 4 max|L1| (1-D)
+    static_assert(!(CUBE && HALF), "the cubic term comes with theta = 1");
     __shared__ int64_t sfx[2][SY * SX];
     __shared__ int64_t sL[2][LY * LX];
+    __shared__ int64_t scub[CUBE ? SY * SX : 1];   // u^3 in 2^(3E-56) (read before the level's second barrier)
+    __shared__ int sbN[NW];
     __shared__ int smax[2][NW];
     __shared__ int smaxp[NW];
     __shared__ int sbL[NW], sbD[NW];
-    __shared__ double red[NW];
+    __shared__ double red[NW], red2[NW];
 
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     const int tx = tid % (DIM == 2 ? TX : TX / PPT), ty = tid / (DIM == 2 ? TX : TX / PPT);
@@ -125,7 +131,7 @@ __global__ void __launch_bounds__(kFxThreads, FxBlocks<HALF>::value)
     const long long units = (long long)tiles_x * (DIM == 2 ? (g.ny + TY - 1) / TY : 1) * g.nt;
     const long long ub = units * blockIdx.x / gridDim.x, ue = units * (blockIdx.x + 1) / gridDim.x;
     float acc = 0.f;
-    double accd = 0.0;
+    double accd = 0.0, accu2 = 0.0;
     for (long long u = ub; u < ue;) {
         // one segment: levels n0 .. n1-1 of one tile
         const int tile = (int)(u / g.nt);
@@ -224,7 +230,15 @@ __global__ void __launch_bounds__(kFxThreads, FxBlocks<HALF>::value)
             const int E = max(fx_tile_exp(fmax), -958);
 #pragma unroll
             for (int a = 0; a < NST; ++a)
-                if (tid + a * NTHR < SX * SY) sfx[b][tid + a * NTHR] = fx_from_f64_fast(rhi[a], rlo[a], E);
+                if (tid + a * NTHR < SX * SY) {
+                    const int64_t v = fx_from_f64_fast(rhi[a], rlo[a], E);
+                    sfx[b][tid + a * NTHR] = v;
+                    if constexpr (CUBE) {
+                        // |v| < 2^56: P = floor(v^2 / 2^56) < 2^56 in 2^(2E-56), C = floor(v P / 2^56) in 2^(3E-56)
+                        const int64_t av = v < 0 ? -v : v;
+                        scub[tid + a * NTHR] = fx_mul_shr(v, fx_mul_shr(av, av, 56), 56);
+                    }
+                }
             if (n + 1 < n1) load(n + 1);
             // level-uniform unit: both levels in 2^(Em-56)
             const int Em = max(E, Ep);
@@ -241,14 +255,22 @@ __global__ void __launch_bounds__(kFxThreads, FxBlocks<HALF>::value)
                     sL[b][tid + a * NTHR] = v;
                     orl |= (uint64_t)(v ^ (v >> 63));
                 }
+            int64_t LC[PPT];   // Lap(u^3) at this thread's points (unscaled stencil, 2^(3E-56))
+            uint64_t orn = 0;
             if (!(HALF && n < n0)) {
 #pragma unroll
-                for (int q = 0; q < PPT; ++q)
+                for (int q = 0; q < PPT; ++q) {
+                    LC[q] = 0;
                     if (inside[q]) {
                         const int64_t un = sfx[b][cu[q]];
                         const int64_t D = same ? up[q] - un : fx_sar(up[q], dEp) - fx_sar(un, dE);
                         ord |= (uint64_t)(D ^ (D >> 63));
+                        if constexpr (CUBE) {
+                            LC[q] = fx_lap<DIM>(scub, cu[q], SX);
+                            orn |= (uint64_t)(LC[q] ^ (LC[q] >> 63));
+                        }
                     }
+                }
             }
             int bl = orl ? 65 - fx_clz64(orl) : 0, bd = ord ? 65 - fx_clz64(ord) : 0;
             bl = (int)__reduce_max_sync(0xffffffffu, (unsigned)bl);
@@ -256,6 +278,10 @@ __global__ void __launch_bounds__(kFxThreads, FxBlocks<HALF>::value)
             if (lane == 0) {
                 sbL[warp] = bl;
                 sbD[warp] = bd;
+            }
+            if constexpr (CUBE) {
+                const int bn = (int)__reduce_max_sync(0xffffffffu, (unsigned)(orn ? 65 - fx_clz64(orn) : 0));
+                if (lane == 0) sbN[warp] = bn;
             }
             if (n + 1 < n1) {
                 const int f = expmax();
@@ -280,10 +306,16 @@ __global__ void __launch_bounds__(kFxThreads, FxBlocks<HALF>::value)
             // S = emax - 60 (>= 0): every term is then resolved to 2^-60 of the largest one.
             // bits of the Laplacian sums as used (a shift to the unit Em only lowers them)
             const int bL = HALF ? max(bL1, bL1p) + 1 : bL1;
-            const int e2 = bL + L2GROW + g.bM2, e1 = bL + g.bM1, eD = bD - g.Q;
+            // (coefficient i enters as M_i 2^(Q - dQ_i); the cube's unit is 2^(3E-56) against 2^(Em-56))
+            const int e2 = bL + L2GROW + g.bM2 - g.dQ2, e1 = bL + g.bM1 - g.dQ1, eD = bD - g.Q;
             int emax = max(e2, eD);
             if (g.lin1) emax = max(emax, e1);
+            if constexpr (CUBE) {
+                const int bN = (int)__reduce_max_sync(0xffffffffu, (unsigned)sbN[lane & (NW - 1)]);
+                if (bN > 0) emax = max(emax, bN + g.bMN - g.dQN + 3 * E - Em);
+            }
             const int S = max(emax - 60, 0);
+            const int S2 = S + g.dQ2, S1 = S + g.dQ1, SN = S + g.dQN - (3 * E - Em);
             const int X = g.Q + Em - 56 + S;
             const int kD = -g.Q - S;                              // D 2^-Q in units 2^S
             float Gh = 0.f, Gl = 0.f, f1 = 0.f, f2 = 0.f, ig = 0.f;
@@ -294,6 +326,7 @@ __global__ void __launch_bounds__(kFxThreads, FxBlocks<HALF>::value)
                 fx_pow2_pair(X + gex - 1046, f1, f2);
                 ig = __ldg(igamf + n);
             }
+            float lu2 = 0.f;
 #pragma unroll
             for (int q = 0; q < PPT; ++q) {
                 if (!inside[q]) continue;
@@ -314,10 +347,19 @@ __global__ void __launch_bounds__(kFxThreads, FxBlocks<HALF>::value)
                     L2s += same ? L2p[q] : fx_sar(L2p[q], dEp);
                 }
                 int64_t R = kD >= 0 ? (D << kD) : fx_sar(D, (uint32_t)(-kD));
-                R -= fx_mul_shr(L2s, g.M2, S);
+                R -= fx_mul_shr(L2s, g.M2, S2);
                 if (g.lin1) {
-                    const int64_t t1 = fx_mul_shr(L1s, g.M1, S);
+                    const int64_t t1 = fx_mul_shr(L1s, g.M1, S1);
                     R = g.neg1 ? R + t1 : R - t1;
+                }
+                if constexpr (CUBE) {
+                    // SN < 0 only when |LC MN| < 2^(60 + SN): the low word is then the exact product
+                    const int64_t tN = SN >= 0 ? fx_mul_shr(LC[q], g.MN, SN)
+                                               : (int64_t)((uint64_t)LC[q] * (uint64_t)g.MN) << (uint32_t)(-SN);
+                    R = g.negN ? R + tN : R - tN;
+                    // sum u^2 for the mean Jacobian 3 mean(u^2): u = un 2^(E-56)
+                    const float vf = fx_to_f32_pair(un, 1.f, 0.f, 1.f, 1.f);
+                    lu2 = fmaf(vf, vf, lu2);
                 }
                 const size_t o = (size_t)n * g.nspace + po[q];
                 if constexpr (ROUT) {
@@ -336,33 +378,46 @@ __global__ void __launch_bounds__(kFxThreads, FxBlocks<HALF>::value)
                     L2p[q] = L2o;
                 }
             }
+            if constexpr (CUBE) accu2 = fma((double)lu2, ldexp(1.0, 2 * E - 112), accu2);
             Ep = E;
             bL1p = bL1;
         }
     }
-    // deterministic block reduction of sum r^2 (sum u^2 is not needed for the linear equations)
+    // deterministic block reduction of sum r^2 and (Cahn-Hilliard) sum u^2
     double a = warp_sum(ROUT ? accd : (double)acc);
-    if (lane == 0) red[warp] = a;
+    const double a2 = CUBE ? warp_sum(accu2) : 0.0;
+    if (lane == 0) {
+        red[warp] = a;
+        red2[warp] = a2;
+    }
     __syncthreads();
     if (tid == 0) {
-        double A = 0.0;
-        for (int w = 0; w < NW; ++w) A += red[w];
+        double A = 0.0, B = 0.0;
+        for (int w = 0; w < NW; ++w) {
+            A += red[w];
+            B += red2[w];
+        }
         partials[2 * blockIdx.x] = A;
-        partials[2 * blockIdx.x + 1] = 0.0;
+        partials[2 * blockIdx.x + 1] = B;
     }
 }
 
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
+// Linear equations with theta = 1 or 1/2, and Cahn-Hilliard (PinT-I, theta = 1),
+// on square cells or in 1-D.
 int residual_fx_supported(const Geo& g) {
-    return g.cN == 0.0 && !g.expl && (g.dim == 1 || g.ihx2 == g.ihy2) && (g.th == 1.0 || g.th == 0.5);
+    if (g.expl || !(g.dim == 1 || g.ihx2 == g.ihy2)) return 0;
+    if (g.cN != 0.0) return g.th == 1.0;
+    return g.th == 1.0 || g.th == 0.5;
 }
 
-// Coefficients in one binary frame 2^Q: M_i = round(|c_i| 2^-Q) < 2^53, where
-// c1 = theta dt c1/h^2 and c2 = theta dt c2/h^4 (theta = 1/2 is exact).  The
-// products L M are exact; the kernel picks per tile and level how many low
-// bits of them to drop.
+// Each coefficient c_i = theta dt c1/h^2, theta dt c2/h^4, theta dt cN/h^2
+// (theta = 1/2 is exact) as its own 53-bit mantissa M_i and exponent:
+// |c_i| = M_i 2^(Q - dQ_i), Q the largest coefficient's exponent.  The products
+// L M_i are exact; the kernel picks per tile and level how many low bits of
+// them to drop.
 GeoFX make_geo_fx(const Geo& g) {
     GeoFX f{};
     f.nx = g.nx;
@@ -373,20 +428,34 @@ GeoFX make_geo_fx(const Geo& g) {
     f.nspace = g.nspace;
     f.half = g.th < 1.0 ? 1 : 0;
     f.inv_dt = g.inv_dt;
-    const double c1 = g.th * g.dt * g.c1 * g.ihx2, c2 = g.th * g.dt * g.c2 * g.ihx2 * g.ihx2;
-    const double cmax = fmax(fabs(c1), fabs(c2));
-    int e = -2000;
-    if (cmax > 0.0) frexp(cmax, &e);
-    f.Q = e - 53 > -1000 ? e - 53 : -1000;
-    auto mant = [&](double c, int64_t& M, int& bits) {
-        M = (int64_t)llrint(ldexp(fabs(c), -f.Q));
-        bits = 0;
-        for (int64_t t = M; t; t >>= 1) ++bits;
-    };
-    mant(c1, f.M1, f.bM1);
-    mant(c2, f.M2, f.bM2);
+    const double c1 = g.th * g.dt * g.c1 * g.ihx2, c2 = g.th * g.dt * g.c2 * g.ihx2 * g.ihx2,
+                 cN = g.th * g.dt * g.cN * g.ihx2;
+    const double cs[3] = {c1, c2, cN};
+    int q[3];
+    int Q = -1000;
+    for (int i = 0; i < 3; ++i) {
+        int e = 0;
+        if (cs[i] != 0.0) frexp(cs[i], &e);
+        q[i] = cs[i] != 0.0 ? e - 53 : -100000;
+        if (cs[i] != 0.0 && q[i] > Q) Q = q[i];
+    }
+    f.Q = Q;
+    int64_t* M[3] = {&f.M1, &f.M2, &f.MN};
+    int* bM[3] = {&f.bM1, &f.bM2, &f.bMN};
+    int* dQ[3] = {&f.dQ1, &f.dQ2, &f.dQN};
+    for (int i = 0; i < 3; ++i) {
+        *M[i] = 0;
+        *bM[i] = 0;
+        *dQ[i] = 0;
+        if (cs[i] == 0.0) continue;
+        *dQ[i] = Q - q[i];
+        *M[i] = (int64_t)llrint(ldexp(fabs(cs[i]), -q[i]));   // exact: the 53-bit mantissa
+        for (int64_t t = *M[i]; t; t >>= 1) ++*bM[i];
+    }
     f.lin1 = c1 != 0.0 ? 1 : 0;
     f.neg1 = c1 < 0.0 ? 1 : 0;
+    f.cube = cN != 0.0 ? 1 : 0;
+    f.negN = cN < 0.0 ? 1 : 0;
     return f;
 }
 
@@ -426,15 +495,19 @@ cudaError_t launch_residual_fx(const GeoFX& f, const Geo& g, const double* U, co
     int gx, gy, gz, chunk;
     residual_fx_grid(g, gx, gy, gz, chunk);
     const dim3 grid(gx), blk(kFxThreads);
-#define PINT_RFX(D, H, R) \
-    return launch_pdl(k_residual_fx<D, H, R>, grid, blk, 0, st, f, U, u0, gdt, igamf, s, r_out, partials, ctl)
+#define PINT_RFX(D, H, R, C) \
+    return launch_pdl(k_residual_fx<D, H, R, C>, grid, blk, 0, st, f, U, u0, gdt, igamf, s, r_out, partials, ctl)
     const bool rout = rout_mode != 0;
+    if (f.cube) {
+        if (g.dim == 2) { if (rout) PINT_RFX(2, false, true, true); else PINT_RFX(2, false, false, true); }
+        else { if (rout) PINT_RFX(1, false, true, true); else PINT_RFX(1, false, false, true); }
+    }
     if (g.dim == 2) {
-        if (rout) { if (f.half) PINT_RFX(2, true, true); else PINT_RFX(2, false, true); }
-        else { if (f.half) PINT_RFX(2, true, false); else PINT_RFX(2, false, false); }
+        if (rout) { if (f.half) PINT_RFX(2, true, true, false); else PINT_RFX(2, false, true, false); }
+        else { if (f.half) PINT_RFX(2, true, false, false); else PINT_RFX(2, false, false, false); }
     } else {
-        if (rout) { if (f.half) PINT_RFX(1, true, true); else PINT_RFX(1, false, true); }
-        else { if (f.half) PINT_RFX(1, true, false); else PINT_RFX(1, false, false); }
+        if (rout) { if (f.half) PINT_RFX(1, true, true, false); else PINT_RFX(1, false, true, false); }
+        else { if (f.half) PINT_RFX(1, true, false, false); else PINT_RFX(1, false, false, false); }
     }
 #undef PINT_RFX
 }

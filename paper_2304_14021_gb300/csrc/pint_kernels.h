@@ -58,12 +58,15 @@ struct GeoFX {
     int half;       // theta = 1/2: A(u_{n-1}) enters too
     int lin1;       // c1 != 0 (the Laplacian term is present)
     int neg1;       // c1 < 0 (signed beta^2)
-    int Q;          // common binary frame of the coefficients
-    int bM1, bM2;   // significant bits of M1, M2
-    int64_t M1, M2; // round(|c_i| 2^-Q) < 2^53
+    int cube;       // cN != 0 (Cahn-Hilliard: the Lap(u^3) term)
+    int negN;       // cN < 0
+    int Q;          // exponent of the largest coefficient's frame
+    int dQ1, dQ2, dQN;       // |c_i| = M_i 2^(Q - dQ_i)
+    int bM1, bM2, bMN;       // significant bits of M_i (53, or 0 for an absent term)
+    int64_t M1, M2, MN;      // the coefficients' 53-bit mantissas
     double inv_dt;
 };
-// Linear equations (no u^3 term), theta 1 or 1/2, square cells or 1-D.
+// Linear equations (theta 1 or 1/2) and Cahn-Hilliard PinT-I (theta 1), square cells or 1-D.
 int residual_fx_supported(const Geo& g);
 GeoFX make_geo_fx(const Geo& g);
 int residual_fx_grid(const Geo& g, int& gx, int& gy, int& gz, int& chunk);

@@ -49,10 +49,11 @@ int main(int argc, char** argv) {
             int64_t L = (int64_t)(rng() >> (64 - bl));
             if (rng() & 1) L = -L;
             const int64_t M = (int64_t)(rng() >> (64 - bm));
-            const int S = (int)(rng() % 64);
+            const int S = (int)(rng() % 136);
             const __int128 p = (__int128)L * M;
-            if ((p >> S) > (__int128)INT64_MAX || (p >> S) < (__int128)INT64_MIN) continue;
-            if ((__int128)fx_mul_shr(L, M, S) != (p >> S)) ++bad;
+            if (S < 127 && ((p >> S) > (__int128)INT64_MAX || (p >> S) < (__int128)INT64_MIN)) continue;
+            const __int128 want = S >= 127 ? (p < 0 ? -1 : 0) : (p >> S);
+            if ((__int128)fx_mul_shr(L, M, S) != want) ++bad;
         }
         printf("mul_shr %ld %ld 0\n", n, bad);
     }

@@ -1,5 +1,6 @@
-"""The block fixed-point residual of PINT_MIXED (integer pipes) against the
-oracle's FP64 residual (Eq. 2.6 with alpha = 0) and the FP64 residual kernel,
+"""The block fixed-point residual of PINT_MIXED (integer pipes; linear equations
+and the Cahn-Hilliard u^3 term) against the oracle's FP64 residual (Eq. 2.6 /
+Eq. 4.8 with alpha = 0) and the FP64 residual kernel,
 element by element, through the C ABI.
 
 On a random iterate the residual is of the size of its terms, and both GPU
@@ -55,6 +56,10 @@ CASES = [
     dict(equation="linear_ch", dim=2, nx=64, ny=64, bc="neumann", nt=8, T=0.01, eps=0.05, beta=0.5, theta=0.5),
     dict(equation="biharmonic", dim=1, nx=1000, bc="neumann", nt=4, T=1e-6, theta=0.5),                 # CN, 1-D
     dict(equation="linear_ch", dim=1, nx=5, bc="ss", nt=2, T=1e-3, eps=0.1, beta=0.3),                  # tiny
+    dict(equation="linear_ch", dim=1, nx=32, bc="neumann", nt=8, T=1e-3, eps=0.01, beta=0.57),          # c1 > c2
+    dict(equation="cahn_hilliard", dim=2, nx=64, ny=64, bc="neumann", nt=8, T=8e-4, eps=0.05),          # u^3 term
+    dict(equation="cahn_hilliard", dim=1, nx=130, bc="neumann", nt=4, T=1e-4, eps=0.05),                # ragged
+    dict(equation="cahn_hilliard", dim=2, nx=40, ny=40, bc="ss", nt=4, T=1e-4, eps=0.1),                # odd reflections
 ]
 
 
@@ -68,6 +73,8 @@ def test_fx_residual_matches_oracle_and_fp64_kernel_on_random_iterates(case):
     out = {}
     for prec in ("mixed", "fp64"):
         with pint.Solver(**dict(kw, precision=prec)) as s:
+            if prec == "mixed":
+                s.set_fx_residual(True)   # raises where the fixed-point form is not supported
             r = torch.empty(p.nt, p.nspace, dtype=torch.float64, device="cuda")
             rel = s.residual(dev(u0), dev(U), r)
             out[prec] = (host(r), rel)
@@ -78,7 +85,7 @@ def test_fx_residual_matches_oracle_and_fp64_kernel_on_random_iterates(case):
     assert np.max(np.abs(out["mixed"][0] - out["fp64"][0])) <= 1e-13 * scale
 
 
-@pytest.mark.parametrize("case", [0, 2, 3, 4, 6, 7])
+@pytest.mark.parametrize("case", [0, 2, 3, 4, 6, 7, 9])
 def test_fx_residual_at_the_sequential_solution_is_fp64_rounding(case):
     # At the sequential solution r = b - K(U) vanishes up to rounding.  The sums that
     # form it reach max|u| (1/dt + ||A||_inf) (the stencil terms, before they cancel):
@@ -94,6 +101,8 @@ def test_fx_residual_at_the_sequential_solution_is_fp64_rounding(case):
     errs = {}
     for prec in ("mixed", "fp64"):
         with pint.Solver(**dict(kw, precision=prec)) as s:
+            if prec == "mixed":
+                s.set_fx_residual(True)
             r = torch.empty(p.nt, p.nspace, dtype=torch.float64, device="cuda")
             s.residual(dev(u0), dev(U), r)
             errs[prec] = np.max(np.abs(host(r) - ref)) / scale
@@ -165,11 +174,16 @@ def test_mixed_solve_same_with_fx_and_fp64_residual(case):
 
 
 def test_fx_residual_option_rejected_where_unsupported():
-    # Cahn-Hilliard (the u^3 term) and FP64 handles keep the FP64 residual kernel
+    # Eyre's splitting (its explicit Laplacian acts on u_{n-1}), cells that are not square
+    # (no integer stencil) and FP64 handles keep the FP64 residual kernel
+    for kw in (dict(equation="cahn_hilliard_eyre", dim=2, nx=16, ny=16, bc="neumann", eps=0.05, nt=8, T=8e-4),
+               dict(equation="linear_ch", dim=2, nx=16, ny=8, bc="neumann", eps=0.05, beta=0.5, nt=8, T=1e-3)):
+        with pint.Solver(**full(kw)) as s:
+            with pytest.raises(pint.PintError):
+                s.set_fx_residual(True)
     with pint.Solver(**full(dict(equation="cahn_hilliard", dim=2, nx=16, ny=16, bc="neumann", eps=0.05,
                                  nt=8, T=8e-4))) as s:
-        with pytest.raises(pint.PintError):
-            s.set_fx_residual(True)
+        s.set_fx_residual(True)   # the u^3 term is supported
     with pint.Solver(**full(dict(precision="fp64"))) as s:
         with pytest.raises(pint.PintError):
             s.set_fx_residual(True)
