@@ -137,6 +137,8 @@ typedef struct {
                                  PINT_FP64, where FP32 inner solves cannot be refined */
     int    time_gemm;         /* time transforms on the tensor cores (PINT_OPT_TIME_GEMM): bit 0 Step 1,
                                  bit 1 Step 3, in the last window solved */
+    int    fused_spatial;     /* 1: Step 2 ran as one fused 2-D kernel per frequency slice */
+    int    tune_cached;       /* 1: the autotuner took this handle's choices from its table */
 } pint_stats;
 
 typedef struct pint_handle pint_handle;
@@ -231,10 +233,10 @@ int pint_profile_read(pint_handle* h, pint_profile* out, int reset);
  *    Enabling it builds the tables of the shorter lengths (allocates device
  *    memory); it runs the host-launched loop. */
 #define PINT_OPT_ADAPTIVE_WINDOWS 2
-/*  PINT_OPT_FUSED_SPATIAL (default 1): on square 2-D grids of 64 or 128 cells per
- *    side with Neumann conditions, solve each frequency slice in one kernel (a
- *    thread-block cluster holds the slice in shared memory) instead of three
- *    passes over the spectrum. */
+/*  PINT_OPT_FUSED_SPATIAL: on square 2-D grids of 64 or 128 cells per side with
+ *    Neumann conditions, solve each frequency slice in one kernel (a thread-block
+ *    cluster holds the slice in shared memory) instead of three passes over the
+ *    spectrum.  Not set: chosen by the autotuner (pint_tune_lookup); 0 or 1: fixed. */
 #define PINT_OPT_FUSED_SPATIAL 3
 /*  PINT_OPT_KRYLOV (default 0 = off): for the linear equations, wrap the
  *    preconditioner in restarted flexible GMRES(value), 1 <= value <= 30:
@@ -280,6 +282,36 @@ int pint_profile_read(pint_handle* h, pint_profile* out, int reset);
  *    Errors: PINT_EINVAL (value out of range, or 1 where unsupported). */
 #define PINT_OPT_TIME_GEMM 8
 int pint_set_option(pint_handle* h, int option, long long value);
+
+/* The project autotuner.  Before a handle's first pint_solve, every Steps 1-3
+ * kernel choice that the caller has left open (PINT_OPT_TIME_GEMM = -1, and
+ * PINT_OPT_FUSED_SPATIAL not set) is measured on the handle's own buffers (CUDA
+ * events; each candidate two warm-up and five timed launches) and the fastest
+ * kept.  The choices of a shape go into a process-wide table keyed by
+ * (equation, dim, nx, ny, nt, precision as run, bc, theta < 1); a later handle of
+ * the same shape takes them from the table without measuring
+ * (pint_stats.tune_cached).  If the environment variable PINT_TUNE_FILE names a
+ * file, the table is loaded from it at the first lookup and every new entry is
+ * appended to it.  The table is mutex-protected. */
+typedef struct {
+    int   time_fwd_gemm;    /* 1: Step 1 as tensor-core DFT products, 0: FFT */
+    int   time_inv_gemm;    /* 1: Step 3 as tensor-core DFT products, 0: FFT */
+    int   fused_spatial;    /* 1: Step 2 as one fused 2-D kernel, 0: three passes */
+    float ms;               /* measured time of the chosen kernels for one application */
+} pint_tune_entry;
+/* 1 and *out filled if the table holds p's shape (p as passed to pint_create; its
+ * precision is mapped to the one the solve runs in), 0 if not, PINT_EINVAL for an
+ * invalid problem. */
+int pint_tune_lookup(const pint_problem* p, pint_tune_entry* out);
+/* Merge the entries of a table file (format: lines "pint-tune equation dim nx ny
+ * nt precision bc half fwd inv fused ms", '#' comments).  Returns the entries
+ * read, PINT_EINVAL for a missing file or a malformed line (entries before it
+ * are kept). */
+int pint_tune_load(const char* path);
+/* Write the whole table; returns the entries written or PINT_EINVAL. */
+int pint_tune_save(const char* path);
+/* Empty the table (a file named by PINT_TUNE_FILE is not read again). */
+void pint_tune_clear(void);
 
 /* Copy the invariants recorded by the last pint_solve (PINT_OPT_LOG_INVARIANTS) into
  * mass_host[i], energy_host[i], i = 0 .. min(cap, levels) - 1, for time levels 1, 2, ... of

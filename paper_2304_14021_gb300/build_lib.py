@@ -18,7 +18,7 @@ BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libpint.so")
 
-SOURCES = ["pint_api.cu", "k_residual.cu", "k_residual_ff.cu", "k_residual_fx.cu", "k_timegemm.cu", "k_timefft.cu", "k_spatial.cu", "k_dst.cu", "pint_static.cu",
+SOURCES = ["pint_api.cu", "k_residual.cu", "k_residual_ff.cu", "k_residual_fx.cu", "k_timegemm.cu", "k_timefft.cu", "k_spatial.cu", "k_dst.cu", "tune_cache.cu", "pint_static.cu",
            "k_krylov.cu", "k_jacobian.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

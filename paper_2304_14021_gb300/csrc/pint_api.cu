@@ -195,6 +195,8 @@ struct pint_handle {
     // CUDA-graph execution of the iteration loop (one while-loop graph per window)
     int use_graphs = 1;
     int fuse2d = 1;                          // fused 2-D spatial kernel where supported
+    int fuse2d_user = 0;                     // fuse2d set by the caller (not left to the autotuner)
+    int tune_cached = 0;                     // the autotuner's choices came from its table
     int capturing = 0;                       // set while the loop body is being captured
     unsigned long long gcond = 0;            // cudaGraphConditionalHandle of the graph being captured
     cudaStream_t capst = nullptr;            // capture stream
@@ -1209,6 +1211,7 @@ int pint_set_option(pint_handle* h, int option, long long value) {
         case PINT_OPT_FUSED_SPATIAL:
             if (value != 0 && value != 1) return PINT_EINVAL;
             h->fuse2d = (int)value;
+            h->fuse2d_user = 1;
             for (auto& sl : h->gslot)   // captured loops hold the old kernel choice
                 if (sl.exec) { cudaGraphExecDestroy(sl.exec); sl.exec = nullptr; }
             return PINT_OK;
@@ -1446,23 +1449,49 @@ static int gmres_window(pint_handle* h, double* U, const double* u0w) {
 // tensor-core DFT products for Step 1 and (PINT_MIXED) Step 3: each variant runs
 // twice to warm up and five times timed with CUDA events on the handle's
 // stream; the faster one is kept for the handle's life.
-static int tune_time_gemm(pint_handle* h) {
+// Key of the autotuner table: the shape and the kernels' variant (precision as run).
+static TuneKey tune_key(const pint_problem& p, const Geo& g) {
+    TuneKey k{};
+    k.equation = p.equation;
+    k.dim = p.dim;
+    k.nx = g.nx;
+    k.ny = g.ny;
+    k.nt = p.nt;
+    k.precision = p.precision;
+    k.bc = p.bc;
+    k.half = p.theta < 1.0 ? 1 : 0;
+    return k;
+}
+
+// The project autotuner, run before a handle's first solve: for each transform
+// choice left to it (PINT_OPT_TIME_GEMM = -1: Step 1 and Step 3 as FFTs or as
+// tensor-core DFT products; PINT_OPT_FUSED_SPATIAL not set by the caller: Step 2
+// as one fused 2-D kernel or three passes) it times every candidate on this
+// handle's buffers with CUDA events (two warm-up and five timed launches) and
+// keeps the fastest.  The result goes into the process-wide table keyed by the
+// problem's shape, so later handles of the same shape take it without measuring.
+static int autotune(pint_handle* h) {
     h->tgemm_tuned = 1;
-    if (!h->wgemm || !time_gemm_supported(h->p.nt, h->geo.nspace)) return PINT_OK;
+    const bool a_gemm = h->wgemm && time_gemm_supported(h->p.nt, h->geo.nspace);
+    const bool a_fuse = h->geo.dim == 2 && slice2d_supported(h->geo, h->fft_x, h->fft_y, h->p.precision != PINT_FP64);
+    const bool t_gemm = a_gemm && h->tgemm_mode == -1, t_fuse = a_fuse && !h->fuse2d_user;
+    if (!t_gemm && !t_fuse) return PINT_OK;
+    const TuneKey key = tune_key(h->p, h->geo);
+    TuneVal v{};
+    if (tune_lookup(key, &v)) {
+        if (t_gemm) {
+            h->gemm_fwd = v.gemm_fwd;
+            h->gemm_inv = v.gemm_inv;
+        }
+        if (t_fuse) h->fuse2d = v.fused;
+        h->tune_cached = 1;
+        return PINT_OK;
+    }
     const Geo& g = h->geo;
     const size_t dof = (size_t)g.nt * g.nspace;
-    double* tU = nullptr;
-    if (cudaMallocAsync((void**)&tU, dof * sizeof(double), h->st) != cudaSuccess) {
-        cudaGetLastError();
-        return PINT_OK;   // keep the FFT
-    }
-    PINT_CK(cudaMemsetAsync(tU, 0, dof * sizeof(double), h->st));
     cudaEvent_t e0, e1;
     PINT_CK(cudaEventCreate(&e0));
     PINT_CK(cudaEventCreate(&e1));
-    const Tabs<float>& tb = tabs_of<float>(h);
-    float* s = reinterpret_cast<float*>(h->s);
-    float2* S = reinterpret_cast<float2*>(h->S);
     auto timeit = [&](auto fn) -> float {
         launch_set_running(h->ctl, 0.0, h->st);
         fn();
@@ -1473,22 +1502,62 @@ static int tune_time_gemm(pint_handle* h) {
         cudaEventSynchronize(e1);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        return cudaGetLastError() == cudaSuccess ? ms : 1e30f;
+        return cudaGetLastError() == cudaSuccess ? ms / 5.f : 1e30f;
     };
-    const float ff = timeit([&] { launch_time_fwd<float>(g.nt, g.nspace, s, S, tb.twt, h->ctl, h->st); });
-    const float gf = timeit([&] { launch_time_gemm(0, g.nt, g.nspace, s, S, h->wgemm, nullptr, h->ctl, nullptr, h->st); });
-    h->gemm_fwd = gf < ff ? 1 : 0;
-    if (h->p.precision == PINT_MIXED) {
-        const float fi = timeit([&] {
-            launch_time_inv<float>(g.nt, g.nspace, S, tb.twt, h->ginv, tU, 1, h->ctl, nullptr, h->st, h->s, nullptr);
-        });
-        const float gi = timeit([&] { launch_time_gemm(1, g.nt, g.nspace, S, tU, h->wgemm, h->ginv, h->ctl, nullptr, h->st); });
-        h->gemm_inv = gi < fi ? 1 : 0;
+    float best = 0.f;
+    v.gemm_fwd = h->gemm_fwd;
+    v.gemm_inv = h->gemm_inv;
+    v.fused = h->fuse2d;
+    if (t_gemm) {
+        double* tU = nullptr;
+        if (cudaMallocAsync((void**)&tU, dof * sizeof(double), h->st) != cudaSuccess) {
+            cudaGetLastError();
+            tU = nullptr;   // keep the FFT
+        }
+        if (tU) {
+            PINT_CK(cudaMemsetAsync(tU, 0, dof * sizeof(double), h->st));
+            const Tabs<float>& tb = tabs_of<float>(h);
+            float* s = reinterpret_cast<float*>(h->s);
+            float2* S = reinterpret_cast<float2*>(h->S);
+            const float ff = timeit([&] { launch_time_fwd<float>(g.nt, g.nspace, s, S, tb.twt, h->ctl, h->st); });
+            const float gf = timeit([&] { launch_time_gemm(0, g.nt, g.nspace, s, S, h->wgemm, nullptr, h->ctl, nullptr, h->st); });
+            v.gemm_fwd = gf < ff ? 1 : 0;
+            best += gf < ff ? gf : ff;
+            if (h->p.precision == PINT_MIXED) {
+                const float fi = timeit([&] {
+                    launch_time_inv<float>(g.nt, g.nspace, S, tb.twt, h->ginv, tU, 1, h->ctl, nullptr, h->st, h->s, nullptr);
+                });
+                const float gi = timeit([&] { launch_time_gemm(1, g.nt, g.nspace, S, tU, h->wgemm, h->ginv, h->ctl, nullptr, h->st); });
+                v.gemm_inv = gi < fi ? 1 : 0;
+                best += gi < fi ? gi : fi;
+            }
+            cudaFreeAsync(tU, h->st);
+        }
+        h->gemm_fwd = v.gemm_fwd;
+        h->gemm_inv = v.gemm_inv;
+    }
+    if (t_fuse) {
+        // Step 2 on a zeroed spectrum, fused and in three passes
+        const bool f32 = f32_transforms(&h->p);
+        PINT_CK(cudaMemsetAsync(h->S, 0, (size_t)(g.nt / 2 + 1) * g.nspace * 2 * (f32 ? 4 : 8), h->st));
+        auto step2 = [&] {
+            if (f32) Impl<float>::spatial(h, reinterpret_cast<float2*>(h->S), tabs_of<float>(h));
+            else Impl<double>::spatial(h, reinterpret_cast<double2*>(h->S), tabs_of<double>(h));
+        };
+        h->fuse2d = 1;
+        const float t1 = timeit(step2);
+        h->fuse2d = 0;
+        const float t3 = timeit(step2);
+        v.fused = t1 <= t3 ? 1 : 0;
+        h->fuse2d = v.fused;
+        best += t1 <= t3 ? t1 : t3;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFreeAsync(tU, h->st);
     PINT_CK(cudaStreamSynchronize(h->st));
+    v.ms = best;
+    // only a measurement of every choice this shape has is a table entry (none fixed by the caller)
+    if (t_gemm == a_gemm && t_fuse == a_fuse) tune_store(key, v);
     return PINT_OK;
 }
 
@@ -1509,7 +1578,7 @@ static int solve_impl(pint_handle* h, const double* u0_dev, double* U_dev, pint_
     int rc = PINT_OK;
     bool converted = false;   // float-float result already converted to U_dev
     activate_level(h, 0);
-    if (!h->tgemm_tuned && h->tgemm_mode == -1 && (rc = tune_time_gemm(h)) != PINT_OK) return rc;
+    if (!h->tgemm_tuned && (rc = autotune(h)) != PINT_OK) return rc;
     // Cahn-Hilliard never starts from the zero iterate: its scalar Jacobian
     // 3 mean(u^2) would be 0 in the first preconditioner, far from the state's,
     // and the iteration can diverge; such windows start from u0 instead.
@@ -1615,6 +1684,8 @@ static int solve_impl(pint_handle* h, const double* u0_dev, double* U_dev, pint_
         S.update_norm = p.tol_update > 0.0 ? c.dnorm : 0.0;
         S.precision = p.precision;
         S.time_gemm = (use_gemm_fwd(h) ? 1 : 0) | (use_gemm_inv(h) ? 2 : 0);
+        S.fused_spatial = fused_spatial(h) ? 1 : 0;
+        S.tune_cached = h->tune_cached;
         S.jbar = h->coef.ch ? c.jbar : 0.0;
         for (int i = 0; i <= k && i < PINT_HIST_MAX; ++i) S.hist[i] = c.hist[i];
         S.contraction = k >= 2 ? pow(c.hist[k] / c.hist[1], 1.0 / (k - 1)) : (k == 1 ? c.hist[1] / c.hist[0] : 0.0);
@@ -1743,5 +1814,36 @@ int pint_precond_apply(pint_handle* h, double jbar, const double* r_dev, double*
     PINT_CK(cudaStreamSynchronize(h->st));
     return PINT_OK;
 }
+
+int pint_tune_lookup(const pint_problem* p, pint_tune_entry* out) {
+    if (!p || validate(p) != PINT_OK) return PINT_EINVAL;
+    pint_problem q = *p;
+    q.precision = effective_precision(p);
+    Geo g;
+    geometry_of(&q, g);
+    TuneVal v{};
+    if (!tune_lookup(tune_key(q, g), &v)) return 0;
+    if (out) {
+        out->time_fwd_gemm = v.gemm_fwd;
+        out->time_inv_gemm = v.gemm_inv;
+        out->fused_spatial = v.fused;
+        out->ms = v.ms;
+    }
+    return 1;
+}
+
+int pint_tune_load(const char* path) {
+    if (!path) return PINT_EINVAL;
+    const int n = tune_load(path);
+    return n < 0 ? PINT_EINVAL : n;
+}
+
+int pint_tune_save(const char* path) {
+    if (!path) return PINT_EINVAL;
+    const int n = tune_save(path);
+    return n < 0 ? PINT_EINVAL : n;
+}
+
+void pint_tune_clear(void) { tune_clear(); }
 
 }  // extern "C"

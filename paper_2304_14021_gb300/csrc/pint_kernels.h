@@ -242,6 +242,21 @@ void launch_zero_start(c_t<T>* S, const double* u0, double inv_dt, int nspace, i
 int slice2d_supported(const Geo& g, int fft_x, int fft_y, int f32);
 // Sine path of a simply supported axis of n points: n + 1 a power of two, 3 <= n <= 4095.
 int dst_axis_supported(int n);
+// Project autotuner table (tune_cache.cu): per problem shape, the transform
+// choices measured fastest on this device.  Thread-safe; PINT_TUNE_FILE names a
+// text file loaded at the first lookup and appended to by every new entry.
+struct TuneKey {
+    int equation, dim, nx, ny, nt, precision, bc, half;
+};
+struct TuneVal {
+    int gemm_fwd, gemm_inv, fused;   // 1: tensor-core DFT for Step 1 / Step 3; one-kernel 2-D Step 2
+    float ms;                        // measured time of the chosen combination
+};
+bool tune_lookup(const TuneKey& k, TuneVal* v);
+void tune_store(const TuneKey& k, const TuneVal& v);
+int tune_load(const char* path);   // entries read; -1: no such file; -2: malformed line (entries before it kept)
+int tune_save(const char* path);   // entries written, or -1
+void tune_clear();
 // Shared-memory attributes and resident-CTA counts of the sine-path kernels of
 // an axis of n points (axis 0: rows, 1: columns; f32: complex64 transforms).
 // Called outside any stream capture before the first launch.

@@ -37,7 +37,8 @@ class Stats(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("windows", C.c_int), ("iters_last", C.c_int),
                 ("rel_residual", C.c_double), ("contraction", C.c_double), ("jbar", C.c_double),
                 ("hist", C.c_double * HIST_MAX), ("segments", C.c_int), ("nt_min", C.c_int),
-                ("retries", C.c_int), ("update_norm", C.c_double), ("precision", C.c_int), ("time_gemm", C.c_int)]
+                ("retries", C.c_int), ("update_norm", C.c_double), ("precision", C.c_int), ("time_gemm", C.c_int),
+                ("fused_spatial", C.c_int), ("tune_cached", C.c_int)]
 
     def as_dict(self) -> dict:
         return {"status": self.status, "iters": self.iters, "windows": self.windows,
@@ -45,7 +46,13 @@ class Stats(C.Structure):
                 "contraction": self.contraction, "jbar": self.jbar, "segments": self.segments,
                 "nt_min": self.nt_min, "retries": self.retries, "update_norm": self.update_norm,
                 "precision": PRECISION_NAMES.get(self.precision, self.precision), "time_gemm": self.time_gemm,
+                "fused_spatial": self.fused_spatial, "tune_cached": self.tune_cached,
                 "hist": [self.hist[i] for i in range(min(self.iters_last + 1, HIST_MAX))]}
+
+
+class TuneEntry(C.Structure):
+    _fields_ = [("time_fwd_gemm", C.c_int), ("time_inv_gemm", C.c_int), ("fused_spatial", C.c_int),
+                ("ms", C.c_float)]
 
 
 NPHASE = 8
@@ -98,6 +105,14 @@ def lib() -> C.CDLL:
         L.pint_solve_batch.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(Stats),
                                        C.POINTER(C.c_int)]
         L.pint_solve_batch.restype = C.c_int
+        L.pint_tune_lookup.argtypes = [C.POINTER(Problem), C.POINTER(TuneEntry)]
+        L.pint_tune_lookup.restype = C.c_int
+        L.pint_tune_load.argtypes = [C.c_char_p]
+        L.pint_tune_load.restype = C.c_int
+        L.pint_tune_save.argtypes = [C.c_char_p]
+        L.pint_tune_save.restype = C.c_int
+        L.pint_tune_clear.argtypes = []
+        L.pint_tune_clear.restype = None
         L.pint_destroy.argtypes = [vp]
         L.pint_destroy.restype = None
         L.pint_strerror.argtypes = [C.c_int]
@@ -127,6 +142,37 @@ def make_problem(equation="biharmonic", dim=1, nx=64, ny=1, bc="ss", eps=1.0, be
 def footprint(**kw) -> int:
     p = make_problem(**kw)
     return int(lib().pint_footprint(C.byref(p)))
+
+
+def tune_lookup(**kw):
+    """The autotuner's entry for this problem's shape, or None (pint_tune_lookup)."""
+    p = make_problem(**kw)
+    e = TuneEntry()
+    rc = lib().pint_tune_lookup(C.byref(p), C.byref(e))
+    if rc < 0:
+        raise PintError(rc, "pint_tune_lookup")
+    if rc == 0:
+        return None
+    return {"time_fwd_gemm": e.time_fwd_gemm, "time_inv_gemm": e.time_inv_gemm, "fused_spatial": e.fused_spatial,
+            "ms": e.ms}
+
+
+def tune_load(path: str) -> int:
+    rc = lib().pint_tune_load(str(path).encode())
+    if rc < 0:
+        raise PintError(rc, "pint_tune_load")
+    return rc
+
+
+def tune_save(path: str) -> int:
+    rc = lib().pint_tune_save(str(path).encode())
+    if rc < 0:
+        raise PintError(rc, "pint_tune_save")
+    return rc
+
+
+def tune_clear() -> None:
+    lib().pint_tune_clear()
 
 
 STATIC_SCRATCH_BYTES = 278528

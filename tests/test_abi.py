@@ -38,7 +38,8 @@ def test_every_declared_symbol_is_exported(lib):
 def test_struct_sizes_match_header_layout(lib):
     # pint_problem: 5 ints (+4 pad), 3 doubles, 2 ints, 3 doubles, 3 ints (+4 pad)
     assert C.sizeof(pint.Problem) == 24 + 24 + 8 + 24 + 16 + 8
-    assert C.sizeof(pint.Stats) == 16 + 3 * 8 + 256 * 8 + 16 + 8 + 8
+    assert C.sizeof(pint.Stats) == 16 + 3 * 8 + 256 * 8 + 16 + 8 + 8 + 8
+    assert C.sizeof(pint.TuneEntry) == 16
 
 
 def test_strerror(lib):

@@ -97,6 +97,38 @@ def test_gemm_choice_by_measurement_is_reported():
     assert st["rc"] == 0 and st["time_gemm"] in (0, 1, 2, 3)
 
 
+def test_autotuner_table_reused_by_a_second_handle_of_the_shape():
+    # 64^2 x 64 has both choices open (tensor-core DFT for N_t = 64, fused 2-D slices for 64^2 Neumann):
+    # the first handle measures them and files the shape; a second handle takes them from the table,
+    # runs the same kernels and gives the same iterate bit for bit
+    pint.tune_clear()
+    kw = full(dict(nx=64, ny=64, nt=64, T=0.05, tol=1e-8))
+    p = oprob(kw)
+    u0 = synth.u0_uniform(p.nspace, -0.05, 0.05, 3)
+    out = []
+    for _ in range(2):
+        with pint.Solver(**kw) as s:
+            U = torch.zeros(p.nt, p.nspace, dtype=torch.float64, device="cuda")
+            st = s.solve(dev(u0), U, check=False)
+            out.append((U.cpu().numpy(), st))
+    (U1, st1), (U2, st2) = out
+    e = pint.tune_lookup(**kw)
+    assert e is not None and e["ms"] > 0
+    assert st1["tune_cached"] == 0 and st2["tune_cached"] == 1
+    assert st1["rc"] == 0 and st2["rc"] == 0
+    assert st2["time_gemm"] == st1["time_gemm"] == (e["time_fwd_gemm"] | 2 * e["time_inv_gemm"])
+    assert st2["fused_spatial"] == st1["fused_spatial"] == e["fused_spatial"]
+    assert np.array_equal(U1, U2)
+    assert O.rel_err(U2, O.sequential(p, u0)) < 1e-7
+    # a caller's fixed choice is kept (and not measured)
+    with pint.Solver(**kw) as s:
+        s.set_fused_spatial(not e["fused_spatial"])
+        U = torch.zeros(p.nt, p.nspace, dtype=torch.float64, device="cuda")
+        st = s.solve(dev(u0), U, check=False)
+        assert st["fused_spatial"] == (0 if e["fused_spatial"] else 1)
+    pint.tune_clear()
+
+
 def test_gemm_option_rejected_where_unsupported():
     with pint.Solver(**full(dict(nt=256, T=0.2))) as s:
         with pytest.raises(pint.PintError):
