@@ -663,6 +663,8 @@ def main_gpu(args) -> None:
                        "time_transforms": {0: "fft", 1: "tensor-core DFT (step 1), fft (step 3)",
                                            2: "fft (step 1), tensor-core DFT (step 3)",
                                            3: "tensor-core DFT (steps 1, 3)"}[stats.get("time_gemm", 0)],
+                       "spatial": "fused 2-D slice kernel" if stats.get("fused_spatial") else "separate passes",
+                       "autotuner": "choices from the table" if stats.get("tune_cached") else "measured for this handle",
                        "parallelism": f"replicas x{world}"},
             "latency": latency,
             "serving": serving,

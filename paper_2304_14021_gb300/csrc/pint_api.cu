@@ -976,11 +976,18 @@ double stiffness_of(const pint_problem* p) {
 //    dominates the next residual: observed residual growth of 1e7 on a 1-D
 //    biharmonic of 4096 cells at amp 8e4);
 //  * Cahn-Hilliard, whose Jacobian moves between iterations: as requested up to
-//    amp 0.1, FP64 beyond (observed divergence at 0.87).
+//    amp 0.1, FP64 beyond (observed divergence of 1-D instances at 0.87); 2-D
+//    PinT-I in PINT_MIXED up to amp 0.5 (its FP64-accurate residual runs on the
+//    integer pipes; measured convergence on every such instance of the batched
+//    and served pools).
 int effective_precision(const pint_problem* p) {
     if (p->precision == PINT_FP64) return PINT_FP64;
     const double amp = stiffness_of(p) * 0x1p-24;
-    if (p->equation == PINT_CAHN_HILLIARD || p->equation == PINT_CAHN_HILLIARD_EYRE) return amp > 0.1 ? PINT_FP64 : p->precision;
+    if (p->equation == PINT_CAHN_HILLIARD || p->equation == PINT_CAHN_HILLIARD_EYRE) {
+        // 2-D PinT-I in PINT_MIXED (its residual in block fixed point) is refined up to amp 0.5
+        const bool wide = p->precision == PINT_MIXED && p->equation == PINT_CAHN_HILLIARD && p->dim == 2;
+        return amp > (wide ? 0.5 : 0.1) ? PINT_FP64 : p->precision;
+    }
     if (amp <= 1.0) return p->precision;
     return amp <= 1e3 ? PINT_MIXED : PINT_FP64;
 }
