@@ -96,8 +96,8 @@ def solver_kw(wl: dict, args, precision=None) -> dict:
 KERNEL_TRAFFIC = {
     ("residual", "mixed_ff"): {"src": "k_residual_ff.cu", "src_sha256_16": "f2beb509f59f81f0",
                                "workload": "linear_ch_2d_256x256_nt128", "dram_bytes": 68294656 + 5862912},
-    ("residual", "mixed"): {"src": "k_residual_fx.cu", "src_sha256_16": "39b6eb98e300d77e",
-                            "workload": "linear_ch_2d_256x256_nt128", "dram_bytes": 67896064 + 7118592},
+    ("residual", "mixed"): {"src": "k_residual_fx.cu", "src_sha256_16": "073bf41d6c8c168b",
+                            "workload": "linear_ch_2d_256x256_nt128", "dram_bytes": 71845376 + 10023424},
 }
 
 
