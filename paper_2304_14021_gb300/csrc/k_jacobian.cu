@@ -98,23 +98,30 @@ __global__ void __launch_bounds__(256) k_apply_M(Geo g, int nk, const c_t<T>* __
 constexpr int kCDotThreads = 256;
 constexpr int kGroup = 4;   // vectors handled per launch (register accumulators)
 
-// partials[(b * ldp + i0 + i) * 2 + {0,1}] = CTA b's part of <v_i, w> = sum conj(v_i) w (FP64), i < G.
+// The vectors of the inner solve hold nk frequency slices of ns points each.  The
+// GMRES cycle runs on every slice separately (M is block-diagonal over the
+// frequencies, so each block gets its own Krylov coefficients): the vector
+// kernels below use a 2-D grid, blockIdx.y = slice k, blockIdx.x = one of nbx
+// CTAs over that slice's points, and read slice k's coefficients.
+
+// partials[((k nbx + bx) ldp + i0 + i) 2 + {0,1}] = that CTA's part of <v_i, w>_k = sum conj(v_i) w, i < G.
 template <class T, int G>
 __global__ void __launch_bounds__(kCDotThreads) k_cmulti_dot(const c_t<T>* __restrict__ w, const c_t<T>* __restrict__ V,
-                                                            size_t ld, size_t n, int ldp, int i0,
+                                                            size_t ld, size_t ns, int ldp, int i0,
                                                             double* __restrict__ partials, const int* __restrict__ skip) {
     if (skip && *skip) return;
     __shared__ double red[kCDotThreads / 32][G][2];
+    const size_t base = (size_t)blockIdx.y * ns;
     // each thread accumulates its strided elements in the vectors' own precision
     // (complex64: FP32, a few hundred terms at most); the CTA sum is taken in FP64
     T re[G], im[G];
 #pragma unroll
     for (int i = 0; i < G; ++i) re[i] = im[i] = T(0);
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        const c_t<T> we = w[e];
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < ns; e += (size_t)gridDim.x * blockDim.x) {
+        const c_t<T> we = w[base + e];
 #pragma unroll
         for (int i = 0; i < G; ++i) {
-            const c_t<T> v = V[i * ld + e];
+            const c_t<T> v = V[i * ld + base + e];
             re[i] = fma(v.x, we.x, fma(v.y, we.y, re[i]));
             im[i] = fma(v.x, we.y, fma(-v.y, we.x, im[i]));
         }
@@ -130,40 +137,45 @@ __global__ void __launch_bounds__(kCDotThreads) k_cmulti_dot(const c_t<T>* __res
         const int i = threadIdx.x;
         double a = 0.0, b = 0.0;
         for (int q = 0; q < kCDotThreads / 32; ++q) { a += red[q][i][0]; b += red[q][i][1]; }
-        partials[((size_t)blockIdx.x * ldp + i0 + i) * 2] = a;
-        partials[((size_t)blockIdx.x * ldp + i0 + i) * 2 + 1] = b;
+        const size_t cta = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+        partials[(cta * ldp + i0 + i) * 2] = a;
+        partials[(cta * ldp + i0 + i) * 2 + 1] = b;
     }
 }
 
-// out = (w + sum_i c_i v_i) * post, i < G, complex coefficients c (FP64 pairs
-// on the device), arithmetic in the vectors' precision; out = w and post = 1
-// when null; with nlim only the terms i0 + i < *nlim (the other vectors are not read).
+// out = (w + sum_i c_{k,i} v_i) * post_k on slice k, i < G (i0 + i < nlim, and
+// < *nlimd when given: the vectors beyond are not read), with c_k from slice k's
+// state (set sel) and post_k its scale (when post is set); out = w when null.
+// Arithmetic in the vectors' precision.
 template <class T, int G>
-__global__ void k_cmulti_axpy(c_t<T>* __restrict__ w, const c_t<T>* __restrict__ V, size_t ld,
-                              const double* __restrict__ c, size_t n, const int* __restrict__ skip,
-                              const int* __restrict__ nlim, int i0, c_t<T>* __restrict__ out,
-                              const double* __restrict__ post) {
+__global__ void k_cmulti_axpy(c_t<T>* __restrict__ w, const c_t<T>* __restrict__ V, size_t ld, size_t ns,
+                              const GmK* __restrict__ gk, int sel, const int* __restrict__ skip, int nlim,
+                              const int* __restrict__ nlimd, int i0, c_t<T>* __restrict__ out, int post) {
     if (skip && *skip) return;
-    const int ng = nlim ? max(0, min(G, *nlim - i0)) : G;
-    const T ps = post ? (T)*post : T(1);
+    const GmK& s = gk[blockIdx.y];
+    if (nlimd) nlim = min(nlim, *nlimd);
+    const int ng = max(0, min(G, nlim - i0));
+    const T ps = post ? (T)s.scale : T(1);
     if (!out) out = w;
     if (ng <= 0 && out == w && !post) return;
+    const double2* c = sel == GM_COEF ? s.coef : (sel == GM_COEFA ? s.coefA : s.y);
     T cr[G], ci[G];
 #pragma unroll
     for (int i = 0; i < G; ++i) {
-        cr[i] = i < ng ? (T)c[2 * i] : T(0);
-        ci[i] = i < ng ? (T)c[2 * i + 1] : T(0);
+        cr[i] = i < ng ? (T)c[i0 + i].x : T(0);
+        ci[i] = i < ng ? (T)c[i0 + i].y : T(0);
     }
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        T xr = w[e].x, xi = w[e].y;
+    const size_t base = (size_t)blockIdx.y * ns;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < ns; e += (size_t)gridDim.x * blockDim.x) {
+        T xr = w[base + e].x, xi = w[base + e].y;
 #pragma unroll
         for (int i = 0; i < G; ++i) {
             if (i >= ng) break;
-            const c_t<T> v = V[i * ld + e];
+            const c_t<T> v = V[i * ld + base + e];
             xr = fma(cr[i], v.x, fma(-ci[i], v.y, xr));
             xi = fma(cr[i], v.y, fma(ci[i], v.x, xi));
         }
-        out[e] = mkc(xr * ps, xi * ps);
+        out[base + e] = mkc(xr * ps, xi * ps);
     }
 }
 
@@ -181,9 +193,9 @@ __global__ void k_caxpby(c_t<T>* __restrict__ z, T a, const c_t<T>* __restrict__
 }
 
 // ---------------------------------------------------------------------------
-// Scalar steps of the inner flexible GMRES, one CTA each.
+// Scalar steps of the inner flexible GMRES: one CTA per frequency slice.
 // ---------------------------------------------------------------------------
-constexpr int kGmThreads = 256;
+constexpr int kGmThreads = 128;
 
 __device__ __forceinline__ double2 gm_mul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 __device__ __forceinline__ double2 gm_conj(double2 a) { return make_double2(a.x, -a.y); }
@@ -197,113 +209,146 @@ __device__ __forceinline__ double2 gm_div(double2 a, double2 b) {
     return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
 }
 
-// out[i] = sum over the nb CTAs, in CTA order, of the partials of vector i < nv:
-// warp w adds the values v = w, w + 8, ... (re and im of each vector), each
-// lane a fixed strided subset, then a fixed shuffle tree.
-__device__ void gm_reduce(const double* __restrict__ part, int nb, int nv, double2* out) {
+// out[i] = sum over the slice's nbx CTAs, in CTA order, of the partials of
+// vector i < nv: warp w adds the values v = w, w + 4, ... (re and im of each
+// vector), each lane a fixed strided subset, then a fixed shuffle tree.
+__device__ void gm_reduce(const double* __restrict__ part, int nbx, int nv, double2* out) {
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const double* pk = part + (size_t)blockIdx.x * nbx * nv * 2;
     double* o = reinterpret_cast<double*>(out);
     for (int v = warp; v < 2 * nv; v += kGmThreads / 32) {
         double a = 0.0;
-        for (int q = lane; q < nb; q += 32) a += part[((size_t)q * nv + v / 2) * 2 + (v & 1)];
+        for (int q = lane; q < nbx; q += 32) a += pk[((size_t)q * nv + v / 2) * 2 + (v & 1)];
         a = warp_sum(a);
         if (lane == 0) o[v] = a;
     }
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kGmThreads) k_gm_init(const double* __restrict__ part_bb,
-                                                        const double* __restrict__ part_rr, int nb,
-                                                        const Ctl* __restrict__ octl, GmState* s, double tol) {
-    __shared__ double2 bb[1], rr[1];
-    gm_reduce(part_bb, nb, 1, bb);
-    gm_reduce(part_rr, nb, 1, rr);
-    if (threadIdx.x != 0) return;
-    const double bn = sqrt(fmax(bb[0].x, 0.0)), beta = sqrt(fmax(rr[0].x, 0.0));
-    const bool run = octl->status == ST_RUNNING && beta > tol * bn;
-    s->ictl.jbar = octl->jbar;
-    s->ictl.status = run ? ST_RUNNING : 0;   // 0: stopped
-    s->skip = run ? 0 : 1;
-    s->skip_re = 1;
-    s->j = 0;
-    s->bn = bn;
-    s->scale = run ? 1.0 / beta : 1.0;
-    s->gv[0] = make_double2(beta, 0.0);
+// Start of a cycle: every slice running, no second Gram-Schmidt pass requested.
+__global__ void k_gm_reset(GmHead* h) {
+    for (int i = threadIdx.x; i < kMaxKrylov; i += blockDim.x) h->skip_re[i] = 1;
+    if (threadIdx.x == 0) {
+        h->ndone = 0;
+        h->skip = 0;
+        h->jmax = 0;
+        h->ictl.status = ST_RUNNING;
+    }
 }
 
-__global__ void __launch_bounds__(kGmThreads) k_gm_orth1(const double* __restrict__ part, int nb, int j, GmState* s) {
-    if (s->skip) return;
-    gm_reduce(part, nb, j + 2, s->tmp);
+// A slice leaves the cycle: its coefficients and scale become 0 (its basis vectors
+// are then zero and stay finite), and the last slice to leave stops the cycle.
+__device__ void gm_leave(GmK& s, GmHead* h, int nk) {
+    s.done = 1;
+    s.scale = 0.0;
+    if (atomicAdd(&h->ndone, 1) + 1 == nk) {
+        h->skip = 1;
+        h->ictl.status = 0;
+    }
+}
+
+__global__ void __launch_bounds__(kGmThreads) k_gm_init(const double* __restrict__ part_bb,
+                                                        const double* __restrict__ part_rr, int nbx,
+                                                        const Ctl* __restrict__ octl, GmHead* h, GmK* gk, int nk,
+                                                        double tol) {
+    __shared__ double2 bb[1], rr[1];
+    gm_reduce(part_bb, nbx, 1, bb);
+    gm_reduce(part_rr, nbx, 1, rr);
     if (threadIdx.x != 0) return;
-    const double ww = s->tmp[j + 1].x;
+    GmK& s = gk[blockIdx.x];
+    const double bn = sqrt(fmax(bb[0].x, 0.0)), beta = sqrt(fmax(rr[0].x, 0.0));
+    if (blockIdx.x == 0) h->ictl.jbar = octl->jbar;
+    s.done = 0;
+    s.j = 0;
+    s.bn = bn;
+    s.scale = beta > 0.0 ? 1.0 / beta : 0.0;
+    s.gv[0] = make_double2(beta, 0.0);
+    // a slice already solved (or zero), or every slice when the outer iteration has stopped
+    if (octl->status != ST_RUNNING || !(beta > tol * bn)) gm_leave(s, h, nk);
+}
+
+__global__ void __launch_bounds__(kGmThreads) k_gm_orth1(const double* __restrict__ part, int nbx, int j, GmHead* h,
+                                                         GmK* gk) {
+    GmK& s = gk[blockIdx.x];
+    if (h->skip || s.done) {
+        if (threadIdx.x == 0)
+            for (int i = 0; i <= j; ++i) s.coef[i] = s.coefA[i] = make_double2(0.0, 0.0);
+        return;
+    }
+    gm_reduce(part, nbx, j + 2, s.tmp);
+    if (threadIdx.x != 0) return;
+    const double ww = s.tmp[j + 1].x;
     double hh = 0.0;
     for (int i = 0; i <= j; ++i) {
-        s->hcol[i] = s->tmp[i];
-        hh += gm_norm(s->tmp[i]);
-        s->coef[i] = gm_scale(s->tmp[i], -1.0);
+        s.hcol[i] = s.tmp[i];
+        hh += gm_norm(s.tmp[i]);
+        s.coef[i] = gm_scale(s.tmp[i], -1.0);
     }
     const double hn2 = ww - hh;
     // ||w - sum h_i v_i||^2 = <w, w> - sum |h_i|^2 cancels: project once more
-    s->reorth = hn2 > 1e-4 * ww ? 0 : 1;
-    s->skip_re = s->reorth ? 0 : 1;
-    s->hn2 = hn2;
+    s.reorth = hn2 > 1e-4 * ww ? 0 : 1;
+    for (int i = 0; i <= j; ++i) s.coefA[i] = s.reorth ? s.coef[i] : make_double2(0.0, 0.0);
+    if (s.reorth) h->skip_re[j] = 0;   // step j's second pass runs (for the slices that asked)
+    s.hn2 = hn2;
 }
 
-__global__ void __launch_bounds__(kGmThreads) k_gm_orth2(const double* __restrict__ part, int nb, int j, GmState* s,
-                                                         double tol) {
-    if (s->skip) return;
-    if (s->reorth) gm_reduce(part, nb, j + 2, s->tmp);
-    if (threadIdx.x != 0) return;
-    double hn2 = s->hn2;
-    if (s->reorth) {
+__global__ void __launch_bounds__(kGmThreads) k_gm_orth2(const double* __restrict__ part, int nbx, int j, GmHead* h,
+                                                         GmK* gk, int nk, double tol) {
+    GmK& s = gk[blockIdx.x];
+    // a slice that left earlier (its own flag), or all of them (the cycle stopped before this launch)
+    const bool run = !s.done && !h->skip;
+    if (run && s.reorth) gm_reduce(part, nbx, j + 2, s.tmp);   // the second pass ran: skip_re[j] was cleared
+    if (threadIdx.x != 0 || !run) return;
+    double hn2 = s.hn2;
+    if (s.reorth) {
         double hh = 0.0;
         for (int i = 0; i <= j; ++i) {
-            s->hcol[i] = gm_add(s->hcol[i], s->tmp[i]);
-            hh += gm_norm(s->tmp[i]);
-            s->coef[i] = gm_scale(s->tmp[i], -1.0);
+            s.hcol[i] = gm_add(s.hcol[i], s.tmp[i]);
+            hh += gm_norm(s.tmp[i]);
+            s.coef[i] = gm_scale(s.tmp[i], -1.0);
         }
-        hn2 = s->tmp[j + 1].x - hh;
+        hn2 = s.tmp[j + 1].x - hh;
     }
-    s->skip_re = 1;
     const double hn = sqrt(fmax(hn2, 0.0));
-    s->scale = hn > 0.0 ? 1.0 / hn : 1.0;
-    double2* hc = s->hcol;
+    s.scale = hn > 0.0 ? 1.0 / hn : 0.0;
+    double2* hc = s.hcol;
     hc[j + 1] = make_double2(hn, 0.0);
     for (int i = 0; i < j; ++i) {   // the previous rotations
-        const double2 a = gm_add(gm_scale(hc[i], s->cs[i]), gm_mul(s->sn[i], hc[i + 1]));
-        hc[i + 1] = gm_sub(gm_scale(hc[i + 1], s->cs[i]), gm_mul(gm_conj(s->sn[i]), hc[i]));
+        const double2 a = gm_add(gm_scale(hc[i], s.cs[i]), gm_mul(s.sn[i], hc[i + 1]));
+        hc[i + 1] = gm_sub(gm_scale(hc[i + 1], s.cs[i]), gm_mul(gm_conj(s.sn[i]), hc[i]));
         hc[i] = a;
     }
     const double na = gm_abs(hc[j]), r = hypot(na, gm_abs(hc[j + 1]));
     if (r == 0.0) {
-        s->cs[j] = 1.0;
-        s->sn[j] = make_double2(0.0, 0.0);
+        s.cs[j] = 1.0;
+        s.sn[j] = make_double2(0.0, 0.0);
     } else if (na == 0.0) {
-        s->cs[j] = 0.0;
-        s->sn[j] = gm_scale(gm_conj(hc[j + 1]), 1.0 / r);
+        s.cs[j] = 0.0;
+        s.sn[j] = gm_scale(gm_conj(hc[j + 1]), 1.0 / r);
     } else {
-        s->cs[j] = na / r;
-        s->sn[j] = gm_scale(gm_mul(gm_scale(hc[j], 1.0 / na), gm_conj(hc[j + 1])), 1.0 / r);
+        s.cs[j] = na / r;
+        s.sn[j] = gm_scale(gm_mul(gm_scale(hc[j], 1.0 / na), gm_conj(hc[j + 1])), 1.0 / r);
     }
-    hc[j] = gm_add(gm_scale(hc[j], s->cs[j]), gm_mul(s->sn[j], hc[j + 1]));
+    hc[j] = gm_add(gm_scale(hc[j], s.cs[j]), gm_mul(s.sn[j], hc[j + 1]));
     hc[j + 1] = make_double2(0.0, 0.0);
-    s->gv[j + 1] = gm_scale(gm_mul(gm_conj(s->sn[j]), s->gv[j]), -1.0);
-    s->gv[j] = gm_scale(s->gv[j], s->cs[j]);
-    for (int i = 0; i <= j; ++i) s->H[i * kMaxKrylov + j] = hc[i];
-    s->j = j + 1;
-    if (gm_abs(s->gv[j + 1]) <= tol * s->bn) {
-        s->skip = 1;
-        s->ictl.status = 0;
-    }
+    s.gv[j + 1] = gm_scale(gm_mul(gm_conj(s.sn[j]), s.gv[j]), -1.0);
+    s.gv[j] = gm_scale(s.gv[j], s.cs[j]);
+    for (int i = 0; i <= j; ++i) s.H[i * kMaxKrylov + j] = hc[i];
+    s.j = j + 1;
+    h->jmax = j + 1;   // the same value from every slice still running
+    if (gm_abs(s.gv[j + 1]) <= tol * s.bn || hn == 0.0) gm_leave(s, h, nk);
 }
 
-__global__ void k_gm_solve(GmState* s) {
+// y_k = H_k^{-1} g_k over slice k's completed steps (zero beyond them).
+__global__ void k_gm_solve(GmK* gk) {
     if (threadIdx.x != 0) return;
-    const int j = s->j;
+    GmK& s = gk[blockIdx.x];
+    const int j = s.j;
+    for (int i = 0; i < kMaxKrylov; ++i) s.y[i] = make_double2(0.0, 0.0);
     for (int i = j - 1; i >= 0; --i) {
-        double2 a = s->gv[i];
-        for (int k = i + 1; k < j; ++k) a = gm_sub(a, gm_mul(s->H[i * kMaxKrylov + k], s->coef[k]));
-        s->coef[i] = gm_div(a, s->H[i * kMaxKrylov + i]);
+        double2 a = s.gv[i];
+        for (int k = i + 1; k < j; ++k) a = gm_sub(a, gm_mul(s.H[i * kMaxKrylov + k], s.y[k]));
+        s.y[i] = gm_div(a, s.H[i * kMaxKrylov + i]);
     }
 }
 
@@ -311,7 +356,12 @@ static int grid_n(size_t n) {
     const size_t b = (n + 255) / 256;
     return (int)(b > 2 * 152 * 4 ? 2 * 152 * 4 : (b < 1 ? 1 : b));
 }
-int cdot_blocks(size_t n) { return grid_n(n); }
+// CTAs per slice of the per-slice vector kernels: about 2 x 152 x 4 in all.
+int cdot_blocks(size_t ns, int nk) {
+    const size_t per = (size_t)(2 * 152 * 4 + nk - 1) / nk;
+    const size_t b = (ns + 255) / 256;
+    return (int)(b < per ? (b < 1 ? 1 : b) : (per < 1 ? 1 : per));
+}
 
 template <class T>
 void launch_jtilde(const double* U, const float2* uff, int nt, int nspace, T* jt, cudaStream_t st) {
@@ -328,37 +378,39 @@ void launch_apply_M(const Geo& g, int nk, const c_t<T>* Y, c_t<T>* W, const T* j
         k_apply_M<T, 1><<<grid, 256, 0, st>>>(g, nk, Y, W, jt, tb, (T)c2, (T)c1, skip, B);
     }
 }
-// Groups of up to kGroup vectors per launch, register accumulators.  Note:
-// w may itself be one of the v_i (the axpy reads w[e] before writing it).
+// Groups of up to kGroup vectors per launch, register accumulators.
 template <class T>
-void launch_cmulti_dot(const c_t<T>* w, const c_t<T>* V, size_t ld, int nv, size_t n, double* partials,
+void launch_cmulti_dot(const c_t<T>* w, const c_t<T>* V, size_t ld, int nv, size_t ns, int nk, double* partials,
                        const int* skip, cudaStream_t st) {
-    const int nb = grid_n(n);
+    const dim3 grid(cdot_blocks(ns, nk), nk);
     for (int i0 = 0; i0 < nv; i0 += kGroup) {
         const c_t<T>* Vi = V + (size_t)i0 * ld;
         switch (nv - i0 >= kGroup ? kGroup : nv - i0) {
-            case 1: k_cmulti_dot<T, 1><<<nb, kCDotThreads, 0, st>>>(w, Vi, ld, n, nv, i0, partials, skip); break;
-            case 2: k_cmulti_dot<T, 2><<<nb, kCDotThreads, 0, st>>>(w, Vi, ld, n, nv, i0, partials, skip); break;
-            case 3: k_cmulti_dot<T, 3><<<nb, kCDotThreads, 0, st>>>(w, Vi, ld, n, nv, i0, partials, skip); break;
-            default: k_cmulti_dot<T, 4><<<nb, kCDotThreads, 0, st>>>(w, Vi, ld, n, nv, i0, partials, skip); break;
+            case 1: k_cmulti_dot<T, 1><<<grid, kCDotThreads, 0, st>>>(w, Vi, ld, ns, nv, i0, partials, skip); break;
+            case 2: k_cmulti_dot<T, 2><<<grid, kCDotThreads, 0, st>>>(w, Vi, ld, ns, nv, i0, partials, skip); break;
+            case 3: k_cmulti_dot<T, 3><<<grid, kCDotThreads, 0, st>>>(w, Vi, ld, ns, nv, i0, partials, skip); break;
+            default: k_cmulti_dot<T, 4><<<grid, kCDotThreads, 0, st>>>(w, Vi, ld, ns, nv, i0, partials, skip); break;
         }
     }
 }
 template <class T>
-void launch_cmulti_axpy(c_t<T>* w, const c_t<T>* V, size_t ld, int nv, const double* c, size_t n, const int* skip,
-                        const int* nlim, cudaStream_t st, c_t<T>* out, const double* post) {
-    const int nb = grid_n(n);
+void launch_cmulti_axpy(c_t<T>* w, const c_t<T>* V, size_t ld, int nv, int nlim, size_t ns, int nk, const GmK* gk,
+                        int sel, const int* skip, cudaStream_t st, c_t<T>* out, int post, const int* nlimd) {
+    const dim3 grid(cdot_blocks(ns, nk), nk);
+    if (nv == 0) {   // out = w * post only
+        k_cmulti_axpy<T, 1><<<grid, 256, 0, st>>>(w, V, ld, ns, gk, sel, skip, 0, nullptr, 0, out, post);
+        return;
+    }
     for (int i0 = 0; i0 < nv; i0 += kGroup) {
         const c_t<T>* Vi = V + (size_t)i0 * ld;
-        const double* ci = c + 2 * i0;
         // the first group reads w and writes out; later groups update out in place; the last one scales
         c_t<T>* src = i0 == 0 ? w : (out ? out : w);
-        const double* ps = i0 + kGroup >= nv ? post : nullptr;
+        const int ps = i0 + kGroup >= nv ? post : 0;
         switch (nv - i0 >= kGroup ? kGroup : nv - i0) {
-            case 1: k_cmulti_axpy<T, 1><<<nb, 256, 0, st>>>(src, Vi, ld, ci, n, skip, nlim, i0, out, ps); break;
-            case 2: k_cmulti_axpy<T, 2><<<nb, 256, 0, st>>>(src, Vi, ld, ci, n, skip, nlim, i0, out, ps); break;
-            case 3: k_cmulti_axpy<T, 3><<<nb, 256, 0, st>>>(src, Vi, ld, ci, n, skip, nlim, i0, out, ps); break;
-            default: k_cmulti_axpy<T, 4><<<nb, 256, 0, st>>>(src, Vi, ld, ci, n, skip, nlim, i0, out, ps); break;
+            case 1: k_cmulti_axpy<T, 1><<<grid, 256, 0, st>>>(src, Vi, ld, ns, gk, sel, skip, nlim, nlimd, i0, out, ps); break;
+            case 2: k_cmulti_axpy<T, 2><<<grid, 256, 0, st>>>(src, Vi, ld, ns, gk, sel, skip, nlim, nlimd, i0, out, ps); break;
+            case 3: k_cmulti_axpy<T, 3><<<grid, 256, 0, st>>>(src, Vi, ld, ns, gk, sel, skip, nlim, nlimd, i0, out, ps); break;
+            default: k_cmulti_axpy<T, 4><<<grid, 256, 0, st>>>(src, Vi, ld, ns, gk, sel, skip, nlim, nlimd, i0, out, ps); break;
         }
     }
 }
@@ -367,26 +419,27 @@ void launch_caxpby(c_t<T>* z, double a, const c_t<T>* x, double b, const c_t<T>*
                    const double* sdev, cudaStream_t st) {
     k_caxpby<T><<<grid_n(n), 256, 0, st>>>(z, (T)a, x, (T)b, y, n, skip, sdev);
 }
-void launch_gm_init(const double* part_bb, const double* part_rr, int nb, const Ctl* octl, GmState* s, double tol,
-                    cudaStream_t st) {
-    k_gm_init<<<1, kGmThreads, 0, st>>>(part_bb, part_rr, nb, octl, s, tol);
+void launch_gm_reset(GmHead* h, cudaStream_t st) { k_gm_reset<<<1, 32, 0, st>>>(h); }
+void launch_gm_init(const double* part_bb, const double* part_rr, int nbx, const Ctl* octl, GmHead* h, GmK* gk,
+                    int nk, double tol, cudaStream_t st) {
+    k_gm_init<<<nk, kGmThreads, 0, st>>>(part_bb, part_rr, nbx, octl, h, gk, nk, tol);
 }
-void launch_gm_orth1(const double* part, int nb, int j, GmState* s, cudaStream_t st) {
-    k_gm_orth1<<<1, kGmThreads, 0, st>>>(part, nb, j, s);
+void launch_gm_orth1(const double* part, int nbx, int j, GmHead* h, GmK* gk, int nk, cudaStream_t st) {
+    k_gm_orth1<<<nk, kGmThreads, 0, st>>>(part, nbx, j, h, gk);
 }
-void launch_gm_orth2(const double* part, int nb, int j, GmState* s, double tol, cudaStream_t st) {
-    k_gm_orth2<<<1, kGmThreads, 0, st>>>(part, nb, j, s, tol);
+void launch_gm_orth2(const double* part, int nbx, int j, GmHead* h, GmK* gk, int nk, double tol, cudaStream_t st) {
+    k_gm_orth2<<<nk, kGmThreads, 0, st>>>(part, nbx, j, h, gk, nk, tol);
 }
-void launch_gm_solve(GmState* s, cudaStream_t st) { k_gm_solve<<<1, 32, 0, st>>>(s); }
+void launch_gm_solve(GmK* gk, int nk, cudaStream_t st) { k_gm_solve<<<nk, 32, 0, st>>>(gk); }
 
 #define PINT_INST(T)                                                                                              \
     template void launch_jtilde<T>(const double*, const float2*, int, int, T*, cudaStream_t);                      \
     template void launch_apply_M<T>(const Geo&, int, const c_t<T>*, c_t<T>*, const T*, const Tabs<T>&, double,    \
                                     double, const int*, const c_t<T>*, cudaStream_t);                             \
-    template void launch_cmulti_dot<T>(const c_t<T>*, const c_t<T>*, size_t, int, size_t, double*, const int*,     \
-                                       cudaStream_t);                                                             \
-    template void launch_cmulti_axpy<T>(c_t<T>*, const c_t<T>*, size_t, int, const double*, size_t, const int*,    \
-                                        const int*, cudaStream_t, c_t<T>*, const double*);                        \
+    template void launch_cmulti_dot<T>(const c_t<T>*, const c_t<T>*, size_t, int, size_t, int, double*,          \
+                                       const int*, cudaStream_t);                                                 \
+    template void launch_cmulti_axpy<T>(c_t<T>*, const c_t<T>*, size_t, int, int, size_t, int, const GmK*, int,   \
+                                        const int*, cudaStream_t, c_t<T>*, int, const int*);                      \
     template void launch_caxpby<T>(c_t<T>*, double, const c_t<T>*, double, const c_t<T>*, size_t, const int*,      \
                                    const double*, cudaStream_t);
 PINT_INST(float)

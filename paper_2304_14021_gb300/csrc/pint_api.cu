@@ -234,7 +234,8 @@ struct pint_handle {
     void* jbuf = nullptr;      // solution, (vary + 1) basis and vary preconditioned spectra
     void* jt = nullptr;        // J~(x), one per spatial point
     double* jpart = nullptr;   // complex dot partial sums
-    pint::GmState* gms = nullptr;    // device state of the inner GMRES cycle
+    pint::GmHead* gmh = nullptr;     // device state of the inner GMRES cycle: head
+    pint::GmK* gmk = nullptr;        //   and one block per frequency slice
     double vary_tol = 1e-4;    // relative residual of the inner solve
     // per-level invariants (PINT_OPT_LOG_INVARIANTS): (mass, energy) of every time level solved
     int log_inv = 0;
@@ -670,44 +671,47 @@ template <class T> struct Impl {
         using C = c_t<T>;
         const Geo& g = h->geo;
         const int nk = g.nt / 2 + 1, m = h->vary;
-        const size_t n = (size_t)nk * g.nspace;
-        const int nb = cdot_blocks(n);
+        const size_t ns = (size_t)g.nspace, n = (size_t)nk * ns;
+        const int nbx = cdot_blocks(ns, nk);
         C* X = reinterpret_cast<C*>(h->jbuf);   // the right-hand side S1 stays in S until the end
         C* V = X + n;
         C* Z = V + (size_t)(m + 1) * n;
         T* jt = reinterpret_cast<T*>(h->jt);
-        GmState* gs = h->gms;
-        const int* skip = &gs->skip;
-        const double* coef = reinterpret_cast<const double*>(gs->coef);
+        GmHead* gh = h->gmh;
+        GmK* gk = h->gmk;
+        const int* skip = &gh->skip;
+        double* part2 = h->jpart + 2 * (size_t)nbx * nk;
         const double c1 = g.expl ? 0.0 : 1.0;
         cudaError_t e;
         launch_jtilde<T>(U, uff, g.nt, g.nspace, jt, h->st);
+        launch_gm_reset(gh, h->st);
         launch_caxpby<T>(X, 1.0, S, 0.0, nullptr, n, nullptr, nullptr, h->st);
         if ((e = spatial(h, X, tb)) != cudaSuccess) return e;           // x0 = P^{-1} S1
         launch_apply_M<T>(g, nk, X, V, jt, tb, h->coef.c2, c1, nullptr, S, h->st);   // r0 = S1 - M x0
-        launch_cmulti_dot<T>(S, S, n, 1, n, h->jpart, nullptr, h->st);
-        launch_cmulti_dot<T>(V, V, n, 1, n, h->jpart + 2 * (size_t)nb, nullptr, h->st);
-        launch_gm_init(h->jpart, h->jpart + 2 * (size_t)nb, nb, h->ctl, gs, h->vary_tol, h->st);
-        launch_caxpby<T>(V, 1.0, V, 0.0, nullptr, n, skip, &gs->scale, h->st);   // v_0 = r0 / ||r0||
+        launch_cmulti_dot<T>(S, S, n, 1, ns, nk, h->jpart, nullptr, h->st);
+        launch_cmulti_dot<T>(V, V, n, 1, ns, nk, part2, nullptr, h->st);
+        launch_gm_init(h->jpart, part2, nbx, h->ctl, gh, gk, nk, h->vary_tol, h->st);
+        launch_cmulti_axpy<T>(V, V, n, 0, 0, ns, nk, gk, GM_COEF, skip, h->st, nullptr, 1);   // v_0 = r0 / ||r0||
         for (int j = 0; j < m; ++j) {
             C* vj = V + (size_t)j * n;
             C* zj = Z + (size_t)j * n;
             C* w = V + (size_t)(j + 1) * n;
             launch_caxpby<T>(zj, 1.0, vj, 0.0, nullptr, n, skip, nullptr, h->st);
-            if ((e = spatial(h, zj, tb, &gs->ictl)) != cudaSuccess) return e;   // z_j = P^{-1} v_j
+            if ((e = spatial(h, zj, tb, &gh->ictl)) != cudaSuccess) return e;   // z_j = P^{-1} v_j
             launch_apply_M<T>(g, nk, zj, w, jt, tb, h->coef.c2, c1, skip, nullptr, h->st);
-            // classical Gram-Schmidt: <v_i, w> for i <= j and <w, w> in one pass (w is v_{j+1});
-            // a second pass when ||w - sum h_i v_i||^2 = <w, w> - sum |h_i|^2 cancels
-            launch_cmulti_dot<T>(w, V, n, j + 2, n, h->jpart, skip, h->st);
-            launch_gm_orth1(h->jpart, nb, j, gs, h->st);
-            launch_cmulti_axpy<T>(w, V, n, j + 1, coef, n, &gs->skip_re, nullptr, h->st);
-            launch_cmulti_dot<T>(w, V, n, j + 2, n, h->jpart, &gs->skip_re, h->st);
-            launch_gm_orth2(h->jpart, nb, j, gs, h->vary_tol, h->st);
+            // classical Gram-Schmidt per slice: <v_i, w> for i <= j and <w, w> in one pass (w is v_{j+1});
+            // a second pass for the slices whose ||w - sum h_i v_i||^2 = <w, w> - sum |h_i|^2 cancels
+            launch_cmulti_dot<T>(w, V, n, j + 2, ns, nk, h->jpart, skip, h->st);
+            launch_gm_orth1(h->jpart, nbx, j, gh, gk, nk, h->st);
+            launch_cmulti_axpy<T>(w, V, n, j + 1, j + 1, ns, nk, gk, GM_COEFA, &gh->skip_re[j], h->st);
+            launch_cmulti_dot<T>(w, V, n, j + 2, ns, nk, h->jpart, &gh->skip_re[j], h->st);
+            launch_gm_orth2(h->jpart, nbx, j, gh, gk, nk, h->vary_tol, h->st);
             // v_{j+1} = (w - sum h_i v_i) / h_{j+1,j}
-            launch_cmulti_axpy<T>(w, V, n, j + 1, coef, n, skip, nullptr, h->st, nullptr, &gs->scale);
+            launch_cmulti_axpy<T>(w, V, n, j + 1, j + 1, ns, nk, gk, GM_COEF, skip, h->st, nullptr, 1);
         }
-        launch_gm_solve(gs, h->st);
-        launch_cmulti_axpy<T>(X, Z, n, m, coef, n, nullptr, &gs->j, h->st, S);   // S2 = x0 + Z y
+        launch_gm_solve(gk, nk, h->st);
+        // S2 = x0 + Z y over the steps run (z_i beyond them were never written)
+        launch_cmulti_axpy<T>(X, Z, n, m, m, ns, nk, gk, GM_Y, nullptr, h->st, S, 0, &gh->jmax);
         return cudaGetLastError();
     }
     static cudaError_t step2(pint_handle* h, c_t<T>* S, const Tabs<T>& tb, const double* U, const float2* uff) {
@@ -1040,7 +1044,8 @@ void pint_destroy(pint_handle* h) {
     af(h->jbuf);
     af(h->jt);
     af(h->jpart);
-    af(h->gms);
+    af(h->gmh);
+    af(h->gmk);
     af(h->inv_dev);
     af(h->wgemm);
     if (h->nlev > 0) activate_level(h, 0);   // the base level owns gam/ginv/gamf/ginvf and tabs_ptrs
@@ -1250,22 +1255,26 @@ int pint_set_option(pint_handle* h, int option, long long value) {
             if (value > 0 && !h->coef.ch) return PINT_EINVAL;   // Cahn-Hilliard only
             for (auto& sl : h->gslot)   // captured loops hold the old Step 2
                 if (sl.exec) { cudaGraphExecDestroy(sl.exec); sl.exec = nullptr; }
-            for (void* q : {h->jbuf, h->jt, (void*)h->jpart, (void*)h->gms})
+            for (void* q : {h->jbuf, h->jt, (void*)h->jpart, (void*)h->gmh, (void*)h->gmk})
                 if (q) cudaFreeAsync(q, h->st);
             h->jbuf = h->jt = nullptr;
             h->jpart = nullptr;
-            h->gms = nullptr;
+            h->gmh = nullptr;
+            h->gmk = nullptr;
             h->vary = 0;
             if (value == 0) return PINT_OK;
             const size_t tsz = f32_transforms(&h->p) ? 4 : 8;
-            const size_t n = (size_t)(h->p.nt / 2 + 1) * h->geo.nspace;
+            const int nk = h->p.nt / 2 + 1;
+            const size_t n = (size_t)nk * h->geo.nspace;
+            // partial sets of up to kMaxKrylov + 1 vectors, for every segment length (nbx nk <= 2*152*4 + nk)
+            const size_t nparts = (size_t)cdot_blocks(h->geo.nspace, nk) * nk + 2 * 152 * 4 + nk;
             auto al = [&](void** ptr, size_t bytes) {
                 if (cudaMallocAsync(ptr, bytes, h->st) != cudaSuccess) { cudaGetLastError(); return false; }
                 return true;
             };
             if (!al(&h->jbuf, (size_t)(2 * value + 2) * n * 2 * tsz) || !al(&h->jt, h->geo.nspace * tsz) ||
-                !al((void**)&h->jpart, (size_t)cdot_blocks(n) * (kMaxKrylov + 1) * 2 * sizeof(double)) ||
-                !al((void**)&h->gms, sizeof(GmState)))
+                !al((void**)&h->jpart, nparts * (kMaxKrylov + 1) * 2 * sizeof(double)) ||
+                !al((void**)&h->gmh, sizeof(GmHead)) || !al((void**)&h->gmk, (size_t)nk * sizeof(GmK)))
                 return PINT_ENOMEM;
             h->vary = (int)value;
             return PINT_OK;

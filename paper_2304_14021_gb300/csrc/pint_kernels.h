@@ -168,7 +168,6 @@ void launch_scale_copy(double* y, const double* x, double a, size_t n, cudaStrea
 // Every vector kernel below takes an optional device flag `skip`: when it is
 // nonzero at launch the kernel does nothing (the inner cycle has stopped), so
 // that one fixed launch sequence serves every cycle and can be captured.
-int cdot_blocks(size_t n);
 template <class T>
 void launch_jtilde(const double* U, const float2* uff, int nt, int nspace, T* jt, cudaStream_t st);
 // W[k] = lambda_1k Y[k] + lambda_2k (c2 Lap^2 Y[k] + Lap((c1 - J~) Y[k])) + lambda_3k Lap Y[k], k < nk
@@ -176,52 +175,61 @@ void launch_jtilde(const double* U, const float2* uff, int nt, int nspace, T* jt
 template <class T>
 void launch_apply_M(const Geo& g, int nk, const c_t<T>* Y, c_t<T>* W, const T* jt, const Tabs<T>& tb, double c2,
                     double c1, const int* skip, const c_t<T>* B, cudaStream_t st);
-// partials[(b nv + i) 2 + {re, im}] of <v_i, w> (cdot_blocks(n) CTAs)
-template <class T>
-void launch_cmulti_dot(const c_t<T>* w, const c_t<T>* V, size_t ld, int nv, size_t n, double* partials,
-                       const int* skip, cudaStream_t st);
-// out = (w + sum_{i < nv} c_i v_i) * post (out = w and post = 1 when null); with nlim, only
-// the terms i < *nlim (the others are not read)
-template <class T>
-void launch_cmulti_axpy(c_t<T>* w, const c_t<T>* V, size_t ld, int nv, const double* c, size_t n, const int* skip,
-                        const int* nlim, cudaStream_t st, c_t<T>* out = nullptr, const double* post = nullptr);
-// z = a x + b y (y may be null); with sdev, a is *sdev instead
-template <class T>
-void launch_caxpby(c_t<T>* z, double a, const c_t<T>* x, double b, const c_t<T>* y, size_t n, const int* skip,
-                   const double* sdev, cudaStream_t st);
-
-// Device state of one cycle of the inner flexible GMRES (classical Gram-Schmidt
-// with a conditional second pass, complex Givens rotations, FP64 scalars).  The
-// small kernels below update it from the dot products' per-CTA partials, which
-// they add in a fixed order, so the cycle is deterministic and needs no host
-// round trip.
-struct GmState {
-    Ctl ictl;            // control word of the cycle's spatial solves: jbar, and status ST_RUNNING while it runs
-    int skip;            // nonzero once the cycle has stopped (converged, or the outer iteration has stopped)
-    int skip_re;         // nonzero: this step's second Gram-Schmidt pass is skipped
-    int j;               // inner iterations completed
-    int reorth;
-    double bn;           // ||S1||
-    double hn2;
-    double scale;        // the factor the next normalization applies
+// Device state of the inner flexible GMRES: a head shared by the cycle and one
+// block per frequency slice (the operator is block-diagonal over the slices,
+// so each gets its own Krylov coefficients; classical Gram-Schmidt with a
+// conditional second pass, complex Givens rotations, FP64 scalars).  The small
+// kernels below update it from the dot products' per-CTA partials, which they
+// add in a fixed order, so the cycle is deterministic and needs no host round trip.
+struct GmHead {
+    Ctl ictl;                 // control word of the cycle's spatial solves: jbar, status ST_RUNNING while it runs
+    int skip;                 // nonzero once every slice has left the cycle (or the outer iteration has stopped)
+    int ndone;                // slices that have left
+    int jmax;                 // steps run
+    int skip_re[kMaxKrylov];  // step j's second Gram-Schmidt pass is skipped unless a slice asked for it
+};
+struct GmK {
+    int done, reorth, j, pad;
+    double bn, hn2, scale;    // ||S1_k||; the norm^2 estimate of the new vector; its normalization factor
     double cs[kMaxKrylov];
     double2 sn[kMaxKrylov];
     double2 gv[kMaxKrylov + 1];
     double2 H[kMaxKrylov * kMaxKrylov];   // upper triangle, row i, column j at i * kMaxKrylov + j
     double2 hcol[kMaxKrylov + 1];
-    double2 coef[kMaxKrylov + 1];        // axpy coefficients (re, im), also the final y
+    double2 coef[kMaxKrylov + 1];        // projection coefficients of the step's last pass
+    double2 coefA[kMaxKrylov + 1];       // those of its first pass when a second one follows, else 0
+    double2 y[kMaxKrylov];               // the solution of the cycle's least-squares problem
     double2 tmp[kMaxKrylov + 2];
 };
-// Start: ||S1|| and ||r0|| from two single-vector partial sets; stop at once when
-// the outer iteration has stopped or ||r0|| <= tol ||S1||.
-void launch_gm_init(const double* part_bb, const double* part_rr, int nb, const Ctl* octl, GmState* s, double tol,
-                    cudaStream_t st);
+// CTAs per slice (x) of the per-slice vector kernels.
+int cdot_blocks(size_t ns, int nk);
+// partials[((k nbx + bx) nv + i) 2 + {re, im}] of <v_i, w> on slice k, nbx = cdot_blocks(ns, nk)
+template <class T>
+void launch_cmulti_dot(const c_t<T>* w, const c_t<T>* V, size_t ld, int nv, size_t ns, int nk, double* partials,
+                       const int* skip, cudaStream_t st);
+// Which coefficients of GmK the axpy reads: coef, coefA, y.
+enum { GM_COEF = 0, GM_COEFA = 1, GM_Y = 2 };
+// out = (w + sum_{i < min(nv, nlim, *nlimd)} c_{k,i} v_i) * (post ? scale_k : 1) on each slice k
+// (out = w when null; nlimd optional; nv = 0: the scaling alone)
+template <class T>
+void launch_cmulti_axpy(c_t<T>* w, const c_t<T>* V, size_t ld, int nv, int nlim, size_t ns, int nk, const GmK* gk,
+                        int sel, const int* skip, cudaStream_t st, c_t<T>* out = nullptr, int post = 0,
+                        const int* nlimd = nullptr);
+// z = a x + b y (y may be null); with sdev, a is *sdev instead
+template <class T>
+void launch_caxpby(c_t<T>* z, double a, const c_t<T>* x, double b, const c_t<T>* y, size_t n, const int* skip,
+                   const double* sdev, cudaStream_t st);
+void launch_gm_reset(GmHead* h, cudaStream_t st);
+// Start: ||S1_k|| and ||r0_k|| from two single-vector partial sets; a slice with
+// ||r0_k|| <= tol ||S1_k|| (or every slice, when the outer iteration has stopped) leaves at once.
+void launch_gm_init(const double* part_bb, const double* part_rr, int nbx, const Ctl* octl, GmHead* h, GmK* gk,
+                    int nk, double tol, cudaStream_t st);
 // Step j, first pass: h_i = <v_i, w>, i <= j, and <w, w> from partials of j + 2 vectors.
-void launch_gm_orth1(const double* part, int nb, int j, GmState* s, cudaStream_t st);
+void launch_gm_orth1(const double* part, int nbx, int j, GmHead* h, GmK* gk, int nk, cudaStream_t st);
 // Step j, second pass (if taken), the norm, the rotations and the stop test.
-void launch_gm_orth2(const double* part, int nb, int j, GmState* s, double tol, cudaStream_t st);
-// y = H^{-1} g over the completed steps, into coef.
-void launch_gm_solve(GmState* s, cudaStream_t st);
+void launch_gm_orth2(const double* part, int nbx, int j, GmHead* h, GmK* gk, int nk, double tol, cudaStream_t st);
+// y_k = H_k^{-1} g_k over slice k's completed steps.
+void launch_gm_solve(GmK* gk, int nk, cudaStream_t st);
 // CTAs of launch_time_inv_ff (with the same control block argument).
 int time_inv_ff_blocks(int nt, int nspace, const Ctl* ctl);
 // Step 2: per frequency k, S[k] <- (lambda_1k I + lambda_2k A)^{-1} S[k], in
