@@ -383,125 +383,6 @@ __global__ void __launch_bounds__(TimeTmaCfg<NT>::NTH)
     }
 }
 
-// The FP64 update of PINT_MIXED with the iterate tile prefetched: at entry one
-// warp starts bulk asynchronous copies of the CTA's U rows (2*CW points x N_t
-// levels, FP64) into shared memory, so they load while the spectrum is read
-// and transformed; the update U += x gamma_n^{-1}/N_t (one FP64 FMA, the FP32
-// value converted exactly) then reads U from shared memory and writes it back
-// with 128-bit stores.  Needs an even number of spatial points (16-byte
-// aligned rows); N_t <= 512 (the U tile stays at 64 KB).
-template <int NT> struct TimePfCfg {
-    static constexpr int CW = NT <= 128 ? 32 : (NT <= 256 ? 16 : 8);
-    static constexpr int NTH = NT * CW >= 8192 ? 1024 : (NT * CW >= 2048 ? 512 : 256);
-    static constexpr size_t TW_OFF = sizeof(float2) * (size_t)NT * CW;
-    static constexpr size_t U_OFF = TW_OFF + sizeof(float2) * NT;
-    static constexpr size_t BAR_OFF = U_OFF + sizeof(double) * (size_t)NT * 2 * CW;
-    static constexpr size_t SMEM = BAR_OFF + 16;
-    static_assert(U_OFF % 16 == 0, "U tile rows must be 16-byte aligned");
-};
-
-template <int NT>
-__global__ void __launch_bounds__(TimePfCfg<NT>::NTH)
-    k_time_inv_pf(int nspace, const float2* __restrict__ S, const float2* __restrict__ twt,
-                  const double* __restrict__ ginv, double* __restrict__ U, const Ctl* __restrict__ ctl,
-                  double* __restrict__ dpart) {
-    using C = float2;
-    using Cfg = TimePfCfg<NT>;
-    constexpr int CW = Cfg::CW, NTH = Cfg::NTH, CH = CW / 2;
-    pdl_wait();
-    if (ctl && ctl->status != ST_RUNNING) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* z = reinterpret_cast<C*>(smem_raw);
-    C* tw = reinterpret_cast<C*>(smem_raw + Cfg::TW_OFF);
-    double* ub = reinterpret_cast<double*>(smem_raw + Cfg::U_OFF);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + Cfg::BAR_OFF);
-    const int tid = threadIdx.x;
-    const long p0 = (long)blockIdx.x * 2 * CW;
-    const int npts = (int)min((long)2 * CW, nspace - p0);   // even: nspace is even
-    if (tid < 32) {
-        if (tid == 0) {
-            mbar_init(bar, 1);
-            mbar_fence_init();
-            mbar_arrive_expect_tx(bar, (uint32_t)(NT * npts * sizeof(double)));
-        }
-        __syncwarp();
-        for (int n = tid; n < NT; n += 32)
-            bulk_g2s(ub + n * 2 * CW, U + (size_t)n * nspace + p0, (uint32_t)(npts * sizeof(double)), bar);
-    }
-    for (int i = tid; i < NT; i += NTH) tw[i] = twt[i];
-    // Hermitian refill from the half spectrum, two points per 128-bit load
-#pragma unroll 4
-    for (int e = tid; e < (NT / 2 + 1) * CH; e += NTH) {
-        const int c = (e % CH) * 2, k = e / CH;
-        const long pa = p0 + c, pb = p0 + CW + c;
-        const C* row = S + (size_t)k * nspace;
-        float4 A = pa < nspace ? __ldg(reinterpret_cast<const float4*>(row + pa)) : make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 B = pb < nspace ? __ldg(reinterpret_cast<const float4*>(row + pb)) : make_float4(0.f, 0.f, 0.f, 0.f);
-        if (k == 0 || k == NT / 2) { A.y = A.w = 0.f; B.y = B.w = 0.f; }  // real in exact arithmetic
-        z[k * CW + c] = mkc(A.x - B.y, A.y + B.x);
-        z[k * CW + c + 1] = mkc(A.z - B.w, A.w + B.z);
-        if (k > 0 && k < NT / 2) {
-            z[(NT - k) * CW + c] = mkc(A.x + B.y, B.x - A.y);
-            z[(NT - k) * CW + c + 1] = mkc(A.z + B.w, B.z - A.w);
-        }
-    }
-    __syncthreads();
-    smem_fft<C, NT, +1, NTH, CW, CW, 1>(z, tw);
-    if (!__syncthreads_and(mbar_wait_bounded(bar, 0))) {
-        if (tid == 0) {
-            atomicExch(const_cast<int*>(&ctl->status), (int)PINT_ECUDA);
-            mbar_wait_bounded(bar, 0);   // let the copies in flight land before the CTA exits
-        }
-        __syncthreads();
-        return;
-    }
-    float d2 = 0.f, u2 = 0.f;
-    const bool want = dpart != nullptr;
-#pragma unroll 4
-    for (int e = tid; e < NT * CH; e += NTH) {
-        const int c = (e % CH) * 2, n = e / CH;
-        const C v0 = z[n * CW + c], v1 = z[n * CW + c + 1];
-        const long pa = p0 + c, pb = p0 + CW + c;
-        const double gi = ginv[n];
-        double* row = U + (size_t)n * nspace;
-        const double* urow = ub + n * 2 * CW;
-        if (pa < nspace) {
-            const double2 u = *reinterpret_cast<const double2*>(urow + c);
-            const double2 w = make_double2(fma(f32_to_f64_exact(v0.x), gi, u.x), fma(f32_to_f64_exact(v1.x), gi, u.y));
-            __stcs(reinterpret_cast<double2*>(row + pa), w);
-            if (want) {
-                const float g32 = f64_to_f32_trunc(gi), da0 = v0.x * g32, da1 = v1.x * g32;
-                const float w0 = f64_to_f32_trunc(w.x), w1 = f64_to_f32_trunc(w.y);
-                d2 = fmaf(da1, da1, fmaf(da0, da0, d2));
-                u2 = fmaf(w1, w1, fmaf(w0, w0, u2));
-            }
-        }
-        if (pb < nspace) {
-            const double2 u = *reinterpret_cast<const double2*>(urow + CW + c);
-            const double2 w = make_double2(fma(f32_to_f64_exact(v0.y), gi, u.x), fma(f32_to_f64_exact(v1.y), gi, u.y));
-            __stcs(reinterpret_cast<double2*>(row + pb), w);
-            if (want) {
-                const float g32 = f64_to_f32_trunc(gi), db0 = v0.y * g32, db1 = v1.y * g32;
-                const float w0 = f64_to_f32_trunc(w.x), w1 = f64_to_f32_trunc(w.y);
-                d2 = fmaf(db1, db1, fmaf(db0, db0, d2));
-                u2 = fmaf(w1, w1, fmaf(w0, w0, u2));
-            }
-        }
-    }
-    if (want) {  // deterministic block reduction (same tree every launch)
-        __shared__ double red[2][32];
-        double a = warp_sum((double)d2), b = warp_sum((double)u2);
-        if (tid % 32 == 0) { red[0][tid / 32] = a; red[1][tid / 32] = b; }
-        __syncthreads();
-        if (tid == 0) {
-            double A = 0.0, B = 0.0;
-            for (int w = 0; w < NTH / 32; ++w) { A += red[0][w]; B += red[1][w]; }
-            dpart[2 * blockIdx.x] = A;
-            dpart[2 * blockIdx.x + 1] = B;
-        }
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Long time axes (1024 < N_t <= 2^20): multi-pass (four-step) FFT with
 // N_t = f_0 f_1 ... f_{S-1}, S = 2 or 3 factors of 32..256.  The signal of the
@@ -730,14 +611,9 @@ static cudaError_t configure_time() {
     if constexpr (sizeof(T) == 4) {
         e = cudaFuncSetAttribute(k_time_inv<T, NT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
         if (e != cudaSuccess) return e;
-        if constexpr (NT <= 512) {
+        if constexpr (NT <= 512)
             e = cudaFuncSetAttribute(k_time_inv_ff_tma<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)TimeTmaCfg<NT>::SMEM);
-            if (e != cudaSuccess) return e;
-            if constexpr (NT >= 4)
-                e = cudaFuncSetAttribute(k_time_inv_pf<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)TimePfCfg<NT>::SMEM);
-        }
     }
     return e;
 }
@@ -784,16 +660,6 @@ static void time_fwd_nt(int nspace, const T* s, c_t<T>* S, const c_t<T>* twt, co
 template <class T, int NT>
 static void time_inv_nt(int nspace, const c_t<T>* S, const c_t<T>* twt, const double* ginv, double* out, int acc,
                         const Ctl* ctl, double* dpart, cudaStream_t st) {
-    if constexpr (sizeof(T) == 4 && NT >= 4 && NT <= 512) {
-        // PINT_MIXED's update with the iterate tile prefetched (even point counts)
-        if (acc && ctl && nspace % 2 == 0) {
-            using Cfg = TimePfCfg<NT>;
-            const int grid = (nspace + 2 * Cfg::CW - 1) / (2 * Cfg::CW);
-            launch_pdl(k_time_inv_pf<NT>, dim3(grid), dim3(Cfg::NTH), Cfg::SMEM, st, nspace, S, twt, ginv, out, ctl,
-                       dpart);
-            return;
-        }
-    }
     constexpr int CW = TimeCfg<T, NT>::CW;
     int grid = (nspace + 2 * CW - 1) / (2 * CW);
     k_time_inv<T, NT, 0><<<grid, TimeCfg<T, NT>::NTH, TimeCfg<T, NT>::SMEM, st>>>(nspace, S, twt, ginv, nullptr, out,
@@ -925,25 +791,14 @@ int time_inv_ff_blocks(int nt, int nspace, const Ctl* ctl) {
     return time_inv_blocks(nt, nspace, 1);
 }
 
-// CTAs of the Step 3 launch that accumulates (the FP64 update of the FP64 iterate;
-// for complex64 transforms on an even point count, N_t 4..512, the prefetching kernel).
 int time_inv_blocks(int nt, int nspace, int f32) {
     if (nt > 1024) return time_long_blocks(nt, nspace, f32);
-    const bool pf = f32 && nspace % 2 == 0 && nt >= 4 && nt <= 512;
     int cw = 32;
     switch (nt) {
 #define CW_(N) case N: cw = f32 ? TimeCfg<float, N>::CW : TimeCfg<double, N>::CW; break;
         CW_(2) CW_(4) CW_(8) CW_(16) CW_(32) CW_(64) CW_(128) CW_(256) CW_(512) CW_(1024)
 #undef CW_
         default: break;
-    }
-    if (pf) {
-        switch (nt) {
-#define CW_(N) case N: cw = TimePfCfg<N>::CW; break;
-            CW_(4) CW_(8) CW_(16) CW_(32) CW_(64) CW_(128) CW_(256) CW_(512)
-#undef CW_
-            default: break;
-        }
     }
     return (nspace + 2 * cw - 1) / (2 * cw);
 }
