@@ -258,12 +258,13 @@ def test_config2_full_size_in_the_benchmark_configuration():
         assert O.rel_err(U, ref) < 1e-8
 
 
-def test_config3_full_size_last_window_properties():
+@pytest.mark.parametrize("precision", ["mixed_ff", "mixed"])
+def test_config3_full_size_last_window_properties(precision):
     # 2-D CH 512^2, eps = 0.02, dt = 1e-4, 8 windows of 256 steps with the adaptive window policy: the
     # sequential oracle is out of reach here, so the returned last window is checked by properties that
     # hold at any size: the oracle's per-step residual of its own levels, zero mass, decreasing energy.
     kw = full(dict(equation="cahn_hilliard", dim=2, nx=512, ny=512, bc="neumann", eps=0.02, nt=256, n_windows=8,
-                   T=2048 * 1e-4, alpha=1e-2, precision="mixed_ff", tol=1e-8, max_iter=250))
+                   T=2048 * 1e-4, alpha=1e-2, precision=precision, tol=1e-8, max_iter=250))
     p = oprob(kw)
     u0 = synth.u0_ch(p.nspace, 0)
     with pint.Solver(**kw) as s:
@@ -282,7 +283,9 @@ def test_config3_full_size_last_window_properties():
     # levels 2..256 of the window solve the backward-Euler steps from level 1
     sub = O.Problem(equation=O.CAHN_HILLIARD, dim=2, nx=512, ny=512, bc="neumann", eps=0.02, T=255 * p.dt, nt=255)
     rho = np.linalg.norm(O.residual(sub, U[0], U[1:])) / O.rhs_norm(sub, U[0])
-    assert rho < 1e-7, rho
+    # float-float: its 48-bit iterate leaves a per-step floor near 1e-8 at this stiffness; the mixed form
+    # (FP64 iterate): each adaptive segment of the window stops at rho <= 1e-8 against its own b
+    assert rho < (1e-7 if precision == "mixed_ff" else 3e-8), rho
     assert max(abs(O.discrete_mass(p, u)) for u in U) < 1e-12
     E = [O.discrete_energy(p, u) for u in U]
     assert all(E[i + 1] <= E[i] * (1 + 1e-12) for i in range(len(E) - 1))
