@@ -207,7 +207,12 @@ typedef struct {
     long long launches[PINT_NPHASE];
 } pint_profile;
 
-/* Enable (on = 1) or disable event timing of the phases.  Errors: PINT_EINVAL, PINT_ECUDA. */
+/* Event timing of the phases: on = 1 records events around every phase; on = 2
+ * (coarse) records only two spans per iteration, so that no event splits the
+ * kernels of one step: the residual with its convergence check, booked to
+ * phase 0, and the whole diagonalized step (Steps 1-3), booked to phase 2;
+ * phases 1 and 3-6 then read 0 ms.  on = 0 disables.  Timed solves run the
+ * host-launched loop (no graph).  Errors: PINT_EINVAL, PINT_ECUDA. */
 int pint_profile_enable(pint_handle* h, int on);
 
 /* Copy the accumulated profile into *out; reset = 1 zeroes it afterwards. */

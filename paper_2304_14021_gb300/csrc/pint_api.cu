@@ -599,8 +599,17 @@ static void prof_flush(pint_handle* h) {  // stream must be idle past the record
     }
     h->nev = 0;
 }
+// prof_on 2 (coarse): events only around the residual with its check (booked
+// to PH_RES) and around the whole diagonalized step, Steps 1-3 (booked to
+// PH_TFWD), so that the event records do not split the step's kernels.
+static bool prof_coarse_skip_begin(const pint_handle* h, int ph) {
+    return h->prof_on == 2 && ph != PH_RES && ph != PH_TFWD && ph != PH_SETUP;
+}
+static bool prof_coarse_skip_end(const pint_handle* h, int ph) {
+    return h->prof_on == 2 && ph != PH_CHECK && ph != PH_TINV && ph != PH_SETUP;
+}
 static void prof_begin(pint_handle* h, int ph) {
-    if (!h->prof_on) return;
+    if (!h->prof_on || prof_coarse_skip_begin(h, ph)) return;
     if (h->nev == pint_handle::NEV) {
         cudaStreamSynchronize(h->st);
         prof_flush(h);
@@ -610,7 +619,7 @@ static void prof_begin(pint_handle* h, int ph) {
 }
 static void prof_end(pint_handle* h, int ph, int nlaunch) {
     h->launches[ph] += nlaunch;
-    if (!h->prof_on) return;
+    if (!h->prof_on || prof_coarse_skip_end(h, ph)) return;
     cudaEventRecord(h->ev[2 * h->nev + 1], h->st);
     h->nev++;
 }
@@ -1186,7 +1195,7 @@ static int read_ctl(pint_handle* h) {
 }
 
 int pint_profile_enable(pint_handle* h, int on) {
-    if (!h || (on != 0 && on != 1)) return PINT_EINVAL;
+    if (!h || on < 0 || on > 2) return PINT_EINVAL;
     if (on && !h->ev[0]) {
         for (int i = 0; i < 2 * pint_handle::NEV; ++i)
             if (cudaEventCreate(&h->ev[i]) != cudaSuccess) return PINT_ECUDA;

@@ -334,8 +334,10 @@ class Solver:
         if rc != PINT_OK:
             raise PintError(rc, "pint_set_option")
 
-    def profile_enable(self, on: bool = True) -> None:
-        rc = lib().pint_profile_enable(self._h, 1 if on else 0)
+    def profile_enable(self, on=True) -> None:
+        """on: False/0 off, True/1 every phase, 2 coarse (residual + check, whole Steps 1-3)."""
+        mode = 2 if on == 2 else (1 if on else 0)
+        rc = lib().pint_profile_enable(self._h, mode)
         if rc != PINT_OK:
             raise PintError(rc, "pint_profile_enable")
 

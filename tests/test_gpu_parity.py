@@ -487,6 +487,39 @@ def test_graph_loop_equals_host_loop(precision, init):
     assert O.rel_err(Ua, O.sequential(p, u0)[-p.nt:]) < (1e-10 if precision == "fp64" else 1e-8)
 
 
+@pytest.mark.parametrize("precision", ["mixed", "mixed_ff"])
+def test_phase_timing_modes_leave_results_and_counts_unchanged(precision):
+    # Event timing (every phase, or the coarse two spans per iteration) records
+    # events only: the kernels and their results are those of the untimed solve.  The coarse mode books the residual with its check to
+    # the residual phase and Steps 1-3 to the time-FFT phase, nothing elsewhere.
+    kw = full(dict(equation="linear_ch", dim=2, nx=64, ny=64, bc="neumann", eps=0.05, beta=0.5, nt=32,
+                   T=0.025, precision=precision, tol=1e-10, init_guess=0))
+    p = oprob(kw)
+    u0 = synth.u0_uniform(p.nspace, -0.05, 0.05, 8)
+    out = []
+    with pint.Solver(**kw) as s:
+        for mode in (0, 1, 2):
+            s.profile_enable(mode)
+            s.profile_read(reset=True)
+            U = torch.zeros(p.nt, p.nspace, dtype=torch.float64, device="cuda")
+            st = s.solve(dev(u0), U)
+            torch.cuda.synchronize()
+            out.append((host(U), st, s.profile_read(reset=True)))
+        s.profile_enable(False)
+    (U0, s0, p0), (U1, s1, p1), (U2, s2, p2) = out
+    assert np.array_equal(U0, U1) and np.array_equal(U0, U2)
+    assert s0["iters"] == s1["iters"] == s2["iters"]
+    for k in pint.PHASES:
+        # both timed modes run the host-launched loop (its launches include the
+        # ones queued past the stop, which the graph loop does not count)
+        assert p1[k]["launches"] == p2[k]["launches"], k
+        assert p0[k]["ms"] == 0.0
+    assert p2["residual"]["ms"] > 0 and p2["time_fwd"]["ms"] > 0
+    for k in ("check", "spatial0", "spatial1", "spatial2", "time_inv"):
+        assert p2[k]["ms"] == 0.0, k
+    assert p1["time_inv"]["ms"] > 0
+
+
 # --- Cahn-Hilliard windows: the adaptive window policy (R9) -------------------
 
 CH_SPINODAL = dict(equation="cahn_hilliard", dim=2, nx=32, ny=32, bc="neumann", eps=0.02, nt=128, n_windows=1,
