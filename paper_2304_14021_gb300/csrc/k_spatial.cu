@@ -529,6 +529,265 @@ __global__ void __launch_bounds__(512, ColWCfg<T, N>::MINB) k_cols_dct_fdi_w(int
 }
 
 // ---------------------------------------------------------------------------
+// Columns, register four-step form (N = G*G, G = 8 or 16; FP32; nx even).  G
+// lanes of a warp transform one column.  Write the column's even/odd
+// reordered sequence as v_j, j = j1 + G j2.  Lane j1 takes the G-point DFT
+// over j2 in registers and multiplies by exp(-2 pi i j1 k2 / N); the lanes
+// swap through the column's shared-memory slot, after which lane k2 holds
+// (Y_{j1,k2})_{j1}, whose G-point DFT over j1 is V_{k2 + G k1} in natural
+// order.  The DCT-II coefficient pairs p with q = N - p, held by lane
+// (G - k2) mod G: a shuffle brings V_q, each lane forms and divides its own
+// X_p, a second shuffle brings the partner's X_q for the inverse
+// pre-twiddle.  The inverse FFT runs the same steps backwards; its 1/N sits
+// in the divide.
+// Tile: CW = 16 columns as 8 column pairs; pair cp, reordered row r is the
+// 16-byte chunk cp*N + (swz(r) ^ cp), so the copies in and out move 16 bytes
+// per lane.  A half-warp holds 8 lanes of each column of a pair, so the
+// strided lane accesses of both DFT steps cover all banks once.  Per-CTA
+// tables in shared memory: the step twiddles as [j][s] (consecutive lanes,
+// consecutive entries), the DCT twiddles w_p and the y eigenvalues.
+// ---------------------------------------------------------------------------
+template <class T, int N> struct ColRCfg {
+    static constexpr int G = N == 64 ? 8 : 16;      // lanes per column = values per lane
+    static constexpr int CW = 16, NPAIR = CW / 2, NTH = G * CW;
+    static constexpr size_t TILE = sizeof(c_t<T>) * (size_t)N * CW;
+    static constexpr int STAGES = 2;
+    static constexpr size_t TAB_OFF = STAGES * TILE;
+    static constexpr size_t SMEM = TAB_OFF + sizeof(c_t<T>) * (G * G + N) + sizeof(T) * N;
+    static constexpr int MINB = N == 64 ? 8 : 2;
+};
+template <class T, int N>
+constexpr bool cols_reg_ok = sizeof(T) == 4 && (N == 64 || N == 256);
+
+// a * exp(DIR 2 pi i M / 16), M a compile-time constant
+template <int DIR, int M, class C> __device__ __forceinline__ C rot16(C a) {
+    using R = typename real_of<C>::type;
+    constexpr double c1 = 0.92387953251128675613, s1 = 0.38268343236508977173, h = 0.70710678118654752440;
+    constexpr double cs[10] = {1.0, c1, h, s1, 0.0, -s1, -h, -c1, -1.0, -c1};
+    constexpr double sn[10] = {0.0, s1, h, c1, 1.0, c1, h, s1, 0.0, -s1};
+    if constexpr (M == 0) {
+        return a;
+    } else if constexpr (M == 4) {
+        return rot90<DIR>(a);
+    } else {
+        const R c = R(cs[M]), s = R(DIR * sn[M]);
+        return mkc(a.x * c - a.y * s, a.x * s + a.y * c);
+    }
+}
+// 16-point DFT in registers, natural order in and out: with j = a + 4c and
+// k = b + 4d, X_k = sum_a w16^{ab} w4^{ad} (sum_c v_{a+4c} w4^{cb}).
+template <int DIR, class C> __device__ __forceinline__ void dft16(C* v) {
+    C t[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        t[a][0] = v[a];
+        t[a][1] = v[a + 4];
+        t[a][2] = v[a + 8];
+        t[a][3] = v[a + 12];
+        dft4<DIR>(t[a]);
+    }
+    t[1][1] = rot16<DIR, 1>(t[1][1]);
+    t[1][2] = rot16<DIR, 2>(t[1][2]);
+    t[1][3] = rot16<DIR, 3>(t[1][3]);
+    t[2][1] = rot16<DIR, 2>(t[2][1]);
+    t[2][2] = rot16<DIR, 4>(t[2][2]);
+    t[2][3] = rot16<DIR, 6>(t[2][3]);
+    t[3][1] = rot16<DIR, 3>(t[3][1]);
+    t[3][2] = rot16<DIR, 6>(t[3][2]);
+    t[3][3] = rot16<DIR, 9>(t[3][3]);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        C u[4] = {t[0][b], t[1][b], t[2][b], t[3][b]};
+        dft4<DIR>(u);
+        v[b] = u[0];
+        v[b + 4] = u[1];
+        v[b + 8] = u[2];
+        v[b + 12] = u[3];
+    }
+}
+template <int G, int DIR, class C> __device__ __forceinline__ void dft_reg(C* v) {
+    if constexpr (G == 8) dft8<DIR>(v);
+    else dft16<DIR>(v);
+}
+template <class C> __device__ __forceinline__ C shfl_c(C a, int src) {
+    return mkc(__shfl_sync(0xffffffffu, a.x, src), __shfl_sync(0xffffffffu, a.y, src));
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+// approximate reciprocal (PTX rcp.approx: relative error within 2^-23)
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// One step of the pair solve on the entries v[m] and v[G-1-m] of lane s,
+// which holds V_{s + G k1} in v[k1].  For s != 0 the pair of entry m is the
+// partner lane's entry G-1-m and vice versa; lane 0 is its own partner with
+// pairs (k1, G - k1), so it takes entries m+1 and G-1-m here (m = G/2 - 1
+// gives it the self-paired entry G/2) and keeps entry 0 for the end.  Each
+// entry is updated in place exactly once.  Each lane forms its own scaled
+// DCT-II coefficient X'_p = (w_p V_p + conj(w_p) V_q) dinv(p), dinv(p) =
+// 1/(2 N D_p), and the inverse pre-twiddle V'_p = conj(w_p)(X'_p - i X'_q)
+// takes the partner's X'_q as the partner rounded it, so both members of a
+// pair are built from the same two coefficients: a rounding error of a small
+// coefficient (cancellation when the other member dominates) stays in that
+// coefficient's own mode instead of leaking into the other one, where the
+// next residual would multiply it by the other, possibly far larger, D.
+template <int G, int M, class C, class DenF>
+__device__ __forceinline__ void pair_step(C* v, int s, int partner, const C* wt, DenF&& dinv) {
+    constexpr int B = G - 1 - M, M1 = (M + 1) % G;
+    const bool z = s == 0;
+    const C va = z ? v[M1] : v[M], vb = v[B];
+    const int pa = s + G * (z ? M1 : M), pb = s + G * B;
+    const C rb = shfl_c(vb, partner), ra = shfl_c(v[M], partner);   // the partner's entries B and M
+    const C qa = z ? vb : rb, qb = z ? va : ra;                     // V of the pair of a, of b
+    const C wa = wt[pa], wb = wt[pb];
+    const C xa = cmul(dinv(pa), cmul(wa, va) + cmul(conjc(wa), qa));
+    const C xb = cmul(dinv(pb), cmul(wb, vb) + cmul(conjc(wb), qb));
+    const C rxb = shfl_c(xb, partner), rxa = shfl_c(xa, partner);
+    const C xqa = z ? xb : rxb, xqb = z ? xa : rxa;                 // X' of the pair of a, of b
+    const C na = cmul(conjc(wa), xa - rot90<+1>(xqa)), nb = cmul(conjc(wb), xb - rot90<+1>(xqb));
+    if constexpr (M1 != B) {
+        v[M] = z ? v[M] : na;
+        v[M1] = z ? na : v[M1];
+        v[B] = nb;
+    } else {                                                // lane 0: a and b are both entry G/2
+        v[M] = z ? v[M] : na;
+        v[B] = z ? na : nb;
+    }
+}
+template <int G, int M> struct PairSteps {
+    template <class C, class DenF>
+    __device__ __forceinline__ static void run(C* v, int s, int partner, const C* wt, DenF&& f) {
+        pair_step<G, M>(v, s, partner, wt, f);
+        PairSteps<G, M + 1>::run(v, s, partner, wt, f);
+    }
+};
+template <int G> struct PairSteps<G, G / 2> {
+    template <class C, class DenF>
+    __device__ __forceinline__ static void run(C*, int, int, const C*, DenF&&) {}
+};
+
+template <class T, int N>
+__global__ void __launch_bounds__(ColRCfg<T, N>::NTH, ColRCfg<T, N>::MINB)
+    k_cols_dct_fdi_r(int nx, int nk, c_t<T>* __restrict__ S, Tabs<T> tb, SolveCoef co, const Ctl* __restrict__ ctl) {
+    using C = c_t<T>;
+    using Cfg = ColRCfg<T, N>;
+    constexpr int G = Cfg::G, CW = Cfg::CW, NPAIR = Cfg::NPAIR, NTH = Cfg::NTH;
+    constexpr int RSTEP = NTH / NPAIR, NCOPY = N / RSTEP;   // rows per copy sweep, sweeps per tile
+    static_assert(G * G == N && (G == 8 || G == 16) && Cfg::STAGES == 2 && N % RSTEP == 0, "four-step shape");
+    pdl_wait();
+    if (ctl && ctl->status != ST_RUNNING) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4* chunks = reinterpret_cast<float4*>(smem_raw);   // TCH chunks per stage
+    constexpr int TCH = (int)(Cfg::TILE / 16);
+    C* tw1 = reinterpret_cast<C*>(smem_raw + Cfg::TAB_OFF);  // [j][s]: exp(-2 pi i s j / N)
+    C* wt = tw1 + G * G;                                     // [p]: w_p = exp(-i pi p / (2N))
+    T* ly = reinterpret_cast<T*>(wt + N);                    // [p]: y eigenvalues
+    const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
+    // lane bits: 0-2 low bits of s, 3 column of the pair, 4 high bit of s (G = 16) or pair (G = 8)
+    const int half = (lane >> 3) & 1;
+    const int s = G == 16 ? (lane & 7) | ((lane >> 4) << 3) : (lane & 7);
+    const int cp = G == 16 ? warp : 2 * warp + (lane >> 4);
+    const int c = 2 * cp + half;                              // column of the tile
+    const int sp = (G - s) % G;                               // partner's s
+    const int partner = G == 16 ? (sp & 7) | (half << 3) | ((sp >> 3) << 4) : sp | (lane & 24);
+    const int nxb = (nx + CW - 1) / CW;
+    const int ntiles = nk * nxb;
+    // copies: thread (pair ccp, row y0 + RSTEP i) moves one 16-byte chunk
+    const int ccp = tid % NPAIR, y0 = tid / NPAIR;
+    auto chunk_of = [](int pr, int r) { return pr * N + (swz<1>(r) ^ pr); };
+    auto stage = [&](int t, float4* buf) {
+        const int k = t / nxb, x0 = (t % nxb) * CW;
+        const bool ok = x0 + 2 * ccp < nx;
+        const C* src = S + (size_t)k * N * nx + (size_t)y0 * nx + x0 + 2 * ccp;
+#pragma unroll
+        for (int i = 0; i < NCOPY; ++i) {
+            const int y = y0 + RSTEP * i;
+            float4* d = buf + chunk_of(ccp, dct_pos(y, N));
+            if (ok) cp_async16(d, src + (size_t)RSTEP * i * nx);
+            else *d = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        cp_async_commit_grp();
+    };
+    stage(blockIdx.x, chunks);
+    for (int i = tid; i < G * G; i += NTH) tw1[i] = tb.twy[(i / G) * (i % G)];
+    for (int p = tid; p < N; p += NTH) {
+        wt[p] = tb.wy[p];
+        ly[p] = tb.lamy[p];
+    }
+    const T c2 = T(co.c2), c1 = solve_c1<T>(co, ctl);
+    const T sigma = T(0.5) / T(N);
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        float4* buf = chunks + (it & 1) * TCH;
+        if (t + gridDim.x < ntiles) {
+            stage(t + gridDim.x, chunks + ((it + 1) & 1) * TCH);
+            cp_async_wait_grp<1>();
+        } else {
+            cp_async_wait_grp<0>();
+        }
+        __syncthreads();
+        const int k = t / nxb, x0 = (t % nxb) * CW, x = x0 + c;
+        C* el = reinterpret_cast<C*>(buf) + half;             // element r of our column: el[2 * chunk_of(cp, r)]
+        C v[G];
+        // forward: lane s = j1 transforms over j2, twiddles, swaps; then lane s = k2 over j1
+#pragma unroll
+        for (int j = 0; j < G; ++j) v[j] = el[2 * chunk_of(cp, s + G * j)];
+        dft_reg<G, -1>(v);
+#pragma unroll
+        for (int j = 1; j < G; ++j) v[j] = cmul(v[j], tw1[j * G + s]);
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < G; ++j) el[2 * chunk_of(cp, j + G * s)] = v[j];
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < G; ++j) v[j] = el[2 * chunk_of(cp, s + G * j)];
+        dft_reg<G, -1>(v);                                    // v[k1] = V_{s + G k1}
+        // the solve on the FFT values (identity above); dead columns pass through
+        const bool live = x < nx;
+        const T lx = live ? tb.lamx[x] : T(0);
+        const C l1 = tb.lam1[k], l2 = tb.lam2[k];
+        // PinT-II adds lambda_3k Lam, lambda_3k = 1 - dt lambda_1k (zero otherwise)
+        const T g3 = tb.dte != T(0) ? T(1) - tb.dte * l1.x : T(0), h3 = -tb.dte * l1.y;
+        auto dinv = [&](int p) {
+            const T lam = lx + ly[p];
+            const T mu = (c2 * lam + c1) * lam;
+            const T dx = fmaf(l2.x, mu, fmaf(g3, lam, l1.x)), dy = fmaf(l2.y, mu, fmaf(h3, lam, l1.y));
+            const T m = sigma * rcp_approx(fmaf(dx, dx, dy * dy));
+            return live ? mkc(dx * m, -dy * m) : mkc(sigma, T(0));
+        };
+        PairSteps<G, 0>::run(v, s, partner, wt, dinv);
+        if (s == 0) v[0] = scalec(cmul(v[0], dinv(0)), T(2));  // p = 0 pairs with itself: V'_0 = X'_0
+        // inverse: lane s = k2 over k1, twiddles, swaps; then lane s = j1 over k2
+        dft_reg<G, +1>(v);
+#pragma unroll
+        for (int j = 1; j < G; ++j) v[j] = cmul(v[j], conjc(tw1[j * G + s]));
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < G; ++j) el[2 * chunk_of(cp, j + G * s)] = v[j];
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < G; ++j) v[j] = el[2 * chunk_of(cp, s + G * j)];
+        dft_reg<G, +1>(v);
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < G; ++j) el[2 * chunk_of(cp, s + G * j)] = v[j];
+        __syncthreads();
+        // copy out: 16-byte chunks, row by row
+        if (x0 + 2 * ccp < nx) {
+            float4* dst = reinterpret_cast<float4*>(S + (size_t)k * N * nx + (size_t)y0 * nx + x0 + 2 * ccp);
+#pragma unroll
+            for (int i = 0; i < NCOPY; ++i)
+                dst[(size_t)RSTEP * i * nx / 2] = buf[chunk_of(ccp, dct_pos(y0 + RSTEP * i, N))];
+        }
+        __syncthreads();   // buf is refilled two tiles later
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Dense path: one CTA per vector of length n (row: stride 1; column: stride nx).
 //   FWD: X = F x;   INV: x = Finv X;   FDI: both with the division between.
 // axis 0 = x (rows, vector b = k*ny + y), axis 1 = y (columns, b = k*nx + x).
@@ -823,11 +1082,19 @@ static int cols_resident();
 template <class T, int N>
 static int cols_w_resident();
 template <class T, int N>
+static int cols_r_resident();
+template <class T, int N>
 static cudaError_t cfg_cols() {
     cudaError_t e = cudaFuncSetAttribute(k_cols_dct_fdi<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)ColCfg<T, N>::SMEM);
     if (e != cudaSuccess) return e;
     if (cols_resident<T, N>() <= 0) return cudaErrorInvalidConfiguration;
+    if constexpr (cols_reg_ok<T, N>) {
+        if ((e = cudaFuncSetAttribute(k_cols_dct_fdi_r<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)ColRCfg<T, N>::SMEM)))
+            return e;
+        if (cols_r_resident<T, N>() <= 0) return cudaErrorInvalidConfiguration;
+    }
     if constexpr (cols_warp_ok<T, N>) {
         if ((e = cudaFuncSetAttribute(k_cols_dct_fdi_w<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)ColWCfg<T, N>::SMEM)))
@@ -943,8 +1210,24 @@ static int cols_w_resident() {
     return r;
 }
 template <class T, int N>
+static int cols_r_resident() {
+    static const int r = persistent_ctas(k_cols_dct_fdi_r<T, N>, ColRCfg<T, N>::NTH, ColRCfg<T, N>::SMEM);
+    return r;
+}
+template <class T, int N>
 static cudaError_t cols_n(int nx, int nk, c_t<T>* S, const Tabs<T>& tb, SolveCoef co, const Ctl* ctl,
                           cudaStream_t st) {
+    if constexpr (cols_reg_ok<T, N>) {
+        using W = ColRCfg<T, N>;
+        if (nx % 2 == 0 && reinterpret_cast<uintptr_t>(S) % 16 == 0) {   // 16-byte copies of column pairs
+            const int resident = cols_r_resident<T, N>();
+            if (resident <= 0) return cudaErrorInvalidConfiguration;
+            const int ntiles = nk * ((nx + W::CW - 1) / W::CW);
+            const int grid = ntiles < resident ? ntiles : resident;
+            launch_pdl(k_cols_dct_fdi_r<T, N>, dim3(grid), dim3(W::NTH), W::SMEM, st, nx, nk, S, tb, co, ctl);
+            return cudaSuccess;
+        }
+    }
     if constexpr (cols_warp_ok<T, N>) {
         using W = ColWCfg<T, N>;
         const int resident = cols_w_resident<T, N>();

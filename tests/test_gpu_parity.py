@@ -237,6 +237,29 @@ def test_linear_ch_2d_solve(precision, alpha, init):
     assert err < (1e-10 if precision == "fp64" else 1e-8), err
 
 
+@pytest.mark.parametrize("precision,alpha", [("mixed", 1e-2), ("mixed", 1e-3), ("mixed_ff", 1e-2)])
+def test_mixed_forms_track_the_exact_iteration(precision, alpha):
+    # The FP64 iteration of the oracle (tests/golden/make_exact_iterations_linear_ch_256.py) reaches
+    # 1e-8 in 4 (alpha 1e-2) / 3 (alpha 1e-3) iterations on the 256^2 x 128 benchmark configuration.
+    # The mixed forms compute the residual FP64-accurately and the transforms in FP32: the FP32
+    # rounding that the stiff high modes amplify in the next residual costs at most one iteration
+    # here.  A Step 2 kernel whose rounding leaks from a dominant DCT coefficient into its
+    # partner's mode (the pair p, N - p) took 7.
+    with open(os.path.join(GOLDEN, "exact_iterations_linear_ch_256.json")) as f:
+        hist = json.load(f)["history"][f"{alpha:g}"]
+    tol = 1e-8
+    exact = next(k for k, h in enumerate(hist) if h <= tol)
+    kw = full(dict(equation="linear_ch", dim=2, nx=256, ny=256, bc="neumann", eps=0.05, beta=0.5, T=0.1, nt=128,
+                   precision=precision, alpha=alpha, tol=tol, init_guess=2))
+    u0 = synth.u0_uniform(256 * 256, -0.05, 0.05, 0)
+    with pint.Solver(**kw) as s:
+        s.set_time_gemm(0)
+        U = torch.zeros(128, 256 * 256, dtype=torch.float64, device="cuda")
+        st = s.solve(dev(u0), U)
+    assert st["rc"] == 0 and st["rel_residual"] <= tol
+    assert st["iters"] <= exact + 1, (st["iters"], exact, st["hist"][:st["iters"] + 1])
+
+
 def test_config2_full_size_in_the_benchmark_configuration():
     # The benchmark's workload exactly: 2-D linCH 256^2 x 128, T = 0.1, float-float, zero start, the
     # CUDA-graph loop, rel. residual 1e-8, alpha 1e-2 and 1e-3; against the oracle's sequential solution
