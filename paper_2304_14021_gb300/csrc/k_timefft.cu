@@ -163,6 +163,22 @@ __global__ void __launch_bounds__(TimeCfg<T, NT>::NTH)
             if (k > 0 && k < NT / 2) z[(NT - k) * CW + c] = mkc(a.x + b.y, b.x - a.y);
         }
     }
+    if constexpr (sizeof(T) == 4 && OUTK == 0) {
+        // the iterate's rows that the update reads, pulled into L2 while the
+        // FFT runs: 4 lines of 128 B per level (the CTA's two 32-point
+        // segments), one line per thread and pass; lines starting past the row
+        // end are skipped
+        if (vec && accumulate) {
+            for (int i = tid; i < NT * 4; i += NTH) {
+                const int n = i >> 2, q = i & 3;
+                const long p = (q < 2 ? p0 : p0 + CW) + 16 * (q & 1);
+                if (p < nspace) {
+                    const double* a = out + (size_t)n * nspace + p;
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+                }
+            }
+        }
+    }
     __syncthreads();
     smem_fft<C, NT, +1, NTH, CW, CW, 1>(z, tw);
     // dpart != nullptr: per-CTA partial sums (sum delta^2, sum U_new^2) of the
