@@ -360,7 +360,13 @@ def oracle_feasible(wl: dict) -> bool:
 
 def start_oracle_worker(workload: str, seed: int):
     path = os.path.join(tempfile.gettempdir(), f"pint_oracle_{workload}_{seed}_{os.getpid()}.npy")
-    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    # it runs beside the timed GPU passes: few threads at low priority, so that
+    # the host thread that launches the solves and reads their status is not
+    # kept waiting for a core (the timed region ends with an event recorded
+    # after the solve's final synchronization)
+    nthr = "2"
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="", OMP_NUM_THREADS=nthr, OPENBLAS_NUM_THREADS=nthr,
+               MKL_NUM_THREADS=nthr)
     cmd = [sys.executable, os.path.abspath(__file__), "--oracle-worker", "--workload", workload, "--seed", str(seed),
            "--oracle-out", path]
     proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env, cwd=ROOT)
@@ -890,6 +896,10 @@ def main() -> None:
         print(json.dumps(cpu_worker(args.workload, args.alpha, args.cpu_budget, args.seed, args.cpu_samples)))
         return
     if args.oracle_worker:
+        try:
+            os.nice(15)
+        except OSError:
+            pass
         print(json.dumps(oracle_solution_worker(args.workload, args.seed, args.oracle_out)))
         return
     if args.impl == "reference":
