@@ -615,7 +615,8 @@ template <class C> __device__ __forceinline__ C shfl_c(C a, int src) {
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
-// approximate reciprocal (PTX rcp.approx: relative error within 2^-23)
+// approximate reciprocal (PTX rcp.approx.ftz.f32): its error is far below the
+// rounding of the complex64 transforms around the divide
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
