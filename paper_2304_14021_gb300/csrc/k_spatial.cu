@@ -20,6 +20,7 @@
 #include <cooperative_groups.h>
 
 #include "../../include/pint.h"
+#include "colr_map.cuh"
 #include "pint_common.cuh"
 #include "pint_kernels.h"
 #include "spatial.cuh"
@@ -39,8 +40,6 @@ template <class T> struct PackDst {
     int nt;
 };
 
-// position of x_i in the even/odd reordered sequence v (v_j = x_2j, v_{n-1-j} = x_{2j+1})
-__device__ __forceinline__ int dct_pos(int i, int n) { return (i & 1) ? n - 1 - (i >> 1) : (i >> 1); }
 
 // DCT-II post-twiddle on the pair (p, q = n-p): V -> X.
 template <class C>
@@ -541,8 +540,8 @@ __global__ void __launch_bounds__(512, ColWCfg<T, N>::MINB) k_cols_dct_fdi_w(int
 // pre-twiddle.  The inverse FFT runs the same steps backwards; its 1/N sits
 // in the divide.
 // Tile: CW = 16 columns as 8 column pairs; pair cp, reordered row r is the
-// 16-byte chunk cp*N + (swz(r) ^ cp), so the copies in and out move 16 bytes
-// per lane.  A half-warp holds 8 lanes of each column of a pair, so the
+// 16-byte chunk colr::chunk(N, cp, r) (an XOR swizzle within aligned groups
+// of G chunks), so the copies in and out move 16 bytes per lane.  A half-warp holds 8 lanes of each column of a pair, so the
 // strided lane accesses of both DFT steps cover all banks once.  Per-CTA
 // tables in shared memory: the step twiddles as [j][s] (consecutive lanes,
 // consecutive entries), the DCT twiddles w_p and the y eigenvalues.
@@ -638,7 +637,7 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // next residual would multiply it by the other, possibly far larger, D.
 template <int G, int M, class C, class DenF>
 __device__ __forceinline__ void pair_step(C* v, int s, int partner, const C* wt, DenF&& dinv) {
-    constexpr int B = G - 1 - M, M1 = (M + 1) % G;
+    constexpr int B = colr::pair_b(G, M), M1 = colr::pair_a_lane0(G, M);
     const bool z = s == 0;
     const C va = z ? v[M1] : v[M], vb = v[B];
     const int pa = s + G * (z ? M1 : M), pb = s + G * B;
@@ -687,19 +686,14 @@ __global__ void __launch_bounds__(ColRCfg<T, N>::NTH, ColRCfg<T, N>::MINB)
     C* tw1 = reinterpret_cast<C*>(smem_raw + Cfg::TAB_OFF);  // [j][s]: exp(-2 pi i s j / N)
     C* wt = tw1 + G * G;                                     // [p]: w_p = exp(-i pi p / (2N))
     T* ly = reinterpret_cast<T*>(wt + N);                    // [p]: y eigenvalues
-    const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
-    // lane bits: 0-2 low bits of s, 3 column of the pair, 4 high bit of s (G = 16) or pair (G = 8)
-    const int half = (lane >> 3) & 1;
-    const int s = G == 16 ? (lane & 7) | ((lane >> 4) << 3) : (lane & 7);
-    const int cp = G == 16 ? warp : 2 * warp + (lane >> 4);
-    const int c = 2 * cp + half;                              // column of the tile
-    const int sp = (G - s) % G;                               // partner's s
-    const int partner = G == 16 ? (sp & 7) | (half << 3) | ((sp >> 3) << 4) : sp | (lane & 24);
+    const int tid = threadIdx.x;
+    const colr::Lane ln = colr::lane(G, tid);
+    const int s = ln.s, half = ln.half, cp = ln.cp, c = ln.c, partner = ln.partner;
     const int nxb = (nx + CW - 1) / CW;
     const int ntiles = nk * nxb;
     // copies: thread (pair ccp, row y0 + RSTEP i) moves one 16-byte chunk
     const int ccp = tid % NPAIR, y0 = tid / NPAIR;
-    auto chunk_of = [](int pr, int r) { return pr * N + (swz<1>(r) ^ pr); };
+    auto chunk_of = [](int pr, int r) { return colr::chunk(N, pr, r); };
     auto stage = [&](int t, float4* buf) {
         const int k = t / nxb, x0 = (t % nxb) * CW;
         const bool ok = x0 + 2 * ccp < nx;
